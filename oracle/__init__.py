@@ -1,0 +1,24 @@
+"""Plain FP64 CPU oracle of the hybrid-snapshot adaptive ROM (Zucatti & Zahr,
+"An adaptive, training-free reduced-order model for convection-dominated
+problems based on hybrid snapshots").
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
+only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg do.  It
+shares no code with the CUDA path (paper_2301_01718_gb300/); the only common
+module is workloads.py, which holds seeded inputs and no method arithmetic.
+
+Every function follows the paper's definitions in the paper's order, with
+numpy/LAPACK primitives (matmul, SVD, eigh, lstsq, solve) as steps and no
+blocking or fusion.  Where the paper is silent the reading taken is stated in
+the docstring and listed in the design doc.
+
+Modules
+  hdm     - conservation laws, FV fluxes, residual R_k (Eq. hdm), BDF1 /
+            SSP-RK2 steps, partial HDM (Eq. partial_hdm2)          [Sec. 2.1-2.3]
+  rom     - POD_m (Eq. pod), gappy coordinates (Eq. red_coord), DEIM and
+            ODEIM points (Eq. odeim), reference state (Eq. mean)   [Sec. 2.3.1]
+  select  - reconstruction error, RRE ordering and threshold (Eq. rre),
+            sampling-set algebra (union, setdiff, Neighbors)        [Sec. 2.3.3, 2.4]
+  filt    - Shapiro filters and the residual-gated filter loop     [Sec. 2.3.4]
+  arom    - Algorithm 1 driver and the metrics of Sec. 3.1
+"""
