@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid-snapshot adaptive ROM (Algorithm 1) on one GB300.
+
+Workload (default): 2D Euler, 2048 x 2048 cells (16.8 M dofs), FP32 states,
+a Mach-3 planar shock at a seeded angle with exact-state inflow and outflow
+sides, SSP-RK2 HDM, k = 64 POD modes from w = 128 snapshots, n_p = 128
+ODEIM points, top 5 % of cells by reconstruction error.  A "step" is one
+hybrid step of Algorithm 1 (lines 3-30: partial HDM, gappy coordinates,
+reconstruction, residual-gated filters, error indicator and selection,
+POD, ODEIM, sampling sets).  The method's own w warm-up full steps and the
+first rebuild run before the benchmark's warm-up steps.
+
+Metric: hybrid steps per second (whole job: summed over replicas).  Also
+reported: sampled cell-updates/s, per-stage milliseconds from CUDA events
+on the library stream, the roofline of the dominant bandwidth kernel,
+FP32-vs-FP64 error on a reduced grid, the end-to-end rate through host
+buffers, and the CPU oracle on a bounded sample.
+
+--impl reference runs the CPU oracle instead (the only reference this
+method has: the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "hybrid steps/s (Algorithm 1, 2D Euler 2048^2, FP32 states)"
+UNIT = "steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=2048)
+    p.add_argument("--k", type=int, default=64)
+    p.add_argument("--frac", type=float, default=0.05)
+    p.add_argument("--seed", type=int, default=3)
+    p.add_argument("--cpu-n", type=int, default=32, help="grid of the CPU oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-err", action="store_true")
+    return p.parse_args()
+
+
+def workload(a, n=None, prec=W.PREC_F32):
+    q0, cfg, _ = W.euler_oblique_shock(n=n or a.n, seed=a.seed, k=a.k, frac=a.frac)
+    return q0, cfg.with_(precision=prec)
+
+
+def config_dict(a, cfg):
+    return {"workload": f"euler2d_oblique_shock_{cfg.nx}x{cfg.ny}_k{cfg.m}_w{cfg.w}"
+                        f"_np{cfg.n_p}_top{a.frac:g}",
+            "cells": cfg.ncell, "dofs": cfg.ndof, "k": cfg.m, "w": cfg.w, "n_p": cfg.n_p,
+            "sample_frac": a.frac, "scheme": "SSP-RK2 Rusanov", "filters": "Shapiro 2/4/6",
+            "l2": "inputs larger than L2 (snapshot window %.1f GB)" % (4 * cfg.ndof * (cfg.w + 1) / 1e9)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_rate(a, steps=2):
+    """Time `steps` hybrid steps of the oracle on a cpu_n^2 grid of the same
+    workload (after its untimed warm-up); scale steps/s by cells to the
+    benchmark grid (the oracle's cost per step is linear in the cells)."""
+    from oracle import arom
+    q0, cfg = workload(a, n=a.cpu_n, prec=W.PREC_F64)
+    A = arom.Arom(q0, cfg)
+    while True:
+        info = A.step()
+        if info.rebuilt and A.k >= cfg.w:
+            break
+    ns = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ns += A.step().n_s
+    dt = time.perf_counter() - t0
+    scale = (a.cpu_n * a.cpu_n) / float(a.n * a.n)
+    return {"value": steps / dt * scale, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"{steps} hybrid steps of the same workload on a {a.cpu_n}x{a.cpu_n} grid "
+                      f"(k={cfg.m}, w={cfg.w}) in {dt:.1f} s, steps/s scaled by cells "
+                      f"({a.cpu_n}^2/{a.n}^2)",
+            "sample_steps_per_s": steps / dt, "sample_cell_updates_per_s": ns / dt}
+
+
+def _cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.strip().split(",") for r in self.out.read().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (FP32 states, 4 bytes)
+# ---------------------------------------------------------------------------
+
+def stage_bytes(cfg, m_eff, n_s_avg, s=4):
+    N, nc, w = cfg.ndof, cfg.ncell, cfg.w
+    frac_breve = 1.0 - n_s_avg / nc
+    return {
+        # psi + Phi y on the S-breve dofs: read Phi rows and psi, write q
+        "recon": s * N * frac_breve * (m_eff + 2),
+        # window read, psi read, Phi write, next psi write
+        "formphi": s * N * (w + 1 + m_eff + 1),
+        # one new snapshot against w+1 ring slots (the new one stays in L2)
+        "gram": s * N * (w + 1),
+        # error indicator: read g, psi, Phi; write eps; keys and radix passes
+        "select": s * N * (m_eff + 2) + s * nc + 8 * nc * 9,
+    }
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_2301_01718_gb300 import build, hyrom
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    q0, cfg = workload(a)
+    stream = torch.cuda.Stream()
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q0d, stream=stream.cuda_stream)
+    del q0d
+    try:
+        # the method's own warm-up: w full steps and the first rebuild
+        while True:
+            info = hyrom.hyrom_step(ctx)
+            if not info["was_full"]:
+                break
+        for _ in range(a.warmup):
+            hyrom.hyrom_step(ctx)
+        hyrom.hyrom_profile(ctx, True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = hyrom.hyrom_kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns_sum, infos = 0, []
+        for _ in range(a.steps):
+            info = hyrom.hyrom_step(ctx)
+            ns_sum += info["n_s"]
+            infos.append(info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = hyrom.hyrom_kernel_launches() - l0
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        stages = hyrom.hyrom_stage_times(ctx)
+        hyrom.hyrom_profile(ctx, False)
+        t = torch.tensor([ms], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.barrier()
+        ms_max = float(t.item())
+        value = world * a.steps / (ms_max / 1e3)
+
+        # end to end through host buffers (pinned): upload gamma_k, step,
+        # download gamma_k+1, every step
+        e2e = None
+        if not a.no_e2e:
+            hbuf = torch.empty(cfg.ndof, dtype=torch.float32, pin_memory=True)
+            hyrom.hyrom_get_state(ctx, hbuf.data_ptr(), on_host=True)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            ke = max(2, a.steps // 2)
+            for _ in range(ke):
+                hyrom.hyrom_set_state(ctx, hbuf.data_ptr(), on_host=True)
+                hyrom.hyrom_step(ctx)
+                hyrom.hyrom_get_state(ctx, hbuf.data_ptr(), on_host=True)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            te = torch.tensor([el], device="cuda")
+            if world > 1:
+                dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e = {"value": world * ke / float(te.item()), "unit": UNIT,
+                   "h2d_bytes_per_step": 4 * cfg.ndof, "d2h_bytes_per_step": 4 * cfg.ndof,
+                   "path": "hyrom_set_state(host) + hyrom_step + hyrom_get_state(host)"}
+        m_eff = infos[-1]["m_eff"]
+    finally:
+        hyrom.hyrom_destroy(ctx)
+
+    n_s_avg = ns_sum / a.steps
+    per = {}
+    byts = stage_bytes(cfg, m_eff, n_s_avg)
+    peaks = _peaks()
+    for name, (tot, cnt) in stages.items():
+        if cnt == 0:
+            continue
+        d = {"ms_per_step": tot / a.steps, "launches": cnt, "ms_per_launch": tot / cnt}
+        if name in byts:
+            d["gbs"] = byts[name] / (tot / cnt * 1e-3) / 1e9
+        per[name] = d
+    # roofline of the dominant kernel with an algorithmic byte count
+    cand = [(per[n]["ms_per_step"], n) for n in byts if n in per]
+    roof = None
+    if cand:
+        _, dom = max(cand)
+        ach = per[dom]["gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
+                "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": None,
+                "bytes_per_launch": byts[dom], "peak_source": peaks["src"]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config_dict(a, cfg),
+           "sampled_cell_updates_per_s": world * ns_sum / (ms_max / 1e3),
+           "n_s_avg": n_s_avg, "m_eff": m_eff, "stages": per,
+           "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e}
+    if rank == 0 and not a.no_err:
+        out["err_vs_fp64"] = err_vs_fp64(a)
+    if rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(a)
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm": float(d["hbm_gbs"]), "src": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm": 6800.0, "src": "fallback 6.8 TB/s"}
+
+
+def err_vs_fp64(a, n=256, steps=12):
+    """FP32 GPU run against the FP64 GPU run (itself checked against the
+    oracle by the parity tests) of the same workload on an n^2 grid: relative
+    L1 and max errors of the state after `steps` hybrid steps."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    outs = {}
+    for prec in (W.PREC_F32, W.PREC_F64):
+        q0, cfg = workload(a, n=n, prec=prec)
+        if prec == W.PREC_F64:
+            cfg = cfg.with_(pod_tol=1e-10, pod_abs=1e-13)
+        q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+        ctx = hyrom.hyrom_init(cfg, q0d)
+        try:
+            hyb = 0
+            while hyb < steps:
+                info = hyrom.hyrom_step(ctx)
+                hyb += 0 if info["was_full"] else 1
+            q = torch.zeros(cfg.ndof, dtype=torch.float32 if prec == W.PREC_F32 else torch.float64,
+                            device="cuda")
+            hyrom.hyrom_get_state(ctx, q)
+            outs[prec] = q.double().cpu().numpy()
+        finally:
+            hyrom.hyrom_destroy(ctx)
+    d = outs[W.PREC_F32] - outs[W.PREC_F64]
+    return {"grid": f"{n}x{n}", "hybrid_steps": steps,
+            "rel_l1": float(np.abs(d).sum() / np.abs(outs[W.PREC_F64]).sum()),
+            "rel_max": float(np.abs(d).max() / np.abs(outs[W.PREC_F64]).max())}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    _, cfg = workload(a)
+    steps = max(1, min(a.steps, 2))
+    cb = cpu_oracle_rate(a, steps=steps)
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": 0, "steps": steps, "warmup": a.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(a, cfg),
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+                             "value": cb["value"], "unit": UNIT},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    out = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * hyrom.h - C ABI of the GB300 (sm_103a) hybrid-snapshot adaptive ROM.
+ *
+ * The method is Algorithm 1 of Zucatti & Zahr, "An adaptive, training-free
+ * reduced-order model for convection-dominated problems based on hybrid
+ * snapshots": at each time step the high-dimensional model (HDM) is solved
+ * only on a sampled set of cells (Sec. 2.3, Eq. partial_hdm2), the rest of
+ * the state is rebuilt from an on-the-fly POD basis by gappy least squares
+ * at ODEIM points (Sec. 2.3.1, Eqs. red_coord, pod, odeim, mean), the mixed
+ * state is passed through residual-gated Shapiro filters (Sec. 2.3.4), and
+ * the next sampled set is chosen from the pointwise reconstruction error
+ * (Sec. 2.3.3, Eq. rre).
+ *
+ * Conventions (all entry points):
+ *   - A state is an array of nvar*Nc values in structure-of-arrays layout,
+ *     q[v*Nc + cell], cell = j*nx + i (x fastest).  Nc = nx*ny; nvar = 1
+ *     (Burgers) or 4 (Euler: rho, rho u, rho v, rho E).
+ *   - "dev" pointers are CUDA device pointers on the device current when the
+ *     context was created; "host" pointers are ordinary host memory (pinned
+ *     memory gives the fastest copies).  Arrays of the state type ("real")
+ *     hold double when the context precision is HYROM_PREC_F64 and float
+ *     when it is HYROM_PREC_F32.
+ *   - The caller keeps ownership of every pointer it passes; the library
+ *     never retains one past the call (q0 is copied).  The context owns all
+ *     of its device workspaces (allocated by hyrom_init, freed by
+ *     hyrom_destroy).
+ *   - Work is enqueued on the stream given to hyrom_init (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).  Calls return
+ *     after their work is enqueued unless they return host-side counts, in
+ *     which case they synchronise that stream.
+ *   - No entry point aborts or throws.  Each returns a hyrom_status; the
+ *     message of the last failure is available from hyrom_last_error().  A
+ *     CUDA error makes the context unusable (HYROM_ECUDA is sticky).
+ *   - One context must not be used by two host threads at once.
+ */
+#ifndef HYROM_H
+#define HYROM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYROM_OK = 0,
+  HYROM_EINVAL = 1,    /* bad argument or configuration                     */
+  HYROM_ENOMEM = 2,    /* device allocation failed                          */
+  HYROM_ECUDA = 3,     /* a CUDA call failed; the context is unusable      */
+  HYROM_ENOTCONV = 4,  /* a Newton solve hit newton_max (result still set)  */
+  HYROM_ESTATE = 5,    /* call out of order (e.g. no basis yet)             */
+  HYROM_ECAP = 6,      /* output buffer too small                           */
+  HYROM_ETIMEOUT = 7   /* an iterative device solver hit its sweep limit    */
+} hyrom_status;
+
+enum { HYROM_PDE_BURGERS = 0, HYROM_PDE_EULER = 1 };
+enum { HYROM_SCHEME_BE = 0, HYROM_SCHEME_RK2 = 1 };
+enum { HYROM_BC_PERIODIC = 0, HYROM_BC_OUTFLOW = 1, HYROM_BC_SHOCK = 2 };
+enum { HYROM_SEL_RRE = 0, HYROM_SEL_TOPFRAC = 1 };
+enum { HYROM_PREC_F64 = 0, HYROM_PREC_F32 = 1 };
+
+/* Run parameters.  HDM: Sec. 2.2 (Eqs. semi_disc, bdf, hdm) with
+ * first-order FV fluxes (Burgers: Godunov; Euler, Sec. 3.1: Rusanov) and
+ * BDF1 (backward Euler, Newton) or SSP-RK2 time stepping.  Boundary sides
+ * are ordered left, right, bottom, top; HYROM_BC_SHOCK imposes the exact
+ * planar shock: the state is shock_post where n.x < shock_d0 +
+ * shock_speed*t, else shock_pre (conserved variables).
+ * Algorithm 1: w snapshots, m POD modes, full HDM every z steps (z <= 0:
+ * never after the warm-up), n_p ODEIM points; selection by the RRE
+ * threshold delta (Eq. rre) or the top fraction top_frac of cells, then
+ * dilation by `halo` cells; subiterations stop at ||dy||_2 < eps_y or jmax
+ * (Sec. 2.3.2); filter passes stop at a relative decrease below eps_f or
+ * jmax_f passes (Sec. 2.3.4) for each Shapiro order filt_orders[0..n_filt)
+ * (n = 1, 2, 3 for orders 2, 4, 6).  POD keeps mode j when
+ * sigma_j > pod_tol*sigma_1 and sigma_j > pod_abs*||X_raw||_F.  Arg-max ties
+ * within relative tie_tol go to the lowest index. */
+typedef struct {
+  int32_t pde, scheme, precision, nx, ny;
+  int32_t bc[4];
+  double dx, dy, dt, gamma;
+  double shock_n[2], shock_d0, shock_speed, shock_pre[4], shock_post[4];
+  int32_t w, m, z, n_p, sel_mode, halo, jmax, jmax_f, newton_max, n_filt;
+  int32_t filt_orders[3], regress_rows;
+  double delta, top_frac, eps_y, eps_f, pod_tol, pod_abs, tie_tol, newton_tol;
+  uint64_t seed;
+} hyrom_config;
+
+/* What one call of hyrom_step / hyrom_advance / hyrom_update_basis did. */
+typedef struct {
+  int64_t k;            /* step index of the snapshot now held (gamma_k)   */
+  int32_t was_full;     /* 1: full HDM solve (Algorithm 1 line 4)           */
+  int32_t rebuilt;      /* 1: basis, points and sets rebuilt (lines 18-30)  */
+  int32_t J;            /* subiterations of the partial HDM (Sec. 2.3.2)   */
+  int32_t n_s;          /* cells of S-hat used by this step                 */
+  int32_t n_g;          /* cells picked by the error indicator (next step)  */
+  int32_t n_p;          /* ODEIM points in effect                           */
+  int32_t m_eff;        /* POD modes in effect                              */
+  int32_t filt_passes;  /* filter passes run                                */
+  int32_t newton_fail;  /* Newton solves that hit newton_max                */
+  int32_t pad;
+  double dy_last;       /* ||y^(J) - y^(J-1)||_2 of the last subiteration   */
+} hyrom_step_info;
+
+typedef struct hyrom_ctx hyrom_ctx;
+
+/* ---- context lifetime ----------------------------------------------------
+ * hyrom_init: validate cfg, allocate the context's device workspaces (the
+ * w+1 snapshot ring, basis, points, masks, filter and reduction buffers)
+ * and copy q0 (nvar*Nc doubles, host or device per q0_on_host) into
+ * gamma_0 (Algorithm 1 line 1), converting to the context precision.
+ * Errors: HYROM_EINVAL (bad config; *out untouched), HYROM_ENOMEM,
+ * HYROM_ECUDA.  On error no context is returned. */
+hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_host,
+                        void* stream, hyrom_ctx** out);
+void hyrom_destroy(hyrom_ctx* ctx);
+const char* hyrom_last_error(const hyrom_ctx* ctx);
+/* Bytes of device memory the context holds. */
+size_t hyrom_device_bytes(const hyrom_ctx* ctx);
+/* Kernels this library has launched since it was loaded (all contexts of
+ * the process; counted on the host at each launch). */
+uint64_t hyrom_kernel_launches(void);
+
+/* Per-stage timing.  hyrom_profile(ctx, 1) creates CUDA events and from
+ * then on records one pair on the context stream around each stage of
+ * Algorithm 1 (ids below); the elapsed times are summed at the
+ * synchronisation points of hyrom_advance / hyrom_update_basis.
+ * hyrom_profile(ctx, 0) stops recording; both reset the totals.
+ * hyrom_stage_times copies the totals (ms[HYROM_NSTAGE], and the number of
+ * intervals into count[HYROM_NSTAGE] when count is not NULL). */
+enum {
+  HYROM_T_FULL = 0,     /* full HDM step (line 4)                          */
+  HYROM_T_PARTIAL = 1,  /* partial HDM on S-hat (line 8)                   */
+  HYROM_T_GAPPY = 2,    /* gappy coordinates (line 9)                      */
+  HYROM_T_RECON = 3,    /* reconstruction on S-breve (line 12)             */
+  HYROM_T_FILTER = 4,   /* SpatialFilter (line 13)                         */
+  HYROM_T_SELECT = 5,   /* error indicator and G_{k+1} (line 20)           */
+  HYROM_T_GRAM = 6,     /* ring Gram row of a new snapshot (FP32 POD)      */
+  HYROM_T_EIG = 7,      /* window Gram centring + eigensolve (line 24)     */
+  HYROM_T_FORMPHI = 8,  /* basis formation and next psi (lines 24, 29)     */
+  HYROM_T_ODEIM = 9,    /* ODEIM points and the sampled pseudo-inverse     */
+  HYROM_T_MASKS = 10,   /* union / dilation / Neighbors (lines 26-28)      */
+  HYROM_NSTAGE = 11
+};
+hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
+hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count);
+
+/* ---- Algorithm 1 --------------------------------------------------------
+ * hyrom_advance: lines 3-14 for k+1: a full HDM step (line 4) or a hybrid
+ * step (lines 6-13: partial HDM with subiterations, gappy coordinates,
+ * reconstruction on S-breve, SpatialFilter).  Errors: HYROM_ESTATE when a
+ * hybrid step is due but no basis exists, HYROM_ENOTCONV (state still
+ * advanced), HYROM_ECUDA.
+ * hyrom_update_basis: lines 15-30 for the current k: psi initialisation,
+ * G_{k+1} by the error indicator, POD_m, ODEIM_{n_p}, union / setdiff /
+ * Neighbors, psi_{k+1}; does nothing when line 18's condition is false.
+ * hyrom_step = hyrom_advance then hyrom_update_basis (one loop iteration).
+ * info may be NULL.  These calls synchronise the stream once per call (they
+ * return counts in info). */
+hyrom_status hyrom_advance(hyrom_ctx* ctx, hyrom_step_info* info);
+hyrom_status hyrom_update_basis(hyrom_ctx* ctx, hyrom_step_info* info);
+hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info);
+
+/* hyrom_sample: the sampled set S-hat in effect for the next step, as
+ * ascending cell ids in idx_dev (capacity cap; HYROM_ECAP if larger; the
+ * count is always written to *n_out) and, when bitmap_dev is not NULL, as a
+ * bitmap of ceil(Nc/32) words (bit c%32 of word c/32).  Algorithm 1 line 26.
+ * HYROM_ESTATE before the first rebuild. */
+hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t* n_out,
+                          uint32_t* bitmap_dev);
+
+/* State access: gamma_k as nvar*Nc reals of the context precision. */
+hyrom_status hyrom_get_state(hyrom_ctx* ctx, void* q, int q_on_host);
+/* Overwrite gamma_k (and its snapshot-Gram entries).  Same layout. */
+hyrom_status hyrom_set_state(hyrom_ctx* ctx, const void* q, int q_on_host);
+/* Basis in effect: Phi (ndof x m_eff reals, column-major, device) and
+ * *m_eff; psi (ndof reals, device); points (n_p int32 dof rows in the order
+ * chosen, device) and *n_p.  Any output pointer may be NULL.
+ * HYROM_ESTATE before the first rebuild. */
+hyrom_status hyrom_get_basis(hyrom_ctx* ctx, void* phi_dev, int32_t* m_eff, void* psi_dev,
+                             int32_t* points_dev, int32_t* n_p);
+
+/* ---- stage entry points --------------------------------------------------
+ * Each runs one step of the method on caller arrays (device pointers) with
+ * the context's configuration, precision, stream and workspaces, leaving
+ * the context's own state untouched.  They exist so that every stage can be
+ * checked against an independent implementation on identical inputs.
+ * `real` arrays follow the context precision. */
+
+/* Full HDM step gamma_k = F_k(gamma_k) from q_prev (Algorithm 1 line 4):
+ * SSP-RK2 from t_{k-1} to t_k, or BDF1 solved by Newton (Eq. hdm). */
+hyrom_status hyrom_stage_full_step(hyrom_ctx* ctx, const void* q_prev, void* q_out, int64_t k);
+
+/* Partial HDM on S-hat (Eq. partial_hdm2; Algorithm 1 line 8): q_io holds
+ * the frozen values on the other cells and, for BDF1, the Newton start on
+ * S-hat; on return it holds the HDM values on S-hat.  s_hat: bitmap. */
+hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* q_io,
+                                      const uint32_t* s_hat, int64_t k);
+
+/* Gappy reduced coordinates y = (P^T Phi)^+ P^T (v - psi) (Eq. red_coord)
+ * by Householder QR in FP64.  phi: ndof x m (column-major), points: n_p dof
+ * rows, y_out: m doubles (device). */
+hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const int32_t* points,
+                               int32_t n_p, const void* v, const void* psi, double* y_out);
+
+/* Reconstruction on S-breve (Algorithm 1 line 12): q_io = psi + Phi y on
+ * every cell whose bit in s_hat is clear (all cells when s_hat is NULL). */
+hyrom_status hyrom_stage_reconstruct(hyrom_ctx* ctx, const void* phi, int32_t m, const double* y,
+                                     const void* psi, const uint32_t* s_hat, void* q_io);
+
+/* SpatialFilter (Algorithm 1 line 13, Sec. 2.3.4) of q_io in place, with
+ * the BDF1 residual relative to q_prev at t_k.  *passes gets the passes
+ * run (may be NULL). */
+hyrom_status hyrom_stage_filter(hyrom_ctx* ctx, void* q_io, const void* q_prev, int64_t k,
+                                int32_t* passes);
+
+/* Pointwise reconstruction error per cell, eps = sum_v (g - psi - Phi y)^2
+ * (Sec. 2.3.3); eps_out: Nc reals. */
+hyrom_status hyrom_stage_cell_error(hyrom_ctx* ctx, const void* g, const void* psi,
+                                    const void* phi, int32_t m, const double* y, void* eps_out);
+
+/* G: the n_g cells first in (descending eps, ascending id) order, n_g from
+ * the RRE threshold (Eq. rre) or the top fraction, with eps mapped to exact
+ * fixed-point integer keys.  Writes a bitmap (ceil(Nc/32) words) and
+ * returns n_g in *n_g (synchronises). */
+hyrom_status hyrom_stage_select(hyrom_ctx* ctx, const void* eps, uint32_t* g_bitmap, int32_t* n_g);
+
+/* POD_m (Eq. pod) of the window X (ndof x w, column-major, columns in time
+ * order) centred at psi: phi_out gets ndof x m_eff orthonormal columns,
+ * sigma_out (device, w doubles, may be NULL) the singular values in
+ * descending order, *m_eff the kept rank (synchronises). */
+hyrom_status hyrom_stage_pod(hyrom_ctx* ctx, const void* window, int32_t w, const void* psi,
+                             void* phi_out, double* sigma_out, int32_t* m_eff);
+
+/* ODEIM_{n_p} (Eq. odeim) of phi (ndof x m): points_out gets n_p dof rows
+ * in the order chosen (the m DEIM points first). */
+hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32_t n_p,
+                               int32_t* points_out);
+
+/* Sampling sets (Algorithm 1 lines 26-28): S-hat = union(G, cells of the
+ * points) dilated by cfg.halo; S-tilde = Neighbors(S-hat) (cells within the
+ * scheme's stencil reach, 1 for BDF1 and 2 for SSP-RK2, not in S-hat).
+ * Bitmaps of ceil(Nc/32) words; *n_s gets |S-hat| (synchronises). */
+hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
+                               int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYROM_H */

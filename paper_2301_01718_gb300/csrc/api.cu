@@ -1,0 +1,1033 @@
+// C ABI of libhyrom (include/hyrom.h): the context, Algorithm 1 of the paper
+// (hybrid snapshot AROM) driven on one GPU stream, and the stage entry
+// points.  All arithmetic runs in the kernels of hdm.cu, filter.cu, rom.cu,
+// select.cu and odeim.cu; this file allocates, validates, enqueues and
+// reads back the few counts the host needs (basis rank, sample sizes,
+// subiteration convergence).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/hyrom.h"
+#include "common.cuh"
+#include "internal.h"
+
+using hy::DevCfg;
+
+struct hyrom_ctx {
+  hyrom_config cfg;
+  DevCfg dc;
+  cudaStream_t st = nullptr;
+  int f32 = 0;
+  size_t esz = 8;
+  int64_t N = 0, nc = 0, nwords = 0;
+  int w = 0, m = 0, np = 0, nslot = 0, wp = 0;
+  int64_t k = 0;
+  int sticky = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  // snapshots and the basis in effect
+  void* ring = nullptr;
+  void* psi = nullptr;
+  void* psi_next = nullptr;
+  void* phi = nullptr;
+  int m_eff = 0;
+  int np_eff = 0;
+  int has_basis = 0;
+  int psi_set = 0;
+  std::vector<int64_t> psi_steps;  // psi = mean of these snapshots
+  int* pts = nullptr;
+  double* pinv = nullptr;
+  double* y = nullptr;
+  double* y2 = nullptr;
+  double* dy = nullptr;
+  int* status = nullptr;
+  // sampling sets
+  uint32_t *g_bm = nullptr, *base_bm = nullptr, *shat = nullptr, *stilde = nullptr;
+  uint32_t* tmp_bm = nullptr;
+  int* tiles = nullptr;
+  int* ntiles = nullptr;
+  int* seg = nullptr;
+  int* nseg = nullptr;
+  long long* n_s_dev = nullptr;
+  long long* n_g_dev = nullptr;
+  long long* list_cnt = nullptr;
+  int64_t n_s = 0;
+  // filter
+  void *fg = nullptr, *ftmp = nullptr, *rho_old = nullptr, *rho_new = nullptr;
+  double* fpart = nullptr;
+  int* fctl = nullptr;
+  int* forders = nullptr;
+  // selection
+  void* eps = nullptr;
+  unsigned long long* keys = nullptr;
+  void* sel_scratch = nullptr;
+  // POD
+  double* H = nullptr;
+  double* Hpart = nullptr;
+  int gram_chunks = 0;
+  double* hp = nullptr;
+  double* pp = nullptr;
+  double* Gc = nullptr;
+  double* V = nullptr;
+  double* lam = nullptr;
+  double* sig = nullptr;
+  double* xraw2 = nullptr;
+  int* m_eff_dev = nullptr;
+  void* C = nullptr;
+  double* Cd = nullptr;
+  int* win_dev = nullptr;
+  int* ps_dev = nullptr;
+  double* X = nullptr;
+  double* rawpart = nullptr;
+  int* rotated = nullptr;
+  double* ident = nullptr;
+  // ODEIM
+  void* od_ws = nullptr;
+  // Newton
+  double* tol_dev = nullptr;
+  double* newton_ws = nullptr;
+  int* fail_dev = nullptr;
+  // pinned host mirror for read-backs
+  void* host = nullptr;
+  // optional per-stage CUDA-event timers (hyrom_profile)
+  int profile = 0;
+  cudaEvent_t ev_a[HYROM_NSTAGE] = {}, ev_b[HYROM_NSTAGE] = {};
+  int ev_pending[HYROM_NSTAGE] = {};
+  double stage_ms[HYROM_NSTAGE] = {};
+  int64_t stage_n[HYROM_NSTAGE] = {};
+};
+
+namespace hy {
+static unsigned long long g_launches = 0;
+void count_launch() { ++g_launches; }
+unsigned long long launch_count() { return g_launches; }
+}  // namespace hy
+
+static __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+static void convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_f64_to_f32<<<152 * 8, 256, 0, HY_S(s)>>>(a, b, n);
+}
+
+namespace {
+
+hyrom_status fail(hyrom_ctx* c, hyrom_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == HYROM_ECUDA) c->sticky = 1;
+  }
+  return s;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, HYROM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+#define CKL()                                                                           \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, HYROM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+bool dalloc(hyrom_ctx* ctx, void** p, size_t n) {
+  if (n == 0) n = 16;
+  n = (n + 255) & ~(size_t)255;
+  if (cudaMalloc(p, n) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->allocs.push_back(*p);
+  ctx->bytes += n;
+  return true;
+}
+
+template <typename P>
+bool dal(hyrom_ctx* ctx, P** p, size_t n) {
+  return dalloc(ctx, (void**)p, n);
+}
+
+hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
+  auto bad = [&](const char* m) {
+    snprintf(why, nwhy, "%s", m);
+    return HYROM_EINVAL;
+  };
+  if (c->pde != HYROM_PDE_BURGERS && c->pde != HYROM_PDE_EULER) return bad("pde");
+  if (c->scheme != HYROM_SCHEME_BE && c->scheme != HYROM_SCHEME_RK2) return bad("scheme");
+  if (c->precision != HYROM_PREC_F64 && c->precision != HYROM_PREC_F32) return bad("precision");
+  if (c->nx < 4 || c->ny < 1) return bad("grid: nx >= 4, ny >= 1");
+  if ((int64_t)c->nx * c->ny * (c->pde == HYROM_PDE_BURGERS ? 1 : 4) > (int64_t)1 << 30)
+    return bad("grid too large (ndof > 2^30)");
+  if (c->pde == HYROM_PDE_BURGERS && c->ny != 1) return bad("Burgers is 1D (ny = 1)");
+  for (int i = 0; i < 4; ++i)
+    if (c->bc[i] < 0 || c->bc[i] > 2) return bad("bc");
+  if ((c->bc[0] == HYROM_BC_PERIODIC) != (c->bc[1] == HYROM_BC_PERIODIC))
+    return bad("x sides must both be periodic or both not");
+  if ((c->bc[2] == HYROM_BC_PERIODIC) != (c->bc[3] == HYROM_BC_PERIODIC))
+    return bad("y sides must both be periodic or both not");
+  if (c->pde == HYROM_PDE_BURGERS && (c->bc[0] == HYROM_BC_SHOCK))
+    return bad("shock sides need the Euler equations");
+  if (c->scheme == HYROM_SCHEME_BE) {
+    if (c->pde != HYROM_PDE_BURGERS) return bad("BDF1 is implemented for Burgers");
+    if (c->precision != HYROM_PREC_F64) return bad("BDF1 Newton runs in FP64");
+    if (c->bc[0] != HYROM_BC_PERIODIC) return bad("BDF1 Burgers is periodic");
+  }
+  if (!(c->dx > 0 && c->dy > 0 && c->dt > 0)) return bad("dx, dy, dt > 0");
+  if (c->m < 1 || c->m > 64) return bad("1 <= m <= 64");
+  if (c->w < c->m || c->w > 128) return bad("m <= w <= 128");
+  if (c->n_p < c->m || c->n_p > 1024) return bad("m <= n_p <= 1024");
+  if (hy::gappy_pinv_smem(c->m, c->n_p) > 227 * 1024) return bad("n_p * m too large");
+  if (c->sel_mode != HYROM_SEL_RRE && c->sel_mode != HYROM_SEL_TOPFRAC) return bad("sel_mode");
+  if (c->sel_mode == HYROM_SEL_RRE && !(c->delta >= 1.0 / 1024 && c->delta <= 1.0))
+    return bad("delta in [2^-10, 1]");
+  if (c->sel_mode == HYROM_SEL_TOPFRAC && !(c->top_frac >= 0.0 && c->top_frac <= 1.0))
+    return bad("top_frac in [0, 1]");
+  if (c->halo < 0 || c->halo > 8) return bad("0 <= halo <= 8");
+  if (c->jmax < 1 || c->jmax_f < 1 || c->newton_max < 1) return bad("iteration limits >= 1");
+  if (c->n_filt < 0 || c->n_filt > 3) return bad("n_filt");
+  for (int i = 0; i < c->n_filt; ++i)
+    if (c->filt_orders[i] < 1 || c->filt_orders[i] > 3) return bad("filt_orders in {1,2,3}");
+  if (!(c->tie_tol >= 0 && c->tie_tol < 1e-3)) return bad("tie_tol");
+  return HYROM_OK;
+}
+
+// ---- stage timers: events on the context stream around each stage ----------
+void t_begin(hyrom_ctx* c, int id) {
+  if (c->profile) cudaEventRecord(c->ev_a[id], c->st);
+}
+void t_end(hyrom_ctx* c, int id) {
+  if (!c->profile) return;
+  cudaEventRecord(c->ev_b[id], c->st);
+  c->ev_pending[id] = 1;
+}
+// after a stream synchronisation: fold finished intervals into the totals
+void t_collect(hyrom_ctx* c) {
+  if (!c->profile) return;
+  for (int i = 0; i < HYROM_NSTAGE; ++i) {
+    if (!c->ev_pending[i]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_a[i], c->ev_b[i]) == cudaSuccess) {
+      c->stage_ms[i] += ms;
+      c->stage_n[i] += 1;
+    }
+    c->ev_pending[i] = 0;
+  }
+}
+
+// ring slot of snapshot step j
+inline int slot_of(const hyrom_ctx* c, int64_t j) { return (int)(j % c->nslot); }
+
+hyrom_status sync(hyrom_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+  CKL();
+  t_collect(ctx);
+  return HYROM_OK;
+}
+
+template <typename T>
+T* ring_at(hyrom_ctx* c, int64_t step) {
+  return (T*)c->ring + (int64_t)slot_of(c, step) * c->N;
+}
+
+// rows of the raw ring Gram for a freshly written slot (FP32 path)
+template <typename T>
+void gram_update(hyrom_ctx* c, int64_t step) {
+  if (!c->f32) return;
+  t_begin(c, HYROM_T_GRAM);
+  hy::launch_gram_row<T>((const T*)c->ring, c->N, c->nslot, slot_of(c, step), c->Hpart,
+                         c->gram_chunks, c->H, c->st);
+  t_end(c, HYROM_T_GRAM);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1, lines 3-14
+// ---------------------------------------------------------------------------
+
+template <typename T>
+hyrom_status newton_full(hyrom_ctx* ctx, const T* qp, T* q) {
+  hy::launch_newton_tol(ctx->dc, (const double*)qp, ctx->cfg.newton_tol, ctx->tol_dev, ctx->st);
+  hy::launch_burgers_newton_full(ctx->dc, (const double*)qp, (double*)q, ctx->tol_dev,
+                                 ctx->cfg.newton_max, ctx->newton_ws, ctx->fail_dev, ctx->st);
+  CKL();
+  return HYROM_OK;
+}
+
+template <typename T>
+hyrom_status newton_partial(hyrom_ctx* ctx, const T* qp, T* q, const uint32_t* shat,
+                            int64_t n_s) {
+  if (n_s >= ctx->nc) return newton_full<T>(ctx, qp, q);
+  hy::launch_newton_tol(ctx->dc, (const double*)qp, ctx->cfg.newton_tol, ctx->tol_dev, ctx->st);
+  hy::launch_burgers_newton_partial(ctx->dc, (const double*)qp, (double*)q, shat, ctx->seg,
+                                    ctx->nseg, ctx->tol_dev, ctx->cfg.newton_max,
+                                    ctx->newton_ws, ctx->fail_dev, ctx->st);
+  CKL();
+  return HYROM_OK;
+}
+
+template <typename T>
+hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
+  const hyrom_config& cf = ctx->cfg;
+  const int64_t k = ctx->k + 1;
+  const bool full = (k + 1 <= cf.w) || (cf.z > 0 && k % cf.z == 0);
+  const T* qp = ring_at<T>(ctx, k - 1);
+  T* q = ring_at<T>(ctx, k);
+  hyrom_step_info inf;
+  memset(&inf, 0, sizeof inf);
+  inf.k = k;
+  inf.was_full = full;
+  CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
+  if (full) {
+    t_begin(ctx, HYROM_T_FULL);
+    if (cf.scheme == HYROM_SCHEME_RK2) {
+      hy::launch_rk2<T>(ctx->dc, qp, q, k, nullptr, nullptr, nullptr, ctx->st);
+    } else {
+      CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+      hyrom_status s = newton_full<T>(ctx, qp, q);
+      if (s) return s;
+    }
+    t_end(ctx, HYROM_T_FULL);
+    inf.n_s = (int32_t)ctx->nc;
+  } else {
+    if (!ctx->has_basis) return fail(ctx, HYROM_ESTATE, "hybrid step %lld without a basis", (long long)k);
+    inf.n_s = (int32_t)ctx->n_s;
+    const T* psi = (const T*)ctx->psi;
+    const T* phi = (const T*)ctx->phi;
+    if (cf.scheme == HYROM_SCHEME_RK2) {
+      t_begin(ctx, HYROM_T_PARTIAL);
+      hy::launch_rk2<T>(ctx->dc, qp, q, k, ctx->shat, ctx->tiles, ctx->ntiles, ctx->st);
+      t_end(ctx, HYROM_T_PARTIAL);
+      t_begin(ctx, HYROM_T_GAPPY);
+      if (ctx->m_eff > 0)
+        hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, q, psi, ctx->y,
+                                  nullptr, nullptr, ctx->st);
+      t_end(ctx, HYROM_T_GAPPY);
+      inf.J = 1;
+    } else {
+      CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+      double* yv = ctx->y;
+      double* yo = ctx->y2;
+      double* hd = (double*)ctx->host;
+      for (int j = 1; j <= cf.jmax; ++j) {
+        hyrom_status s = newton_partial<T>(ctx, qp, q, ctx->shat, ctx->n_s);
+        if (s) return s;
+        inf.J = j;
+        if (ctx->m_eff == 0) {
+          std::swap(yv, yo);
+          break;
+        }
+        hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, q, psi, yv,
+                                  j > 1 ? yo : nullptr, ctx->dy, ctx->st);
+        CK(cudaMemcpyAsync(hd, ctx->dy, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        if (hyrom_status s2 = sync(ctx)) return s2;
+        inf.dy_last = hd[0];
+        std::swap(yv, yo);  // yo now holds y^(j)
+        if (j > 1 && hd[0] < cf.eps_y) break;
+        hy::launch_reconstruct<T>(phi, ctx->N, ctx->nc, ctx->m_eff, yo, psi, ctx->stilde, 1, q,
+                                  ctx->st);
+      }
+      if (yo != ctx->y)
+        CK(cudaMemcpyAsync(ctx->y, yo, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    }
+    // line 12: reconstruction on S-breve
+    t_begin(ctx, HYROM_T_RECON);
+    hy::launch_reconstruct<T>(phi, ctx->N, ctx->nc, ctx->m_eff, ctx->y, psi, ctx->shat, 0, q,
+                              ctx->st);
+    t_end(ctx, HYROM_T_RECON);
+    // line 13: SpatialFilter
+    t_begin(ctx, HYROM_T_FILTER);
+    if (cf.n_filt > 0)
+      hy::launch_filter<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp, k,
+                           (T*)ctx->fg, (T*)ctx->ftmp, (T*)ctx->rho_old, (T*)ctx->rho_new,
+                           ctx->fpart, ctx->fctl, ctx->st);
+    t_end(ctx, HYROM_T_FILTER);
+  }
+  CKL();
+  ctx->k = k;
+  gram_update<T>(ctx, k);
+  int* hi = (int*)ctx->host;
+  CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (!full && cf.n_filt > 0)
+    CK(cudaMemcpyAsync(hi + 1, ctx->fctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  inf.newton_fail = hi[0];
+  inf.filt_passes = (!full && cf.n_filt > 0) ? hi[1] : 0;
+  inf.n_p = ctx->np_eff;
+  inf.m_eff = ctx->m_eff;
+  if (info) *info = inf;
+  if (inf.newton_fail) return fail(ctx, HYROM_ENOTCONV, "Newton hit newton_max in %d solve(s)", inf.newton_fail);
+  return HYROM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1, lines 15-30
+// ---------------------------------------------------------------------------
+
+template <typename T>
+hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<int>& win,
+                   const T* psi, const std::vector<int>* psi_slots, T* phi_out, T* psi_next,
+                   int* m_eff_host) {
+  const int w = (int)win.size();
+  const int wp = w % 2 ? w + 1 : w;
+  CK(cudaMemcpyAsync(ctx->win_dev, win.data(), w * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  const hyrom_config& cf = ctx->cfg;
+  if (!ctx->f32) {
+    // FP64: one-sided Jacobi SVD of the centred window
+    hy::launch_center_window<T>(ring, ctx->N, ctx->win_dev, w, wp, psi, ctx->X, ctx->rawpart,
+                                ctx->xraw2, ctx->st);
+    hy::launch_identity(ctx->V, wp, ctx->st);
+    int* hi = (int*)ctx->host;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+      CK(cudaMemsetAsync(ctx->rotated, 0, sizeof(int), ctx->st));
+      for (int r = 0; r < wp - 1; ++r)
+        hy::launch_hestenes_round(ctx->X, ctx->N, wp, ctx->V, r, 1e-15, ctx->rotated, ctx->st);
+      CK(cudaMemcpyAsync(hi, ctx->rotated, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      if (hyrom_status s = sync(ctx)) return s;
+      if (!hi[0]) break;
+    }
+    hy::launch_colnorm2(ctx->X, ctx->N, wp, ctx->lam, ctx->st);
+    hy::launch_pod_coeffs<double>(ctx->lam, nullptr, wp, wp, cf.m, cf.pod_tol, cf.pod_abs,
+                                  ctx->xraw2, ctx->sig, ctx->m_eff_dev, ctx->Cd, ctx->st);
+    hy::launch_phi_from_columns<T>(ctx->X, ctx->N, wp, ctx->Cd, ctx->m_eff_dev, cf.m, phi_out,
+                                   ctx->st);
+    if (psi_next) hy::launch_window_mean<T>(ring, ctx->N, ctx->win_dev, w, psi_next, ctx->st);
+  } else {
+    // FP32: raw ring Gram, centred by the identity, FP64 Jacobi
+    t_begin(ctx, HYROM_T_EIG);
+    bool ident_ok = psi_slots != nullptr;
+    if (ident_ok) {
+      CK(cudaMemcpyAsync(ctx->ps_dev, psi_slots->data(), psi_slots->size() * sizeof(int),
+                         cudaMemcpyHostToDevice, ctx->st));
+      hy::launch_gram_center(ctx->H, nslot, ctx->win_dev, w, ctx->ps_dev, (int)psi_slots->size(),
+                             ctx->Gc, wp, ctx->xraw2, ctx->st);
+    } else {
+      hy::launch_dots<T>(psi, ring, ctx->N, nslot, ctx->Hpart, ctx->gram_chunks, ctx->hp, ctx->st);
+      hy::launch_dots<T>(psi, psi, ctx->N, 1, ctx->Hpart, ctx->gram_chunks, ctx->pp, ctx->st);
+      hy::launch_gram_center_explicit(ctx->H, nslot, ctx->win_dev, w, ctx->hp, ctx->pp, ctx->Gc,
+                                      wp, ctx->xraw2, ctx->st);
+    }
+    hy::launch_jacobi_sym(ctx->Gc, wp, ctx->V, ctx->lam, 60, nullptr, 0, ctx->st);
+    hy::launch_pod_coeffs<T>(ctx->lam, ctx->V, wp, w, cf.m, cf.pod_tol, cf.pod_abs, ctx->xraw2,
+                             ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
+    t_end(ctx, HYROM_T_EIG);
+    t_begin(ctx, HYROM_T_FORMPHI);
+    hy::launch_form_phi<T>(ring, ctx->N, ctx->win_dev, w, psi, (const T*)ctx->C, cf.m,
+                           ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg, ctx->st);
+    t_end(ctx, HYROM_T_FORMPHI);
+  }
+  hy::launch_sign_fix<T>(phi_out, ctx->N, cf.m, ctx->m_eff_dev, ctx->st);
+  CKL();
+  int* hi = (int*)ctx->host;
+  CK(cudaMemcpyAsync(hi, ctx->m_eff_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  *m_eff_host = hi[0];
+  return HYROM_OK;
+}
+
+template <typename T>
+hyrom_status masks_and_tiles(hyrom_ctx* ctx, const uint32_t* gbm, const int* pts, int np,
+                             uint32_t* shat, uint32_t* stilde, int64_t* n_s) {
+  const int rs = ctx->cfg.scheme == HYROM_SCHEME_RK2 ? 2 : 1;
+  t_begin(ctx, HYROM_T_MASKS);
+  hy::launch_masks(ctx->dc, gbm, pts, np, ctx->cfg.halo, rs, ctx->base_bm, shat, stilde,
+                   ctx->n_s_dev, ctx->st);
+  t_end(ctx, HYROM_T_MASKS);
+  CKL();
+  long long* hl = (long long*)ctx->host;
+  CK(cudaMemcpyAsync(hl, ctx->n_s_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  *n_s = hl[0];
+  return HYROM_OK;
+}
+
+template <typename T>
+hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
+  const hyrom_config& cf = ctx->cfg;
+  const int64_t k = ctx->k;
+  const int w = cf.w;
+  hyrom_step_info inf;
+  if (info)
+    inf = *info;
+  else
+    memset(&inf, 0, sizeof inf);
+  inf.k = k;
+  if (k == w - 1) {  // lines 15-16: psi_{w-1} = mean(gamma_0..gamma_{w-1})
+    std::vector<int> win(w);
+    ctx->psi_steps.clear();
+    for (int i = 0; i < w; ++i) {
+      win[i] = slot_of(ctx, i);
+      ctx->psi_steps.push_back(i);
+    }
+    CK(cudaMemcpyAsync(ctx->win_dev, win.data(), w * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    hy::launch_window_mean<T>((const T*)ctx->ring, ctx->N, ctx->win_dev, w, (T*)ctx->psi, ctx->st);
+    ctx->psi_set = 1;
+  }
+  const bool due = k >= w - 1 && (cf.z <= 0 || (k + 1) % cf.z != 0);
+  if (!due) {
+    inf.n_p = ctx->np_eff;
+    inf.m_eff = ctx->m_eff;
+    if (info) *info = inf;
+    return sync(ctx);
+  }
+  if (!ctx->psi_set) return fail(ctx, HYROM_ESTATE, "no reference state at step %lld", (long long)k);
+  inf.rebuilt = 1;
+  const T* gk = ring_at<T>(ctx, k);
+  // lines 19-22: G_{k+1} from the reconstruction error of the final gamma_k
+  const uint32_t* gbm = nullptr;
+  int64_t n_g = 0;
+  if (k >= w && ctx->has_basis) {
+    t_begin(ctx, HYROM_T_SELECT);
+    if (ctx->m_eff > 0)
+      hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, gk,
+                                (const T*)ctx->psi, ctx->y2, nullptr, nullptr, ctx->st);
+    hy::launch_cell_error<T>(gk, (const T*)ctx->psi, (const T*)ctx->phi, ctx->nc, ctx->dc.nvar,
+                             ctx->m_eff, ctx->y2, (T*)ctx->eps, ctx->st);
+    hy::launch_select(ctx->eps, ctx->f32, ctx->nc, cf.sel_mode, cf.delta, cf.top_frac, ctx->keys,
+                      ctx->sel_scratch, ctx->g_bm, ctx->n_g_dev, ctx->st);
+    t_end(ctx, HYROM_T_SELECT);
+    CKL();
+    long long* hl = (long long*)ctx->host;
+    CK(cudaMemcpyAsync(hl, ctx->n_g_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+    if (hyrom_status s = sync(ctx)) return s;
+    n_g = hl[0];
+    gbm = ctx->g_bm;
+  }
+  inf.n_g = (int32_t)n_g;
+  // line 24: POD of the window centred at the psi in effect
+  std::vector<int> win(w);
+  for (int i = 0; i < w; ++i) win[i] = slot_of(ctx, k - w + 1 + i);
+  std::vector<int> ps;
+  bool ps_ok = true;
+  for (int64_t j : ctx->psi_steps) {
+    if (j < k - w) ps_ok = false;
+    ps.push_back(slot_of(ctx, j));
+  }
+  int me = 0;
+  hyrom_status s = pod_t<T>(ctx, (const T*)ctx->ring, ctx->nslot, win, (const T*)ctx->psi,
+                            ps_ok ? &ps : nullptr, (T*)ctx->phi, (T*)ctx->psi_next, &me);
+  if (s) return s;
+  ctx->m_eff = me;
+  // line 25: ODEIM points
+  ctx->np_eff = 0;
+  if (me > 0) {
+    int np = cf.n_p;
+    if (np > ctx->N) np = (int)ctx->N;
+    t_begin(ctx, HYROM_T_ODEIM);
+    hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts, ctx->od_ws,
+                        ctx->st);
+    ctx->np_eff = np;
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));
+    hy::launch_gappy_pinv<T>((const T*)ctx->phi, ctx->N, me, ctx->pts, np, ctx->pinv,
+                             ctx->status, ctx->st);
+    t_end(ctx, HYROM_T_ODEIM);
+  }
+  // lines 26-28: sampling sets
+  if ((s = masks_and_tiles<T>(ctx, gbm, ctx->pts, ctx->np_eff, ctx->shat, ctx->stilde, &ctx->n_s)))
+    return s;
+  if (cf.scheme == HYROM_SCHEME_RK2)
+    hy::launch_active_tiles(ctx->dc, ctx->shat, hy::rk2_tile_width(ctx->dc),
+                            hy::rk2_tile_height(ctx->dc), ctx->tiles, ctx->ntiles, ctx->st);
+  // line 29: psi_{k+1} = mean of the window
+  std::swap(ctx->psi, ctx->psi_next);
+  ctx->psi_steps.clear();
+  for (int i = 0; i < w; ++i) ctx->psi_steps.push_back(k - w + 1 + i);
+  ctx->has_basis = 1;
+  CKL();
+  if ((s = sync(ctx))) return s;
+  inf.n_p = ctx->np_eff;
+  inf.m_eff = ctx->m_eff;
+  if (info) *info = inf;
+  return HYROM_OK;
+}
+
+template <typename T>
+hyrom_status init_state(hyrom_ctx* ctx, const double* q0, int on_host) {
+  T* g0 = ring_at<T>(ctx, 0);
+  if (!ctx->f32) {
+    CK(cudaMemcpyAsync(g0, q0, ctx->N * sizeof(double),
+                       on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    // convert through the filter scratch (device) buffer
+    double* tmp = (double*)ctx->X;
+    CK(cudaMemcpyAsync(tmp, q0, ctx->N * sizeof(double),
+                       on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->st));
+    convert_f64_to_f32(tmp, (float*)g0, ctx->N, ctx->st);
+  }
+  gram_update<T>(ctx, 0);
+  CKL();
+  return sync(ctx);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public entry points
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_host, void* stream,
+                        hyrom_ctx** out) {
+  if (!cfg || !q0 || !out) return HYROM_EINVAL;
+  char why[256];
+  if (validate(cfg, why, sizeof why) != HYROM_OK) {
+    fprintf(stderr, "hyrom_init: invalid configuration: %s\n", why);
+    return HYROM_EINVAL;
+  }
+  hyrom_ctx* ctx = new hyrom_ctx();
+  ctx->cfg = *cfg;
+  ctx->dc = hy::make_devcfg(*cfg);
+  ctx->st = (cudaStream_t)stream;
+  ctx->f32 = cfg->precision == HYROM_PREC_F32;
+  ctx->esz = ctx->f32 ? 4 : 8;
+  ctx->N = ctx->dc.ndof;
+  ctx->nc = ctx->dc.nc;
+  ctx->nwords = (ctx->nc + 31) / 32;
+  ctx->w = cfg->w;
+  ctx->m = cfg->m;
+  ctx->np = cfg->n_p;
+  ctx->nslot = cfg->w + 1;
+  ctx->wp = (cfg->w + 1) % 2 ? cfg->w + 2 : cfg->w + 1;  // even, >= w + 1
+  const int64_t N = ctx->N, nc = ctx->nc, nw = ctx->nwords;
+  const size_t es = ctx->esz;
+  const int wp = ctx->wp, m = ctx->m;
+  ctx->gram_chunks = 1024;
+  const int ntiles_max = (int)(((cfg->nx + 31) / 32 + 1) * ((cfg->ny + 7) / 8 + 1) + (cfg->nx + 255) / 256 + 1);
+  bool ok = true;
+  ok &= dalloc(ctx, &ctx->ring, (size_t)ctx->nslot * N * es);
+  ok &= dalloc(ctx, &ctx->psi, N * es);
+  ok &= dalloc(ctx, &ctx->psi_next, N * es);
+  ok &= dalloc(ctx, &ctx->phi, (size_t)N * m * es);
+  ok &= dal(ctx, &ctx->pts, 1024 * sizeof(int));
+  ok &= dal(ctx, &ctx->pinv, (size_t)m * cfg->n_p * sizeof(double));
+  ok &= dal(ctx, &ctx->y, 256 * sizeof(double));
+  ok &= dal(ctx, &ctx->y2, 256 * sizeof(double));
+  ok &= dal(ctx, &ctx->dy, 64);
+  ok &= dal(ctx, &ctx->status, 64);
+  ok &= dal(ctx, &ctx->g_bm, nw * 4);
+  ok &= dal(ctx, &ctx->base_bm, nw * 4);
+  ok &= dal(ctx, &ctx->shat, nw * 4);
+  ok &= dal(ctx, &ctx->stilde, nw * 4);
+  ok &= dal(ctx, &ctx->tmp_bm, nw * 4);
+  ok &= dal(ctx, &ctx->tiles, (size_t)ntiles_max * sizeof(int));
+  ok &= dal(ctx, &ctx->ntiles, 64);
+  ok &= dal(ctx, &ctx->seg, (size_t)cfg->nx * sizeof(int));
+  ok &= dal(ctx, &ctx->nseg, 64);
+  ok &= dal(ctx, &ctx->n_s_dev, 64);
+  ok &= dal(ctx, &ctx->n_g_dev, 64);
+  ok &= dal(ctx, &ctx->list_cnt, 1024 * sizeof(long long));
+  ok &= dalloc(ctx, &ctx->fg, N * es);
+  ok &= dalloc(ctx, &ctx->ftmp, N * es);
+  ok &= dalloc(ctx, &ctx->rho_old, nc * es);
+  ok &= dalloc(ctx, &ctx->rho_new, nc * es);
+  ok &= dal(ctx, &ctx->fpart, 3 * 152 * 4 * sizeof(double));
+  ok &= dal(ctx, &ctx->fctl, 64);
+  ok &= dalloc(ctx, &ctx->eps, nc * es);
+  ok &= dal(ctx, &ctx->keys, nc * sizeof(unsigned long long));
+  ok &= dalloc(ctx, &ctx->sel_scratch, hy::select_scratch_bytes());
+  ok &= dal(ctx, &ctx->H, (size_t)ctx->nslot * ctx->nslot * sizeof(double));
+  ok &= dal(ctx, &ctx->Hpart, (size_t)(ctx->nslot + 1) * ctx->gram_chunks * sizeof(double));
+  ok &= dal(ctx, &ctx->hp, (size_t)(ctx->nslot + 1) * sizeof(double));
+  ok &= dal(ctx, &ctx->pp, 64);
+  ok &= dal(ctx, &ctx->Gc, (size_t)wp * wp * sizeof(double));
+  ok &= dal(ctx, &ctx->V, (size_t)wp * wp * sizeof(double));
+  ok &= dal(ctx, &ctx->lam, (size_t)wp * sizeof(double));
+  ok &= dal(ctx, &ctx->sig, (size_t)wp * sizeof(double));
+  ok &= dal(ctx, &ctx->xraw2, 64);
+  ok &= dal(ctx, &ctx->m_eff_dev, 64);
+  ok &= dalloc(ctx, &ctx->C, (size_t)wp * m * es);
+  ok &= dal(ctx, &ctx->Cd, (size_t)wp * m * sizeof(double));
+  ok &= dal(ctx, &ctx->win_dev, 256 * sizeof(int));
+  ok &= dal(ctx, &ctx->ps_dev, 256 * sizeof(int));
+  // FP64 path: centred window for the one-sided Jacobi; FP32 path: q0 staging
+  ok &= dal(ctx, &ctx->X, ctx->f32 ? (size_t)N * sizeof(double) : (size_t)N * wp * sizeof(double));
+  ok &= dal(ctx, &ctx->rawpart, 152 * 4 * sizeof(double));
+  ok &= dal(ctx, &ctx->rotated, 64);
+  ok &= dal(ctx, &ctx->ident, (size_t)wp * wp * sizeof(double));
+  ok &= dalloc(ctx, &ctx->od_ws, hy::odeim_ws_bytes(N, m));
+  ok &= dal(ctx, &ctx->tol_dev, 64);
+  ok &= dal(ctx, &ctx->newton_ws, (size_t)6 * cfg->nx * sizeof(double));
+  ok &= dal(ctx, &ctx->fail_dev, 64);
+  if (!ok) {
+    hyrom_destroy(ctx);
+    fprintf(stderr, "hyrom_init: device allocation failed\n");
+    return HYROM_ENOMEM;
+  }
+  if (cudaMallocHost(&ctx->host, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    hyrom_destroy(ctx);
+    return HYROM_ENOMEM;
+  }
+  std::vector<double> id((size_t)wp * wp, 0.0);
+  for (int i = 0; i < wp; ++i) id[(size_t)i * wp + i] = 1.0;
+  hyrom_status s = HYROM_OK;
+  if (cudaMemcpy(ctx->ident, id.data(), id.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemset(ctx->H, 0, (size_t)ctx->nslot * ctx->nslot * sizeof(double)) != cudaSuccess) {
+    s = HYROM_ECUDA;
+  }
+  if (s == HYROM_OK) s = ctx->f32 ? init_state<float>(ctx, q0, q0_on_host)
+                                  : init_state<double>(ctx, q0, q0_on_host);
+  if (s != HYROM_OK) {
+    fprintf(stderr, "hyrom_init: %s\n", ctx->err.c_str());
+    hyrom_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return HYROM_OK;
+}
+
+void hyrom_destroy(hyrom_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->host) cudaFreeHost(ctx->host);
+  for (int i = 0; i < HYROM_NSTAGE; ++i) {
+    if (ctx->ev_a[i]) cudaEventDestroy(ctx->ev_a[i]);
+    if (ctx->ev_b[i]) cudaEventDestroy(ctx->ev_b[i]);
+  }
+  delete ctx;
+}
+
+const char* hyrom_last_error(const hyrom_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t hyrom_device_bytes(const hyrom_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+uint64_t hyrom_kernel_launches(void) { return hy::launch_count(); }
+
+hyrom_status hyrom_profile(hyrom_ctx* ctx, int on) {
+  if (!ctx) return HYROM_EINVAL;
+  if (on && !ctx->ev_a[0]) {
+    for (int i = 0; i < HYROM_NSTAGE; ++i) {
+      CK(cudaEventCreate(&ctx->ev_a[i]));
+      CK(cudaEventCreate(&ctx->ev_b[i]));
+    }
+  }
+  ctx->profile = on ? 1 : 0;
+  for (int i = 0; i < HYROM_NSTAGE; ++i) {
+    ctx->stage_ms[i] = 0.0;
+    ctx->stage_n[i] = 0;
+    ctx->ev_pending[i] = 0;
+  }
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count) {
+  if (!ctx || !ms) return HYROM_EINVAL;
+  for (int i = 0; i < HYROM_NSTAGE; ++i) {
+    ms[i] = ctx->stage_ms[i];
+    if (count) count[i] = ctx->stage_n[i];
+  }
+  return HYROM_OK;
+}
+
+#define GUARD()                                                              \
+  do {                                                                       \
+    if (!ctx) return HYROM_EINVAL;                                           \
+    if (ctx->sticky) return HYROM_ECUDA;                                     \
+  } while (0)
+
+hyrom_status hyrom_advance(hyrom_ctx* ctx, hyrom_step_info* info) {
+  GUARD();
+  return ctx->f32 ? advance_t<float>(ctx, info) : advance_t<double>(ctx, info);
+}
+
+hyrom_status hyrom_update_basis(hyrom_ctx* ctx, hyrom_step_info* info) {
+  GUARD();
+  return ctx->f32 ? update_basis_t<float>(ctx, info) : update_basis_t<double>(ctx, info);
+}
+
+hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info) {
+  GUARD();
+  hyrom_step_info inf;
+  memset(&inf, 0, sizeof inf);
+  hyrom_status s = hyrom_advance(ctx, &inf);
+  if (s != HYROM_OK && s != HYROM_ENOTCONV) return s;
+  hyrom_status s2 = hyrom_update_basis(ctx, &inf);
+  if (info) *info = inf;
+  return s2 != HYROM_OK ? s2 : s;
+}
+
+hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t* n_out,
+                          uint32_t* bitmap_dev) {
+  GUARD();
+  if (!ctx->has_basis) return fail(ctx, HYROM_ESTATE, "no sampled set before the first rebuild");
+  if (n_out) *n_out = ctx->n_s;
+  if (bitmap_dev)
+    CK(cudaMemcpyAsync(bitmap_dev, ctx->shat, ctx->nwords * 4, cudaMemcpyDeviceToDevice, ctx->st));
+  if (idx_dev) {
+    if (cap < ctx->n_s) return fail(ctx, HYROM_ECAP, "capacity %lld < %lld", (long long)cap, (long long)ctx->n_s);
+    hy::launch_bits_to_list(ctx->shat, ctx->nc, ctx->list_cnt, idx_dev, cap, ctx->st);
+  }
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_get_state(hyrom_ctx* ctx, void* q, int q_on_host) {
+  GUARD();
+  if (!q) return HYROM_EINVAL;
+  const void* src = (const char*)ctx->ring + (size_t)slot_of(ctx, ctx->k) * ctx->N * ctx->esz;
+  CK(cudaMemcpyAsync(q, src, ctx->N * ctx->esz,
+                     q_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->st));
+  return sync(ctx);
+}
+
+hyrom_status hyrom_set_state(hyrom_ctx* ctx, const void* q, int q_on_host) {
+  GUARD();
+  if (!q) return HYROM_EINVAL;
+  void* dst = (char*)ctx->ring + (size_t)slot_of(ctx, ctx->k) * ctx->N * ctx->esz;
+  CK(cudaMemcpyAsync(dst, q, ctx->N * ctx->esz,
+                     q_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->st));
+  if (ctx->f32)
+    gram_update<float>(ctx, ctx->k);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_get_basis(hyrom_ctx* ctx, void* phi_dev, int32_t* m_eff, void* psi_dev,
+                             int32_t* points_dev, int32_t* n_p) {
+  GUARD();
+  if (!ctx->has_basis) return fail(ctx, HYROM_ESTATE, "no basis before the first rebuild");
+  if (m_eff) *m_eff = ctx->m_eff;
+  if (n_p) *n_p = ctx->np_eff;
+  if (phi_dev && ctx->m_eff)
+    CK(cudaMemcpyAsync(phi_dev, ctx->phi, (size_t)ctx->N * ctx->m_eff * ctx->esz,
+                       cudaMemcpyDeviceToDevice, ctx->st));
+  if (psi_dev)
+    CK(cudaMemcpyAsync(psi_dev, ctx->psi, ctx->N * ctx->esz, cudaMemcpyDeviceToDevice, ctx->st));
+  if (points_dev && ctx->np_eff)
+    CK(cudaMemcpyAsync(points_dev, ctx->pts, ctx->np_eff * sizeof(int), cudaMemcpyDeviceToDevice,
+                       ctx->st));
+  return sync(ctx);
+}
+
+// ---- stage entry points ------------------------------------------------------
+
+hyrom_status hyrom_stage_full_step(hyrom_ctx* ctx, const void* q_prev, void* q_out, int64_t k) {
+  GUARD();
+  if (!q_prev || !q_out || q_prev == q_out) return HYROM_EINVAL;
+  CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
+  if (ctx->cfg.scheme == HYROM_SCHEME_RK2) {
+    if (ctx->f32)
+      hy::launch_rk2<float>(ctx->dc, (const float*)q_prev, (float*)q_out, k, nullptr, nullptr,
+                            nullptr, ctx->st);
+    else
+      hy::launch_rk2<double>(ctx->dc, (const double*)q_prev, (double*)q_out, k, nullptr, nullptr,
+                             nullptr, ctx->st);
+  } else {
+    CK(cudaMemcpyAsync(q_out, q_prev, ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    if (hyrom_status s = newton_full<double>(ctx, (const double*)q_prev, (double*)q_out)) return s;
+  }
+  CKL();
+  int* hi = (int*)ctx->host;
+  CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  return hi[0] ? fail(ctx, HYROM_ENOTCONV, "Newton did not converge") : HYROM_OK;
+}
+
+hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* q_io,
+                                      const uint32_t* s_hat, int64_t k) {
+  GUARD();
+  if (!q_prev || !q_io || !s_hat || q_prev == q_io) return HYROM_EINVAL;
+  CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
+  if (ctx->cfg.scheme == HYROM_SCHEME_RK2) {
+    hy::launch_active_tiles(ctx->dc, s_hat, hy::rk2_tile_width(ctx->dc),
+                            hy::rk2_tile_height(ctx->dc), ctx->tiles, ctx->ntiles, ctx->st);
+    if (ctx->f32)
+      hy::launch_rk2<float>(ctx->dc, (const float*)q_prev, (float*)q_io, k, s_hat, ctx->tiles,
+                            ctx->ntiles, ctx->st);
+    else
+      hy::launch_rk2<double>(ctx->dc, (const double*)q_prev, (double*)q_io, k, s_hat, ctx->tiles,
+                             ctx->ntiles, ctx->st);
+  } else {
+    // count the sampled cells to detect the all-cells (cyclic) case
+    CK(cudaMemsetAsync(ctx->n_s_dev, 0, sizeof(long long), ctx->st));
+    long long* hl = (long long*)ctx->host;
+    hy::launch_masks(ctx->dc, s_hat, nullptr, 0, 0, 1, ctx->base_bm, ctx->tmp_bm,
+                     ctx->g_bm, ctx->n_s_dev, ctx->st);
+    CK(cudaMemcpyAsync(hl, ctx->n_s_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+    if (hyrom_status s = sync(ctx)) return s;
+    if (hyrom_status s = newton_partial<double>(ctx, (const double*)q_prev, (double*)q_io, s_hat, hl[0]))
+      return s;
+  }
+  CKL();
+  int* hi = (int*)ctx->host;
+  CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  return hi[0] ? fail(ctx, HYROM_ENOTCONV, "Newton did not converge") : HYROM_OK;
+}
+
+hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const int32_t* points,
+                               int32_t n_p, const void* v, const void* psi, double* y_out) {
+  GUARD();
+  if (!phi || !points || !v || !psi || !y_out || m < 1 || m > 256 || n_p < m || n_p > 1024)
+    return HYROM_EINVAL;
+  if (hy::gappy_pinv_smem(m, n_p) > 227 * 1024) return HYROM_EINVAL;
+  double* pinv = nullptr;
+  if (cudaMallocAsync((void**)&pinv, (size_t)m * n_p * sizeof(double), ctx->st) != cudaSuccess)
+    return fail(ctx, HYROM_ENOMEM, "pinv allocation");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));
+  if (ctx->f32) {
+    hy::launch_gappy_pinv<float>((const float*)phi, ctx->N, m, points, n_p, pinv, ctx->status, ctx->st);
+    hy::launch_gappy_apply<float>(pinv, m, n_p, points, (const float*)v, (const float*)psi, y_out,
+                                  nullptr, nullptr, ctx->st);
+  } else {
+    hy::launch_gappy_pinv<double>((const double*)phi, ctx->N, m, points, n_p, pinv, ctx->status, ctx->st);
+    hy::launch_gappy_apply<double>(pinv, m, n_p, points, (const double*)v, (const double*)psi,
+                                   y_out, nullptr, nullptr, ctx->st);
+  }
+  CKL();
+  CK(cudaFreeAsync(pinv, ctx->st));
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_reconstruct(hyrom_ctx* ctx, const void* phi, int32_t m, const double* y,
+                                     const void* psi, const uint32_t* s_hat, void* q_io) {
+  GUARD();
+  if (!phi || !y || !psi || !q_io || m < 0 || m > 256) return HYROM_EINVAL;
+  if (ctx->f32)
+    hy::launch_reconstruct<float>((const float*)phi, ctx->N, ctx->nc, m, y, (const float*)psi,
+                                  s_hat, 0, (float*)q_io, ctx->st);
+  else
+    hy::launch_reconstruct<double>((const double*)phi, ctx->N, ctx->nc, m, y, (const double*)psi,
+                                   s_hat, 0, (double*)q_io, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_filter(hyrom_ctx* ctx, void* q_io, const void* q_prev, int64_t k,
+                                int32_t* passes) {
+  GUARD();
+  if (!q_io || !q_prev) return HYROM_EINVAL;
+  const hyrom_config& cf = ctx->cfg;
+  if (cf.n_filt > 0) {
+    if (ctx->f32)
+      hy::launch_filter<float>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
+                               (float*)q_io, (const float*)q_prev, k, (float*)ctx->fg,
+                               (float*)ctx->ftmp, (float*)ctx->rho_old, (float*)ctx->rho_new,
+                               ctx->fpart, ctx->fctl, ctx->st);
+    else
+      hy::launch_filter<double>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
+                                (double*)q_io, (const double*)q_prev, k, (double*)ctx->fg,
+                                (double*)ctx->ftmp, (double*)ctx->rho_old, (double*)ctx->rho_new,
+                                ctx->fpart, ctx->fctl, ctx->st);
+  }
+  CKL();
+  int* hi = (int*)ctx->host;
+  hi[1] = 0;
+  if (cf.n_filt > 0)
+    CK(cudaMemcpyAsync(hi + 1, ctx->fctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  if (passes) *passes = hi[1];
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_stage_cell_error(hyrom_ctx* ctx, const void* g, const void* psi,
+                                    const void* phi, int32_t m, const double* y, void* eps_out) {
+  GUARD();
+  if (!g || !psi || !eps_out || m < 0 || m > 256 || (m > 0 && (!phi || !y))) return HYROM_EINVAL;
+  if (ctx->f32)
+    hy::launch_cell_error<float>((const float*)g, (const float*)psi, (const float*)phi, ctx->nc,
+                                 ctx->dc.nvar, m, y, (float*)eps_out, ctx->st);
+  else
+    hy::launch_cell_error<double>((const double*)g, (const double*)psi, (const double*)phi,
+                                  ctx->nc, ctx->dc.nvar, m, y, (double*)eps_out, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_select(hyrom_ctx* ctx, const void* eps, uint32_t* g_bitmap,
+                                int32_t* n_g) {
+  GUARD();
+  if (!eps || !g_bitmap) return HYROM_EINVAL;
+  const hyrom_config& cf = ctx->cfg;
+  hy::launch_select(eps, ctx->f32, ctx->nc, cf.sel_mode, cf.delta, cf.top_frac, ctx->keys,
+                    ctx->sel_scratch, g_bitmap, ctx->n_g_dev, ctx->st);
+  CKL();
+  long long* hl = (long long*)ctx->host;
+  CK(cudaMemcpyAsync(hl, ctx->n_g_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  if (n_g) *n_g = (int32_t)hl[0];
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_stage_pod(hyrom_ctx* ctx, const void* window, int32_t w, const void* psi,
+                             void* phi_out, double* sigma_out, int32_t* m_eff) {
+  GUARD();
+  if (!window || !psi || !phi_out || w < 1 || w > ctx->cfg.w) return HYROM_EINVAL;
+  std::vector<int> win(w);
+  for (int i = 0; i < w; ++i) win[i] = i;
+  int me = 0;
+  hyrom_status s;
+  if (ctx->f32) {
+    // raw Gram of the caller's window (all pairs), psi given explicitly
+    for (int i = 0; i < w; ++i)
+      hy::launch_gram_row<float>((const float*)window, ctx->N, w, i, ctx->Hpart, ctx->gram_chunks,
+                                 ctx->H, ctx->st);
+    s = pod_t<float>(ctx, (const float*)window, w, win, (const float*)psi, nullptr,
+                     (float*)phi_out, (float*)ctx->ftmp, &me);
+  } else {
+    s = pod_t<double>(ctx, (const double*)window, w, win, (const double*)psi, nullptr,
+                      (double*)phi_out, nullptr, &me);
+  }
+  if (s) return s;
+  if (sigma_out)
+    CK(cudaMemcpyAsync(sigma_out, ctx->sig, w * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  if (m_eff) *m_eff = me;
+  if (ctx->f32 && ctx->k >= 0) {
+    // the ring Gram rows were overwritten: rebuild them for the live ring
+    CK(cudaMemsetAsync(ctx->H, 0, (size_t)ctx->nslot * ctx->nslot * sizeof(double), ctx->st));
+    const int64_t lo = ctx->k - ctx->w > 0 ? ctx->k - ctx->w : 0;
+    for (int64_t j = lo; j <= ctx->k; ++j) gram_update<float>(ctx, j);
+  }
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32_t n_p,
+                               int32_t* points_out) {
+  GUARD();
+  if (!phi || !points_out || m < 1 || m > ctx->cfg.m || n_p < m || n_p > 1024) return HYROM_EINVAL;
+  if (ctx->f32)
+    hy::launch_odeim<float>((const float*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
+                            ctx->od_ws, ctx->st);
+  else
+    hy::launch_odeim<double>((const double*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
+                             ctx->od_ws, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
+                               int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s) {
+  GUARD();
+  if (!s_hat || !s_tilde || n_p < 0 || (n_p > 0 && !points)) return HYROM_EINVAL;
+  int64_t ns = 0;
+  hyrom_status s = ctx->f32 ? masks_and_tiles<float>(ctx, g_bitmap, points, n_p, s_hat, s_tilde, &ns)
+                            : masks_and_tiles<double>(ctx, g_bitmap, points, n_p, s_hat, s_tilde, &ns);
+  if (s) return s;
+  if (n_s) *n_s = (int32_t)ns;
+  return HYROM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// High-dimensional model on the GPU: Sec. 2.1-2.2 of the paper (conservation
+// law, semi-discrete FV operator f*, BDF residual R_k = q - F_k(q)),
+// Sec. 2.3 (the partial residual restricted to the sampled cells, Eq.
+// partial_hdm2) and Sec. 3.1 (Euler equations, ideal gas).
+//
+// Fluxes: Burgers f(u) = u^2/2 with the Godunov flux; Euler with the
+// Rusanov flux.  Time stepping: SSP-RK2 (explicit; the partial step on
+// S-hat needs gamma_{k-1} two cells away) and BDF1 solved by Newton with the
+// exact tridiagonal Jacobian (Burgers; per contiguous segment of S-hat, or
+// one cyclic system for the full periodic step).
+//
+// Memory layout: SoA q[v*Nc + j*nx + i].  The RK2 kernel stages a tile of
+// 32 x 8 cells (256 x 1 in 1D) plus a two-cell halo in shared memory, runs
+// stage 1 on the tile plus a one-cell ring in shared memory and stage 2 on
+// the tile, so each launch reads gamma_{k-1} once and writes gamma_k once.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hy {
+
+// ---------------------------------------------------------------------------
+// boundary values
+// ---------------------------------------------------------------------------
+
+template <typename T>
+HY_DEV void shock_state(const DevCfg& c, int gi, int gj, double t, T* out) {
+  const double x = ((double)gi + 0.5) * c.dx;
+  const double y = ((double)gj + 0.5) * c.dy;
+  const double proj = c.sn0 * x + c.sn1 * y;
+  const double front = c.sd0 + c.sspeed * t;
+  const bool post = proj < front;
+  for (int v = 0; v < 4; ++v) out[v] = (T)(post ? c.post[v] : c.pre[v]);
+}
+
+// State at grid position (gi, gj), which may lie one layer outside the
+// domain: periodic sides wrap, outflow sides repeat the boundary cell, shock
+// sides take the exact planar-shock state at time t.  Positions outside on
+// both axes (corners) are never read by the 5-point stencils; they are
+// clamped.
+template <typename T, int NV>
+HY_DEV void fetch(const DevCfg& c, const T* __restrict__ q, int gi, int gj, double t, T* out) {
+  const bool twoD = c.ny > 1;
+  if (!twoD) gj = 0;
+  bool outx = false, outy = false;
+  int side = -1;
+  if (gi < 0 || gi >= c.nx) {
+    if (c.bc[0] == HYROM_BC_PERIODIC) {
+      gi = imod(gi, c.nx);
+    } else {
+      side = gi < 0 ? 0 : 1;
+      outx = true;
+    }
+  }
+  if (twoD && (gj < 0 || gj >= c.ny)) {
+    if (c.bc[2] == HYROM_BC_PERIODIC) {
+      gj = imod(gj, c.ny);
+    } else {
+      if (!outx) side = gj < 0 ? 2 : 3;
+      outy = true;
+    }
+  }
+  if ((outx || outy) && !(outx && outy) && c.bc[side] == HYROM_BC_SHOCK) {
+    T s[4];
+    shock_state<T>(c, gi, gj, t, s);
+    for (int v = 0; v < NV; ++v) out[v] = s[v];
+    return;
+  }
+  gi = gi < 0 ? 0 : (gi >= c.nx ? c.nx - 1 : gi);
+  gj = gj < 0 ? 0 : (gj >= c.ny ? c.ny - 1 : gj);
+  const int64_t cell = (int64_t)gj * c.nx + gi;
+  for (int v = 0; v < NV; ++v) out[v] = q[v * c.nc + cell];
+}
+
+// ---------------------------------------------------------------------------
+// fluxes (fixed evaluation order; see common.cuh)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+HY_DEV T godunov(T uL, T uR) {
+  const T a = uL > (T)0 ? uL : (T)0;
+  const T b = uR < (T)0 ? uR : (T)0;
+  const T fa = (T)0.5 * a * a;
+  const T fb = (T)0.5 * b * b;
+  return fa > fb ? fa : fb;
+}
+
+template <typename T>
+HY_DEV void prims(const T* q, T g, T& u, T& v, T& p, T& cs) {
+  u = q[1] / q[0];
+  v = q[2] / q[0];
+  p = (g - (T)1) * (q[3] - (T)0.5 * q[0] * (u * u + v * v));
+  const T a2 = g * p / q[0];
+  cs = sqrt(a2 > (T)0 ? a2 : (T)0);
+}
+
+// Rusanov flux across a face normal to x (AX = 0) or y (AX = 1).
+template <typename T, int AX>
+HY_DEV void rusanov(const T* qL, const T* qR, T g, T* F) {
+  T uL, vL, pL, cL, uR, vR, pR, cR;
+  prims(qL, g, uL, vL, pL, cL);
+  prims(qR, g, uR, vR, pR, cR);
+  T fL[4], fR[4], a;
+  if (AX == 0) {
+    fL[0] = qL[1];
+    fL[1] = qL[1] * uL + pL;
+    fL[2] = qL[2] * uL;
+    fL[3] = (qL[3] + pL) * uL;
+    fR[0] = qR[1];
+    fR[1] = qR[1] * uR + pR;
+    fR[2] = qR[2] * uR;
+    fR[3] = (qR[3] + pR) * uR;
+    const T sl = fabs(uL) + cL, sr = fabs(uR) + cR;
+    a = sl > sr ? sl : sr;
+  } else {
+    fL[0] = qL[2];
+    fL[1] = qL[1] * vL;
+    fL[2] = qL[2] * vL + pL;
+    fL[3] = (qL[3] + pL) * vL;
+    fR[0] = qR[2];
+    fR[1] = qR[1] * vR;
+    fR[2] = qR[2] * vR + pR;
+    fR[3] = (qR[3] + pR) * vR;
+    const T sl = fabs(vL) + cL, sr = fabs(vR) + cR;
+    a = sl > sr ? sl : sr;
+  }
+  const T ha = (T)0.5 * a;
+  for (int v = 0; v < 4; ++v) F[v] = (T)0.5 * (fL[v] + fR[v]) - ha * (qR[v] - qL[v]);
+}
+
+// f*(q) at one cell from its 5-point neighbourhood.
+template <typename T, int NV>
+HY_DEV void rhs_cell(const DevCfg& c, const T* qC, const T* qW, const T* qE, const T* qS,
+                     const T* qN, T* out) {
+  const T dx = (T)c.dx, dy = (T)c.dy;
+  if (NV == 1) {
+    const T Fl = godunov<T>(qW[0], qC[0]);
+    const T Fr = godunov<T>(qC[0], qE[0]);
+    out[0] = -(Fr - Fl) / dx;
+  } else {
+    const T g = (T)c.gamma;
+    T Fl[4], Fr[4];
+    rusanov<T, 0>(qW, qC, g, Fl);
+    rusanov<T, 0>(qC, qE, g, Fr);
+    for (int v = 0; v < 4; ++v) out[v] = -(Fr[v] - Fl[v]) / dx;
+    if (c.ny > 1) {
+      T Gb[4], Gt[4];
+      rusanov<T, 1>(qS, qC, g, Gb);
+      rusanov<T, 1>(qC, qN, g, Gt);
+      for (int v = 0; v < 4; ++v) out[v] = out[v] - (Gt[v] - Gb[v]) / dy;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused SSP-RK2 step over tiles (full grid, or the active tiles of S-hat)
+// ---------------------------------------------------------------------------
+
+template <typename T, int NV, int TX, int TY>
+__global__ void __launch_bounds__(256) k_rk2_tile(DevCfg c, const T* __restrict__ q,
+                                                  T* __restrict__ out, int64_t k,
+                                                  const uint32_t* __restrict__ mask,
+                                                  const int* __restrict__ tiles,
+                                                  const int* __restrict__ ntiles_dev, int ntiles_all) {
+  constexpr int HX = TX + 4, HY = TY + 4, H1X = TX + 2, H1Y = TY + 2;
+  __shared__ T qs[NV][HY][HX];
+  __shared__ T q1s[NV][H1Y][H1X];
+  const bool twoD = c.ny > 1;
+  const int tiles_x = (c.nx + TX - 1) / TX;
+  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  const double t0 = (double)(k - 1) * c.dt, t1 = (double)k * c.dt;
+  const T dt = (T)c.dt;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int tile = tiles ? tiles[it] : it;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < HY * HX; idx += blockDim.x) {
+      const int ly = idx / HX, lx = idx % HX;
+      if (!twoD && ly != 2) continue;
+      T v[NV];
+      fetch<T, NV>(c, q, x0 + lx - 2, y0 + ly - 2, t0, v);
+      for (int a = 0; a < NV; ++a) qs[a][ly][lx] = v[a];
+    }
+    __syncthreads();
+    // stage 1 on the tile and its one-cell ring (positions inside the
+    // domain after periodic wrap)
+    for (int idx = threadIdx.x; idx < H1Y * H1X; idx += blockDim.x) {
+      const int ly = idx / H1X, lx = idx % H1X;
+      if (!twoD && ly != 1) continue;
+      const int gi = x0 + lx - 1, gj = twoD ? y0 + ly - 1 : 0;
+      const bool inx = (gi >= 0 && gi < c.nx) || c.bc[0] == HYROM_BC_PERIODIC;
+      const bool iny = !twoD || (gj >= 0 && gj < c.ny) || c.bc[2] == HYROM_BC_PERIODIC;
+      if (!(inx && iny)) continue;
+      T qC[NV], qW[NV], qE[NV], qS[NV], qN[NV], r[NV];
+      const int sy = ly + 1, sx = lx + 1;
+      for (int a = 0; a < NV; ++a) {
+        qC[a] = qs[a][sy][sx];
+        qW[a] = qs[a][sy][sx - 1];
+        qE[a] = qs[a][sy][sx + 1];
+        qS[a] = twoD ? qs[a][sy - 1][sx] : qC[a];
+        qN[a] = twoD ? qs[a][sy + 1][sx] : qC[a];
+      }
+      rhs_cell<T, NV>(c, qC, qW, qE, qS, qN, r);
+      for (int a = 0; a < NV; ++a) q1s[a][ly][lx] = qC[a] + dt * r[a];
+    }
+    __syncthreads();
+    // boundary values of the stage-1 state at t_k on non-periodic sides
+    for (int idx = threadIdx.x; idx < H1Y * H1X; idx += blockDim.x) {
+      const int ly = idx / H1X, lx = idx % H1X;
+      if (!twoD && ly != 1) continue;
+      const int gi = x0 + lx - 1, gj = twoD ? y0 + ly - 1 : 0;
+      const bool outx = !((gi >= 0 && gi < c.nx) || c.bc[0] == HYROM_BC_PERIODIC);
+      const bool outy = twoD && !((gj >= 0 && gj < c.ny) || c.bc[2] == HYROM_BC_PERIODIC);
+      if (outx == outy) continue;  // inside, or an unused corner
+      const int side = outx ? (gi < 0 ? 0 : 1) : (gj < 0 ? 2 : 3);
+      if (c.bc[side] == HYROM_BC_SHOCK) {
+        T s[4];
+        shock_state<T>(c, gi, gj, t1, s);
+        for (int a = 0; a < NV; ++a) q1s[a][ly][lx] = s[a];
+      } else {
+        const int cx = outx ? (gi < 0 ? lx + 1 : lx - 1) : lx;
+        const int cy = outy ? (gj < 0 ? ly + 1 : ly - 1) : ly;
+        for (int a = 0; a < NV; ++a) q1s[a][ly][lx] = q1s[a][cy][cx];
+      }
+    }
+    __syncthreads();
+    // stage 2 on the tile
+    for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+      const int ly = idx / TX, lx = idx % TX;
+      const int gi = x0 + lx, gj = y0 + ly;
+      if (gi >= c.nx || gj >= c.ny) continue;
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      if (mask && !bit_get(mask, cell)) continue;
+      T qC[NV], qW[NV], qE[NV], qS[NV], qN[NV], r[NV];
+      const int sy = ly + 1, sx = lx + 1;
+      for (int a = 0; a < NV; ++a) {
+        qC[a] = q1s[a][sy][sx];
+        qW[a] = q1s[a][sy][sx - 1];
+        qE[a] = q1s[a][sy][sx + 1];
+        qS[a] = twoD ? q1s[a][sy - 1][sx] : qC[a];
+        qN[a] = twoD ? q1s[a][sy + 1][sx] : qC[a];
+      }
+      rhs_cell<T, NV>(c, qC, qW, qE, qS, qN, r);
+      for (int a = 0; a < NV; ++a) {
+        const T q0 = qs[a][ly + 2][lx + 2];
+        out[a * c.nc + cell] = (T)0.5 * q0 + (T)0.5 * (qC[a] + dt * r[a]);
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
+                const int* tiles, const int* ntiles_dev, cudaStream_t s) {
+  const bool twoD = c.ny > 1;
+  const int TX = twoD ? 32 : 256, TY = twoD ? 8 : 1;
+  const int ntx = (c.nx + TX - 1) / TX, nty = (c.ny + TY - 1) / TY;
+  const int nt = ntx * nty;
+  int grid = tiles ? (nt < 152 * 8 ? nt : 152 * 8) : nt;
+  if (grid < 1) grid = 1;
+  if (c.nvar == 4) {
+    if (twoD)
+      k_rk2_tile<T, 4, 32, 8><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+    else
+      k_rk2_tile<T, 4, 256, 1><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+  } else {
+    if (twoD)
+      k_rk2_tile<T, 1, 32, 8><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+    else
+      k_rk2_tile<T, 1, 256, 1><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+  }
+}
+
+int rk2_tile_width(const DevCfg& c) { return c.ny > 1 ? 32 : 256; }
+int rk2_tile_height(const DevCfg& c) { return c.ny > 1 ? 8 : 1; }
+
+// ---------------------------------------------------------------------------
+// per-cell BDF1 residual measure rho_i = sum_v |R_v|,
+// R = (q - q_prev) - dt f*(q, t)   (the filter's error indicator)
+// ---------------------------------------------------------------------------
+
+template <typename T, int NV>
+__global__ void k_cell_residual(DevCfg c, const T* __restrict__ q, const T* __restrict__ qp,
+                                double t, T* __restrict__ rho, const uint32_t* __restrict__ only,
+                                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const bool twoD = c.ny > 1;
+  const T dt = (T)c.dt;
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < c.nc;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    if (only && !bit_get(only, cell)) continue;
+    const int gi = (int)(cell % c.nx), gj = (int)(cell / c.nx);
+    T qC[NV], qW[NV], qE[NV], qS[NV], qN[NV], r[NV];
+    for (int a = 0; a < NV; ++a) qC[a] = q[a * c.nc + cell];
+    fetch<T, NV>(c, q, gi - 1, gj, t, qW);
+    fetch<T, NV>(c, q, gi + 1, gj, t, qE);
+    if (twoD) {
+      fetch<T, NV>(c, q, gi, gj - 1, t, qS);
+      fetch<T, NV>(c, q, gi, gj + 1, t, qN);
+    } else {
+      for (int a = 0; a < NV; ++a) qS[a] = qN[a] = qC[a];
+    }
+    rhs_cell<T, NV>(c, qC, qW, qE, qS, qN, r);
+    T acc = (T)0;
+    for (int a = 0; a < NV; ++a) {
+      const T R = (qC[a] - qp[a * c.nc + cell]) - dt * r[a];
+      acc = a == 0 ? fabs(R) : acc + fabs(R);
+    }
+    rho[cell] = acc;
+  }
+}
+
+template <typename T>
+void launch_cell_residual(const DevCfg& c, const T* q, const T* qp, int64_t k, T* rho,
+                          const uint32_t* only, cudaStream_t s) {
+  const double t = (double)k * c.dt;
+  int64_t blocks = (c.nc + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (c.nvar == 4)
+    k_cell_residual<T, 4><<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, qp, t, rho, only, nullptr);
+  else
+    k_cell_residual<T, 1><<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, qp, t, rho, only, nullptr);
+}
+
+template <typename T>
+void launch_cell_residual_skip(const DevCfg& c, const T* q, const T* qp, int64_t k, T* rho,
+                               const int* skip, cudaStream_t s) {
+  const double t = (double)k * c.dt;
+  int64_t blocks = (c.nc + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (c.nvar == 4)
+    k_cell_residual<T, 4><<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, qp, t, rho, nullptr, skip);
+  else
+    k_cell_residual<T, 1><<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, qp, t, rho, nullptr, skip);
+}
+
+// ---------------------------------------------------------------------------
+// Burgers BDF1 solved by Newton (FP64)
+// ---------------------------------------------------------------------------
+
+HY_DEV void godunov_d(double uL, double uR, double& dL, double& dR) {
+  const double a = uL > 0.0 ? uL : 0.0;
+  const double b = uR < 0.0 ? uR : 0.0;
+  const bool left = 0.5 * a * a >= 0.5 * b * b;
+  dL = left ? a : 0.0;
+  dR = left ? 0.0 : b;
+}
+
+HY_DEV double burgers_R(const DevCfg& c, const double* u, const double* up, int i) {
+  const int n = c.nx;
+  const double uW = u[imod(i - 1, n)], uC = u[i], uE = u[imod(i + 1, n)];
+  const double Fl = godunov<double>(uW, uC), Fr = godunov<double>(uC, uE);
+  const double r = -(Fr - Fl) / c.dx;
+  return (uC - up[i]) - c.dt * r;
+}
+
+HY_DEV void burgers_J(const DevCfg& c, const double* u, int i, double& sub, double& dia,
+                      double& sup) {
+  const int n = c.nx;
+  const double lam = c.dt / c.dx;
+  double dLm, dRm, dLp, dRp;
+  godunov_d(u[imod(i - 1, n)], u[i], dLm, dRm);
+  godunov_d(u[i], u[imod(i + 1, n)], dLp, dRp);
+  sub = -lam * dLm;
+  dia = 1.0 + lam * (dLp - dRm);
+  sup = lam * dRp;
+}
+
+// Newton on all cells of the periodic grid: residual and Jacobian in
+// parallel, the cyclic tridiagonal solve (Sherman-Morrison with two Thomas
+// sweeps) by one thread.  ws: 6*n doubles.
+__global__ void k_burgers_newton_full(DevCfg c, const double* __restrict__ up, double* u,
+                                      const double* __restrict__ tol_dev, int newton_max,
+                                      double* ws, int* fail) {
+  const int n = c.nx;
+  double *A = ws, *B = ws + n, *C = ws + 2 * n, *R = ws + 3 * n, *X = ws + 4 * n, *Z = ws + 5 * n;
+  const double tol = *tol_dev;
+  for (int it = 0;; ++it) {
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double r = burgers_R(c, u, up, i);
+      R[i] = r;
+      mx = fmax(mx, fabs(r));
+      burgers_J(c, u, i, A[i], B[i], C[i]);
+    }
+    mx = block_max(mx);
+    if (mx <= tol) return;
+    if (it >= newton_max) {
+      if (threadIdx.x == 0) atomicAdd(fail, 1);
+      return;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // cyclic system: A[0] multiplies x[n-1], C[n-1] multiplies x[0]
+      const double g = -B[0];
+      const double b0 = B[0] - g, bl = B[n - 1] - A[0] * C[n - 1] / g;
+      // Thomas on the modified tridiagonal for rhs R -> X and rhs u -> Z
+      double cp_prev = 0.0, xp = 0.0, zp = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double bi = i == 0 ? b0 : (i == n - 1 ? bl : B[i]);
+        const double ai = i == 0 ? 0.0 : A[i];
+        const double den = bi - ai * cp_prev;
+        const double ci = i == n - 1 ? 0.0 : C[i];
+        const double ri = R[i];
+        const double ui = i == 0 ? g : (i == n - 1 ? C[n - 1] : 0.0);
+        const double cpi = ci / den;
+        xp = (ri - ai * xp) / den;
+        zp = (ui - ai * zp) / den;
+        X[i] = xp;
+        Z[i] = zp;
+        R[i] = cpi;  // reuse R as c'
+        cp_prev = cpi;
+      }
+      for (int i = n - 2; i >= 0; --i) {
+        X[i] = X[i] - R[i] * X[i + 1];
+        Z[i] = Z[i] - R[i] * Z[i + 1];
+      }
+      const double fact = (X[0] + A[0] * X[n - 1] / g) / (1.0 + Z[0] + A[0] * Z[n - 1] / g);
+      for (int i = 0; i < n; ++i) X[i] = X[i] - fact * Z[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = u[i] - X[i];
+    __syncthreads();
+  }
+}
+
+// Segment starts of S-hat (cells in S-hat whose left neighbour is not).
+__global__ void k_segment_starts(DevCfg c, const uint32_t* __restrict__ s_hat, int* starts,
+                                 int* nstart) {
+  const int n = c.nx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (bit_get(s_hat, i) && !bit_get(s_hat, imod(i - 1, n))) starts[atomicAdd(nstart, 1)] = i;
+  }
+}
+
+// Newton on one contiguous segment of S-hat per thread; the neighbours
+// outside the segment are frozen (S-tilde values of u).  ws: 4*n doubles
+// indexed by cell (segments are disjoint).
+__global__ void k_burgers_newton_seg(DevCfg c, const double* __restrict__ up, double* u,
+                                     const uint32_t* __restrict__ s_hat,
+                                     const int* __restrict__ starts,
+                                     const int* __restrict__ nstart,
+                                     const double* __restrict__ tol_dev, int newton_max,
+                                     double* ws, int* fail) {
+  const int n = c.nx;
+  const int ns = *nstart;
+  const double tol = *tol_dev;
+  double *A = ws, *B = ws + n, *C = ws + 2 * n, *R = ws + 3 * n;
+  for (int sgi = blockIdx.x * blockDim.x + threadIdx.x; sgi < ns; sgi += gridDim.x * blockDim.x) {
+    const int s = starts[sgi];
+    int len = 0;
+    while (len < n && bit_get(s_hat, (s + len) % n)) ++len;
+    for (int it = 0;; ++it) {
+      double mx = 0.0;
+      for (int l = 0; l < len; ++l) {
+        const int i = (s + l) % n;
+        const double r = burgers_R(c, u, up, i);
+        R[i] = r;
+        mx = fmax(mx, fabs(r));
+        burgers_J(c, u, i, A[i], B[i], C[i]);
+      }
+      if (mx <= tol) break;
+      if (it >= newton_max) {
+        atomicAdd(fail, 1);
+        break;
+      }
+      // Thomas (sub-diagonal of the first and super-diagonal of the last
+      // unknown multiply frozen values and drop out)
+      double cp = 0.0, xp = 0.0;
+      for (int l = 0; l < len; ++l) {
+        const int i = (s + l) % n;
+        const double ai = l == 0 ? 0.0 : A[i];
+        const double den = B[i] - ai * cp;
+        const double ci = l == len - 1 ? 0.0 : C[i];
+        cp = ci / den;
+        xp = (R[i] - ai * xp) / den;
+        A[i] = cp;  // store c'
+        R[i] = xp;  // store x'
+      }
+      double xn = 0.0;
+      for (int l = len - 1; l >= 0; --l) {
+        const int i = (s + l) % n;
+        const double x = l == len - 1 ? R[i] : R[i] - A[i] * xn;
+        xn = x;
+        u[i] = u[i] - x;
+      }
+    }
+  }
+}
+
+__global__ void k_absmax(const double* __restrict__ x, int64_t n, double scale, double* out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  m = block_max(m);
+  if (threadIdx.x == 0) *out = scale * fmax(1.0, m);
+}
+
+void launch_newton_tol(const DevCfg& c, const double* qp, double newton_tol, double* tol_dev,
+                       cudaStream_t s) {
+  k_absmax<<<1, 1024, 0, HY_S(s)>>>(qp, c.ndof, newton_tol, tol_dev);
+}
+
+void launch_burgers_newton_full(const DevCfg& c, const double* up, double* u,
+                                const double* tol_dev, int newton_max, double* ws, int* fail,
+                                cudaStream_t s) {
+  k_burgers_newton_full<<<1, 1024, 0, HY_S(s)>>>(c, up, u, tol_dev, newton_max, ws, fail);
+}
+
+void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
+                                   const uint32_t* s_hat, int* starts, int* nstart,
+                                   const double* tol_dev, int newton_max, double* ws, int* fail,
+                                   cudaStream_t s) {
+  cudaMemsetAsync(nstart, 0, sizeof(int), s);
+  k_segment_starts<<<(c.nx + 255) / 256, 256, 0, HY_S(s)>>>(c, s_hat, starts, nstart);
+  k_burgers_newton_seg<<<(c.nx + 127) / 128, 128, 0, HY_S(s)>>>(c, up, u, s_hat, starts, nstart,
+                                                          tol_dev, newton_max, ws, fail);
+}
+
+template void launch_rk2<float>(const DevCfg&, const float*, float*, int64_t, const uint32_t*,
+                                 const int*, const int*, cudaStream_t);
+template void launch_rk2<double>(const DevCfg&, const double*, double*, int64_t, const uint32_t*,
+                                  const int*, const int*, cudaStream_t);
+template void launch_cell_residual<float>(const DevCfg&, const float*, const float*, int64_t,
+                                          float*, const uint32_t*, cudaStream_t);
+template void launch_cell_residual<double>(const DevCfg&, const double*, const double*, int64_t,
+                                           double*, const uint32_t*, cudaStream_t);
+template void launch_cell_residual_skip<float>(const DevCfg&, const float*, const float*,
+                                               int64_t, float*, const int*, cudaStream_t);
+template void launch_cell_residual_skip<double>(const DevCfg&, const double*, const double*,
+                                                int64_t, double*, const int*, cudaStream_t);
+
+}  // namespace hy

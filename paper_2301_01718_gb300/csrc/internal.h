@@ -1,0 +1,113 @@
+// Host-side launchers shared between the translation units of libhyrom.
+// Not part of the public ABI (include/hyrom.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hy {
+
+struct DevCfg;
+
+// hdm.cu
+template <typename T>
+void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
+                const int* tiles, const int* ntiles_dev, cudaStream_t s);
+int rk2_tile_width(const DevCfg& c);
+int rk2_tile_height(const DevCfg& c);
+template <typename T>
+void launch_cell_residual(const DevCfg& c, const T* q, const T* qp, int64_t k, T* rho,
+                          const uint32_t* only, cudaStream_t s);
+template <typename T>
+void launch_cell_residual_skip(const DevCfg& c, const T* q, const T* qp, int64_t k, T* rho,
+                               const int* skip, cudaStream_t s);
+void launch_newton_tol(const DevCfg& c, const double* qp, double newton_tol, double* tol_dev,
+                       cudaStream_t s);
+void launch_burgers_newton_full(const DevCfg& c, const double* up, double* u,
+                                const double* tol_dev, int newton_max, double* ws, int* fail,
+                                cudaStream_t s);
+void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
+                                   const uint32_t* s_hat, int* starts, int* nstart,
+                                   const double* tol_dev, int newton_max, double* ws, int* fail,
+                                   cudaStream_t s);
+
+// filter.cu
+template <typename T>
+void launch_shapiro(const DevCfg& c, int n, const T* in, T* tmp, T* out, const int* done,
+                    cudaStream_t s);
+template <typename T>
+void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, double eps_f,
+                   T* q, const T* qp, int64_t k, T* g, T* tmp, T* rho_old, T* rho_new,
+                   double* part, int* ctl, cudaStream_t s);
+
+// rom.cu
+template <typename T>
+void launch_gappy_pinv(const T* phi, int64_t N, int m, const int* pts, int np, double* pinv,
+                       int* status, cudaStream_t s);
+size_t gappy_pinv_smem(int m, int np);
+template <typename T>
+void launch_gappy_apply(const double* pinv, int m, int np, const int* pts, const T* v,
+                        const T* psi, double* y, const double* y_prev, double* dy,
+                        cudaStream_t s);
+template <typename T>
+void launch_reconstruct(const T* phi, int64_t N, int64_t nc, int m, const double* y,
+                        const T* psi, const uint32_t* s_hat, int only_set, T* q, cudaStream_t s);
+template <typename T>
+void launch_cell_error(const T* g, const T* psi, const T* phi, int64_t nc, int nvar, int m,
+                       const double* y, T* eps, cudaStream_t s);
+template <typename T>
+void launch_gram_row(const T* ring, int64_t N, int nslot, int s, double* part, int max_chunks,
+                     double* H, cudaStream_t st);
+void launch_gram_center(const double* H, int nslot, const int* win, int w, const int* ps,
+                        int npsi, double* G, int ldg, double* xraw2, cudaStream_t s);
+void launch_gram_center_explicit(const double* H, int nslot, const int* win, int w,
+                                 const double* hp, const double* pp, double* G, int ldg,
+                                 double* xraw2, cudaStream_t s);
+template <typename T>
+void launch_dots(const T* a, const T* ring, int64_t N, int nslot, double* part, int max_chunks,
+                 double* out, cudaStream_t st);
+void launch_jacobi_sym(const double* A, int n, double* V, double* lam, int max_sweeps,
+                       int* sweeps_out, int warm, cudaStream_t s);
+template <typename T>
+void launch_pod_coeffs(const double* lam, const double* V, int n, int w, int m, double pod_tol,
+                       double pod_abs, const double* xraw2, double* sig_out, int* m_eff_out,
+                       T* C, cudaStream_t s);
+template <typename T>
+void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* psi, const T* C,
+                     int m, const int* m_eff_dev, T* phi, T* psi_next, cudaStream_t s);
+template <typename T>
+void launch_center_window(const T* ring, int64_t N, const int* win, int w, int wp, const T* psi,
+                          double* X, double* raw_part, double* raw_out, cudaStream_t s);
+void launch_hestenes_round(double* X, int64_t N, int wp, double* V, int r, double tol,
+                           int* rotated, cudaStream_t s);
+void launch_identity(double* V, int n, cudaStream_t s);
+void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
+template <typename T>
+void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,
+                             const int* m_eff, int m, T* phi, cudaStream_t s);
+template <typename T>
+void launch_window_mean(const T* ring, int64_t N, const int* win, int w, T* out, cudaStream_t s);
+template <typename T>
+void launch_sign_fix(T* phi, int64_t N, int m, const int* m_eff, cudaStream_t s);
+
+// select.cu
+void launch_select(const void* eps, int is_f32, int64_t nc, int mode, double delta,
+                   double top_frac, unsigned long long* keys, void* scratch, uint32_t* g_bitmap,
+                   long long* n_g_dev, cudaStream_t s);
+size_t select_scratch_bytes();
+void launch_masks(const DevCfg& c, const uint32_t* g_bitmap, const int* pts, int np, int halo,
+                  int stencil_r, uint32_t* base, uint32_t* s_hat, uint32_t* s_tilde,
+                  long long* n_s_dev, cudaStream_t s);
+void launch_active_tiles(const DevCfg& c, const uint32_t* bm, int TX, int TY, int* tiles,
+                         int* ntiles, cudaStream_t s);
+void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch, int* out,
+                         int64_t cap, cudaStream_t s);
+
+// odeim.cu
+template <typename T>
+void launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
+                  cudaStream_t s);
+size_t odeim_ws_bytes(int64_t N, int m);
+void launch_jacobi_padded(const double* M, int m, int n, double* V, double* lam, double* pad,
+                          cudaStream_t s);
+
+}  // namespace hy

@@ -1,0 +1,839 @@
+// Reduced-basis kernels: Sec. 2.3.1 of the paper.
+//
+//  * gappy coordinates y = (P^T Phi)^+ P^T (v - psi) (Eq. red_coord): the
+//    pseudo-inverse of the n_p x m sampled basis is formed once per basis
+//    (Householder QR in FP64, one CTA) and applied per solve (an m x n_p
+//    FP64 GEMV).
+//  * reconstruction psi + Phi y on S-breve (Algorithm 1 line 12) and the
+//    pointwise reconstruction error per cell (Sec. 2.3.3): HBM-bound GEMVs
+//    over Phi (column-major, so each column read is coalesced).
+//  * POD_m (Eq. pod), two implementations:
+//      FP64 states: one-sided (Hestenes) Jacobi SVD of the centred window,
+//        one CTA per column pair per round; relative accuracy of the small
+//        singular values is that of the data.
+//      FP32 states: the snapshot-ring Gram matrix H_ij = gamma_i . gamma_j is
+//        kept up to date with one new row per snapshot (FP64 accumulation of
+//        FP32 products), centred by the identity
+//        (X - psi 1^T)^T (X - psi 1^T) = H - h 1^T - 1 h^T + (psi.psi) 1 1^T
+//        with psi the mean of ring slots, diagonalised by two-sided Jacobi in
+//        FP64 (one CTA), and Phi = X_c V_m Sigma_m^{-1} is formed in one pass
+//        over the window that also produces the next reference state psi
+//        (Eq. mean).
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hy {
+
+// ---------------------------------------------------------------------------
+// gappy least squares
+// ---------------------------------------------------------------------------
+
+// Pseudo-inverse of A = Phi[points, 0:m] (n_p x m, full column rank) as
+// pinv (m x n_p, row-major) = R^{-1} Q^T from a Householder QR.  Dynamic
+// shared memory: A and Q (n_p*m each) + R (m*m) + beta (m) doubles.
+template <typename T>
+__global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
+                             const int* __restrict__ pts, int np, double* __restrict__ pinv,
+                             int* status) {
+  extern __shared__ double sm[];
+  double* A = sm;                  // column-major n_p x m
+  double* Q = A + (size_t)np * m;  // column-major n_p x m
+  double* R = Q + (size_t)np * m;  // row-major m x m
+  double* beta = R + (size_t)m * m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int idx = tid; idx < np * m; idx += nt) {
+    const int i = idx % np, j = idx / np;
+    A[idx] = (double)phi[(int64_t)j * N + pts[i]];
+  }
+  __syncthreads();
+  // Householder QR: reflector j stored in A[j:, j] with v_j = 1 implied off
+  for (int j = 0; j < m; ++j) {
+    double s = 0.0;
+    for (int i = j + tid; i < np; i += nt) s = fma(A[j * np + i], A[j * np + i], s);
+    s = block_sum(s);
+    const double ajj = A[j * np + j];
+    const double nrm = sqrt(s);
+    const double alpha = ajj >= 0.0 ? -nrm : nrm;  // R_jj
+    const double v0 = ajj - alpha;
+    // v = [1, A[j+1:, j] / v0], beta = -v0 / alpha
+    __syncthreads();
+    if (tid == 0) {
+      beta[j] = (nrm == 0.0) ? 0.0 : -v0 / alpha;
+      A[j * np + j] = alpha;
+    }
+    for (int i = j + 1 + tid; i < np; i += nt) A[j * np + i] = (v0 == 0.0) ? 0.0 : A[j * np + i] / v0;
+    __syncthreads();
+    const double bj = beta[j];
+    // apply (I - beta v v^T) to columns j+1..m-1, one warp per column
+    for (int col = j + 1 + wid; col < m; col += nw) {
+      double d = 0.0;
+      for (int i = j + lane; i < np; i += 32) {
+        const double vi = i == j ? 1.0 : A[j * np + i];
+        d = fma(vi, A[col * np + i], d);
+      }
+      d = warp_sum(d) * bj;
+      for (int i = j + lane; i < np; i += 32) {
+        const double vi = i == j ? 1.0 : A[j * np + i];
+        A[col * np + i] = A[col * np + i] - d * vi;
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < m * m; idx += nt) {
+    const int r = idx / m, cc = idx % m;
+    R[idx] = cc >= r ? A[cc * np + r] : 0.0;
+  }
+  // Q = H_0 ... H_{m-1} [I; 0]
+  for (int idx = tid; idx < np * m; idx += nt) {
+    const int i = idx % np, j = idx / np;
+    Q[idx] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    const double bj = beta[j];
+    for (int col = j + wid; col < m; col += nw) {
+      double d = 0.0;
+      for (int i = j + lane; i < np; i += 32) {
+        const double vi = i == j ? 1.0 : A[j * np + i];
+        d = fma(vi, Q[col * np + i], d);
+      }
+      d = warp_sum(d) * bj;
+      for (int i = j + lane; i < np; i += 32) {
+        const double vi = i == j ? 1.0 : A[j * np + i];
+        Q[col * np + i] = Q[col * np + i] - d * vi;
+      }
+    }
+    __syncthreads();
+  }
+  bool bad = false;
+  for (int j = 0; j < m; ++j) bad |= (R[j * m + j] == 0.0);
+  if (bad && tid == 0) atomicAdd(status, 1);
+  // pinv = R^{-1} Q^T : back substitution, one thread per column i of Q^T
+  for (int i = tid; i < np; i += nt) {
+    for (int r = m - 1; r >= 0; --r) {
+      double acc = Q[r * np + i];
+      for (int cc = r + 1; cc < m; ++cc) acc = fma(-R[r * m + cc], pinv[(int64_t)cc * np + i], acc);
+      pinv[(int64_t)r * np + i] = acc / R[r * m + r];
+    }
+  }
+}
+
+template <typename T>
+void launch_gappy_pinv(const T* phi, int64_t N, int m, const int* pts, int np, double* pinv,
+                       int* status, cudaStream_t s) {
+  if (m <= 0) return;
+  const size_t smem = sizeof(double) * ((size_t)2 * np * m + (size_t)m * m + m);
+  cudaFuncSetAttribute(k_gappy_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gappy_pinv<T><<<1, 256, smem, HY_S(s)>>>(phi, N, m, pts, np, pinv, status);
+}
+
+size_t gappy_pinv_smem(int m, int np) {
+  return sizeof(double) * ((size_t)2 * np * m + (size_t)m * m + m);
+}
+
+// y = pinv (v[P] - psi[P]); also |y - y_prev|_2 into *dy when y_prev given.
+template <typename T>
+__global__ void k_gappy_apply(const double* __restrict__ pinv, int m, int np,
+                              const int* __restrict__ pts, const T* __restrict__ v,
+                              const T* __restrict__ psi, double* __restrict__ y,
+                              const double* __restrict__ y_prev, double* dy) {
+  __shared__ double b[1024];
+  __shared__ double ynew[256];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < np; i += blockDim.x) b[i] = (double)v[pts[i]] - (double)psi[pts[i]];
+  __syncthreads();
+  for (int j = wid; j < m; j += nw) {
+    double acc = 0.0;
+    for (int i = lane; i < np; i += 32) acc = fma(pinv[(int64_t)j * np + i], b[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) ynew[j] = acc;
+  }
+  __syncthreads();
+  double d2 = 0.0;
+  for (int j = tid; j < m; j += blockDim.x) {
+    if (y_prev) {
+      const double d = ynew[j] - y_prev[j];
+      d2 = fma(d, d, d2);
+    }
+  }
+  d2 = block_sum(d2);
+  for (int j = tid; j < m; j += blockDim.x) y[j] = ynew[j];
+  if (dy && tid == 0) *dy = sqrt(d2);
+}
+
+template <typename T>
+void launch_gappy_apply(const double* pinv, int m, int np, const int* pts, const T* v,
+                        const T* psi, double* y, const double* y_prev, double* dy,
+                        cudaStream_t s) {
+  k_gappy_apply<T><<<1, 256, 0, HY_S(s)>>>(pinv, m, np, pts, v, psi, y, y_prev, dy);
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction and pointwise error
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_reconstruct(const T* __restrict__ phi, int64_t N, int64_t nc, int m,
+                              const double* __restrict__ y, const T* __restrict__ psi,
+                              const uint32_t* __restrict__ s_hat, int only_set,
+                              T* __restrict__ q) {
+  __shared__ T ys[256];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) ys[j] = (T)y[j];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (s_hat && bit_get(s_hat, r % nc) != (bool)only_set) continue;
+    T acc = (T)0;
+    for (int j = 0; j < m; ++j) acc = fma(phi[(int64_t)j * N + r], ys[j], acc);
+    q[r] = psi[r] + acc;
+  }
+}
+
+template <typename T>
+void launch_reconstruct(const T* phi, int64_t N, int64_t nc, int m, const double* y,
+                        const T* psi, const uint32_t* s_hat, int only_set, T* q, cudaStream_t s) {
+  int64_t blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_reconstruct<T><<<(int)blocks, 256, 0, HY_S(s)>>>(phi, N, nc, m, y, psi, s_hat, only_set, q);
+}
+
+template <typename T>
+__global__ void k_cell_error(const T* __restrict__ g, const T* __restrict__ psi,
+                             const T* __restrict__ phi, int64_t nc, int nvar, int m,
+                             const double* __restrict__ y, T* __restrict__ eps) {
+  __shared__ T ys[256];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) ys[j] = (T)y[j];
+  __syncthreads();
+  const int64_t N = nc * nvar;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    T e = (T)0;
+    for (int v = 0; v < nvar; ++v) {
+      const int64_t r = v * nc + c;
+      T acc = (T)0;
+      for (int j = 0; j < m; ++j) acc = fma(phi[(int64_t)j * N + r], ys[j], acc);
+      const T d = (g[r] - psi[r]) - acc;
+      e = v == 0 ? d * d : e + d * d;
+    }
+    eps[c] = e;
+  }
+}
+
+template <typename T>
+void launch_cell_error(const T* g, const T* psi, const T* phi, int64_t nc, int nvar, int m,
+                       const double* y, T* eps, cudaStream_t s) {
+  int64_t blocks = (nc + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_cell_error<T><<<(int)blocks, 256, 0, HY_S(s)>>>(g, psi, phi, nc, nvar, m, y, eps);
+}
+
+// ---------------------------------------------------------------------------
+// snapshot-ring Gram matrix (FP32 path)
+// ---------------------------------------------------------------------------
+
+// part[j * nchunk + chunk] = sum over the chunk's rows of ring[s][r]*ring[j][r]
+// Grid: x = ring slot j (fastest, so the CTAs in flight share the chunk of
+// slot s through L2), y = row chunk.
+template <typename T>
+__global__ void k_gram_row(const T* __restrict__ ring, int64_t N, int s, int64_t chunk,
+                           double* __restrict__ part) {
+  const int j = blockIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * chunk;
+  int64_t r1 = r0 + chunk;
+  if (r1 > N) r1 = N;
+  const T* a = ring + (int64_t)s * N;
+  const T* b = ring + (int64_t)j * N;
+  double acc = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+    acc = fma((double)a[r], (double)b[r], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(int64_t)j * gridDim.y + blockIdx.y] = acc;
+}
+
+__global__ void k_gram_finalize(const double* __restrict__ part, int nslot, int nchunk, int s,
+                                double* __restrict__ H) {
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nchunk; i += blockDim.x) acc += part[(int64_t)j * nchunk + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    H[(int64_t)s * nslot + j] = acc;
+    H[(int64_t)j * nslot + s] = acc;
+  }
+}
+
+template <typename T>
+void launch_gram_row(const T* ring, int64_t N, int nslot, int s, double* part, int max_chunks,
+                     double* H, cudaStream_t st) {
+  int64_t chunk = (N + max_chunks - 1) / max_chunks;
+  if (chunk < 1024) chunk = 1024;
+  const int nchunk = (int)((N + chunk - 1) / chunk);
+  dim3 grid(nslot, nchunk);
+  k_gram_row<T><<<grid, 256, 0, HY_S(st)>>>(ring, N, s, chunk, part);
+  k_gram_finalize<<<nslot, 256, 0, HY_S(st)>>>(part, nslot, nchunk, s, H);
+}
+
+// Centred Gram of the window from the ring Gram H (nslot x nslot):
+// G[a][b] = H[wa][wb] - h[a] - h[b] + pp, with h[a] = (sum_{j in ps} H[wa][j])/npsi and
+// pp = (sum_{j,l in ps} H[j][l]) / (npsi*npsi).  Also xraw2 = sum_a H[wa][wa].
+__global__ void k_gram_center(const double* __restrict__ H, int nslot, const int* __restrict__ win,
+                              int w, const int* __restrict__ ps, int npsi, double* __restrict__ G,
+                              int ldg, double* xraw2) {
+  __shared__ double h[256];
+  __shared__ double pp;
+  const int tid = threadIdx.x;
+  for (int a = tid; a < w; a += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < npsi; ++j) acc += H[(int64_t)win[a] * nslot + ps[j]];
+    h[a] = acc / npsi;
+  }
+  double acc = 0.0;
+  for (int idx = tid; idx < npsi * npsi; idx += blockDim.x)
+    acc += H[(int64_t)ps[idx / npsi] * nslot + ps[idx % npsi]];
+  acc = block_sum(acc);
+  double xr = 0.0;
+  for (int a = tid; a < w; a += blockDim.x) xr += H[(int64_t)win[a] * nslot + win[a]];
+  xr = block_sum(xr);
+  if (tid == 0) {
+    pp = acc / ((double)npsi * npsi);
+    *xraw2 = xr;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ldg * ldg; idx += blockDim.x) {
+    const int a = idx / ldg, b = idx % ldg;
+    double v = 0.0;
+    if (a < w && b < w) v = ((H[(int64_t)win[a] * nslot + win[b]] - h[a]) - h[b]) + pp;
+    G[idx] = v;
+  }
+}
+
+void launch_gram_center(const double* H, int nslot, const int* win, int w, const int* ps,
+                        int npsi, double* G, int ldg, double* xraw2, cudaStream_t s) {
+  k_gram_center<<<1, 256, 0, HY_S(s)>>>(H, nslot, win, w, ps, npsi, G, ldg, xraw2);
+}
+
+// Same with psi given by its dots hp[j] = psi . ring[j] (all nslot slots)
+// and pp = psi . psi (for a psi that is not a mean of ring slots).
+__global__ void k_gram_center_explicit(const double* __restrict__ H, int nslot,
+                                       const int* __restrict__ win, int w,
+                                       const double* __restrict__ hp, const double* __restrict__ pp,
+                                       double* __restrict__ G, int ldg, double* xraw2) {
+  const int tid = threadIdx.x;
+  double xr = 0.0;
+  for (int a = tid; a < w; a += blockDim.x) xr += H[(int64_t)win[a] * nslot + win[a]];
+  xr = block_sum(xr);
+  if (tid == 0) *xraw2 = xr;
+  const double p2 = *pp;
+  for (int idx = tid; idx < ldg * ldg; idx += blockDim.x) {
+    const int a = idx / ldg, b = idx % ldg;
+    double v = 0.0;
+    if (a < w && b < w) v = ((H[(int64_t)win[a] * nslot + win[b]] - hp[win[a]]) - hp[win[b]]) + p2;
+    G[idx] = v;
+  }
+}
+
+void launch_gram_center_explicit(const double* H, int nslot, const int* win, int w,
+                                 const double* hp, const double* pp, double* G, int ldg,
+                                 double* xraw2, cudaStream_t s) {
+  k_gram_center_explicit<<<1, 256, 0, HY_S(s)>>>(H, nslot, win, w, hp, pp, G, ldg, xraw2);
+}
+
+// out[j] = a . ring[j] for all nslot slots (same two-level order as the
+// ring Gram rows).
+template <typename T>
+__global__ void k_dots(const T* __restrict__ a, const T* __restrict__ ring, int64_t N,
+                       int64_t chunk, double* __restrict__ part) {
+  const int j = blockIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * chunk;
+  int64_t r1 = r0 + chunk;
+  if (r1 > N) r1 = N;
+  const T* b = ring + (int64_t)j * N;
+  double acc = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+    acc = fma((double)a[r], (double)b[r], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(int64_t)j * gridDim.y + blockIdx.y] = acc;
+}
+
+__global__ void k_dots_finalize(const double* __restrict__ part, int nchunk,
+                                double* __restrict__ out) {
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nchunk; i += blockDim.x) acc += part[(int64_t)j * nchunk + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[j] = acc;
+}
+
+template <typename T>
+void launch_dots(const T* a, const T* ring, int64_t N, int nslot, double* part, int max_chunks,
+                 double* out, cudaStream_t st) {
+  int64_t chunk = (N + max_chunks - 1) / max_chunks;
+  if (chunk < 1024) chunk = 1024;
+  const int nchunk = (int)((N + chunk - 1) / chunk);
+  dim3 grid(nslot, nchunk);
+  k_dots<T><<<grid, 256, 0, HY_S(st)>>>(a, ring, N, chunk, part);
+  k_dots_finalize<<<nslot, 256, 0, HY_S(st)>>>(part, nchunk, out);
+}
+template void launch_dots<float>(const float*, const float*, int64_t, int, double*, int, double*,
+                                 cudaStream_t);
+template void launch_dots<double>(const double*, const double*, int64_t, int, double*, int,
+                                  double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// two-sided cyclic Jacobi (FP64, one CTA): A (n x n, n even) in dynamic
+// shared memory, V (n x n column-major) in global memory.  Round-robin
+// ordering: n/2 disjoint rotations per round.
+// ---------------------------------------------------------------------------
+
+HY_DEV void rr_pair(int n, int r, int b, int& p, int& q) {
+  int a, c;
+  if (b == 0) {
+    a = r;
+    c = n - 1;
+  } else {
+    a = (r + b) % (n - 1);
+    c = (r - b + (n - 1)) % (n - 1);
+  }
+  p = a < c ? a : c;
+  q = a < c ? c : a;
+}
+
+__global__ void k_jacobi_sym(const double* __restrict__ Ain, int n, double* __restrict__ V,
+                             double* __restrict__ lam, int max_sweeps, int* sweeps_out,
+                             int warm) {
+  extern __shared__ double A[];
+  __shared__ double cs[2 * 128];
+  __shared__ int rotated;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int half = n / 2;
+  for (int i = tid; i < n * n; i += nt) A[i] = Ain[i];
+  if (!warm)
+    for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  int sw = 0;
+  for (; sw < max_sweeps; ++sw) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int b = tid; b < half; b += nt) {
+        int p, q;
+        rr_pair(n, r, b, p, q);
+        const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-16 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+          rotated = 1;
+        }
+        cs[2 * b] = c;
+        cs[2 * b + 1] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {  // rows
+        const int b = idx / n, k = idx % n;
+        const double c = cs[2 * b], s = cs[2 * b + 1];
+        if (s == 0.0) continue;
+        int p, q;
+        rr_pair(n, r, b, p, q);
+        const double ap = A[p * n + k], aq = A[q * n + k];
+        A[p * n + k] = c * ap - s * aq;
+        A[q * n + k] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {  // columns of A and V
+        const int b = idx / n, k = idx % n;
+        const double c = cs[2 * b], s = cs[2 * b + 1];
+        if (s == 0.0) continue;
+        int p, q;
+        rr_pair(n, r, b, p, q);
+        const double ap = A[k * n + p], aq = A[k * n + q];
+        A[k * n + p] = c * ap - s * aq;
+        A[k * n + q] = s * ap + c * aq;
+        const double vp = V[(int64_t)p * n + k], vq = V[(int64_t)q * n + k];
+        V[(int64_t)p * n + k] = c * vp - s * vq;
+        V[(int64_t)q * n + k] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+  }
+  for (int i = tid; i < n; i += nt) lam[i] = A[i * n + i];
+  if (tid == 0 && sweeps_out) *sweeps_out = sw;
+}
+
+__global__ void k_pad_sym(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int a = idx / n, b = idx % n;
+    P[idx] = (a < m && b < m) ? M[a * m + b] : 0.0;
+  }
+}
+
+// Eigenpairs of the symmetric m x m matrix M by Jacobi on its zero-padded
+// n x n copy (n even); the padding index stays decoupled.
+void launch_jacobi_padded(const double* M, int m, int n, double* V, double* lam, double* pad,
+                          cudaStream_t s) {
+  k_pad_sym<<<1, 256, 0, HY_S(s)>>>(M, m, n, pad);
+  launch_jacobi_sym(pad, n, V, lam, 60, nullptr, 0, s);
+}
+
+void launch_jacobi_sym(const double* A, int n, double* V, double* lam, int max_sweeps,
+                       int* sweeps_out, int warm, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)n * n;
+  cudaFuncSetAttribute(k_jacobi_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi_sym<<<1, 1024, smem, HY_S(s)>>>(A, n, V, lam, max_sweeps, sweeps_out, warm);
+}
+
+// Order eigenpairs (lam[0..n), columns of V; V = NULL means the identity)
+// by descending eigenvalue into
+// sig (sqrt(max(lam, 0))) and perm; m_eff by the rank rule
+// sigma_j > pod_tol*sigma_1 and sigma_j > pod_abs*sqrt(xraw2); coefficient
+// matrix C (w x m_eff, row-major ldc = m) = V_perm / sigma.
+template <typename T>
+__global__ void k_pod_coeffs(const double* __restrict__ lam, const double* __restrict__ V, int n,
+                             int w, int m, double pod_tol, double pod_abs,
+                             const double* __restrict__ xraw2, double* __restrict__ sig_out,
+                             int* m_eff_out, T* __restrict__ C) {
+  __shared__ int perm[256];
+  __shared__ double sg[256];
+  __shared__ int me;
+  if (threadIdx.x == 0) {
+    // selection sort (n <= 256) over the w real eigenpairs, descending
+    for (int i = 0; i < w; ++i) perm[i] = i;
+    for (int i = 0; i < w; ++i) {
+      int b = i;
+      for (int j = i + 1; j < w; ++j)
+        if (lam[perm[j]] > lam[perm[b]]) b = j;
+      const int t = perm[i];
+      perm[i] = perm[b];
+      perm[b] = t;
+    }
+    for (int i = 0; i < w; ++i) {
+      const double l = lam[perm[i]];
+      sg[i] = sqrt(l > 0.0 ? l : 0.0);
+    }
+    const double floor_abs = pod_abs * sqrt(*xraw2);
+    int k = 0;
+    for (int i = 0; i < m && i < w; ++i)
+      if (sg[i] > pod_tol * sg[0] && sg[i] > floor_abs) ++k;
+    me = k;
+    *m_eff_out = k;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < w; i += blockDim.x)
+    if (sig_out) sig_out[i] = sg[i];
+  for (int idx = threadIdx.x; idx < w * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    const double vij = V ? V[(int64_t)perm[j] * n + i] : (perm[j] == i ? 1.0 : 0.0);
+    C[idx] = j < me ? (T)(vij / sg[j]) : (T)0;
+  }
+}
+
+template <typename T>
+void launch_pod_coeffs(const double* lam, const double* V, int n, int w, int m, double pod_tol,
+                       double pod_abs, const double* xraw2, double* sig_out, int* m_eff_out,
+                       T* C, cudaStream_t s) {
+  k_pod_coeffs<T><<<1, 256, 0, HY_S(s)>>>(lam, V, n, w, m, pod_tol, pod_abs, xraw2, sig_out, m_eff_out,
+                                    C);
+}
+
+// Phi[:, j] = sum_i (ring[win[i]] - psi) C[i][j]  (j < m_eff), and
+// psi_next = mean of the window slots, in one pass over the window.
+template <typename T, int MMAX>
+__global__ void __launch_bounds__(256) k_form_phi(const T* __restrict__ ring, int64_t N,
+                                                  const int* __restrict__ win, int w,
+                                                  const T* __restrict__ psi,
+                                                  const T* __restrict__ C, int m,
+                                                  const int* __restrict__ m_eff_dev,
+                                                  T* __restrict__ phi, T* __restrict__ psi_next) {
+  extern __shared__ unsigned char smraw[];
+  T* Cs = reinterpret_cast<T*>(smraw);
+  __shared__ int ws[256];
+  const int me = *m_eff_dev;
+  for (int i = threadIdx.x; i < w * m; i += blockDim.x) Cs[i] = C[i];
+  for (int i = threadIdx.x; i < w; i += blockDim.x) ws[i] = win[i];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    T acc[MMAX];
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) acc[j] = (T)0;
+    const T pr = psi[r];
+    T sum = (T)0, comp = (T)0;  // Kahan-compensated window sum
+    for (int i = 0; i < w; ++i) {
+      const T g = ring[(int64_t)ws[i] * N + r];
+      const T yk = g - comp;
+      const T tk = sum + yk;
+      comp = (tk - sum) - yk;
+      sum = tk;
+      const T x = g - pr;
+      const T* Ci = Cs + i * m;
+#pragma unroll
+      for (int j = 0; j < MMAX; ++j)
+        if (j < me) acc[j] = fma(x, Ci[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j)
+      if (j < me) phi[(int64_t)j * N + r] = acc[j];
+    psi_next[r] = sum / (T)w;
+  }
+}
+
+template <typename T>
+void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* psi, const T* C,
+                     int m, const int* m_eff_dev, T* phi, T* psi_next, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t)w * m;
+  int64_t blocks = (N + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+#define HY_FORM(MM)                                                                          \
+  do {                                                                                       \
+    cudaFuncSetAttribute(k_form_phi<T, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                         (int)smem);                                                         \
+    k_form_phi<T, MM><<<(int)blocks, 256, smem, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,  \
+                                                     phi, psi_next);                         \
+  } while (0)
+  if (m <= 8)
+    HY_FORM(8);
+  else if (m <= 16)
+    HY_FORM(16);
+  else if (m <= 32)
+    HY_FORM(32);
+  else
+    HY_FORM(64);
+#undef HY_FORM
+}
+
+// ---------------------------------------------------------------------------
+// one-sided (Hestenes) Jacobi SVD of the centred window (FP64 path)
+// ---------------------------------------------------------------------------
+
+// X (N x wp, column-major, FP64) = ring[win[i]] - psi, zero columns beyond w.
+template <typename T>
+__global__ void k_center_window(const T* __restrict__ ring, int64_t N, const int* __restrict__ win,
+                                int w, int wp, const T* __restrict__ psi, double* __restrict__ X,
+                                double* __restrict__ raw_part) {
+  double raw = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * wp;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N);
+    const int64_t r = idx % N;
+    if (i < w) {
+      const double g = (double)ring[(int64_t)win[i] * N + r];
+      raw = fma(g, g, raw);
+      X[idx] = g - (double)psi[r];
+    } else {
+      X[idx] = 0.0;
+    }
+  }
+  raw = block_sum(raw);
+  if (threadIdx.x == 0) raw_part[blockIdx.x] = raw;
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int n, double* out) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  a = block_sum(a);
+  if (threadIdx.x == 0) *out = a;
+}
+
+// One round: CTA b orthogonalises the column pair (p, q) of X and applies
+// the same rotation to V (wp x wp column-major).
+__global__ void k_hestenes_round(double* __restrict__ X, int64_t N, int wp,
+                                 double* __restrict__ V, int r, double tol, int* rotated) {
+  int p, q;
+  rr_pair(wp, r, blockIdx.x, p, q);
+  double* xp = X + (int64_t)p * N;
+  double* xq = X + (int64_t)q * N;
+  double a = 0.0, b = 0.0, g = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const double u = xp[i], v = xq[i];
+    a = fma(u, u, a);
+    b = fma(v, v, b);
+    g = fma(u, v, g);
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  g = block_sum(g);
+  if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) return;
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const double u = xp[i], v = xq[i];
+    xp[i] = c * u - s * v;
+    xq[i] = s * u + c * v;
+  }
+  for (int i = threadIdx.x; i < wp; i += blockDim.x) {
+    const double u = V[(int64_t)p * wp + i], v = V[(int64_t)q * wp + i];
+    V[(int64_t)p * wp + i] = c * u - s * v;
+    V[(int64_t)q * wp + i] = s * u + c * v;
+  }
+  if (threadIdx.x == 0) *rotated = 1;
+}
+
+void launch_hestenes_round(double* X, int64_t N, int wp, double* V, int r, double tol,
+                           int* rotated, cudaStream_t s) {
+  k_hestenes_round<<<wp / 2, 256, 0, HY_S(s)>>>(X, N, wp, V, r, tol, rotated);
+}
+
+__global__ void k_colnorm2(const double* __restrict__ X, int64_t N, double* __restrict__ out) {
+  const double* x = X + (int64_t)blockIdx.x * N;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) a = fma(x[i], x[i], a);
+  a = block_sum(a);
+  if (threadIdx.x == 0) out[blockIdx.x] = a;
+}
+
+__global__ void k_identity(double* V, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x)
+    V[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+void launch_identity(double* V, int n, cudaStream_t s) { k_identity<<<16, 256, 0, HY_S(s)>>>(V, n); }
+
+void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s) {
+  k_colnorm2<<<ncol, 256, 0, HY_S(s)>>>(X, N, out);
+}
+
+// Phi[:, j] = X[:, perm_j] / sigma_j for the kept modes; perm and the rank
+// come from k_pod_coeffs run on the column norms (lam = squared norms, V = I).
+template <typename T>
+__global__ void k_phi_from_columns(const double* __restrict__ X, int64_t N, int wp,
+                                   const double* __restrict__ C, const int* __restrict__ m_eff,
+                                   int m, T* __restrict__ phi) {
+  const int me = *m_eff;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N * me;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / N);
+    const int64_t r = idx % N;
+    // C is the identity-permutation coefficient block: column j has one
+    // non-zero 1/sigma_j in row perm_j
+    double acc = 0.0;
+    for (int i = 0; i < wp; ++i) {
+      const double cij = C[(int64_t)i * m + j];
+      if (cij != 0.0) acc = X[(int64_t)i * N + r] * cij;
+    }
+    phi[idx] = (T)acc;
+  }
+}
+
+template <typename T>
+void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,
+                             const int* m_eff, int m, T* phi, cudaStream_t s) {
+  k_phi_from_columns<T><<<152 * 8, 256, 0, HY_S(s)>>>(X, N, wp, C, m_eff, m, phi);
+}
+
+// psi_next = mean of the window slots (FP64 path)
+template <typename T>
+__global__ void k_window_mean(const T* __restrict__ ring, int64_t N, const int* __restrict__ win,
+                              int w, T* __restrict__ out) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    T acc = (T)0;
+    for (int i = 0; i < w; ++i) acc += ring[(int64_t)win[i] * N + r];
+    out[r] = acc / (T)w;
+  }
+}
+
+template <typename T>
+void launch_window_mean(const T* ring, int64_t N, const int* win, int w, T* out, cudaStream_t s) {
+  int64_t blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_window_mean<T><<<(int)blocks, 256, 0, HY_S(s)>>>(ring, N, win, w, out);
+}
+
+// Sign convention: flip column j when its largest-magnitude entry (lowest
+// row on ties) is negative.  One CTA per column.
+template <typename T>
+__global__ void k_sign_fix(T* __restrict__ phi, int64_t N, const int* __restrict__ m_eff) {
+  const int j = blockIdx.x;
+  if (j >= *m_eff) return;
+  T* col = phi + (int64_t)j * N;
+  __shared__ double bv[32];
+  __shared__ long long bi[32];
+  double best = -1.0;
+  long long arg = -1;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const double a = fabs((double)col[i]);
+    if (a > best) {
+      best = a;
+      arg = i;
+    }
+  }
+  // warp then block arg-max (ties -> lowest row)
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (ob > best || (ob == best && oi >= 0 && (arg < 0 || oi < arg))) {
+      best = ob;
+      arg = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    bv[wid] = best;
+    bi[wid] = arg;
+  }
+  __syncthreads();
+  __shared__ int flip;
+  if (threadIdx.x == 0) {
+    double b = -1.0;
+    long long a = -1;
+    for (int wdx = 0; wdx < (int)(blockDim.x >> 5); ++wdx)
+      if (bv[wdx] > b || (bv[wdx] == b && bi[wdx] >= 0 && (a < 0 || bi[wdx] < a))) {
+        b = bv[wdx];
+        a = bi[wdx];
+      }
+    flip = (a >= 0 && col[a] < (T)0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (flip)
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) col[i] = -col[i];
+}
+
+template <typename T>
+void launch_sign_fix(T* phi, int64_t N, int m, const int* m_eff, cudaStream_t s) {
+  if (m > 0) k_sign_fix<T><<<m, 1024, 0, HY_S(s)>>>(phi, N, m_eff);
+}
+
+#define HY_INST(T)                                                                              \
+  template void launch_gappy_pinv<T>(const T*, int64_t, int, const int*, int, double*, int*,    \
+                                     cudaStream_t);                                             \
+  template void launch_gappy_apply<T>(const double*, int, int, const int*, const T*, const T*,  \
+                                      double*, const double*, double*, cudaStream_t);           \
+  template void launch_reconstruct<T>(const T*, int64_t, int64_t, int, const double*, const T*, \
+                                      const uint32_t*, int, T*, cudaStream_t);                  \
+  template void launch_cell_error<T>(const T*, const T*, const T*, int64_t, int, int,           \
+                                     const double*, T*, cudaStream_t);                          \
+  template void launch_gram_row<T>(const T*, int64_t, int, int, double*, int, double*,          \
+                                   cudaStream_t);                                               \
+  template void launch_pod_coeffs<T>(const double*, const double*, int, int, int, double,       \
+                                     double, const double*, double*, int*, T*, cudaStream_t);   \
+  template void launch_form_phi<T>(const T*, int64_t, const int*, int, const T*, const T*, int, \
+                                   const int*, T*, T*, cudaStream_t);                           \
+  template void launch_phi_from_columns<T>(const double*, int64_t, int, const double*,          \
+                                           const int*, int, T*, cudaStream_t);                  \
+  template void launch_window_mean<T>(const T*, int64_t, const int*, int, T*, cudaStream_t);   \
+  template void launch_sign_fix<T>(T*, int64_t, int, const int*, cudaStream_t);
+HY_INST(float)
+HY_INST(double)
+#undef HY_INST
+
+template <typename T>
+void launch_center_window(const T* ring, int64_t N, const int* win, int w, int wp, const T* psi,
+                          double* X, double* raw_part, double* raw_out, cudaStream_t s) {
+  const int blocks = 152 * 4;
+  k_center_window<T><<<blocks, 256, 0, HY_S(s)>>>(ring, N, win, w, wp, psi, X, raw_part);
+  k_sum_parts<<<1, 256, 0, HY_S(s)>>>(raw_part, blocks, raw_out);
+}
+template void launch_center_window<float>(const float*, int64_t, const int*, int, int,
+                                          const float*, double*, double*, double*, cudaStream_t);
+template void launch_center_window<double>(const double*, int64_t, const int*, int, int,
+                                           const double*, double*, double*, double*,
+                                           cudaStream_t);
+
+}  // namespace hy

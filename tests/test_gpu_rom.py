@@ -1,0 +1,131 @@
+"""GPU parity of the reduced-basis stages against the oracle (Sec. 2.3.1,
+2.3.3): gappy coordinates (Eq. red_coord), reconstruction, pointwise error,
+POD_m (Eq. pod) on windows of known spectrum, and ODEIM points (Eq. odeim),
+which must be identical row for row (both sides decide in FP64 on the same
+quantity; ties within 1e-12 go to the lowest row)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import rom, select
+from tests.gpu_util import Ctx, dev, host, dev_bits, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(prec, nx=72, ny=40, m=8, n_p=16, w=12):
+    return W.ArConfig(pde=W.PDE_EULER, scheme=W.SCHEME_RK2, nx=nx, ny=ny, dx=0.1, dy=0.1,
+                      dt=0.01, w=w, m=m, n_p=n_p, precision=prec)
+
+
+def _basis(N, m, seed, prec, concentrated=True):
+    g = np.random.Generator(np.random.PCG64(seed))
+    A = g.standard_normal((N, m))
+    if concentrated:   # a localized basis, like one around a moving front
+        A *= np.exp(-((np.arange(N) % 700) / 90.0) ** 2)[:, None] + 1e-3
+    Q, _ = np.linalg.qr(A)
+    if prec == W.PREC_F32:
+        Q = Q.astype(np.float32).astype(np.float64)
+    return Q
+
+
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+def test_gappy_coordinates(prec):
+    cfg = _cfg(prec)
+    N = cfg.ndof
+    Phi = _basis(N, cfg.m, 1, prec)
+    g = np.random.Generator(np.random.PCG64(2))
+    P = rom.odeim(Phi, cfg.n_p, cfg.tie_tol)
+    psi = g.standard_normal(N)
+    v = psi + Phi @ g.standard_normal(cfg.m) + 1e-3 * g.standard_normal(N)
+    if prec == W.PREC_F32:
+        psi = psi.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    want = rom.gappy_coords(Phi, P, v, psi)
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        y = torch.zeros(cfg.m, dtype=torch.float64, device="cuda")
+        phid = dev(Phi.T.copy(), dt)            # column-major N x m
+        hy.hyrom_stage_gappy(ctx, phid, cfg.m, dev(P, torch.int32), len(P), dev(v, dt),
+                             dev(psi, dt), y)
+        got = host(y)
+    assert rel_err(got, want) < (1e-12 if prec == W.PREC_F64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+def test_reconstruct_and_cell_error(prec):
+    cfg = _cfg(prec)
+    N, nc = cfg.ndof, cfg.ncell
+    Phi = _basis(N, cfg.m, 3, prec)
+    g = np.random.Generator(np.random.PCG64(4))
+    psi = g.standard_normal(N)
+    yv = g.standard_normal(cfg.m)
+    q = g.standard_normal(N)
+    if prec == W.PREC_F32:
+        psi = psi.astype(np.float32).astype(np.float64)
+        q = q.astype(np.float32).astype(np.float64)
+    shat = g.random(nc) < 0.2
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    tol = 1e-13 if prec == W.PREC_F64 else 2e-6
+    with Ctx(cfg) as (hy, ctx):
+        phid = dev(Phi.T.copy(), dt)
+        qd = dev(q, dt)
+        hy.hyrom_stage_reconstruct(ctx, phid, cfg.m, dev(yv), dev(psi, dt), dev_bits(shat), qd)
+        got = host(qd).reshape(4, -1)
+        eps = torch.zeros(nc, dtype=dt, device="cuda")
+        hy.hyrom_stage_cell_error(ctx, dev(q, dt), dev(psi, dt), phid, cfg.m, dev(yv), eps)
+        got_e = host(eps)
+    rec = (psi + Phi @ yv).reshape(4, -1)
+    assert np.array_equal(got[:, shat], q.reshape(4, -1)[:, shat])
+    assert rel_err(got[:, ~shat], rec[:, ~shat]) < tol
+    want_e = select.cell_error(q, psi, Phi, yv, 4)
+    assert rel_err(got_e, want_e) < tol * 10
+
+
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+@pytest.mark.parametrize("w", [12, 11])
+def test_pod_of_known_spectrum(prec, w):
+    cfg = _cfg(prec, w=w, m=6)
+    N = cfg.ndof
+    g = np.random.Generator(np.random.PCG64(10 + w))
+    U, _ = np.linalg.qr(g.standard_normal((N, w)))
+    V, _ = np.linalg.qr(g.standard_normal((w, w)))
+    sig = 0.6 ** np.arange(w)
+    psi = 2.0 + g.standard_normal(N) * 0.1
+    X = psi[:, None] + (U * sig) @ V.T
+    if prec == W.PREC_F32:
+        X = X.astype(np.float32).astype(np.float64)
+        psi = psi.astype(np.float32).astype(np.float64)
+    raw = float(np.sqrt((X * X).sum()))
+    Phi_o, s_o = rom.pod(X - psi[:, None], cfg.m, cfg.pod_tol, cfg.pod_abs * raw)
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        phi = torch.zeros(cfg.m * N, dtype=dt, device="cuda")
+        sg = torch.zeros(w, dtype=torch.float64, device="cuda")
+        me = hy.hyrom_stage_pod(ctx, dev(X.T.copy(), dt), w, dev(psi, dt), phi, sg)
+        Pg = host(phi)[: me * N].reshape(me, N).T.astype(np.float64)
+        sg = host(sg)
+    assert me == Phi_o.shape[1] == cfg.m
+    if prec == W.PREC_F64:
+        assert rel_err(sg[:w], s_o[:w]) < 1e-13
+        assert np.abs(Pg @ Pg.T - Phi_o @ Phi_o.T).max() < 1e-12
+        assert np.abs(Pg - Phi_o).max() < 1e-12          # same sign convention
+    else:
+        assert rel_err(sg[:cfg.m], s_o[:cfg.m]) < 1e-5
+        assert np.abs(Pg @ Pg.T - Phi_o @ Phi_o.T).max() < 2e-4
+
+
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+@pytest.mark.parametrize("N,m,n_p,conc", [(600, 4, 9, False), (40000, 8, 17, True),
+                                          (40000, 16, 32, False)])
+def test_odeim_points_identical(prec, N, m, n_p, conc):
+    cfg = W.ArConfig(pde=W.PDE_BURGERS, scheme=W.SCHEME_RK2, nx=N, ny=1, dx=1.0 / N, dy=1.0,
+                     dt=1e-3, w=m + 2, m=m, n_p=n_p, precision=prec)
+    Phi = _basis(N, m, 20 + m, prec, concentrated=conc)
+    want = rom.odeim(Phi, n_p, cfg.tie_tol)
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        pts = torch.zeros(n_p, dtype=torch.int32, device="cuda")
+        hy.hyrom_stage_odeim(ctx, dev(Phi.T.copy(), dt), m, n_p, pts)
+        got = host(pts).tolist()
+    assert got == want
