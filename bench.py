@@ -222,6 +222,7 @@ def run_ours(a):
         ck = clocks.stop()
         ms = e0.elapsed_time(e1)
         stages = hyrom.hyrom_stage_times(ctx)
+        odc = hyrom.hyrom_odeim_counters(ctx)
         hyrom.hyrom_profile(ctx, False)
         t = torch.tensor([ms], device="cuda")
         if world > 1:
@@ -282,7 +283,8 @@ def run_ours(a):
            "config": config_dict(a, cfg),
            "sampled_cell_updates_per_s": world * ns_sum / (ms_max / 1e3),
            "n_s_avg": n_s_avg, "m_eff": m_eff, "stages": per,
-           "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e}
+           "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e,
+           "odeim_counters_last_step": odc}
     if rank == 0 and not a.no_err:
         out["err_vs_fp64"] = err_vs_fp64(a)
     if rank == 0 and not a.no_cpu_baseline:

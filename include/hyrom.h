@@ -138,11 +138,17 @@ enum {
   HYROM_T_GRAM = 6,     /* ring Gram row of a new snapshot (FP32 POD)      */
   HYROM_T_EIG = 7,      /* window Gram centring + eigensolve (line 24)     */
   HYROM_T_FORMPHI = 8,  /* basis formation and next psi (lines 24, 29)     */
-  HYROM_T_ODEIM = 9,    /* ODEIM points and the sampled pseudo-inverse     */
+  HYROM_T_ODEIM = 9,    /* ODEIM oversampling and the sampled pseudo-inverse */
   HYROM_T_MASKS = 10,   /* union / dilation / Neighbors (lines 26-28)      */
-  HYROM_NSTAGE = 11
+  HYROM_T_DEIM = 11,    /* DEIM points, the first m of ODEIM (line 25)     */
+  HYROM_NSTAGE = 12
 };
 hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
+/* Work counters of the last ODEIM call (rebuild or stage entry point):
+ * out4[0] rows scored exactly by DEIM beyond the probe, out4[1] rows
+ * screened by the FP32 bound in oversampling, out4[2] exact FP64 secular
+ * solves in oversampling, out4[3] oversampling steps.  Synchronises. */
+hyrom_status hyrom_odeim_counters(hyrom_ctx* ctx, int64_t* out4);
 hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count);
 
 /* ---- Algorithm 1 --------------------------------------------------------

@@ -90,6 +90,7 @@ struct hyrom_ctx {
   double* rawpart = nullptr;
   int* rotated = nullptr;
   double* ident = nullptr;
+  double* jbuf = nullptr;
   // ODEIM
   void* od_ws = nullptr;
   // Newton
@@ -233,6 +234,13 @@ void t_collect(hyrom_ctx* c) {
     }
     c->ev_pending[i] = 0;
   }
+}
+
+// DEIM -> oversampling boundary inside the ODEIM launcher
+void odeim_mark(void* p, int) {
+  hyrom_ctx* c = (hyrom_ctx*)p;
+  t_end(c, HYROM_T_DEIM);
+  t_begin(c, HYROM_T_ODEIM);
 }
 
 // ring slot of snapshot step j
@@ -426,7 +434,10 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
       hy::launch_gram_center_explicit(ctx->H, nslot, ctx->win_dev, w, ctx->hp, ctx->pp, ctx->Gc,
                                       wp, ctx->xraw2, ctx->st);
     }
-    hy::launch_jacobi_sym(ctx->Gc, wp, ctx->V, ctx->lam, 60, nullptr, 0, ctx->st);
+    if (hy::run_jacobi_multi(ctx->Gc, wp, ctx->V, ctx->lam, ctx->jbuf, ctx->rotated,
+                             (int*)ctx->host + 8, ctx->xraw2 + 1, (double*)ctx->host + 8, 60,
+                             ctx->st) < 0)
+      return fail(ctx, HYROM_ECUDA, "Jacobi eigensolver: %s", cudaGetErrorString(cudaGetLastError()));
     hy::launch_pod_coeffs<T>(ctx->lam, ctx->V, wp, w, cf.m, cf.pod_tol, cf.pod_abs, ctx->xraw2,
                              ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
     t_end(ctx, HYROM_T_EIG);
@@ -532,9 +543,10 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   if (me > 0) {
     int np = cf.n_p;
     if (np > ctx->N) np = (int)ctx->N;
-    t_begin(ctx, HYROM_T_ODEIM);
-    hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts, ctx->od_ws,
-                        ctx->st);
+    t_begin(ctx, HYROM_T_DEIM);
+    if (hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts,
+                            ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx) < 0)
+      return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
     ctx->np_eff = np;
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));
     hy::launch_gappy_pinv<T>((const T*)ctx->phi, ctx->N, me, ctx->pts, np, ctx->pinv,
@@ -654,6 +666,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->lam, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->sig, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->xraw2, 64);
+  ok &= dal(ctx, &ctx->jbuf, (size_t)2 * wp * wp * sizeof(double));
   ok &= dal(ctx, &ctx->m_eff_dev, 64);
   ok &= dalloc(ctx, &ctx->C, (size_t)wp * m * es);
   ok &= dal(ctx, &ctx->Cd, (size_t)wp * m * sizeof(double));
@@ -729,6 +742,16 @@ hyrom_status hyrom_profile(hyrom_ctx* ctx, int on) {
     ctx->stage_n[i] = 0;
     ctx->ev_pending[i] = 0;
   }
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_odeim_counters(hyrom_ctx* ctx, int64_t* out4) {
+  if (!ctx || !out4) return HYROM_EINVAL;
+  if (ctx->sticky) return HYROM_ECUDA;
+  unsigned long long* h = (unsigned long long*)ctx->host;
+  hy::odeim_stats(ctx->od_ws, h, ctx->st);
+  if (hyrom_status s = sync(ctx)) return s;
+  for (int i = 0; i < 4; ++i) out4[i] = (int64_t)h[i];
   return HYROM_OK;
 }
 
@@ -1008,12 +1031,14 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
                                int32_t* points_out) {
   GUARD();
   if (!phi || !points_out || m < 1 || m > ctx->cfg.m || n_p < m || n_p > 1024) return HYROM_EINVAL;
+  int rc;
   if (ctx->f32)
-    hy::launch_odeim<float>((const float*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
-                            ctx->od_ws, ctx->st);
+    rc = hy::launch_odeim<float>((const float*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
+                                 ctx->od_ws, (char*)ctx->host + 256, ctx->st);
   else
-    hy::launch_odeim<double>((const double*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
-                             ctx->od_ws, ctx->st);
+    rc = hy::launch_odeim<double>((const double*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol,
+                                  points_out, ctx->od_ws, (char*)ctx->host + 256, ctx->st);
+  if (rc < 0) return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
   CKL();
   return sync(ctx);
 }

@@ -80,6 +80,9 @@ void launch_center_window(const T* ring, int64_t N, const int* win, int w, int w
 void launch_hestenes_round(double* X, int64_t N, int wp, double* V, int r, double tol,
                            int* rotated, cudaStream_t s);
 void launch_identity(double* V, int n, cudaStream_t s);
+int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
+                     int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
+                     cudaStream_t s);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
 template <typename T>
 void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,
@@ -104,9 +107,11 @@ void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch,
 
 // odeim.cu
 template <typename T>
-void launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
-                  cudaStream_t s);
+int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
+                 void* host_pinned, cudaStream_t s, void (*mark)(void*, int) = nullptr,
+                 void* mark_arg = nullptr);
 size_t odeim_ws_bytes(int64_t N, int m);
+void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
 void launch_jacobi_padded(const double* M, int m, int n, double* V, double* lam, double* pad,
                           cudaStream_t s);
 

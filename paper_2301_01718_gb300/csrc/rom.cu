@@ -237,6 +237,19 @@ void launch_cell_error(const T* g, const T* psi, const T* phi, int64_t nc, int n
 // part[j * nchunk + chunk] = sum over the chunk's rows of ring[s][r]*ring[j][r]
 // Grid: x = ring slot j (fastest, so the CTAs in flight share the chunk of
 // slot s through L2), y = row chunk.
+// Dot product accumulated exactly enough for the centring identity: each
+// product a*b is split exactly into p + e (p = fl(a*b), e = fma(a, b, -p)),
+// and the running sum is a float-float pair (hi, lo) updated with the
+// error-free TwoSum of Knuth; lo also collects the product errors.  The
+// per-thread pair is combined in FP64.  FP32 data only (FP64 data uses FP64).
+HY_DEV void ff_add(float& hi, float& lo, float p, float e) {
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float t = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo = lo + (t + e);
+}
+
 template <typename T>
 __global__ void k_gram_row(const T* __restrict__ ring, int64_t N, int s, int64_t chunk,
                            double* __restrict__ part) {
@@ -247,8 +260,19 @@ __global__ void k_gram_row(const T* __restrict__ ring, int64_t N, int s, int64_t
   const T* a = ring + (int64_t)s * N;
   const T* b = ring + (int64_t)j * N;
   double acc = 0.0;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
-    acc = fma((double)a[r], (double)b[r], acc);
+  if (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const float x = (float)a[r], y = (float)b[r];
+      const float p = x * y;
+      const float e = fmaf(x, y, -p);
+      ff_add(hi, lo, p, e);
+    }
+    acc = (double)hi + (double)lo;
+  } else {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+      acc = fma((double)a[r], (double)b[r], acc);
+  }
   acc = block_sum(acc);
   if (threadIdx.x == 0) part[(int64_t)j * gridDim.y + blockIdx.y] = acc;
 }
@@ -382,6 +406,13 @@ template void launch_dots<float>(const float*, const float*, int64_t, int, doubl
 template void launch_dots<double>(const double*, const double*, int64_t, int, double*, int,
                                   double*, cudaStream_t);
 
+__global__ void k_identity(double* V, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x)
+    V[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+void launch_identity(double* V, int n, cudaStream_t s) { k_identity<<<16, 256, 0, HY_S(s)>>>(V, n); }
+
 // ---------------------------------------------------------------------------
 // two-sided cyclic Jacobi (FP64, one CTA): A (n x n, n even) in dynamic
 // shared memory, V (n x n column-major) in global memory.  Round-robin
@@ -407,12 +438,24 @@ __global__ void k_jacobi_sym(const double* __restrict__ Ain, int n, double* __re
   extern __shared__ double A[];
   __shared__ double cs[2 * 128];
   __shared__ int rotated;
+  __shared__ double scale;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int half = n / 2;
   for (int i = tid; i < n * n; i += nt) A[i] = Ain[i];
   if (!warm)
     for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
   __syncthreads();
+  // rotation threshold: relative to the two diagonal entries, with a floor
+  // at rounding level of the largest diagonal entry (rounding noise would
+  // otherwise keep near-null pairs rotating forever)
+  {
+    double mx = 0.0;
+    for (int i = tid; i < n; i += nt) mx = fmax(mx, fabs(A[i * n + i]));
+    mx = block_max(mx);
+    if (tid == 0) scale = mx;
+  }
+  __syncthreads();
+  const double floor_abs = 1e-16 * scale;
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
     if (tid == 0) rotated = 0;
@@ -423,7 +466,7 @@ __global__ void k_jacobi_sym(const double* __restrict__ Ain, int n, double* __re
         rr_pair(n, r, b, p, q);
         const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
         double c = 1.0, s = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-16 * sqrt(fabs(app * aqq))) {
+        if (fabs(apq) > floor_abs && fabs(apq) > 1e-14 * sqrt(fabs(app * aqq))) {
           const double tau = (aqq - app) / (2.0 * apq);
           const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + t * t);
@@ -464,6 +507,118 @@ __global__ void k_jacobi_sym(const double* __restrict__ Ain, int n, double* __re
   }
   for (int i = tid; i < n; i += nt) lam[i] = A[i * n + i];
   if (tid == 0 && sweeps_out) *sweeps_out = sw;
+}
+
+// One round of two-sided cyclic Jacobi spread over n/2 CTAs (CTA b owns the
+// rows of rotation pair b).  Every CTA recomputes the round's n/2 rotations
+// from Ain (three entries each), rotates its two rows, applies all column
+// rotations to them and writes Aout; V (column-major, column j of V is row j
+// of the stored array) is rotated in place (CTA b touches only columns p, q).
+// Reading Ain and writing Aout keeps CTAs independent: one launch per round.
+__global__ void k_jacobi_round(const double* __restrict__ Ain, double* __restrict__ Aout, int n,
+                               double* __restrict__ V, int r, double floor_abs, int* rotated) {
+  __shared__ double cs[2 * 128];
+  __shared__ double rp[128], rq[128];
+  const int half = n / 2, tid = threadIdx.x;
+  for (int b = tid; b < half; b += blockDim.x) {
+    int p, q;
+    rr_pair(n, r, b, p, q);
+    const double apq = Ain[p * n + q], app = Ain[p * n + p], aqq = Ain[q * n + q];
+    double c = 1.0, sn = 0.0;
+    if (fabs(apq) > floor_abs && fabs(apq) > 1e-14 * sqrt(fabs(app * aqq))) {
+      const double tau = (aqq - app) / (2.0 * apq);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      c = 1.0 / sqrt(1.0 + t * t);
+      sn = t * c;
+    }
+    cs[2 * b] = c;
+    cs[2 * b + 1] = sn;
+  }
+  __syncthreads();
+  int p, q;
+  rr_pair(n, r, blockIdx.x, p, q);
+  const double c = cs[2 * blockIdx.x], sn = cs[2 * blockIdx.x + 1];
+  for (int k = tid; k < n; k += blockDim.x) {
+    const double ap = Ain[p * n + k], aq = Ain[q * n + k];
+    rp[k] = c * ap - sn * aq;
+    rq[k] = sn * ap + c * aq;
+    if (sn != 0.0) {
+      const double vp = V[(int64_t)p * n + k], vq = V[(int64_t)q * n + k];
+      V[(int64_t)p * n + k] = c * vp - sn * vq;
+      V[(int64_t)q * n + k] = sn * vp + c * vq;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < n; k += blockDim.x) {
+    // column rotation of the pair that contains k: in round r of the circle
+    // schedule, player n-1 meets r and every other k meets (2r - k) mod (n-1)
+    const int nm1 = n - 1;
+    int partner, b2;
+    if (k == nm1 || k == r) {
+      partner = k == nm1 ? r : nm1;
+      b2 = 0;
+    } else {
+      partner = ((2 * r - k) % nm1 + nm1) % nm1;
+      const int b1 = ((k - r) % nm1 + nm1) % nm1;
+      b2 = b1 <= n / 2 - 1 ? b1 : nm1 - b1;
+    }
+    const int p2 = k < partner ? k : partner, q2 = k < partner ? partner : k;
+    const double c2 = cs[2 * b2], s2 = cs[2 * b2 + 1];
+    double np_, nq_;
+    if (k == p2) {
+      np_ = c2 * rp[p2] - s2 * rp[q2];
+      nq_ = c2 * rq[p2] - s2 * rq[q2];
+    } else {
+      np_ = s2 * rp[p2] + c2 * rp[q2];
+      nq_ = s2 * rq[p2] + c2 * rq[q2];
+    }
+    Aout[p * n + k] = np_;
+    Aout[q * n + k] = nq_;
+  }
+  if (tid == 0 && sn != 0.0) *rotated = 1;
+}
+
+__global__ void k_diag_max(const double* __restrict__ A, int n, double* out) {
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(A[i * n + i]));
+  mx = block_max(mx);
+  if (threadIdx.x == 0) *out = mx;
+}
+
+__global__ void k_copy_diag(const double* __restrict__ A, int n, double* __restrict__ lam) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[i * n + i];
+}
+
+// Multi-CTA Jacobi: A (n x n, n even, n <= 128) is copied into the ping-pong
+// pair (buf, buf + n*n); V starts at the identity.  The host reads one flag
+// per sweep (through `host_flag`, pinned) and stops after a sweep without
+// rotation or after max_sweeps.  Returns the sweeps run, or -1 on a CUDA error.
+int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
+                     int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
+                     cudaStream_t s) {
+  double* A0 = buf;
+  double* A1 = buf + (size_t)n * n;
+  cudaMemcpyAsync(A0, A, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s);
+  k_identity<<<16, 256, 0, HY_S(s)>>>(V, n);
+  k_diag_max<<<1, 128, 0, HY_S(s)>>>(A0, n, scale_dev);
+  cudaMemcpyAsync(host_scale, scale_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  const double floor_abs = 1e-16 * host_scale[0];
+  int sw = 0;
+  for (; sw < max_sweeps; ++sw) {
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    for (int r = 0; r < n - 1; ++r) {
+      k_jacobi_round<<<n / 2, 128, 0, HY_S(s)>>>(A0, A1, n, V, r, floor_abs, flag);
+      double* t = A0;
+      A0 = A1;
+      A1 = t;
+    }
+    cudaMemcpyAsync(host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    if (!host_flag[0]) break;
+  }
+  k_copy_diag<<<1, 128, 0, HY_S(s)>>>(A0, n, lam);
+  return sw;
 }
 
 __global__ void k_pad_sym(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
@@ -542,19 +697,27 @@ void launch_pod_coeffs(const double* lam, const double* V, int n, int w, int m, 
 }
 
 // Phi[:, j] = sum_i (ring[win[i]] - psi) C[i][j]  (j < m_eff), and
-// psi_next = mean of the window slots, in one pass over the window.
+// psi_next = mean of the window slots, in one pass over the window.  One
+// row per thread; the snapshot values of 16 window slots are loaded before
+// they are used, so each thread keeps 16 independent loads in flight (the
+// kernel is otherwise latency-bound), and coefficients come four at a time
+// from shared memory (rows of C padded to MMAX).
 template <typename T, int MMAX>
-__global__ void __launch_bounds__(256) k_form_phi(const T* __restrict__ ring, int64_t N,
-                                                  const int* __restrict__ win, int w,
-                                                  const T* __restrict__ psi,
-                                                  const T* __restrict__ C, int m,
-                                                  const int* __restrict__ m_eff_dev,
-                                                  T* __restrict__ phi, T* __restrict__ psi_next) {
+__global__ void __launch_bounds__(256, 2) k_form_phi(const T* __restrict__ ring, int64_t N,
+                                                     const int* __restrict__ win, int w,
+                                                     const T* __restrict__ psi,
+                                                     const T* __restrict__ C, int m,
+                                                     const int* __restrict__ m_eff_dev,
+                                                     T* __restrict__ phi, T* __restrict__ psi_next) {
+  constexpr int U = 16;
   extern __shared__ unsigned char smraw[];
-  T* Cs = reinterpret_cast<T*>(smraw);
+  T* Cs = reinterpret_cast<T*>(smraw);  // w x MMAX, zero padded
   __shared__ int ws[256];
   const int me = *m_eff_dev;
-  for (int i = threadIdx.x; i < w * m; i += blockDim.x) Cs[i] = C[i];
+  for (int i = threadIdx.x; i < w * MMAX; i += blockDim.x) {
+    const int r = i / MMAX, j = i % MMAX;
+    Cs[i] = j < m && j < me ? C[r * m + j] : (T)0;
+  }
   for (int i = threadIdx.x; i < w; i += blockDim.x) ws[i] = win[i];
   __syncthreads();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
@@ -564,17 +727,33 @@ __global__ void __launch_bounds__(256) k_form_phi(const T* __restrict__ ring, in
     for (int j = 0; j < MMAX; ++j) acc[j] = (T)0;
     const T pr = psi[r];
     T sum = (T)0, comp = (T)0;  // Kahan-compensated window sum
-    for (int i = 0; i < w; ++i) {
-      const T g = ring[(int64_t)ws[i] * N + r];
-      const T yk = g - comp;
-      const T tk = sum + yk;
-      comp = (tk - sum) - yk;
-      sum = tk;
-      const T x = g - pr;
-      const T* Ci = Cs + i * m;
+    for (int i0 = 0; i0 < w; i0 += U) {
+      T g[U];
 #pragma unroll
-      for (int j = 0; j < MMAX; ++j)
-        if (j < me) acc[j] = fma(x, Ci[j], acc[j]);
+      for (int u = 0; u < U; ++u)
+        g[u] = i0 + u < w ? __ldg(ring + (int64_t)ws[i0 + u] * N + r) : (T)0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (i0 + u < w) {
+          const T yk = g[u] - comp, tk = sum + yk;
+          comp = (tk - sum) - yk;
+          sum = tk;
+          const T x = g[u] - pr;
+          const T* Ci = Cs + (i0 + u) * MMAX;
+#pragma unroll
+          for (int j = 0; j < MMAX; j += 4) {
+            T cv[4];
+            if (sizeof(T) == 4) {
+              const float4 q = *reinterpret_cast<const float4*>(Ci + j);
+              cv[0] = q.x; cv[1] = q.y; cv[2] = q.z; cv[3] = q.w;
+            } else {
+              cv[0] = Ci[j]; cv[1] = Ci[j + 1]; cv[2] = Ci[j + 2]; cv[3] = Ci[j + 3];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[j + v] = fma(x, cv[v], acc[j + v]);
+          }
+        }
+      }
     }
 #pragma unroll
     for (int j = 0; j < MMAX; ++j)
@@ -586,7 +765,8 @@ __global__ void __launch_bounds__(256) k_form_phi(const T* __restrict__ ring, in
 template <typename T>
 void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* psi, const T* C,
                      int m, const int* m_eff_dev, T* phi, T* psi_next, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (size_t)w * m;
+  const int mm = m <= 8 ? 8 : (m <= 16 ? 16 : (m <= 32 ? 32 : 64));
+  const size_t smem = sizeof(T) * (size_t)w * mm;
   int64_t blocks = (N + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
 #define HY_FORM(MM)                                                                          \
@@ -688,12 +868,8 @@ __global__ void k_colnorm2(const double* __restrict__ X, int64_t N, double* __re
   if (threadIdx.x == 0) out[blockIdx.x] = a;
 }
 
-__global__ void k_identity(double* V, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x)
-    V[i] = (i / n == i % n) ? 1.0 : 0.0;
-}
 
-void launch_identity(double* V, int n, cudaStream_t s) { k_identity<<<16, 256, 0, HY_S(s)>>>(V, n); }
+
 
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s) {
   k_colnorm2<<<ncol, 256, 0, HY_S(s)>>>(X, N, out);

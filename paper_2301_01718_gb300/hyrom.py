@@ -113,6 +113,7 @@ def lib():
         "hyrom_device_bytes": (C.c_size_t, [vp]),
         "hyrom_kernel_launches": (C.c_uint64, []),
         "hyrom_profile": (st, [vp, C.c_int]),
+        "hyrom_odeim_counters": (st, [vp, C.POINTER(i64)]),
         "hyrom_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(i64)]),
         "hyrom_advance": (st, [vp, C.POINTER(HyromStepInfo)]),
         "hyrom_update_basis": (st, [vp, C.POINTER(HyromStepInfo)]),
@@ -177,11 +178,18 @@ def hyrom_kernel_launches():
 
 
 STAGES = ["full", "partial", "gappy", "recon", "filter", "select", "gram", "eig", "formphi",
-          "odeim", "masks"]
+          "odeim", "masks", "deim"]
 
 
 def hyrom_profile(ctx, on=True):
     _check(ctx, lib().hyrom_profile(ctx, int(bool(on))))
+
+
+def hyrom_odeim_counters(ctx):
+    out = (C.c_int64 * 4)()
+    _check(ctx, lib().hyrom_odeim_counters(ctx, out))
+    return {"deim_rows": out[0], "odeim_screened": out[1], "odeim_exact": out[2],
+            "odeim_steps": out[3]}
 
 
 def hyrom_stage_times(ctx):
