@@ -210,6 +210,7 @@ def run_ours(a):
         clocks.start()
         l0 = hyrom.hyrom_kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         ns_sum, infos = 0, []
         for _ in range(a.steps):
@@ -217,6 +218,7 @@ def run_ours(a):
             ns_sum += info["n_s"]
             infos.append(info)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         launches = hyrom.hyrom_kernel_launches() - l0
         ck = clocks.stop()

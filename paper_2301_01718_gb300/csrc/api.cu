@@ -65,6 +65,10 @@ struct hyrom_ctx {
   void *fg = nullptr, *ftmp = nullptr, *rho_old = nullptr, *rho_new = nullptr;
   double* fpart = nullptr;
   int* fctl = nullptr;
+  uint32_t* kbits = nullptr;
+  int* ftiles_a = nullptr;
+  int* ftiles_b = nullptr;
+  int* fcounts = nullptr;
   int* forders = nullptr;
   // selection
   void* eps = nullptr;
@@ -365,9 +369,9 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     // line 13: SpatialFilter
     t_begin(ctx, HYROM_T_FILTER);
     if (cf.n_filt > 0)
-      hy::launch_filter<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp, k,
-                           (T*)ctx->fg, (T*)ctx->ftmp, (T*)ctx->rho_old, (T*)ctx->rho_new,
-                           ctx->fpart, ctx->fctl, ctx->st);
+      hy::launch_filter_sparse<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp,
+                                  k, (T*)ctx->fg, ctx->kbits, ctx->ftiles_a, ctx->ftiles_b,
+                                  ctx->fcounts, ctx->fpart, ctx->fctl, ctx->st);
     t_end(ctx, HYROM_T_FILTER);
   }
   CKL();
@@ -446,7 +450,9 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
                            ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg, ctx->st);
     t_end(ctx, HYROM_T_FORMPHI);
   }
-  hy::launch_sign_fix<T>(phi_out, ctx->N, cf.m, ctx->m_eff_dev, ctx->st);
+  // column signs: normalised on the FP64 path (direct basis comparison);
+  // the method is invariant to them, so the FP32 path skips the extra pass
+  if (!ctx->f32) hy::launch_sign_fix<T>(phi_out, ctx->N, cf.m, ctx->m_eff_dev, ctx->st);
   CKL();
   int* hi = (int*)ctx->host;
   CK(cudaMemcpyAsync(hi, ctx->m_eff_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -652,7 +658,11 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dalloc(ctx, &ctx->ftmp, N * es);
   ok &= dalloc(ctx, &ctx->rho_old, nc * es);
   ok &= dalloc(ctx, &ctx->rho_new, nc * es);
-  ok &= dal(ctx, &ctx->fpart, 3 * 152 * 4 * sizeof(double));
+  ok &= dal(ctx, &ctx->fpart, 3 * 152 * 8 * sizeof(double));
+  ok &= dal(ctx, &ctx->kbits, nw * 4);
+  ok &= dal(ctx, &ctx->ftiles_a, (size_t)ntiles_max * sizeof(int));
+  ok &= dal(ctx, &ctx->ftiles_b, (size_t)ntiles_max * sizeof(int));
+  ok &= dal(ctx, &ctx->fcounts, 64);
   ok &= dal(ctx, &ctx->fctl, 64);
   ok &= dalloc(ctx, &ctx->eps, nc * es);
   ok &= dal(ctx, &ctx->keys, nc * sizeof(unsigned long long));
@@ -945,15 +955,15 @@ hyrom_status hyrom_stage_filter(hyrom_ctx* ctx, void* q_io, const void* q_prev, 
   const hyrom_config& cf = ctx->cfg;
   if (cf.n_filt > 0) {
     if (ctx->f32)
-      hy::launch_filter<float>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
-                               (float*)q_io, (const float*)q_prev, k, (float*)ctx->fg,
-                               (float*)ctx->ftmp, (float*)ctx->rho_old, (float*)ctx->rho_new,
-                               ctx->fpart, ctx->fctl, ctx->st);
+      hy::launch_filter_sparse<float>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
+                                      (float*)q_io, (const float*)q_prev, k, (float*)ctx->fg,
+                                      ctx->kbits, ctx->ftiles_a, ctx->ftiles_b, ctx->fcounts,
+                                      ctx->fpart, ctx->fctl, ctx->st);
     else
-      hy::launch_filter<double>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
-                                (double*)q_io, (const double*)q_prev, k, (double*)ctx->fg,
-                                (double*)ctx->ftmp, (double*)ctx->rho_old, (double*)ctx->rho_new,
-                                ctx->fpart, ctx->fctl, ctx->st);
+      hy::launch_filter_sparse<double>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
+                                       (double*)q_io, (const double*)q_prev, k, (double*)ctx->fg,
+                                       ctx->kbits, ctx->ftiles_a, ctx->ftiles_b, ctx->fcounts,
+                                       ctx->fpart, ctx->fctl, ctx->st);
   }
   CKL();
   int* hi = (int*)ctx->host;

@@ -73,6 +73,13 @@ HY_DEV double bitsd(unsigned long long b) { return __longlong_as_double((long lo
 
 // Butterfly sum; lane 0's value is broadcast so that every lane holds the
 // same bits (lanes would otherwise associate the terms differently).
+// order-preserving map of a double to an unsigned 64-bit key (integer
+// compares instead of FP64 compares, which run on the narrow FP64 pipe)
+HY_DEV unsigned long long dkey(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 template <typename T>
 HY_DEV T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -14,6 +14,7 @@
 // reading anything back.
 #include "common.cuh"
 #include "internal.h"
+#include "phys.cuh"
 
 namespace hy {
 
@@ -161,9 +162,314 @@ void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// fused, sparse filter pass
+//
+// One kernel per pass computes, for every cell of a tile, rho_old = rho(q),
+// the filtered state g = F_y(F_x(q)) and rho_new = rho(g) in shared memory
+// and takes the gate decision; kept cells get g in gbuf and a bit in kbits.
+// The values are those of the separate kernels above (same expressions, same
+// order), so FP64 results are identical.  After the first pass of an order,
+// q has changed only on the kept cells K, so g can change only within
+// distance n of K and rho_old / rho_new only within distance n + 1: every
+// other cell keeps its previous decision ("not kept").  The next pass
+// therefore visits only the tiles within n + 1 cells of K.
+// ---------------------------------------------------------------------------
+
+template <typename T, int NV>
+HY_DEV void nb_value(const DevCfg& c, const T* sm, int stride_v, int pos, int gi, int gj, double t,
+                     T* out) {
+  // neighbour value for the residual: smem value (in-domain, wrapped or
+  // clamped), or the exact shock state on a shock side
+  const bool outx = (gi < 0 || gi >= c.nx) && c.bc[0] != HYROM_BC_PERIODIC;
+  const bool outy = c.ny > 1 && (gj < 0 || gj >= c.ny) && c.bc[2] != HYROM_BC_PERIODIC;
+  if (outx || outy) {
+    const int side = outx ? (gi < 0 ? 0 : 1) : (gj < 0 ? 2 : 3);
+    if (c.bc[side] == HYROM_BC_SHOCK) {
+      T s4[4];
+      shock_state<T>(c, gi, gj, t, s4);
+      for (int a = 0; a < NV; ++a) out[a] = s4[a];
+      return;
+    }
+  }
+  for (int a = 0; a < NV; ++a) out[a] = sm[a * stride_v + pos];
+}
+
+template <typename T, int NV, int NF, int TX, int TY>
+__global__ void __launch_bounds__(256) k_filter_pass(DevCfg c, const T* __restrict__ q,
+                                                     const T* __restrict__ qp, double t,
+                                                     T* __restrict__ gbuf, uint32_t* __restrict__ kbits,
+                                                     const int* __restrict__ tiles,
+                                                     const int* __restrict__ ntiles_dev,
+                                                     int ntiles_all, double* __restrict__ part,
+                                                     const int* __restrict__ done) {
+  constexpr bool TWO = TY > 1;
+  constexpr int H = NF + 1;
+  constexpr int SX = TX + 2 * H, SY = TWO ? TY + 2 * H : 1;
+  constexpr int FX = TX + 2, FY = SY;  // F_x rows aligned with the q rows
+  constexpr int GX = TX + 2, GY = TWO ? TY + 2 : 1;
+  extern __shared__ unsigned char fsm[];
+  T* qs = reinterpret_cast<T*>(fsm);
+  T* fx = qs + NV * SY * SX;
+  T* gs = fx + NV * FY * FX;
+  if (*done) return;
+  const int tiles_x = (c.nx + TX - 1) / TX;
+  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
+  const T scale = (T)(NF == 1 ? 0.25 : (NF == 2 ? 0.0625 : 0.015625));
+  const T dt = (T)c.dt;
+  double cnt = 0.0, dec = 0.0, tot = 0.0;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int tile = tiles ? tiles[it] : it;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    __syncthreads();
+    // q on the tile and an H-cell halo (periodic sides wrap, others clamp)
+    for (int idx = threadIdx.x; idx < SY * SX; idx += blockDim.x) {
+      const int sy = idx / SX, sx = idx % SX;
+      int gi = x0 - H + sx, gj = TWO ? y0 - H + sy : 0;
+      gi = perx ? imod(gi, c.nx) : (gi < 0 ? 0 : (gi >= c.nx ? c.nx - 1 : gi));
+      if (TWO) gj = pery ? imod(gj, c.ny) : (gj < 0 ? 0 : (gj >= c.ny ? c.ny - 1 : gj));
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      for (int a = 0; a < NV; ++a) qs[(a * SY + sy) * SX + sx] = q[a * c.nc + cell];
+    }
+    __syncthreads();
+    // F_x on columns tile +- 1, every staged row (rows hold clamped/wrapped
+    // data; row fy is global row y0 - H + fy, like the q rows)
+    for (int idx = threadIdx.x; idx < FY * FX; idx += blockDim.x) {
+      const int fy = idx / FX, fxc = idx % FX;
+      const int sy = fy, sx = fxc + NF;
+      for (int a = 0; a < NV; ++a) {
+        const T* row = qs + (a * SY + sy) * SX;
+        T acc = (T)0;
+#pragma unroll
+        for (int tt = 0; tt < 2 * NF + 1; ++tt) {
+          const double wt = Shapiro<NF>::w(tt);
+          const T x = row[sx + tt - NF];
+          const T term = wt == 1.0 ? x : (wt == -1.0 ? -x : (T)wt * x);
+          acc = tt == 0 ? term : acc + term;
+        }
+        fx[(a * FY + fy) * FX + fxc] = acc * scale;
+      }
+    }
+    __syncthreads();
+    // g = F_y(F_x q) on tile +- 1: g row gy is global row y0 - 1 + gy, whose
+    // taps are F_x rows gy + tt (tt = 0..2 NF) since H - 1 = NF
+    for (int idx = threadIdx.x; idx < GY * GX; idx += blockDim.x) {
+      const int gy = idx / GX, gx = idx % GX;
+      for (int a = 0; a < NV; ++a) {
+        T val;
+        if (TWO) {
+          T acc = (T)0;
+#pragma unroll
+          for (int tt = 0; tt < 2 * NF + 1; ++tt) {
+            const double wt = Shapiro<NF>::w(tt);
+            const T x = fx[(a * FY + gy + tt) * FX + gx];
+            const T term = wt == 1.0 ? x : (wt == -1.0 ? -x : (T)wt * x);
+            acc = tt == 0 ? term : acc + term;
+          }
+          val = acc * scale;
+        } else {
+          val = fx[a * FX + gx];
+        }
+        gs[(a * GY + gy) * GX + gx] = val;
+      }
+    }
+    __syncthreads();
+    // residual measures and the gate on the tile
+    for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+      const int ly = idx / TX, lx = idx % TX;
+      const int gi = x0 + lx, gj = y0 + ly;
+      if (gi >= c.nx || gj >= c.ny) continue;
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      T qC[NV], qW[NV], qE[NV], qS[NV], qN[NV], r[NV];
+      T gC[NV], gW[NV], gE[NV], gS[NV], gN[NV], rg[NV];
+      // q neighbours (clamped smem == outflow ghost; shock sides exact)
+      const int qsy = TWO ? ly + H : 0, qsx = lx + H;
+      const int qv = SY * SX;
+      nb_value<T, NV>(c, qs, qv, qsy * SX + qsx, gi, gj, t, qC);
+      nb_value<T, NV>(c, qs, qv, qsy * SX + qsx - 1, gi - 1, gj, t, qW);
+      nb_value<T, NV>(c, qs, qv, qsy * SX + qsx + 1, gi + 1, gj, t, qE);
+      if (TWO) {
+        nb_value<T, NV>(c, qs, qv, (qsy - 1) * SX + qsx, gi, gj - 1, t, qS);
+        nb_value<T, NV>(c, qs, qv, (qsy + 1) * SX + qsx, gi, gj + 1, t, qN);
+      } else {
+        for (int a = 0; a < NV; ++a) qS[a] = qN[a] = qC[a];
+      }
+      // g neighbours: out-of-domain non-periodic positions take the
+      // boundary cell's g (outflow) or the shock state
+      const int gy = TWO ? ly + 1 : 0, gx = lx + 1, gv = GY * GX;
+      const int wxm = (gi - 1 < 0 && !perx) ? gx : gx - 1;
+      const int wxp = (gi + 1 >= c.nx && !perx) ? gx : gx + 1;
+      nb_value<T, NV>(c, gs, gv, gy * GX + gx, gi, gj, t, gC);
+      nb_value<T, NV>(c, gs, gv, gy * GX + wxm, gi - 1, gj, t, gW);
+      nb_value<T, NV>(c, gs, gv, gy * GX + wxp, gi + 1, gj, t, gE);
+      if (TWO) {
+        const int wym = (gj - 1 < 0 && !pery) ? gy : gy - 1;
+        const int wyp = (gj + 1 >= c.ny && !pery) ? gy : gy + 1;
+        nb_value<T, NV>(c, gs, gv, wym * GX + gx, gi, gj - 1, t, gS);
+        nb_value<T, NV>(c, gs, gv, wyp * GX + gx, gi, gj + 1, t, gN);
+      } else {
+        for (int a = 0; a < NV; ++a) gS[a] = gN[a] = gC[a];
+      }
+      rhs_cell<T, NV>(c, qC, qW, qE, qS, qN, r);
+      rhs_cell<T, NV>(c, gC, gW, gE, gS, gN, rg);
+      T ro = (T)0, rn = (T)0;
+      for (int a = 0; a < NV; ++a) {
+        const T p = qp[a * c.nc + cell];
+        const T Ro = (qC[a] - p) - dt * r[a];
+        const T Rn = (gC[a] - p) - dt * rg[a];
+        ro = a == 0 ? fabs(Ro) : ro + fabs(Ro);
+        rn = a == 0 ? fabs(Rn) : rn + fabs(Rn);
+      }
+      if (rn < ro) {
+        for (int a = 0; a < NV; ++a) gbuf[a * c.nc + cell] = gC[a];
+        atomicOr(&kbits[cell >> 5], 1u << (cell & 31));
+        cnt += 1.0;
+        dec += (double)(ro - rn);
+        tot += (double)ro;
+      }
+    }
+  }
+  cnt = block_sum(cnt);
+  dec = block_sum(dec);
+  tot = block_sum(tot);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = cnt;
+    part[3 * blockIdx.x + 1] = dec;
+    part[3 * blockIdx.x + 2] = tot;
+  }
+}
+
+// q = g on the kept cells of the listed tiles
+template <typename T>
+__global__ void k_filter_apply(DevCfg c, T* __restrict__ q, const T* __restrict__ gbuf,
+                               const uint32_t* __restrict__ kbits, int TX, int TY,
+                               const int* __restrict__ tiles, const int* __restrict__ ntiles_dev,
+                               int ntiles_all) {
+  const int tiles_x = (c.nx + TX - 1) / TX;
+  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int tile = tiles ? tiles[it] : it;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
+      const int gi = x0 + idx % TX, gj = y0 + idx / TX;
+      if (gi >= c.nx || gj >= c.ny) continue;
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      if (!bit_get(kbits, cell)) continue;
+      for (int v = 0; v < c.nvar; ++v) q[v * c.nc + cell] = gbuf[v * c.nc + cell];
+    }
+  }
+}
+
+// tiles that contain a cell within box distance R of a kept cell
+__global__ void k_filter_next_tiles(DevCfg c, const uint32_t* __restrict__ kbits, int TX, int TY,
+                                    int R, int* __restrict__ tiles, int* __restrict__ ntiles,
+                                    const int* __restrict__ done) {
+  if (*done) return;
+  const int tx = (c.nx + TX - 1) / TX, ty = (c.ny + TY - 1) / TY;
+  const bool twoD = c.ny > 1;
+  const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
+  const int Ry = twoD ? R : 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tx * ty; t += gridDim.x * blockDim.x) {
+    const int x0 = (t % tx) * TX, y0 = (t / tx) * TY;
+    bool any = false;
+    for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j) {
+      int jj = j;
+      if (twoD) {
+        if (pery)
+          jj = imod(j, c.ny);
+        else if (j < 0 || j >= c.ny)
+          continue;
+      } else {
+        jj = 0;
+      }
+      const int64_t rowbase = (int64_t)jj * c.nx;
+      for (int i = x0 - R; i < x0 + TX + R && !any; ++i) {
+        int ii = i;
+        if (perx)
+          ii = imod(i, c.nx);
+        else if (i < 0 || i >= c.nx)
+          continue;
+        any = bit_get(kbits, rowbase + ii);
+      }
+    }
+    if (any) tiles[atomicAdd(ntiles, 1)] = t;
+  }
+}
+
+template <typename T>
+void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
+                          double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
+                          int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
+                          cudaStream_t s) {
+  const bool twoD = c.ny > 1;
+  const int TX = twoD ? 32 : 256, TY = twoD ? 8 : 1;
+  const int nt = ((c.nx + TX - 1) / TX) * ((c.ny + TY - 1) / TY);
+  const int64_t nwords = (c.nc + 31) / 32;
+  const double t = (double)k * c.dt;
+  cudaMemsetAsync(ctl, 0, 3 * sizeof(int), s);
+  for (int o = 0; o < norders; ++o) {
+    const int n = orders[o];
+    k_set_int<<<1, 1, 0, HY_S(s)>>>(ctl, 0);
+    int* cur = nullptr;  // first pass: all tiles
+    int* nxt = tiles_a;
+    int* cur_n = counts;
+    int* nxt_n = counts + 1;
+    for (int pass = 0; pass < jmax_f; ++pass) {
+      cudaMemsetAsync(kbits, 0, nwords * sizeof(uint32_t), s);
+      const int grid = cur ? 152 * 8 : (nt < 152 * 8 ? nt : 152 * 8);
+#define HY_FP(NV, NN, TXX, TYY)                                                              \
+  do {                                                                                       \
+    constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
+    constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
+    constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
+    cudaFuncSetAttribute(k_filter_pass<T, NV, NN, TXX, TYY>,                                 \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_);             \
+    k_filter_pass<T, NV, NN, TXX, TYY><<<grid, 256, sm_, HY_S(s)>>>(                         \
+        c, q, qp, t, gbuf, kbits, cur, cur_n, nt, part, ctl);                                \
+  } while (0)
+#define HY_FP_N(NV, TXX, TYY) \
+  do {                        \
+    if (n == 1)               \
+      HY_FP(NV, 1, TXX, TYY); \
+    else if (n == 2)          \
+      HY_FP(NV, 2, TXX, TYY); \
+    else                      \
+      HY_FP(NV, 3, TXX, TYY); \
+  } while (0)
+      if (c.nvar == 4) {
+        if (twoD) HY_FP_N(4, 32, 8); else HY_FP_N(4, 256, 1);
+      } else {
+        if (twoD) HY_FP_N(1, 32, 8); else HY_FP_N(1, 256, 1);
+      }
+#undef HY_FP_N
+#undef HY_FP
+      k_gate_finalize<<<1, 256, 0, HY_S(s)>>>(part, grid, eps_f, ctl);
+      k_filter_apply<T><<<cur ? 152 * 8 : grid, 256, 0, HY_S(s)>>>(c, q, gbuf, kbits, TX, TY, cur,
+                                                                   cur_n, nt);
+      if (pass + 1 < jmax_f) {
+        cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
+        k_filter_next_tiles<<<(nt + 255) / 256, 256, 0, HY_S(s)>>>(c, kbits, TX, TY, n + 1, nxt,
+                                                                   nxt_n, ctl);
+        cur = nxt;
+        nxt = (nxt == tiles_a) ? tiles_b : tiles_a;
+        int* tn = cur_n;
+        cur_n = nxt_n;
+        nxt_n = tn;
+      }
+    }
+  }
+}
+
 template void launch_filter<float>(const DevCfg&, const int*, int, int, double, float*,
                                    const float*, int64_t, float*, float*, float*, float*, double*,
                                    int*, cudaStream_t);
+template void launch_filter_sparse<float>(const DevCfg&, const int*, int, int, double, float*,
+                                          const float*, int64_t, float*, uint32_t*, int*, int*,
+                                          int*, double*, int*, cudaStream_t);
+template void launch_filter_sparse<double>(const DevCfg&, const int*, int, int, double, double*,
+                                           const double*, int64_t, double*, uint32_t*, int*, int*,
+                                           int*, double*, int*, cudaStream_t);
 template void launch_filter<double>(const DevCfg&, const int*, int, int, double, double*,
                                     const double*, int64_t, double*, double*, double*, double*,
                                     double*, int*, cudaStream_t);

@@ -39,6 +39,12 @@ void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, 
                    T* q, const T* qp, int64_t k, T* g, T* tmp, T* rho_old, T* rho_new,
                    double* part, int* ctl, cudaStream_t s);
 
+template <typename T>
+void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
+                          double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
+                          int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
+                          cudaStream_t s);
+
 // rom.cu
 template <typename T>
 void launch_gappy_pinv(const T* phi, int64_t N, int m, const int* pts, int np, double* pinv,

@@ -109,11 +109,23 @@ __global__ void k_bucket_scan(const int* __restrict__ bcnt, int* __restrict__ bs
   }
 }
 
+// warp-aggregated: lanes with the same bucket share one atomic
 __global__ void k_bucket_scatter(int64_t N, const unsigned char* __restrict__ bkt, int* bcur,
                                  int* __restrict__ ord) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x)
-    ord[atomicAdd(&bcur[bkt[i]], 1)] = (int)i;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; base < N;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    const bool valid = i < N;
+    const int b = valid ? bkt[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int pos = 0;
+    if (valid && lane == leader) pos = atomicAdd(&bcur[b], __popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (valid) ord[pos + rank] = (int)i;
+  }
 }
 
 // ---- DEIM -------------------------------------------------------------------
@@ -289,16 +301,16 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
                              int m, double* __restrict__ lam_s, double* __restrict__ W_s,
                              OdCtl* ctl) {
   __shared__ int perm[128];
+  __shared__ unsigned long long key[128];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) key[i] = dkey(lam[i]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {  // ascending rank
+    int r = 0;
+    for (int i = 0; i < m; ++i) r += (key[i] < key[j]) || (key[i] == key[j] && i < j);
+    perm[r] = j;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int i = 0; i < m; ++i) {
-      int b = i;
-      for (int j = i + 1; j < m; ++j)
-        if (lam[perm[j]] < lam[perm[b]]) b = j;
-      const int t = perm[i];
-      perm[i] = perm[b];
-      perm[b] = t;
-    }
     for (int i = 0; i < m; ++i) lam_s[i] = lam[perm[i]];
     ctl->lam1 = lam[perm[0]];
     ctl->lam2 = m > 1 ? lam[perm[1]] : INFINITY;
@@ -316,12 +328,14 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
   }
 }
 
-// Smallest root of 1 + sum_j z_j^2 / (lam_j - mu) on (l1, min(l2, l1 + |z|^2)):
-// Newton steps on the secular function (increasing on the interval), kept
-// inside a bracket that shrinks with every evaluation, with a bisection
-// step whenever Newton leaves it; stops when the bracket has collapsed to
-// adjacent doubles or the step is below 4 ulp.  One warp; lane j holds
-// z_j and z_{j+32}.
+// Smallest root of 1 + sum_j z_j^2 / (lam_j - mu) (lam ascending): with
+// mu = l1 + tau and d_j = lam_j - l1 it is the root in (0, min(d_2, |z|^2)] of
+//   h(tau) = tau (1 + sum_{j>=2} z_j^2 / (d_j - tau)) - z_1^2,
+// which is increasing and has no pole at tau = 0 (the secular equation
+// multiplied by tau).  Start: the root of the quadratic model with the sum
+// expanded to first order in tau; then Newton steps on h kept inside a
+// shrinking bracket (bisection when a step leaves it), until the step is
+// below 2 ulp of tau.  One warp; lane j holds z_j and z_{j+32}.
 __device__ double secular_min_warp(const double* __restrict__ W, const double* __restrict__ lam,
                                    int m, const double* rb, double l1, double l2) {
   const int lane = threadIdx.x & 31;
@@ -333,37 +347,62 @@ __device__ double secular_min_warp(const double* __restrict__ W, const double* _
     for (int a = 0; a < m; ++a) z1 = fma(W[j1 * m + a], rb[a], z1);
   const double q0 = z0 * z0, q1 = z1 * z1;
   const double zz = warp_sum(q0 + q1);
-  if (m == 1) return l1 + __shfl_sync(0xffffffffu, q0, 0);
-  double lo = l1, hi = fmin(l2, l1 + zz);
-  if (!(hi > lo)) return hi;  // z1 = 0 or a double eigenvalue: lambda_1 stays
-  double mu = 0.5 * (lo + hi);
+  const double zf = __shfl_sync(0xffffffffu, q0, 0);  // z_1^2
+  if (m == 1) return l1 + zf;
+  // shifted poles of the other terms (lane 0's first slot is the pole itself)
+  const double d0 = lam[j0 < m ? j0 : 0] - l1, d1 = j1 < m ? lam[j1] - l1 : 0.0;
+  const double w0 = (j0 >= 1 && j0 < m) ? q0 : 0.0, w1 = j1 < m ? q1 : 0.0;
+  double hi = fmin(l2 - l1, zz), lo = 0.0;
+  if (!(hi > 0.0) || zf == 0.0) return l1;  // z_1 = 0 or a double eigenvalue
+  // quadratic model: S0 = sum w/d, S1 = sum w/d^2
+  double s0 = 0.0, s1 = 0.0;
+  if (w0 > 0.0) {
+    const double r = 1.0 / d0;
+    s0 = w0 * r;
+    s1 = w0 * r * r;
+  }
+  if (w1 > 0.0) {
+    const double r = 1.0 / d1;
+    s0 = s0 + w1 * r;
+    s1 = s1 + w1 * r * r;
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  const double bq = 1.0 + s0;
+  double tau = 2.0 * zf / (bq + sqrt(bq * bq + 4.0 * s1 * zf));
+  if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
   const double eps = 2.220446049250313e-16;
   for (int itr = 0; itr < 200; ++itr) {
-    double f = 0.0, df = 0.0;
-    if (j0 < m) {
-      const double r = 1.0 / (lam[j0] - mu);
-      f = q0 * r;
-      df = q0 * r * r;
+    double g = 0.0, dg = 0.0;
+    if (w0 > 0.0) {
+      const double r = 1.0 / (d0 - tau);
+      g = w0 * r;
+      dg = w0 * r * r;
     }
-    if (j1 < m) {
-      const double r = 1.0 / (lam[j1] - mu);
-      f = f + q1 * r;
-      df = df + q1 * r * r;
+    if (w1 > 0.0) {
+      const double r = 1.0 / (d1 - tau);
+      g = g + w1 * r;
+      dg = dg + w1 * r * r;
     }
-    f = 1.0 + warp_sum(f);
-    df = warp_sum(df);
-    if (f == 0.0) return mu;
-    if (f < 0.0)
-      lo = mu;
+    g = warp_sum(g);
+    dg = warp_sum(dg);
+    const double h = tau * (1.0 + g) - zf;
+    if (h == 0.0) break;
+    if (h < 0.0)
+      lo = tau;
     else
-      hi = mu;
-    if (hi - lo <= 2.0 * eps * fabs(hi)) return hi;
-    double nm = mu - f / df;
-    if (!(nm > lo && nm < hi)) nm = 0.5 * (lo + hi);
-    if (fabs(nm - mu) <= 2.0 * eps * fabs(mu)) return nm;
-    mu = nm;
+      hi = tau;
+    if (hi - lo <= 2.0 * eps * hi) {
+      tau = hi;
+      break;
+    }
+    double nt = tau - h / ((1.0 + g) + tau * dg);
+    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+    const bool done = fabs(nt - tau) <= 2.0 * eps * tau;
+    tau = nt;
+    if (done) break;
   }
-  return hi;
+  return l1 + tau;
 }
 
 // One warp per ordered row in [p0, p1) (p1 < 0: up to ctl->n_c).  With
@@ -627,14 +666,60 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
     if (lane == 0) z[j] = acc;
   }
   __syncthreads();
-  if (tid == 0) {
-    double rho = 0.0, dmax = 0.0;
-    for (int j = 0; j < m; ++j) {
-      rho = fma(z[j], z[j], rho);
-      dmax = fmax(dmax, fabs(ds[j]));
+  __shared__ int nonsmall[64], nns, anyclose;
+  __shared__ double tol_s, nz_s;
+  {
+    double r = 0.0, dm = 0.0;
+    for (int j = tid; j < m; j += blockDim.x) {
+      r = fma(z[j], z[j], r);
+      dm = fmax(dm, fabs(ds[j]));
     }
-    const double nz = sqrt(rho);
-    const double tol = 8.0 * 2.220446049250313e-16 * fmax(dmax, rho);
+    r = block_sum(r);
+    dm = block_max(dm);
+    if (tid == 0) {
+      nz_s = sqrt(r);
+      tol_s = 8.0 * 2.220446049250313e-16 * fmax(dm, r);
+      anyclose = 0;
+    }
+  }
+  __syncthreads();
+  const double tol = tol_s, nz = nz_s;
+  if (tid == 0) {  // integer work only: ordered list of non-negligible z
+    int c = 0;
+    for (int i = 0; i < m; ++i)
+      if (!(fabs(z[i]) * nz <= tol)) nonsmall[c++] = i;
+    nns = c;
+  }
+  __syncthreads();
+  for (int k = 1 + tid; k < nns; k += blockDim.x) {  // adjacent pairs, in parallel
+    const int ip = nonsmall[k - 1], i = nonsmall[k];
+    const double t = hypot(z[ip], z[i]);
+    const double c = z[i] / t, sn = z[ip] / t;
+    if (fabs(c * sn * (ds[i] - ds[ip])) <= tol) anyclose = 1;
+  }
+  __syncthreads();
+  if (!anyclose) {
+    // fast path: no rotation; K = the non-negligible entries, D = the rest
+    for (int k = tid; k < nns; k += blockDim.x) {
+      const int i = nonsmall[k];
+      wk->K[k] = i;
+      wk->dK[k] = ds[i];
+      wk->zK[k] = z[i];
+    }
+    if (tid == 0) {
+      int nD = 0;
+      for (int i = 0, k = 0; i < m; ++i) {
+        if (k < nns && nonsmall[k] == i) {
+          ++k;
+          continue;
+        }
+        wk->D[nD] = i;
+        wk->dD[nD++] = ds[i];
+      }
+      wk->nK = nns;
+      wk->nD = nD;
+    }
+  } else if (tid == 0) {
     int nK = 0, nD = 0, prev = -1;
     for (int i = 0; i < m; ++i) {
       if (fabs(z[i]) * nz <= tol) {
@@ -652,10 +737,10 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
         // fold z[prev] into z[i]; prev becomes an eigenpair
         const double dp = c * c * ds[prev] + sn * sn * ds[i];
         const double di = sn * sn * ds[prev] + c * c * ds[i];
-        for (int a = 0; a < m; ++a) {
-          const double wp = Ws[prev * m + a], wi = Ws[i * m + a];
-          Ws[prev * m + a] = c * wp - sn * wi;
-          Ws[i * m + a] = sn * wp + c * wi;
+        for (int a2 = 0; a2 < m; ++a2) {
+          const double wp = Ws[prev * m + a2], wi = Ws[i * m + a2];
+          Ws[prev * m + a2] = c * wp - sn * wi;
+          Ws[i * m + a2] = sn * wp + c * wi;
         }
         z[prev] = 0.0;
         z[i] = t;
@@ -722,19 +807,43 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   const double dorg = wk->dK[o];
   double del[2];
   for (int u = 0; u < 2; ++u) del[u] = dv[u] - dorg;
+  // f(tau) = 1 + sum_i z_i^2 / (del_i - tau), increasing between the poles:
+  // Newton steps kept inside a shrinking bracket (bisection when a step
+  // leaves it); the iterate itself is the result once the step is below
+  // 2 ulp or the bracket has collapsed.
+  double t = (o == j) ? 0.5 * hi : 0.5 * lo;
+  double tau = t;
+  const double eps = 2.220446049250313e-16;
   for (int it = 0; it < 400; ++it) {
-    const double t = 0.5 * (lo + hi);
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    tau = t;
     if (t <= lo || t >= hi) break;
-    double f = 0.0;
+    double f = 0.0, df = 0.0;
     for (int u = 0; u < 2; ++u)
-      if (lane + 32 * u < nK) f = f + z2[u] / (del[u] - t);
+      if (lane + 32 * u < nK) {
+        const double r = 1.0 / (del[u] - t);
+        f = f + z2[u] * r;
+        df = df + z2[u] * r * r;
+      }
     f = 1.0 + warp_sum(f);
+    df = warp_sum(df);
+    if (f == 0.0) break;
     if (f < 0.0)
       lo = t;
     else
       hi = t;
+    if (hi - lo <= 2.0 * eps * fmax(fabs(hi), fabs(lo))) {
+      tau = 0.5 * (lo + hi);
+      break;
+    }
+    double nt = t - f / df;
+    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+    if (fabs(nt - t) <= 2.0 * eps * fabs(t)) {
+      tau = nt;
+      break;
+    }
+    t = nt;
   }
-  const double tau = (o == j) ? hi : lo;  // the end nearer the interior
   for (int u = 0; u < 2; ++u) {
     const int i = lane + 32 * u;
     if (i < nK) Delta[i * 64 + j] = del[u] - tau;
@@ -784,28 +893,29 @@ __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restri
                            int m, double* __restrict__ d_out, double* __restrict__ W_out,
                            OdCtl* ctl) {
   __shared__ double lv[64];
+  __shared__ unsigned long long key[64];
   __shared__ int src[64];  // >= 0: new pair index; < 0: -(deflated idx)-1
   __shared__ int perm[64];
   const int tid = threadIdx.x;
+  const int nK = wk->nK, nD = wk->nD;
+  for (int j = tid; j < m; j += blockDim.x) {
+    if (j < nK) {
+      lv[j] = lamnew[j];
+      src[j] = j;
+    } else {
+      lv[j] = wk->dD[j - nK];
+      src[j] = -wk->D[j - nK] - 1;
+    }
+    key[j] = dkey(lv[j]);
+  }
+  __syncthreads();
+  for (int j = tid; j < m; j += blockDim.x) {  // rank = position in ascending order
+    int r = 0;
+    for (int i = 0; i < m; ++i) r += (key[i] < key[j]) || (key[i] == key[j] && i < j);
+    perm[r] = j;
+  }
+  __syncthreads();
   if (tid == 0) {
-    int n = 0;
-    for (int j = 0; j < wk->nK; ++j) {
-      lv[n] = lamnew[j];
-      src[n++] = j;
-    }
-    for (int j = 0; j < wk->nD; ++j) {
-      lv[n] = wk->dD[j];
-      src[n++] = -wk->D[j] - 1;
-    }
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int i = 0; i < m; ++i) {
-      int b = i;
-      for (int q = i + 1; q < m; ++q)
-        if (lv[perm[q]] < lv[perm[b]]) b = q;
-      const int t = perm[i];
-      perm[i] = perm[b];
-      perm[b] = t;
-    }
     ctl->lam1 = lv[perm[0]];
     ctl->lam2 = m > 1 ? lv[perm[1]] : INFINITY;
     ctl->lmax = lv[perm[m - 1]];
@@ -815,7 +925,7 @@ __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restri
     ctl->argmin = 0x7fffffff;
     ctl->n_c = 0;
   }
-  __syncthreads();
+  (void)nD;
   for (int i = tid; i < m; i += blockDim.x) d_out[i] = lv[perm[i]];
   for (int idx = tid; idx < m * m; idx += blockDim.x) {
     const int j = idx / m, a = idx % m;

@@ -578,6 +578,113 @@ __global__ void k_jacobi_round(const double* __restrict__ Ain, double* __restric
   if (tid == 0 && sn != 0.0) *rotated = 1;
 }
 
+// Grid barrier for a cooperative launch (all CTAs co-resident).  The spin is
+// bounded: after ~2^22 polls (about a second) the waiting CTA sets *err and
+// returns false, and every caller leaves the kernel.
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+};
+
+__device__ bool grid_sync_bounded(GridBar* bar, unsigned nblocks, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &bar->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nblocks - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned i = 0;
+      while (*vgen == g) {
+        if (++i > (1u << 22) || *((volatile int*)err)) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One full sweep (n - 1 rounds) of the multi-CTA Jacobi in one cooperative
+// launch; A ping-pongs between A0 and A1 every round (the result ends in A0
+// when n - 1 is even, else in A1).
+__global__ void k_jacobi_sweep(double* A0, double* A1, int n, double* __restrict__ V,
+                               double floor_abs, int* rotated, GridBar* bar, int* err) {
+  __shared__ double cs[2 * 128];
+  __shared__ double rp[128], rq[128];
+  const int half = n / 2, tid = threadIdx.x, nm1 = n - 1;
+  for (int r = 0; r < n - 1; ++r) {
+    const double* Ain = (r % 2 == 0) ? A0 : A1;
+    double* Aout = (r % 2 == 0) ? A1 : A0;
+    for (int b = tid; b < half; b += blockDim.x) {
+      int p, q;
+      rr_pair(n, r, b, p, q);
+      const double apq = __ldcg(Ain + p * n + q), app = __ldcg(Ain + p * n + p),
+                   aqq = __ldcg(Ain + q * n + q);
+      double c = 1.0, sn = 0.0;
+      if (fabs(apq) > floor_abs && fabs(apq) > 1e-14 * sqrt(fabs(app * aqq))) {
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        c = 1.0 / sqrt(1.0 + t * t);
+        sn = t * c;
+      }
+      cs[2 * b] = c;
+      cs[2 * b + 1] = sn;
+    }
+    __syncthreads();
+    int p, q;
+    rr_pair(n, r, blockIdx.x, p, q);
+    const double c = cs[2 * blockIdx.x], sn = cs[2 * blockIdx.x + 1];
+    for (int k = tid; k < n; k += blockDim.x) {
+      const double ap = __ldcg(Ain + p * n + k), aq = __ldcg(Ain + q * n + k);
+      rp[k] = c * ap - sn * aq;
+      rq[k] = sn * ap + c * aq;
+      if (sn != 0.0) {
+        const double vp = __ldcg(V + (int64_t)p * n + k), vq = __ldcg(V + (int64_t)q * n + k);
+        V[(int64_t)p * n + k] = c * vp - sn * vq;
+        V[(int64_t)q * n + k] = sn * vp + c * vq;
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += blockDim.x) {
+      int partner, b2;
+      if (k == nm1 || k == r) {
+        partner = k == nm1 ? r : nm1;
+        b2 = 0;
+      } else {
+        partner = ((2 * r - k) % nm1 + nm1) % nm1;
+        const int b1 = ((k - r) % nm1 + nm1) % nm1;
+        b2 = b1 <= half - 1 ? b1 : nm1 - b1;
+      }
+      const int p2 = k < partner ? k : partner, q2 = k < partner ? partner : k;
+      const double c2 = cs[2 * b2], s2 = cs[2 * b2 + 1];
+      double np_, nq_;
+      if (k == p2) {
+        np_ = c2 * rp[p2] - s2 * rp[q2];
+        nq_ = c2 * rq[p2] - s2 * rq[q2];
+      } else {
+        np_ = s2 * rp[p2] + c2 * rp[q2];
+        nq_ = s2 * rq[p2] + c2 * rq[q2];
+      }
+      Aout[p * n + k] = np_;
+      Aout[q * n + k] = nq_;
+    }
+    if (tid == 0 && sn != 0.0) *rotated = 1;
+    if (!grid_sync_bounded(bar, gridDim.x, err)) return;
+  }
+}
+
 __global__ void k_diag_max(const double* __restrict__ A, int n, double* out) {
   double mx = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(A[i * n + i]));
@@ -604,17 +711,28 @@ int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf
   cudaMemcpyAsync(host_scale, scale_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
   const double floor_abs = 1e-16 * host_scale[0];
+  // flag[0]: rotated in this sweep; flag[1]: barrier timeout; flag[2..3]: barrier
+  GridBar* bar = (GridBar*)(flag + 2);
+  int* err = flag + 1;
+  cudaMemsetAsync(flag, 0, 4 * sizeof(int), s);
   int sw = 0;
+  const int nb = n / 2;
   for (; sw < max_sweeps; ++sw) {
     cudaMemsetAsync(flag, 0, sizeof(int), s);
-    for (int r = 0; r < n - 1; ++r) {
-      k_jacobi_round<<<n / 2, 128, 0, HY_S(s)>>>(A0, A1, n, V, r, floor_abs, flag);
+    void* args[] = {(void*)&A0, (void*)&A1, (void*)&n, (void*)&V, (void*)&floor_abs,
+                    (void*)&flag, (void*)&bar, (void*)&err};
+    ::hy::count_launch();
+    if (cudaLaunchCooperativeKernel((void*)k_jacobi_sweep, dim3(nb), dim3(128), args, 0, s) !=
+        cudaSuccess)
+      return -1;
+    if ((n - 1) % 2 == 1) {  // the result of the last round is in A1
       double* t = A0;
       A0 = A1;
       A1 = t;
     }
-    cudaMemcpyAsync(host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(host_flag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    if (host_flag[1]) return -2;
     if (!host_flag[0]) break;
   }
   k_copy_diag<<<1, 128, 0, HY_S(s)>>>(A0, n, lam);
@@ -655,22 +773,22 @@ __global__ void k_pod_coeffs(const double* __restrict__ lam, const double* __res
                              int* m_eff_out, T* __restrict__ C) {
   __shared__ int perm[256];
   __shared__ double sg[256];
+  __shared__ unsigned long long key[256];
   __shared__ int me;
+  for (int i = threadIdx.x; i < w; i += blockDim.x) key[i] = dkey(lam[i]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {  // descending rank, ties by index
+    int r = 0;
+    for (int i = 0; i < w; ++i) r += (key[i] > key[j]) || (key[i] == key[j] && i < j);
+    perm[r] = j;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < w; i += blockDim.x) {
+    const double l = lam[perm[i]];
+    sg[i] = sqrt(l > 0.0 ? l : 0.0);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    // selection sort (n <= 256) over the w real eigenpairs, descending
-    for (int i = 0; i < w; ++i) perm[i] = i;
-    for (int i = 0; i < w; ++i) {
-      int b = i;
-      for (int j = i + 1; j < w; ++j)
-        if (lam[perm[j]] > lam[perm[b]]) b = j;
-      const int t = perm[i];
-      perm[i] = perm[b];
-      perm[b] = t;
-    }
-    for (int i = 0; i < w; ++i) {
-      const double l = lam[perm[i]];
-      sg[i] = sqrt(l > 0.0 ? l : 0.0);
-    }
     const double floor_abs = pod_abs * sqrt(*xraw2);
     int k = 0;
     for (int i = 0; i < m && i < w; ++i)
