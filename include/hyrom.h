@@ -141,7 +141,14 @@ enum {
   HYROM_T_ODEIM = 9,    /* ODEIM oversampling and the sampled pseudo-inverse */
   HYROM_T_MASKS = 10,   /* union / dilation / Neighbors (lines 26-28)      */
   HYROM_T_DEIM = 11,    /* DEIM points, the first m of ODEIM (line 25)     */
-  HYROM_NSTAGE = 12
+  /* parts of HYROM_T_DEIM / HYROM_T_ODEIM: */
+  HYROM_T_OD_INIT = 12,   /* row-norm buckets + first eigensystem          */
+  HYROM_T_OD_PROBE = 13,  /* exact scores of the largest-norm rows         */
+  HYROM_T_OD_SCREEN = 14, /* FP32 bound screen and its probe               */
+  HYROM_T_OD_EXACT = 15,  /* exact scores of the surviving rows            */
+  HYROM_T_OD_UPDATE = 16, /* rank-one eigensystem update                   */
+  HYROM_T_OD_PICK = 17,   /* tie-aware arg-max and commit                  */
+  HYROM_NSTAGE = 18
 };
 hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
 /* Work counters of the last ODEIM call (rebuild or stage entry point):

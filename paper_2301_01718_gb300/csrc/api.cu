@@ -103,10 +103,14 @@ struct hyrom_ctx {
   int* fail_dev = nullptr;
   // pinned host mirror for read-backs
   void* host = nullptr;
-  // optional per-stage CUDA-event timers (hyrom_profile)
+  // optional per-stage CUDA-event timers (hyrom_profile): up to kEvPairs
+  // intervals per stage between two synchronisations
+  static constexpr int kEvPairs = 160;
   int profile = 0;
-  cudaEvent_t ev_a[HYROM_NSTAGE] = {}, ev_b[HYROM_NSTAGE] = {};
-  int ev_pending[HYROM_NSTAGE] = {};
+  cudaEvent_t* ev_a[HYROM_NSTAGE] = {};
+  cudaEvent_t* ev_b[HYROM_NSTAGE] = {};
+  int ev_used[HYROM_NSTAGE] = {};
+  int ev_open[HYROM_NSTAGE] = {};
   double stage_ms[HYROM_NSTAGE] = {};
   int64_t stage_n[HYROM_NSTAGE] = {};
 };
@@ -219,32 +223,39 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
 
 // ---- stage timers: events on the context stream around each stage ----------
 void t_begin(hyrom_ctx* c, int id) {
-  if (c->profile) cudaEventRecord(c->ev_a[id], c->st);
+  if (!c->profile || c->ev_used[id] >= hyrom_ctx::kEvPairs) return;
+  cudaEventRecord(c->ev_a[id][c->ev_used[id]], c->st);
+  c->ev_open[id] = 1;
 }
 void t_end(hyrom_ctx* c, int id) {
-  if (!c->profile) return;
-  cudaEventRecord(c->ev_b[id], c->st);
-  c->ev_pending[id] = 1;
+  if (!c->profile || !c->ev_open[id]) return;
+  cudaEventRecord(c->ev_b[id][c->ev_used[id]], c->st);
+  c->ev_used[id] += 1;
+  c->ev_open[id] = 0;
 }
 // after a stream synchronisation: fold finished intervals into the totals
 void t_collect(hyrom_ctx* c) {
   if (!c->profile) return;
   for (int i = 0; i < HYROM_NSTAGE; ++i) {
-    if (!c->ev_pending[i]) continue;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev_a[i], c->ev_b[i]) == cudaSuccess) {
-      c->stage_ms[i] += ms;
-      c->stage_n[i] += 1;
+    for (int j = 0; j < c->ev_used[i]; ++j) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev_a[i][j], c->ev_b[i][j]) == cudaSuccess) {
+        c->stage_ms[i] += ms;
+        c->stage_n[i] += 1;
+      }
     }
-    c->ev_pending[i] = 0;
+    c->ev_used[i] = 0;
   }
 }
 
-// DEIM -> oversampling boundary inside the ODEIM launcher
-void odeim_mark(void* p, int) {
+// sub-stage marks from inside the ODEIM launcher: id >= 0 begins stage id,
+// id < 0 ends stage -id - 1
+void odeim_mark(void* p, int id) {
   hyrom_ctx* c = (hyrom_ctx*)p;
-  t_end(c, HYROM_T_DEIM);
-  t_begin(c, HYROM_T_ODEIM);
+  if (id >= 0)
+    t_begin(c, id);
+  else
+    t_end(c, -id - 1);
 }
 
 // ring slot of snapshot step j
@@ -726,8 +737,13 @@ void hyrom_destroy(hyrom_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host) cudaFreeHost(ctx->host);
   for (int i = 0; i < HYROM_NSTAGE; ++i) {
-    if (ctx->ev_a[i]) cudaEventDestroy(ctx->ev_a[i]);
-    if (ctx->ev_b[i]) cudaEventDestroy(ctx->ev_b[i]);
+    if (!ctx->ev_a[i]) continue;
+    for (int j = 0; j < hyrom_ctx::kEvPairs; ++j) {
+      cudaEventDestroy(ctx->ev_a[i][j]);
+      cudaEventDestroy(ctx->ev_b[i][j]);
+    }
+    delete[] ctx->ev_a[i];
+    delete[] ctx->ev_b[i];
   }
   delete ctx;
 }
@@ -742,15 +758,20 @@ hyrom_status hyrom_profile(hyrom_ctx* ctx, int on) {
   if (!ctx) return HYROM_EINVAL;
   if (on && !ctx->ev_a[0]) {
     for (int i = 0; i < HYROM_NSTAGE; ++i) {
-      CK(cudaEventCreate(&ctx->ev_a[i]));
-      CK(cudaEventCreate(&ctx->ev_b[i]));
+      ctx->ev_a[i] = new cudaEvent_t[hyrom_ctx::kEvPairs];
+      ctx->ev_b[i] = new cudaEvent_t[hyrom_ctx::kEvPairs];
+      for (int j = 0; j < hyrom_ctx::kEvPairs; ++j) {
+        CK(cudaEventCreate(&ctx->ev_a[i][j]));
+        CK(cudaEventCreate(&ctx->ev_b[i][j]));
+      }
     }
   }
   ctx->profile = on ? 1 : 0;
   for (int i = 0; i < HYROM_NSTAGE; ++i) {
     ctx->stage_ms[i] = 0.0;
     ctx->stage_n[i] = 0;
-    ctx->ev_pending[i] = 0;
+    ctx->ev_used[i] = 0;
+    ctx->ev_open[i] = 0;
   }
   return HYROM_OK;
 }

@@ -1035,6 +1035,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   if (m <= 0) return 0;
   if (np > N) np = (int)N;
   OdeimBufs o = carve(ws, N, m);
+  auto M_ = [&](int id) {
+    if (mark) mark(mark_arg, id);
+  };
+  M_(12);
   cudaMemsetAsync(o.ctl, 0, sizeof(OdCtl), s);
   cudaMemsetAsync(o.picked, 0, N, s);
   cudaMemsetAsync(o.bcnt, 0, (kNB + 1) * sizeof(int), s);
@@ -1045,6 +1049,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   k_bucket_scan<<<1, 32, 0, HY_S(s)>>>(o.bcnt, o.bstart, o.bcur);
   k_bucket_scatter<<<(int)blocks, 256, 0, HY_S(s)>>>(N, o.bkt, o.bcur, o.ord);
   const int probe = (int)(N < kProbe ? N : kProbe);
+  M_(-13);
   // DEIM
   for (int l = 0; l < m; ++l) {
     k_deim_solve<T><<<1, 32, 0, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
@@ -1057,7 +1062,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
     if (l + 1 < m) k_deim_extend<T><<<1, 32, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
   }
-  if (mark) mark(mark_arg, 1);
+  if (mark) {  // DEIM ends, oversampling begins
+    mark(mark_arg, -12);
+    mark(mark_arg, 9);
+  }
   if (np <= m) return 0;
   // ODEIM oversampling
   const int n = m % 2 ? m + 1 : m;  // Jacobi wants an even order
@@ -1065,25 +1073,36 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   const size_t smem = sizeof(double) * ((size_t)m * m + 64 + 64 * 8);
   cudaFuncSetAttribute(k_odeim_score<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_odeim_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  M_(12);
   k_pad_sym2<<<1, 256, 0, HY_S(s)>>>(o.M, m, n, o.Mp);
   if (run_jacobi_multi(o.Mp, n, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, o.jscale,
                        (double*)host_pinned + 1, 60, s) < 0)
     return -1;
   k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl);
+  M_(-13);
   for (int l = m; l < np; ++l) {
+    M_(13);
     k_odeim_score<T><<<(probe + 7) / 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord,
                                                         o.picked, 0, probe, 0, tie_tol, o.ctl,
                                                         o.scores);
     k_odeim_plan<<<1, 1, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
+    M_(-14);
+    M_(14);
     k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord,
                                                     o.picked, probe, o.ctl, o.scores);
     k_odeim_probe_best<T><<<1, 64, 0, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl,
                                                  o.scores);
+    M_(-15);
+    M_(15);
     k_odeim_exact<T><<<152 * 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, probe,
                                                       tie_tol, o.ctl, o.scores);
+    M_(-16);
+    M_(17);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
+    M_(-18);
     if (l + 1 < np) {
+      M_(16);
       k_r1_prepare<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
       k_r1_roots<<<m, 32, 0, HY_S(s)>>>(o.r1, o.Delta);
       k_r1_vectors<<<m, 64, 0, HY_S(s)>>>(o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
@@ -1091,6 +1110,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                                          o.ctl);
       std::swap(o.lam_s, o.lam_s2);
       std::swap(o.W_s, o.W_s2);
+      M_(-17);
     }
   }
   return 0;

@@ -178,7 +178,8 @@ def hyrom_kernel_launches():
 
 
 STAGES = ["full", "partial", "gappy", "recon", "filter", "select", "gram", "eig", "formphi",
-          "odeim", "masks", "deim"]
+          "odeim", "masks", "deim", "od_init", "od_probe", "od_screen", "od_exact",
+          "od_update", "od_pick"]
 
 
 def hyrom_profile(ctx, on=True):
@@ -292,3 +293,4 @@ def hyrom_stage_masks(ctx, g_bitmap, points, n_p, s_hat, s_tilde):
     _check(ctx, lib().hyrom_stage_masks(ctx, _ptr(g_bitmap), _ptr(points), int(n_p), _ptr(s_hat),
                                         _ptr(s_tilde), C.byref(n)))
     return n.value
+
