@@ -257,6 +257,41 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
 hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
                                int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
 
+/* ---- allocation-free variant ---------------------------------------------
+ * hyrom_gappy_static: the gappy reduced coordinates of hyrom_stage_gappy,
+ * y = (P^T Phi)^+ P^T (v - psi) (Algorithm 1, the gappy least-squares step),
+ * for callers that cannot allocate device memory: host applications that
+ * budget all device memory up front and pass only pointers into their own
+ * pools, plugins that must not use the CUDA allocator of the program that
+ * loads them, and time-critical loops where cudaMalloc / cudaFree would add
+ * an implicit device synchronisation.  It needs no context and never calls
+ * cudaMalloc, cudaFree or an allocating library routine.  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ *   phi: ndof x m (column-major), points: n_p dof rows in [0, ndof) (not
+ *   checked: the caller guarantees the range), v, psi: ndof values; all
+ *   device arrays of `precision` (HYROM_PREC_F64 -> double, HYROM_PREC_F32
+ *   -> float) except points (int32).  y_out: m doubles on the device.  Work is
+ *   enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *   the call does not synchronise.  A rank-deficient P^T Phi gives
+ *   non-finite y, as hyrom_stage_gappy does.
+ *   err, err_len: optional caller buffer (may be NULL / 0) that receives a
+ *   NUL-terminated reason on failure and an empty string on success.
+ * Limits: 1 <= m <= 64 and m <= n_p <= min(128, ndof); other sizes return
+ * HYROM_EINVAL before any work is enqueued.
+ * Scratch: file-scope device arrays of 64 x 128 doubles plus a counter
+ * (about 64 KB), present on every GPU that loads the library until the
+ * process exits.  Each call clears the counter itself on `stream`; the
+ * pseudo-inverse is written in full before it is read, so nothing needs to
+ * start at zero.  Every call on a device shares this scratch: calls whose
+ * work can overlap on the GPU (different streams without ordering between
+ * them) race on it and must be serialised by the caller.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the scratch's device address with cudaGetSymbolAddress; make that first
+ * call before any stream capture on that device. */
+hyrom_status hyrom_gappy_static(const void* phi, int64_t ndof, int32_t m, const int32_t* points,
+                                int32_t n_p, const void* v, const void* psi, int32_t precision,
+                                double* y_out, void* stream, char* err, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

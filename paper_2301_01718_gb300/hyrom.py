@@ -132,6 +132,7 @@ def lib():
         "hyrom_stage_pod": (st, [vp, vp, i32, vp, vp, vp, C.POINTER(i32)]),
         "hyrom_stage_odeim": (st, [vp, vp, i32, i32, vp]),
         "hyrom_stage_masks": (st, [vp, vp, vp, i32, vp, vp, C.POINTER(i32)]),
+        "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -294,3 +295,13 @@ def hyrom_stage_masks(ctx, g_bitmap, points, n_p, s_hat, s_tilde):
                                         _ptr(s_tilde), C.byref(n)))
     return n.value
 
+
+def hyrom_gappy_static(phi, ndof, m, points, n_p, v, psi, precision, y_out, stream=None):
+    """Allocation-free gappy coordinates: no context, scratch in a static
+    device array.  Raises HyromError with the library's reason on failure."""
+    err = C.create_string_buffer(256)
+    s = lib().hyrom_gappy_static(_ptr(phi), int(ndof), int(m), _ptr(points), int(n_p), _ptr(v),
+                                 _ptr(psi), int(precision), _ptr(y_out), _ptr(stream), err,
+                                 len(err))
+    if s != HYROM_OK:
+        raise HyromError(s, err.value.decode())
