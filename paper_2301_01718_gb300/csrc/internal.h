@@ -71,8 +71,6 @@ void launch_gram_center_explicit(const double* H, int nslot, const int* win, int
 template <typename T>
 void launch_dots(const T* a, const T* ring, int64_t N, int nslot, double* part, int max_chunks,
                  double* out, cudaStream_t st);
-void launch_jacobi_sym(const double* A, int n, double* V, double* lam, int max_sweeps,
-                       int* sweeps_out, int warm, cudaStream_t s);
 template <typename T>
 void launch_pod_coeffs(const double* lam, const double* V, int n, int w, int m, double pod_tol,
                        double pod_abs, const double* xraw2, double* sig_out, int* m_eff_out,
@@ -118,7 +116,5 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                  void* mark_arg = nullptr);
 size_t odeim_ws_bytes(int64_t N, int m);
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
-void launch_jacobi_padded(const double* M, int m, int n, double* V, double* lam, double* pad,
-                          cudaStream_t s);
 
 }  // namespace hy

@@ -30,6 +30,7 @@ namespace hy {
 
 constexpr int kNB = 256;       // norm buckets
 constexpr int kProbe = 2048;   // rows scored before the bound is applied
+constexpr int kLdw = 65;       // odd leading dimension of W in shared memory
 
 struct OdCtl {
   unsigned long long smax;  // bits of the best score so far (>= 0)
@@ -37,10 +38,11 @@ struct OdCtl {
   int n_c;                  // ordered rows to score
   double cn2;               // 1 + |c|^2            (DEIM)
   double lam1, lam2, lmax;  // eigenvalues of M (ODEIM)
-  unsigned long long lbest;  // packed (heuristic score bits, position) (ODEIM)
+  int n_list;                // rows passed on by the z_1 filter (ODEIM)
+  int pad_;
   unsigned long long ubest;  // packed (upper bound bits, position) (ODEIM)
-  // counters over one ODEIM call: DEIM rows scored, ODEIM rows screened,
-  // ODEIM exact scores, greedy steps
+  // counters over one ODEIM call: DEIM rows scored, ODEIM rows given the
+  // full FP32 bound, ODEIM exact scores, greedy steps
   unsigned long long stat[4];
 };
 
@@ -141,27 +143,54 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
                              const int* __restrict__ pts, const double* __restrict__ Lf,
                              const double* __restrict__ Uf, double* __restrict__ yv,
                              double* __restrict__ cvec, OdCtl* ctl) {
-  __shared__ double y[64], c[64];
+  // L and U transposed into shared memory (stride 65: conflict-free), so
+  // that both solves run column by column: after x_i is known every lane
+  // updates its two right-hand-side entries (j = lane, lane + 32).
+  extern __shared__ double dsm[];
+  double* Lt = dsm;            // Lt[i * 65 + j] = L[j][i]
+  double* Ut = dsm + 64 * 65;  // Ut[i * 65 + j] = U[j][i]
   const int lane = threadIdx.x;
-  for (int i = 0; i < l; ++i) {  // forward: L y = b
-    double acc = 0.0;
-    for (int j = lane; j < i; j += 32) acc = fma(Lf[i * 64 + j], y[j], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) y[i] = (double)phi[(int64_t)l * N + pts[i]] - acc;
-    __syncwarp();
+  for (int r = 0; r < l; ++r)
+    for (int c = lane; c < l; c += 32) {
+      Lt[c * 65 + r] = Lf[r * 64 + c];
+      Ut[c * 65 + r] = Uf[r * 64 + c];
+    }
+  double b0 = 0.0, b1 = 0.0;  // right-hand side, entries lane and lane + 32
+  if (lane < l) b0 = (double)phi[(int64_t)l * N + pts[lane]];
+  if (lane + 32 < l) b1 = (double)phi[(int64_t)l * N + pts[lane + 32]];
+  __syncwarp();
+  // forward: L y = b (unit diagonal)
+  for (int i = 0; i < l; ++i) {
+    const double yi = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31);
+    const double* col = Lt + i * 65;
+    if (lane > i && lane < l) b0 = b0 - col[lane] * yi;
+    if (lane + 32 > i && lane + 32 < l) b1 = b1 - col[lane + 32] * yi;
   }
-  for (int i = l - 1; i >= 0; --i) {  // backward: U c = y
-    double acc = 0.0;
-    for (int j = i + 1 + lane; j < l; j += 32) acc = fma(Uf[i * 64 + j], c[j], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) c[i] = (y[i] - acc) / Uf[i * 64 + i];
-    __syncwarp();
+  const double y0 = b0, y1 = b1;
+  // backward: U c = y
+  for (int i = l - 1; i >= 0; --i) {
+    const double ui = Ut[i * 65 + i];
+    const double ci = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31) / ui;
+    if (lane == (i & 31)) {
+      if (i < 32)
+        b0 = ci;
+      else
+        b1 = ci;
+    }
+    const double* col = Ut + i * 65;
+    if (lane < i) b0 = b0 - col[lane] * ci;
+    if (lane + 32 < i) b1 = b1 - col[lane + 32] * ci;
   }
   double cn = 0.0;
-  for (int j = lane; j < l; j += 32) {
-    cvec[j] = c[j];
-    yv[j] = y[j];
-    cn = fma(c[j], c[j], cn);
+  if (lane < l) {
+    cvec[lane] = b0;
+    yv[lane] = y0;
+    cn = b0 * b0;
+  }
+  if (lane + 32 < l) {
+    cvec[lane + 32] = b1;
+    yv[lane + 32] = y1;
+    cn = fma(b1, b1, cn);
   }
   cn = warp_sum(cn);
   if (lane == 0) {
@@ -178,26 +207,44 @@ template <typename T>
 __global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const OdCtl* ctl,
                               double* __restrict__ Lf, double* __restrict__ Uf,
                               const double* __restrict__ yv) {
-  __shared__ double ell[64];
+  // column-oriented solve of U^T ell = a with U^T's columns = U's rows
+  __shared__ double Us[64 * 64];
   const int lane = threadIdx.x;
   const int p = ctl->argmin;
-  for (int j = 0; j < l; ++j) {  // forward with U^T: ell_j U_jj = a_j - sum_{i<j} U_ij ell_i
-    double acc = 0.0;
-    for (int i = lane; i < j; i += 32) acc = fma(Uf[i * 64 + j], ell[i], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) ell[j] = ((double)phi[(int64_t)j * N + p] - acc) / Uf[j * 64 + j];
-    __syncwarp();
+  for (int r = 0; r < l; ++r)
+    for (int c = lane; c < l; c += 32) Us[r * 64 + c] = Uf[r * 64 + c];
+  double a0 = 0.0, a1 = 0.0;
+  if (lane < l) a0 = (double)phi[(int64_t)lane * N + p];
+  if (lane + 32 < l) a1 = (double)phi[(int64_t)(lane + 32) * N + p];
+  const double pl = (double)phi[(int64_t)l * N + p];
+  __syncwarp();
+  for (int j = 0; j < l; ++j) {  // ell_j = (a_j - sum_{i<j} U_ij ell_i) / U_jj
+    const double ej = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31) / Us[j * 64 + j];
+    if (lane == (j & 31)) {
+      if (j < 32)
+        a0 = ej;
+      else
+        a1 = ej;
+    }
+    const double* row = Us + j * 64;
+    if (lane > j && lane < l) a0 = a0 - row[lane] * ej;
+    if (lane + 32 > j && lane + 32 < l) a1 = a1 - row[lane + 32] * ej;
   }
   double dot = 0.0;
-  for (int j = lane; j < l; j += 32) {
-    Lf[l * 64 + j] = ell[j];
-    Uf[j * 64 + l] = yv[j];
-    dot = fma(ell[j], yv[j], dot);
+  if (lane < l) {
+    Lf[l * 64 + lane] = a0;
+    Uf[lane * 64 + l] = yv[lane];
+    dot = a0 * yv[lane];
+  }
+  if (lane + 32 < l) {
+    Lf[l * 64 + lane + 32] = a1;
+    Uf[(lane + 32) * 64 + l] = yv[lane + 32];
+    dot = fma(a1, yv[lane + 32], dot);
   }
   dot = warp_sum(dot);
   if (lane == 0) {
     Lf[l * 64 + l] = 1.0;
-    Uf[l * 64 + l] = (double)phi[(int64_t)l * N + p] - dot;
+    Uf[l * 64 + l] = pl - dot;
   }
 }
 
@@ -228,18 +275,32 @@ __global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
   if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(best));
 }
 
-__global__ void k_deim_plan(OdCtl* ctl,
-                            const unsigned int* __restrict__ bmax, const int* __restrict__ bstart,
-                            int probe_end, double tie_tol) {
+// one thread per bucket: the last non-empty bucket whose largest squared
+// norm reaches tau bounds the rows still to score
+__device__ void plan_rows(OdCtl* ctl, const unsigned int* __restrict__ bmax,
+                          const int* __restrict__ bstart, int probe_end, double tau) {
+  int blast = -1;
+  for (int b = threadIdx.x; b < kNB; b += blockDim.x)
+    if (bstart[b + 1] > bstart[b] && (double)__uint_as_float(bmax[b]) >= tau) blast = b;
+  __shared__ int red[32];
+  for (int o = 16; o > 0; o >>= 1) blast = max(blast, __shfl_xor_sync(0xffffffffu, blast, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = blast;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) blast = max(blast, red[w]);
+    blast = max(blast, red[0]);
+    const int n = blast >= 0 ? bstart[blast + 1] : 0;
+    ctl->n_c = n > probe_end ? n : probe_end;
+  }
+}
+
+// DEIM: |r_i| <= |phi_i| sqrt(1 + |c|^2), so rows need |phi_i|^2 >= lim^2 / cn2
+__global__ void k_deim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
+                            const int* __restrict__ bstart, int probe_end, double tie_tol) {
   const double s = bitsd(ctl->smax);
   const double lim = s * (1.0 - 2.0 * tie_tol);
-  const double tau = lim * lim / (ctl->cn2 * (1.0 + 1e-5));
-  int blast = -1;
-  for (int b = 0; b < kNB; ++b)
-    if (bstart[b + 1] > bstart[b] && (double)__uint_as_float(bmax[b]) >= tau) blast = b;
-  int n = blast >= 0 ? bstart[blast + 1] : 0;
-  ctl->n_c = n > probe_end ? n : probe_end;
-  ctl->stat[0] += (unsigned long long)(ctl->n_c - probe_end);
+  plan_rows(ctl, bmax, bstart, probe_end, lim * lim / (ctl->cn2 * (1.0 + 1e-5)));
+  if (threadIdx.x == 0) ctl->stat[0] += (unsigned long long)(ctl->n_c - probe_end);
 }
 
 // lowest row among the scored rows within the tie window of the best
@@ -316,7 +377,7 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
     ctl->lam2 = m > 1 ? lam[perm[1]] : INFINITY;
     ctl->lmax = lam[perm[m - 1]];
     ctl->smax = 0ull;
-    ctl->lbest = 0ull;
+    ctl->n_list = 0;
     ctl->ubest = 0ull;
     ctl->argmin = 0x7fffffff;
     ctl->n_c = 0;
@@ -330,21 +391,30 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
 
 // Smallest root of 1 + sum_j z_j^2 / (lam_j - mu) (lam ascending): with
 // mu = l1 + tau and d_j = lam_j - l1 it is the root in (0, min(d_2, |z|^2)] of
-//   h(tau) = tau (1 + sum_{j>=2} z_j^2 / (d_j - tau)) - z_1^2,
+//   h(tau) = tau (1 + g(tau)) - z_1^2,   g(tau) = sum_{j>=2} z_j^2 / (d_j - tau),
 // which is increasing and has no pole at tau = 0 (the secular equation
-// multiplied by tau).  Start: the root of the quadratic model with the sum
-// expanded to first order in tau; then Newton steps on h kept inside a
-// shrinking bracket (bisection when a step leaves it), until the step is
-// below 2 ulp of tau.  One warp; lane j holds z_j and z_{j+32}.
-__device__ double secular_min_warp(const double* __restrict__ W, const double* __restrict__ lam,
-                                   int m, const double* rb, double l1, double l2) {
+// multiplied by tau).  Each step solves the two-pole model of the secular
+// equation: the pole at 0 exactly, and g replaced by a + b / (d_2 - tau)
+// with a and b matching g and g' at the current iterate (the "middle way"
+// of Li's secular-equation solver, as in LAPACK's dlaed4); the model's
+// smaller root is
+//   tau' = 2 z_1^2 d_2 / (B + sqrt(B^2 - 4 C z_1^2 d_2)),
+//   C = 1 + a,  B = C d_2 + z_1^2 + b.
+// The first step is taken from tau = 0 (so it lies in (0, d_2)); later
+// steps are kept inside a shrinking bracket (bisection otherwise).  Stop
+// when |h| is within the rounding error of its evaluation, the step is below
+// 2 ulp, or the bracket has collapsed.  One warp; lane j holds z_j and
+// z_{j+32}.
+__device__ double secular_min_warp(const double* __restrict__ W, int ldw,
+                                   const double* __restrict__ lam, int m, const double* rb,
+                                   double l1, double l2) {
   const int lane = threadIdx.x & 31;
   double z0 = 0.0, z1 = 0.0;
   const int j0 = lane, j1 = lane + 32;
   if (j0 < m)
-    for (int a = 0; a < m; ++a) z0 = fma(W[j0 * m + a], rb[a], z0);
+    for (int a = 0; a < m; ++a) z0 = fma(W[j0 * ldw + a], rb[a], z0);
   if (j1 < m)
-    for (int a = 0; a < m; ++a) z1 = fma(W[j1 * m + a], rb[a], z1);
+    for (int a = 0; a < m; ++a) z1 = fma(W[j1 * ldw + a], rb[a], z1);
   const double q0 = z0 * z0, q1 = z1 * z1;
   const double zz = warp_sum(q0 + q1);
   const double zf = __shfl_sync(0xffffffffu, q0, 0);  // z_1^2
@@ -352,28 +422,16 @@ __device__ double secular_min_warp(const double* __restrict__ W, const double* _
   // shifted poles of the other terms (lane 0's first slot is the pole itself)
   const double d0 = lam[j0 < m ? j0 : 0] - l1, d1 = j1 < m ? lam[j1] - l1 : 0.0;
   const double w0 = (j0 >= 1 && j0 < m) ? q0 : 0.0, w1 = j1 < m ? q1 : 0.0;
-  double hi = fmin(l2 - l1, zz), lo = 0.0;
+  const double d2 = l2 - l1;
+  double hi = fmin(d2, zz), lo = 0.0;
   if (!(hi > 0.0) || zf == 0.0) return l1;  // z_1 = 0 or a double eigenvalue
-  // quadratic model: S0 = sum w/d, S1 = sum w/d^2
-  double s0 = 0.0, s1 = 0.0;
-  if (w0 > 0.0) {
-    const double r = 1.0 / d0;
-    s0 = w0 * r;
-    s1 = w0 * r * r;
-  }
-  if (w1 > 0.0) {
-    const double r = 1.0 / d1;
-    s0 = s0 + w1 * r;
-    s1 = s1 + w1 * r * r;
-  }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  const double bq = 1.0 + s0;
-  double tau = 2.0 * zf / (bq + sqrt(bq * bq + 4.0 * s1 * zf));
-  if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
   const double eps = 2.220446049250313e-16;
-  for (int itr = 0; itr < 200; ++itr) {
-    double g = 0.0, dg = 0.0;
+  double tau = 0.0, g = 0.0, dg = 0.0;
+  for (int itr = 0; itr < 100; ++itr) {
+    if (itr > 0) {
+      g = 0.0;
+      dg = 0.0;
+    }
     if (w0 > 0.0) {
       const double r = 1.0 / (d0 - tau);
       g = w0 * r;
@@ -386,200 +444,261 @@ __device__ double secular_min_warp(const double* __restrict__ W, const double* _
     }
     g = warp_sum(g);
     dg = warp_sum(dg);
-    const double h = tau * (1.0 + g) - zf;
-    if (h == 0.0) break;
-    if (h < 0.0)
-      lo = tau;
-    else
-      hi = tau;
-    if (hi - lo <= 2.0 * eps * hi) {
-      tau = hi;
+    if (itr > 0) {
+      const double h = tau * (1.0 + g) - zf;
+      if (fabs(h) <= 16.0 * eps * (tau * (1.0 + g) + zf)) break;
+      if (h < 0.0)
+        lo = tau;
+      else
+        hi = tau;
+      if (hi - lo <= 2.0 * eps * hi) {
+        tau = hi;
+        break;
+      }
+    }
+    const double gap = d2 - tau;
+    const double C = 1.0 + (g - dg * gap);
+    const double B = C * d2 + zf + dg * gap * gap;
+    const double nt = 2.0 * zf * d2 / (B + sqrt(fmax(B * B - 4.0 * C * zf * d2, 0.0)));
+    if (itr > 0 && fabs(nt - tau) <= 2.0 * eps * tau) {
+      tau = nt;
       break;
     }
-    double nt = tau - h / ((1.0 + g) + tau * dg);
-    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
-    const bool done = fabs(nt - tau) <= 2.0 * eps * tau;
-    tau = nt;
-    if (done) break;
+    tau = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
   }
   return l1 + tau;
 }
 
-// One warp per ordered row in [p0, p1) (p1 < 0: up to ctl->n_c).  With
-// `prune`, rows whose Rayleigh bound cannot reach lim = smax (1 - 2 tie)
-// are skipped (smax read at kernel start).  Lane j holds z_j and z_{j+32}.
+// ---- ODEIM scoring: certified FP32 bounds, then exact FP64 scores ---------
+//
+// With z = W^T phi, d_j = l_j - l1 and mu = l1 + tau, tau is the root in
+// [0, d_2) of the increasing function
+//   h(tau) = tau (1 + sum_{j>=2} z_j^2 / (d_j - tau)) - z_1^2,
+// so tau <= z_1^2 and tau <= d_2 (interlacing).  FP32 dot products of m <= 64
+// terms on operands rounded to FP32 are within dl = 8e-6 |phi| of the exact
+// components ((m + 2) 2^-24 |W_j| |phi| = 3.9e-6 |phi|; the factor 2 covers
+// the rounding of the stored norm), so with b1 = |z~_1| + dl and
+// a_j = max(|z~_j| - dl, 0) the function
+//   h_L(t) = t (1 + sum_{j>=2} a_j^2 / (d_j - t)) - b1^2  <=  h(t),
+// and h_L(t) >= 0 proves tau <= t.  Every bound below is evaluated with
+// directed rounding, so it stays an upper bound of the exact score.
+
+// Stage 1, one thread per ordered row in [p0, ctl->n_c): the bound
+// U1 = min(l1 + b1^2, l2) from z_1 alone (one m-term dot product).  Rows
+// with U1 >= lim = smax (1 - 2 tie) are appended to `list` for stage 2.
 template <typename T>
-__global__ void k_odeim_score(const T* __restrict__ phi, int64_t N, int m,
-                              const double* __restrict__ lam_s, const double* __restrict__ W_s,
-                              const int* __restrict__ ord, const unsigned char* __restrict__ picked,
-                              int p0, int p1, int prune, double tie_tol, OdCtl* ctl,
-                              double* __restrict__ scores) {
-  extern __shared__ double sh[];
-  double* W = sh;             // m x m column-major (column j = eigenvector j)
-  double* lam = W + m * m;    // m
-  double* rowbuf = lam + 64;  // per warp: 64
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) W[i] = W_s[i];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = lam_s[i];
+__global__ void __launch_bounds__(256) k_odeim_z1(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
+    double* __restrict__ scores, int* __restrict__ list) {
+  __shared__ float w1[64];
+  for (int a = threadIdx.x; a < 64; a += blockDim.x) w1[a] = a < m ? (float)W_s[a] : 0.f;
   __syncthreads();
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  const int end = p1 >= 0 ? p1 : ctl->n_c;
-  double* rb = rowbuf + 64 * wid;
-  double best = 0.0;
-  for (int pos = p0 + blockIdx.x * nw + wid; pos < end; pos += gridDim.x * nw) {
-    const int i = ord[pos];
-    double sc = -1.0;
-    if (!picked[i]) {
-      for (int a = lane; a < m; a += 32) rb[a] = (double)phi[(int64_t)a * N + i];
-      __syncwarp();
-      bool skip = false;
-      if (prune) {
-        // z_1 = w_1 . phi: Rayleigh-quotient and interlacing upper bound
-        double d = 0.0;
-        for (int a = lane; a < m; a += 32) d = fma(W[a], rb[a], d);
-        d = warp_sum(d);
-        const double ub = fmin(l2, l1 + d * d);
-        skip = ub * (1.0 + 1e-12) < lim;
+  const int end = ctl->n_c;
+  const int lane = threadIdx.x & 31;
+  for (int base = p0 + blockIdx.x * blockDim.x; base < end; base += gridDim.x * blockDim.x) {
+    const int pos = base + threadIdx.x;
+    bool pass = false;
+    if (pos < end) {
+      const int i = ord[pos];
+      double U = -1.0;
+      if (!picked[i]) {
+        float z1 = 0.f;
+#pragma unroll 16
+        for (int a = 0; a < m; ++a) z1 = fmaf(w1[a], (float)phi[(int64_t)a * N + i], z1);
+        const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
+        const float b1 = __fadd_ru(fabsf(z1), dl);
+        U = fmin(__dadd_ru(l1, (double)__fmul_ru(b1, b1)), l2);
+        pass = U >= lim;
       }
-      if (!skip) {
-        sc = secular_min_warp(W, lam, m, rb, l1, l2);
-        best = sc > best ? sc : best;
-      }
-      __syncwarp();
+      scores[pos] = U;
     }
-    if (lane == 0) scores[pos] = sc;
+    // warp-aggregated append
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (bal) {
+      int first = 0;
+      if (lane == 0) first = atomicAdd(&ctl->n_list, __popc(bal));
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (pass) list[first + __popc(bal & ((1u << lane) - 1u))] = pos;
+    }
   }
-  best = block_max(best);
-  if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(best));
 }
 
-// FP32 screen of the ordered rows [p0, ctl->n_c): a rigorous upper bound U
-// of lambda_min(M + phi phi^T) into scores[pos] (-1 for picked rows), and
-// the rows with the largest upper bound and the largest heuristic lower bound
-// (the 2x2 bound of the cited ODEIM construction) packed into ctl->ubest /
-// ctl->lbest for the exact probe.  With z = W^T phi and mu the root,
-//   z1^2/(mu - l1) = 1 + sum_{j>=2} z_j^2/(l_j - mu)
-//                 >= 1 + sum_{2<=j<=KS} z_j^2/(l_j - l1) + rest/(lmax - l1) =: c
-// (l1 <= mu <= l_j), so mu <= l1 + z1^2 / c; also mu <= l2.  The KS leading
-// z_j are FP32 dot products with |error| <= d = 8e-6 |phi| (m <= 64): z1 is
-// rounded up, the others and |phi|^2 down, so the bound stays an upper bound.
-constexpr int KS = 8;
+// Stage 2, one warp per row (rows [p0, p1) of the order, or with list !=
+// NULL the ctl->n_list positions in list): the bound from all m components,
+// lane j holding z_j and z_{j+32}.  The root of h_L is approached with the
+// two-pole model steps of secular_min_warp in FP32 (first step from t = 0)
+// until |h_L| is at its rounding level; h_L(t') >= 0 is then checked, in
+// directed rounding, at t' slightly above the iterate.  Rows whose check
+// fails keep U = min(U1, l2).  The row with the largest bound is packed into
+// ctl->ubest for the exact probe.
+HY_DEV float warp_sum_rd(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
 template <typename T>
-__global__ void k_odeim_screen(const T* __restrict__ phi, int64_t N, int m,
-                               const double* __restrict__ W_s, const double* __restrict__ lam_s,
-                               const float* __restrict__ nrm, const int* __restrict__ ord,
-                               const unsigned char* __restrict__ picked, int p0, OdCtl* ctl,
-                               double* __restrict__ scores) {
-  __shared__ float wk[KS][64];
-  __shared__ double inv[KS];
-  const int ks = m < KS ? m : KS;
-  const double l1 = ctl->lam1, l2 = ctl->lam2, lm = ctl->lmax;
-  for (int i = threadIdx.x; i < KS * 64; i += blockDim.x) {
-    const int j = i / 64, a = i % 64;
-    wk[j][a] = (j < ks && a < m) ? (float)W_s[j * m + a] : 0.f;
+__global__ void __launch_bounds__(256) k_odeim_screen(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
+    const double* __restrict__ lam_s, const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int p0, int p1, const int* __restrict__ list,
+    OdCtl* ctl, double* __restrict__ scores) {
+  __shared__ float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
+  __shared__ float dn[64], du[64];
+  __shared__ float ph[8][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double l1 = ctl->lam1, l2 = ctl->lam2;
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+    const int a = i >> 6, j = i & 63;
+    Wt[a][j] = (a < m && j < m) ? (float)W_s[j * m + a] : 0.f;
   }
-  for (int j = threadIdx.x; j < KS; j += blockDim.x)
-    inv[j] = (j >= 1 && j < ks && lam_s[j] > l1) ? 1.0 / (lam_s[j] - l1) : 0.0;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    if (j >= 1 && j < m) {
+      dn[j] = (float)(lam_s[j] - l1);
+      du[j] = __double2float_ru(__dsub_ru(lam_s[j], l1));
+    } else {  // j = 0 carries z_1 itself; j >= m is padding
+      dn[j] = INFINITY;
+      du[j] = INFINITY;
+    }
+  }
   __syncthreads();
-  const double invm = lm > l1 ? 1.0 / (lm - l1) : 0.0;
-  const int end = ctl->n_c;
-  unsigned long long bestL = 0ull, bestU = 0ull, cnt = 0;
-  for (int pos = p0 + blockIdx.x * blockDim.x + threadIdx.x; pos < end;
-       pos += gridDim.x * blockDim.x) {
+  const float d2n = m > 1 ? dn[1] : INFINITY, d2u = m > 1 ? du[1] : INFINITY;
+  const float dn0 = dn[lane], dn1 = dn[lane + 32], du0 = du[lane], du1 = du[lane + 32];
+  const int count = list ? ctl->n_list : (p1 >= 0 ? p1 : ctl->n_c) - p0;
+  float* pr = ph[wid];
+  unsigned long long bestU = 0ull, cnt = 0;
+  for (int t0 = blockIdx.x * nw + wid; t0 < count; t0 += gridDim.x * nw) {
+    const int pos = list ? list[t0] : p0 + t0;
     const int i = ord[pos];
     if (picked[i]) {
-      scores[pos] = -1.0;
+      if (lane == 0) scores[pos] = -1.0;
       continue;
     }
-    float zf[KS];
-#pragma unroll
-    for (int j = 0; j < KS; ++j) zf[j] = 0.f;
+    pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
+    pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
+    __syncwarp();
+    float z0 = 0.f, z1 = 0.f;
+#pragma unroll 8
     for (int a = 0; a < m; ++a) {
-      const float x = (float)phi[(int64_t)a * N + i];
-#pragma unroll
-      for (int j = 0; j < KS; ++j) zf[j] = fmaf(wk[j][a], x, zf[j]);
+      const float x = pr[a];
+      z0 = fmaf(Wt[a][lane], x, z0);
+      z1 = fmaf(Wt[a][lane + 32], x, z1);
     }
-    const double nr = (double)nrm[i];
-    const double dlt = 8e-6 * sqrt(nr);
-    const double z1u = fabs((double)zf[0]) + dlt;
-    double c = 1.0, used = z1u * z1u;
-#pragma unroll
-    for (int j = 1; j < KS; ++j) {
-      if (j < ks) {
-        const double zl = fmax(fabs((double)zf[j]) - dlt, 0.0);
-        c += zl * zl * inv[j];
-        used += (fabs((double)zf[j]) + dlt) * (fabs((double)zf[j]) + dlt);
+    __syncwarp();
+    const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
+    const float zf = __shfl_sync(0xffffffffu, z0, 0);
+    const float b1 = __fadd_ru(fabsf(zf), dl);
+    const float b1s = __fmul_ru(b1, b1);
+    // lower bounds of z_j^2 (j >= 2); lane 0's first slot is z_1 itself
+    float a0 = lane == 0 ? 0.f : fmaxf(__fsub_rd(fabsf(z0), dl), 0.f);
+    float a1 = fmaxf(__fsub_rd(fabsf(z1), dl), 0.f);
+    a0 = __fmul_rd(a0, a0);
+    a1 = __fmul_rd(a1, a1);
+    double U = fmin(__dadd_ru(l1, (double)b1s), l2);
+    if (m == 1 || !(d2n > 0.f)) {
+      // U already exact up to rounding (m = 1) or the interlacing bound l2
+    } else {
+      float t = 0.f, lo = 0.f, hi = fminf(d2n, b1s);
+      float g = warp_sum(a0 / dn0 + a1 / dn1);
+      float dg = warp_sum(a0 / (dn0 * dn0) + a1 / (dn1 * dn1));
+      for (int it = 0; it < 16; ++it) {
+        if (it > 0) {
+          const float r0 = __frcp_rn(dn0 - t), r1 = __frcp_rn(dn1 - t);
+          const float q0 = a0 * r0, q1 = a1 * r1;
+          g = warp_sum(q0 + q1);
+          dg = warp_sum(fmaf(q0, r0, q1 * r1));
+          const float h = fmaf(t, 1.f + g, -b1s);
+          if (fabsf(h) <= 32.f * 1.1920929e-7f * (t * (1.f + g) + b1s)) break;
+          if (h < 0.f)
+            lo = t;
+          else
+            hi = t;
+        }
+        const float gap = d2n - t;
+        const float C = 1.f + (g - dg * gap);
+        const float B = C * d2n + b1s + dg * gap * gap;
+        const float nt = 2.f * b1s * d2n / (B + sqrtf(fmaxf(B * B - 4.f * C * b1s * d2n, 0.f)));
+        if (it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t) {
+          t = nt;
+          break;
+        }
+        t = (nt > lo && nt < hi) ? nt : 0.5f * (lo + hi);
+      }
+      // certify h_L(t') >= 0: t' 3e-5 above the iterate, else 5e-4
+      for (int tr = 0; tr < 2; ++tr) {
+        const float tu = __fmul_ru(t, tr == 0 ? 1.f + 1.0f / 32768.f : 1.f + 1.0f / 2048.f);
+        if (!(tu < d2u)) break;
+        const float S = warp_sum_rd(__fadd_rd(__fmul_rd(a0, __frcp_rd(__fsub_ru(du0, tu))),
+                                              __fmul_rd(a1, __frcp_rd(__fsub_ru(du1, tu)))));
+        const float hl = __fsub_rd(__fmul_rd(tu, __fadd_rd(1.f, S)), b1s);
+        if (hl >= 0.f) {
+          U = fmin(U, __dadd_ru(l1, (double)tu));
+          break;
+        }
       }
     }
-    const double rest = nr * (1.0 - 3e-5) - used;
-    if (rest > 0.0) c += rest * invm;
-    double U = l1 + z1u * z1u / c;
-    if (m > 1) U = fmin(U, l2);
-    U = U * (1.0 + 1e-12);
-    scores[pos] = U;
-    ++cnt;
-    const double g = m > 1 ? l2 - l1 : 0.0;
-    const double z1 = (double)zf[0];
-    const double sg = g + nr;
-    const double L = l1 + 0.5 * (sg - sqrt(fmax(sg * sg - 4.0 * g * z1 * z1, 0.0)));
-    const unsigned long long kL =
-        ((unsigned long long)(__double_as_longlong(L) >> 20) << 32) | (unsigned)pos;
-    const unsigned long long kU =
-        ((unsigned long long)(__double_as_longlong(U) >> 20) << 32) | (unsigned)pos;
-    bestL = kL > bestL ? kL : bestL;
-    bestU = kU > bestU ? kU : bestU;
+    if (lane == 0) {
+      scores[pos] = U;
+      ++cnt;
+      const unsigned long long kU =
+          ((unsigned long long)(__double_as_longlong(U) >> 20) << 32) | (unsigned)pos;
+      bestU = kU > bestU ? kU : bestU;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long u = __shfl_xor_sync(0xffffffffu, bestL, o);
-    bestL = u > bestL ? u : bestL;
-    u = __shfl_xor_sync(0xffffffffu, bestU, o);
-    bestU = u > bestU ? u : bestU;
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (bestL) atomicMax(&ctl->lbest, bestL);
+  if (lane == 0) {
     if (bestU) atomicMax(&ctl->ubest, bestU);
-    atomicAdd(&ctl->stat[1], cnt);
+    if (cnt) atomicAdd(&ctl->stat[1], cnt);
   }
 }
 
-// exact score of the heuristic best row -> raise smax to it
+// stage a CTA's copy of W (m x m, column j = eigenvector j) with an odd
+// leading dimension, and the eigenvalues
+HY_DEV void stage_w(const double* __restrict__ W_s, const double* __restrict__ lam_s, int m,
+                    double* W, double* lam) {
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    const int j = i / m, a = i - j * m;
+    W[j * kLdw + a] = W_s[i];
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = lam_s[i];
+}
+
+// exact score of the row with the largest screen bound -> raise smax to it
 template <typename T>
 __global__ void k_odeim_probe_best(const T* __restrict__ phi, int64_t N, int m,
                                    const double* __restrict__ lam_s, const double* __restrict__ W_s,
-                                   const int* __restrict__ ord, OdCtl* ctl,
-                                   double* __restrict__ scores) {
-  __shared__ double W[64 * 64], lam[64], rb[2][64];
-  const unsigned long long key[2] = {ctl->lbest, ctl->ubest};
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) W[i] = W_s[i];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    lam[i] = lam_s[i];
-    for (int t = 0; t < 2; ++t)
-      if (key[t]) rb[t][i] = (double)phi[(int64_t)i * N + ord[(int)(key[t] & 0xffffffffull)]];
-  }
+                                   const int* __restrict__ ord, OdCtl* ctl) {
+  extern __shared__ double sh[];
+  double* W = sh;              // 64 x kLdw
+  double* lam = W + 64 * kLdw;  // 64
+  double* rb = lam + 64;        // 64
+  const unsigned long long key = ctl->ubest;
+  if (!key) return;
+  const int row = ord[(int)(key & 0xffffffffull)];
+  stage_w(W_s, lam_s, m, W, lam);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rb[i] = (double)phi[(int64_t)i * N + row];
   __syncthreads();
-  const int t = threadIdx.x >> 5;
-  if (t < 2 && key[t]) {
-    const double mu = secular_min_warp(W, lam, m, rb[t], ctl->lam1, ctl->lam2);
-    if ((threadIdx.x & 31) == 0) atomicMax(&ctl->smax, dbits(mu));
+  if (threadIdx.x < 32) {
+    const double mu = secular_min_warp(W, kLdw, lam, m, rb, ctl->lam1, ctl->lam2);
+    if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(mu));
   }
 }
 
-// exact scores of the screened rows whose bound reaches smax (1 - 2 tie);
-// the others get -1.  One warp per row.
+// exact scores of the rows whose bound reaches smax (1 - 2 tie); the others
+// get -1.  One warp per row.
 template <typename T>
 __global__ void k_odeim_exact(const T* __restrict__ phi, int64_t N, int m,
                               const double* __restrict__ lam_s, const double* __restrict__ W_s,
                               const int* __restrict__ ord, int p0, double tie_tol, OdCtl* ctl,
                               double* __restrict__ scores) {
   extern __shared__ double sh[];
-  double* W = sh;
-  double* lam = W + m * m;
-  double* rowbuf = lam + 64;
+  double* W = sh;               // 64 x kLdw
+  double* lam = W + 64 * kLdw;  // 64
+  double* rowbuf = lam + 64;    // per warp: 64
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) W[i] = W_s[i];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = lam_s[i];
+  stage_w(W_s, lam_s, m, W, lam);
   __syncthreads();
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
@@ -596,7 +715,7 @@ __global__ void k_odeim_exact(const T* __restrict__ phi, int64_t N, int m,
     const int i = ord[pos];
     for (int a = lane; a < m; a += 32) rb[a] = (double)phi[(int64_t)a * N + i];
     __syncwarp();
-    const double mu = secular_min_warp(W, lam, m, rb, l1, l2);
+    const double mu = secular_min_warp(W, kLdw, lam, m, rb, l1, l2);
     __syncwarp();
     if (lane == 0) scores[pos] = mu;
     best = mu > best ? mu : best;
@@ -607,16 +726,12 @@ __global__ void k_odeim_exact(const T* __restrict__ phi, int64_t N, int m,
   if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
 }
 
+// ODEIM: mu - l1 <= z_1^2 <= |phi_i|^2, so rows need |phi_i|^2 >= lim - l1
 __global__ void k_odeim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
                              const int* __restrict__ bstart, int probe_end, double tie_tol) {
-  ctl->stat[3] += 1;
+  if (threadIdx.x == 0) ctl->stat[3] += 1;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  const double tau = (lim - ctl->lam1) / (1.0 + 1e-5);
-  int blast = -1;
-  for (int b = 0; b < kNB; ++b)
-    if (bstart[b + 1] > bstart[b] && (double)__uint_as_float(bmax[b]) >= tau) blast = b;
-  int n = blast >= 0 ? bstart[blast + 1] : 0;
-  ctl->n_c = n > probe_end ? n : probe_end;
+  plan_rows(ctl, bmax, bstart, probe_end, (lim - ctl->lam1) / (1.0 + 1e-5));
 }
 
 // ---- rank-one update of the eigensystem of M (one per oversampling step) ----
@@ -768,6 +883,20 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
 }
 
 // One warp per root (CTA j); Delta[i * 64 + j] = d_i - lambda_j.
+// Root j lies in (d_j, d_{j+1}) (the last one in (d_n, d_n + |z|^2)); it is
+// computed as tau in coordinates shifted to the nearer pole o, so that
+// d_i - lambda_j = (d_i - d_o) - tau keeps full relative accuracy.  Each
+// step solves the two-pole model of f(tau) = 1 + sum_i z_i^2 / (del_i - tau)
+// (the "middle way" of Li's secular solver, as in LAPACK's dlaed4): with
+// psi the terms with poles at or left of d_j and phi the rest,
+//   f ~ c + s / (del_j - tau') + S / (del_{j+1} - tau'),
+//   s = psi' (del_j - tau)^2, S = phi' (del_{j+1} - tau)^2,
+//   c = f - psi' (del_j - tau) - phi' (del_{j+1} - tau),
+// a quadratic in the correction whose root in the interval is taken
+// (the last root has no right pole: tau' = del_n + s / c).  Steps are kept
+// inside a shrinking bracket (bisection otherwise); the iteration stops once
+// |f| is within the rounding error of its evaluation, the step is below
+// 2 ulp, or the bracket has collapsed.
 __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   const int j = blockIdx.x, lane = threadIdx.x;
   const int nK = wk->nK;
@@ -779,11 +908,12 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
     const double zi = i < nK ? wk->zK[i] : 0.0;
     z2[u] = zi * zi;
   }
-  double rho = warp_sum(z2[0] + z2[1]);
+  const double rho = warp_sum(z2[0] + z2[1]);
   const double dj = wk->dK[j];
+  const bool last = j == nK - 1;
   int o;
   double lo, hi;
-  if (j == nK - 1) {
+  if (last) {
     o = j;
     lo = 0.0;
     hi = rho;
@@ -807,50 +937,73 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   const double dorg = wk->dK[o];
   double del[2];
   for (int u = 0; u < 2; ++u) del[u] = dv[u] - dorg;
-  // f(tau) = 1 + sum_i z_i^2 / (del_i - tau), increasing between the poles:
-  // Newton steps kept inside a shrinking bracket (bisection when a step
-  // leaves it); the iterate itself is the result once the step is below
-  // 2 ulp or the bracket has collapsed.
+  const double delj = dj - dorg, deln = last ? 0.0 : wk->dK[j + 1] - dorg;
   double t = (o == j) ? 0.5 * hi : 0.5 * lo;
-  double tau = t;
   const double eps = 2.220446049250313e-16;
-  for (int it = 0; it < 400; ++it) {
-    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
-    tau = t;
-    if (t <= lo || t >= hi) break;
-    double f = 0.0, df = 0.0;
-    for (int u = 0; u < 2; ++u)
-      if (lane + 32 * u < nK) {
+  for (int it = 0; it < 100; ++it) {
+    double f = 0.0, fa = 0.0, dps = 0.0, dph = 0.0;
+    for (int u = 0; u < 2; ++u) {
+      const int i = lane + 32 * u;
+      if (i < nK) {
         const double r = 1.0 / (del[u] - t);
-        f = f + z2[u] * r;
-        df = df + z2[u] * r * r;
+        const double q = z2[u] * r;
+        f = f + q;
+        fa = fa + fabs(q);
+        if (i <= j)
+          dps = dps + q * r;
+        else
+          dph = dph + q * r;
       }
+    }
     f = 1.0 + warp_sum(f);
-    df = warp_sum(df);
-    if (f == 0.0) break;
+    fa = warp_sum(fa);
+    dps = warp_sum(dps);
+    dph = warp_sum(dph);
+    if (fabs(f) <= 8.0 * eps * (1.0 + fa + fabs(t) * (dps + dph))) break;
     if (f < 0.0)
       lo = t;
     else
       hi = t;
     if (hi - lo <= 2.0 * eps * fmax(fabs(hi), fabs(lo))) {
-      tau = 0.5 * (lo + hi);
+      t = 0.5 * (lo + hi);
       break;
     }
-    double nt = t - f / df;
+    const double Dj = delj - t;  // < 0
+    double eta = NAN;
+    if (last) {
+      const double sL = dps * Dj * Dj, c = f - dps * Dj;
+      if (c > 0.0) eta = Dj + sL / c;
+    } else {
+      const double Dn = deln - t;  // > 0
+      const double sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+      const double A = f - dps * Dj - dph * Dn;
+      const double B = A * (Dj + Dn) + sL + sR;
+      const double Cq = f * Dj * Dn;
+      // A eta^2 - B eta + Cq = 0: the root in (Dj, Dn)
+      if (A == 0.0) {
+        if (B != 0.0) eta = Cq / B;
+      } else {
+        const double q = 0.5 * (B + copysign(sqrt(fmax(B * B - 4.0 * A * Cq, 0.0)), B));
+        const double e1 = q / A, e2 = q != 0.0 ? Cq / q : NAN;
+        if (e1 > Dj && e1 < Dn) eta = e1;
+        if (e2 > Dj && e2 < Dn) eta = e2;
+      }
+    }
+    double nt = t + eta;
+    if (fabs(nt - t) <= 2.0 * eps * fabs(t)) {  // before the bracket test: a
+      t = nt;                                    // converged step may sit on it
+      break;
+    }
     if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
-    if (fabs(nt - t) <= 2.0 * eps * fabs(t)) {
-      tau = nt;
-      break;
-    }
     t = nt;
   }
   for (int u = 0; u < 2; ++u) {
     const int i = lane + 32 * u;
-    if (i < nK) Delta[i * 64 + j] = del[u] - tau;
+    if (i < nK) Delta[i * 64 + j] = del[u] - t;
   }
   if (lane == 0) {
     wk->org[j] = o;
-    wk->tau[j] = tau;
+    wk->tau[j] = t;
   }
 }
 
@@ -859,16 +1012,35 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
 __global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __restrict__ Delta,
                              const double* __restrict__ Wrot, int m, double* __restrict__ Wnew,
                              double* __restrict__ lamnew) {
-  __shared__ double zh[64], v[64];
+  __shared__ double zh[64], v[64], dK[64];
+  __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
+  __shared__ int Ks[64];
   const int j = blockIdx.x, tid = threadIdx.x;
   const int nK = wk->nK;
   if (j >= nK) return;
+  for (int i = tid; i < nK; i += blockDim.x) {
+    dK[i] = wk->dK[i];
+    Ks[i] = wk->K[i];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nK * m; idx += blockDim.x) {
+    const int i = idx / m, a = idx - i * m;
+    Wk[i * 65 + a] = Wrot[Ks[i] * m + a];
+  }
+  __syncthreads();
   if (tid < nK) {
+    // Loewner: zh_i^2 = (lambda_i - d_i) prod_{q != i} (lambda_q - d_i) / (d_q - d_i),
+    // the products taken as two independent chains
     const int i = tid;
-    const double di = wk->dK[i];
-    double pr = -Delta[i * 64 + i];  // lambda_i - d_i > 0
-    for (int q = 0; q < nK; ++q)
-      if (q != i) pr *= (-Delta[i * 64 + q]) / (wk->dK[q] - di);
+    const double di = dK[i];
+    const double* Dr = Delta + i * 64;
+    double pr0 = -Dr[i], pr1 = 1.0;
+    for (int q = 0; q + 1 < nK; q += 2) {
+      if (q != i) pr0 *= (-Dr[q]) / (dK[q] - di);
+      if (q + 1 != i) pr1 *= (-Dr[q + 1]) / (dK[q + 1] - di);
+    }
+    if ((nK & 1) && nK - 1 != i) pr0 *= (-Dr[nK - 1]) / (dK[nK - 1] - di);
+    const double pr = pr0 * pr1;
     const double zz = sqrt(fmax(pr, 0.0));
     zh[i] = wk->zK[i] >= 0.0 ? zz : -zz;
   }
@@ -881,7 +1053,7 @@ __global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __rest
   const double inv = 1.0 / sqrt(nrm);
   for (int a = tid; a < m; a += blockDim.x) {
     double acc = 0.0;
-    for (int i = 0; i < nK; ++i) acc = fma(Wrot[wk->K[i] * m + a], v[i], acc);
+    for (int i = 0; i < nK; ++i) acc = fma(Wk[i * 65 + a], v[i], acc);
     Wnew[j * m + a] = acc * inv;
   }
   if (tid == 0) lamnew[j] = wk->dK[wk->org[j]] + wk->tau[j];
@@ -920,7 +1092,7 @@ __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restri
     ctl->lam2 = m > 1 ? lv[perm[1]] : INFINITY;
     ctl->lmax = lv[perm[m - 1]];
     ctl->smax = 0ull;
-    ctl->lbest = 0ull;
+    ctl->n_list = 0;
     ctl->ubest = 0ull;
     ctl->argmin = 0x7fffffff;
     ctl->n_c = 0;
@@ -944,6 +1116,7 @@ __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* _
 // ---- driver -----------------------------------------------------------------
 
 struct OdeimBufs {
+  int* list;
   float* nrm;
   unsigned char* bkt;
   unsigned char* picked;
@@ -978,7 +1151,7 @@ struct OdeimBufs {
 
 size_t odeim_ws_bytes(int64_t N, int m) {
   size_t b = 0;
-  b += N * sizeof(float) + N + N + N * sizeof(int) + N * sizeof(double);
+  b += N * sizeof(float) + N + N + 2 * N * sizeof(int) + N * sizeof(double) + 256;
   b += (3 * (kNB + 1) + kNB) * sizeof(int);
   b += sizeof(double) * (64 + 6 * (size_t)(m + 1) * (m + 1) + 4 * m + 64);
   b += 16 * 256;
@@ -1000,6 +1173,7 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.scores = (double*)take(N * sizeof(double));
   o.nrm = (float*)take(N * sizeof(float));
   o.ord = (int*)take(N * sizeof(int));
+  o.list = (int*)take(N * sizeof(int));
   o.bkt = (unsigned char*)take(N);
   o.picked = (unsigned char*)take(N);
   o.bcnt = (int*)take((kNB + 1) * sizeof(int));
@@ -1051,11 +1225,13 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   const int probe = (int)(N < kProbe ? N : kProbe);
   M_(-13);
   // DEIM
+  const size_t dsmem = sizeof(double) * 2 * 64 * 65;
+  cudaFuncSetAttribute(k_deim_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
   for (int l = 0; l < m; ++l) {
-    k_deim_solve<T><<<1, 32, 0, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
+    k_deim_solve<T><<<1, 32, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
     k_deim_score<T><<<(probe + 255) / 256, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, 0,
                                                         probe, o.ctl, o.scores);
-    k_deim_plan<<<1, 1, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
+    k_deim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
     k_deim_score<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, probe, -1,
                                             o.ctl, o.scores);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
@@ -1070,9 +1246,8 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   // ODEIM oversampling
   const int n = m % 2 ? m + 1 : m;  // Jacobi wants an even order
   k_odeim_gram<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
-  const size_t smem = sizeof(double) * ((size_t)m * m + 64 + 64 * 8);
-  cudaFuncSetAttribute(k_odeim_score<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_odeim_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 * 8);
+  const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64);
   M_(12);
   k_pad_sym2<<<1, 256, 0, HY_S(s)>>>(o.M, m, n, o.Mp);
   if (run_jacobi_multi(o.Mp, n, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, o.jscale,
@@ -1082,19 +1257,23 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   M_(-13);
   for (int l = m; l < np; ++l) {
     M_(13);
-    k_odeim_score<T><<<(probe + 7) / 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord,
-                                                        o.picked, 0, probe, 0, tie_tol, o.ctl,
-                                                        o.scores);
-    k_odeim_plan<<<1, 1, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
+    // full FP32 bounds of the largest-norm rows, exact score of the best
+    k_odeim_screen<T><<<(probe + 7) / 8, 256, 0, HY_S(s)>>>(
+        phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores);
+    k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
+    k_odeim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
     M_(-14);
     M_(14);
+    // the other rows whose norm can reach the best score: the z_1 bound for
+    // all, the full bound for those it does not exclude
+    k_odeim_z1<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
+                                                tie_tol, o.ctl, o.scores, o.list);
     k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord,
-                                                    o.picked, probe, o.ctl, o.scores);
-    k_odeim_probe_best<T><<<1, 64, 0, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl,
-                                                 o.scores);
+                                                    o.picked, 0, -1, o.list, o.ctl, o.scores);
+    k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     M_(-15);
     M_(15);
-    k_odeim_exact<T><<<152 * 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, probe,
+    k_odeim_exact<T><<<152 * 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, 0,
                                                       tie_tol, o.ctl, o.scores);
     M_(-16);
     M_(17);

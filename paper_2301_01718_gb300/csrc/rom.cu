@@ -414,9 +414,9 @@ __global__ void k_identity(double* V, int n) {
 void launch_identity(double* V, int n, cudaStream_t s) { k_identity<<<16, 256, 0, HY_S(s)>>>(V, n); }
 
 // ---------------------------------------------------------------------------
-// two-sided cyclic Jacobi (FP64, one CTA): A (n x n, n even) in dynamic
-// shared memory, V (n x n column-major) in global memory.  Round-robin
-// ordering: n/2 disjoint rotations per round.
+// two-sided cyclic Jacobi (FP64) spread over n/2 CTAs: A (n x n, n even),
+// V (n x n column-major) in global memory.  Round-robin ordering: n/2
+// disjoint rotations per round, pair b of round r given by rr_pair.
 // ---------------------------------------------------------------------------
 
 HY_DEV void rr_pair(int n, int r, int b, int& p, int& q) {
@@ -430,152 +430,6 @@ HY_DEV void rr_pair(int n, int r, int b, int& p, int& q) {
   }
   p = a < c ? a : c;
   q = a < c ? c : a;
-}
-
-__global__ void k_jacobi_sym(const double* __restrict__ Ain, int n, double* __restrict__ V,
-                             double* __restrict__ lam, int max_sweeps, int* sweeps_out,
-                             int warm) {
-  extern __shared__ double A[];
-  __shared__ double cs[2 * 128];
-  __shared__ int rotated;
-  __shared__ double scale;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int half = n / 2;
-  for (int i = tid; i < n * n; i += nt) A[i] = Ain[i];
-  if (!warm)
-    for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-  __syncthreads();
-  // rotation threshold: relative to the two diagonal entries, with a floor
-  // at rounding level of the largest diagonal entry (rounding noise would
-  // otherwise keep near-null pairs rotating forever)
-  {
-    double mx = 0.0;
-    for (int i = tid; i < n; i += nt) mx = fmax(mx, fabs(A[i * n + i]));
-    mx = block_max(mx);
-    if (tid == 0) scale = mx;
-  }
-  __syncthreads();
-  const double floor_abs = 1e-16 * scale;
-  int sw = 0;
-  for (; sw < max_sweeps; ++sw) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int r = 0; r < n - 1; ++r) {
-      for (int b = tid; b < half; b += nt) {
-        int p, q;
-        rr_pair(n, r, b, p, q);
-        const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > floor_abs && fabs(apq) > 1e-14 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-          rotated = 1;
-        }
-        cs[2 * b] = c;
-        cs[2 * b + 1] = s;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {  // rows
-        const int b = idx / n, k = idx % n;
-        const double c = cs[2 * b], s = cs[2 * b + 1];
-        if (s == 0.0) continue;
-        int p, q;
-        rr_pair(n, r, b, p, q);
-        const double ap = A[p * n + k], aq = A[q * n + k];
-        A[p * n + k] = c * ap - s * aq;
-        A[q * n + k] = s * ap + c * aq;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {  // columns of A and V
-        const int b = idx / n, k = idx % n;
-        const double c = cs[2 * b], s = cs[2 * b + 1];
-        if (s == 0.0) continue;
-        int p, q;
-        rr_pair(n, r, b, p, q);
-        const double ap = A[k * n + p], aq = A[k * n + q];
-        A[k * n + p] = c * ap - s * aq;
-        A[k * n + q] = s * ap + c * aq;
-        const double vp = V[(int64_t)p * n + k], vq = V[(int64_t)q * n + k];
-        V[(int64_t)p * n + k] = c * vp - s * vq;
-        V[(int64_t)q * n + k] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-    if (!rotated) break;
-  }
-  for (int i = tid; i < n; i += nt) lam[i] = A[i * n + i];
-  if (tid == 0 && sweeps_out) *sweeps_out = sw;
-}
-
-// One round of two-sided cyclic Jacobi spread over n/2 CTAs (CTA b owns the
-// rows of rotation pair b).  Every CTA recomputes the round's n/2 rotations
-// from Ain (three entries each), rotates its two rows, applies all column
-// rotations to them and writes Aout; V (column-major, column j of V is row j
-// of the stored array) is rotated in place (CTA b touches only columns p, q).
-// Reading Ain and writing Aout keeps CTAs independent: one launch per round.
-__global__ void k_jacobi_round(const double* __restrict__ Ain, double* __restrict__ Aout, int n,
-                               double* __restrict__ V, int r, double floor_abs, int* rotated) {
-  __shared__ double cs[2 * 128];
-  __shared__ double rp[128], rq[128];
-  const int half = n / 2, tid = threadIdx.x;
-  for (int b = tid; b < half; b += blockDim.x) {
-    int p, q;
-    rr_pair(n, r, b, p, q);
-    const double apq = Ain[p * n + q], app = Ain[p * n + p], aqq = Ain[q * n + q];
-    double c = 1.0, sn = 0.0;
-    if (fabs(apq) > floor_abs && fabs(apq) > 1e-14 * sqrt(fabs(app * aqq))) {
-      const double tau = (aqq - app) / (2.0 * apq);
-      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-      c = 1.0 / sqrt(1.0 + t * t);
-      sn = t * c;
-    }
-    cs[2 * b] = c;
-    cs[2 * b + 1] = sn;
-  }
-  __syncthreads();
-  int p, q;
-  rr_pair(n, r, blockIdx.x, p, q);
-  const double c = cs[2 * blockIdx.x], sn = cs[2 * blockIdx.x + 1];
-  for (int k = tid; k < n; k += blockDim.x) {
-    const double ap = Ain[p * n + k], aq = Ain[q * n + k];
-    rp[k] = c * ap - sn * aq;
-    rq[k] = sn * ap + c * aq;
-    if (sn != 0.0) {
-      const double vp = V[(int64_t)p * n + k], vq = V[(int64_t)q * n + k];
-      V[(int64_t)p * n + k] = c * vp - sn * vq;
-      V[(int64_t)q * n + k] = sn * vp + c * vq;
-    }
-  }
-  __syncthreads();
-  for (int k = tid; k < n; k += blockDim.x) {
-    // column rotation of the pair that contains k: in round r of the circle
-    // schedule, player n-1 meets r and every other k meets (2r - k) mod (n-1)
-    const int nm1 = n - 1;
-    int partner, b2;
-    if (k == nm1 || k == r) {
-      partner = k == nm1 ? r : nm1;
-      b2 = 0;
-    } else {
-      partner = ((2 * r - k) % nm1 + nm1) % nm1;
-      const int b1 = ((k - r) % nm1 + nm1) % nm1;
-      b2 = b1 <= n / 2 - 1 ? b1 : nm1 - b1;
-    }
-    const int p2 = k < partner ? k : partner, q2 = k < partner ? partner : k;
-    const double c2 = cs[2 * b2], s2 = cs[2 * b2 + 1];
-    double np_, nq_;
-    if (k == p2) {
-      np_ = c2 * rp[p2] - s2 * rp[q2];
-      nq_ = c2 * rq[p2] - s2 * rq[q2];
-    } else {
-      np_ = s2 * rp[p2] + c2 * rp[q2];
-      nq_ = s2 * rq[p2] + c2 * rq[q2];
-    }
-    Aout[p * n + k] = np_;
-    Aout[q * n + k] = nq_;
-  }
-  if (tid == 0 && sn != 0.0) *rotated = 1;
 }
 
 // Grid barrier for a cooperative launch (all CTAs co-resident).  The spin is
@@ -677,6 +531,10 @@ __global__ void k_jacobi_sweep(double* A0, double* A1, int n, double* __restrict
         np_ = s2 * rp[p2] + c2 * rp[q2];
         nq_ = s2 * rq[p2] + c2 * rq[q2];
       }
+      // the entry this rotation annihilates is zero, not rounding noise of
+      // size eps |A| that would keep later sweeps rotating
+      if (sn != 0.0 && k == q) np_ = 0.0;
+      if (sn != 0.0 && k == p) nq_ = 0.0;
       Aout[p * n + k] = np_;
       Aout[q * n + k] = nq_;
     }
@@ -737,28 +595,6 @@ int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf
   }
   k_copy_diag<<<1, 128, 0, HY_S(s)>>>(A0, n, lam);
   return sw;
-}
-
-__global__ void k_pad_sym(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int a = idx / n, b = idx % n;
-    P[idx] = (a < m && b < m) ? M[a * m + b] : 0.0;
-  }
-}
-
-// Eigenpairs of the symmetric m x m matrix M by Jacobi on its zero-padded
-// n x n copy (n even); the padding index stays decoupled.
-void launch_jacobi_padded(const double* M, int m, int n, double* V, double* lam, double* pad,
-                          cudaStream_t s) {
-  k_pad_sym<<<1, 256, 0, HY_S(s)>>>(M, m, n, pad);
-  launch_jacobi_sym(pad, n, V, lam, 60, nullptr, 0, s);
-}
-
-void launch_jacobi_sym(const double* A, int n, double* V, double* lam, int max_sweeps,
-                       int* sweeps_out, int warm, cudaStream_t s) {
-  const size_t smem = sizeof(double) * (size_t)n * n;
-  cudaFuncSetAttribute(k_jacobi_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jacobi_sym<<<1, 1024, smem, HY_S(s)>>>(A, n, V, lam, max_sweeps, sweeps_out, warm);
 }
 
 // Order eigenpairs (lam[0..n), columns of V; V = NULL means the identity)
@@ -880,6 +716,109 @@ __global__ void __launch_bounds__(256, 2) k_form_phi(const T* __restrict__ ring,
   }
 }
 
+// FP32, m > 16: the same product as a register-tiled SGEMM.  A CTA takes
+// 128-row tiles of the window: the raw values (w x 128, k-major) are staged
+// in shared memory, one thread per row forms the Kahan window mean and
+// centres the row in place, then each thread accumulates 8 rows x CT
+// columns of Phi (CT = MM / 16), reading 8 centred values and CT
+// coefficients from shared memory per window step (8 CT FMAs per 2 + CT/4
+// shared loads).
+template <int MM>
+__global__ void __launch_bounds__(256, 2) k_form_phi_tiled(
+    const float* __restrict__ ring, int64_t N, const int* __restrict__ win, int w,
+    const float* __restrict__ psi, const float* __restrict__ C, int m,
+    const int* __restrict__ m_eff_dev, float* __restrict__ phi, float* __restrict__ psi_next) {
+  constexpr int TR = 128;
+  constexpr int CT = MM / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* Xs = reinterpret_cast<float*>(smraw);  // w x TR
+  float* Cs = Xs + w * TR;                      // w x MM, zero padded
+  __shared__ int ws[128];
+  const int tid = threadIdx.x;
+  const int me = *m_eff_dev;
+  for (int i = tid; i < w * MM; i += blockDim.x) {
+    const int r = i / MM, j = i % MM;
+    Cs[i] = j < m && j < me ? C[r * m + j] : 0.f;
+  }
+  for (int i = tid; i < w; i += blockDim.x) ws[i] = win[i];
+  const int rg = tid >> 4, cg = tid & 15;
+  const bool vec = (N & 3) == 0;
+  for (int64_t base = (int64_t)blockIdx.x * TR; base < N; base += (int64_t)gridDim.x * TR) {
+    __syncthreads();  // Cs/ws ready; the previous tile's Xs fully consumed
+    for (int idx = tid; idx < w * (TR / 4); idx += blockDim.x) {
+      const int k = idx / (TR / 4), q = idx % (TR / 4);
+      const int64_t r0 = base + 4 * q;
+      const float* src = ring + (int64_t)ws[k] * N + r0;
+      float4 v;
+      if (vec && r0 + 3 < N) {
+        v = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        v.x = r0 < N ? src[0] : 0.f;
+        v.y = r0 + 1 < N ? src[1] : 0.f;
+        v.z = r0 + 2 < N ? src[2] : 0.f;
+        v.w = r0 + 3 < N ? src[3] : 0.f;
+      }
+      *reinterpret_cast<float4*>(Xs + k * TR + 4 * q) = v;
+    }
+    __syncthreads();
+    if (tid < TR) {
+      const int64_t r = base + tid;
+      const float pr = r < N ? psi[r] : 0.f;
+      float sum = 0.f, comp = 0.f;  // Kahan-compensated window sum
+      for (int k = 0; k < w; ++k) {
+        const float g = Xs[k * TR + tid];
+        const float yk = g - comp, tk = sum + yk;
+        comp = (tk - sum) - yk;
+        sum = tk;
+        Xs[k * TR + tid] = g - pr;
+      }
+      if (r < N) psi_next[r] = sum / (float)w;
+    }
+    __syncthreads();
+    float acc[8][CT];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < CT; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const float4 xa = *reinterpret_cast<const float4*>(Xs + k * TR + rg * 8);
+      const float4 xb = *reinterpret_cast<const float4*>(Xs + k * TR + rg * 8 + 4);
+      const float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+      float cv[CT];
+      if (CT == 4) {
+        const float4 c4 = *reinterpret_cast<const float4*>(Cs + k * MM + cg * CT);
+        cv[0] = c4.x;
+        cv[1 % CT] = c4.y;
+        cv[2 % CT] = c4.z;
+        cv[3 % CT] = c4.w;
+      } else {
+        const float2 c2 = *reinterpret_cast<const float2*>(Cs + k * MM + cg * CT);
+        cv[0] = c2.x;
+        cv[1 % CT] = c2.y;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(x[i], cv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < CT; ++j) {
+      const int col = cg * CT + j;
+      if (col >= me) continue;
+      float* dst = phi + (int64_t)col * N + base + rg * 8;
+      if (vec && base + rg * 8 + 7 < N) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (base + rg * 8 + i < N) dst[i] = acc[i][j];
+      }
+    }
+  }
+}
+
 template <typename T>
 void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* psi, const T* C,
                      int m, const int* m_eff_dev, T* phi, T* psi_next, cudaStream_t s) {
@@ -894,6 +833,29 @@ void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* p
     k_form_phi<T, MM><<<(int)blocks, 256, smem, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,  \
                                                      phi, psi_next);                         \
   } while (0)
+  if (sizeof(T) == 4 && m > 16) {
+    const float* ringf = reinterpret_cast<const float*>(ring);
+    const float* psif = reinterpret_cast<const float*>(psi);
+    const float* Cf = reinterpret_cast<const float*>(C);
+    float* phif = reinterpret_cast<float*>(phi);
+    float* pnf = reinterpret_cast<float*>(psi_next);
+    const int mt = m <= 32 ? 32 : 64;
+    const size_t sm2 = sizeof(float) * (size_t)w * (128 + mt);
+    int64_t tiles = (N + 127) / 128;
+    if (tiles > 152 * 2) tiles = 152 * 2;
+    if (mt == 32) {
+      cudaFuncSetAttribute(k_form_phi_tiled<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm2);
+      k_form_phi_tiled<32><<<(int)tiles, 256, sm2, HY_S(s)>>>(ringf, N, win, w, psif, Cf, m,
+                                                              m_eff_dev, phif, pnf);
+    } else {
+      cudaFuncSetAttribute(k_form_phi_tiled<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm2);
+      k_form_phi_tiled<64><<<(int)tiles, 256, sm2, HY_S(s)>>>(ringf, N, win, w, psif, Cf, m,
+                                                              m_eff_dev, phif, pnf);
+    }
+    return;
+  }
   if (m <= 8)
     HY_FORM(8);
   else if (m <= 16)

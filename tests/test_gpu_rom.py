@@ -115,6 +115,43 @@ def test_pod_of_known_spectrum(prec, w):
         assert np.abs(Pg @ Pg.T - Phi_o @ Phi_o.T).max() < 2e-4
 
 
+@pytest.mark.parametrize("pde,nx,ny", [(W.PDE_BURGERS, 1073, 1), (W.PDE_EULER, 33, 17)])
+@pytest.mark.parametrize("m", [20, 40])
+def test_pod_fp32_wide_basis(pde, nx, ny, m):
+    """FP32 POD with m > 16 (the register-tiled product Phi = X_c C): row
+    counts that are not a multiple of the 128-row tile (Burgers, 1073 rows,
+    not even a multiple of 4; Euler 33 x 17, 2244 rows)."""
+    w = 48
+    cfg = W.ArConfig(pde=pde, scheme=W.SCHEME_RK2, nx=nx, ny=ny, dx=0.1, dy=0.1, dt=0.01,
+                     w=w, m=m, n_p=2 * m, precision=W.PREC_F32, pod_tol=1e-6, pod_abs=1e-6)
+    N = cfg.ndof
+    g = np.random.Generator(np.random.PCG64(100 + m + nx))
+    U, _ = np.linalg.qr(g.standard_normal((N, w)))
+    V, _ = np.linalg.qr(g.standard_normal((w, w)))
+    sig = 0.9 ** np.arange(w)
+    psi = (1.0 + g.standard_normal(N) * 0.1).astype(np.float32).astype(np.float64)
+    X = (psi[:, None] + (U * sig) @ V.T).astype(np.float32).astype(np.float64)
+    raw = float(np.sqrt((X * X).sum()))
+    Phi_o, s_o = rom.pod(X - psi[:, None], m, cfg.pod_tol, cfg.pod_abs * raw)
+    with Ctx(cfg) as (hy, ctx):
+        phi = torch.zeros(m * N, dtype=torch.float32, device="cuda")
+        sg = torch.zeros(w, dtype=torch.float64, device="cuda")
+        me = hy.hyrom_stage_pod(ctx, dev(X.T.copy(), torch.float32), w,
+                                dev(psi, torch.float32), phi, sg)
+        Pg = host(phi)[: me * N].reshape(me, N).T.astype(np.float64)
+        sg = host(sg)
+    assert me == Phi_o.shape[1] == m
+    assert rel_err(sg[:m], s_o[:m]) < 1e-5
+    # directions: FP32 rounding of the product, amplified by sigma_1 / sigma_j;
+    # lengths: FP32 rounding of the columns (a few 1e-8)
+    nrm = np.linalg.norm(Pg, axis=0)
+    assert np.abs(nrm - 1.0).max() < 1e-6
+    for j in range(m):
+        c = abs(float(Pg[:, j] @ Phi_o[:, j])) / nrm[j]
+        assert 1.0 - c < 1e-10 * (s_o[0] / s_o[j]) ** 2 + 1e-11, (j, 1.0 - c)
+    assert np.abs(Pg.T @ Pg - np.eye(m)).max() < 1e-5
+
+
 @pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
 @pytest.mark.parametrize("N,m,n_p,conc", [(600, 4, 9, False), (40000, 8, 17, True),
                                           (40000, 16, 32, False)])
