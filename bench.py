@@ -5,7 +5,7 @@ Workload (default): 2D Euler, 2048 x 2048 cells (16.8 M dofs), FP32 states,
 a Mach-3 planar shock at a seeded angle with exact-state inflow and outflow
 sides, SSP-RK2 HDM, k = 64 POD modes from w = 128 snapshots, n_p = 128
 ODEIM points, top 5 % of cells by reconstruction error.  A "step" is one
-hybrid step of Algorithm 1 (lines 3-30: partial HDM, gappy coordinates,
+hybrid step of Algorithm 1 (advance and basis update: partial HDM, gappy coordinates,
 reconstruction, residual-gated filters, error indicator and selection,
 POD, ODEIM, sampling sets).  The method's own w warm-up full steps and the
 first rebuild run before the benchmark's warm-up steps.

@@ -89,8 +89,8 @@ typedef struct {
 /* What one call of hyrom_step / hyrom_advance / hyrom_update_basis did. */
 typedef struct {
   int64_t k;            /* step index of the snapshot now held (gamma_k)   */
-  int32_t was_full;     /* 1: full HDM solve (Algorithm 1 line 4)           */
-  int32_t rebuilt;      /* 1: basis, points and sets rebuilt (lines 18-30)  */
+  int32_t was_full;     /* 1: full HDM solve (Algorithm 1)                  */
+  int32_t rebuilt;      /* 1: basis, points and sets rebuilt               */
   int32_t J;            /* subiterations of the partial HDM (Sec. 2.3.2)   */
   int32_t n_s;          /* cells of S-hat used by this step                 */
   int32_t n_g;          /* cells picked by the error indicator (next step)  */
@@ -108,7 +108,8 @@ typedef struct hyrom_ctx hyrom_ctx;
  * hyrom_init: validate cfg, allocate the context's device workspaces (the
  * w+1 snapshot ring, basis, points, masks, filter and reduction buffers)
  * and copy q0 (nvar*Nc doubles, host or device per q0_on_host) into
- * gamma_0 (Algorithm 1 line 1), converting to the context precision.
+ * gamma_0 (the initial state of Algorithm 1), converting to the context
+ * precision.
  * Errors: HYROM_EINVAL (bad config; *out untouched), HYROM_ENOMEM,
  * HYROM_ECUDA.  On error no context is returned. */
 hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_host,
@@ -129,18 +130,18 @@ uint64_t hyrom_kernel_launches(void);
  * hyrom_stage_times copies the totals (ms[HYROM_NSTAGE], and the number of
  * intervals into count[HYROM_NSTAGE] when count is not NULL). */
 enum {
-  HYROM_T_FULL = 0,     /* full HDM step (line 4)                          */
-  HYROM_T_PARTIAL = 1,  /* partial HDM on S-hat (line 8)                   */
-  HYROM_T_GAPPY = 2,    /* gappy coordinates (line 9)                      */
-  HYROM_T_RECON = 3,    /* reconstruction on S-breve (line 12)             */
-  HYROM_T_FILTER = 4,   /* SpatialFilter (line 13)                         */
-  HYROM_T_SELECT = 5,   /* error indicator and G_{k+1} (line 20)           */
+  HYROM_T_FULL = 0,     /* full HDM step                                   */
+  HYROM_T_PARTIAL = 1,  /* partial HDM on S-hat                            */
+  HYROM_T_GAPPY = 2,    /* gappy coordinates                               */
+  HYROM_T_RECON = 3,    /* reconstruction on S-breve                       */
+  HYROM_T_FILTER = 4,   /* SpatialFilter                                   */
+  HYROM_T_SELECT = 5,   /* error indicator and G_{k+1}                     */
   HYROM_T_GRAM = 6,     /* ring Gram row of a new snapshot (FP32 POD)      */
-  HYROM_T_EIG = 7,      /* window Gram centring + eigensolve (line 24)     */
-  HYROM_T_FORMPHI = 8,  /* basis formation and next psi (lines 24, 29)     */
+  HYROM_T_EIG = 7,      /* window Gram centring + eigensolve (POD)         */
+  HYROM_T_FORMPHI = 8,  /* basis formation and next psi                    */
   HYROM_T_ODEIM = 9,    /* ODEIM oversampling and the sampled pseudo-inverse */
-  HYROM_T_MASKS = 10,   /* union / dilation / Neighbors (lines 26-28)      */
-  HYROM_T_DEIM = 11,    /* DEIM points, the first m of ODEIM (line 25)     */
+  HYROM_T_MASKS = 10,   /* union / dilation / Neighbors                    */
+  HYROM_T_DEIM = 11,    /* DEIM points, the first m of ODEIM               */
   /* parts of HYROM_T_DEIM / HYROM_T_ODEIM: */
   HYROM_T_OD_INIT = 12,   /* row-norm buckets + first eigensystem          */
   HYROM_T_OD_PROBE = 13,  /* exact scores of the largest-norm rows         */
@@ -152,21 +153,22 @@ enum {
 };
 hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
 /* Work counters of the last ODEIM call (rebuild or stage entry point):
- * out4[0] rows scored exactly by DEIM beyond the probe, out4[1] rows
- * screened by the FP32 bound in oversampling, out4[2] exact FP64 secular
- * solves in oversampling, out4[3] oversampling steps.  Synchronises. */
+ * out4[0] rows scored exactly by DEIM beyond the probe, out4[1] rows given
+ * the full certified FP32 bound in oversampling (the probe rows and those the
+ * z_1 bound does not exclude), out4[2] exact FP64 secular solves in
+ * oversampling, out4[3] oversampling steps.  Synchronises. */
 hyrom_status hyrom_odeim_counters(hyrom_ctx* ctx, int64_t* out4);
 hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count);
 
 /* ---- Algorithm 1 --------------------------------------------------------
- * hyrom_advance: lines 3-14 for k+1: a full HDM step (line 4) or a hybrid
- * step (lines 6-13: partial HDM with subiterations, gappy coordinates,
+ * hyrom_advance: the advance part of Algorithm 1 for k+1: a full HDM step
+ * or a hybrid step (predictor, partial HDM with subiterations, gappy coordinates,
  * reconstruction on S-breve, SpatialFilter).  Errors: HYROM_ESTATE when a
  * hybrid step is due but no basis exists, HYROM_ENOTCONV (state still
  * advanced), HYROM_ECUDA.
- * hyrom_update_basis: lines 15-30 for the current k: psi initialisation,
+ * hyrom_update_basis: the basis-update part for the current k: psi initialisation,
  * G_{k+1} by the error indicator, POD_m, ODEIM_{n_p}, union / setdiff /
- * Neighbors, psi_{k+1}; does nothing when line 18's condition is false.
+ * Neighbors, psi_{k+1}; does nothing when the rebuild test is false.
  * hyrom_step = hyrom_advance then hyrom_update_basis (one loop iteration).
  * info may be NULL.  These calls synchronise the stream once per call (they
  * return counts in info). */
@@ -177,7 +179,7 @@ hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info);
 /* hyrom_sample: the sampled set S-hat in effect for the next step, as
  * ascending cell ids in idx_dev (capacity cap; HYROM_ECAP if larger; the
  * count is always written to *n_out) and, when bitmap_dev is not NULL, as a
- * bitmap of ceil(Nc/32) words (bit c%32 of word c/32).  Algorithm 1 line 26.
+ * bitmap of ceil(Nc/32) words (bit c%32 of word c/32).  Algorithm 1, S-hat.
  * HYROM_ESTATE before the first rebuild. */
 hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t* n_out,
                           uint32_t* bitmap_dev);
@@ -200,11 +202,11 @@ hyrom_status hyrom_get_basis(hyrom_ctx* ctx, void* phi_dev, int32_t* m_eff, void
  * checked against an independent implementation on identical inputs.
  * `real` arrays follow the context precision. */
 
-/* Full HDM step gamma_k = F_k(gamma_k) from q_prev (Algorithm 1 line 4):
+/* Full HDM step gamma_k = F_k(gamma_k) from q_prev (Algorithm 1):
  * SSP-RK2 from t_{k-1} to t_k, or BDF1 solved by Newton (Eq. hdm). */
 hyrom_status hyrom_stage_full_step(hyrom_ctx* ctx, const void* q_prev, void* q_out, int64_t k);
 
-/* Partial HDM on S-hat (Eq. partial_hdm2; Algorithm 1 line 8): q_io holds
+/* Partial HDM on S-hat (Eq. partial_hdm2; Algorithm 1): q_io holds
  * the frozen values on the other cells and, for BDF1, the Newton start on
  * S-hat; on return it holds the HDM values on S-hat.  s_hat: bitmap. */
 hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* q_io,
@@ -216,12 +218,12 @@ hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* 
 hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const int32_t* points,
                                int32_t n_p, const void* v, const void* psi, double* y_out);
 
-/* Reconstruction on S-breve (Algorithm 1 line 12): q_io = psi + Phi y on
+/* Reconstruction on S-breve (Algorithm 1): q_io = psi + Phi y on
  * every cell whose bit in s_hat is clear (all cells when s_hat is NULL). */
 hyrom_status hyrom_stage_reconstruct(hyrom_ctx* ctx, const void* phi, int32_t m, const double* y,
                                      const void* psi, const uint32_t* s_hat, void* q_io);
 
-/* SpatialFilter (Algorithm 1 line 13, Sec. 2.3.4) of q_io in place, with
+/* SpatialFilter (Algorithm 1, Sec. 2.3.4) of q_io in place, with
  * the BDF1 residual relative to q_prev at t_k.  *passes gets the passes
  * run (may be NULL). */
 hyrom_status hyrom_stage_filter(hyrom_ctx* ctx, void* q_io, const void* q_prev, int64_t k,
@@ -250,7 +252,7 @@ hyrom_status hyrom_stage_pod(hyrom_ctx* ctx, const void* window, int32_t w, cons
 hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32_t n_p,
                                int32_t* points_out);
 
-/* Sampling sets (Algorithm 1 lines 26-28): S-hat = union(G, cells of the
+/* Sampling sets (Algorithm 1): S-hat = union(G, cells of the
  * points) dilated by cfg.halo; S-tilde = Neighbors(S-hat) (cells within the
  * scheme's stencil reach, 1 for BDF1 and 2 for SSP-RK2, not in S-hat).
  * Bitmaps of ceil(Nc/32) words; *n_s gets |S-hat| (synchronises). */

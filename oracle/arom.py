@@ -93,7 +93,7 @@ class Arom:
         info = StepInfo(k=k, was_full=self._is_full(k))
         t = k * cfg.dt
         if info.was_full:
-            gam = hdm.full_step(prev, cfg, k)                     # line 4
+            gam = hdm.full_step(prev, cfg, k)                     # full HDM step
             info.n_s = cfg.ncell
         else:
             s_hat = self.s_hat
@@ -106,9 +106,9 @@ class Arom:
                 y = self._gappy(v)
                 info.J = 1
             else:
-                v = prev.copy()                                   # line 6
+                v = prev.copy()                                   # predictor
                 y = None
-                for j in range(1, cfg.jmax + 1):                  # lines 7-11
+                for j in range(1, cfg.jmax + 1):                  # subiterations
                     v, _, _ = hdm.newton_be(prev, cfg, t, active=s_hat, q_init=v)
                     y_new = self._gappy(v)
                     conv = y is not None and np.linalg.norm(y_new - y) < cfg.eps_y
@@ -119,34 +119,34 @@ class Arom:
                     rec = self._rec(y)
                     v = v.copy()
                     v[:, self.s_tilde] = rec[:, self.s_tilde]
-            rec = self._rec(y)                                    # line 12
+            rec = self._rec(y)                                    # reconstruction
             v = v.copy()
             v[:, s_breve] = rec[:, s_breve]
-            gam, info.filt_passes, _ = filt.spatial_filter(v, prev, cfg, t)  # line 13
+            gam, info.filt_passes, _ = filt.spatial_filter(v, prev, cfg, t)  # SpatialFilter
             self.y = y
         self.snaps[k] = gam
         self.k = k
         self.snaps.pop(k - cfg.w - 1, None)
 
-        if k == cfg.w - 1:                                        # lines 15-16
+        if k == cfg.w - 1:                                        # psi initialisation
             self.psi = rom.window_mean([self.snaps[j] for j in range(0, cfg.w)])
-        if self._rebuild_due(k):                                  # line 18
+        if self._rebuild_due(k):                                  # rebuild test
             info.rebuilt = True
-            if k >= cfg.w and self.Phi is not None:               # lines 19-20
+            if k >= cfg.w and self.Phi is not None:               # error indicator
                 y2 = self._gappy(gam)
                 eps = select.cell_error(self._flat(gam), self._flat(self.psi),
                                         self.Phi, y2, cfg.nvar)
                 self.G, info.n_g = select.select_cells(eps, cfg.sel_mode,
                                                        cfg.delta, cfg.top_frac)
             else:
-                self.G, info.n_g = np.zeros(0, np.int64), 0      # line 22
+                self.G, info.n_g = np.zeros(0, np.int64), 0      # no previous basis
             win = [self.snaps[j] for j in range(k - cfg.w + 1, k + 1)]
             Xc = np.stack([self._flat(g) - self._flat(self.psi) for g in win], axis=1)
             raw = float(np.sqrt(sum(float(np.sum(g * g)) for g in win)))
-            self.Phi, _ = rom.pod(Xc, cfg.m, cfg.pod_tol, cfg.pod_abs * raw)  # line 24
-            self.P = rom.odeim(self.Phi, cfg.n_p, cfg.tie_tol)    # line 25
+            self.Phi, _ = rom.pod(Xc, cfg.m, cfg.pod_tol, cfg.pod_abs * raw)  # POD
+            self.P = rom.odeim(self.Phi, cfg.n_p, cfg.tie_tol)    # ODEIM
             self.s_hat, self.s_tilde = select.build_masks(self.G, self.P, cfg)  # 26-28
-            self.psi = rom.window_mean(win)                       # line 29
+            self.psi = rom.window_mean(win)                       # psi update
         info.n_p = len(self.P)
         info.m_eff = 0 if self.Phi is None else self.Phi.shape[1]
         self.history.append(info)

@@ -77,7 +77,7 @@ def cell_residual(q, q_prev, cfg, t):
 
 
 def spatial_filter(q, q_prev, cfg, t):
-    """SpatialFilter of Algorithm 1 (line 13).  Returns (q_filtered,
+    """SpatialFilter of Algorithm 1.  Returns (q_filtered,
     passes_run, cells_kept_total)."""
     q = q.copy()
     passes = 0

@@ -205,7 +205,7 @@ def newton_be(q_prev, cfg, t, active=None, q_init=None):
 
     active: boolean mask over cells of the unknowns (Eq. partial_hdm2 with
     the other cells frozen at q_init); None means all cells (the full HDM
-    solve, Algorithm 1 line 4).  Stops when max|R_active| <= newton_tol *
+    solve, the full HDM step of Algorithm 1).  Stops when max|R_active| <= newton_tol *
     max(1, max|q_prev|) or after newton_max iterations.
     Returns (q, iterations, converged).  Burgers only.
     """
@@ -231,7 +231,7 @@ def newton_be(q_prev, cfg, t, active=None, q_init=None):
 
 
 def full_step(q_prev, cfg, k):
-    """Full HDM snapshot at step k (Algorithm 1 line 4): gamma_k = F_k(gamma_k)."""
+    """Full HDM snapshot at step k (Algorithm 1): gamma_k = F_k(gamma_k)."""
     t = k * cfg.dt
     if cfg.scheme == W.SCHEME_BE:
         q, _, _ = newton_be(q_prev, cfg, t)

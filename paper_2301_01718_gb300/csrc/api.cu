@@ -284,7 +284,7 @@ void gram_update(hyrom_ctx* c, int64_t step) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1, lines 3-14
+// Algorithm 1, advance part: full-step test, full HDM step or hybrid step
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -372,12 +372,12 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
       if (yo != ctx->y)
         CK(cudaMemcpyAsync(ctx->y, yo, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
     }
-    // line 12: reconstruction on S-breve
+    // reconstruction on S-breve
     t_begin(ctx, HYROM_T_RECON);
     hy::launch_reconstruct<T>(phi, ctx->N, ctx->nc, ctx->m_eff, ctx->y, psi, ctx->shat, 0, q,
                               ctx->st);
     t_end(ctx, HYROM_T_RECON);
-    // line 13: SpatialFilter
+    // SpatialFilter
     t_begin(ctx, HYROM_T_FILTER);
     if (cf.n_filt > 0)
       hy::launch_filter_sparse<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp,
@@ -403,7 +403,8 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1, lines 15-30
+// Algorithm 1, basis-update part: psi initialisation, rebuild test, selection,
+// POD, ODEIM, sampling sets, psi update
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -449,9 +450,8 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
       hy::launch_gram_center_explicit(ctx->H, nslot, ctx->win_dev, w, ctx->hp, ctx->pp, ctx->Gc,
                                       wp, ctx->xraw2, ctx->st);
     }
-    if (hy::run_jacobi_multi(ctx->Gc, wp, ctx->V, ctx->lam, ctx->jbuf, ctx->rotated,
-                             (int*)ctx->host + 8, ctx->xraw2 + 1, (double*)ctx->host + 8, 60,
-                             ctx->st) < 0)
+    if (hy::run_psd_eig(ctx->Gc, wp, ctx->V, ctx->lam, ctx->jbuf, ctx->rotated,
+                        (int*)ctx->host + 8, 60, ctx->st) < 0)
       return fail(ctx, HYROM_ECUDA, "Jacobi eigensolver: %s", cudaGetErrorString(cudaGetLastError()));
     hy::launch_pod_coeffs<T>(ctx->lam, ctx->V, wp, w, cf.m, cf.pod_tol, cf.pod_abs, ctx->xraw2,
                              ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
@@ -499,7 +499,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   else
     memset(&inf, 0, sizeof inf);
   inf.k = k;
-  if (k == w - 1) {  // lines 15-16: psi_{w-1} = mean(gamma_0..gamma_{w-1})
+  if (k == w - 1) {  // psi initialisation: psi_{w-1} = mean(gamma_0..gamma_{w-1})
     std::vector<int> win(w);
     ctx->psi_steps.clear();
     for (int i = 0; i < w; ++i) {
@@ -520,7 +520,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   if (!ctx->psi_set) return fail(ctx, HYROM_ESTATE, "no reference state at step %lld", (long long)k);
   inf.rebuilt = 1;
   const T* gk = ring_at<T>(ctx, k);
-  // lines 19-22: G_{k+1} from the reconstruction error of the final gamma_k
+  // selection: G_{k+1} from the reconstruction error of the final gamma_k
   const uint32_t* gbm = nullptr;
   int64_t n_g = 0;
   if (k >= w && ctx->has_basis) {
@@ -541,7 +541,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     gbm = ctx->g_bm;
   }
   inf.n_g = (int32_t)n_g;
-  // line 24: POD of the window centred at the psi in effect
+  // POD of the window centred at the psi in effect
   std::vector<int> win(w);
   for (int i = 0; i < w; ++i) win[i] = slot_of(ctx, k - w + 1 + i);
   std::vector<int> ps;
@@ -555,7 +555,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
                             ps_ok ? &ps : nullptr, (T*)ctx->phi, (T*)ctx->psi_next, &me);
   if (s) return s;
   ctx->m_eff = me;
-  // line 25: ODEIM points
+  // ODEIM points
   ctx->np_eff = 0;
   if (me > 0) {
     int np = cf.n_p;
@@ -570,13 +570,13 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
                              ctx->status, ctx->st);
     t_end(ctx, HYROM_T_ODEIM);
   }
-  // lines 26-28: sampling sets
+  // sampling sets
   if ((s = masks_and_tiles<T>(ctx, gbm, ctx->pts, ctx->np_eff, ctx->shat, ctx->stilde, &ctx->n_s)))
     return s;
   if (cf.scheme == HYROM_SCHEME_RK2)
     hy::launch_active_tiles(ctx->dc, ctx->shat, hy::rk2_tile_width(ctx->dc),
                             hy::rk2_tile_height(ctx->dc), ctx->tiles, ctx->ntiles, ctx->st);
-  // line 29: psi_{k+1} = mean of the window
+  // psi update: psi_{k+1} = mean of the window
   std::swap(ctx->psi, ctx->psi_next);
   ctx->psi_steps.clear();
   for (int i = 0; i < w; ++i) ctx->psi_steps.push_back(k - w + 1 + i);
@@ -687,7 +687,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->lam, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->sig, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->xraw2, 64);
-  ok &= dal(ctx, &ctx->jbuf, (size_t)2 * wp * wp * sizeof(double));
+  ok &= dal(ctx, &ctx->jbuf, ((size_t)2 * wp * wp + 512) * sizeof(double));
   ok &= dal(ctx, &ctx->m_eff_dev, 64);
   ok &= dalloc(ctx, &ctx->C, (size_t)wp * m * es);
   ok &= dal(ctx, &ctx->Cd, (size_t)wp * m * sizeof(double));

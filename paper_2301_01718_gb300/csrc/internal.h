@@ -87,6 +87,8 @@ void launch_identity(double* V, int n, cudaStream_t s);
 int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
                      int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
                      cudaStream_t s);
+int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
+                int* host_flag, int max_sweeps, cudaStream_t s);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
 template <typename T>
 void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,

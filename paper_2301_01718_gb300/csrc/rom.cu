@@ -4,7 +4,7 @@
 //    pseudo-inverse of the n_p x m sampled basis is formed once per basis
 //    (Householder QR in FP64, one CTA) and applied per solve (an m x n_p
 //    FP64 GEMV).
-//  * reconstruction psi + Phi y on S-breve (Algorithm 1 line 12) and the
+//  * reconstruction psi + Phi y on S-breve (Algorithm 1) and the
 //    pointwise reconstruction error per cell (Sec. 2.3.3): HBM-bound GEMVs
 //    over Phi (column-major, so each column read is coalesced).
 //  * POD_m (Eq. pod), two implementations:
@@ -12,13 +12,14 @@
 //        one CTA per column pair per round; relative accuracy of the small
 //        singular values is that of the data.
 //      FP32 states: the snapshot-ring Gram matrix H_ij = gamma_i . gamma_j is
-//        kept up to date with one new row per snapshot (FP64 accumulation of
-//        FP32 products), centred by the identity
+//        kept up to date with one new row per snapshot (float-float
+//        accumulation of exact FP32 products), centred by the identity
 //        (X - psi 1^T)^T (X - psi 1^T) = H - h 1^T - 1 h^T + (psi.psi) 1 1^T
-//        with psi the mean of ring slots, diagonalised by two-sided Jacobi in
-//        FP64 (one CTA), and Phi = X_c V_m Sigma_m^{-1} is formed in one pass
-//        over the window that also produces the next reference state psi
-//        (Eq. mean).
+//        with psi the mean of ring slots, diagonalised in FP64 by pivoted
+//        Cholesky and one-sided Jacobi (one thread-block cluster), and
+//        Phi = X_c V_m Sigma_m^{-1} is formed in one pass over the window
+//        that also produces the next reference state psi (Eq. mean).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -597,6 +598,319 @@ int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf
   return sw;
 }
 
+// ---------------------------------------------------------------------------
+// Eigenpairs of a symmetric positive semidefinite G (n x n, n <= 136) by
+// pivoted Cholesky and one-sided Jacobi (the preconditioned Jacobi SVD of
+// Drmac and Veselic, SIAM J. Matrix Anal. Appl. 29, 2008):
+// Pi^T G Pi = R^T R with the pivot the largest remaining diagonal entry, to
+// the numerical rank r where that entry drops below n eps max(diag G); the r
+// columns of B = R^T (n x r) are then made mutually orthogonal by plane
+// rotations, B V = U S, so that G = (Pi U) S^2 (Pi U)^T.  The pivoting grades
+// the columns of B and the rotations converge in a few sweeps (two-sided
+// Jacobi on G needs about one sweep per decade of its spectrum).  Eigenvalue
+// j is |b_j|^2 and its eigenvector Pi b_j / |b_j|; no rotation is
+// accumulated.
+// ---------------------------------------------------------------------------
+
+constexpr int kEigMaxN = 136;
+
+// Pivoted Cholesky in one CTA with G in shared memory (logical order through
+// piv, so rows and columns are never moved).  B (column k = row k of R over
+// the logical columns) and piv go to global memory, r to *rank.
+__global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, int ldg, int n,
+                                                double* __restrict__ B, int* __restrict__ piv_out,
+                                                int* __restrict__ rank_out) {
+  extern __shared__ double A[];  // n x n
+  __shared__ int piv[kEigMaxN];
+  __shared__ double rk[kEigMaxN];
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int pk_s, stop_s;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx - i * n;
+    A[idx] = G[(int64_t)i * ldg + j];
+    B[idx] = 0.0;
+  }
+  for (int i = tid; i < n; i += nt) piv[i] = i;
+  __syncthreads();
+  double m0 = 0.0;
+  for (int i = tid; i < n; i += nt) m0 = fmax(m0, A[i * n + i]);
+  m0 = block_max(m0);
+  const double tol = n * 2.220446049250313e-16 * m0;
+  int r = n;
+  for (int k = 0; k < n; ++k) {
+    // largest remaining diagonal entry (lowest logical index on ties)
+    double best = -1.0;
+    int bidx = k;
+    for (int i = k + tid; i < n; i += nt) {
+      const double v = A[piv[i] * n + piv[i]];
+      if (v > best) {
+        best = v;
+        bidx = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ov > best || (ov == best && oi < bidx)) {
+        best = ov;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) {
+      bv[wid] = best;
+      bi[wid] = bidx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = bv[0];
+      int ix = bi[0];
+      for (int w2 = 1; w2 < (nt >> 5); ++w2)
+        if (bv[w2] > b || (bv[w2] == b && bi[w2] < ix)) {
+          b = bv[w2];
+          ix = bi[w2];
+        }
+      pk_s = ix;
+      stop_s = !(b > tol);
+      if (!stop_s && ix != k) {
+        const int t = piv[k];
+        piv[k] = piv[ix];
+        piv[ix] = t;
+      }
+    }
+    __syncthreads();
+    if (stop_s) {
+      r = k;
+      break;
+    }
+    const int sw = pk_s;
+    if (sw != k)  // the computed rows of R follow the column exchange
+      for (int i = tid; i < k; i += nt) {
+        const double t = B[i * n + k];
+        B[i * n + k] = B[i * n + sw];
+        B[i * n + sw] = t;
+      }
+    const int pk = piv[k];
+    const double rkk = sqrt(A[pk * n + pk]);
+    for (int j = k + tid; j < n; j += nt) {
+      const double v = j == k ? rkk : A[pk * n + piv[j]] / rkk;
+      rk[j] = v;
+      B[k * n + j] = v;
+    }
+    __syncthreads();
+    const int s = n - k - 1;
+    for (int idx = tid; idx < s * s; idx += nt) {
+      const int i = k + 1 + idx / s, j = k + 1 + idx % s;
+      A[piv[i] * n + piv[j]] -= rk[i] * rk[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *rank_out = r;
+  for (int i = tid; i < n; i += nt) piv_out[i] = piv[i];
+}
+
+// One sweep (r' - 1 rounds, r' = r rounded up to even) of one-sided Jacobi
+// on the columns of B in one cooperative launch; CTA b rotates pair b of the
+// round in place (pairs of a round are disjoint).
+__global__ void k_osj_sweep(double* B, int n, const int* __restrict__ rank, double tol,
+                            int* rotated, GridBar* bar, int* err) {
+  __shared__ double cp[kEigMaxN], cq[kEigMaxN];
+  __shared__ double red[3][32];
+  const int r = *rank, rp = (r + 1) & ~1;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int rd = 0; rd < rp - 1; ++rd) {
+    if ((int)blockIdx.x < rp / 2) {
+      int p, q;
+      rr_pair(rp, rd, blockIdx.x, p, q);
+      if (q < r) {
+        double a = 0.0, c = 0.0, g = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) {
+          const double x = __ldcg(B + (int64_t)p * n + i), y = __ldcg(B + (int64_t)q * n + i);
+          cp[i] = x;
+          cq[i] = y;
+          a = fma(x, x, a);
+          c = fma(y, y, c);
+          g = fma(x, y, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (lane == 0) {
+          red[0][wid] = a;
+          red[1][wid] = c;
+          red[2][wid] = g;
+        }
+        __syncthreads();
+        a = red[0][0];
+        c = red[1][0];
+        g = red[2][0];
+        for (int w2 = 1; w2 < nw; ++w2) {
+          a += red[0][w2];
+          c += red[1][w2];
+          g += red[2][w2];
+        }
+        if (fabs(g) > tol * sqrt(a * c) && a > 0.0 && c > 0.0) {
+          const double zeta = (c - a) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = tid; i < n; i += blockDim.x) {
+            B[(int64_t)p * n + i] = cs * cp[i] - sn * cq[i];
+            B[(int64_t)q * n + i] = sn * cp[i] + cs * cq[i];
+          }
+          if (tid == 0) *rotated = 1;
+        }
+      }
+    }
+    if (!grid_sync_bounded(bar, gridDim.x, err)) return;
+  }
+}
+
+// All sweeps in one launch of one 16-CTA thread-block cluster: column j of B
+// lives in the shared memory of CTA j % 16 (slot j / 16); in each round,
+// pair b goes to CTA b % 16, one warp per pair, which reads both columns
+// through distributed shared memory, rotates them and writes them back.
+// A cluster barrier ends each round.  Every CTA runs the same number of
+// rounds and barriers: after a sweep all read the same rotation flag (kept
+// in CTA 0, one per sweep parity) and stop together; at most max_sweeps.
+constexpr int kOsjCta = 16;
+constexpr int kOsjSlots = (kEigMaxN + kOsjCta - 1) / kOsjCta;
+
+__global__ void __launch_bounds__(256) k_osj_cluster(double* __restrict__ B, int n,
+                                                     const int* __restrict__ rank, double tol,
+                                                     int max_sweeps, int* __restrict__ sweeps_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double col[kOsjSlots][kEigMaxN];
+  __shared__ int rot_flag[2];
+  const int me = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r = *rank, rp = (r + 1) & ~1;
+  for (int idx = threadIdx.x; idx < kOsjSlots * n; idx += blockDim.x) {
+    const int sl = idx / n, i = idx - sl * n;
+    const int j = sl * kOsjCta + me;
+    col[sl][i] = j < r ? B[(int64_t)j * n + i] : 0.0;
+  }
+  if (threadIdx.x < 2) rot_flag[threadIdx.x] = 0;
+  cl.sync();
+  int* flag0 = cl.map_shared_rank(&rot_flag[0], 0);
+  int sw = 0;
+  for (; sw < max_sweeps; ++sw) {
+    for (int rd = 0; rd < rp - 1; ++rd) {
+      for (int b = me + kOsjCta * wid; b < rp / 2; b += kOsjCta * nw) {
+        int p, q;
+        rr_pair(rp, rd, b, p, q);
+        if (q >= r) continue;
+        double* cp = cl.map_shared_rank(&col[p / kOsjCta][0], p % kOsjCta);
+        double* cq = cl.map_shared_rank(&col[q / kOsjCta][0], q % kOsjCta);
+        double xv[5], yv[5];
+        double a = 0.0, c = 0.0, g = 0.0;
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          const int i = lane + 32 * u;
+          xv[u] = i < n ? cp[i] : 0.0;
+          yv[u] = i < n ? cq[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          a = fma(xv[u], xv[u], a);
+          c = fma(yv[u], yv[u], c);
+          g = fma(xv[u], yv[u], g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (fabs(g) > tol * sqrt(a * c) && a > 0.0 && c > 0.0) {
+          const double zeta = (c - a) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+#pragma unroll
+          for (int u = 0; u < 5; ++u) {
+            const int i = lane + 32 * u;
+            if (i < n) {
+              cp[i] = cs * xv[u] - sn * yv[u];
+              cq[i] = sn * xv[u] + cs * yv[u];
+            }
+          }
+          if (lane == 0) atomicOr(flag0 + (sw & 1), 1);
+        }
+      }
+      cl.sync();
+    }
+    const int rotated = *((volatile int*)(flag0 + (sw & 1)));
+    cl.sync();  // everyone has read this sweep's flag before it is reused
+    if (me == 0 && threadIdx.x == 0) rot_flag[(sw + 1) & 1] = 0;
+    cl.sync();
+    if (!rotated) break;
+  }
+  for (int idx = threadIdx.x; idx < kOsjSlots * n; idx += blockDim.x) {
+    const int sl = idx / n, i = idx - sl * n;
+    const int j = sl * kOsjCta + me;
+    if (j < r) B[(int64_t)j * n + i] = col[sl][i];
+  }
+  if (me == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+}
+
+// lam[j] = |b_j|^2 and V[:, j] = Pi b_j / |b_j| for j < r; zero beyond.
+__global__ void k_osj_finish(const double* __restrict__ B, int n, const int* __restrict__ rank,
+                             const int* __restrict__ piv, double* __restrict__ lam,
+                             double* __restrict__ V) {
+  const int j = blockIdx.x;
+  const int r = *rank;
+  double s = 0.0;
+  if (j < r)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double x = B[(int64_t)j * n + i];
+      s = fma(x, x, s);
+    }
+  s = block_sum(s);
+  const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  if (threadIdx.x == 0) lam[j] = j < r ? s : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    V[(int64_t)j * n + piv[i]] = j < r ? B[(int64_t)j * n + i] * inv : 0.0;
+}
+
+// G (n x n, ld n) -> lam (n), V (n x n column-major).  buf: n * n doubles
+// and 2 * kEigMaxN ints; flag: 4 ints (rotated, timeout, barrier).  Returns
+// the sweeps run, -1 on a CUDA error, -2 when a grid barrier timed out.
+int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
+                int* host_flag, int max_sweeps, cudaStream_t s) {
+  if (n > kEigMaxN) return -1;
+  double* B = buf;
+  int* piv = reinterpret_cast<int*>(buf + (size_t)n * n);
+  int* rank = piv + kEigMaxN;
+  const size_t smem = sizeof(double) * (size_t)n * n;
+  cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pchol<<<1, 1024, smem, HY_S(s)>>>(G, n, n, B, piv, rank);
+  (void)flag;
+  (void)host_flag;
+  const double tol = 1e-14;
+  cudaFuncSetAttribute(k_osj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(kOsjCta);
+  lc.blockDim = dim3(256);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kOsjCta;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  ::hy::count_launch();
+  if (cudaLaunchKernelEx(&lc, k_osj_cluster, B, n, (const int*)rank, tol, max_sweeps,
+                         (int*)nullptr) != cudaSuccess)
+    return -1;
+  const int sw = 0;
+  k_osj_finish<<<n, 128, 0, HY_S(s)>>>(B, n, rank, piv, lam, V);
+  return sw;
+}
+
 // Order eigenpairs (lam[0..n), columns of V; V = NULL means the identity)
 // by descending eigenvalue into
 // sig (sqrt(max(lam, 0))) and perm; m_eff by the rank rule
@@ -745,34 +1059,61 @@ __global__ void __launch_bounds__(256, 2) k_form_phi_tiled(
   const bool vec = (N & 3) == 0;
   for (int64_t base = (int64_t)blockIdx.x * TR; base < N; base += (int64_t)gridDim.x * TR) {
     __syncthreads();  // Cs/ws ready; the previous tile's Xs fully consumed
-    for (int idx = tid; idx < w * (TR / 4); idx += blockDim.x) {
-      const int k = idx / (TR / 4), q = idx % (TR / 4);
-      const int64_t r0 = base + 4 * q;
-      const float* src = ring + (int64_t)ws[k] * N + r0;
-      float4 v;
-      if (vec && r0 + 3 < N) {
-        v = __ldg(reinterpret_cast<const float4*>(src));
-      } else {
-        v.x = r0 < N ? src[0] : 0.f;
-        v.y = r0 + 1 < N ? src[1] : 0.f;
-        v.z = r0 + 2 < N ? src[2] : 0.f;
-        v.w = r0 + 3 < N ? src[3] : 0.f;
+    // stage the raw values: all (at most 16) loads of a thread in flight
+    // before the first store
+    {
+      float4 buf[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int idx = tid + u * 256;
+        if (idx < w * (TR / 4)) {
+          const int k = idx >> 5, q = idx & 31;
+          const int64_t r0 = base + 4 * q;
+          const float* src = ring + (int64_t)ws[k] * N + r0;
+          if (vec && r0 + 3 < N) {
+            buf[u] = __ldg(reinterpret_cast<const float4*>(src));
+          } else {
+            buf[u].x = r0 < N ? src[0] : 0.f;
+            buf[u].y = r0 + 1 < N ? src[1] : 0.f;
+            buf[u].z = r0 + 2 < N ? src[2] : 0.f;
+            buf[u].w = r0 + 3 < N ? src[3] : 0.f;
+          }
+        }
       }
-      *reinterpret_cast<float4*>(Xs + k * TR + 4 * q) = v;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int idx = tid + u * 256;
+        if (idx < w * (TR / 4))
+          *reinterpret_cast<float4*>(Xs + (idx >> 5) * TR + 4 * (idx & 31)) = buf[u];
+      }
     }
     __syncthreads();
-    if (tid < TR) {
-      const int64_t r = base + tid;
+    {
+      // two threads per row, each over half of the window: Kahan partial
+      // sums of the raw values, then the row is centred in place
+      __shared__ float part_s[2][TR], part_c[2][TR];
+      const int row = tid & (TR - 1), half = tid >> 7;
+      const int64_t r = base + row;
       const float pr = r < N ? psi[r] : 0.f;
-      float sum = 0.f, comp = 0.f;  // Kahan-compensated window sum
-      for (int k = 0; k < w; ++k) {
-        const float g = Xs[k * TR + tid];
+      const int k0 = half ? w / 2 : 0, k1 = half ? w : w / 2;
+      float sum = 0.f, comp = 0.f;
+      for (int k = k0; k < k1; ++k) {
+        const float g = Xs[k * TR + row];
         const float yk = g - comp, tk = sum + yk;
         comp = (tk - sum) - yk;
         sum = tk;
-        Xs[k * TR + tid] = g - pr;
+        Xs[k * TR + row] = g - pr;
       }
-      if (r < N) psi_next[r] = sum / (float)w;
+      part_s[half][row] = sum;
+      part_c[half][row] = comp;
+      __syncthreads();
+      if (half == 0 && r < N) {
+        // (s0 - c0) + (s1 - c1) with the rounding of s0 + s1 recovered
+        const float s0 = part_s[0][row], s1 = part_s[1][row];
+        const float a = s0 + s1, bb = a - s0;
+        const float e = (s0 - (a - bb)) + (s1 - bb);
+        psi_next[r] = (a + (e - (part_c[0][row] + part_c[1][row]))) / (float)w;
+      }
     }
     __syncthreads();
     float acc[8][CT];

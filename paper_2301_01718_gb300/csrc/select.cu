@@ -1,5 +1,5 @@
 // Error-indicator selection and sampling sets: Sec. 2.3.3 (RRE ordering,
-// Eq. rre, S-hat = G union P) and Algorithm 1 lines 26-28 (union, setdiff,
+// Eq. rre, S-hat = G union P) and the sampling-set steps of Algorithm 1 (union, setdiff,
 // Neighbors; Fig. 1).
 //
 // Exact selection: each cell's error eps maps to an integer key

@@ -190,7 +190,7 @@ def hyrom_profile(ctx, on=True):
 def hyrom_odeim_counters(ctx):
     out = (C.c_int64 * 4)()
     _check(ctx, lib().hyrom_odeim_counters(ctx, out))
-    return {"deim_rows": out[0], "odeim_screened": out[1], "odeim_exact": out[2],
+    return {"deim_rows": out[0], "odeim_full_bound": out[1], "odeim_exact": out[2],
             "odeim_steps": out[3]}
 
 

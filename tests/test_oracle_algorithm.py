@@ -1,5 +1,5 @@
 """Pins of the oracle's Algorithm 1 driver: the full/hybrid/rebuild schedule
-(an integer sequence fixed by lines 3 and 18 of the algorithm, written out
+(an integer sequence fixed by the full-step and rebuild tests of the algorithm, written out
 by hand below), the all-cells invariant (a hybrid step whose sampled set is
 every cell, with the filter off, is the full HDM step), exact
 reproduction of a state in the reduced affine subspace, and a steady state.
@@ -55,7 +55,7 @@ def test_all_cells_hybrid_step_is_the_full_hdm_step(scheme):
 
 
 def test_state_in_the_affine_subspace_is_reproduced():
-    """Reconstruction (Algorithm 1 line 12) from the gappy coordinates of a
+    """Reconstruction on S-breve (Algorithm 1) from the gappy coordinates of a
     state psi + Phi a returns that state on every cell."""
     u0, cfg = _tiny_burgers()
     g = np.random.Generator(np.random.PCG64(1))
