@@ -614,17 +614,19 @@ int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf
 
 constexpr int kEigMaxN = 136;
 
-// Pivoted Cholesky in one CTA with G in shared memory (logical order through
-// piv, so rows and columns are never moved).  B (column k = row k of R over
-// the logical columns) and piv go to global memory, r to *rank.
+// Pivoted Cholesky in one CTA, the lower triangle of G in shared memory;
+// the pivot exchange swaps rows and columns in place (O(n) entries), so the
+// trailing update walks contiguous rows.  FP64 throughput bounds this
+// kernel: the update is s (s + 1) / 2 explicit FMAs at trailing size s.
+// B (column k = row k of R over the pivoted order), piv and r go to global
+// memory.
 __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, int ldg, int n,
                                                 double* __restrict__ B, int* __restrict__ piv_out,
                                                 int* __restrict__ rank_out) {
-  extern __shared__ double A[];  // n x n
+  extern __shared__ double A[];  // n x n, lower triangle used
   __shared__ int piv[kEigMaxN];
   __shared__ double rk[kEigMaxN];
-  __shared__ double bv[32];
-  __shared__ int bi[32];
+  __shared__ double rk_s[2];
   __shared__ int pk_s, stop_s;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
   for (int idx = tid; idx < n * n; idx += nt) {
@@ -640,43 +642,33 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
   const double tol = n * 2.220446049250313e-16 * m0;
   int r = n;
   for (int k = 0; k < n; ++k) {
-    // largest remaining diagonal entry (lowest logical index on ties)
-    double best = -1.0;
-    int bidx = k;
-    for (int i = k + tid; i < n; i += nt) {
-      const double v = A[piv[i] * n + piv[i]];
-      if (v > best) {
-        best = v;
-        bidx = i;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ov > best || (ov == best && oi < bidx)) {
-        best = ov;
-        bidx = oi;
-      }
-    }
-    if (lane == 0) {
-      bv[wid] = best;
-      bi[wid] = bidx;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double b = bv[0];
-      int ix = bi[0];
-      for (int w2 = 1; w2 < (nt >> 5); ++w2)
-        if (bv[w2] > b || (bv[w2] == b && bi[w2] < ix)) {
-          b = bv[w2];
-          ix = bi[w2];
+    // largest remaining diagonal entry (lowest index on ties), one warp
+    if (wid == 0) {
+      double best = -1.0;
+      int bidx = k;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = A[i * n + i];
+        if (v > best) {
+          best = v;
+          bidx = i;
         }
-      pk_s = ix;
-      stop_s = !(b > tol);
-      if (!stop_s && ix != k) {
-        const int t = piv[k];
-        piv[k] = piv[ix];
-        piv[ix] = t;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ov > best || (ov == best && oi < bidx)) {
+          best = ov;
+          bidx = oi;
+        }
+      }
+      if (lane == 0) {
+        pk_s = bidx;
+        stop_s = !(best > tol);
+        if (!stop_s && bidx != k) {
+          const int t = piv[k];
+          piv[k] = piv[bidx];
+          piv[bidx] = t;
+        }
       }
     }
     __syncthreads();
@@ -684,25 +676,48 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
       r = k;
       break;
     }
-    const int sw = pk_s;
-    if (sw != k)  // the computed rows of R follow the column exchange
+    const int p = pk_s;
+    if (p != k) {
+      // symmetric exchange of k and p on the trailing lower triangle, and of
+      // columns k and p of the rows of R already formed
+      if (tid == 0) {
+        const double t = A[k * n + k];
+        A[k * n + k] = A[p * n + p];
+        A[p * n + p] = t;
+      }
+      for (int i = k + 1 + tid; i < n; i += nt) {
+        if (i < p) {  // (i, k) <-> (p, i)
+          const double t = A[i * n + k];
+          A[i * n + k] = A[p * n + i];
+          A[p * n + i] = t;
+        } else if (i > p) {  // (i, k) <-> (i, p)
+          const double t = A[i * n + k];
+          A[i * n + k] = A[i * n + p];
+          A[i * n + p] = t;
+        }
+      }
       for (int i = tid; i < k; i += nt) {
         const double t = B[i * n + k];
-        B[i * n + k] = B[i * n + sw];
-        B[i * n + sw] = t;
+        B[i * n + k] = B[i * n + p];
+        B[i * n + p] = t;
       }
-    const int pk = piv[k];
-    const double rkk = sqrt(A[pk * n + pk]);
+    }
+    if (tid == 0) {
+      const double rkk = sqrt(A[k * n + k]);
+      rk_s[0] = rkk;
+      rk_s[1] = 1.0 / rkk;
+    }
+    __syncthreads();
     for (int j = k + tid; j < n; j += nt) {
-      const double v = j == k ? rkk : A[pk * n + piv[j]] / rkk;
+      const double v = j == k ? rk_s[0] : A[j * n + k] * rk_s[1];
       rk[j] = v;
       B[k * n + j] = v;
     }
     __syncthreads();
-    const int s = n - k - 1;
-    for (int idx = tid; idx < s * s; idx += nt) {
-      const int i = k + 1 + idx / s, j = k + 1 + idx % s;
-      A[piv[i] * n + piv[j]] -= rk[i] * rk[j];
+    // trailing lower triangle: rows i > k, columns k < j <= i
+    for (int i = k + 1 + wid; i < n; i += nt >> 5) {
+      const double ri = rk[i];
+      for (int j = k + 1 + lane; j <= i; j += 32) A[i * n + j] = fma(-ri, rk[j], A[i * n + j]);
     }
     __syncthreads();
   }
@@ -769,14 +784,19 @@ __global__ void k_osj_sweep(double* B, int n, const int* __restrict__ rank, doub
 }
 
 // All sweeps in one launch of one 16-CTA thread-block cluster: column j of B
-// lives in the shared memory of CTA j % 16 (slot j / 16); in each round,
-// pair b goes to CTA b % 16, one warp per pair, which reads both columns
-// through distributed shared memory, rotates them and writes them back.
-// A cluster barrier ends each round.  Every CTA runs the same number of
-// rounds and barriers: after a sweep all read the same rotation flag (kept
-// in CTA 0, one per sweep parity) and stop together; at most max_sweeps.
+// lives in the shared memory of CTA j % 16 (slot j / 16).  In each round
+// pair b goes to CTA b % 16 and to a group of 8 lanes there, which reads both
+// columns through distributed shared memory, forms their inner product,
+// rotates them and writes them back; a cluster barrier ends the round.  The
+// squared column norms are formed at the start of each sweep and carried
+// through the rotations exactly as the rotation changes them
+// (a' = a - t g, c' = c + t g), so a pair costs one inner product.  Every
+// CTA runs the same number of rounds and barriers: after a sweep all read
+// the same rotation flag (kept in CTA 0, one per sweep parity) and stop
+// together; at most max_sweeps.
 constexpr int kOsjCta = 16;
 constexpr int kOsjSlots = (kEigMaxN + kOsjCta - 1) / kOsjCta;
+constexpr int kOsjLanes = 8;  // lanes per pair
 
 __global__ void __launch_bounds__(256) k_osj_cluster(double* __restrict__ B, int n,
                                                      const int* __restrict__ rank, double tol,
@@ -784,75 +804,95 @@ __global__ void __launch_bounds__(256) k_osj_cluster(double* __restrict__ B, int
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double col[kOsjSlots][kEigMaxN];
+  __shared__ double nrm2[kOsjSlots];
   __shared__ int rot_flag[2];
   const int me = (int)cl.block_rank();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int gl = tid & (kOsjLanes - 1), grp = tid / kOsjLanes;  // lane in group, group
+  const int ngrp = blockDim.x / kOsjLanes;
   const int r = *rank, rp = (r + 1) & ~1;
-  for (int idx = threadIdx.x; idx < kOsjSlots * n; idx += blockDim.x) {
+  for (int idx = tid; idx < kOsjSlots * n; idx += blockDim.x) {
     const int sl = idx / n, i = idx - sl * n;
     const int j = sl * kOsjCta + me;
     col[sl][i] = j < r ? B[(int64_t)j * n + i] : 0.0;
   }
-  if (threadIdx.x < 2) rot_flag[threadIdx.x] = 0;
+  if (tid < 2) rot_flag[tid] = 0;
   cl.sync();
   int* flag0 = cl.map_shared_rank(&rot_flag[0], 0);
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
+    // squared norms of the local columns (one warp per slot)
+    for (int sl = wid; sl < kOsjSlots; sl += blockDim.x >> 5) {
+      double a = 0.0;
+      for (int i = lane; i < n; i += 32) a = fma(col[sl][i], col[sl][i], a);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) nrm2[sl] = a;
+    }
+    cl.sync();
     for (int rd = 0; rd < rp - 1; ++rd) {
-      for (int b = me + kOsjCta * wid; b < rp / 2; b += kOsjCta * nw) {
-        int p, q;
-        rr_pair(rp, rd, b, p, q);
-        if (q >= r) continue;
+      // every group runs the same number of iterations, so the 8-lane
+      // shuffles below always see their whole group
+      for (int b0 = 0; b0 < rp / 2; b0 += kOsjCta * ngrp) {
+        const int b = b0 + me + kOsjCta * grp;
+        int p = 0, q = 0;
+        if (b < rp / 2) rr_pair(rp, rd, b, p, q);
+        const bool act = b < rp / 2 && q < r;
         double* cp = cl.map_shared_rank(&col[p / kOsjCta][0], p % kOsjCta);
         double* cq = cl.map_shared_rank(&col[q / kOsjCta][0], q % kOsjCta);
-        double xv[5], yv[5];
-        double a = 0.0, c = 0.0, g = 0.0;
+        double* np_ = cl.map_shared_rank(&nrm2[p / kOsjCta], p % kOsjCta);
+        double* nq_ = cl.map_shared_rank(&nrm2[q / kOsjCta], q % kOsjCta);
+        // all of a lane's elements are loaded before any is used
+        constexpr int kPer = (kEigMaxN + kOsjLanes - 1) / kOsjLanes;
+        double xv[kPer], yv[kPer];
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          const int i = lane + 32 * u;
-          xv[u] = i < n ? cp[i] : 0.0;
-          yv[u] = i < n ? cq[i] : 0.0;
+        for (int u = 0; u < kPer; ++u) {
+          const int i = gl + kOsjLanes * u;
+          xv[u] = act && i < n ? cp[i] : 0.0;
+          yv[u] = act && i < n ? cq[i] : 0.0;
         }
+        const double a = act ? *np_ : 0.0, c = act ? *nq_ : 0.0;
+        double g0 = 0.0, g1 = 0.0;
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          a = fma(xv[u], xv[u], a);
-          c = fma(yv[u], yv[u], c);
-          g = fma(xv[u], yv[u], g);
+        for (int u = 0; u < kPer; u += 2) {
+          g0 = fma(xv[u], yv[u], g0);
+          if (u + 1 < kPer) g1 = fma(xv[u + 1], yv[u + 1], g1);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          c += __shfl_xor_sync(0xffffffffu, c, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
+        double g = g0 + g1;
+        for (int o = kOsjLanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (!act) continue;
         if (fabs(g) > tol * sqrt(a * c) && a > 0.0 && c > 0.0) {
           const double zeta = (c - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
 #pragma unroll
-          for (int u = 0; u < 5; ++u) {
-            const int i = lane + 32 * u;
+          for (int u = 0; u < kPer; ++u) {
+            const int i = gl + kOsjLanes * u;
             if (i < n) {
-              cp[i] = cs * xv[u] - sn * yv[u];
-              cq[i] = sn * xv[u] + cs * yv[u];
+              cp[i] = fma(cs, xv[u], -sn * yv[u]);
+              cq[i] = fma(sn, xv[u], cs * yv[u]);
             }
           }
-          if (lane == 0) atomicOr(flag0 + (sw & 1), 1);
+          if (gl == 0) {
+            *np_ = fma(-t, g, a);
+            *nq_ = fma(t, g, c);
+            atomicOr(flag0 + (sw & 1), 1);
+          }
         }
       }
       cl.sync();
     }
     const int rotated = *((volatile int*)(flag0 + (sw & 1)));
     cl.sync();  // everyone has read this sweep's flag before it is reused
-    if (me == 0 && threadIdx.x == 0) rot_flag[(sw + 1) & 1] = 0;
+    if (me == 0 && tid == 0) rot_flag[(sw + 1) & 1] = 0;
     cl.sync();
     if (!rotated) break;
   }
-  for (int idx = threadIdx.x; idx < kOsjSlots * n; idx += blockDim.x) {
+  for (int idx = tid; idx < kOsjSlots * n; idx += blockDim.x) {
     const int sl = idx / n, i = idx - sl * n;
     const int j = sl * kOsjCta + me;
     if (j < r) B[(int64_t)j * n + i] = col[sl][i];
   }
-  if (me == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+  if (me == 0 && tid == 0 && sweeps_out) *sweeps_out = sw;
 }
 
 // lam[j] = |b_j|^2 and V[:, j] = Pi b_j / |b_j| for j < r; zero beyond.
