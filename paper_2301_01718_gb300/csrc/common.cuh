@@ -80,6 +80,26 @@ HY_DEV unsigned long long dkey(double x) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// Copy count values from global src to shared dst, the block's threads each
+// issuing up to U loads before their first store (small kernels are
+// otherwise bound by one global-memory latency per loop iteration).
+template <int U = 8, typename T>
+__device__ void stage_copy(T* dst, const T* __restrict__ src, int count) {
+  for (int base = threadIdx.x; base < count; base += blockDim.x * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * blockDim.x;
+      v[u] = i < count ? src[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < count) dst[i] = v[u];
+    }
+  }
+}
+
 template <typename T>
 HY_DEV T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

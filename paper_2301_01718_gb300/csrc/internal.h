@@ -88,7 +88,7 @@ int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf
                      int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
                      cudaStream_t s);
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
-                int* host_flag, int max_sweeps, cudaStream_t s);
+                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
 template <typename T>
 void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,

@@ -149,12 +149,29 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
   extern __shared__ double dsm[];
   double* Lt = dsm;            // Lt[i * 65 + j] = L[j][i]
   double* Ut = dsm + 64 * 65;  // Ut[i * 65 + j] = U[j][i]
-  const int lane = threadIdx.x;
-  for (int r = 0; r < l; ++r)
-    for (int c = lane; c < l; c += 32) {
-      Lt[c * 65 + r] = Lf[r * 64 + c];
-      Ut[c * 65 + r] = Uf[r * 64 + c];
+  // all threads stage (8 loads in flight each); warp 0 solves
+  for (int base = threadIdx.x; base < l * l; base += blockDim.x * 8) {
+    double lv[8], uv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int rr = idx / (l > 0 ? l : 1), cc = idx - rr * l;
+      lv[u] = idx < l * l ? Lf[rr * 64 + cc] : 0.0;
+      uv[u] = idx < l * l ? Uf[rr * 64 + cc] : 0.0;
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < l * l) {
+        const int rr = idx / l, cc = idx - rr * l;
+        Lt[cc * 65 + rr] = lv[u];
+        Ut[cc * 65 + rr] = uv[u];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   double b0 = 0.0, b1 = 0.0;  // right-hand side, entries lane and lane + 32
   if (lane < l) b0 = (double)phi[(int64_t)l * N + pts[lane]];
   if (lane + 32 < l) b1 = (double)phi[(int64_t)l * N + pts[lane + 32]];
@@ -209,10 +226,11 @@ __global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const
                               const double* __restrict__ yv) {
   // column-oriented solve of U^T ell = a with U^T's columns = U's rows
   __shared__ double Us[64 * 64];
-  const int lane = threadIdx.x;
   const int p = ctl->argmin;
-  for (int r = 0; r < l; ++r)
-    for (int c = lane; c < l; c += 32) Us[r * 64 + c] = Uf[r * 64 + c];
+  stage_copy(Us, Uf, l * 64);  // rows 0..l-1 (stride 64)
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   double a0 = 0.0, a1 = 0.0;
   if (lane < l) a0 = (double)phi[(int64_t)lane * N + p];
   if (lane + 32 < l) a1 = (double)phi[(int64_t)(lane + 32) * N + p];
@@ -411,10 +429,24 @@ __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
   const int lane = threadIdx.x & 31;
   double z0 = 0.0, z1 = 0.0;
   const int j0 = lane, j1 = lane + 32;
-  if (j0 < m)
-    for (int a = 0; a < m; ++a) z0 = fma(W[j0 * ldw + a], rb[a], z0);
-  if (j1 < m)
-    for (int a = 0; a < m; ++a) z1 = fma(W[j1 * ldw + a], rb[a], z1);
+  if (j0 < m || j1 < m) {  // two chains per component
+    double z0b = 0.0, z1b = 0.0;
+    const double* w0 = W + (j0 < m ? j0 : 0) * ldw;
+    const double* w1 = W + (j1 < m ? j1 : 0) * ldw;
+    int a = 0;
+    for (; a + 1 < m; a += 2) {
+      z0 = fma(w0[a], rb[a], z0);
+      z0b = fma(w0[a + 1], rb[a + 1], z0b);
+      z1 = fma(w1[a], rb[a], z1);
+      z1b = fma(w1[a + 1], rb[a + 1], z1b);
+    }
+    if (a < m) {
+      z0 = fma(w0[a], rb[a], z0);
+      z1 = fma(w1[a], rb[a], z1);
+    }
+    z0 = j0 < m ? z0 + z0b : 0.0;
+    z1 = j1 < m ? z1 + z1b : 0.0;
+  }
   const double q0 = z0 * z0, q1 = z1 * z1;
   const double zz = warp_sum(q0 + q1);
   const double zf = __shfl_sync(0xffffffffu, q0, 0);  // z_1^2
@@ -658,9 +690,21 @@ __global__ void __launch_bounds__(256) k_odeim_screen(
 // leading dimension, and the eigenvalues
 HY_DEV void stage_w(const double* __restrict__ W_s, const double* __restrict__ lam_s, int m,
                     double* W, double* lam) {
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const int j = i / m, a = i - j * m;
-    W[j * kLdw + a] = W_s[i];
+  for (int base = threadIdx.x; base < m * m; base += blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * blockDim.x;
+      v[u] = i < m * m ? W_s[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < m * m) {
+        const int j = i / m, a = i - j * m;
+        W[j * kLdw + a] = v[u];
+      }
+    }
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = lam_s[i];
 }
@@ -772,7 +816,7 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
     ph[a] = (double)phi[(int64_t)a * N + p];
     ds[a] = d[a];
   }
-  for (int i = tid; i < m * m; i += blockDim.x) Ws[i] = W[i];
+  stage_copy(Ws, W, m * m);
   __syncthreads();
   for (int j = wid; j < m; j += nw) {
     double acc = 0.0;
@@ -1014,6 +1058,7 @@ __global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __rest
                              double* __restrict__ lamnew) {
   __shared__ double zh[64], v[64], dK[64];
   __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
+  __shared__ double Ds[64 * 65];  // Delta rows, stride 65
   __shared__ int Ks[64];
   const int j = blockIdx.x, tid = threadIdx.x;
   const int nK = wk->nK;
@@ -1023,38 +1068,59 @@ __global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __rest
     Ks[i] = wk->K[i];
   }
   __syncthreads();
-  for (int idx = tid; idx < nK * m; idx += blockDim.x) {
-    const int i = idx / m, a = idx - i * m;
-    Wk[i * 65 + a] = Wrot[Ks[i] * m + a];
+  for (int base = tid; base < nK * 64; base += blockDim.x * 8) {
+    double wv[8], dv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int i = idx >> 6, a = idx & 63;
+      wv[u] = idx < nK * 64 && a < m ? Wrot[Ks[i] * m + a] : 0.0;
+      dv[u] = idx < nK * 64 && a < nK ? Delta[idx] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < nK * 64) {
+        Wk[(idx >> 6) * 65 + (idx & 63)] = wv[u];
+        Ds[(idx >> 6) * 65 + (idx & 63)] = dv[u];
+      }
+    }
   }
   __syncthreads();
   if (tid < nK) {
     // Loewner: zh_i^2 = (lambda_i - d_i) prod_{q != i} (lambda_q - d_i) / (d_q - d_i),
-    // the products taken as two independent chains
+    // the product taken as four independent chains
     const int i = tid;
     const double di = dK[i];
-    const double* Dr = Delta + i * 64;
-    double pr0 = -Dr[i], pr1 = 1.0;
-    for (int q = 0; q + 1 < nK; q += 2) {
-      if (q != i) pr0 *= (-Dr[q]) / (dK[q] - di);
-      if (q + 1 != i) pr1 *= (-Dr[q + 1]) / (dK[q + 1] - di);
+    const double* Dr = Ds + i * 65;
+    double pr[4] = {-Dr[i], 1.0, 1.0, 1.0};
+    for (int q0 = 0; q0 < nK; q0 += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u;
+        if (q < nK && q != i) pr[u] *= (-Dr[q]) / (dK[q] - di);
+      }
     }
-    if ((nK & 1) && nK - 1 != i) pr0 *= (-Dr[nK - 1]) / (dK[nK - 1] - di);
-    const double pr = pr0 * pr1;
-    const double zz = sqrt(fmax(pr, 0.0));
+    const double prod = (pr[0] * pr[1]) * (pr[2] * pr[3]);
+    const double zz = sqrt(fmax(prod, 0.0));
     zh[i] = wk->zK[i] >= 0.0 ? zz : -zz;
   }
   __syncthreads();
-  if (tid < nK) v[tid] = zh[tid] / Delta[tid * 64 + j];
+  if (tid < nK) v[tid] = zh[tid] / Ds[tid * 65 + j];
   __syncthreads();
   double nrm = 0.0;
   if (tid < 64) nrm = tid < nK ? v[tid] * v[tid] : 0.0;
   nrm = block_sum(nrm);
   const double inv = 1.0 / sqrt(nrm);
   for (int a = tid; a < m; a += blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < nK; ++i) acc = fma(Wk[i * 65 + a], v[i], acc);
-    Wnew[j * m + a] = acc * inv;
+    double acc0 = 0.0, acc1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nK; i += 2) {
+      acc0 = fma(Wk[i * 65 + a], v[i], acc0);
+      acc1 = fma(Wk[(i + 1) * 65 + a], v[i + 1], acc1);
+    }
+    if (i < nK) acc0 = fma(Wk[i * 65 + a], v[i], acc0);
+    Wnew[j * m + a] = (acc0 + acc1) * inv;
   }
   if (tid == 0) lamnew[j] = wk->dK[wk->org[j]] + wk->tau[j];
 }
@@ -1156,7 +1222,7 @@ size_t odeim_ws_bytes(int64_t N, int m) {
   b += sizeof(double) * (64 + 6 * (size_t)(m + 1) * (m + 1) + 4 * m + 64);
   b += 16 * 256;
   b += sizeof(double) * (5 * 64 * 64 + 3 * 64) + sizeof(R1Work) + 16 * 256;
-  b += sizeof(double) * 2 * (m + 1) * (m + 1) + 3 * 256;
+  b += sizeof(double) * (2 * (m + 1) * (m + 1) + 512) + 3 * 256;
   b += sizeof(double) * (2 * 64 * 64 + 64) + 3 * 256;
   return b + 4096;
 }
@@ -1194,7 +1260,7 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.lam_s2 = (double*)take(64 * sizeof(double));
   o.W_s2 = (double*)take((size_t)64 * 64 * sizeof(double));
   o.r1 = (R1Work*)take(sizeof(R1Work));
-  o.jbuf = (double*)take((size_t)2 * (m + 1) * (m + 1) * sizeof(double));
+  o.jbuf = (double*)take(((size_t)2 * (m + 1) * (m + 1) + 512) * sizeof(double));
   o.jscale = (double*)take(64);
   o.jflag = (int*)take(64);
   o.Lf = (double*)take((size_t)64 * 64 * sizeof(double));
@@ -1228,7 +1294,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   const size_t dsmem = sizeof(double) * 2 * 64 * 65;
   cudaFuncSetAttribute(k_deim_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
   for (int l = 0; l < m; ++l) {
-    k_deim_solve<T><<<1, 32, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
+    k_deim_solve<T><<<1, 256, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
     k_deim_score<T><<<(probe + 255) / 256, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, 0,
                                                         probe, o.ctl, o.scores);
     k_deim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
@@ -1236,7 +1302,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                                             o.ctl, o.scores);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
-    if (l + 1 < m) k_deim_extend<T><<<1, 32, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
+    if (l + 1 < m) k_deim_extend<T><<<1, 256, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
   }
   if (mark) {  // DEIM ends, oversampling begins
     mark(mark_arg, -12);
@@ -1249,11 +1315,22 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   const size_t smem = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 * 8);
   const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64);
   M_(12);
-  k_pad_sym2<<<1, 256, 0, HY_S(s)>>>(o.M, m, n, o.Mp);
-  if (run_jacobi_multi(o.Mp, n, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, o.jscale,
-                       (double*)host_pinned + 1, 60, s) < 0)
+  // eigensystem of M: pivoted Cholesky + one-sided Jacobi; two-sided
+  // Jacobi if M is numerically rank deficient (its null space is needed)
+  int rank_m = 0;
+  if (run_psd_eig(o.M, m, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, 60, s,
+                  (int*)host_pinned + 2) < 0)
     return -1;
-  k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl);
+  rank_m = ((int*)host_pinned)[2];
+  if (rank_m == m) {
+    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, m, m, o.lam_s, o.W_s, o.ctl);
+  } else {
+    k_pad_sym2<<<1, 256, 0, HY_S(s)>>>(o.M, m, n, o.Mp);
+    if (run_jacobi_multi(o.Mp, n, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, o.jscale,
+                         (double*)host_pinned + 1, 60, s) < 0)
+      return -1;
+    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl);
+  }
   M_(-13);
   for (int l = m; l < np; ++l) {
     M_(13);
@@ -1284,7 +1361,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
       M_(16);
       k_r1_prepare<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
       k_r1_roots<<<m, 32, 0, HY_S(s)>>>(o.r1, o.Delta);
-      k_r1_vectors<<<m, 64, 0, HY_S(s)>>>(o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
+      k_r1_vectors<<<m, 256, 0, HY_S(s)>>>(o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
       k_r1_merge<<<1, 256, 0, HY_S(s)>>>(o.r1, o.Wrot, o.Wnew, o.lamnew, m, o.lam_s2, o.W_s2,
                                          o.ctl);
       std::swap(o.lam_s, o.lam_s2);

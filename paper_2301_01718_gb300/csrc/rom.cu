@@ -915,10 +915,10 @@ __global__ void k_osj_finish(const double* __restrict__ B, int n, const int* __r
 }
 
 // G (n x n, ld n) -> lam (n), V (n x n column-major).  buf: n * n doubles
-// and 2 * kEigMaxN ints; flag: 4 ints (rotated, timeout, barrier).  Returns
-// the sweeps run, -1 on a CUDA error, -2 when a grid barrier timed out.
+// and 2 * kEigMaxN ints.  With host_rank (pinned) the numerical rank is
+// read back (one synchronisation).  Returns 0, or -1 on a CUDA error.
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
-                int* host_flag, int max_sweeps, cudaStream_t s) {
+                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank) {
   if (n > kEigMaxN) return -1;
   double* B = buf;
   int* piv = reinterpret_cast<int*>(buf + (size_t)n * n);
@@ -948,6 +948,10 @@ int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int
     return -1;
   const int sw = 0;
   k_osj_finish<<<n, 128, 0, HY_S(s)>>>(B, n, rank, piv, lam, V);
+  if (host_rank) {
+    cudaMemcpyAsync(host_rank, rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  }
   return sw;
 }
 
