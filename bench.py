@@ -78,9 +78,10 @@ def config_dict(a, cfg):
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_rate(a, steps=2):
+def cpu_oracle_rate(a, steps=2, warmup=0):
     """Time `steps` hybrid steps of the oracle on a cpu_n^2 grid of the same
-    workload (after its untimed warm-up); scale steps/s by cells to the
+    workload (after its untimed warm-up: the method's w full steps and first
+    rebuild, then `warmup` hybrid steps); scale steps/s by cells to the
     benchmark grid (the oracle's cost per step is linear in the cells)."""
     from oracle import arom
     q0, cfg = workload(a, n=a.cpu_n, prec=W.PREC_F64)
@@ -89,6 +90,8 @@ def cpu_oracle_rate(a, steps=2):
         info = A.step()
         if info.rebuilt and A.k >= cfg.w:
             break
+    for _ in range(warmup):
+        A.step()
     ns = 0
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -276,8 +279,12 @@ def run_ours(a):
     if cand:
         _, dom = max(cand)
         ach = per[dom]["gbs"]
+        traffic = None
+        if dom == "formphi" and FORMPHI_TRAFFIC_PER_DOF is not None and cfg.w == 128 \
+                and m_eff == 64:
+            traffic = FORMPHI_TRAFFIC_PER_DOF * cfg.ndof
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
-                "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": None,
+                "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": traffic,
                 "bytes_per_launch": byts[dom], "peak_source": peaks["src"]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
@@ -294,6 +301,13 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+# DRAM bytes per launch of the roofline kernel per dof, from the ncu capture
+# summarised in profiles/form_phi_dram_traffic.md (k_form_phi_tiled, w = 128,
+# m = 64, 1024 x 1024 cells), scaled by dofs; set to None when the kernel
+# changes until it is captured again.
+FORMPHI_TRAFFIC_PER_DOF = 3222344960 / 4194304  # 768.3 B per dof
 
 
 def _peaks():
@@ -337,14 +351,17 @@ def err_vs_fp64(a, n=256, steps=12):
 
 
 def run_reference(a):
+    """The CPU oracle as the reference arm: --warmup untimed and --steps timed
+    hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
+    workload), steps/s scaled by cells to the benchmark grid."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     _, cfg = workload(a)
-    steps = max(1, min(a.steps, 2))
-    cb = cpu_oracle_rate(a, steps=steps)
+    steps = max(1, a.steps)
+    cb = cpu_oracle_rate(a, steps=steps, warmup=a.warmup)
     return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
-            "n_gpus": 0, "steps": steps, "warmup": a.warmup, "higher_is_better": True,
+            "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(a, cfg),
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
