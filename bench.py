@@ -180,6 +180,23 @@ def stage_bytes(cfg, m_eff, n_s_avg, s=4):
     }
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (ms): all ranks time the same number of steps
+    between barriers, so the job's time is the maximum."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, ms_max):
+    """Steps per second of the whole job: every replica did `steps` steps."""
+    return world * steps / (ms_max / 1e3)
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -229,12 +246,8 @@ def run_ours(a):
         stages = hyrom.hyrom_stage_times(ctx)
         odc = hyrom.hyrom_odeim_counters(ctx)
         hyrom.hyrom_profile(ctx, False)
-        t = torch.tensor([ms], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.barrier()
-        ms_max = float(t.item())
-        value = world * a.steps / (ms_max / 1e3)
+        ms_max = max_over_ranks(ms, world, "cuda")
+        value = whole_job_rate(a.steps, world, ms_max)
 
         # end to end through host buffers (pinned): upload gamma_k, step,
         # download gamma_k+1, every step
@@ -252,10 +265,8 @@ def run_ours(a):
                 hyrom.hyrom_get_state(ctx, hbuf.data_ptr(), on_host=True)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            te = torch.tensor([el], device="cuda")
-            if world > 1:
-                dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            e2e = {"value": world * ke / float(te.item()), "unit": UNIT,
+            el_max = max_over_ranks(el * 1e3, world, "cuda")
+            e2e = {"value": whole_job_rate(ke, world, el_max), "unit": UNIT,
                    "h2d_bytes_per_step": 4 * cfg.ndof, "d2h_bytes_per_step": 4 * cfg.ndof,
                    "path": "hyrom_set_state(host) + hyrom_step + hyrom_get_state(host)"}
         m_eff = infos[-1]["m_eff"]
