@@ -407,12 +407,15 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
 // POD, ODEIM, sampling sets, psi update
 // ---------------------------------------------------------------------------
 
+constexpr bool kUseTensorBasisProduct = false;
+
 template <typename T>
 hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<int>& win,
                    const T* psi, const std::vector<int>* psi_slots, T* phi_out, T* psi_next,
                    int* m_eff_host) {
   const int w = (int)win.size();
   const int wp = w % 2 ? w + 1 : w;
+  bool tc_used = false;
   CK(cudaMemcpyAsync(ctx->win_dev, win.data(), w * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
   const hyrom_config& cf = ctx->cfg;
   if (!ctx->f32) {
@@ -457,8 +460,21 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
                              ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
     t_end(ctx, HYROM_T_EIG);
     t_begin(ctx, HYROM_T_FORMPHI);
-    hy::launch_form_phi<T>(ring, ctx->N, ctx->win_dev, w, psi, (const T*)ctx->C, cf.m,
-                           ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg, ctx->st);
+    if constexpr (sizeof(T) == 4) {
+      // the tensor-core product is kept off until its pipeline beats the
+      // register-tiled SIMT product (see formphi_tc.cu)
+      if (kUseTensorBasisProduct && hy::form_phi_tc_ok(ctx->N, w, cf.m)) {
+        // tensor-core product; its bounded waits report through fail_dev[4]
+        CK(cudaMemsetAsync(ctx->fail_dev + 4, 0, sizeof(int), ctx->st));
+        hy::launch_form_phi_tc(ring, ctx->N, ctx->win_dev, w, psi, (const float*)ctx->C, cf.m,
+                               ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg,
+                               ctx->fail_dev + 4, ctx->st);
+        tc_used = true;
+      }
+    }
+    if (!tc_used)
+      hy::launch_form_phi<T>(ring, ctx->N, ctx->win_dev, w, psi, (const T*)ctx->C, cf.m,
+                             ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg, ctx->st);
     t_end(ctx, HYROM_T_FORMPHI);
   }
   // column signs: normalised on the FP64 path (direct basis comparison);
@@ -467,7 +483,11 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
   CKL();
   int* hi = (int*)ctx->host;
   CK(cudaMemcpyAsync(hi, ctx->m_eff_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  hi[1] = 0;
+  if (tc_used)
+    CK(cudaMemcpyAsync(hi + 1, ctx->fail_dev + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (hyrom_status s = sync(ctx)) return s;
+  if (hi[1]) return fail(ctx, HYROM_ETIMEOUT, "basis product: a pipeline wait timed out");
   *m_eff_host = hi[0];
   return HYROM_OK;
 }

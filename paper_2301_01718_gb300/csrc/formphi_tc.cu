@@ -1,0 +1,382 @@
+// The POD basis product Phi = (X - psi 1^T) C and the next reference state
+// psi_next = mean of the window (Sec. 2.2, POD and window mean) on the
+// 5th-generation tensor cores.
+//
+// X is the snapshot window (N rows x w slots of the FP32 ring), C the w x m
+// coefficient matrix V Sigma^{-1} (m <= 64, w <= 128).  The product is a
+// dense contraction of 2 N w m flops over 4 N (w + m + 2) bytes, so on the
+// tensor cores it is bound by HBM.  FP32 accuracy is kept with TF32 and an
+// error-compensated split: with a = a_hi + a_lo (a_hi = a with its 13 low
+// mantissa bits cleared, a_lo exact), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// three MMAs accumulating into one FP32 tile (error ~2^-21 |a||b|).
+//
+// One persistent CTA per SM takes 128-row tiles.  Per tile and per chunk of
+// 32 window slots:
+//   * the 32 lanes of warp 0 issue bulk async copies (cp.async.bulk) of the
+//     chunk's slots (128 rows = 512 contiguous bytes each, one per lane) into
+//     a 4-stage ring of raw FP32 chunks, three chunks ahead, completing on an
+//     mbarrier with the byte count;
+//   * all 256 threads (2 per row, 16 slots each) take the raw values, update
+//     the Kahan window sum of their row, centre by psi, split into TF32
+//     hi/lo and write both into the chunk's A stage in the 128-byte-swizzled
+//     K-major layout the tensor core reads;
+//   * one thread issues the chunk's 4 x 3 tcgen05.mma (M = 128, N = 64,
+//     K = 8, kind::tf32) into one of two 128 x 64 FP32 accumulators in
+//     tensor memory (tiles alternate) and commits them to the A stage's
+//     mbarrier.
+// A tile's epilogue runs after the next tile's first chunk has been issued,
+// so the MMAs' latency hides behind that work: the 8 warps read the
+// accumulator with tcgen05.ld (warp w: rows 32 (w % 4) .., columns
+// 32 (w / 4) ..) and store Phi (column-major, coalesced over rows) and
+// psi_next.  C is split and staged
+// once per CTA.  Every mbarrier wait is bounded (about a second); on a
+// timeout the kernel records it in *err, stops issuing work and frees its
+// tensor memory before returning.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hy {
+namespace {
+
+constexpr int kRows = 128;     // tile rows (UMMA M)
+constexpr int kCols = 64;      // basis columns (UMMA N), zero padded beyond m_eff
+constexpr int kChunk = 32;     // window slots per chunk: one 128-byte atom of TF32
+constexpr int kMaxW = 128;
+constexpr int kThreads = 256;
+constexpr int kRawStages = 4;
+constexpr int kAStages = 2;
+constexpr int kAtomGroup = 1024;                          // 8 rows x 128 bytes
+constexpr int kBBytes = (kMaxW / kChunk) * (kCols / 8) * kAtomGroup;  // 32 KB
+constexpr int kABytes = (kRows / 8) * kAtomGroup;                    // 16 KB
+constexpr int kRawBytes = kChunk * kRows * 4;                        // 16 KB
+constexpr int kSmemBytes = 2 * kBBytes + kAStages * 2 * kABytes + kRawStages * kRawBytes + 1024;
+constexpr uint32_t kTmemCols = 128;  // two 64-column accumulators
+constexpr uint32_t kWaitLimit = 1u << 20;
+
+// kind::tf32: D in FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9
+// and 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                            ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+
+HY_DEV uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) in a K-major, 128-byte-swizzled block of
+// 8-row groups holding one 32-element atom along k: row r of a group is 128
+// bytes at r * 128, and its 16-byte chunk c sits at chunk position c ^ r.
+HY_DEV int sw128(int row, int k) {
+  const int g = row >> 3, r = row & 7, c = k >> 2, e = k & 3;
+  return g * kAtomGroup + r * 128 + ((c ^ r) << 4) + (e << 2);
+}
+
+// shared-memory matrix descriptor: start address, leading offset (unused by
+// swizzled K-major layouts), stride between 8-row groups 1024 bytes,
+// descriptor version 1, 128-byte swizzle
+HY_DEV uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+         ((uint64_t)(kAtomGroup >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+HY_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count)
+               : "memory");
+}
+
+HY_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = saddr(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+HY_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+HY_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(bar))
+      : "memory");
+}
+
+HY_DEV void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+HY_DEV void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+
+HY_DEV void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+HY_DEV void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_form_phi_tc(const float* __restrict__ ring, int64_t N, const int* __restrict__ win, int w,
+                  const float* __restrict__ psi, const float* __restrict__ C, int m,
+                  const int* __restrict__ m_eff_dev, float* __restrict__ phi,
+                  float* __restrict__ psi_next, int* __restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* base =
+      smraw + ((1024 - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
+  unsigned char* Bhi = base;
+  unsigned char* Blo = Bhi + kBBytes;
+  unsigned char* Aarea = Blo + kBBytes;                     // kAStages x (hi, lo)
+  float* raw = reinterpret_cast<float*>(Aarea + kAStages * 2 * kABytes);  // kRawStages chunks
+  __shared__ uint64_t raw_full[kRawStages], mma_done[kAStages], tile_done[2];
+  __shared__ uint32_t tmem_s;
+  __shared__ int ws[kMaxW];
+  __shared__ float part_s[2][2][kRows], part_c[2][2][kRows];  // [tile parity][half][row]
+  __shared__ int stop_s;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int me = *m_eff_dev;
+  const int nch = (w + kChunk - 1) / kChunk;
+  const int64_t ntile = (N + kRows - 1) / kRows;
+  const int64_t my_tiles = ntile > blockIdx.x ? (ntile - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * nch;  // chunks this CTA processes
+
+  // C split into TF32 hi/lo, K-major swizzled: B[n][k], one block per atom of k
+  for (int i = tid; i < kMaxW * kCols; i += kThreads) {
+    const int k = i / kCols, n = i % kCols;
+    const float c = (k < w && n < m && n < me) ? C[k * m + n] : 0.f;
+    float hi, lo;
+    split_tf32(c, hi, lo);
+    const int off = (k / kChunk) * (kCols / 8) * kAtomGroup + sw128(n, k % kChunk);
+    *reinterpret_cast<float*>(Bhi + off) = hi;
+    *reinterpret_cast<float*>(Blo + off) = lo;
+  }
+  for (int i = tid; i < w; i += kThreads) ws[i] = win[i];
+  if (tid == 0) {
+    for (int s = 0; s < kRawStages; ++s) mbar_init(&raw_full[s], 1);
+    for (int s = 0; s < kAStages; ++s) mbar_init(&mma_done[s], 1);
+    mbar_init(&tile_done[0], 1);
+    mbar_init(&tile_done[1], 1);
+    stop_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_s)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // generic-proxy writes of B become visible to the tensor core's async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_s;
+
+  // chunk g -> (tile, chunk of the tile); warp 0 issues one slot per lane
+  auto issue_raw = [&](int64_t g) {
+    const int64_t tile = blockIdx.x + (g / nch) * (int64_t)gridDim.x;
+    const int c = (int)(g % nch);
+    const int64_t row0 = tile * kRows;
+    const int rows = (int)(N - row0 < kRows ? N - row0 : kRows);
+    const int k0 = c * kChunk;
+    const int nk = w - k0 < kChunk ? w - k0 : kChunk;
+    const int s = (int)(g % kRawStages);
+    float* dst = raw + s * (kRawBytes / 4);
+    const int lane = tid & 31;
+    if (lane == 0) mbar_expect_tx(&raw_full[s], (uint32_t)(nk * rows * 4));
+    __syncwarp();
+    if (lane < nk)
+      bulk_g2s(dst + lane * kRows, ring + (int64_t)ws[k0 + lane] * N + row0,
+               (uint32_t)(rows * 4), &raw_full[s]);
+  };
+  if (warp == 0)
+    for (int64_t g = 0; g < total && g < kRawStages - 1; ++g) issue_raw(g);
+
+  const int row = tid & (kRows - 1), half = tid >> 7;
+  float ksum = 0.f, kcomp = 0.f, pr = 0.f;
+  bool ok = true;
+  // epilogue of the tile with local index t (accumulator t & 1)
+  auto epilogue = [&](int64_t t) -> bool {
+    const int64_t row0 = (blockIdx.x + t * (int64_t)gridDim.x) * kRows;
+    if (!mbar_wait(&tile_done[t & 1], (uint32_t)((t >> 1) & 1))) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int pb = (int)(t & 1);
+    if (half == 0 && row0 + row < N) {
+      const float s0 = part_s[pb][0][row], s1 = part_s[pb][1][row];
+      const float a = s0 + s1, bb = a - s0;
+      const float e = (s0 - (a - bb)) + (s1 - bb);
+      psi_next[row0 + row] =
+          (a + (e - (part_c[pb][0][row] + part_c[pb][1][row]))) / (float)w;
+    }
+    const int lanegrp = warp & 3, colgrp = warp >> 2;
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * lanegrp) << 16) + (uint32_t)(kCols * pb + 32 * colgrp), v);
+    const int64_t r = row0 + 32 * lanegrp + (tid & 31);
+    if (r < N) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = 32 * colgrp + j;
+        if (col < me) phi[(int64_t)col * N + r] = v[j];
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    return true;
+  };
+  for (int64_t g = 0; g < total; ++g) {
+    const int64_t t = g / nch;
+    const int64_t tile = blockIdx.x + t * (int64_t)gridDim.x;
+    const int c = (int)(g % nch);
+    const int64_t row0 = tile * kRows;
+    const bool valid_row = row0 + row < N;
+    if (c == 0) {
+      ksum = 0.f;
+      kcomp = 0.f;
+      pr = valid_row ? psi[row0 + row] : 0.f;
+    }
+    if (warp == 0 && g + kRawStages - 1 < total) issue_raw(g + kRawStages - 1);  // warp-uniform
+    const int rs = (int)(g % kRawStages), as = (int)(g % kAStages);
+    ok = mbar_wait(&raw_full[rs], (uint32_t)((g / kRawStages) & 1));
+    if (ok && g >= kAStages) ok = mbar_wait(&mma_done[as], (uint32_t)((g / kAStages - 1) & 1));
+    if (!ok) {
+      if (tid == 0) atomicExch(err, 1);
+      stop_s = 1;
+    }
+    __syncthreads();
+    if (stop_s) break;
+    // raw -> Kahan sum, centre, split, swizzled A stage (16 slots per thread)
+    const float* rv = raw + rs * (kRawBytes / 4);
+    unsigned char* Ahi = Aarea + as * 2 * kABytes;
+    unsigned char* Alo = Ahi + kABytes;
+    const int k0 = c * kChunk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float hi4[4], lo4[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int kl = half * 16 + q * 4 + e;
+        float x = 0.f;
+        if (k0 + kl < w && valid_row) {
+          const float gv = rv[kl * kRows + row];
+          const float yk = gv - kcomp, tk = ksum + yk;
+          kcomp = (tk - ksum) - yk;
+          ksum = tk;
+          x = gv - pr;
+        }
+        split_tf32(x, hi4[e], lo4[e]);
+      }
+      const int off = sw128(row, half * 16 + q * 4);
+      *reinterpret_cast<float4*>(Ahi + off) = make_float4(hi4[0], hi4[1], hi4[2], hi4[3]);
+      *reinterpret_cast<float4*>(Alo + off) = make_float4(lo4[0], lo4[1], lo4[2], lo4[3]);
+    }
+    if (c == nch - 1) {
+      part_s[t & 1][half][row] = ksum;
+      part_c[t & 1][half][row] = kcomp;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + (uint32_t)(kCols * (t & 1));
+      const uint32_t ahi = saddr(Ahi), alo = saddr(Alo);
+      const uint32_t bofs = (uint32_t)(c * (kCols / 8) * kAtomGroup);
+      const uint32_t bhi = saddr(Bhi) + bofs, blo = saddr(Blo) + bofs;
+#pragma unroll
+      for (int kk = 0; kk < kChunk / 8; ++kk) {
+        const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along k inside the atom
+        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
+        mma_tf32(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+        mma_tf32(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+      }
+      mma_commit(&mma_done[as]);
+      if (c == nch - 1) mma_commit(&tile_done[t & 1]);
+    }
+    // the previous tile's epilogue, behind this chunk's MMAs
+    if (c == 0 && t > 0) {
+      if (!epilogue(t - 1)) {
+        if (tid == 0) atomicExch(err, 1);
+        stop_s = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (!stop_s && total > 0) {
+    if (!epilogue(total / nch - 1)) {
+      if (tid == 0) atomicExch(err, 1);
+      stop_s = 1;
+    }
+  }
+  // drain: the last commits must land before the CTA's shared memory goes
+  if (tid == 0 && total > 0 && !stop_s) {
+    for (int s = 0; s < kAStages; ++s) {
+      const int64_t uses = (total - s + kAStages - 1) / kAStages;  // chunks that used stage s
+      if (uses > 0 && !mbar_wait(&mma_done[s], (uint32_t)((uses - 1) & 1))) atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+}  // namespace
+
+bool form_phi_tc_ok(int64_t N, int w, int m) {
+  return N > 0 && (N & 3) == 0 && w >= 1 && w <= kMaxW && m >= 1 && m <= kCols;
+}
+
+void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
+                        const float* C, int m, const int* m_eff_dev, float* phi,
+                        float* psi_next, int* err, cudaStream_t s) {
+  cudaFuncSetAttribute(k_form_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  int64_t tiles = (N + kRows - 1) / kRows;
+  const int grid = (int)(tiles < 152 ? tiles : 152);
+  k_form_phi_tc<<<grid, kThreads, kSmemBytes, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,
+                                                         phi, psi_next, err);
+}
+
+}  // namespace hy

@@ -87,6 +87,13 @@ void launch_identity(double* V, int n, cudaStream_t s);
 int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
                      int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
                      cudaStream_t s);
+// Phi = (X - psi 1^T) C and psi_next on the tensor cores (formphi_tc.cu):
+// FP32 ring, N % 4 == 0, w <= 128, m <= 64.  *err is set if a pipeline wait
+// timed out.
+bool form_phi_tc_ok(int64_t N, int w, int m);
+void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
+                        const float* C, int m, const int* m_eff_dev, float* phi,
+                        float* psi_next, int* err, cudaStream_t s);
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
                 int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
