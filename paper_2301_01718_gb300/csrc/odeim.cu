@@ -31,6 +31,7 @@ namespace hy {
 constexpr int kNB = 256;       // norm buckets
 constexpr int kProbe = 2048;   // rows scored before the bound is applied
 constexpr int kLdw = 65;       // odd leading dimension of W in shared memory
+constexpr int kCompact = 524288;  // leading ordered rows kept row-major (FP32, 64 wide)
 
 struct OdCtl {
   unsigned long long smax;  // bits of the best score so far (>= 0)
@@ -138,6 +139,24 @@ __global__ void k_bucket_scatter(int64_t N, const unsigned char* __restrict__ bk
 // (|L| <= 1 up to the tie tolerance).  Each step costs two triangular solves
 // (one warp, O(l^2)); k_deim_extend then borders L and U with the new point.
 // Lf, Uf: 64 x 64 row-major; y = L^{-1} Phi[P, l] is kept for the border.
+// Rows ord[0 .. C) of Phi copied once per call into a row-major FP32 array
+// R (64 values per row, zero beyond m), so that the per-step scoring passes
+// read each candidate row as 256 contiguous bytes instead of m scattered
+// sectors of the column-major basis.  One warp per row.
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ phi, int64_t N, int m,
+                              const int* __restrict__ ord, int C, float* __restrict__ R) {
+  const int lane = threadIdx.x & 31;
+  for (int pos = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pos < C;
+       pos += gridDim.x * (blockDim.x >> 5)) {
+    const int i = ord[pos];
+    const float x0 = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
+    const float x1 = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
+    R[(int64_t)pos * 64 + lane] = x0;
+    R[(int64_t)pos * 64 + lane + 32] = x1;
+  }
+}
+
 template <typename T>
 __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
                              const int* __restrict__ pts, const double* __restrict__ Lf,
@@ -271,7 +290,8 @@ template <typename T>
 __global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
                              const double* __restrict__ cvec, const int* __restrict__ ord,
                              const unsigned char* __restrict__ picked, int p0, int p1,
-                             OdCtl* ctl, double* __restrict__ scores) {
+                             OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R,
+                             int C) {
   __shared__ double cs[64];
   for (int j = threadIdx.x; j < l; j += blockDim.x) cs[j] = cvec[j];
   __syncthreads();
@@ -283,8 +303,14 @@ __global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
     double sc = -1.0;
     if (!picked[i]) {
       double s = 0.0;
-      for (int j = 0; j < l; ++j) s = fma((double)phi[(int64_t)j * N + i], cs[j], s);
-      sc = fabs((double)phi[(int64_t)l * N + i] - s);
+      if (sizeof(T) == 4 && pos < C) {  // the copy holds the FP32 values exactly
+        const float* rr = R + (int64_t)pos * 64;
+        for (int j = 0; j < l; ++j) s = fma((double)rr[j], cs[j], s);
+        sc = fabs((double)rr[l] - s);
+      } else {
+        for (int j = 0; j < l; ++j) s = fma((double)phi[(int64_t)j * N + i], cs[j], s);
+        sc = fabs((double)phi[(int64_t)l * N + i] - s);
+      }
       best = sc > best ? sc : best;
     }
     scores[pos] = sc;
@@ -523,7 +549,7 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
-    double* __restrict__ scores, int* __restrict__ list) {
+    double* __restrict__ scores, int* __restrict__ list, const float* __restrict__ R, int C) {
   __shared__ float w1[64];
   for (int a = threadIdx.x; a < 64; a += blockDim.x) w1[a] = a < m ? (float)W_s[a] : 0.f;
   __syncthreads();
@@ -539,8 +565,20 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
       double U = -1.0;
       if (!picked[i]) {
         float z1 = 0.f;
-#pragma unroll 16
-        for (int a = 0; a < m; ++a) z1 = fmaf(w1[a], (float)phi[(int64_t)a * N + i], z1);
+        if (pos < C) {  // contiguous copy (zero beyond m: same sum)
+          const float4* rp = reinterpret_cast<const float4*>(R + (int64_t)pos * 64);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float4 v = rp[q];
+            z1 = fmaf(w1[4 * q], v.x, z1);
+            z1 = fmaf(w1[4 * q + 1], v.y, z1);
+            z1 = fmaf(w1[4 * q + 2], v.z, z1);
+            z1 = fmaf(w1[4 * q + 3], v.w, z1);
+          }
+        } else {
+          for (int a = 0; a < 64; ++a)
+            z1 = fmaf(w1[a], a < m ? (float)phi[(int64_t)a * N + i] : 0.f, z1);
+        }
         const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
         const float b1 = __fadd_ru(fabsf(z1), dl);
         U = fmin(__dadd_ru(l1, (double)__fmul_ru(b1, b1)), l2);
@@ -577,7 +615,7 @@ __global__ void __launch_bounds__(256) k_odeim_screen(
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
     const double* __restrict__ lam_s, const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, int p1, const int* __restrict__ list,
-    OdCtl* ctl, double* __restrict__ scores) {
+    OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R, int C) {
   __shared__ float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
   __shared__ float dn[64], du[64];
   __shared__ float ph[8][64];
@@ -609,8 +647,13 @@ __global__ void __launch_bounds__(256) k_odeim_screen(
       if (lane == 0) scores[pos] = -1.0;
       continue;
     }
-    pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
-    pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
+    if (pos < C) {
+      pr[lane] = R[(int64_t)pos * 64 + lane];
+      pr[lane + 32] = R[(int64_t)pos * 64 + lane + 32];
+    } else {
+      pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
+      pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
+    }
     __syncwarp();
     float z0 = 0.f, z1 = 0.f;
 #pragma unroll 8
@@ -1183,6 +1226,7 @@ __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* _
 
 struct OdeimBufs {
   int* list;
+  float* rows;
   float* nrm;
   unsigned char* bkt;
   unsigned char* picked;
@@ -1218,6 +1262,7 @@ struct OdeimBufs {
 size_t odeim_ws_bytes(int64_t N, int m) {
   size_t b = 0;
   b += N * sizeof(float) + N + N + 2 * N * sizeof(int) + N * sizeof(double) + 256;
+  b += (size_t)(N < kCompact ? N : kCompact) * 64 * sizeof(float) + 256;
   b += (3 * (kNB + 1) + kNB) * sizeof(int);
   b += sizeof(double) * (64 + 6 * (size_t)(m + 1) * (m + 1) + 4 * m + 64);
   b += 16 * 256;
@@ -1240,6 +1285,7 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.nrm = (float*)take(N * sizeof(float));
   o.ord = (int*)take(N * sizeof(int));
   o.list = (int*)take(N * sizeof(int));
+  o.rows = (float*)take((size_t)(N < kCompact ? N : kCompact) * 64 * sizeof(float));
   o.bkt = (unsigned char*)take(N);
   o.picked = (unsigned char*)take(N);
   o.bcnt = (int*)take((kNB + 1) * sizeof(int));
@@ -1288,6 +1334,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   k_rownorm<T><<<(int)blocks, 256, 0, HY_S(s)>>>(phi, N, m, o.nrm, o.bkt, o.bcnt, o.bmax);
   k_bucket_scan<<<1, 32, 0, HY_S(s)>>>(o.bcnt, o.bstart, o.bcur);
   k_bucket_scatter<<<(int)blocks, 256, 0, HY_S(s)>>>(N, o.bkt, o.bcur, o.ord);
+  const int C = (int)(N < kCompact ? N : kCompact);
+  if (m <= 64) {
+    k_gather_rows<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.ord, C, o.rows);
+  }
   const int probe = (int)(N < kProbe ? N : kProbe);
   M_(-13);
   // DEIM
@@ -1296,10 +1346,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   for (int l = 0; l < m; ++l) {
     k_deim_solve<T><<<1, 256, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
     k_deim_score<T><<<(probe + 255) / 256, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, 0,
-                                                        probe, o.ctl, o.scores);
+                                                        probe, o.ctl, o.scores, o.rows, C);
     k_deim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
     k_deim_score<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, probe, -1,
-                                            o.ctl, o.scores);
+                                            o.ctl, o.scores, o.rows, C);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
     if (l + 1 < m) k_deim_extend<T><<<1, 256, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
@@ -1336,7 +1386,8 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     M_(13);
     // full FP32 bounds of the largest-norm rows, exact score of the best
     k_odeim_screen<T><<<(probe + 7) / 8, 256, 0, HY_S(s)>>>(
-        phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores);
+        phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores,
+        o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     k_odeim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
     M_(-14);
@@ -1344,9 +1395,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     // the other rows whose norm can reach the best score: the z_1 bound for
     // all, the full bound for those it does not exclude
     k_odeim_z1<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
-                                                tie_tol, o.ctl, o.scores, o.list);
+                                                tie_tol, o.ctl, o.scores, o.list, o.rows, C);
     k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord,
-                                                    o.picked, 0, -1, o.list, o.ctl, o.scores);
+                                                    o.picked, 0, -1, o.list, o.ctl, o.scores,
+                                                    o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     M_(-15);
     M_(15);
