@@ -203,10 +203,13 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
     if (lane + 32 > i && lane + 32 < l) b1 = b1 - col[lane + 32] * yi;
   }
   const double y0 = b0, y1 = b1;
-  // backward: U c = y
+  // backward: U c = y, with the reciprocals of U's diagonal formed up front
+  // (a division on every step of the dependent chain costs ~650 cycles)
+  const double iu0 = lane < l ? 1.0 / Ut[lane * 65 + lane] : 0.0;
+  const double iu1 = lane + 32 < l ? 1.0 / Ut[(lane + 32) * 65 + lane + 32] : 0.0;
   for (int i = l - 1; i >= 0; --i) {
-    const double ui = Ut[i * 65 + i];
-    const double ci = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31) / ui;
+    const double ci = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31) *
+                      __shfl_sync(0xffffffffu, i < 32 ? iu0 : iu1, i & 31);
     if (lane == (i & 31)) {
       if (i < 32)
         b0 = ci;
@@ -255,8 +258,11 @@ __global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const
   if (lane + 32 < l) a1 = (double)phi[(int64_t)(lane + 32) * N + p];
   const double pl = (double)phi[(int64_t)l * N + p];
   __syncwarp();
+  const double iu0 = lane < l ? 1.0 / Us[lane * 64 + lane] : 0.0;
+  const double iu1 = lane + 32 < l ? 1.0 / Us[(lane + 32) * 64 + lane + 32] : 0.0;
   for (int j = 0; j < l; ++j) {  // ell_j = (a_j - sum_{i<j} U_ij ell_i) / U_jj
-    const double ej = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31) / Us[j * 64 + j];
+    const double ej = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31) *
+                      __shfl_sync(0xffffffffu, j < 32 ? iu0 : iu1, j & 31);
     if (lane == (j & 31)) {
       if (j < 32)
         a0 = ej;
@@ -444,10 +450,11 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
 // smaller root is
 //   tau' = 2 z_1^2 d_2 / (B + sqrt(B^2 - 4 C z_1^2 d_2)),
 //   C = 1 + a,  B = C d_2 + z_1^2 + b.
-// The first step is taken from tau = 0 (so it lies in (0, d_2)); later
-// steps are kept inside a shrinking bracket (bisection otherwise).  Stop
-// when |h| is within the rounding error of its evaluation, the step is below
-// 2 ulp, or the bracket has collapsed.  One warp; lane j holds z_j and
+// These steps run in FP32 (an FP64 divide or square root costs ~650
+// cycles on this GPU, an FP32 reciprocal ~85), from tau = 0 until the step is
+// at FP32 rounding; FP64 Newton steps on h then finish inside a shrinking
+// bracket (bisection otherwise).  Stop when |h| is within the rounding error
+// of its evaluation, the step is below 2 ulp, or the bracket has collapsed.  One warp; lane j holds z_j and
 // z_{j+32}.
 __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
                                    const double* __restrict__ lam, int m, const double* rb,
@@ -455,23 +462,24 @@ __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
   const int lane = threadIdx.x & 31;
   double z0 = 0.0, z1 = 0.0;
   const int j0 = lane, j1 = lane + 32;
-  if (j0 < m || j1 < m) {  // two chains per component
-    double z0b = 0.0, z1b = 0.0;
+  if (j0 < m || j1 < m) {  // four chains per component
     const double* w0 = W + (j0 < m ? j0 : 0) * ldw;
     const double* w1 = W + (j1 < m ? j1 : 0) * ldw;
+    double p0[4] = {0.0, 0.0, 0.0, 0.0}, p1[4] = {0.0, 0.0, 0.0, 0.0};
     int a = 0;
-    for (; a + 1 < m; a += 2) {
-      z0 = fma(w0[a], rb[a], z0);
-      z0b = fma(w0[a + 1], rb[a + 1], z0b);
-      z1 = fma(w1[a], rb[a], z1);
-      z1b = fma(w1[a + 1], rb[a + 1], z1b);
+    for (; a + 3 < m; a += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        p0[u] = fma(w0[a + u], rb[a + u], p0[u]);
+        p1[u] = fma(w1[a + u], rb[a + u], p1[u]);
+      }
     }
-    if (a < m) {
-      z0 = fma(w0[a], rb[a], z0);
-      z1 = fma(w1[a], rb[a], z1);
+    for (; a < m; ++a) {
+      p0[0] = fma(w0[a], rb[a], p0[0]);
+      p1[0] = fma(w1[a], rb[a], p1[0]);
     }
-    z0 = j0 < m ? z0 + z0b : 0.0;
-    z1 = j1 < m ? z1 + z1b : 0.0;
+    z0 = j0 < m ? (p0[0] + p0[1]) + (p0[2] + p0[3]) : 0.0;
+    z1 = j1 < m ? (p1[0] + p1[1]) + (p1[2] + p1[3]) : 0.0;
   }
   const double q0 = z0 * z0, q1 = z1 * z1;
   const double zz = warp_sum(q0 + q1);
@@ -484,41 +492,73 @@ __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
   double hi = fmin(d2, zz), lo = 0.0;
   if (!(hi > 0.0) || zf == 0.0) return l1;  // z_1 = 0 or a double eigenvalue
   const double eps = 2.220446049250313e-16;
-  double tau = 0.0, g = 0.0, dg = 0.0;
-  for (int itr = 0; itr < 100; ++itr) {
-    if (itr > 0) {
-      g = 0.0;
-      dg = 0.0;
+  // FP32 two-pole model steps (cheap) to a starting point for FP64 Newton
+  double tau;
+  {
+    const float fd0 = (float)d0, fd1 = (float)d1, fw0 = (float)w0, fw1 = (float)w1;
+    const float fzf = (float)zf, fd2 = (float)d2;
+    float t = 0.f, flo = 0.f, fhi = (float)hi;
+    for (int it = 0; it < 12; ++it) {
+      float g = 0.f, dg = 0.f;
+      if (fw0 > 0.f) {
+        const float r = __frcp_rn(fd0 - t);
+        g = fw0 * r;
+        dg = g * r;
+      }
+      if (fw1 > 0.f) {
+        const float r = __frcp_rn(fd1 - t);
+        const float q = fw1 * r;
+        g += q;
+        dg = fmaf(q, r, dg);
+      }
+      g = warp_sum(g);
+      dg = warp_sum(dg);
+      if (it > 0) {
+        const float h = fmaf(t, 1.f + g, -fzf);
+        if (h < 0.f)
+          flo = t;
+        else
+          fhi = t;
+      }
+      const float gap = fd2 - t;
+      const float C = 1.f + (g - dg * gap);
+      const float B = C * fd2 + fzf + dg * gap * gap;
+      const float nt = 2.f * fzf * fd2 / (B + sqrtf(fmaxf(B * B - 4.f * C * fzf * fd2, 0.f)));
+      const bool done = it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t;
+      t = (nt > flo && nt < fhi) ? nt : 0.5f * (flo + fhi);
+      if (done) break;
     }
+    tau = (double)t;
+    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+  }
+  // FP64 Newton steps on h inside the bracket
+  for (int itr = 0; itr < 60; ++itr) {
+    double g = 0.0, dg = 0.0;
     if (w0 > 0.0) {
       const double r = 1.0 / (d0 - tau);
       g = w0 * r;
-      dg = w0 * r * r;
+      dg = g * r;
     }
     if (w1 > 0.0) {
       const double r = 1.0 / (d1 - tau);
-      g = g + w1 * r;
-      dg = dg + w1 * r * r;
+      const double q = w1 * r;
+      g = g + q;
+      dg = fma(q, r, dg);
     }
     g = warp_sum(g);
     dg = warp_sum(dg);
-    if (itr > 0) {
-      const double h = tau * (1.0 + g) - zf;
-      if (fabs(h) <= 16.0 * eps * (tau * (1.0 + g) + zf)) break;
-      if (h < 0.0)
-        lo = tau;
-      else
-        hi = tau;
-      if (hi - lo <= 2.0 * eps * hi) {
-        tau = hi;
-        break;
-      }
+    const double h = tau * (1.0 + g) - zf;
+    if (fabs(h) <= 16.0 * eps * (tau * (1.0 + g) + zf)) break;
+    if (h < 0.0)
+      lo = tau;
+    else
+      hi = tau;
+    if (hi - lo <= 2.0 * eps * hi) {
+      tau = hi;
+      break;
     }
-    const double gap = d2 - tau;
-    const double C = 1.0 + (g - dg * gap);
-    const double B = C * d2 + zf + dg * gap * gap;
-    const double nt = 2.0 * zf * d2 / (B + sqrt(fmax(B * B - 4.0 * C * zf * d2, 0.0)));
-    if (itr > 0 && fabs(nt - tau) <= 2.0 * eps * tau) {
+    const double nt = tau - h / fma(tau, dg, 1.0 + g);
+    if (fabs(nt - tau) <= 2.0 * eps * tau) {
       tau = nt;
       break;
     }

@@ -789,8 +789,8 @@ __global__ void k_osj_sweep(double* B, int n, const int* __restrict__ rank, doub
 // columns through distributed shared memory, forms their inner product,
 // rotates them and writes them back; a cluster barrier ends the round.  The
 // squared column norms are formed at the start of each sweep and carried
-// through the rotations exactly as the rotation changes them
-// (a' = a - t g, c' = c + t g), so a pair costs one inner product.  Every
+// through the rotations (a' = cs^2 a - 2 cs sn g + sn^2 c, and likewise c'),
+// so a pair costs one inner product.  Every
 // CTA runs the same number of rounds and barriers: after a sweep all read
 // the same rotation flag (kept in CTA 0, one per sweep parity) and stop
 // together; at most max_sweeps.
@@ -851,30 +851,43 @@ __global__ void __launch_bounds__(256) k_osj_cluster(double* __restrict__ B, int
           yv[u] = act && i < n ? cq[i] : 0.0;
         }
         const double a = act ? *np_ : 0.0, c = act ? *nq_ : 0.0;
-        double g0 = 0.0, g1 = 0.0;
+        double gp[4] = {0.0, 0.0, 0.0, 0.0};  // four chains (an FP64 FMA is ~64 cycles)
 #pragma unroll
-        for (int u = 0; u < kPer; u += 2) {
-          g0 = fma(xv[u], yv[u], g0);
-          if (u + 1 < kPer) g1 = fma(xv[u + 1], yv[u + 1], g1);
-        }
-        double g = g0 + g1;
+        for (int u = 0; u < kPer; ++u) gp[u & 3] = fma(xv[u], yv[u], gp[u & 3]);
+        double g = (gp[0] + gp[1]) + (gp[2] + gp[3]);
         for (int o = kOsjLanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
         if (!act) continue;
-        if (fabs(g) > tol * sqrt(a * c) && a > 0.0 && c > 0.0) {
-          const double zeta = (c - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+        if (g * g > tol * tol * (a * c) && a > 0.0 && c > 0.0) {
+          // The angle comes from FP32 arithmetic (an FP64 divide or square
+          // root costs ~650 cycles): any angle near the optimum converges, and
+          // the rotation stays orthogonal because cs = (1 + t^2)^{-1/2} is
+          // formed in FP64 (FP32 seed, two Newton steps) and sn = cs t.
+          const float df = (float)(c - a), g2 = (float)(2.0 * g);
+          const float sc = fmaxf(fabsf(df), fabsf(g2));
+          const float u = df / sc, v = g2 / sc;
+          float tf = copysignf(1.f, u) * v / (fabsf(u) + sqrtf(fmaf(u, u, v * v)));
+          double t = (double)tf;
+          if (!(tf != 0.f) || !isfinite(tf)) {  // out of FP32 range: FP64 formula
+            const double zeta = (c - a) / (2.0 * g);
+            t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          }
+          const double x = fma(t, t, 1.0);
+          double y = (double)rsqrtf((float)x);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          const double cs = y, sn = cs * t;
 #pragma unroll
-          for (int u = 0; u < kPer; ++u) {
-            const int i = gl + kOsjLanes * u;
+          for (int u2 = 0; u2 < kPer; ++u2) {
+            const int i = gl + kOsjLanes * u2;
             if (i < n) {
-              cp[i] = fma(cs, xv[u], -sn * yv[u]);
-              cq[i] = fma(sn, xv[u], cs * yv[u]);
+              cp[i] = fma(cs, xv[u2], -sn * yv[u2]);
+              cq[i] = fma(sn, xv[u2], cs * yv[u2]);
             }
           }
-          if (gl == 0) {
-            *np_ = fma(-t, g, a);
-            *nq_ = fma(t, g, c);
+          if (gl == 0) {  // squared norms after the rotation (any angle)
+            const double cc = cs * cs, ss = sn * sn, x2 = 2.0 * cs * sn * g;
+            *np_ = fma(cc, a, fma(ss, c, -x2));
+            *nq_ = fma(ss, a, fma(cc, c, x2));
             atomicOr(flag0 + (sw & 1), 1);
           }
         }
