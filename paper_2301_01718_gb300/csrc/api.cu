@@ -407,7 +407,7 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
 // POD, ODEIM, sampling sets, psi update
 // ---------------------------------------------------------------------------
 
-constexpr bool kUseTensorBasisProduct = false;
+constexpr bool kUseTensorBasisProduct = true;
 
 template <typename T>
 hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<int>& win,

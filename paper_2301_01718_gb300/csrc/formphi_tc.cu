@@ -10,28 +10,22 @@
 // mantissa bits cleared, a_lo exact), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
 // three MMAs accumulating into one FP32 tile (error ~2^-21 |a||b|).
 //
-// One persistent CTA per SM takes 128-row tiles.  Per tile and per chunk of
-// 32 window slots:
-//   * the 32 lanes of warp 0 issue bulk async copies (cp.async.bulk) of the
-//     chunk's slots (128 rows = 512 contiguous bytes each, one per lane) into
-//     a 4-stage ring of raw FP32 chunks, three chunks ahead, completing on an
-//     mbarrier with the byte count;
-//   * all 256 threads (2 per row, 16 slots each) take the raw values, update
-//     the Kahan window sum of their row, centre by psi, split into TF32
-//     hi/lo and write both into the chunk's A stage in the 128-byte-swizzled
-//     K-major layout the tensor core reads;
-//   * one thread issues the chunk's 4 x 3 tcgen05.mma (M = 128, N = 64,
-//     K = 8, kind::tf32) into one of two 128 x 64 FP32 accumulators in
-//     tensor memory (tiles alternate) and commits them to the A stage's
-//     mbarrier.
-// A tile's epilogue runs after the next tile's first chunk has been issued,
-// so the MMAs' latency hides behind that work: the 8 warps read the
-// accumulator with tcgen05.ld (warp w: rows 32 (w % 4) .., columns
-// 32 (w / 4) ..) and store Phi (column-major, coalesced over rows) and
-// psi_next.  C is split and staged
-// once per CTA.  Every mbarrier wait is bounded (about a second); on a
-// timeout the kernel records it in *err, stops issuing work and frees its
-// tensor memory before returning.
+// One persistent CTA per SM takes 128-row tiles, with warp-specialised
+// roles handing chunks of 32 window slots to each other through mbarriers:
+//   * warp 0 (producer): bulk async copies (cp.async.bulk, one 512-byte slot
+//     of 128 rows per lane) into a 4-stage ring of raw FP32 chunks;
+//   * warps 8-11 (converters, one thread per row): Kahan window sum, centring
+//     by psi, TF32 hi/lo split, writes into a 2-stage ring of A tiles in the
+//     128-byte-swizzled K-major layout the tensor core reads; at a tile's
+//     end each writes its row of psi_next;
+//   * warp 1 (MMA): per chunk 4 x 3 tcgen05.mma (M = 128, N = 64, K = 8,
+//     kind::tf32) into one of two 128 x 64 FP32 accumulators in tensor
+//     memory (tiles alternate), committed to the chunk's and tile's mbarriers;
+//   * warps 4-7 (epilogue): tcgen05.ld of a finished accumulator (warp w:
+//     rows 32 (w % 4) ..), release it, and coalesced stores of Phi.
+// C is split and staged once per CTA.  Every mbarrier wait is bounded (about
+// a second); a timeout sets *err and a shared stop flag that ends every
+// role's loop, and the tensor memory is freed before the CTA returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,7 +39,7 @@ constexpr int kRows = 128;     // tile rows (UMMA M)
 constexpr int kCols = 64;      // basis columns (UMMA N), zero padded beyond m_eff
 constexpr int kChunk = 32;     // window slots per chunk: one 128-byte atom of TF32
 constexpr int kMaxW = 128;
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;  // 12 warps: producer, MMA, 2 idle, 4 epilogue, 4 converters
 constexpr int kRawStages = 4;
 constexpr int kAStages = 2;
 constexpr int kAtomGroup = 1024;                          // 8 rows x 128 bytes
@@ -165,15 +159,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       smraw + ((1024 - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
   unsigned char* Bhi = base;
   unsigned char* Blo = Bhi + kBBytes;
-  unsigned char* Aarea = Blo + kBBytes;                     // kAStages x (hi, lo)
+  unsigned char* Aarea = Blo + kBBytes;                                   // kAStages x (hi, lo)
   float* raw = reinterpret_cast<float*>(Aarea + kAStages * 2 * kABytes);  // kRawStages chunks
-  __shared__ uint64_t raw_full[kRawStages], mma_done[kAStages], tile_done[2];
+  __shared__ uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+  __shared__ uint64_t a_full[kAStages], a_empty[kAStages], d_full[2], d_empty[2];
   __shared__ uint32_t tmem_s;
   __shared__ int ws[kMaxW];
-  __shared__ float part_s[2][2][kRows], part_c[2][2][kRows];  // [tile parity][half][row]
-  __shared__ int stop_s;
+  __shared__ volatile int stop_s;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int me = *m_eff_dev;
   const int nch = (w + kChunk - 1) / kChunk;
   const int64_t ntile = (N + kRows - 1) / kRows;
@@ -192,10 +186,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int i = tid; i < w; i += kThreads) ws[i] = win[i];
   if (tid == 0) {
-    for (int s = 0; s < kRawStages; ++s) mbar_init(&raw_full[s], 1);
-    for (int s = 0; s < kAStages; ++s) mbar_init(&mma_done[s], 1);
-    mbar_init(&tile_done[0], 1);
-    mbar_init(&tile_done[1], 1);
+    for (int s = 0; s < kRawStages; ++s) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], 4);
+    }
+    for (int s = 0; s < kAStages; ++s) {
+      mbar_init(&a_full[s], 4);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&d_full[s], 1);
+      mbar_init(&d_empty[s], 4);
+    }
     stop_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -212,148 +214,156 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_s;
-
-  // chunk g -> (tile, chunk of the tile); warp 0 issues one slot per lane
-  auto issue_raw = [&](int64_t g) {
-    const int64_t tile = blockIdx.x + (g / nch) * (int64_t)gridDim.x;
-    const int c = (int)(g % nch);
-    const int64_t row0 = tile * kRows;
-    const int rows = (int)(N - row0 < kRows ? N - row0 : kRows);
-    const int k0 = c * kChunk;
-    const int nk = w - k0 < kChunk ? w - k0 : kChunk;
-    const int s = (int)(g % kRawStages);
-    float* dst = raw + s * (kRawBytes / 4);
-    const int lane = tid & 31;
-    if (lane == 0) mbar_expect_tx(&raw_full[s], (uint32_t)(nk * rows * 4));
-    __syncwarp();
-    if (lane < nk)
-      bulk_g2s(dst + lane * kRows, ring + (int64_t)ws[k0 + lane] * N + row0,
-               (uint32_t)(rows * 4), &raw_full[s]);
+  auto fail = [&]() {
+    if (lane == 0) atomicExch(err, 1);
+    stop_s = 1;
   };
-  if (warp == 0)
-    for (int64_t g = 0; g < total && g < kRawStages - 1; ++g) issue_raw(g);
 
-  const int row = tid & (kRows - 1), half = tid >> 7;
-  float ksum = 0.f, kcomp = 0.f, pr = 0.f;
-  bool ok = true;
-  // epilogue of the tile with local index t (accumulator t & 1)
-  auto epilogue = [&](int64_t t) -> bool {
-    const int64_t row0 = (blockIdx.x + t * (int64_t)gridDim.x) * kRows;
-    if (!mbar_wait(&tile_done[t & 1], (uint32_t)((t >> 1) & 1))) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int pb = (int)(t & 1);
-    if (half == 0 && row0 + row < N) {
-      const float s0 = part_s[pb][0][row], s1 = part_s[pb][1][row];
-      const float a = s0 + s1, bb = a - s0;
-      const float e = (s0 - (a - bb)) + (s1 - bb);
-      psi_next[row0 + row] =
-          (a + (e - (part_c[pb][0][row] + part_c[pb][1][row]))) / (float)w;
+  if (warp == 0) {
+    // ---- producer: raw chunk g into stage g % kRawStages ----
+    for (int64_t g = 0; g < total && !stop_s; ++g) {
+      const int s = (int)(g % kRawStages);
+      if (g >= kRawStages &&
+          !mbar_wait(&raw_empty[s], (uint32_t)((g / kRawStages - 1) & 1))) {
+        fail();
+        break;
+      }
+      const int64_t tile = blockIdx.x + (g / nch) * (int64_t)gridDim.x;
+      const int c = (int)(g % nch);
+      const int64_t row0 = tile * kRows;
+      const int rows = (int)(N - row0 < kRows ? N - row0 : kRows);
+      const int k0 = c * kChunk;
+      const int nk = w - k0 < kChunk ? w - k0 : kChunk;
+      float* dst = raw + s * (kRawBytes / 4);
+      if (lane == 0) mbar_expect_tx(&raw_full[s], (uint32_t)(nk * rows * 4));
+      __syncwarp();
+      if (lane < nk)
+        bulk_g2s(dst + lane * kRows, ring + (int64_t)ws[k0 + lane] * N + row0,
+                 (uint32_t)(rows * 4), &raw_full[s]);
     }
-    const int lanegrp = warp & 3, colgrp = warp >> 2;
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * lanegrp) << 16) + (uint32_t)(kCols * pb + 32 * colgrp), v);
-    const int64_t r = row0 + 32 * lanegrp + (tid & 31);
-    if (r < N) {
+  } else if (warp == 1) {
+    // ---- MMA issue (one thread) ----
+    if (lane == 0) {
+      for (int64_t g = 0; g < total && !stop_s; ++g) {
+        const int64_t t = g / nch;
+        const int c = (int)(g % nch);
+        const int as = (int)(g % kAStages), b = (int)(t & 1);
+        if (!mbar_wait(&a_full[as], (uint32_t)((g / kAStages) & 1))) {
+          fail();
+          break;
+        }
+        if (c == 0 && t >= 2 && !mbar_wait(&d_empty[b], (uint32_t)(((t >> 1) - 1) & 1))) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(kCols * b);
+        unsigned char* Ahi = Aarea + as * 2 * kABytes;
+        const uint32_t ahi = saddr(Ahi), alo = saddr(Ahi + kABytes);
+        const uint32_t bofs = (uint32_t)(c * (kCols / 8) * kAtomGroup);
+        const uint32_t bhi = saddr(Bhi) + bofs, blo = saddr(Blo) + bofs;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = 32 * colgrp + j;
-        if (col < me) phi[(int64_t)col * N + r] = v[j];
+        for (int kk = 0; kk < kChunk / 8; ++kk) {
+          const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along k inside the atom
+          const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
+          mma_tf32(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+          mma_tf32(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+        }
+        mma_commit(&a_empty[as]);
+        if (c == nch - 1) mma_commit(&d_full[b]);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    return true;
-  };
-  for (int64_t g = 0; g < total; ++g) {
-    const int64_t t = g / nch;
-    const int64_t tile = blockIdx.x + t * (int64_t)gridDim.x;
-    const int c = (int)(g % nch);
-    const int64_t row0 = tile * kRows;
-    const bool valid_row = row0 + row < N;
-    if (c == 0) {
-      ksum = 0.f;
-      kcomp = 0.f;
-      pr = valid_row ? psi[row0 + row] : 0.f;
+  } else if (warp >= 8) {
+    // ---- converters: thread = row, all 32 slots of each chunk ----
+    const int row = tid - 8 * 32;
+    float ksum = 0.f, kcomp = 0.f, pr = 0.f, pr_next = 0.f;
+    if (my_tiles > 0) {
+      const int64_t r0 = (int64_t)blockIdx.x * kRows + row;
+      pr_next = r0 < N ? psi[r0] : 0.f;
     }
-    if (warp == 0 && g + kRawStages - 1 < total) issue_raw(g + kRawStages - 1);  // warp-uniform
-    const int rs = (int)(g % kRawStages), as = (int)(g % kAStages);
-    ok = mbar_wait(&raw_full[rs], (uint32_t)((g / kRawStages) & 1));
-    if (ok && g >= kAStages) ok = mbar_wait(&mma_done[as], (uint32_t)((g / kAStages - 1) & 1));
-    if (!ok) {
-      if (tid == 0) atomicExch(err, 1);
-      stop_s = 1;
-    }
-    __syncthreads();
-    if (stop_s) break;
-    // raw -> Kahan sum, centre, split, swizzled A stage (16 slots per thread)
-    const float* rv = raw + rs * (kRawBytes / 4);
-    unsigned char* Ahi = Aarea + as * 2 * kABytes;
-    unsigned char* Alo = Ahi + kABytes;
-    const int k0 = c * kChunk;
+    for (int64_t g = 0; g < total && !stop_s; ++g) {
+      const int64_t t = g / nch;
+      const int c = (int)(g % nch);
+      const int64_t row0 = (blockIdx.x + t * (int64_t)gridDim.x) * kRows;
+      const bool valid = row0 + row < N;
+      if (c == 0) {
+        ksum = 0.f;
+        kcomp = 0.f;
+        pr = pr_next;
+        const int64_t rn = row0 + (int64_t)gridDim.x * kRows + row;  // next tile's row
+        pr_next = (t + 1 < my_tiles && rn < N) ? psi[rn] : 0.f;
+      }
+      const int rs = (int)(g % kRawStages), as = (int)(g % kAStages);
+      if (!mbar_wait(&raw_full[rs], (uint32_t)((g / kRawStages) & 1))) {
+        fail();
+        break;
+      }
+      const float* rv = raw + rs * (kRawBytes / 4);
+      const int k0 = c * kChunk;
+      float x[kChunk];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float hi4[4], lo4[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int kl = half * 16 + q * 4 + e;
-        float x = 0.f;
-        if (k0 + kl < w && valid_row) {
+      for (int kl = 0; kl < kChunk; ++kl) {
+        float v = 0.f;
+        if (k0 + kl < w && valid) {
           const float gv = rv[kl * kRows + row];
           const float yk = gv - kcomp, tk = ksum + yk;
           kcomp = (tk - ksum) - yk;
           ksum = tk;
-          x = gv - pr;
+          v = gv - pr;
         }
-        split_tf32(x, hi4[e], lo4[e]);
+        x[kl] = v;
       }
-      const int off = sw128(row, half * 16 + q * 4);
-      *reinterpret_cast<float4*>(Ahi + off) = make_float4(hi4[0], hi4[1], hi4[2], hi4[3]);
-      *reinterpret_cast<float4*>(Alo + off) = make_float4(lo4[0], lo4[1], lo4[2], lo4[3]);
-    }
-    if (c == nch - 1) {
-      part_s[t & 1][half][row] = ksum;
-      part_c[t & 1][half][row] = kcomp;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + (uint32_t)(kCols * (t & 1));
-      const uint32_t ahi = saddr(Ahi), alo = saddr(Alo);
-      const uint32_t bofs = (uint32_t)(c * (kCols / 8) * kAtomGroup);
-      const uint32_t bhi = saddr(Bhi) + bofs, blo = saddr(Blo) + bofs;
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&raw_empty[rs])) : "memory");
+      if (g >= kAStages && !mbar_wait(&a_empty[as], (uint32_t)((g / kAStages - 1) & 1))) {
+        fail();
+        break;
+      }
+      unsigned char* Ahi = Aarea + as * 2 * kABytes;
+      unsigned char* Alo = Ahi + kABytes;
 #pragma unroll
-      for (int kk = 0; kk < kChunk / 8; ++kk) {
-        const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along k inside the atom
-        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
-        mma_tf32(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-        mma_tf32(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+      for (int q = 0; q < kChunk / 4; ++q) {
+        float hi4[4], lo4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(x[4 * q + e], hi4[e], lo4[e]);
+        const int off = sw128(row, 4 * q);
+        *reinterpret_cast<float4*>(Ahi + off) = make_float4(hi4[0], hi4[1], hi4[2], hi4[3]);
+        *reinterpret_cast<float4*>(Alo + off) = make_float4(lo4[0], lo4[1], lo4[2], lo4[3]);
       }
-      mma_commit(&mma_done[as]);
-      if (c == nch - 1) mma_commit(&tile_done[t & 1]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&a_full[as])) : "memory");
+      if (c == nch - 1 && valid) psi_next[row0 + row] = (ksum - kcomp) / (float)w;
     }
-    // the previous tile's epilogue, behind this chunk's MMAs
-    if (c == 0 && t > 0) {
-      if (!epilogue(t - 1)) {
-        if (tid == 0) atomicExch(err, 1);
-        stop_s = 1;
+  } else if (warp >= 4) {
+    // ---- epilogue: accumulator of tile t -> Phi ----
+    const int lanegrp = warp & 3;
+    for (int64_t t = 0; t < my_tiles && !stop_s; ++t) {
+      const int b = (int)(t & 1);
+      if (!mbar_wait(&d_full[b], (uint32_t)((t >> 1) & 1))) {
+        fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v0[32], v1[32];
+      const uint32_t ta = tmem + ((uint32_t)(32 * lanegrp) << 16) + (uint32_t)(kCols * b);
+      tmem_ld32(ta, v0);
+      tmem_ld32(ta + 32, v1);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&d_empty[b])) : "memory");
+      const int64_t r = (blockIdx.x + t * (int64_t)gridDim.x) * kRows + 32 * lanegrp + lane;
+      if (r < N) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j < me) phi[(int64_t)j * N + r] = v0[j];
+          if (32 + j < me) phi[(int64_t)(32 + j) * N + r] = v1[j];
+        }
       }
     }
   }
-  __syncthreads();
-  if (!stop_s && total > 0) {
-    if (!epilogue(total / nch - 1)) {
-      if (tid == 0) atomicExch(err, 1);
-      stop_s = 1;
-    }
-  }
-  // drain: the last commits must land before the CTA's shared memory goes
-  if (tid == 0 && total > 0 && !stop_s) {
-    for (int s = 0; s < kAStages; ++s) {
-      const int64_t uses = (total - s + kAStages - 1) / kAStages;  // chunks that used stage s
-      if (uses > 0 && !mbar_wait(&mma_done[s], (uint32_t)((uses - 1) & 1))) atomicExch(err, 1);
-    }
-  }
+  // all roles done; in-flight MMAs ended before their last commit was seen
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
