@@ -315,10 +315,10 @@ def run_ours(a):
 
 
 # DRAM bytes per launch of the roofline kernel per dof, from the ncu capture
-# summarised in profiles/form_phi_dram_traffic.md (k_form_phi_tiled, w = 128,
+# summarised in profiles/form_phi_tc_euler_1024.md (k_form_phi_tc, w = 128,
 # m = 64, 1024 x 1024 cells), scaled by dofs; set to None when the kernel
 # changes until it is captured again.
-FORMPHI_TRAFFIC_PER_DOF = 3222344960 / 4194304  # 768.3 B per dof
+FORMPHI_TRAFFIC_PER_DOF = (2164486000 + 1059815000) / 4194304  # 768.7 B per dof
 
 
 def _peaks():

@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 8) {
     // ---- converters: thread = row, all 32 slots of each chunk ----
     const int row = tid - 8 * 32;
-    float ksum = 0.f, kcomp = 0.f, pr = 0.f, pr_next = 0.f;
+    // four Kahan accumulators (slot index mod 4) keep the dependent chains short
+    float ksum[4] = {0.f, 0.f, 0.f, 0.f}, kcomp[4] = {0.f, 0.f, 0.f, 0.f};
+    float pr = 0.f, pr_next = 0.f;
     if (my_tiles > 0) {
       const int64_t r0 = (int64_t)blockIdx.x * kRows + row;
       pr_next = r0 < N ? psi[r0] : 0.f;
@@ -288,8 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row0 = (blockIdx.x + t * (int64_t)gridDim.x) * kRows;
       const bool valid = row0 + row < N;
       if (c == 0) {
-        ksum = 0.f;
-        kcomp = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ksum[u] = kcomp[u] = 0.f;
         pr = pr_next;
         const int64_t rn = row0 + (int64_t)gridDim.x * kRows + row;  // next tile's row
         pr_next = (t + 1 < my_tiles && rn < N) ? psi[rn] : 0.f;
@@ -307,9 +309,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v = 0.f;
         if (k0 + kl < w && valid) {
           const float gv = rv[kl * kRows + row];
-          const float yk = gv - kcomp, tk = ksum + yk;
-          kcomp = (tk - ksum) - yk;
-          ksum = tk;
+          const int u = kl & 3;
+          const float yk = gv - kcomp[u], tk = ksum[u] + yk;
+          kcomp[u] = (tk - ksum[u]) - yk;
+          ksum[u] = tk;
           v = gv - pr;
         }
         x[kl] = v;
@@ -334,7 +337,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&a_full[as])) : "memory");
-      if (c == nch - 1 && valid) psi_next[row0 + row] = (ksum - kcomp) / (float)w;
+      if (c == nch - 1 && valid) {
+        // Kahan-add the four partial sums (each carried with its compensation)
+        float sum = 0.f, comp = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float yk = (ksum[u] - kcomp[u]) - comp, tk = sum + yk;
+          comp = (tk - sum) - yk;
+          sum = tk;
+        }
+        psi_next[row0 + row] = (sum - comp) / (float)w;
+      }
     }
   } else if (warp >= 4) {
     // ---- epilogue: accumulator of tile t -> Phi ----
