@@ -196,7 +196,7 @@ HY_DEV void nb_value(const DevCfg& c, const T* sm, int stride_v, int pos, int gi
 }
 
 template <typename T, int NV, int NF, int TX, int TY>
-__global__ void __launch_bounds__(256) k_filter_pass(DevCfg c, const T* __restrict__ q,
+__global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const T* __restrict__ q,
                                                      const T* __restrict__ qp, double t,
                                                      T* __restrict__ gbuf, uint32_t* __restrict__ kbits,
                                                      const int* __restrict__ tiles,
@@ -224,13 +224,30 @@ __global__ void __launch_bounds__(256) k_filter_pass(DevCfg c, const T* __restri
     const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
     __syncthreads();
     // q on the tile and an H-cell halo (periodic sides wrap, others clamp)
-    for (int idx = threadIdx.x; idx < SY * SX; idx += blockDim.x) {
-      const int sy = idx / SX, sx = idx % SX;
-      int gi = x0 - H + sx, gj = TWO ? y0 - H + sy : 0;
-      gi = perx ? imod(gi, c.nx) : (gi < 0 ? 0 : (gi >= c.nx ? c.nx - 1 : gi));
-      if (TWO) gj = pery ? imod(gj, c.ny) : (gj < 0 ? 0 : (gj >= c.ny ? c.ny - 1 : gj));
-      const int64_t cell = (int64_t)gj * c.nx + gi;
-      for (int a = 0; a < NV; ++a) qs[(a * SY + sy) * SX + sx] = q[a * c.nc + cell];
+    // (all of a thread's loads are issued before its stores)
+    constexpr int kPer = (SY * SX + 255) / 256;
+    T stage[kPer][NV];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      if (idx < SY * SX) {
+        const int sy = idx / SX, sx = idx % SX;
+        int gi = x0 - H + sx, gj = TWO ? y0 - H + sy : 0;
+        gi = perx ? imod(gi, c.nx) : (gi < 0 ? 0 : (gi >= c.nx ? c.nx - 1 : gi));
+        if (TWO) gj = pery ? imod(gj, c.ny) : (gj < 0 ? 0 : (gj >= c.ny ? c.ny - 1 : gj));
+        const int64_t cell = (int64_t)gj * c.nx + gi;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) stage[u][a] = q[a * c.nc + cell];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      if (idx < SY * SX) {
+        const int sy = idx / SX, sx = idx % SX;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) qs[(a * SY + sy) * SX + sx] = stage[u][a];
+      }
     }
     __syncthreads();
     // F_x on columns tile +- 1, every staged row (rows hold clamped/wrapped
@@ -362,6 +379,29 @@ __global__ void k_filter_apply(DevCfg c, T* __restrict__ q, const T* __restrict_
 }
 
 // tiles that contain a cell within box distance R of a kept cell
+// any bit set in [b, b + len) of the bitmap (len <= 64: at most 3 words)
+HY_DEV bool bits_any(const uint32_t* __restrict__ bm, int64_t b, int len) {
+  const int64_t w0 = b >> 5;
+  const int off = (int)(b & 31);
+  const int64_t e = b + len;  // exclusive end
+  const int64_t w_last = (e - 1) >> 5;
+  uint32_t acc = 0u;
+  for (int64_t wd = w0; wd <= w_last; ++wd) {
+    uint32_t v = bm[wd];
+    if (wd == w0) v &= 0xffffffffu << off;
+    if (wd == w_last) {
+      const int hi = (int)((e - 1) & 31);
+      v &= hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
+    }
+    acc |= v;
+  }
+  return acc != 0u;
+}
+
+// Tiles within R cells (x and y) of a kept cell.  Interior tiles read each
+// of their TY + 2R rows as at most three masked words of the bitmap; tiles
+// whose neighbourhood crosses the domain edge take the per-cell path (with
+// the periodic wrap or the clip).  One thread per tile.
 __global__ void k_filter_next_tiles(DevCfg c, const uint32_t* __restrict__ kbits, int TX, int TY,
                                     int R, int* __restrict__ tiles, int* __restrict__ ntiles,
                                     const int* __restrict__ done) {
@@ -373,24 +413,31 @@ __global__ void k_filter_next_tiles(DevCfg c, const uint32_t* __restrict__ kbits
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tx * ty; t += gridDim.x * blockDim.x) {
     const int x0 = (t % tx) * TX, y0 = (t / tx) * TY;
     bool any = false;
-    for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j) {
-      int jj = j;
-      if (twoD) {
-        if (pery)
-          jj = imod(j, c.ny);
-        else if (j < 0 || j >= c.ny)
-          continue;
-      } else {
-        jj = 0;
-      }
-      const int64_t rowbase = (int64_t)jj * c.nx;
-      for (int i = x0 - R; i < x0 + TX + R && !any; ++i) {
-        int ii = i;
-        if (perx)
-          ii = imod(i, c.nx);
-        else if (i < 0 || i >= c.nx)
-          continue;
-        any = bit_get(kbits, rowbase + ii);
+    const bool inx = x0 - R >= 0 && x0 + TX + R <= c.nx;
+    const bool iny = !twoD || (y0 - Ry >= 0 && y0 + TY + Ry <= c.ny);
+    if (inx && iny && TX + 2 * R <= 64) {
+      for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j)
+        any = bits_any(kbits, (int64_t)(twoD ? j : 0) * c.nx + (x0 - R), TX + 2 * R);
+    } else {
+      for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j) {
+        int jj = j;
+        if (twoD) {
+          if (pery)
+            jj = imod(j, c.ny);
+          else if (j < 0 || j >= c.ny)
+            continue;
+        } else {
+          jj = 0;
+        }
+        const int64_t rowbase = (int64_t)jj * c.nx;
+        for (int i = x0 - R; i < x0 + TX + R && !any; ++i) {
+          int ii = i;
+          if (perx)
+            ii = imod(i, c.nx);
+          else if (i < 0 || i >= c.nx)
+            continue;
+          any = bit_get(kbits, rowbase + ii);
+        }
       }
     }
     if (any) tiles[atomicAdd(ntiles, 1)] = t;
