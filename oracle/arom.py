@@ -83,7 +83,15 @@ class Arom:
         return r.reshape(self.shape)
 
     def _gappy(self, v):
-        return rom.gappy_coords(self.Phi, self.P, self._flat(v), self._flat(self.psi))
+        rows = self._sample_rows() if self.cfg.regress_rows == W.ROWS_SAMPLE else self.P
+        return rom.gappy_coords(self.Phi, rows, self._flat(v), self._flat(self.psi))
+
+    def _sample_rows(self):
+        """All dof rows of the cells of S-hat in effect (variable-major): the
+        regression rows of the sample-row form of the reduced solve, which
+        contain P (P is a subset of S-hat, Sec. 2.2)."""
+        cells = np.flatnonzero(self.s_hat)
+        return np.concatenate([v * self.cfg.ncell + cells for v in range(self.cfg.nvar)])
 
     # -- one iteration of Algorithm 1's loop ----------------------------------
     def step(self):
@@ -145,7 +153,7 @@ class Arom:
             raw = float(np.sqrt(sum(float(np.sum(g * g)) for g in win)))
             self.Phi, _ = rom.pod(Xc, cfg.m, cfg.pod_tol, cfg.pod_abs * raw)  # POD
             self.P = rom.odeim(self.Phi, cfg.n_p, cfg.tie_tol)    # ODEIM
-            self.s_hat, self.s_tilde = select.build_masks(self.G, self.P, cfg)  # 26-28
+            self.s_hat, self.s_tilde = select.build_masks(self.G, self.P, cfg)  # sampling sets
             self.psi = rom.window_mean(win)                       # psi update
         info.n_p = len(self.P)
         info.m_eff = 0 if self.Phi is None else self.Phi.shape[1]

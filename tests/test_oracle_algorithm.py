@@ -93,3 +93,31 @@ def test_hybrid_trajectory_tracks_the_hdm():
     sbar, sstar, pbar = arom.sampling_averages(A.history, cfg.ncell, cfg.ndof)
     assert sbar == sstar          # z = infinity: warm-up steps are excluded
     assert 0 < sstar < 100
+
+
+def test_sample_rows_contain_the_points_and_reproduce_affine_states():
+    """Sample-row form of the reduced solve: the regression rows are all dofs
+    of S-hat, which contain the ODEIM rows P; a state psi + Phi a is
+    reproduced exactly from them."""
+    u0, cfg = _tiny_burgers(regress_rows=W.ROWS_SAMPLE)
+    A = arom.Arom(u0, cfg)
+    while True:
+        info = A.step()
+        if info.rebuilt and A.k >= cfg.w:
+            break
+    rows = A._sample_rows()
+    assert set(int(p) for p in A.P) <= set(int(r) for r in rows)
+    assert len(rows) == cfg.nvar * int(A.s_hat.sum())
+    a = np.random.Generator(np.random.PCG64(2)).standard_normal(A.Phi.shape[1])
+    truth = A._flat(A.psi) + A.Phi @ a
+    assert np.abs(A._gappy(truth.reshape(A.shape)) - a).max() < 1e-12
+
+
+def test_sample_row_hybrid_trajectory_tracks_the_hdm():
+    u0, cfg, _ = W.burgers_sine(n=128, seed=1)
+    cfg = cfg.with_(regress_rows=W.ROWS_SAMPLE)
+    steps = 40
+    A = arom.Arom(u0, cfg)
+    A.run(steps)
+    ref = arom.hdm_trajectory(u0, cfg, steps)
+    assert arom.rel_l1(A.gamma, ref[-1]) < 1e-5

@@ -32,7 +32,8 @@ SCHEME_BE, SCHEME_RK2 = 0, 1            # backward Euler (BDF1), SSP-RK2
 BC_PERIODIC, BC_OUTFLOW, BC_SHOCK = 0, 1, 2
 SEL_RRE, SEL_TOPFRAC = 0, 1             # RRE threshold delta, top fraction
 PREC_F64, PREC_F32 = 0, 1
-ROWS_ODEIM, ROWS_SAMPLE = 0, 1
+ROWS_ODEIM, ROWS_SAMPLE = 0, 1          # regression rows of the reduced solve
+RED_F32, RED_TF32, RED_BF16 = 0, 1, 2   # sample-row normal matrix: FP32 / tensor cores
 
 MASK64 = (1 << 64) - 1
 
@@ -96,6 +97,7 @@ class ArConfig:
     newton_tol: float = 1e-13
     newton_max: int = 50
     regress_rows: int = ROWS_ODEIM
+    reduced_prec: int = RED_F32
     precision: int = PREC_F64
     seed: int = 0
 
