@@ -59,6 +59,13 @@ enum { HYROM_SCHEME_BE = 0, HYROM_SCHEME_RK2 = 1 };
 enum { HYROM_BC_PERIODIC = 0, HYROM_BC_OUTFLOW = 1, HYROM_BC_SHOCK = 2 };
 enum { HYROM_SEL_RRE = 0, HYROM_SEL_TOPFRAC = 1 };
 enum { HYROM_PREC_F64 = 0, HYROM_PREC_F32 = 1 };
+/* Regression rows of the reduced solve: the ODEIM rows P (the paper's
+ * form), or every dof row of the sample cells S-hat (which contain P). */
+enum { HYROM_ROWS_ODEIM = 0, HYROM_ROWS_SAMPLE = 1 };
+/* Precision of the sample-row normal matrix Phi_S^T Phi_S: FP32 products
+ * (FP64 for FP64 states), or TF32 / BF16 products on the tensor cores; always
+ * accumulated in at least FP32, factored and solved in FP64. */
+enum { HYROM_RED_F32 = 0, HYROM_RED_TF32 = 1, HYROM_RED_BF16 = 2 };
 
 /* Run parameters.  HDM: Sec. 2.2 (Eqs. semi_disc, bdf, hdm) with
  * first-order FV fluxes (Burgers: Godunov; Euler, Sec. 3.1: Rusanov) and
@@ -74,14 +81,17 @@ enum { HYROM_PREC_F64 = 0, HYROM_PREC_F32 = 1 };
  * jmax_f passes (Sec. 2.3.4) for each Shapiro order filt_orders[0..n_filt)
  * (n = 1, 2, 3 for orders 2, 4, 6).  POD keeps mode j when
  * sigma_j > pod_tol*sigma_1 and sigma_j > pod_abs*||X_raw||_F.  Arg-max ties
- * within relative tie_tol go to the lowest index. */
+ * within relative tie_tol go to the lowest index.  The reduced coordinates
+ * are fitted on the rows regress_rows selects (HYROM_ROWS_*), the sample-row
+ * normal matrix in precision reduced_prec (HYROM_RED_*; TF32 and BF16 need
+ * FP32 states).  reserved_ must be 0. */
 typedef struct {
   int32_t pde, scheme, precision, nx, ny;
   int32_t bc[4];
   double dx, dy, dt, gamma;
   double shock_n[2], shock_d0, shock_speed, shock_pre[4], shock_post[4];
   int32_t w, m, z, n_p, sel_mode, halo, jmax, jmax_f, newton_max, n_filt;
-  int32_t filt_orders[3], regress_rows;
+  int32_t filt_orders[3], regress_rows, reduced_prec, reserved_;
   double delta, top_frac, eps_y, eps_f, pod_tol, pod_abs, tie_tol, newton_tol;
   uint64_t seed;
 } hyrom_config;
@@ -217,6 +227,15 @@ hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* 
  * rows, y_out: m doubles (device). */
 hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const int32_t* points,
                                int32_t n_p, const void* v, const void* psi, double* y_out);
+
+/* Sample-row reduced coordinates: y minimising ||(Phi y - (v - psi))_S||_2
+ * over every dof row of the n_cells cells (device int32, ascending), by the
+ * normal equations with the context's reduced_prec normal matrix and an FP64
+ * Cholesky solve.  phi: ndof x m (column-major, m <= 64), y_out: m doubles
+ * (device).  HYROM_ENOTCONV if the normal matrix is not positive definite. */
+hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,
+                                    const int32_t* cells, int32_t n_cells, const void* v,
+                                    const void* psi, double* y_out);
 
 /* Reconstruction on S-breve (Algorithm 1): q_io = psi + Phi y on
  * every cell whose bit in s_hat is clear (all cells when s_hat is NULL). */

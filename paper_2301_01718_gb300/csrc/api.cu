@@ -101,6 +101,16 @@ struct hyrom_ctx {
   double* tol_dev = nullptr;
   double* newton_ws = nullptr;
   int* fail_dev = nullptr;
+  // sample-row reduced solve: S-hat cells (ascending), normal-matrix partials,
+  // the normal matrix, its Cholesky factor and inverse diagonal, right-hand
+  // side; sample_ok = the factor of the current basis and S-hat is valid
+  int* s_cells = nullptr;
+  double* s_part = nullptr;
+  double* s_G = nullptr;
+  double* s_L = nullptr;
+  double* s_dinv = nullptr;
+  double* s_b = nullptr;
+  bool sample_ok = false;
   // pinned host mirror for read-backs
   void* host = nullptr;
   // optional per-stage CUDA-event timers (hyrom_profile): up to kEvPairs
@@ -213,6 +223,12 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
   if (c->sel_mode == HYROM_SEL_TOPFRAC && !(c->top_frac >= 0.0 && c->top_frac <= 1.0))
     return bad("top_frac in [0, 1]");
   if (c->halo < 0 || c->halo > 8) return bad("0 <= halo <= 8");
+  if (c->regress_rows != HYROM_ROWS_ODEIM && c->regress_rows != HYROM_ROWS_SAMPLE)
+    return bad("regress_rows");
+  if (c->reduced_prec < HYROM_RED_F32 || c->reduced_prec > HYROM_RED_BF16) return bad("reduced_prec");
+  if (c->reduced_prec != HYROM_RED_F32 && c->precision != HYROM_PREC_F32)
+    return bad("TF32 / BF16 normal matrices need FP32 states");
+  if (c->reserved_ != 0) return bad("reserved_ must be 0");
   if (c->jmax < 1 || c->jmax_f < 1 || c->newton_max < 1) return bad("iteration limits >= 1");
   if (c->n_filt < 0 || c->n_filt > 3) return bad("n_filt");
   for (int i = 0; i < c->n_filt; ++i)
@@ -284,6 +300,21 @@ void gram_update(hyrom_ctx* c, int64_t step) {
 }
 
 // ---------------------------------------------------------------------------
+// Reduced coordinates of v (Sec. 2.2): on the ODEIM rows P through the
+// stored pseudo-inverse, or on every dof row of S-hat through the stored
+// Cholesky factor of the sample-row normal matrix.
+template <typename T>
+void gappy_y(hyrom_ctx* ctx, const T* v, const T* psi, double* y, const double* y_prev,
+             double* dy) {
+  if (ctx->sample_ok)
+    hy::launch_sample_solve<T>((const T*)ctx->phi, ctx->N, ctx->m_eff, ctx->s_cells,
+                               (int)ctx->n_s, ctx->dc.nvar, ctx->nc, v, psi, ctx->s_part,
+                               ctx->s_b, ctx->s_L, ctx->s_dinv, y, y_prev, dy, ctx->st);
+  else
+    hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, v, psi, y, y_prev,
+                              dy, ctx->st);
+}
+
 // Algorithm 1, advance part: full-step test, full HDM step or hybrid step
 // ---------------------------------------------------------------------------
 
@@ -342,8 +373,7 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
       t_end(ctx, HYROM_T_PARTIAL);
       t_begin(ctx, HYROM_T_GAPPY);
       if (ctx->m_eff > 0)
-        hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, q, psi, ctx->y,
-                                  nullptr, nullptr, ctx->st);
+        gappy_y<T>(ctx, q, psi, ctx->y, nullptr, nullptr);
       t_end(ctx, HYROM_T_GAPPY);
       inf.J = 1;
     } else {
@@ -359,8 +389,7 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
           std::swap(yv, yo);
           break;
         }
-        hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, q, psi, yv,
-                                  j > 1 ? yo : nullptr, ctx->dy, ctx->st);
+        gappy_y<T>(ctx, q, psi, yv, j > 1 ? yo : nullptr, ctx->dy);
         CK(cudaMemcpyAsync(hd, ctx->dy, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         if (hyrom_status s2 = sync(ctx)) return s2;
         inf.dy_last = hd[0];
@@ -546,8 +575,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   if (k >= w && ctx->has_basis) {
     t_begin(ctx, HYROM_T_SELECT);
     if (ctx->m_eff > 0)
-      hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, gk,
-                                (const T*)ctx->psi, ctx->y2, nullptr, nullptr, ctx->st);
+      gappy_y<T>(ctx, gk, (const T*)ctx->psi, ctx->y2, nullptr, nullptr);
     hy::launch_cell_error<T>(gk, (const T*)ctx->psi, (const T*)ctx->phi, ctx->nc, ctx->dc.nvar,
                              ctx->m_eff, ctx->y2, (T*)ctx->eps, ctx->st);
     hy::launch_select(ctx->eps, ctx->f32, ctx->nc, cf.sel_mode, cf.delta, cf.top_frac, ctx->keys,
@@ -593,6 +621,22 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   // sampling sets
   if ((s = masks_and_tiles<T>(ctx, gbm, ctx->pts, ctx->np_eff, ctx->shat, ctx->stilde, &ctx->n_s)))
     return s;
+  // sample-row form: normal matrix of the new basis on the new S-hat
+  ctx->sample_ok = false;
+  if (cf.regress_rows == HYROM_ROWS_SAMPLE && me > 0 && ctx->n_s > 0) {
+    t_begin(ctx, HYROM_T_GAPPY);
+    hy::launch_bits_to_list(ctx->shat, ctx->nc, ctx->list_cnt, ctx->s_cells, ctx->nc, ctx->st);
+    CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, sizeof(int), ctx->st));
+    hy::launch_sample_normal<T>((const T*)ctx->phi, ctx->N, me, ctx->s_cells, (int)ctx->n_s,
+                                ctx->dc.nvar, ctx->nc, cf.reduced_prec, ctx->s_part, ctx->s_G,
+                                ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
+    t_end(ctx, HYROM_T_GAPPY);
+    int* hf = (int*)ctx->host + 12;
+    CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    if ((s = sync(ctx))) return s;
+    // a sample set that does not determine y falls back to the ODEIM rows
+    ctx->sample_ok = hf[0] == 0;
+  }
   if (cf.scheme == HYROM_SCHEME_RK2)
     hy::launch_active_tiles(ctx->dc, ctx->shat, hy::rk2_tile_width(ctx->dc),
                             hy::rk2_tile_height(ctx->dc), ctx->tiles, ctx->ntiles, ctx->st);
@@ -669,6 +713,14 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dalloc(ctx, &ctx->phi, (size_t)N * m * es);
   ok &= dal(ctx, &ctx->pts, 1024 * sizeof(int));
   ok &= dal(ctx, &ctx->pinv, (size_t)m * cfg->n_p * sizeof(double));
+  if (cfg->regress_rows == HYROM_ROWS_SAMPLE) {
+    ok &= dal(ctx, &ctx->s_cells, (size_t)nc * sizeof(int));
+    ok &= dal(ctx, &ctx->s_part, hy::sample_part_doubles() * sizeof(double));
+    ok &= dal(ctx, &ctx->s_G, 4096 * sizeof(double));
+    ok &= dal(ctx, &ctx->s_L, 4096 * sizeof(double));
+    ok &= dal(ctx, &ctx->s_dinv, 64 * sizeof(double));
+    ok &= dal(ctx, &ctx->s_b, 64 * sizeof(double));
+  }
   ok &= dal(ctx, &ctx->y, 256 * sizeof(double));
   ok &= dal(ctx, &ctx->y2, 256 * sizeof(double));
   ok &= dal(ctx, &ctx->dy, 64);
@@ -973,6 +1025,44 @@ hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const
   CKL();
   CK(cudaFreeAsync(pinv, ctx->st));
   return sync(ctx);
+}
+
+hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,
+                                    const int32_t* cells, int32_t n_cells, const void* v,
+                                    const void* psi, double* y_out) {
+  GUARD();
+  if (!phi || !cells || !v || !psi || !y_out || m < 1 || m > 64 || n_cells < 1 ||
+      n_cells > ctx->nc)
+    return HYROM_EINVAL;
+  if (ctx->cfg.regress_rows != HYROM_ROWS_SAMPLE)
+    return fail(ctx, HYROM_ESTATE, "the context was not configured for sample rows");
+  // the factor of the context's own basis is overwritten: fall back to the
+  // ODEIM rows until the next rebuild
+  ctx->sample_ok = false;
+  CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, sizeof(int), ctx->st));
+  if (ctx->f32) {
+    hy::launch_sample_normal<float>((const float*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
+                                    ctx->nc, ctx->cfg.reduced_prec, ctx->s_part, ctx->s_G,
+                                    ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
+    hy::launch_sample_solve<float>((const float*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
+                                   ctx->nc, (const float*)v, (const float*)psi, ctx->s_part,
+                                   ctx->s_b, ctx->s_L, ctx->s_dinv, y_out, nullptr, nullptr,
+                                   ctx->st);
+  } else {
+    hy::launch_sample_normal<double>((const double*)phi, ctx->N, m, cells, n_cells,
+                                     ctx->dc.nvar, ctx->nc, ctx->cfg.reduced_prec, ctx->s_part,
+                                     ctx->s_G, ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
+    hy::launch_sample_solve<double>((const double*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
+                                    ctx->nc, (const double*)v, (const double*)psi, ctx->s_part,
+                                    ctx->s_b, ctx->s_L, ctx->s_dinv, y_out, nullptr, nullptr,
+                                    ctx->st);
+  }
+  CKL();
+  int* hf = (int*)ctx->host + 12;
+  CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status st = sync(ctx)) return st;
+  if (hf[0]) return fail(ctx, HYROM_ENOTCONV, "sample-row normal matrix is not positive definite");
+  return HYROM_OK;
 }
 
 hyrom_status hyrom_stage_reconstruct(hyrom_ctx* ctx, const void* phi, int32_t m, const double* y,

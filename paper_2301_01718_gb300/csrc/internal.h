@@ -118,6 +118,19 @@ void launch_active_tiles(const DevCfg& c, const uint32_t* bm, int TX, int TY, in
 void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch, int* out,
                          int64_t cap, cudaStream_t s);
 
+// reduced.cu: sample-row reduced solve (normal equations on all dof rows
+// of the listed cells; red = HYROM_RED_* precision of the normal matrix)
+size_t sample_part_doubles();
+template <typename T>
+void launch_sample_normal(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
+                          int64_t nc, int red, double* part, double* G, double* L, double* dinv,
+                          int* fail, cudaStream_t s);
+template <typename T>
+void launch_sample_solve(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
+                         int64_t nc, const T* v, const T* psi, double* part, double* b,
+                         const double* L, const double* dinv, double* y, const double* y_prev,
+                         double* dy, cudaStream_t s);
+
 // odeim.cu
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,

@@ -1,0 +1,274 @@
+// Sample-row form of the reduced solve (Sec. 2.2, reduced coordinates, with
+// every dof row of the sample cells S-hat as regression rows instead of the
+// ODEIM rows P, which S-hat contains):
+//   y = argmin || (Phi y - (v - psi))_S ||_2,
+// solved through the normal equations
+//   (Phi_S^T Phi_S) y = Phi_S^T (v - psi)_S.
+// The m x m normal matrix is formed once per basis and sample set (at the
+// rebuild) and Cholesky-factored in FP64; each solve forms the right-hand
+// side (one pass over the sample rows of Phi, v and psi) and substitutes.
+// Rows are variable-major: row r = (v, cell) with v = r / n_s and cell the
+// (r % n_s)-th sample cell in ascending order.
+//
+// The normal matrix comes in three precisions (the reduced-precision form of
+// the sample-row solve): FP32 products accumulated in FP32 within a CTA and
+// in FP64 across CTAs (FP64 throughout for FP64 states), or TF32 / BF16
+// products on the tensor cores accumulated in FP32 (reduced_tc.cu).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hy {
+namespace {
+
+constexpr int kRowsChunk = 64;  // rows staged per iteration
+constexpr int kPad = 68;        // staged row stride (floats or doubles)
+
+HY_DEV int64_t sample_dof(const int* __restrict__ cells, int ns, int64_t nc, int64_t r) {
+  const int v = (int)(r / ns);
+  return (int64_t)v * nc + cells[r - (int64_t)v * ns];
+}
+
+// CTA b accumulates the rows [b * rpc, (b + 1) * rpc): thread t owns the 4 x 4
+// block (t / 16, t % 16) of the 64 x 64 matrix (columns >= m are zero).  With
+// rhs != nullptr it forms the right-hand side instead (threads 0..63, one
+// column each).  A: accumulator type (float for FP32 states, double for
+// FP64).  Partials (FP64) go to part[b * 64 * 64 ...] or part[b * 64 ...].
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_sample_moments(
+    const T* __restrict__ phi, int64_t N, int m, const int* __restrict__ cells, int ns, int nvar,
+    int64_t nc, int64_t rpc, const T* __restrict__ v, const T* __restrict__ psi, int rhs,
+    double* __restrict__ part) {
+  __shared__ A xs[kRowsChunk][kPad];
+  __shared__ A ds[kRowsChunk];
+  const int tid = threadIdx.x;
+  const int bi = tid >> 4, bj = tid & 15;
+  A acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = A(0);
+  A accr = A(0);
+  const int64_t nrows = (int64_t)ns * nvar;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int64_t r1 = r0 + rpc < nrows ? r0 + rpc : nrows;
+  for (int64_t base = r0; base < r1; base += kRowsChunk) {
+    __syncthreads();
+    // stage 64 rows x 64 columns: consecutive threads take consecutive rows
+    // of one column (coalesced along the sorted cells)
+#pragma unroll 4
+    for (int idx = tid; idx < kRowsChunk * 64; idx += 256) {
+      const int rr = idx & (kRowsChunk - 1), j = idx >> 6;
+      const int64_t r = base + rr;
+      A x = A(0);
+      if (r < r1 && j < m) x = (A)phi[(int64_t)j * N + sample_dof(cells, ns, nc, r)];
+      xs[rr][j] = x;
+    }
+    if (rhs && tid < kRowsChunk) {
+      const int64_t r = base + tid;
+      A d = A(0);
+      if (r < r1) {
+        const int64_t dof = sample_dof(cells, ns, nc, r);
+        d = (A)v[dof] - (A)psi[dof];
+      }
+      ds[tid] = d;
+    }
+    __syncthreads();
+    if (rhs) {
+      if (tid < 64)
+        for (int rr = 0; rr < kRowsChunk; ++rr) accr = fma(xs[rr][tid], ds[rr], accr);
+    } else {
+      for (int rr = 0; rr < kRowsChunk; ++rr) {
+        A x4[4], y4[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          x4[a] = xs[rr][4 * bi + a];
+          y4[a] = xs[rr][4 * bj + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(x4[a], y4[b], acc[a][b]);
+      }
+    }
+  }
+  if (rhs) {
+    if (tid < 64) part[(int64_t)blockIdx.x * 64 + tid] = (double)accr;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        part[(int64_t)blockIdx.x * 4096 + (4 * bi + a) * 64 + 4 * bj + b] = (double)acc[a][b];
+  }
+}
+
+// out[e] = sum over nb partials of part[b * len + e] (FP64, four chains)
+__global__ void k_sum_partials(const double* __restrict__ part, int nb, int len,
+                               double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int b = 0;
+    for (; b + 3 < nb; b += 4)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] += part[(int64_t)(b + u) * len + e];
+    for (; b < nb; ++b) s[0] += part[(int64_t)b * len + e];
+    out[e] = (s[0] + s[1]) + (s[2] + s[3]);
+  }
+}
+
+// FP64 Cholesky G = L L^T of the m x m normal matrix (stored 64 x 64), one
+// CTA.  L (lower, 64 x 64) and inverse diagonal to Lout / dinv; *fail = 1 if a
+// pivot is not positive (the sample rows do not determine y).
+__global__ void k_sample_chol(const double* __restrict__ G, int m, double* __restrict__ Lout,
+                              double* __restrict__ dinv, int* __restrict__ fail) {
+  __shared__ double Ls[64][65];
+  __shared__ double piv[2];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < 64 * 64; idx += blockDim.x) {
+    const int i = idx >> 6, j = idx & 63;
+    Ls[i][j] = (i < m && j < m) ? G[idx] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (tid == 0) {
+      const double a = Ls[k][k];
+      if (!(a > 0.0)) {
+        *fail = 1;
+        piv[0] = 0.0;
+        piv[1] = 0.0;
+      } else {
+        // 1/sqrt(a) from an FP32 seed and two FP64 Newton steps
+        double y = (double)rsqrtf((float)a);
+        y = y * fma(-0.5 * a * y, y, 1.5);
+        y = y * fma(-0.5 * a * y, y, 1.5);
+        piv[0] = a * y;  // sqrt(a)
+        piv[1] = y;      // 1 / sqrt(a)
+      }
+    }
+    __syncthreads();
+    const double r = piv[1];
+    if (tid == 0) Ls[k][k] = piv[0];
+    for (int i = k + 1 + tid; i < m; i += blockDim.x) Ls[i][k] *= r;
+    __syncthreads();
+    // trailing update of the lower triangle, one thread per (i, j), j <= i
+    const int s = m - k - 1;
+    for (int idx = tid; idx < s * s; idx += blockDim.x) {
+      const int i = k + 1 + idx / s, j = k + 1 + idx % s;
+      if (j <= i) Ls[i][j] = fma(-Ls[i][k], Ls[j][k], Ls[i][j]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < 64 * 64; idx += blockDim.x) {
+    const int i = idx >> 6, j = idx & 63;
+    Lout[idx] = (i < m && j <= i) ? Ls[i][j] : 0.0;
+  }
+  for (int i = tid; i < 64; i += blockDim.x) dinv[i] = i < m && Ls[i][i] > 0.0 ? 1.0 / Ls[i][i] : 0.0;
+}
+
+// y = L^{-T} L^{-1} b by one warp (column-oriented, reciprocal diagonal);
+// with y_prev, *dy = ||y - y_prev||_2.
+__global__ void k_sample_solve(const double* __restrict__ L, const double* __restrict__ dinv,
+                               const double* __restrict__ b, int m, double* __restrict__ y,
+                               const double* __restrict__ y_prev, double* __restrict__ dy) {
+  __shared__ double Ls[64][65];
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) Ls[idx >> 6][idx & 63] = L[idx];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double x0 = lane < m ? b[lane] : 0.0, x1 = lane + 32 < m ? b[lane + 32] : 0.0;
+  const double i0 = dinv[lane], i1 = dinv[lane + 32];
+  for (int k = 0; k < m; ++k) {  // forward: L z = b
+    const double zk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31) *
+                      __shfl_sync(0xffffffffu, k < 32 ? i0 : i1, k & 31);
+    if (lane == (k & 31)) {
+      if (k < 32)
+        x0 = zk;
+      else
+        x1 = zk;
+    }
+    if (lane > k && lane < m) x0 = fma(-Ls[lane][k], zk, x0);
+    if (lane + 32 > k && lane + 32 < m) x1 = fma(-Ls[lane + 32][k], zk, x1);
+  }
+  for (int k = m - 1; k >= 0; --k) {  // backward: L^T y = z
+    const double yk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31) *
+                      __shfl_sync(0xffffffffu, k < 32 ? i0 : i1, k & 31);
+    if (lane == (k & 31)) {
+      if (k < 32)
+        x0 = yk;
+      else
+        x1 = yk;
+    }
+    if (lane < k) x0 = fma(-Ls[k][lane], yk, x0);
+    if (lane + 32 < k) x1 = fma(-Ls[k][lane + 32], yk, x1);
+  }
+  double d = 0.0;
+  if (lane < m) {
+    if (y_prev) d = (x0 - y_prev[lane]) * (x0 - y_prev[lane]);
+    y[lane] = x0;
+  }
+  if (lane + 32 < m) {
+    if (y_prev) d = fma(x1 - y_prev[lane + 32], x1 - y_prev[lane + 32], d);
+    y[lane + 32] = x1;
+  }
+  d = warp_sum(d);
+  if (lane == 0 && y_prev && dy) *dy = sqrt(d);
+}
+
+int nblocks_for(int64_t nrows) {
+  int64_t nb = (nrows + 2047) / 2048;
+  if (nb > 152 * 2) nb = 152 * 2;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+}  // namespace
+
+size_t sample_part_doubles() { return (size_t)152 * 2 * 4096; }
+
+template <typename T>
+void launch_sample_normal(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
+                          int64_t nc, int red, double* part, double* G, double* L, double* dinv,
+                          int* fail, cudaStream_t s) {
+  (void)red;
+  const int64_t nrows = (int64_t)ns * nvar;
+  const int nb = nblocks_for(nrows);
+  const int64_t rpc = (nrows + nb - 1) / nb;
+  using A = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  k_sample_moments<T, A><<<nb, 256, 0, HY_S(s)>>>(phi, N, m, cells, ns, nvar, nc, rpc, nullptr,
+                                                   nullptr, 0, part);
+  k_sum_partials<<<16, 256, 0, HY_S(s)>>>(part, nb, 4096, G);
+  k_sample_chol<<<1, 256, 0, HY_S(s)>>>(G, m, L, dinv, fail);
+}
+
+template <typename T>
+void launch_sample_solve(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
+                         int64_t nc, const T* v, const T* psi, double* part, double* b,
+                         const double* L, const double* dinv, double* y, const double* y_prev,
+                         double* dy, cudaStream_t s) {
+  const int64_t nrows = (int64_t)ns * nvar;
+  const int nb = nblocks_for(nrows);
+  const int64_t rpc = (nrows + nb - 1) / nb;
+  using A = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  k_sample_moments<T, A><<<nb, 256, 0, HY_S(s)>>>(phi, N, m, cells, ns, nvar, nc, rpc, v, psi, 1,
+                                                   part);
+  k_sum_partials<<<1, 64, 0, HY_S(s)>>>(part, nb, 64, b);
+  k_sample_solve<<<1, 256, 0, HY_S(s)>>>(L, dinv, b, m, y, y_prev, dy);
+}
+
+#define HY_INST(T)                                                                            \
+  template void launch_sample_normal<T>(const T*, int64_t, int, const int*, int, int, int64_t, \
+                                        int, double*, double*, double*, double*, int*,         \
+                                        cudaStream_t);                                         \
+  template void launch_sample_solve<T>(const T*, int64_t, int, const int*, int, int, int64_t,  \
+                                       const T*, const T*, double*, double*, const double*,    \
+                                       const double*, double*, const double*, double*,         \
+                                       cudaStream_t);
+HY_INST(float)
+HY_INST(double)
+#undef HY_INST
+
+}  // namespace hy

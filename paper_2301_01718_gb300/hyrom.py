@@ -32,6 +32,7 @@ class HyromConfig(C.Structure):
         ("sel_mode", C.c_int32), ("halo", C.c_int32), ("jmax", C.c_int32),
         ("jmax_f", C.c_int32), ("newton_max", C.c_int32), ("n_filt", C.c_int32),
         ("filt_orders", C.c_int32 * 3), ("regress_rows", C.c_int32),
+        ("reduced_prec", C.c_int32), ("reserved_", C.c_int32),
         ("delta", C.c_double), ("top_frac", C.c_double), ("eps_y", C.c_double),
         ("eps_f", C.c_double), ("pod_tol", C.c_double), ("pod_abs", C.c_double),
         ("tie_tol", C.c_double), ("newton_tol", C.c_double),
@@ -132,6 +133,7 @@ def lib():
         "hyrom_stage_pod": (st, [vp, vp, i32, vp, vp, vp, C.POINTER(i32)]),
         "hyrom_stage_odeim": (st, [vp, vp, i32, i32, vp]),
         "hyrom_stage_masks": (st, [vp, vp, vp, i32, vp, vp, C.POINTER(i32)]),
+        "hyrom_stage_gappy_rows": (st, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
     }
     for name, (res, args) in sigs.items():
@@ -287,6 +289,11 @@ def hyrom_stage_pod(ctx, window, w, psi, phi_out, sigma_out=None):
 
 def hyrom_stage_odeim(ctx, phi, m, n_p, points_out):
     _check(ctx, lib().hyrom_stage_odeim(ctx, _ptr(phi), int(m), int(n_p), _ptr(points_out)))
+
+
+def hyrom_stage_gappy_rows(ctx, phi, m, cells, n_cells, v, psi, y_out):
+    _check(ctx, lib().hyrom_stage_gappy_rows(ctx, _ptr(phi), int(m), _ptr(cells), int(n_cells),
+                                             _ptr(v), _ptr(psi), _ptr(y_out)))
 
 
 def hyrom_stage_masks(ctx, g_bitmap, points, n_p, s_hat, s_tilde):

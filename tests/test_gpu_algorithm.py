@@ -19,6 +19,13 @@ def _cases():
                                pod_abs=1e-13, top_frac=0.05), 16
     q, c, _ = W.euler_oblique_shock(n=64, seed=3, k=3)
     yield "shock", q, c.with_(precision=W.PREC_F64, pod_tol=1e-10, pod_abs=1e-13), 16
+    # the sample-row form of the reduced solve (all dof rows of S-hat)
+    u, c, _ = W.burgers_sine(n=256, seed=1)
+    yield "burgers_sample_rows", u, c.with_(w=8, m=4, n_p=8, regress_rows=W.ROWS_SAMPLE), 30
+    q, c, _ = W.euler_vortex(n=48, seed=2)
+    yield "vortex_sample_rows", q, c.with_(w=6, m=4, n_p=8, precision=W.PREC_F64,
+                                           pod_tol=1e-10, pod_abs=1e-13, top_frac=0.05,
+                                           regress_rows=W.ROWS_SAMPLE), 16
 
 
 def _lockstep(q0, cfg, steps):

@@ -115,6 +115,34 @@ def test_pod_of_known_spectrum(prec, w):
         assert np.abs(Pg @ Pg.T - Phi_o @ Phi_o.T).max() < 2e-4
 
 
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+@pytest.mark.parametrize("frac", [0.03, 0.3])
+def test_sample_row_coordinates(prec, frac):
+    """Sample-row reduced coordinates (every dof row of a cell set, normal
+    equations, FP64 Cholesky) against the oracle's least squares on the same
+    rows: 1e-12 relative in FP64, 1e-5 in FP32 (FP32 products summed in FP32
+    within a block; more than 128 rows per block and several blocks)."""
+    cfg = _cfg(prec, nx=96, ny=64, m=24, n_p=48, w=48).with_(regress_rows=W.ROWS_SAMPLE)
+    N, nc = cfg.ndof, cfg.ncell
+    Phi = _basis(N, cfg.m, 21, prec, concentrated=False)
+    g = np.random.Generator(np.random.PCG64(22))
+    cells = np.flatnonzero(g.random(nc) < frac).astype(np.int32)
+    psi = g.standard_normal(N)
+    v = psi + Phi @ g.standard_normal(cfg.m) + 1e-2 * g.standard_normal(N)
+    if prec == W.PREC_F32:
+        psi, v = (x.astype(np.float32).astype(np.float64) for x in (psi, v))
+    rows = np.concatenate([a * nc + cells for a in range(4)])
+    want = rom.gappy_coords(Phi, rows, v, psi)
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        y = torch.zeros(cfg.m, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_gappy_rows(ctx, dev(Phi.T.copy(), dt), cfg.m, dev(cells, torch.int32),
+                                  len(cells), dev(v, dt), dev(psi, dt), y)
+        got = host(y)
+    tol = 1e-12 if prec == W.PREC_F64 else 1e-5
+    assert rel_err(got, want) < tol, rel_err(got, want)
+
+
 @pytest.mark.parametrize("pde,nx,ny", [(W.PDE_BURGERS, 1073, 1), (W.PDE_EULER, 33, 17)])
 @pytest.mark.parametrize("m", [20, 40])
 def test_pod_fp32_wide_basis(pde, nx, ny, m):
