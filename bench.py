@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-err", action="store_true")
+    p.add_argument("--no-precision-form", action="store_true")
+    p.add_argument("--precision-steps", type=int, default=4,
+                   help="timed steps per variant of the precision form")
     return p.parse_args()
 
 
@@ -307,6 +310,8 @@ def run_ours(a):
            "odeim_counters_last_step": odc}
     if rank == 0 and not a.no_err:
         out["err_vs_fp64"] = err_vs_fp64(a)
+    if rank == 0 and not a.no_precision_form:
+        out["precision_form"] = precision_form(a)
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(a)
     if world > 1:
@@ -331,17 +336,21 @@ def _peaks():
         return {"hbm": 6800.0, "src": "fallback 6.8 TB/s"}
 
 
-def err_vs_fp64(a, n=256, steps=12):
+def err_vs_fp64(a, n=256, steps=12, **kw):
     """FP32 GPU run against the FP64 GPU run (itself checked against the
     oracle by the parity tests) of the same workload on an n^2 grid: relative
-    L1 and max errors of the state after `steps` hybrid steps."""
+    L1 and max errors of the state after `steps` hybrid steps.  kw: config
+    fields of the FP32 run (the FP64 run keeps the FP32 normal matrix, the
+    only one FP64 states have)."""
     import torch
     from paper_2301_01718_gb300 import hyrom
     outs = {}
     for prec in (W.PREC_F32, W.PREC_F64):
         q0, cfg = workload(a, n=n, prec=prec)
+        if kw:
+            cfg = cfg.with_(**kw)
         if prec == W.PREC_F64:
-            cfg = cfg.with_(pod_tol=1e-10, pod_abs=1e-13)
+            cfg = cfg.with_(pod_tol=1e-10, pod_abs=1e-13, reduced_prec=W.RED_F32)
         q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
         ctx = hyrom.hyrom_init(cfg, q0d)
         try:
@@ -359,6 +368,57 @@ def err_vs_fp64(a, n=256, steps=12):
     return {"grid": f"{n}x{n}", "hybrid_steps": steps,
             "rel_l1": float(np.abs(d).sum() / np.abs(outs[W.PREC_F64]).sum()),
             "rel_max": float(np.abs(d).max() / np.abs(outs[W.PREC_F64]).max())}
+
+
+PRECISIONS = {"f32_cuda_cores": W.RED_F32, "tf32": W.RED_TF32, "bf16": W.RED_BF16,
+              "tf32_split": W.RED_TF32_SPLIT}
+
+
+def precision_form(a):
+    """The reduced solve in its sample-row form (every dof row of S-hat) with
+    the normal matrix Phi_S^T Phi_S in each precision: FP32 on the CUDA cores,
+    TF32 and BF16 on the tensor cores (FP32 accumulation), and the TF32 hi/lo
+    split; states, flux and right-hand side FP32, Cholesky and solve FP64.
+    Per variant: the normal matrix's time per rebuild, steps/s of the whole
+    step on the benchmark workload, and the state error against FP64."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    out = {}
+    for name, red in PRECISIONS.items():
+        q0, cfg = workload(a)
+        cfg = cfg.with_(regress_rows=W.ROWS_SAMPLE, reduced_prec=red)
+        stream = torch.cuda.Stream()
+        q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+        ctx = hyrom.hyrom_init(cfg, q0d, stream=stream.cuda_stream)
+        del q0d
+        try:
+            while hyrom.hyrom_step(ctx)["was_full"]:
+                pass
+            for _ in range(3):
+                hyrom.hyrom_step(ctx)
+            hyrom.hyrom_profile(ctx, True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.precision_steps):
+                hyrom.hyrom_step(ctx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = hyrom.hyrom_stage_times(ctx)
+            hyrom.hyrom_profile(ctx, False)
+        finally:
+            hyrom.hyrom_destroy(ctx)
+        tot, cnt = st["snormal"]
+        gt, gc = st["gappy"]
+        out[name] = {"snormal_ms_per_rebuild": tot / max(cnt, 1), "rebuilds": cnt,
+                     "gappy_ms_per_step": gt / a.precision_steps,
+                     "steps_per_s": a.precision_steps / (ms / 1e3),
+                     "err_vs_fp64": None if a.no_err else err_vs_fp64(
+                         a, regress_rows=W.ROWS_SAMPLE, reduced_prec=red)}
+    return {"workload": "same grid and method, reduced coordinates fitted on every dof row "
+                        "of S-hat (normal equations)", "steps": a.precision_steps,
+            "variants": out}
 
 
 def run_reference(a):

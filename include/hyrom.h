@@ -63,9 +63,11 @@ enum { HYROM_PREC_F64 = 0, HYROM_PREC_F32 = 1 };
  * form), or every dof row of the sample cells S-hat (which contain P). */
 enum { HYROM_ROWS_ODEIM = 0, HYROM_ROWS_SAMPLE = 1 };
 /* Precision of the sample-row normal matrix Phi_S^T Phi_S: FP32 products
- * (FP64 for FP64 states), or TF32 / BF16 products on the tensor cores; always
+ * on the CUDA cores (FP64 for FP64 states), or on the tensor cores TF32
+ * products (inputs rounded to nearest, relative error 2^-11), BF16 products
+ * (2^-8), or FP32-level products of a TF32 hi/lo split of each input; always
  * accumulated in at least FP32, factored and solved in FP64. */
-enum { HYROM_RED_F32 = 0, HYROM_RED_TF32 = 1, HYROM_RED_BF16 = 2 };
+enum { HYROM_RED_F32 = 0, HYROM_RED_TF32 = 1, HYROM_RED_BF16 = 2, HYROM_RED_TF32_SPLIT = 3 };
 
 /* Run parameters.  HDM: Sec. 2.2 (Eqs. semi_disc, bdf, hdm) with
  * first-order FV fluxes (Burgers: Godunov; Euler, Sec. 3.1: Rusanov) and
@@ -83,8 +85,8 @@ enum { HYROM_RED_F32 = 0, HYROM_RED_TF32 = 1, HYROM_RED_BF16 = 2 };
  * sigma_j > pod_tol*sigma_1 and sigma_j > pod_abs*||X_raw||_F.  Arg-max ties
  * within relative tie_tol go to the lowest index.  The reduced coordinates
  * are fitted on the rows regress_rows selects (HYROM_ROWS_*), the sample-row
- * normal matrix in precision reduced_prec (HYROM_RED_*; TF32 and BF16 need
- * FP32 states).  reserved_ must be 0. */
+ * normal matrix in precision reduced_prec (HYROM_RED_*; the tensor-core
+ * precisions need FP32 states).  reserved_ must be 0. */
 typedef struct {
   int32_t pde, scheme, precision, nx, ny;
   int32_t bc[4];
@@ -159,7 +161,8 @@ enum {
   HYROM_T_OD_EXACT = 15,  /* exact scores of the surviving rows            */
   HYROM_T_OD_UPDATE = 16, /* rank-one eigensystem update                   */
   HYROM_T_OD_PICK = 17,   /* tie-aware arg-max and commit                  */
-  HYROM_NSTAGE = 18
+  HYROM_T_SNORMAL = 18,   /* sample-row normal matrix and its factor       */
+  HYROM_NSTAGE = 19
 };
 hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
 /* Work counters of the last ODEIM call (rebuild or stage entry point):

@@ -9,6 +9,12 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
                  starts from)
   odeim          ODEIM_{n_p} (Eq. odeim): DEIM points, then oversampling
   window_mean    psi = (1/w) sum of w snapshots   (Eq. mean)
+  gappy_coords_normal
+                 the same coordinates on the rows given, from the normal
+                 equations with the normal matrix formed from inputs rounded
+                 to TF32, BF16 or a TF32 hi/lo pair (the reduced-precision
+                 form of the sample-row solve); round_tf32, round_bf16 and
+                 split_tf32 are those roundings, bit for bit
 
 Readings where the paper is silent (listed in the design doc):
   * numerical rank: mode j is kept when sigma_j > pod_tol * sigma_1 and
@@ -29,6 +35,8 @@ Readings where the paper is silent (listed in the design doc):
 from __future__ import annotations
 
 import numpy as np
+
+import workloads as W
 
 
 def pod(Xc, m, pod_tol, abs_floor=0.0):
@@ -63,6 +71,57 @@ def gappy_coords(Phi, P, v, psi):
     b = v[P] - psi[P]
     y, *_ = np.linalg.lstsq(A, b, rcond=None)
     return y
+
+
+def round_tf32(x):
+    """FP32 values rounded to TF32 (10 stored mantissa bits; FP32 exponent
+    range), to nearest with ties away from zero: half of the dropped 13-bit
+    field is added to the magnitude bits, which are then cut.  Finite inputs
+    whose magnitude rounds below FP32's largest finite value."""
+    b = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def round_bf16(x):
+    """FP32 values rounded to BF16 (7 stored mantissa bits), to nearest with
+    ties to even (the kept field's lowest bit decides a tie).  Finite
+    inputs."""
+    b = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def split_tf32(x):
+    """x = hi + lo with hi = x's 13 low mantissa bits cleared (a TF32 value)
+    and lo = round_tf32(x - hi) (x - hi is exact in FP32): hi + lo is within
+    2^-21 |x| of x."""
+    x32 = np.ascontiguousarray(np.asarray(x, np.float32))
+    hi = (x32.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    return hi.astype(np.float64), round_tf32(x32 - hi)
+
+
+def gappy_coords_normal(Phi, rows, v, psi, red):
+    """Reduced coordinates (Eq. red_coord) on `rows` from the normal
+    equations (X^T X) y = X^T (v - psi)_rows, X = Phi[rows], where the
+    normal matrix is formed from X rounded as `red` says (workloads.RED_*:
+    F32 = the FP32 values as given, TF32 / BF16 = round_tf32 / round_bf16,
+    TF32_SPLIT = hi + lo of split_tf32), and the right-hand side from X as
+    given; everything in FP64, solved by Cholesky."""
+    X = np.asarray(Phi, np.float64)[rows, :]
+    if red == W.RED_TF32:
+        Xr = round_tf32(X)
+    elif red == W.RED_BF16:
+        Xr = round_bf16(X)
+    elif red == W.RED_TF32_SPLIT:
+        hi, lo = split_tf32(X)
+        Xr = hi + lo
+    else:
+        Xr = X
+    G = Xr.T @ Xr
+    b = X.T @ (np.asarray(v, np.float64)[rows] - np.asarray(psi, np.float64)[rows])
+    L = np.linalg.cholesky(G)
+    return np.linalg.solve(L.T, np.linalg.solve(L, b))
 
 
 def argmax_tie(score, tie_tol, exclude=()):

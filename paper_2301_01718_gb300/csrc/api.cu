@@ -225,9 +225,10 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
   if (c->halo < 0 || c->halo > 8) return bad("0 <= halo <= 8");
   if (c->regress_rows != HYROM_ROWS_ODEIM && c->regress_rows != HYROM_ROWS_SAMPLE)
     return bad("regress_rows");
-  if (c->reduced_prec < HYROM_RED_F32 || c->reduced_prec > HYROM_RED_BF16) return bad("reduced_prec");
+  if (c->reduced_prec < HYROM_RED_F32 || c->reduced_prec > HYROM_RED_TF32_SPLIT)
+    return bad("reduced_prec");
   if (c->reduced_prec != HYROM_RED_F32 && c->precision != HYROM_PREC_F32)
-    return bad("TF32 / BF16 normal matrices need FP32 states");
+    return bad("tensor-core normal matrices need FP32 states");
   if (c->reserved_ != 0) return bad("reserved_ must be 0");
   if (c->jmax < 1 || c->jmax_f < 1 || c->newton_max < 1) return bad("iteration limits >= 1");
   if (c->n_filt < 0 || c->n_filt > 3) return bad("n_filt");
@@ -624,16 +625,17 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   // sample-row form: normal matrix of the new basis on the new S-hat
   ctx->sample_ok = false;
   if (cf.regress_rows == HYROM_ROWS_SAMPLE && me > 0 && ctx->n_s > 0) {
-    t_begin(ctx, HYROM_T_GAPPY);
+    t_begin(ctx, HYROM_T_SNORMAL);
     hy::launch_bits_to_list(ctx->shat, ctx->nc, ctx->list_cnt, ctx->s_cells, ctx->nc, ctx->st);
-    CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, 2 * sizeof(int), ctx->st));
     hy::launch_sample_normal<T>((const T*)ctx->phi, ctx->N, me, ctx->s_cells, (int)ctx->n_s,
                                 ctx->dc.nvar, ctx->nc, cf.reduced_prec, ctx->s_part, ctx->s_G,
                                 ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
-    t_end(ctx, HYROM_T_GAPPY);
+    t_end(ctx, HYROM_T_SNORMAL);
     int* hf = (int*)ctx->host + 12;
-    CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     if ((s = sync(ctx))) return s;
+    if (hf[1]) return fail(ctx, HYROM_ETIMEOUT, "sample-row normal matrix: a device wait gave up");
     // a sample set that does not determine y falls back to the ODEIM rows
     ctx->sample_ok = hf[0] == 0;
   }
@@ -1039,7 +1041,7 @@ hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,
   // the factor of the context's own basis is overwritten: fall back to the
   // ODEIM rows until the next rebuild
   ctx->sample_ok = false;
-  CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, 2 * sizeof(int), ctx->st));
   if (ctx->f32) {
     hy::launch_sample_normal<float>((const float*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
                                     ctx->nc, ctx->cfg.reduced_prec, ctx->s_part, ctx->s_G,
@@ -1059,8 +1061,9 @@ hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,
   }
   CKL();
   int* hf = (int*)ctx->host + 12;
-  CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(hf, ctx->fail_dev + 8, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (hyrom_status st = sync(ctx)) return st;
+  if (hf[1]) return fail(ctx, HYROM_ETIMEOUT, "sample-row normal matrix: a device wait gave up");
   if (hf[0]) return fail(ctx, HYROM_ENOTCONV, "sample-row normal matrix is not positive definite");
   return HYROM_OK;
 }

@@ -31,9 +31,12 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace hy {
 namespace {
+
+using namespace tc;
 
 constexpr int kRows = 128;     // tile rows (UMMA M)
 constexpr int kCols = 64;      // basis columns (UMMA N), zero padded beyond m_eff
@@ -42,13 +45,11 @@ constexpr int kMaxW = 128;
 constexpr int kThreads = 384;  // 12 warps: producer, MMA, 2 idle, 4 epilogue, 4 converters
 constexpr int kRawStages = 4;
 constexpr int kAStages = 2;
-constexpr int kAtomGroup = 1024;                          // 8 rows x 128 bytes
 constexpr int kBBytes = (kMaxW / kChunk) * (kCols / 8) * kAtomGroup;  // 32 KB
 constexpr int kABytes = (kRows / 8) * kAtomGroup;                    // 16 KB
 constexpr int kRawBytes = kChunk * kRows * 4;                        // 16 KB
 constexpr int kSmemBytes = 2 * kBBytes + kAStages * 2 * kABytes + kRawStages * kRawBytes + 1024;
 constexpr uint32_t kTmemCols = 128;  // two 64-column accumulators
-constexpr uint32_t kWaitLimit = 1u << 20;
 
 // kind::tf32: D in FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9
 // and 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
@@ -56,97 +57,13 @@ constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
                             ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
-HY_DEV uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of element (row, k) in a K-major, 128-byte-swizzled block of
-// 8-row groups holding one 32-element atom along k: row r of a group is 128
-// bytes at r * 128, and its 16-byte chunk c sits at chunk position c ^ r.
-HY_DEV int sw128(int row, int k) {
-  const int g = row >> 3, r = row & 7, c = k >> 2, e = k & 3;
-  return g * kAtomGroup + r * 128 + ((c ^ r) << 4) + (e << 2);
-}
-
-// shared-memory matrix descriptor: start address, leading offset (unused by
-// swizzled K-major layouts), stride between 8-row groups 1024 bytes,
-// descriptor version 1, 128-byte swizzle
-HY_DEV uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
-         ((uint64_t)(kAtomGroup >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-HY_DEV void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count)
-               : "memory");
-}
-
-HY_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = saddr(bar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-HY_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-HY_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(saddr(dst)),
-      "l"(src), "r"(bytes), "r"(saddr(bar))
-      : "memory");
-}
-
-HY_DEV void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-HY_DEV void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          saddr(bar))
-      : "memory");
+HY_DEV void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  mma_tf32(d, a, b, kIdesc, accumulate);
 }
 
 HY_DEV void split_tf32(float x, float& hi, float& lo) {
   hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
   lo = x - hi;
-}
-
-HY_DEV void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-      "[%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -266,9 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kk = 0; kk < kChunk / 8; ++kk) {
           const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along k inside the atom
           const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-          mma_tf32(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
-          mma_tf32(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-          mma_tf32(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+          mma(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
+          mma(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+          mma(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
         }
         mma_commit(&a_empty[as]);
         if (c == nch - 1) mma_commit(&d_full[b]);
@@ -318,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         x[kl] = v;
       }
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&raw_empty[rs])) : "memory");
+      if (lane == 0) mbar_arrive(&raw_empty[rs]);
       if (g >= kAStages && !mbar_wait(&a_empty[as], (uint32_t)((g / kAStages - 1) & 1))) {
         fail();
         break;
@@ -336,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&a_full[as])) : "memory");
+      if (lane == 0) mbar_arrive(&a_full[as]);
       if (c == nch - 1 && valid) {
         // Kahan-add the four partial sums (each carried with its compensation)
         float sum = 0.f, comp = 0.f;
@@ -365,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_ld32(ta + 32, v1);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&d_empty[b])) : "memory");
+      if (lane == 0) mbar_arrive(&d_empty[b]);
       const int64_t r = (blockIdx.x + t * (int64_t)gridDim.x) * kRows + 32 * lanegrp + lane;
       if (r < N) {
 #pragma unroll

@@ -119,7 +119,8 @@ void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch,
                          int64_t cap, cudaStream_t s);
 
 // reduced.cu: sample-row reduced solve (normal equations on all dof rows
-// of the listed cells; red = HYROM_RED_* precision of the normal matrix)
+// of the listed cells; red = HYROM_RED_* precision of the normal matrix;
+// fail[0]: not positive definite, fail[1]: a device wait gave up)
 size_t sample_part_doubles();
 template <typename T>
 void launch_sample_normal(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
@@ -130,6 +131,11 @@ void launch_sample_solve(const T* phi, int64_t N, int m, const int* cells, int n
                          int64_t nc, const T* v, const T* psi, double* part, double* b,
                          const double* L, const double* dinv, double* y, const double* y_prev,
                          double* dy, cudaStream_t s);
+// reduced_tc.cu: CTA partials of the normal matrix on the tensor cores
+// (red = HYROM_RED_TF32, _BF16 or _TF32_SPLIT) to part[b * 4096 ...];
+// returns the number of partials; *err = 1 if a wait gave up
+int launch_sample_gram_tc(const float* phi, int64_t N, int m, const int* cells, int ns, int nvar,
+                          int64_t nc, int red, double* part, int* err, cudaStream_t s);
 
 // odeim.cu
 template <typename T>

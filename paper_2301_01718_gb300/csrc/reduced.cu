@@ -10,10 +10,13 @@
 // Rows are variable-major: row r = (v, cell) with v = r / n_s and cell the
 // (r % n_s)-th sample cell in ascending order.
 //
-// The normal matrix comes in three precisions (the reduced-precision form of
+// The normal matrix comes in four precisions (the reduced-precision form of
 // the sample-row solve): FP32 products accumulated in FP32 within a CTA and
-// in FP64 across CTAs (FP64 throughout for FP64 states), or TF32 / BF16
-// products on the tensor cores accumulated in FP32 (reduced_tc.cu).
+// in FP64 across CTAs (FP64 throughout for FP64 states), or on the tensor
+// cores (reduced_tc.cu) TF32 or BF16 products, or FP32-level products of a
+// TF32 hi/lo split, accumulated in FP32 within a CTA and in FP64 across.
+// fail[0] = 1: a Cholesky pivot is not positive; fail[1] = 1: a bounded wait
+// of the tensor-core kernel gave up.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -233,7 +236,14 @@ template <typename T>
 void launch_sample_normal(const T* phi, int64_t N, int m, const int* cells, int ns, int nvar,
                           int64_t nc, int red, double* part, double* G, double* L, double* dinv,
                           int* fail, cudaStream_t s) {
-  (void)red;
+  if constexpr (sizeof(T) == 4) {
+    if (red != 0) {
+      const int nbt = launch_sample_gram_tc(phi, N, m, cells, ns, nvar, nc, red, part, fail + 1, s);
+      k_sum_partials<<<16, 256, 0, HY_S(s)>>>(part, nbt, 4096, G);
+      k_sample_chol<<<1, 256, 0, HY_S(s)>>>(G, m, L, dinv, fail);
+      return;
+    }
+  }
   const int64_t nrows = (int64_t)ns * nvar;
   const int nb = nblocks_for(nrows);
   const int64_t rpc = (nrows + nb - 1) / nb;

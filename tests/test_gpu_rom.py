@@ -143,6 +143,54 @@ def test_sample_row_coordinates(prec, frac):
     assert rel_err(got, want) < tol, rel_err(got, want)
 
 
+@pytest.mark.parametrize("red", [W.RED_TF32, W.RED_BF16, W.RED_TF32_SPLIT])
+@pytest.mark.parametrize("nx,ny,m,frac", [(96, 64, 24, 0.03), (96, 64, 61, 0.3),
+                                          (256, 256, 37, 1.0)])
+def test_sample_row_coordinates_tensor_cores(red, nx, ny, m, frac):
+    """Sample-row reduced coordinates with the normal matrix on the tensor
+    cores (TF32, BF16, TF32 hi/lo split; FP32 accumulation, FP64 Cholesky)
+    against the oracle's normal equations with the same input rounding
+    (gappy_coords_normal): within 1e-5, the bar of the FP32 CUDA-core path,
+    which leaves only the FP32 accumulation.  For TF32 and BF16 the GPU must
+    also sit far closer to that rounded solution than the rounding moves it
+    from the FP64 least-squares one (it rounds exactly as defined); the
+    split form is within 1e-5 of the FP64 least squares.  Sizes: a few
+    128-row stages, m not a multiple of 4 or 16, and 262 144 rows (more
+    stages per CTA than the ring holds, so every ring slot is reused)."""
+    cfg = _cfg(W.PREC_F32, nx=nx, ny=ny, m=m, n_p=2 * m, w=2 * m).with_(
+        regress_rows=W.ROWS_SAMPLE, reduced_prec=red)
+    N, nc = cfg.ndof, cfg.ncell
+    Phi = _basis(N, m, 31 + m, W.PREC_F32, concentrated=False)
+    g = np.random.Generator(np.random.PCG64(32 + m))
+    cells = np.flatnonzero(g.random(nc) < frac).astype(np.int32)
+    psi = g.standard_normal(N).astype(np.float32).astype(np.float64)
+    v = (psi + Phi @ g.standard_normal(m) + 1e-2 * g.standard_normal(N)).astype(
+        np.float32).astype(np.float64)
+    rows = np.concatenate([a * nc + cells for a in range(4)])
+    exact = rom.gappy_coords(Phi, rows, v, psi)
+    want = rom.gappy_coords_normal(Phi, rows, v, psi, red)
+    with Ctx(cfg) as (hy, ctx):
+        y = torch.zeros(m, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_gappy_rows(ctx, dev(Phi.T.copy(), torch.float32), m,
+                                  dev(cells, torch.int32), len(cells),
+                                  dev(v, torch.float32), dev(psi, torch.float32), y)
+        got = host(y)
+    nrm = np.linalg.norm(exact)
+    e_def = float(np.linalg.norm(got - want) / nrm)      # vs the rounded definition
+    e_round = float(np.linalg.norm(want - exact) / nrm)  # what the rounding itself does
+    e_fp64 = float(np.linalg.norm(got - exact) / nrm)
+    print(f"red={red} rows={len(rows)} m={m} err_vs_def={e_def:.3g} "
+          f"rounding={e_round:.3g} err_vs_fp64={e_fp64:.3g}")
+    assert rel_err(got, want) < 1e-5, rel_err(got, want)
+    if red == W.RED_TF32_SPLIT:
+        assert rel_err(got, exact) < 1e-5, rel_err(got, exact)
+    elif frac < 1.0:
+        # with all 262 144 rows of an orthonormal basis (G = I) the rounding
+        # moves y by only a few 1e-6, the size of the FP32 accumulation error
+        # over 1792 rows per CTA, so only the 1e-5 bar applies there
+        assert e_def < 0.1 * e_round, (e_def, e_round)
+
+
 @pytest.mark.parametrize("pde,nx,ny", [(W.PDE_BURGERS, 1073, 1), (W.PDE_EULER, 33, 17)])
 @pytest.mark.parametrize("m", [20, 40])
 def test_pod_fp32_wide_basis(pde, nx, ny, m):

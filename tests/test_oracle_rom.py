@@ -127,3 +127,88 @@ def test_secular_root_matches_dense_eigensolve():
 def test_window_mean_is_the_average():
     snaps = [np.full(5, float(j)) for j in range(4)]
     assert np.array_equal(rom.window_mean(snaps), np.full(5, 1.5))
+
+
+# ---- the reduced-precision form of the sample-row solve ---------------------
+
+def test_round_bf16_is_torch_bfloat16():
+    """round_bf16 against PyTorch's FP32 -> bfloat16 conversion (round to
+    nearest even), on random values and on constructed ties."""
+    torch = pytest.importorskip("torch")
+    g = np.random.Generator(np.random.PCG64(70))
+    x = (g.standard_normal(200000) * 10.0 ** g.uniform(-6, 6, 200000)).astype(np.float32)
+    bits = x.view(np.uint32)
+    ties = ((bits & np.uint32(0xFFFF0000)) | np.uint32(0x8000)).view(np.float32)[:5000]
+    x = np.concatenate([x, ties, -ties])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(rom.round_bf16(x), want)
+
+
+def test_round_tf32_cases_and_bound():
+    """TF32 rounding: hand-worked cases (a tie goes away from zero, below half
+    goes down, above half goes up, a carry into the exponent), the result
+    keeps 10 mantissa bits, and |round(x) - x| <= 2^-11 |x|."""
+    e = 2.0 ** -10   # one TF32 unit in the last place at 1
+    cases = {1 + e / 2: 1 + e, -(1 + e / 2): -(1 + e), 1 + e / 4: 1.0, 1 + e / 2 + 2 ** -20: 1 + e,
+             1 + 3 * e / 2: 1 + 2 * e, 2 - e / 2: 2.0, 0.0: 0.0, 3.0: 3.0}
+    for x, want in cases.items():
+        assert rom.round_tf32(np.float32(x)) == want, (x, rom.round_tf32(np.float32(x)), want)
+    g = np.random.Generator(np.random.PCG64(71))
+    x = (g.standard_normal(100000) * 10.0 ** g.uniform(-8, 8, 100000)).astype(np.float32)
+    r = rom.round_tf32(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -11 * np.abs(x.astype(np.float64)))
+    assert np.all(r.astype(np.float32).view(np.uint32) & np.uint32(0x1FFF) == 0)
+
+
+def test_split_tf32_reconstructs_to_2_pow_21():
+    g = np.random.Generator(np.random.PCG64(72))
+    x = (g.standard_normal(100000) * 10.0 ** g.uniform(-8, 8, 100000)).astype(np.float32)
+    hi, lo = rom.split_tf32(x)
+    xd = x.astype(np.float64)
+    assert np.all(hi.astype(np.float32).view(np.uint32) & np.uint32(0x1FFF) == 0)
+    assert np.all(lo.astype(np.float32).view(np.uint32) & np.uint32(0x1FFF) == 0)
+    assert np.all(np.abs(hi + lo - xd) <= 2.0 ** -21 * np.abs(xd))
+    assert np.all(np.abs(hi) <= np.abs(xd))
+
+
+@pytest.mark.parametrize("red", [W.RED_F32, W.RED_TF32, W.RED_BF16, W.RED_TF32_SPLIT])
+def test_normal_equations_exact_on_representable_inputs(red):
+    """With a basis whose entries are already BF16 (hence TF32) values, no
+    rounding changes anything: every precision's normal-equation solution is
+    the least-squares solution of gappy_coords."""
+    g = np.random.Generator(np.random.PCG64(73))
+    N, m = 400, 7
+    Phi = g.integers(-64, 65, size=(N, m)) / 64.0      # 7-bit integers over 2^6
+    rows = np.sort(g.choice(N, 90, replace=False))
+    psi = g.standard_normal(N)
+    v = psi + Phi @ g.standard_normal(m) + 0.1 * g.standard_normal(N)
+    want = rom.gappy_coords(Phi, rows, v, psi)
+    got = rom.gappy_coords_normal(Phi, rows, v, psi, red)
+    assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()
+
+
+def test_normal_equations_follow_the_rounded_matrix():
+    """TF32 and BF16 normal matrices move y by about kappa times their input
+    rounding (and by no more than the first-order bound), BF16 more than
+    TF32, the split form by no more than FP32 rounding."""
+    g = np.random.Generator(np.random.PCG64(74))
+    N, m = 3000, 12
+    Phi, _ = np.linalg.qr(g.standard_normal((N, m)))
+    Phi = Phi.astype(np.float32).astype(np.float64)
+    rows = np.sort(g.choice(N, 600, replace=False))
+    psi = g.standard_normal(N)
+    v = psi + Phi @ g.standard_normal(m)
+    exact = rom.gappy_coords(Phi, rows, v, psi)
+    X = Phi[rows]
+    kappa = np.linalg.cond(X.T @ X)
+    errs = {}
+    for red, u in ((W.RED_TF32, 2.0 ** -11), (W.RED_BF16, 2.0 ** -8),
+                   (W.RED_TF32_SPLIT, 2.0 ** -21)):
+        y = rom.gappy_coords_normal(Phi, rows, v, psi, red)
+        errs[red] = np.linalg.norm(y - exact) / np.linalg.norm(exact)
+        # |E| <= (2u + u^2) |X|^T |X| entrywise
+        eta = (2 * u + u * u) * np.linalg.norm(np.abs(X).T @ np.abs(X), 2) / \
+            np.linalg.norm(X.T @ X, 2)
+        assert errs[red] <= kappa * eta / (1 - kappa * eta) + 1e-12, (red, errs[red])
+    assert errs[W.RED_BF16] > 4 * errs[W.RED_TF32] > 0
+    assert errs[W.RED_TF32_SPLIT] < 1e-6

@@ -33,7 +33,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_SHOCK = 0, 1, 2
 SEL_RRE, SEL_TOPFRAC = 0, 1             # RRE threshold delta, top fraction
 PREC_F64, PREC_F32 = 0, 1
 ROWS_ODEIM, ROWS_SAMPLE = 0, 1          # regression rows of the reduced solve
-RED_F32, RED_TF32, RED_BF16 = 0, 1, 2   # sample-row normal matrix: FP32 / tensor cores
+RED_F32, RED_TF32, RED_BF16, RED_TF32_SPLIT = 0, 1, 2, 3   # sample-row normal matrix precisions
 
 MASK64 = (1 << 64) - 1
 
