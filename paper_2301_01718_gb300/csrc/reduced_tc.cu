@@ -18,15 +18,25 @@
 // the two-half forms are products of different rows and are never read;
 // keeping M = 128 keeps accumulator row i in tensor-memory lane i.
 //
-// One CTA per SM takes a contiguous range of sample rows in stages of 128:
-//   * warps 1-16 (converters): each lane loads one sample row of 16 basis
-//     columns (a warp: 32 consecutive rows of one column per load, coalesced
-//     along the sorted cells), rounds, and writes the swizzled atoms;
-//   * warp 0 (one thread): the MMAs of each full stage, committed to the
-//     stage's empty barrier, and at the end to the accumulator's barrier;
-//   * warps 1-4 (epilogue, after converting): tcgen05.ld of the accumulator,
-//     block sums, and the CTA's FP64 partial G to part[b * 4096 ...]; the
-//     partials are summed in FP64 by the caller.
+// The tensor core's FP32 accumulation is not unbiased: over n accumulating
+// MMAs the error of a sum grows like n times the FP32 unit.  So no tensor
+// memory accumulator runs for more than kPeriod stages: two accumulators
+// alternate, and each finished one is drained into compensated (Kahan) FP32
+// sums in shared memory while the MMAs fill the other.
+//
+// One CTA per SM takes a contiguous range of sample rows in stages (128
+// rows; 64 for the split form):
+//   * warps 1-16 (converters): each lane loads one sample row of 16 (split:
+//     8) basis columns (a warp: 32 consecutive rows of one column per load,
+//     coalesced along the sorted cells), rounds, and writes the swizzled
+//     atoms;
+//   * warp 0 (one thread): the MMAs of each full stage into the period's
+//     accumulator, committed to the stage's empty barrier and at a period's
+//     end to the accumulator's full barrier;
+//   * warps 17-20 (epilogue, one lane quarter of the accumulators each):
+//     tcgen05.ld of each finished accumulator, block sums, Kahan updates of
+//     their rows, release of the accumulator; at the end the CTA's FP64
+//     partial G to part[b * 4096 ...], summed in FP64 by the caller.
 // Every mbarrier wait is bounded; a timeout sets *err and ends every role's
 // loop, and the tensor memory is freed only after the MMAs completed.
 #include <cuda_bf16.h>
@@ -42,23 +52,28 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 544;      // 17 warps
-constexpr int kRowsStage = 128;    // sample rows per stage
-constexpr int kColsWarp = 16;      // basis columns per converter warp and stage
+constexpr int kThreads = 672;      // 21 warps: MMA, 16 converters, 4 epilogue
 constexpr int kAtomBytes = 16384;  // 128 rows x 128 bytes
-constexpr int kRingBytes = 196608;
-constexpr int kSmemBytes = kRingBytes + 1024;
-constexpr uint32_t kTmemCols = 128;
+constexpr int kRingBytes = 163840;
+constexpr int kKahanBytes = 2 * 128 * 65 * 4;  // sums and compensations, 128 x 64 (+1 pad)
+constexpr int kSmemBytes = kRingBytes + kKahanBytes + 1024;
+constexpr int kPeriod = 2;         // stages per accumulator period
+constexpr uint32_t kTmemCols = 256;  // two 128 x 128 FP32 accumulators
 
 enum { kTf32 = 1, kBf16 = 2, kSplit = 3 };  // the HYROM_RED_* values
 
 template <int MODE>
 struct Mode {
-  // sample rows per atom, atoms per stage, stages in the ring
+  // sample rows per atom and per stage, atoms per stage, stages in the ring
   static constexpr int kRowsAtom = MODE == kBf16 ? 128 : (MODE == kTf32 ? 64 : 32);
+  static constexpr int kRowsStage = MODE == kSplit ? 64 : 128;
   static constexpr int kAtoms = kRowsStage / kRowsAtom;
   static constexpr int kStageBytes = kAtoms * kAtomBytes;
   static constexpr int kStages = kRingBytes / kStageBytes;
+  // converter warps: 32-row blocks per stage, columns per warp, column step
+  static constexpr int kBlk = kRowsStage / 32;
+  static constexpr int kColsWarp = 4 * kBlk;
+  static constexpr int kColStep = 16 / kBlk;
   // D FP32 (bits 4-5 = 1); A, B formats at bits 7-9, 10-12 (kind::tf32:
   // TF32 = 2, kind::f16: BF16 = 1); both K-major; N >> 3 at 17-22, M >> 4 at
   // 24-28; M = N = 128
@@ -86,7 +101,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   using P = Mode<MODE>;
   extern __shared__ unsigned char smraw[];
   unsigned char* ring = smraw + ((1024 - (saddr(smraw) & 1023u)) & 1023u);  // 1024-aligned
-  __shared__ uint64_t full[P::kStages], empty[P::kStages], d_full;
+  float (*ks)[65] = reinterpret_cast<float (*)[65]>(ring + kRingBytes);  // Kahan sums
+  float (*kc)[65] = ks + 128;                                            // compensations
+  __shared__ uint64_t full[P::kStages], empty[P::kStages], d_full[2], d_empty[2], d_all;
   __shared__ uint32_t tmem_s;
   __shared__ volatile int stop_s;
 
@@ -94,14 +111,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t nrows = (int64_t)ns * nvar;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int64_t r1 = r0 + rpc < nrows ? r0 + rpc : nrows;
-  const int nst = r1 > r0 ? (int)((r1 - r0 + kRowsStage - 1) / kRowsStage) : 0;
+  const int nst = r1 > r0 ? (int)((r1 - r0 + P::kRowsStage - 1) / P::kRowsStage) : 0;
+  const int nper = (nst + kPeriod - 1) / kPeriod;
 
   if (tid == 0) {
     for (int s = 0; s < P::kStages; ++s) {
       mbar_init(&full[s], 16);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&d_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d_full[b], 1);
+      mbar_init(&d_empty[b], 4);
+    }
+    mbar_init(&d_all, 1);
     stop_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -120,49 +142,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       for (int g = 0; g < nst && !stop_s; ++g) {
         const int s = g % P::kStages;
+        const int p = g / kPeriod, b = p & 1;
+        const bool first = g % kPeriod == 0;
+        if (first && p >= 2 && !mbar_wait(&d_empty[b], (uint32_t)(((p >> 1) - 1) & 1))) {
+          fail();
+          break;
+        }
         if (!mbar_wait(&full[s], (uint32_t)((g / P::kStages) & 1))) {
           fail();
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = saddr(ring + s * P::kStageBytes);
+        const uint32_t d = tmem + 128u * (uint32_t)b;
 #pragma unroll
         for (int a = 0; a < P::kAtoms; ++a)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per MMA
-            const uint64_t d = sdesc(st + a * kAtomBytes + kk * 32);
-            const uint32_t acc = (g > 0 || a > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t desc = sdesc(st + a * kAtomBytes + kk * 32);
+            const uint32_t acc = (!first || a > 0 || kk > 0) ? 1u : 0u;
             if (MODE == kBf16)
-              mma_f16(tmem, d, d, P::kIdesc, acc);
+              mma_f16(d, desc, desc, P::kIdesc, acc);
             else
-              mma_tf32(tmem, d, d, P::kIdesc, acc);
+              mma_tf32(d, desc, desc, P::kIdesc, acc);
           }
         mma_commit(&empty[s]);
+        if (g % kPeriod == kPeriod - 1 || g == nst - 1) mma_commit(&d_full[b]);
       }
-      // the accumulator's barrier completes once every MMA above has; wait
-      // for it here too so that no MMA is in flight when the memory is freed
-      mma_commit(&d_full);
-      if (!mbar_wait(&d_full, 0)) fail();
+      // completes once every MMA above has: none is in flight when the
+      // tensor memory is freed
+      mma_commit(&d_all);
+      if (!mbar_wait(&d_all, 0)) fail();
     }
-  } else {
-    // ---- converters: lane = sample row of a 32-row block, 16 columns ----
+  } else if (warp <= 16) {
+    // ---- converters: lane = sample row of a 32-row block ----
     const int cw = warp - 1;
-    const int blk = cw & 3, j0 = cw >> 2;  // columns j0 + 4 t
-    const int rl = blk * 32 + lane;        // row within the stage
+    const int blk = cw % P::kBlk, j0 = cw / P::kBlk;  // columns j0 + kColStep t
+    const int rl = blk * 32 + lane;                   // row within the stage
     for (int g = 0; g < nst && !stop_s; ++g) {
       const int s = g % P::kStages;
-      const int64_t r = r0 + (int64_t)g * kRowsStage + rl;
-      float x[kColsWarp];
+      const int64_t r = r0 + (int64_t)g * P::kRowsStage + rl;
+      float x[P::kColsWarp];
       if (r < r1) {
         const int64_t dof = sample_dof_tc(cells, ns, nc, r);
 #pragma unroll
-        for (int t = 0; t < kColsWarp; ++t) {
-          const int j = j0 + 4 * t;
+        for (int t = 0; t < P::kColsWarp; ++t) {
+          const int j = j0 + P::kColStep * t;
           x[t] = j < m ? phi[(int64_t)j * N + dof] : 0.f;
         }
       } else {
 #pragma unroll
-        for (int t = 0; t < kColsWarp; ++t) x[t] = 0.f;
+        for (int t = 0; t < P::kColsWarp; ++t) x[t] = 0.f;
       }
       if (g >= P::kStages && !mbar_wait(&empty[s], (uint32_t)((g / P::kStages - 1) & 1))) {
         fail();
@@ -173,22 +203,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         unsigned char* at = st + (rl >> 6) * kAtomBytes;
         const int h = (rl >> 5) & 1;
 #pragma unroll
-        for (int t = 0; t < kColsWarp; ++t)
-          *reinterpret_cast<uint32_t*>(at + sw128(h * 64 + j0 + 4 * t, lane)) = to_tf32(x[t]);
+        for (int t = 0; t < P::kColsWarp; ++t)
+          *reinterpret_cast<uint32_t*>(at + sw128(h * 64 + j0 + P::kColStep * t, lane)) =
+              to_tf32(x[t]);
       } else if (MODE == kBf16) {
         const int h = rl >> 6, k = rl & 63;
 #pragma unroll
-        for (int t = 0; t < kColsWarp; ++t)
-          *reinterpret_cast<__nv_bfloat16*>(st + sw128_h(h * 64 + j0 + 4 * t, k)) =
+        for (int t = 0; t < P::kColsWarp; ++t)
+          *reinterpret_cast<__nv_bfloat16*>(st + sw128_h(h * 64 + j0 + P::kColStep * t, k)) =
               __float2bfloat16_rn(x[t]);
       } else {
         unsigned char* at = st + blk * kAtomBytes;
 #pragma unroll
-        for (int t = 0; t < kColsWarp; ++t) {
+        for (int t = 0; t < P::kColsWarp; ++t) {
           const uint32_t hi = __float_as_uint(x[t]) & 0xFFFFE000u;
           const uint32_t lo = to_tf32(x[t] - __uint_as_float(hi));
-          *reinterpret_cast<uint32_t*>(at + sw128(j0 + 4 * t, lane)) = hi;
-          *reinterpret_cast<uint32_t*>(at + sw128(64 + j0 + 4 * t, lane)) = lo;
+          const int j = j0 + P::kColStep * t;
+          *reinterpret_cast<uint32_t*>(at + sw128(j, lane)) = hi;
+          *reinterpret_cast<uint32_t*>(at + sw128(64 + j, lane)) = lo;
         }
       }
       // generic-proxy writes become visible to the tensor core's async proxy
@@ -196,55 +228,56 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
     }
-
-    // ---- epilogue: warps 1-4, one lane quarter of the accumulator each ----
-    if (warp <= 4) {
-      const int q = warp & 3;             // lanes 32 q .. 32 q + 31
-      const int i = (q & 1) * 32 + lane;  // row of G
-      float (*gs)[65] = reinterpret_cast<float (*)[65]>(ring);  // 64 x 65, ring reused
-      bool ok = nst == 0 || mbar_wait(&d_full, 0);
+  } else {
+    // ---- epilogue: warps 17-20, lanes 32 q .. 32 q + 31 of each accumulator ----
+    const int q = warp & 3;
+    const int drow = 32 * q + lane;  // accumulator row = tensor-memory lane
+    // accumulator rows 0-63 take their diagonal block (columns 0-63), rows
+    // 64-127 theirs (64-127); the split form adds the other block too
+    const uint32_t own = q < 2 ? 0u : 64u;
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) ks[drow][j] = kc[drow][j] = 0.f;
+    for (int p = 0; p < nper && !stop_s; ++p) {
+      const int b = p & 1;
+      bool ok = mbar_wait(&d_full[b], (uint32_t)((p >> 1) & 1));
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-      if (!ok) fail();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16);
-      // rows 0-63 of the accumulator (q < 2) write their diagonal block
-      // (columns 0-63), then rows 64-127 add theirs (columns 64-127); the
-      // split form adds the off-diagonal block of each row as well
-      const uint32_t own = q < 2 ? 0u : 64u;
-      // the named barriers are passed unconditionally by all four warps (a
-      // warp that gave up only skips its memory accesses)
-      for (int phase = 0; phase < 2; ++phase) {
-        if (ok && (q >= 2) == (phase == 1)) {
-#pragma unroll 1
-          for (int hc = 0; hc < 2; ++hc) {
-            float v[32];
-            if (nst == 0) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = 0.f;
-            } else {
-              tmem_ld32(ta + own + 32 * hc, v);
-              if (MODE == kSplit) {
-                float o[32];
-                tmem_ld32(ta + (64u - own) + 32 * hc, o);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += o[j];
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (phase == 0)
-                gs[i][32 * hc + j] = v[j];
-              else
-                gs[i][32 * hc + j] += v[j];
-            }
-          }
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!ok) {
+        fail();
+        break;
       }
-      if (!stop_s)
-        for (int e = tid - 32; e < 64 * 64; e += 128)
-          part[(int64_t)blockIdx.x * 4096 + e] = (double)gs[e >> 6][e & 63];
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + 128u * (uint32_t)b;
+#pragma unroll 1
+      for (int hc = 0; hc < 2; ++hc) {
+        float v[32];
+        tmem_ld32(ta + own + 32 * hc, v);
+        if (MODE == kSplit) {
+          float o[32];
+          tmem_ld32(ta + (64u - own) + 32 * hc, o);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += o[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float sj = ks[drow][32 * hc + j];
+          const float y = v[j] - kc[drow][32 * hc + j];
+          const float t = sj + y;
+          kc[drow][32 * hc + j] = (t - sj) - y;
+          ks[drow][32 * hc + j] = t;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d_empty[b]);
     }
+    // passed unconditionally by all four epilogue warps
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (!stop_s)
+      for (int e = tid - 17 * 32; e < 64 * 64; e += 128) {
+        const int i = e >> 6, j = e & 63;
+        part[(int64_t)blockIdx.x * 4096 + e] =
+            ((double)ks[i][j] - (double)kc[i][j]) + ((double)ks[64 + i][j] - (double)kc[64 + i][j]);
+      }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -255,12 +288,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int MODE>
 void launch_mode(const float* phi, int64_t N, int m, const int* cells, int ns, int nvar,
                  int64_t nc, double* part, int* nb_out, int* err, cudaStream_t s) {
+  constexpr int kRS = Mode<MODE>::kRowsStage;
   const int64_t nrows = (int64_t)ns * nvar;
-  int64_t nb = (nrows + kRowsStage - 1) / kRowsStage;
+  int64_t nb = (nrows + kRS - 1) / kRS;
   if (nb > 152) nb = 152;
   if (nb < 1) nb = 1;
   int64_t rpc = (nrows + nb - 1) / nb;
-  rpc = (rpc + kRowsStage - 1) / kRowsStage * kRowsStage;
+  rpc = (rpc + kRS - 1) / kRS * kRS;
   nb = rpc > 0 ? (nrows + rpc - 1) / rpc : 1;
   if (nb < 1) nb = 1;
   cudaFuncSetAttribute(k_sample_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -98,7 +98,9 @@ __global__ void k_sel_mode(SelState* st, const unsigned long long* total, int mo
   }
 }
 
-// histogram of digit `d` (bits 8d..8d+7) over keys whose bits above match
+// histogram of digit `d` (bits 8d..8d+7) over keys whose bits above match;
+// counts are aggregated per warp over lanes with the same digit, and key
+// sums are formed only for the RRE rule (the top fraction needs counts)
 __global__ void k_sel_hist(const unsigned long long* __restrict__ keys, int64_t nc, int d,
                            const SelState* __restrict__ st, unsigned int* __restrict__ hcnt,
                            unsigned long long* __restrict__ hsum) {
@@ -110,22 +112,33 @@ __global__ void k_sel_hist(const unsigned long long* __restrict__ keys, int64_t 
   }
   __syncthreads();
   if (!st->empty) {
+    const bool sums = st->mode != HYROM_SEL_TOPFRAC;
     const int hi = 8 * (d + 1);
+    const int lane = threadIdx.x & 31;
     const unsigned long long pre = st->prefix;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const unsigned long long k = keys[i];
-      if (hi < 64 && (k >> hi) != (pre >> hi)) continue;
-      const int dg = (int)((k >> (8 * d)) & 255ull);
-      atomicAdd(&sc[dg], 1u);
-      atomicAdd(&ss[dg], k);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // i - lane is the same for the 32 lanes of a warp: uniform trip count
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - lane < nc; i += stride) {
+      unsigned long long k = 0;
+      bool valid = i < nc;
+      if (valid) {
+        k = keys[i];
+        valid = hi >= 64 || (k >> hi) == (pre >> hi);
+      }
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        const int dg = (int)((k >> (8 * d)) & 255ull);
+        const unsigned peers = __match_any_sync(vm, dg);
+        if (lane == __ffs(peers) - 1) atomicAdd(&sc[dg], (unsigned)__popc(peers));
+        if (sums) atomicAdd(&ss[dg], k);
+      }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     if (sc[i]) {
       atomicAdd(&hcnt[i], sc[i]);
-      atomicAdd(&hsum[i], ss[i]);
+      if (ss[i]) atomicAdd(&hsum[i], ss[i]);
     }
   }
 }
@@ -136,29 +149,68 @@ HY_DEV bool rre_met(const SelState* st, unsigned long long acc) {
   return lhs >= rhs;
 }
 
-__global__ void k_sel_level(int d, SelState* st, unsigned int* hcnt, unsigned long long* hsum) {
-  if (st->empty) return;
-  int chosen = 0;
-  for (int dg = 255; dg >= 0; --dg) {
-    const long long c = hcnt[dg];
-    const unsigned long long sm = hsum[dg];
+// Choose digit d of K*: scanning the digits from 255 down, the first at
+// which the rule is met (top fraction: the cells above plus this digit's
+// reach n_target; RRE: a nonempty digit whose keys plus all above meet Eq.
+// rre), else 0.  One block of 256 threads: thread t = digit t; suffix sums
+// of counts and key sums give each digit what lies above it, and the
+// largest digit meeting the rule is the first from the top.  Clears the
+// histogram for the next digit.
+__global__ void __launch_bounds__(256) k_sel_level(int d, SelState* st, unsigned int* hcnt,
+                                                   unsigned long long* hsum) {
+  __shared__ long long wc[8];
+  __shared__ unsigned long long wsm[8];
+  __shared__ int chosen_s;
+  __shared__ long long above_c[256];
+  __shared__ unsigned long long above_s[256];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) chosen_s = 0;
+  const bool empty = st->empty;
+  // reversed order: r = 255 - digit, so an inclusive scan over r sums the
+  // digits >= this one
+  const int dg = 255 - t;
+  const long long c = empty ? 0 : (long long)hcnt[dg];
+  const unsigned long long sm = empty ? 0ull : hsum[dg];
+  long long ic = c;
+  unsigned long long is = sm;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long yc = __shfl_up_sync(0xffffffffu, ic, o);
+    const unsigned long long ys = __shfl_up_sync(0xffffffffu, is, o);
+    if (lane >= o) {
+      ic += yc;
+      is += ys;
+    }
+  }
+  if (lane == 31) {
+    wc[wid] = ic;
+    wsm[wid] = is;
+  }
+  __syncthreads();
+  long long bc = 0;
+  unsigned long long bs = 0;
+  for (int w = 0; w < wid; ++w) {
+    bc += wc[w];
+    bs += wsm[w];
+  }
+  above_c[dg] = bc + ic - c;  // cells with a larger digit
+  above_s[dg] = bs + is - sm;
+  if (!empty) {
     bool stop;
     if (st->mode == HYROM_SEL_TOPFRAC)
-      stop = st->cnt_gt + c >= st->n_target;
+      stop = st->cnt_gt + above_c[dg] + c >= st->n_target;
     else
-      stop = c > 0 && rre_met(st, st->acc_gt + sm);
-    if (stop || dg == 0) {
-      chosen = dg;
-      break;
-    }
-    st->cnt_gt += c;
-    st->acc_gt += sm;
+      stop = c > 0 && rre_met(st, st->acc_gt + above_s[dg] + sm);
+    if (stop) atomicMax(&chosen_s, dg);
   }
+  hcnt[dg] = 0;
+  hsum[dg] = 0;
+  __syncthreads();
+  if (t != 0 || empty) return;
+  const int chosen = chosen_s;
+  st->cnt_gt += above_c[chosen];
+  st->acc_gt += above_s[chosen];
   st->prefix |= ((unsigned long long)chosen) << (8 * d);
-  for (int i = 0; i < 256; ++i) {
-    hcnt[i] = 0;
-    hsum[i] = 0;
-  }
   if (d == 0) {
     const unsigned long long K = st->prefix;
     long long r;
@@ -195,15 +247,31 @@ __global__ void k_sel_count_eq(const unsigned long long* __restrict__ keys, int6
   if (threadIdx.x == 0) cnt[blockIdx.x] = n;
 }
 
-__global__ void k_exclusive_scan_ll(long long* v, int n) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    long long a = 0;
-    for (int i = 0; i < n; ++i) {
-      const long long t = v[i];
-      v[i] = a;
-      a += t;
-    }
+// In-place exclusive prefix sum of n <= 1024 counts by one block of 1024
+// threads (warp shuffle scans, then a scan of the 32 warp totals).
+__global__ void __launch_bounds__(1024) k_exclusive_scan_ll(long long* v, int n) {
+  __shared__ long long wsum[32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const long long x = t < n ? v[t] : 0;
+  long long incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
   }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = wsum[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  if (t < n) v[t] = (wid > 0 ? wsum[wid - 1] : 0) + incl - x;
 }
 
 __global__ void k_sel_mark(const unsigned long long* __restrict__ keys, int64_t nc, int64_t chunk,
@@ -274,12 +342,17 @@ void launch_select(const void* eps, int is_f32, int64_t nc, int mode, double del
   k_sel_setup<<<1, 1, 0, HY_S(s)>>>(emax, nc, st);
   k_keys<<<(int)blocks, 256, 0, HY_S(s)>>>(eps, is_f32, nc, st, keys, total);
   k_sel_mode<<<1, 1, 0, HY_S(s)>>>(st, total, mode, delta, top_frac, nc);
-  for (int d = 7; d >= 0; --d) {
+  // keys are below 2^(63 - ceil(log2 nc)): the digits above are zero and
+  // their passes would choose digit 0 with nothing above it
+  int lg = 0;
+  while ((1LL << lg) < nc) ++lg;
+  const int top = (63 - lg - 1) / 8;
+  for (int d = top; d >= 0; --d) {
     k_sel_hist<<<(int)blocks, 256, 0, HY_S(s)>>>(keys, nc, d, st, hcnt, hsum);
-    k_sel_level<<<1, 1, 0, HY_S(s)>>>(d, st, hcnt, hsum);
+    k_sel_level<<<1, 256, 0, HY_S(s)>>>(d, st, hcnt, hsum);
   }
   k_sel_count_eq<<<nchunk, 256, 0, HY_S(s)>>>(keys, nc, chunk, st, cnt);
-  k_exclusive_scan_ll<<<1, 1, 0, HY_S(s)>>>(cnt, nchunk);
+  k_exclusive_scan_ll<<<1, 1024, 0, HY_S(s)>>>(cnt, nchunk);
   const int64_t nwords = (nc + 31) / 32;
   cudaMemsetAsync(g_bitmap, 0, nwords * sizeof(uint32_t), s);
   k_sel_mark<<<nchunk, 256, 0, HY_S(s)>>>(keys, nc, chunk, st, cnt, g_bitmap);
@@ -375,21 +448,33 @@ __global__ void k_bits_count(const uint32_t* __restrict__ bm, int64_t nwords, in
   if (threadIdx.x == 0) cnt[blockIdx.x] = n;
 }
 
+// one warp per chunk: lane l takes word w0 + 32 i + l; a warp scan of the
+// words' popcounts gives each lane its output offset
 __global__ void k_bits_list(const uint32_t* __restrict__ bm, int64_t nwords, int64_t wchunk,
                             const long long* __restrict__ off, int* __restrict__ out, int64_t cap) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
   const int64_t w0 = blockIdx.x * wchunk;
   int64_t w1 = w0 + wchunk;
   if (w1 > nwords) w1 = nwords;
   long long o = off[blockIdx.x];
-  for (int64_t w = w0; w < w1; ++w) {
-    uint32_t b = bm[w];
+  for (int64_t wb = w0; wb < w1; wb += 32) {
+    const int64_t w = wb + lane;
+    uint32_t b = w < w1 ? bm[w] : 0u;
+    const int c = __popc(b);
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    long long my = o + incl - c;
     while (b) {
       const int t = __ffs(b) - 1;
       b &= b - 1;
-      if (o < cap) out[o] = (int)(w * 32 + t);
-      ++o;
+      if (my < cap) out[my] = (int)(w * 32 + t);
+      ++my;
     }
+    o += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
@@ -401,7 +486,7 @@ void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch,
   if (wchunk < 1) wchunk = 1;
   const int nchunk = (int)((nwords + wchunk - 1) / wchunk);
   k_bits_count<<<nchunk, 256, 0, HY_S(s)>>>(bm, nwords, wchunk, cnt_scratch);
-  k_exclusive_scan_ll<<<1, 1, 0, HY_S(s)>>>(cnt_scratch, nchunk);
+  k_exclusive_scan_ll<<<1, 1024, 0, HY_S(s)>>>(cnt_scratch, nchunk);
   k_bits_list<<<nchunk, 32, 0, HY_S(s)>>>(bm, nwords, wchunk, cnt_scratch, out, cap);
 }
 
