@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--no-precision-form", action="store_true")
     p.add_argument("--precision-steps", type=int, default=4,
                    help="timed steps per variant of the precision form")
+    p.add_argument("--micro", choices=["sample_gram"], default=None,
+                   help="instead of the step: time one stage on a synthetic input "
+                        "(sample_gram: the sample-row normal matrix in each precision)")
     return p.parse_args()
 
 
@@ -248,6 +251,7 @@ def run_ours(a):
         ms = e0.elapsed_time(e1)
         stages = hyrom.hyrom_stage_times(ctx)
         odc = hyrom.hyrom_odeim_counters(ctx)
+        eig_sw = hyrom.hyrom_eig_sweeps(ctx)
         hyrom.hyrom_profile(ctx, False)
         ms_max = max_over_ranks(ms, world, "cuda")
         value = whole_job_rate(a.steps, world, ms_max)
@@ -307,7 +311,7 @@ def run_ours(a):
            "sampled_cell_updates_per_s": world * ns_sum / (ms_max / 1e3),
            "n_s_avg": n_s_avg, "m_eff": m_eff, "stages": per,
            "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e,
-           "odeim_counters_last_step": odc}
+           "odeim_counters_last_step": odc, "eig_sweeps_last_step": eig_sw}
     if rank == 0 and not a.no_err:
         out["err_vs_fp64"] = err_vs_fp64(a)
     if rank == 0 and not a.no_precision_form:
@@ -421,6 +425,46 @@ def precision_form(a):
             "variants": out}
 
 
+def micro_sample_gram(a, m=64, calls=10):
+    """The sample-row normal matrix (hyrom_stage_gappy_rows) on an n^2 Euler
+    grid with a random FP32 basis of m columns and every other cell sampled:
+    CUDA-event time of the normal matrix per call in each precision, and its
+    algorithmic bytes (4 B x rows x m) per second."""
+    import torch
+    from paper_2301_01718_gb300 import build, hyrom
+    build.build()
+    n = a.n
+    out = {}
+    for name, red in PRECISIONS.items():
+        cfg = W.ArConfig(pde=W.PDE_EULER, scheme=W.SCHEME_RK2, nx=n, ny=n, dx=1.0 / n,
+                         dy=1.0 / n, dt=1e-4, w=m, m=m, n_p=2 * m, precision=W.PREC_F32,
+                         regress_rows=W.ROWS_SAMPLE, reduced_prec=red)
+        N, nc = cfg.ndof, cfg.ncell
+        g = torch.Generator(device="cuda").manual_seed(a.seed)
+        phi = torch.randn(m * N, device="cuda", generator=g) / N ** 0.5
+        cells = torch.arange(0, nc, 2, dtype=torch.int32, device="cuda")
+        v = torch.randn(N, device="cuda", generator=g)
+        psi = torch.randn(N, device="cuda", generator=g)
+        ctx = hyrom.hyrom_init(cfg, torch.zeros(N, dtype=torch.float64, device="cuda"))
+        try:
+            y = torch.zeros(m, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                hyrom.hyrom_stage_gappy_rows(ctx, phi, m, cells, len(cells), v, psi, y)
+            hyrom.hyrom_profile(ctx, True)
+            for _ in range(calls):
+                hyrom.hyrom_stage_gappy_rows(ctx, phi, m, cells, len(cells), v, psi, y)
+            st = hyrom.hyrom_stage_times(ctx)
+            hyrom.hyrom_profile(ctx, False)
+        finally:
+            hyrom.hyrom_destroy(ctx)
+        rows = 4 * len(cells)
+        ms = st["snormal"][0] / max(st["snormal"][1], 1)
+        out[name] = {"ms": ms, "gbs": 4.0 * rows * m / (ms * 1e-3) / 1e9,
+                     "solve_ms": st["gappy"][0] / max(st["gappy"][1], 1)}
+    return {"micro": "sample_gram", "grid": f"{n}x{n}", "m": m,
+            "rows": rows, "sample": "every other cell", "calls": calls, "variants": out}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -443,7 +487,10 @@ def run_reference(a):
 
 def main():
     a = parse()
-    out = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if a.micro == "sample_gram":
+        out = micro_sample_gram(a)
+    else:
+        out = run_reference(a) if a.impl == "reference" else run_ours(a)
     if out is not None:
         print(json.dumps(out))
 

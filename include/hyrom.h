@@ -171,6 +171,13 @@ hyrom_status hyrom_profile(hyrom_ctx* ctx, int on);
  * z_1 bound does not exclude), out4[2] exact FP64 secular solves in
  * oversampling, out4[3] oversampling steps.  Synchronises. */
 hyrom_status hyrom_odeim_counters(hyrom_ctx* ctx, int64_t* out4);
+/* Sweeps of the one-sided Jacobi eigensolver (pivoted Cholesky, then
+ * rotations of the factor's columns until no pair is rotated; at most 60) in
+ * the last rebuild: out2[0] the POD eigenproblem of the window Gram matrix
+ * (FP32 contexts; 0 for FP64 contexts, whose POD is a one-sided Jacobi SVD
+ * of the window itself), out2[1] ODEIM's first m x m eigensystem (0 before
+ * the first ODEIM call).  Synchronises. */
+hyrom_status hyrom_eig_sweeps(hyrom_ctx* ctx, int32_t* out2);
 hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count);
 
 /* ---- Algorithm 1 --------------------------------------------------------

@@ -771,8 +771,10 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->X, ctx->f32 ? (size_t)N * sizeof(double) : (size_t)N * wp * sizeof(double));
   ok &= dal(ctx, &ctx->rawpart, 152 * 4 * sizeof(double));
   ok &= dal(ctx, &ctx->rotated, 64);
+  if (ok) ok &= cudaMemsetAsync(ctx->rotated, 0, 64, ctx->st) == cudaSuccess;
   ok &= dal(ctx, &ctx->ident, (size_t)wp * wp * sizeof(double));
   ok &= dalloc(ctx, &ctx->od_ws, hy::odeim_ws_bytes(N, m));
+  if (ok) ok &= cudaMemsetAsync(ctx->od_ws, 0, 256, ctx->st) == cudaSuccess;  // control block
   ok &= dal(ctx, &ctx->tol_dev, 64);
   ok &= dal(ctx, &ctx->newton_ws, (size_t)6 * cfg->nx * sizeof(double));
   ok &= dal(ctx, &ctx->fail_dev, 64);
@@ -857,6 +859,18 @@ hyrom_status hyrom_odeim_counters(hyrom_ctx* ctx, int64_t* out4) {
   hy::odeim_stats(ctx->od_ws, h, ctx->st);
   if (hyrom_status s = sync(ctx)) return s;
   for (int i = 0; i < 4; ++i) out4[i] = (int64_t)h[i];
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_eig_sweeps(hyrom_ctx* ctx, int32_t* out2) {
+  if (!ctx || !out2) return HYROM_EINVAL;
+  if (ctx->sticky) return HYROM_ECUDA;
+  int* h = (int*)ctx->host;
+  CK(cudaMemcpyAsync(h, ctx->rotated + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  hy::odeim_eig_sweeps(ctx->od_ws, h + 1, ctx->st);
+  if (hyrom_status s = sync(ctx)) return s;
+  out2[0] = h[0];
+  out2[1] = h[1];
   return HYROM_OK;
 }
 
@@ -1043,21 +1057,29 @@ hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,
   ctx->sample_ok = false;
   CK(cudaMemsetAsync(ctx->fail_dev + 8, 0, 2 * sizeof(int), ctx->st));
   if (ctx->f32) {
+    t_begin(ctx, HYROM_T_SNORMAL);
     hy::launch_sample_normal<float>((const float*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
                                     ctx->nc, ctx->cfg.reduced_prec, ctx->s_part, ctx->s_G,
                                     ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
+    t_end(ctx, HYROM_T_SNORMAL);
+    t_begin(ctx, HYROM_T_GAPPY);
     hy::launch_sample_solve<float>((const float*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
                                    ctx->nc, (const float*)v, (const float*)psi, ctx->s_part,
                                    ctx->s_b, ctx->s_L, ctx->s_dinv, y_out, nullptr, nullptr,
                                    ctx->st);
+    t_end(ctx, HYROM_T_GAPPY);
   } else {
+    t_begin(ctx, HYROM_T_SNORMAL);
     hy::launch_sample_normal<double>((const double*)phi, ctx->N, m, cells, n_cells,
                                      ctx->dc.nvar, ctx->nc, ctx->cfg.reduced_prec, ctx->s_part,
                                      ctx->s_G, ctx->s_L, ctx->s_dinv, ctx->fail_dev + 8, ctx->st);
+    t_end(ctx, HYROM_T_SNORMAL);
+    t_begin(ctx, HYROM_T_GAPPY);
     hy::launch_sample_solve<double>((const double*)phi, ctx->N, m, cells, n_cells, ctx->dc.nvar,
                                     ctx->nc, (const double*)v, (const double*)psi, ctx->s_part,
                                     ctx->s_b, ctx->s_L, ctx->s_dinv, y_out, nullptr, nullptr,
                                     ctx->st);
+    t_end(ctx, HYROM_T_GAPPY);
   }
   CKL();
   int* hf = (int*)ctx->host + 12;

@@ -144,5 +144,6 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                  void* mark_arg = nullptr);
 size_t odeim_ws_bytes(int64_t N, int m);
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
+void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s);
 
 }  // namespace hy

@@ -40,7 +40,7 @@ struct OdCtl {
   double cn2;               // 1 + |c|^2            (DEIM)
   double lam1, lam2, lmax;  // eigenvalues of M (ODEIM)
   int n_list;                // rows passed on by the z_1 filter (ODEIM)
-  int pad_;
+  int eig_sweeps;            // Jacobi sweeps of the first eigensystem (ODEIM)
   unsigned long long ubest;  // packed (upper bound bits, position) (ODEIM)
   // counters over one ODEIM call: DEIM rows scored, ODEIM rows given the
   // full FP32 bound, ODEIM exact scores, greedy steps
@@ -53,6 +53,12 @@ size_t odeim_ctl_bytes() { return 256; }
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s) {
   const OdCtl* c = (const OdCtl*)ws;
   cudaMemcpyAsync(out4, c->stat, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+}
+
+// Jacobi sweeps of the last ODEIM call's first eigensystem
+void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s) {
+  const OdCtl* c = (const OdCtl*)ws;
+  cudaMemcpyAsync(out, &c->eig_sweeps, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 // ---- row norms and buckets --------------------------------------------------
@@ -1412,6 +1418,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                   (int*)host_pinned + 2) < 0)
     return -1;
   rank_m = ((int*)host_pinned)[2];
+  cudaMemcpyAsync(&o.ctl->eig_sweeps, o.jflag + 4, sizeof(int), cudaMemcpyDeviceToDevice, s);
   if (rank_m == m) {
     k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, m, m, o.lam_s, o.W_s, o.ctl);
   } else {

@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cw = warp - 1;
     const int blk = cw % P::kBlk, j0 = cw / P::kBlk;  // columns j0 + kColStep t
     const int rl = blk * 32 + lane;                   // row within the stage
-    for (int g = 0; g < nst && !stop_s; ++g) {
-      const int s = g % P::kStages;
+    // the gathers of stage g + 1 are issued before stage g waits for its
+    // ring slot, so two stages of loads are in flight per thread
+    auto gather = [&](int g, float* x) {
       const int64_t r = r0 + (int64_t)g * P::kRowsStage + rl;
-      float x[P::kColsWarp];
-      if (r < r1) {
+      if (g < nst && r < r1) {
         const int64_t dof = sample_dof_tc(cells, ns, nc, r);
 #pragma unroll
         for (int t = 0; t < P::kColsWarp; ++t) {
@@ -194,6 +194,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int t = 0; t < P::kColsWarp; ++t) x[t] = 0.f;
       }
+    };
+    float xn[P::kColsWarp];
+    gather(0, xn);
+    for (int g = 0; g < nst && !stop_s; ++g) {
+      const int s = g % P::kStages;
+      float x[P::kColsWarp];
+#pragma unroll
+      for (int t = 0; t < P::kColsWarp; ++t) x[t] = xn[t];
+      gather(g + 1, xn);
       if (g >= P::kStages && !mbar_wait(&empty[s], (uint32_t)((g / P::kStages - 1) & 1))) {
         fail();
         break;

@@ -783,129 +783,198 @@ __global__ void k_osj_sweep(double* B, int n, const int* __restrict__ rank, doub
   }
 }
 
-// All sweeps in one launch of one 16-CTA thread-block cluster: column j of B
-// lives in the shared memory of CTA j % 16 (slot j / 16).  In each round
-// pair b goes to CTA b % 16 and to a group of 8 lanes there, which reads both
-// columns through distributed shared memory, forms their inner product,
-// rotates them and writes them back; a cluster barrier ends the round.  The
-// squared column norms are formed at the start of each sweep and carried
+// One-sided Jacobi on the columns of B (n <= 128), all sweeps in one launch
+// of one thread-block cluster of C = ceil(n / 8) CTAs, by blocks: the
+// columns form nb = 2 C blocks of four, block j held in CTA j % C (slot
+// j / C).  A sweep is a round-robin tournament of the blocks (nb - 1
+// rounds); in a round, CTA c takes the pair of blocks rr_pair(nb, rd, c),
+// copies both into its own shared memory through distributed shared
+// memory, rotates the 16 pairs across the two blocks (and, in the sweep's
+// first round, the 6 pairs within each block) in warp-local inner rounds of
+// 4 disjoint pairs, 8 lanes per pair, and writes the blocks back; one
+// cluster barrier ends the round.  Every column pair meets once per sweep.
+// The squared column norms are formed at the start of each sweep and carried
 // through the rotations (a' = cs^2 a - 2 cs sn g + sn^2 c, and likewise c'),
-// so a pair costs one inner product.  Every
-// CTA runs the same number of rounds and barriers: after a sweep all read
-// the same rotation flag (kept in CTA 0, one per sweep parity) and stop
-// together; at most max_sweeps.
-constexpr int kOsjCta = 16;
-constexpr int kOsjSlots = (kEigMaxN + kOsjCta - 1) / kOsjCta;
-constexpr int kOsjLanes = 8;  // lanes per pair
+// so a pair costs one inner product.  Every CTA runs the same number of
+// rounds and barriers: after a sweep all read the same rotation flag (kept
+// in CTA 0, one per sweep parity) and stop together; at most max_sweeps.
+constexpr int kBjCols = 4;     // columns per block
+constexpr int kBjMaxN = 128;   // rows (and columns) at most
+constexpr int kBjThreads = kBjMaxN;  // one thread per row when blocks move; 4 warps
 
-__global__ void __launch_bounds__(256) k_osj_cluster(double* __restrict__ B, int n,
-                                                     const int* __restrict__ rank, double tol,
-                                                     int max_sweeps, int* __restrict__ sweeps_out) {
+// Rotate columns X, Y (length n, in this CTA's shared memory) with carried
+// squared norms *na, *nc by one warp (lane l holds rows l + 32 u); returns
+// whether a rotation was applied.  A warp-wide FP64 instruction occupies an
+// SM sub-partition for 64 cycles, so each of the CTA's four warps takes one
+// pair and the scalar work per pair is kept to a few FP64 instructions.
+HY_DEV bool bj_rotate(double* X, double* Y, double* na, double* nc, int n, int lane, double tol) {
+  constexpr int kPer = kBjMaxN / 32;
+  double xv[kPer], yv[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = lane + 32 * u;
+    xv[u] = i < n ? X[i] : 0.0;
+    yv[u] = i < n ? Y[i] : 0.0;
+  }
+  const double a = *na, c = *nc;
+  double g = fma(xv[0], yv[0], xv[1] * yv[1]) + fma(xv[2], yv[2], xv[3] * yv[3]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if (!(g * g > tol * tol * (a * c) && a > 0.0 && c > 0.0)) return false;
+  // Angle in FP32 (any angle near the optimum converges): t = tan(theta),
+  // cs = (1 + t^2)^{-1/2}, sn = cs t.  The rotation is made orthogonal to
+  // FP64 precision by scaling (cs, sn) with q^{-1/2}, q = cs^2 + sn^2 =
+  // 1 + e (|e| < 1e-6, exact squares of FP32 values): q^{-1/2} = 1 - e/2 +
+  // 3e^2/8 to within e^3.
+  const float df = (float)(c - a), g2 = (float)(2.0 * g);
+  const float sc = fmaxf(fabsf(df), fabsf(g2));
+  const float uu = df / sc, vv = g2 / sc;
+  const float tf = copysignf(1.f, uu) * vv / (fabsf(uu) + sqrtf(fmaf(uu, uu, vv * vv)));
+  double cs, sn;
+  if (tf != 0.f && isfinite(tf)) {
+    const float c32 = rsqrtf(fmaf(tf, tf, 1.f));
+    const double c0 = (double)c32, s0 = (double)(c32 * tf);
+    const double e = fma(c0, c0, s0 * s0) - 1.0;
+    const double rq = 1.0 + fma(0.375 * e, e, -0.5 * e);
+    cs = c0 * rq;
+    sn = s0 * rq;
+  } else {  // out of FP32 range: FP64 formulas
+    const double zeta = (c - a) / (2.0 * g);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+    cs = 1.0 / sqrt(fma(t, t, 1.0));
+    sn = cs * t;
+  }
+#pragma unroll
+  for (int u2 = 0; u2 < kPer; ++u2) {
+    const int i = lane + 32 * u2;
+    if (i < n) {
+      X[i] = fma(cs, xv[u2], -sn * yv[u2]);
+      Y[i] = fma(sn, xv[u2], cs * yv[u2]);
+    }
+  }
+  if (lane == 0) {  // squared norms after the rotation (any angle)
+    const double cc = cs * cs, ss = sn * sn, x2 = 2.0 * cs * sn * g;
+    *na = fma(cc, a, fma(ss, c, -x2));
+    *nc = fma(ss, a, fma(cc, c, x2));
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kBjThreads, 1) k_osj_block(double* __restrict__ B, int n,
+                                                          const int* __restrict__ rank,
+                                                          double tol, int max_sweeps,
+                                                          int* __restrict__ sweeps_out) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ double col[kOsjSlots][kEigMaxN];
-  __shared__ double nrm2[kOsjSlots];
+  __shared__ double hcol[2][kBjCols][kBjMaxN];  // home blocks me (slot 0), me + C (slot 1)
+  __shared__ double hnrm[2][kBjCols];
+  __shared__ double wcol[2][kBjCols][kBjMaxN];  // the round's pair of blocks
+  __shared__ double wnrm[2][kBjCols];
   __shared__ int rot_flag[2];
-  const int me = (int)cl.block_rank();
+  __shared__ int rot_local;
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const int nb = 2 * C;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int gl = tid & (kOsjLanes - 1), grp = tid / kOsjLanes;  // lane in group, group
-  const int ngrp = blockDim.x / kOsjLanes;
-  const int r = *rank, rp = (r + 1) & ~1;
-  for (int idx = tid; idx < kOsjSlots * n; idx += blockDim.x) {
-    const int sl = idx / n, i = idx - sl * n;
-    const int j = sl * kOsjCta + me;
-    col[sl][i] = j < r ? B[(int64_t)j * n + i] : 0.0;
+  const int nw = blockDim.x >> 5;
+  const int r = *rank;
+  // thread t owns row t of every block it moves (blockDim = kBjMaxN rows)
+  const int row = tid;
+#pragma unroll
+  for (int k = 0; k < 2 * kBjCols; ++k) {
+    const int sl = k / kBjCols, c = k % kBjCols;
+    const int j = kBjCols * (me + C * sl) + c;
+    hcol[sl][c][row] = (j < r && row < n) ? B[(int64_t)j * n + row] : 0.0;
   }
   if (tid < 2) rot_flag[tid] = 0;
   cl.sync();
   int* flag0 = cl.map_shared_rank(&rot_flag[0], 0);
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
-    // squared norms of the local columns (one warp per slot)
-    for (int sl = wid; sl < kOsjSlots; sl += blockDim.x >> 5) {
+    // squared norms of the home columns (one warp per column)
+    for (int k = wid; k < 2 * kBjCols; k += nw) {
+      const int sl = k / kBjCols, c = k % kBjCols;
       double a = 0.0;
-      for (int i = lane; i < n; i += 32) a = fma(col[sl][i], col[sl][i], a);
+      for (int i = lane; i < n; i += 32) a = fma(hcol[sl][c][i], hcol[sl][c][i], a);
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) nrm2[sl] = a;
+      if (lane == 0) hnrm[sl][c] = a;
     }
+    if (tid == 0) rot_local = 0;
     cl.sync();
-    for (int rd = 0; rd < rp - 1; ++rd) {
-      // every group runs the same number of iterations, so the 8-lane
-      // shuffles below always see their whole group
-      for (int b0 = 0; b0 < rp / 2; b0 += kOsjCta * ngrp) {
-        const int b = b0 + me + kOsjCta * grp;
-        int p = 0, q = 0;
-        if (b < rp / 2) rr_pair(rp, rd, b, p, q);
-        const bool act = b < rp / 2 && q < r;
-        double* cp = cl.map_shared_rank(&col[p / kOsjCta][0], p % kOsjCta);
-        double* cq = cl.map_shared_rank(&col[q / kOsjCta][0], q % kOsjCta);
-        double* np_ = cl.map_shared_rank(&nrm2[p / kOsjCta], p % kOsjCta);
-        double* nq_ = cl.map_shared_rank(&nrm2[q / kOsjCta], q % kOsjCta);
-        // all of a lane's elements are loaded before any is used
-        constexpr int kPer = (kEigMaxN + kOsjLanes - 1) / kOsjLanes;
-        double xv[kPer], yv[kPer];
+    for (int rd = 0; rd < nb - 1; ++rd) {
+      int pb, qb;
+      rr_pair(nb, rd, me, pb, qb);
+      // the two blocks (and their norms) in their home CTAs
+      double(*hp)[kBjMaxN] = cl.map_shared_rank(hcol[pb / C], (unsigned)(pb % C));
+      double(*hq)[kBjMaxN] = cl.map_shared_rank(hcol[qb / C], (unsigned)(qb % C));
+      double* np_ = cl.map_shared_rank(hnrm[pb / C], (unsigned)(pb % C));
+      double* nq_ = cl.map_shared_rank(hnrm[qb / C], (unsigned)(qb % C));
+      {  // gather: all eight remote loads of a thread are issued before any is used
+        double v[2 * kBjCols];
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int i = gl + kOsjLanes * u;
-          xv[u] = act && i < n ? cp[i] : 0.0;
-          yv[u] = act && i < n ? cq[i] : 0.0;
+        for (int c = 0; c < kBjCols; ++c) {
+          v[c] = hp[c][row];
+          v[kBjCols + c] = hq[c][row];
         }
-        const double a = act ? *np_ : 0.0, c = act ? *nq_ : 0.0;
-        double gp[4] = {0.0, 0.0, 0.0, 0.0};  // four chains (an FP64 FMA is ~64 cycles)
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) gp[u & 3] = fma(xv[u], yv[u], gp[u & 3]);
-        double g = (gp[0] + gp[1]) + (gp[2] + gp[3]);
-        for (int o = kOsjLanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        if (!act) continue;
-        if (g * g > tol * tol * (a * c) && a > 0.0 && c > 0.0) {
-          // The angle comes from FP32 arithmetic (an FP64 divide or square
-          // root costs ~650 cycles): any angle near the optimum converges, and
-          // the rotation stays orthogonal because cs = (1 + t^2)^{-1/2} is
-          // formed in FP64 (FP32 seed, two Newton steps) and sn = cs t.
-          const float df = (float)(c - a), g2 = (float)(2.0 * g);
-          const float sc = fmaxf(fabsf(df), fabsf(g2));
-          const float u = df / sc, v = g2 / sc;
-          float tf = copysignf(1.f, u) * v / (fabsf(u) + sqrtf(fmaf(u, u, v * v)));
-          double t = (double)tf;
-          if (!(tf != 0.f) || !isfinite(tf)) {  // out of FP32 range: FP64 formula
-            const double zeta = (c - a) / (2.0 * g);
-            t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          }
-          const double x = fma(t, t, 1.0);
-          double y = (double)rsqrtf((float)x);
-          y = y * fma(-0.5 * x * y, y, 1.5);
-          y = y * fma(-0.5 * x * y, y, 1.5);
-          const double cs = y, sn = cs * t;
-#pragma unroll
-          for (int u2 = 0; u2 < kPer; ++u2) {
-            const int i = gl + kOsjLanes * u2;
-            if (i < n) {
-              cp[i] = fma(cs, xv[u2], -sn * yv[u2]);
-              cq[i] = fma(sn, xv[u2], cs * yv[u2]);
-            }
-          }
-          if (gl == 0) {  // squared norms after the rotation (any angle)
-            const double cc = cs * cs, ss = sn * sn, x2 = 2.0 * cs * sn * g;
-            *np_ = fma(cc, a, fma(ss, c, -x2));
-            *nq_ = fma(ss, a, fma(cc, c, x2));
-            atomicOr(flag0 + (sw & 1), 1);
-          }
+        for (int c = 0; c < kBjCols; ++c) {
+          wcol[0][c][row] = v[c];
+          wcol[1][c][row] = v[kBjCols + c];
         }
+      }
+      if (tid < 2 * kBjCols) {
+        const int s2 = tid / kBjCols, c = tid % kBjCols;
+        wnrm[s2][c] = s2 == 0 ? np_[c] : nq_[c];
+      }
+      __syncthreads();
+      // inner rounds of four disjoint pairs, one per warp
+      bool rot = false;
+      if (rd == 0) {
+        // pairs within each block: (0,1)(2,3), (0,2)(1,3), (0,3)(1,2); warp
+        // w takes block w / 2, pair w % 2
+        const int wx[3][2] = {{0, 2}, {0, 1}, {0, 1}}, wy[3][2] = {{1, 3}, {2, 3}, {3, 2}};
+        const int s2 = wid >> 1, h = wid & 1;
+        for (int t = 0; t < 3; ++t) {
+          const int x = wx[t][h], y = wy[t][h];
+          rot |= bj_rotate(wcol[s2][x], wcol[s2][y], &wnrm[s2][x], &wnrm[s2][y], n, lane, tol);
+          __syncthreads();
+        }
+      }
+      // pairs across the two blocks: warp w takes column w of the first and
+      // column (w + t) mod 4 of the second, t = 0..3
+      for (int t = 0; t < kBjCols; ++t) {
+        const int y = (wid + t) % kBjCols;
+        rot |= bj_rotate(wcol[0][wid], wcol[1][y], &wnrm[0][wid], &wnrm[1][y], n, lane, tol);
+        __syncthreads();
+      }
+      if (rot && lane == 0) rot_local = 1;
+      __syncthreads();
+      // write the two blocks back to their homes
+#pragma unroll
+      for (int c = 0; c < kBjCols; ++c) {
+        hp[c][row] = wcol[0][c][row];
+        hq[c][row] = wcol[1][c][row];
+      }
+      if (tid < 2 * kBjCols) {
+        const int s2 = tid / kBjCols, c = tid % kBjCols;
+        (s2 == 0 ? np_ : nq_)[c] = wnrm[s2][c];
       }
       cl.sync();
     }
+    if (tid == 0 && rot_local) atomicOr(flag0 + (sw & 1), 1);
+    cl.sync();
     const int rotated = *((volatile int*)(flag0 + (sw & 1)));
     cl.sync();  // everyone has read this sweep's flag before it is reused
     if (me == 0 && tid == 0) rot_flag[(sw + 1) & 1] = 0;
     cl.sync();
     if (!rotated) break;
   }
-  for (int idx = tid; idx < kOsjSlots * n; idx += blockDim.x) {
-    const int sl = idx / n, i = idx - sl * n;
-    const int j = sl * kOsjCta + me;
-    if (j < r) B[(int64_t)j * n + i] = col[sl][i];
+#pragma unroll
+  for (int k = 0; k < 2 * kBjCols; ++k) {
+    const int sl = k / kBjCols, c = k % kBjCols;
+    const int j = kBjCols * (me + C * sl) + c;
+    if (j < r && row < n) B[(int64_t)j * n + row] = hcol[sl][c][row];
   }
-  if (me == 0 && tid == 0 && sweeps_out) *sweeps_out = sw;
+  if (sweeps_out && me == 0 && tid == 0) *sweeps_out = sw < max_sweeps ? sw + 1 : max_sweeps;
 }
 
 // lam[j] = |b_j|^2 and V[:, j] = Pi b_j / |b_j| for j < r; zero beyond.
@@ -928,8 +997,9 @@ __global__ void k_osj_finish(const double* __restrict__ B, int n, const int* __r
 }
 
 // G (n x n, ld n) -> lam (n), V (n x n column-major).  buf: n * n doubles
-// and 2 * kEigMaxN ints.  With host_rank (pinned) the numerical rank is
-// read back (one synchronisation).  Returns 0, or -1 on a CUDA error.
+// and 2 * kEigMaxN ints.  flag (device, 5 ints, nullable): flag[4] = the
+// sweeps the one-sided Jacobi ran.  With host_rank (pinned) the numerical
+// rank is read back (one synchronisation).  Returns 0, or -1 on a CUDA error.
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
                 int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank) {
   if (n > kEigMaxN) return -1;
@@ -939,25 +1009,26 @@ int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int
   const size_t smem = sizeof(double) * (size_t)n * n;
   cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_pchol<<<1, 1024, smem, HY_S(s)>>>(G, n, n, B, piv, rank);
-  (void)flag;
   (void)host_flag;
   const double tol = 1e-14;
-  cudaFuncSetAttribute(k_osj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (n > kBjMaxN) return -1;
+  const int C = (n + 2 * kBjCols - 1) / (2 * kBjCols);  // two blocks of four per CTA
+  cudaFuncSetAttribute(k_osj_block, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(kOsjCta);
-  lc.blockDim = dim3(256);
+  lc.gridDim = dim3(C);
+  lc.blockDim = dim3(kBjThreads);
   lc.dynamicSmemBytes = 0;
   lc.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kOsjCta;
+  at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
   ::hy::count_launch();
-  if (cudaLaunchKernelEx(&lc, k_osj_cluster, B, n, (const int*)rank, tol, max_sweeps,
-                         (int*)nullptr) != cudaSuccess)
+  if (cudaLaunchKernelEx(&lc, k_osj_block, B, n, (const int*)rank, tol, max_sweeps,
+                         flag ? flag + 4 : (int*)nullptr) != cudaSuccess)
     return -1;
   const int sw = 0;
   k_osj_finish<<<n, 128, 0, HY_S(s)>>>(B, n, rank, piv, lam, V);

@@ -115,6 +115,7 @@ def lib():
         "hyrom_kernel_launches": (C.c_uint64, []),
         "hyrom_profile": (st, [vp, C.c_int]),
         "hyrom_odeim_counters": (st, [vp, C.POINTER(i64)]),
+        "hyrom_eig_sweeps": (st, [vp, C.POINTER(C.c_int32)]),
         "hyrom_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(i64)]),
         "hyrom_advance": (st, [vp, C.POINTER(HyromStepInfo)]),
         "hyrom_update_basis": (st, [vp, C.POINTER(HyromStepInfo)]),
@@ -194,6 +195,12 @@ def hyrom_odeim_counters(ctx):
     _check(ctx, lib().hyrom_odeim_counters(ctx, out))
     return {"deim_rows": out[0], "odeim_full_bound": out[1], "odeim_exact": out[2],
             "odeim_steps": out[3]}
+
+
+def hyrom_eig_sweeps(ctx):
+    out = (C.c_int32 * 2)()
+    _check(ctx, lib().hyrom_eig_sweeps(ctx, out))
+    return {"pod": out[0], "odeim": out[1]}
 
 
 def hyrom_stage_times(ctx):
