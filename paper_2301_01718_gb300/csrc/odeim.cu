@@ -414,9 +414,32 @@ __global__ void k_odeim_rank1(const T* __restrict__ phi, int64_t N, int m, const
 
 // sort the Jacobi eigenpairs ascending: lam_s, W_s (m x m column-major);
 // reset the step's control block
+// The screens read the eigensystem in FP32, written once per step where it
+// changes: wt32[a * 64 + j] = W_ja (zero for j >= m), then dn[64] and du[64]
+// at wt32 + 4096: d_j = lam_j - lam_1 (sorted) rounded to nearest and upward
+// for 1 <= j < m, +inf otherwise (slot 0 carries z_1 itself).  One CTA.
+HY_DEV void w32_tail(const double* __restrict__ lam_sorted, int m, float* __restrict__ wt32) {
+  for (int idx = threadIdx.x; idx < m * (64 - m); idx += blockDim.x) {
+    const int a = idx / (64 - m), j = m + idx % (64 - m);
+    wt32[a * 64 + j] = 0.f;
+  }
+  float* dn = wt32 + 64 * 64;
+  float* du = dn + 64;
+  const double l1 = lam_sorted[0];
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    if (j >= 1 && j < m) {
+      dn[j] = (float)(lam_sorted[j] - l1);
+      du[j] = __double2float_ru(__dsub_ru(lam_sorted[j], l1));
+    } else {
+      dn[j] = INFINITY;
+      du[j] = INFINITY;
+    }
+  }
+}
+
 __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __restrict__ V, int n,
                              int m, double* __restrict__ lam_s, double* __restrict__ W_s,
-                             OdCtl* ctl) {
+                             OdCtl* ctl, float* __restrict__ wt32) {
   __shared__ int perm[128];
   __shared__ unsigned long long key[128];
   for (int i = threadIdx.x; i < m; i += blockDim.x) key[i] = dkey(lam[i]);
@@ -441,8 +464,11 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
   __syncthreads();
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     const int j = idx / m, a = idx % m;
-    W_s[idx] = V[(int64_t)perm[j] * n + a];
+    const double v = V[(int64_t)perm[j] * n + a];
+    W_s[idx] = v;
+    wt32[a * 64 + j] = (float)v;
   }
+  w32_tail(lam_s, m, wt32);
 }
 
 // Smallest root of 1 + sum_j z_j^2 / (lam_j - mu) (lam ascending): with
@@ -460,33 +486,13 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
 // cycles on this GPU, an FP32 reciprocal ~85), from tau = 0 until the step is
 // at FP32 rounding; FP64 Newton steps on h then finish inside a shrinking
 // bracket (bisection otherwise).  Stop when |h| is within the rounding error
-// of its evaluation, the step is below 2 ulp, or the bracket has collapsed.  One warp; lane j holds z_j and
-// z_{j+32}.
-__device__ double secular_min_warp(const double* __restrict__ W, int ldw,
-                                   const double* __restrict__ lam, int m, const double* rb,
-                                   double l1, double l2) {
+// of its evaluation, the step is below 2 ulp, or the bracket has collapsed.  One warp; z in shared
+// memory (lane j takes z_j and z_{j+32}).
+__device__ double secular_root_warp(const double* __restrict__ z, const double* __restrict__ lam,
+                                    int m, double l1, double l2) {
   const int lane = threadIdx.x & 31;
-  double z0 = 0.0, z1 = 0.0;
   const int j0 = lane, j1 = lane + 32;
-  if (j0 < m || j1 < m) {  // four chains per component
-    const double* w0 = W + (j0 < m ? j0 : 0) * ldw;
-    const double* w1 = W + (j1 < m ? j1 : 0) * ldw;
-    double p0[4] = {0.0, 0.0, 0.0, 0.0}, p1[4] = {0.0, 0.0, 0.0, 0.0};
-    int a = 0;
-    for (; a + 3 < m; a += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        p0[u] = fma(w0[a + u], rb[a + u], p0[u]);
-        p1[u] = fma(w1[a + u], rb[a + u], p1[u]);
-      }
-    }
-    for (; a < m; ++a) {
-      p0[0] = fma(w0[a], rb[a], p0[0]);
-      p1[0] = fma(w1[a], rb[a], p1[0]);
-    }
-    z0 = j0 < m ? (p0[0] + p0[1]) + (p0[2] + p0[3]) : 0.0;
-    z1 = j1 < m ? (p1[0] + p1[1]) + (p1[2] + p1[3]) : 0.0;
-  }
+  const double z0 = j0 < m ? z[j0] : 0.0, z1 = j1 < m ? z[j1] : 0.0;
   const double q0 = z0 * z0, q1 = z1 * z1;
   const double zz = warp_sum(q0 + q1);
   const double zf = __shfl_sync(0xffffffffu, q0, 0);  // z_1^2
@@ -541,12 +547,12 @@ __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
   for (int itr = 0; itr < 60; ++itr) {
     double g = 0.0, dg = 0.0;
     if (w0 > 0.0) {
-      const double r = 1.0 / (d0 - tau);
+      const double r = rcp64(d0 - tau);
       g = w0 * r;
       dg = g * r;
     }
     if (w1 > 0.0) {
-      const double r = 1.0 / (d1 - tau);
+      const double r = rcp64(d1 - tau);
       const double q = w1 * r;
       g = g + q;
       dg = fma(q, r, dg);
@@ -571,6 +577,37 @@ __device__ double secular_min_warp(const double* __restrict__ W, int ldw,
     tau = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
   }
   return l1 + tau;
+}
+
+// z = W^T rb for the m x m eigenvector block W (column j at W + j ldw) by the
+// whole CTA (blockDim a multiple of 64): thread t forms component t % 64 over
+// one of blockDim / 64 contiguous parts of the m terms (four chains), the
+// parts are then added in a fixed order.  A warp-wide FP64 instruction
+// occupies an SM sub-partition for 64 cycles, so the 64 x 64 product is
+// spread over all the CTA's warps.  Synchronises the CTA on entry and exit.
+HY_DEV void z_block(const double* W, int ldw, const double* rb, int m, double* zp, double* z) {
+  const int t = threadIdx.x, j = t & 63, h = t >> 6, parts = blockDim.x >> 6;
+  const int len = (m + parts - 1) / parts;
+  const int a0 = h * len, a1 = a0 + len < m ? a0 + len : m;
+  __syncthreads();
+  double p[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < m) {
+    const double* w = W + j * ldw;
+    int a = a0;
+    for (; a + 3 < a1; a += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[u] = fma(w[a + u], rb[a + u], p[u]);
+    }
+    for (; a < a1; ++a) p[0] = fma(w[a], rb[a], p[0]);
+  }
+  zp[h * 64 + j] = (p[0] + p[1]) + (p[2] + p[3]);
+  __syncthreads();
+  if (t < 64) {
+    double sm = 0.0;
+    for (int q = 0; q < parts; ++q) sm += zp[q * 64 + t];
+    z[t] = t < m ? sm : 0.0;
+  }
+  __syncthreads();
 }
 
 // ---- ODEIM scoring: certified FP32 bounds, then exact FP64 scores ---------
@@ -658,26 +695,22 @@ HY_DEV float warp_sum_rd(float v) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_odeim_screen(
-    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
-    const double* __restrict__ lam_s, const float* __restrict__ nrm, const int* __restrict__ ord,
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, int p1, const int* __restrict__ list,
     OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R, int C) {
-  __shared__ float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
+  __shared__ __align__(16) float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
   __shared__ float dn[64], du[64];
   __shared__ float ph[8][64];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double l1 = ctl->lam1, l2 = ctl->lam2;
-  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-    const int a = i >> 6, j = i & 63;
-    Wt[a][j] = (a < m && j < m) ? (float)W_s[j * m + a] : 0.f;
-  }
-  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-    if (j >= 1 && j < m) {
-      dn[j] = (float)(lam_s[j] - l1);
-      du[j] = __double2float_ru(__dsub_ru(lam_s[j], l1));
-    } else {  // j = 0 carries z_1 itself; j >= m is padding
-      dn[j] = INFINITY;
-      du[j] = INFINITY;
+  {  // the step's FP32 eigensystem: rows a < m of Wt, then the shifts
+    const float4* src = reinterpret_cast<const float4*>(wt32);
+    float4* dst = reinterpret_cast<float4*>(&Wt[0][0]);
+    for (int i = threadIdx.x; i < m * 16; i += blockDim.x) dst[i] = src[i];
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+      dn[j] = wt32[4096 + j];
+      du[j] = wt32[4096 + 64 + j];
     }
   }
   __syncthreads();
@@ -799,63 +832,97 @@ HY_DEV void stage_w(const double* __restrict__ W_s, const double* __restrict__ l
 }
 
 // exact score of the row with the largest screen bound -> raise smax to it
+// (z by the whole CTA, the root by warp 0)
 template <typename T>
-__global__ void k_odeim_probe_best(const T* __restrict__ phi, int64_t N, int m,
-                                   const double* __restrict__ lam_s, const double* __restrict__ W_s,
-                                   const int* __restrict__ ord, OdCtl* ctl) {
+__global__ void __launch_bounds__(256) k_odeim_probe_best(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
+    const double* __restrict__ W_s, const int* __restrict__ ord, OdCtl* ctl) {
   extern __shared__ double sh[];
-  double* W = sh;              // 64 x kLdw
+  double* W = sh;               // 64 x kLdw
   double* lam = W + 64 * kLdw;  // 64
   double* rb = lam + 64;        // 64
+  double* zp = rb + 64;         // 4 x 64
+  double* zs = zp + 4 * 64;     // 64
   const unsigned long long key = ctl->ubest;
   if (!key) return;
   const int row = ord[(int)(key & 0xffffffffull)];
   stage_w(W_s, lam_s, m, W, lam);
   for (int i = threadIdx.x; i < m; i += blockDim.x) rb[i] = (double)phi[(int64_t)i * N + row];
-  __syncthreads();
+  z_block(W, kLdw, rb, m, zp, zs);
   if (threadIdx.x < 32) {
-    const double mu = secular_min_warp(W, kLdw, lam, m, rb, ctl->lam1, ctl->lam2);
+    const double mu = secular_root_warp(zs, lam, m, ctl->lam1, ctl->lam2);
     if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(mu));
   }
 }
 
 // exact scores of the rows whose bound reaches smax (1 - 2 tie); the others
-// get -1.  One warp per row.
+// get -1.  One CTA of 128 threads per SM walks tiles of 128 positions,
+// interleaved over the CTAs (position p0 + c + G (128 k + t) for CTA c of G)
+// because the rows that reach the limit are the largest-norm ones at the
+// front of the order: the tile's rows that reach it are listed in shared
+// memory, W is staged at the CTA's first such row, and the rows are scored
+// four at a time — z by the whole CTA for each, then warp w solves the
+// secular equation of the w-th row.
+constexpr int kExactThreads = 128;
 template <typename T>
-__global__ void k_odeim_exact(const T* __restrict__ phi, int64_t N, int m,
-                              const double* __restrict__ lam_s, const double* __restrict__ W_s,
-                              const int* __restrict__ ord, int p0, double tie_tol, OdCtl* ctl,
-                              double* __restrict__ scores) {
+__global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
+    const double* __restrict__ W_s, const int* __restrict__ ord, int p0, double tie_tol,
+    OdCtl* ctl, double* __restrict__ scores) {
   extern __shared__ double sh[];
   double* W = sh;               // 64 x kLdw
   double* lam = W + 64 * kLdw;  // 64
-  double* rowbuf = lam + 64;    // per warp: 64
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  stage_w(W_s, lam_s, m, W, lam);
-  __syncthreads();
+  double* rb = lam + 64;        // 4 x 64: rows of the group
+  double* zp = rb + 4 * 64;     // 2 x 64
+  double* zs = zp + 2 * 64;     // 4 x 64
+  __shared__ int list[kExactThreads];
+  __shared__ int nlist;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
   const int end = ctl->n_c;
-  double* rb = rowbuf + 64 * wid;
   double best = 0.0;
   unsigned long long cnt = 0;
-  for (int pos = p0 + blockIdx.x * nw + wid; pos < end; pos += gridDim.x * nw) {
-    const double U = scores[pos];
-    if (U < lim) {
-      if (lane == 0 && U >= 0.0) scores[pos] = -1.0;
-      continue;
+  bool staged = false;
+  if (tid == 0) nlist = 0;
+  __syncthreads();
+  const int G = gridDim.x;
+  for (int base = 0; p0 + blockIdx.x + G * base < end; base += kExactThreads) {
+    const int pos = p0 + blockIdx.x + G * (base + tid);
+    if (pos < end) {
+      const double U = scores[pos];
+      if (U < lim) {
+        if (U >= 0.0) scores[pos] = -1.0;
+      } else {
+        list[atomicAdd(&nlist, 1)] = pos;
+      }
     }
-    const int i = ord[pos];
-    for (int a = lane; a < m; a += 32) rb[a] = (double)phi[(int64_t)a * N + i];
-    __syncwarp();
-    const double mu = secular_min_warp(W, kLdw, lam, m, rb, l1, l2);
-    __syncwarp();
-    if (lane == 0) scores[pos] = mu;
-    best = mu > best ? mu : best;
-    ++cnt;
+    __syncthreads();
+    const int n = nlist;
+    if (n > 0 && !staged) {
+      stage_w(W_s, lam_s, m, W, lam);
+      staged = true;
+    }
+    for (int g = 0; g < n; g += 4) {
+      const int ng = n - g < 4 ? n - g : 4;
+      for (int idx = tid; idx < ng * 64; idx += kExactThreads) {
+        const int q = idx >> 6, a = idx & 63;
+        rb[idx] = a < m ? (double)phi[(int64_t)a * N + ord[list[g + q]]] : 0.0;
+      }
+      for (int q = 0; q < ng; ++q) z_block(W, kLdw, rb + 64 * q, m, zp, zs + 64 * q);
+      if (wid < ng) {
+        const double mu = secular_root_warp(zs + 64 * wid, lam, m, l1, l2);
+        if (lane == 0) scores[list[g + wid]] = mu;
+        best = mu > best ? mu : best;
+        ++cnt;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) nlist = 0;
+    __syncthreads();
   }
   best = block_max(best);
-  if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(best));
+  if (tid == 0) atomicMax(&ctl->smax, dbits(best));
   if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
 }
 
@@ -891,6 +958,7 @@ struct R1Work {
   double dD[64];   // deflated eigenvalues
   int org[64];     // root j: origin index into K
   double tau[64];  // root j = dK[org[j]] + tau[j]
+  double zh[64];   // Loewner z of the non-deflated components
 };
 
 template <typename T>
@@ -899,21 +967,32 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
                              double* __restrict__ Wrot, R1Work* wk) {
   __shared__ double Ws[64 * 64];
   __shared__ double ph[64], z[64], ds[64];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int p = ctl->argmin;
   for (int a = tid; a < m; a += blockDim.x) {
     ph[a] = (double)phi[(int64_t)a * N + p];
     ds[a] = d[a];
   }
   stage_copy(Ws, W, m * m);
-  __syncthreads();
-  for (int j = wid; j < m; j += nw) {
-    double acc = 0.0;
-    for (int a = lane; a < m; a += 32) acc = fma(Ws[j * m + a], ph[a], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) z[j] = acc;
+  __shared__ double zp[4][64];
+  {  // z = W^T phi: thread t forms component t % 64 over a quarter of the terms
+    __syncthreads();
+    const int j = tid & 63, h = tid >> 6;
+    const int len = (m + 3) / 4, a0 = h * len, a1 = a0 + len < m ? a0 + len : m;
+    double p0 = 0.0, p1 = 0.0;
+    if (j < m && h < 4) {
+      int a = a0;
+      for (; a + 1 < a1; a += 2) {
+        p0 = fma(Ws[j * m + a], ph[a], p0);
+        p1 = fma(Ws[j * m + a + 1], ph[a + 1], p1);
+      }
+      if (a < a1) p0 = fma(Ws[j * m + a], ph[a], p0);
+    }
+    if (h < 4) zp[h][j] = p0 + p1;
+    __syncthreads();
+    if (tid < m) z[tid] = (zp[0][tid] + zp[1][tid]) + (zp[2][tid] + zp[3][tid]);
+    __syncthreads();
   }
-  __syncthreads();
   __shared__ int nonsmall[64], nns, anyclose;
   __shared__ double tol_s, nz_s;
   {
@@ -932,11 +1011,15 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
   }
   __syncthreads();
   const double tol = tol_s, nz = nz_s;
-  if (tid == 0) {  // integer work only: ordered list of non-negligible z
-    int c = 0;
-    for (int i = 0; i < m; ++i)
-      if (!(fabs(z[i]) * nz <= tol)) nonsmall[c++] = i;
-    nns = c;
+  if (tid < 64) {  // ordered list of the non-negligible z (two warps, ballots)
+    const bool keep = tid < m && !(fabs(z[tid]) * nz <= tol);
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    __shared__ int wcnt[2];
+    if (lane == 0) wcnt[wid] = __popc(b);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    const int off = (wid == 1 ? wcnt[0] : 0) + __popc(b & ((1u << lane) - 1u));
+    if (keep) nonsmall[off] = tid;
+    if (tid == 0) nns = wcnt[0] + wcnt[1];
   }
   __syncthreads();
   for (int k = 1 + tid; k < nns; k += blockDim.x) {  // adjacent pairs, in parallel
@@ -1078,7 +1161,7 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
     for (int u = 0; u < 2; ++u) {
       const int i = lane + 32 * u;
       if (i < nK) {
-        const double r = 1.0 / (del[u] - t);
+        const double r = rcp64(del[u] - t);
         const double q = z2[u] * r;
         f = f + q;
         fa = fa + fabs(q);
@@ -1140,77 +1223,88 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   }
 }
 
-// Eigenvector j of diag(dK) + z z^T (Loewner z), mapped back through W.
-// CTA j writes column j of Wnew (m values) and lamnew[j].
-__global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __restrict__ Delta,
-                             const double* __restrict__ Wrot, int m, double* __restrict__ Wnew,
-                             double* __restrict__ lamnew) {
-  __shared__ double zh[64], v[64], dK[64];
+// Loewner's z (Gu & Eisenstat): with Delta_iq = d_i - lambda_q,
+//   zh_i^2 = (lambda_i - d_i) prod_{q != i} (lambda_q - d_i) / (d_q - d_i),
+// signed like z_i.  One warp per component i (lane: q and q + 32), a product
+// tree over the lanes.
+__global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __restrict__ Delta) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nK = wk->nK;
+  if (i >= nK) return;
+  const double di = wk->dK[i];
+  double pr = 1.0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = lane + 32 * u;
+    if (q < nK) {
+      const double lq = -Delta[i * 64 + q];  // lambda_q - d_i
+      pr *= q == i ? lq : lq * rcp64(wk->dK[q] - di);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pr *= __shfl_xor_sync(0xffffffffu, pr, o);
+  if (lane == 0) {
+    const double zz = sqrt(fmax(pr, 0.0));
+    wk->zh[i] = wk->zK[i] >= 0.0 ? zz : -zz;
+  }
+}
+
+// Eigenvector j of diag(dK) + z z^T, v_i = zh_i / (d_i - lambda_j), mapped
+// back through W.  CTA j writes column j of Wnew (m values) and lamnew[j];
+// the product with W is split over the CTA's eight warps (thread t: row
+// a = t % 64 over a quarter of the components).
+__global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ wk,
+                                                    const double* __restrict__ Delta,
+                                                    const double* __restrict__ Wrot, int m,
+                                                    double* __restrict__ Wnew,
+                                                    double* __restrict__ lamnew) {
+  __shared__ double v[64];
   __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
-  __shared__ double Ds[64 * 65];  // Delta rows, stride 65
+  __shared__ double part[4][64];
   __shared__ int Ks[64];
   const int j = blockIdx.x, tid = threadIdx.x;
   const int nK = wk->nK;
   if (j >= nK) return;
-  for (int i = tid; i < nK; i += blockDim.x) {
-    dK[i] = wk->dK[i];
-    Ks[i] = wk->K[i];
-  }
+  for (int i = tid; i < nK; i += blockDim.x) Ks[i] = wk->K[i];
   __syncthreads();
   for (int base = tid; base < nK * 64; base += blockDim.x * 8) {
-    double wv[8], dv[8];
+    double wv[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
       const int i = idx >> 6, a = idx & 63;
       wv[u] = idx < nK * 64 && a < m ? Wrot[Ks[i] * m + a] : 0.0;
-      dv[u] = idx < nK * 64 && a < nK ? Delta[idx] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
-      if (idx < nK * 64) {
-        Wk[(idx >> 6) * 65 + (idx & 63)] = wv[u];
-        Ds[(idx >> 6) * 65 + (idx & 63)] = dv[u];
-      }
+      if (idx < nK * 64) Wk[(idx >> 6) * 65 + (idx & 63)] = wv[u];
     }
   }
-  __syncthreads();
-  if (tid < nK) {
-    // Loewner: zh_i^2 = (lambda_i - d_i) prod_{q != i} (lambda_q - d_i) / (d_q - d_i),
-    // the product taken as four independent chains
-    const int i = tid;
-    const double di = dK[i];
-    const double* Dr = Ds + i * 65;
-    double pr[4] = {-Dr[i], 1.0, 1.0, 1.0};
-    for (int q0 = 0; q0 < nK; q0 += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + u;
-        if (q < nK && q != i) pr[u] *= (-Dr[q]) / (dK[q] - di);
-      }
-    }
-    const double prod = (pr[0] * pr[1]) * (pr[2] * pr[3]);
-    const double zz = sqrt(fmax(prod, 0.0));
-    zh[i] = wk->zK[i] >= 0.0 ? zz : -zz;
+  double vi = 0.0;
+  if (tid < 64) {
+    if (tid < nK) vi = wk->zh[tid] * rcp64(Delta[tid * 64 + j]);
+    v[tid] = vi;
   }
   __syncthreads();
-  if (tid < nK) v[tid] = zh[tid] / Ds[tid * 65 + j];
-  __syncthreads();
-  double nrm = 0.0;
-  if (tid < 64) nrm = tid < nK ? v[tid] * v[tid] : 0.0;
+  double nrm = tid < 64 ? vi * vi : 0.0;
   nrm = block_sum(nrm);
   const double inv = 1.0 / sqrt(nrm);
-  for (int a = tid; a < m; a += blockDim.x) {
+  {
+    const int a = tid & 63, h = tid >> 6;
+    const int i0 = h * 16, i1 = i0 + 16 < nK ? i0 + 16 : nK;
     double acc0 = 0.0, acc1 = 0.0;
-    int i = 0;
-    for (; i + 1 < nK; i += 2) {
+    int i = i0;
+    for (; i + 1 < i1; i += 2) {
       acc0 = fma(Wk[i * 65 + a], v[i], acc0);
       acc1 = fma(Wk[(i + 1) * 65 + a], v[i + 1], acc1);
     }
-    if (i < nK) acc0 = fma(Wk[i * 65 + a], v[i], acc0);
-    Wnew[j * m + a] = (acc0 + acc1) * inv;
+    if (i < i1) acc0 = fma(Wk[i * 65 + a], v[i], acc0);
+    part[h][a] = acc0 + acc1;
   }
+  __syncthreads();
+  if (tid < m) Wnew[j * m + tid] = ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
   if (tid == 0) lamnew[j] = wk->dK[wk->org[j]] + wk->tau[j];
 }
 
@@ -1218,7 +1312,7 @@ __global__ void k_r1_vectors(const R1Work* __restrict__ wk, const double* __rest
 __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restrict__ Wrot,
                            const double* __restrict__ Wnew, const double* __restrict__ lamnew,
                            int m, double* __restrict__ d_out, double* __restrict__ W_out,
-                           OdCtl* ctl) {
+                           OdCtl* ctl, float* __restrict__ wt32) {
   __shared__ double lv[64];
   __shared__ unsigned long long key[64];
   __shared__ int src[64];  // >= 0: new pair index; < 0: -(deflated idx)-1
@@ -1254,11 +1348,31 @@ __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restri
   }
   (void)nD;
   for (int i = tid; i < m; i += blockDim.x) d_out[i] = lv[perm[i]];
-  for (int idx = tid; idx < m * m; idx += blockDim.x) {
-    const int j = idx / m, a = idx % m;
-    const int sidx = src[perm[j]];
-    W_out[idx] = sidx >= 0 ? Wnew[sidx * m + a] : Wrot[(-sidx - 1) * m + a];
+  // eight loads in flight per thread before any store
+  for (int base = tid; base < m * m; base += blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      v[u] = 0.0;
+      if (idx < m * m) {
+        const int j = idx / m, a = idx - j * m;
+        const int sidx = src[perm[j]];
+        v[u] = sidx >= 0 ? Wnew[sidx * m + a] : Wrot[(-sidx - 1) * m + a];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < m * m) {
+        W_out[idx] = v[u];
+        const int j = idx / m, a = idx - j * m;
+        wt32[a * 64 + j] = (float)v[u];
+      }
+    }
   }
+  __syncthreads();  // d_out complete
+  w32_tail(d_out, m, wt32);
 }
 
 __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
@@ -1303,6 +1417,7 @@ struct OdeimBufs {
   double* Uf;
   double* yv;
   OdCtl* ctl;
+  float* wt32;  // the step's eigensystem in FP32 for the screens (4096 + 128)
 };
 
 size_t odeim_ws_bytes(int64_t N, int m) {
@@ -1315,6 +1430,7 @@ size_t odeim_ws_bytes(int64_t N, int m) {
   b += sizeof(double) * (5 * 64 * 64 + 3 * 64) + sizeof(R1Work) + 16 * 256;
   b += sizeof(double) * (2 * (m + 1) * (m + 1) + 512) + 3 * 256;
   b += sizeof(double) * (2 * 64 * 64 + 64) + 3 * 256;
+  b += sizeof(float) * (64 * 64 + 128) + 256;
   return b + 4096;
 }
 
@@ -1358,6 +1474,7 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.Lf = (double*)take((size_t)64 * 64 * sizeof(double));
   o.Uf = (double*)take((size_t)64 * 64 * sizeof(double));
   o.yv = (double*)take(64 * sizeof(double));
+  o.wt32 = (float*)take((64 * 64 + 128) * sizeof(float));
   return o;
 }
 
@@ -1408,8 +1525,8 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   // ODEIM oversampling
   const int n = m % 2 ? m + 1 : m;  // Jacobi wants an even order
   k_odeim_gram<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
-  const size_t smem = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 * 8);
-  const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64);
+  const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 + 4 * 64 + 64);
+  const size_t smem_ex = sizeof(double) * ((size_t)64 * kLdw + 64 + 4 * 64 + 2 * 64 + 4 * 64);
   M_(12);
   // eigensystem of M: pivoted Cholesky + one-sided Jacobi; two-sided
   // Jacobi if M is numerically rank deficient (its null space is needed)
@@ -1420,21 +1537,20 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   rank_m = ((int*)host_pinned)[2];
   cudaMemcpyAsync(&o.ctl->eig_sweeps, o.jflag + 4, sizeof(int), cudaMemcpyDeviceToDevice, s);
   if (rank_m == m) {
-    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, m, m, o.lam_s, o.W_s, o.ctl);
+    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, m, m, o.lam_s, o.W_s, o.ctl, o.wt32);
   } else {
     k_pad_sym2<<<1, 256, 0, HY_S(s)>>>(o.M, m, n, o.Mp);
     if (run_jacobi_multi(o.Mp, n, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, o.jscale,
                          (double*)host_pinned + 1, 60, s) < 0)
       return -1;
-    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl);
+    k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl, o.wt32);
   }
   M_(-13);
   for (int l = m; l < np; ++l) {
     M_(13);
     // full FP32 bounds of the largest-norm rows, exact score of the best
     k_odeim_screen<T><<<(probe + 7) / 8, 256, 0, HY_S(s)>>>(
-        phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores,
-        o.rows, C);
+        phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores, o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     k_odeim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
     M_(-14);
@@ -1443,14 +1559,13 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     // all, the full bound for those it does not exclude
     k_odeim_z1<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
                                                 tie_tol, o.ctl, o.scores, o.list, o.rows, C);
-    k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.lam_s, o.nrm, o.ord,
-                                                    o.picked, 0, -1, o.list, o.ctl, o.scores,
-                                                    o.rows, C);
+    k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0,
+                                                    -1, o.list, o.ctl, o.scores, o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     M_(-15);
     M_(15);
-    k_odeim_exact<T><<<152 * 8, 256, smem, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, 0,
-                                                      tie_tol, o.ctl, o.scores);
+    k_odeim_exact<T><<<152, kExactThreads, smem_ex, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord,
+                                                              0, tie_tol, o.ctl, o.scores);
     M_(-16);
     M_(17);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
@@ -1460,9 +1575,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
       M_(16);
       k_r1_prepare<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
       k_r1_roots<<<m, 32, 0, HY_S(s)>>>(o.r1, o.Delta);
+      k_r1_loewner<<<(m + 3) / 4, 128, 0, HY_S(s)>>>(o.r1, o.Delta);
       k_r1_vectors<<<m, 256, 0, HY_S(s)>>>(o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
       k_r1_merge<<<1, 256, 0, HY_S(s)>>>(o.r1, o.Wrot, o.Wnew, o.lamnew, m, o.lam_s2, o.W_s2,
-                                         o.ctl);
+                                         o.ctl, o.wt32);
       std::swap(o.lam_s, o.lam_s2);
       std::swap(o.W_s, o.W_s2);
       M_(-17);
