@@ -398,49 +398,59 @@ HY_DEV bool bits_any(const uint32_t* __restrict__ bm, int64_t b, int len) {
   return acc != 0u;
 }
 
-// Tiles within R cells (x and y) of a kept cell.  Interior tiles read each
-// of their TY + 2R rows as at most three masked words of the bitmap; tiles
-// whose neighbourhood crosses the domain edge take the per-cell path (with
-// the periodic wrap or the clip).  One thread per tile.
+// Tiles within R cells (x and y) of a kept cell, one warp per tile.
+// Interior tiles: lane r reads neighbourhood row r (TY + 2R rows) as at most
+// three masked words of the bitmap, and a ballot combines the rows.  Tiles
+// whose neighbourhood crosses the domain edge (and 1D tiles, wider than 64
+// cells) take the per-cell path with the periodic wrap or the clip, their
+// cells spread over the lanes 32 at a time.
 __global__ void k_filter_next_tiles(DevCfg c, const uint32_t* __restrict__ kbits, int TX, int TY,
                                     int R, int* __restrict__ tiles, int* __restrict__ ntiles,
                                     const int* __restrict__ done) {
   if (*done) return;
+  const int lane = threadIdx.x & 31;
   const int tx = (c.nx + TX - 1) / TX, ty = (c.ny + TY - 1) / TY;
   const bool twoD = c.ny > 1;
   const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
   const int Ry = twoD ? R : 0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tx * ty; t += gridDim.x * blockDim.x) {
+  const int nrows = TY + 2 * Ry, ncols = TX + 2 * R;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tx * ty; t += warps) {
     const int x0 = (t % tx) * TX, y0 = (t / tx) * TY;
-    bool any = false;
     const bool inx = x0 - R >= 0 && x0 + TX + R <= c.nx;
     const bool iny = !twoD || (y0 - Ry >= 0 && y0 + TY + Ry <= c.ny);
-    if (inx && iny && TX + 2 * R <= 64) {
-      for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j)
-        any = bits_any(kbits, (int64_t)(twoD ? j : 0) * c.nx + (x0 - R), TX + 2 * R);
+    bool any = false;
+    if (inx && iny && ncols <= 64 && nrows <= 32) {
+      bool mine = false;
+      if (lane < nrows)
+        mine = bits_any(kbits, (int64_t)(twoD ? y0 - Ry + lane : 0) * c.nx + (x0 - R), ncols);
+      any = __any_sync(0xffffffffu, mine);
     } else {
-      for (int j = y0 - Ry; j < y0 + TY + Ry && !any; ++j) {
-        int jj = j;
-        if (twoD) {
-          if (pery)
-            jj = imod(j, c.ny);
-          else if (j < 0 || j >= c.ny)
-            continue;
-        } else {
-          jj = 0;
-        }
-        const int64_t rowbase = (int64_t)jj * c.nx;
-        for (int i = x0 - R; i < x0 + TX + R && !any; ++i) {
-          int ii = i;
+      const int cells = nrows * ncols;
+      for (int e0 = 0; e0 < cells && !any; e0 += 32) {
+        bool mine = false;
+        const int e = e0 + lane;
+        if (e < cells) {
+          const int j = y0 - Ry + e / ncols, i = x0 - R + e % ncols;
+          int jj = 0, ii = i;
+          bool ok = true;
+          if (twoD) {
+            jj = j;
+            if (pery)
+              jj = imod(j, c.ny);
+            else if (j < 0 || j >= c.ny)
+              ok = false;
+          }
           if (perx)
             ii = imod(i, c.nx);
           else if (i < 0 || i >= c.nx)
-            continue;
-          any = bit_get(kbits, rowbase + ii);
+            ok = false;
+          mine = ok && bit_get(kbits, (int64_t)jj * c.nx + ii);
         }
+        any = __any_sync(0xffffffffu, mine);
       }
     }
-    if (any) tiles[atomicAdd(ntiles, 1)] = t;
+    if (any && lane == 0) tiles[atomicAdd(ntiles, 1)] = t;
   }
 }
 
@@ -496,8 +506,8 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
                                                                    cur_n, nt);
       if (pass + 1 < jmax_f) {
         cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
-        k_filter_next_tiles<<<(nt + 255) / 256, 256, 0, HY_S(s)>>>(c, kbits, TX, TY, n + 1, nxt,
-                                                                   nxt_n, ctl);
+        k_filter_next_tiles<<<(nt + 7) / 8, 256, 0, HY_S(s)>>>(c, kbits, TX, TY, n + 1, nxt,
+                                                               nxt_n, ctl);
         cur = nxt;
         nxt = (nxt == tiles_a) ? tiles_b : tiles_a;
         int* tn = cur_n;
