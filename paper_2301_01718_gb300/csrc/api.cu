@@ -111,6 +111,8 @@ struct hyrom_ctx {
   double* s_dinv = nullptr;
   double* s_b = nullptr;
   bool sample_ok = false;
+  // the basis product formed ODEIM's row-norm data for the current basis
+  bool norms_ready = false;
   // pinned host mirror for read-backs
   void* host = nullptr;
   // optional per-stage CUDA-event timers (hyrom_profile): up to kEvPairs
@@ -491,14 +493,21 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
     t_end(ctx, HYROM_T_EIG);
     t_begin(ctx, HYROM_T_FORMPHI);
     if constexpr (sizeof(T) == 4) {
-      // the tensor-core product is kept off until its pipeline beats the
-      // register-tiled SIMT product (see formphi_tc.cu)
       if (kUseTensorBasisProduct && hy::form_phi_tc_ok(ctx->N, w, cf.m)) {
-        // tensor-core product; its bounded waits report through fail_dev[4]
+        // tensor-core product; its bounded waits report through fail_dev[4].
+        // For the context's own basis its epilogue also forms ODEIM's
+        // row-norm data, so the rebuild's ODEIM skips that pass over Phi.
         CK(cudaMemsetAsync(ctx->fail_dev + 4, 0, sizeof(int), ctx->st));
+        hy::OdeimNorms nout = {nullptr, nullptr, nullptr, nullptr};
+        if (phi_out == (T*)ctx->phi) {
+          nout = hy::odeim_norm_bufs(ctx->od_ws, ctx->N);
+          CK(cudaMemsetAsync(nout.bcnt, 0, (hy::kNormBucketCount + 1) * sizeof(int), ctx->st));
+          CK(cudaMemsetAsync(nout.bmax, 0, hy::kNormBucketCount * sizeof(int), ctx->st));
+        }
         hy::launch_form_phi_tc(ring, ctx->N, ctx->win_dev, w, psi, (const float*)ctx->C, cf.m,
                                ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg,
-                               ctx->fail_dev + 4, ctx->st);
+                               ctx->fail_dev + 4, nout, ctx->st);
+        ctx->norms_ready = nout.nrm != nullptr;
         tc_used = true;
       }
     }
@@ -610,8 +619,11 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     int np = cf.n_p;
     if (np > ctx->N) np = (int)ctx->N;
     t_begin(ctx, HYROM_T_DEIM);
+    const bool nr = ctx->norms_ready;
+    ctx->norms_ready = false;
     if (hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts,
-                            ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx) < 0)
+                            ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx,
+                            nr) < 0)
       return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
     ctx->np_eff = np;
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));

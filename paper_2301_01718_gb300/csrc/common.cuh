@@ -121,6 +121,15 @@ HY_DEV double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// Bucket of a row's squared-norm bound v among 256 (ratio 2^(1/4) per
+// bucket, bucket 255 for v = 0): the order ODEIM scans rows in.
+constexpr int kNormBuckets = 256;
+HY_DEV int nrm_bucket(float v) {
+  if (!(v > 0.0f)) return kNormBuckets - 1;
+  int b = (int)floorf(24.0f - 4.0f * log2f(v));
+  return b < 0 ? 0 : (b > kNormBuckets - 2 ? kNormBuckets - 2 : b);
+}
+
 template <typename T>
 HY_DEV T warp_max(T v) {
   for (int o = 16; o > 0; o >>= 1) {

@@ -22,7 +22,10 @@
 //     kind::tf32) into one of two 128 x 64 FP32 accumulators in tensor
 //     memory (tiles alternate), committed to the chunk's and tile's mbarriers;
 //   * warps 4-7 (epilogue): tcgen05.ld of a finished accumulator (warp w:
-//     rows 32 (w % 4) ..), release it, and coalesced stores of Phi.
+//     rows 32 (w % 4) ..), release it, and coalesced stores of Phi; when
+//     asked, also each row's squared-norm bound and bucket for ODEIM (the
+//     FP32 sum in column order, as ODEIM's own row-norm pass forms it), with
+//     per-CTA bucket counts and maxima in shared memory flushed at the end.
 // C is split and staged once per CTA.  Every mbarrier wait is bounded (about
 // a second); a timeout sets *err and a shared stop flag that ends every
 // role's loop, and the tensor memory is freed before the CTA returns.
@@ -37,6 +40,7 @@ namespace hy {
 namespace {
 
 using namespace tc;
+static_assert(kNormBucketCount == kNormBuckets, "row-norm buckets");
 
 constexpr int kRows = 128;     // tile rows (UMMA M)
 constexpr int kCols = 64;      // basis columns (UMMA N), zero padded beyond m_eff
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_form_phi_tc(const float* __restrict__ ring, int64_t N, const int* __restrict__ win, int w,
                   const float* __restrict__ psi, const float* __restrict__ C, int m,
                   const int* __restrict__ m_eff_dev, float* __restrict__ phi,
-                  float* __restrict__ psi_next, int* __restrict__ err) {
+                  float* __restrict__ psi_next, int* __restrict__ err, OdeimNorms nout) {
   extern __shared__ unsigned char smraw[];
   unsigned char* base =
       smraw + ((1024 - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
@@ -83,6 +87,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_s;
   __shared__ int ws[kMaxW];
   __shared__ volatile int stop_s;
+  __shared__ int hcnt[kNormBuckets];
+  __shared__ unsigned int hmax[kNormBuckets];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int me = *m_eff_dev;
@@ -102,6 +108,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     *reinterpret_cast<float*>(Blo + off) = lo;
   }
   for (int i = tid; i < w; i += kThreads) ws[i] = win[i];
+  for (int i = tid; i < kNormBuckets; i += kThreads) {
+    hcnt[i] = 0;
+    hmax[i] = 0u;
+  }
   if (tid == 0) {
     for (int s = 0; s < kRawStages; ++s) {
       mbar_init(&raw_full[s], 1);
@@ -201,7 +211,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t r0 = (int64_t)blockIdx.x * kRows + row;
       pr_next = r0 < N ? psi[r0] : 0.f;
     }
-    for (int64_t g = 0; g < total && !stop_s; ++g) {
+    for (int64_t g = 0; g < total; ++g) {
+      if (__any_sync(0xffffffffu, stop_s != 0)) break;  // warp-uniform (__syncwarp below)
       const int64_t t = g / nch;
       const int c = (int)(g % nch);
       const int64_t row0 = (blockIdx.x + t * (int64_t)gridDim.x) * kRows;
@@ -214,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         pr_next = (t + 1 < my_tiles && rn < N) ? psi[rn] : 0.f;
       }
       const int rs = (int)(g % kRawStages), as = (int)(g % kAStages);
-      if (!mbar_wait(&raw_full[rs], (uint32_t)((g / kRawStages) & 1))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (uint32_t)((g / kRawStages) & 1)))) {
         fail();
         break;
       }
@@ -236,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&raw_empty[rs]);
-      if (g >= kAStages && !mbar_wait(&a_empty[as], (uint32_t)((g / kAStages - 1) & 1))) {
+      if (g >= kAStages &&
+          !__all_sync(0xffffffffu, mbar_wait(&a_empty[as], (uint32_t)((g / kAStages - 1) & 1)))) {
         fail();
         break;
       }
@@ -269,9 +281,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 4) {
     // ---- epilogue: accumulator of tile t -> Phi ----
     const int lanegrp = warp & 3;
-    for (int64_t t = 0; t < my_tiles && !stop_s; ++t) {
+    // loop decisions are warp-uniform: the loads and ballots below are
+    // warp-collective
+    for (int64_t t = 0; t < my_tiles; ++t) {
+      if (__any_sync(0xffffffffu, stop_s != 0)) break;
       const int b = (int)(t & 1);
-      if (!mbar_wait(&d_full[b], (uint32_t)((t >> 1) & 1))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&d_full[b], (uint32_t)((t >> 1) & 1)))) {
         fail();
         break;
       }
@@ -291,12 +306,41 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (32 + j < me) phi[(int64_t)(32 + j) * N + r] = v1[j];
         }
       }
+      if (nout.nrm) {
+        const bool valid = r < N;
+        float acc = 0.f;  // columns past m_eff are zero
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = fmaf(v0[j], v0[j], acc);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = fmaf(v1[j], v1[j], acc);
+        // an upper bound of the exact squared norm (m terms of relative
+        // error <= 2^-24 each; 1e-5 covers m <= 128)
+        const float up = __double2float_ru((double)acc * (1.0 + 1e-5));
+        const int b = nrm_bucket(up);
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+          nout.nrm[r] = up;
+          nout.bkt[r] = (unsigned char)b;
+          const unsigned peers = __match_any_sync(vm, b);
+          const unsigned mx = __reduce_max_sync(peers, __float_as_uint(up));
+          if (lane == __ffs(peers) - 1) {
+            atomicAdd(&hcnt[b], __popc(peers));
+            atomicMax(&hmax[b], mx);
+          }
+        }
+      }
     }
   }
   // all roles done; in-flight MMAs ended before their last commit was seen
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (nout.nrm)
+    for (int i = tid; i < kNormBuckets; i += kThreads)
+      if (hcnt[i]) {
+        atomicAdd(&nout.bcnt[i], hcnt[i]);
+        atomicMax(&nout.bmax[i], hmax[i]);
+      }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
@@ -311,12 +355,12 @@ bool form_phi_tc_ok(int64_t N, int w, int m) {
 
 void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
                         const float* C, int m, const int* m_eff_dev, float* phi,
-                        float* psi_next, int* err, cudaStream_t s) {
+                        float* psi_next, int* err, OdeimNorms norms, cudaStream_t s) {
   cudaFuncSetAttribute(k_form_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   int64_t tiles = (N + kRows - 1) / kRows;
   const int grid = (int)(tiles < 152 ? tiles : 152);
   k_form_phi_tc<<<grid, kThreads, kSmemBytes, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,
-                                                         phi, psi_next, err);
+                                                         phi, psi_next, err, norms);
 }
 
 }  // namespace hy

@@ -87,13 +87,23 @@ void launch_identity(double* V, int n, cudaStream_t s);
 int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
                      int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,
                      cudaStream_t s);
+// Row-norm data ODEIM orders its rows by (odeim.cu); the basis product can
+// form it in its epilogue.
+constexpr int kNormBucketCount = 256;
+struct OdeimNorms {
+  float* nrm;          // N upper bounds of the squared row norms
+  unsigned char* bkt;  // N bucket ids
+  int* bcnt;           // 257 bucket counts (zeroed before the producer runs)
+  unsigned int* bmax;  // 256 bucket maxima (bits of the FP32 bounds; zeroed likewise)
+};
 // Phi = (X - psi 1^T) C and psi_next on the tensor cores (formphi_tc.cu):
 // FP32 ring, N % 4 == 0, w <= 128, m <= 64.  *err is set if a pipeline wait
-// timed out.
+// timed out.  With norms.nrm != NULL the epilogue also forms ODEIM's
+// row-norm data for the new Phi.
 bool form_phi_tc_ok(int64_t N, int w, int m);
 void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
                         const float* C, int m, const int* m_eff_dev, float* phi,
-                        float* psi_next, int* err, cudaStream_t s);
+                        float* psi_next, int* err, OdeimNorms norms, cudaStream_t s);
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
                 int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
@@ -137,11 +147,13 @@ void launch_sample_solve(const T* phi, int64_t N, int m, const int* cells, int n
 int launch_sample_gram_tc(const float* phi, int64_t N, int m, const int* cells, int ns, int nvar,
                           int64_t nc, int red, double* part, int* err, cudaStream_t s);
 
-// odeim.cu
+// odeim.cu.  norms_ready: the row-norm bounds, bucket ids and bucket counts
+// and maxima (OdeimNorms) were already formed for phi (by the basis product).
+OdeimNorms odeim_norm_bufs(void* ws, int64_t N);
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int) = nullptr,
-                 void* mark_arg = nullptr);
+                 void* mark_arg = nullptr, bool norms_ready = false);
 size_t odeim_ws_bytes(int64_t N, int m);
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
 void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s);

@@ -63,11 +63,7 @@ void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s) {
 
 // ---- row norms and buckets --------------------------------------------------
 
-HY_DEV int nrm_bucket(float v) {
-  if (!(v > 0.0f)) return kNB - 1;
-  int b = (int)floorf(24.0f - 4.0f * log2f(v));
-  return b < 0 ? 0 : (b > kNB - 2 ? kNB - 2 : b);
-}
+static_assert(kNB == kNormBuckets, "row-norm buckets");
 
 template <typename T>
 __global__ void k_rownorm(const T* __restrict__ phi, int64_t N, int m, float* __restrict__ nrm,
@@ -205,8 +201,8 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
   for (int i = 0; i < l; ++i) {
     const double yi = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31);
     const double* col = Lt + i * 65;
-    if (lane > i && lane < l) b0 = b0 - col[lane] * yi;
-    if (lane + 32 > i && lane + 32 < l) b1 = b1 - col[lane + 32] * yi;
+    if (lane > i && lane < l) b0 = fma(-col[lane], yi, b0);
+    if (lane + 32 > i && lane + 32 < l) b1 = fma(-col[lane + 32], yi, b1);
   }
   const double y0 = b0, y1 = b1;
   // backward: U c = y, with the reciprocals of U's diagonal formed up front
@@ -223,8 +219,8 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
         b1 = ci;
     }
     const double* col = Ut + i * 65;
-    if (lane < i) b0 = b0 - col[lane] * ci;
-    if (lane + 32 < i) b1 = b1 - col[lane + 32] * ci;
+    if (lane < i) b0 = fma(-col[lane], ci, b0);
+    if (lane + 32 < i) b1 = fma(-col[lane + 32], ci, b1);
   }
   double cn = 0.0;
   if (lane < l) {
@@ -276,8 +272,8 @@ __global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const
         a1 = ej;
     }
     const double* row = Us + j * 64;
-    if (lane > j && lane < l) a0 = a0 - row[lane] * ej;
-    if (lane + 32 > j && lane + 32 < l) a1 = a1 - row[lane + 32] * ej;
+    if (lane > j && lane < l) a0 = fma(-row[lane], ej, a0);
+    if (lane + 32 > j && lane + 32 < l) a1 = fma(-row[lane + 32], ej, a1);
   }
   double dot = 0.0;
   if (lane < l) {
@@ -314,14 +310,15 @@ __global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
     const int i = ord[pos];
     double sc = -1.0;
     if (!picked[i]) {
-      double s = 0.0;
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains
       if (sizeof(T) == 4 && pos < C) {  // the copy holds the FP32 values exactly
         const float* rr = R + (int64_t)pos * 64;
-        for (int j = 0; j < l; ++j) s = fma((double)rr[j], cs[j], s);
-        sc = fabs((double)rr[l] - s);
+        for (int j = 0; j < l; ++j) s4[j & 3] = fma((double)rr[j], cs[j], s4[j & 3]);
+        sc = fabs((double)rr[l] - ((s4[0] + s4[1]) + (s4[2] + s4[3])));
       } else {
-        for (int j = 0; j < l; ++j) s = fma((double)phi[(int64_t)j * N + i], cs[j], s);
-        sc = fabs((double)phi[(int64_t)l * N + i] - s);
+        for (int j = 0; j < l; ++j)
+          s4[j & 3] = fma((double)phi[(int64_t)j * N + i], cs[j], s4[j & 3]);
+        sc = fabs((double)phi[(int64_t)l * N + i] - ((s4[0] + s4[1]) + (s4[2] + s4[3])));
       }
       best = sc > best ? sc : best;
     }
@@ -390,14 +387,36 @@ __global__ void k_commit(OdCtl* ctl, int l, int* __restrict__ pts, unsigned char
 
 // M = A^T A over the first l points (m x m, FP64)
 template <typename T>
-__global__ void k_odeim_gram(const T* __restrict__ phi, int64_t N, int m, const int* __restrict__ pts,
-                             int l, double* __restrict__ M) {
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int a = idx / m, b = idx % m;
-    double acc = 0.0;
-    for (int r = 0; r < l; ++r)
-      acc = fma((double)phi[(int64_t)a * N + pts[r]], (double)phi[(int64_t)b * N + pts[r]], acc);
-    M[idx] = acc;
+__global__ void __launch_bounds__(256) k_odeim_gram(const T* __restrict__ phi, int64_t N, int m,
+                                                    const int* __restrict__ pts, int l,
+                                                    double* __restrict__ M) {
+  // M = A^T A, A = the l sampled rows of Phi (l x m): every CTA stages A in
+  // shared memory (eight loads in flight per thread), CTA c forms the rows
+  // a = c, c + G, ... of M, one entry per thread, four chains over the l
+  // terms (fma(x, y) = fma(y, x), so M is exactly symmetric)
+  __shared__ double A[64][65];
+  const int tid = threadIdx.x;
+  for (int base = tid; base < l * m; base += blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int r = idx / m, a = idx - r * m;
+      v[u] = idx < l * m ? (double)phi[(int64_t)a * N + pts[r]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < l * m) A[idx / m][idx % m] = v[u];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 4 * 64; e += blockDim.x) {
+    const int a = blockIdx.x + gridDim.x * (e >> 6), b = e & 63;
+    if (a >= m || b >= m) continue;
+    double p4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = 0; r < l; ++r) p4[r & 3] = fma(A[r][a], A[r][b], p4[r & 3]);
+    M[a * m + b] = (p4[0] + p4[1]) + (p4[2] + p4[3]);
   }
 }
 
@@ -856,45 +875,53 @@ __global__ void __launch_bounds__(256) k_odeim_probe_best(
 }
 
 // exact scores of the rows whose bound reaches smax (1 - 2 tie); the others
-// get -1.  One CTA of 128 threads per SM walks tiles of 128 positions,
-// interleaved over the CTAs (position p0 + c + G (128 k + t) for CTA c of G)
-// because the rows that reach the limit are the largest-norm ones at the
-// front of the order: the tile's rows that reach it are listed in shared
+// get -1.  Only the probe positions [0, probe) and the ctl->n_list positions
+// in `list` (the rows the z_1 bound passed to the full screen) can reach it:
+// every other row keeps its z_1 bound, which is below the limit of that
+// time and so below every later one.  One CTA of 128 threads per SM walks
+// tiles of 128 of these, interleaved over the CTAs (entry c + G (128 k + t)
+// for CTA c of G) because the rows that reach the limit are the largest-norm
+// ones at the front of the order: the tile's rows that reach it are listed in shared
 // memory, W is staged at the CTA's first such row, and the rows are scored
 // four at a time — z by the whole CTA for each, then warp w solves the
-// secular equation of the w-th row.
+// secular equation of the w-th row.  Before each group the limit is raised
+// to the best exact score any CTA has found so far; rows whose bound no
+// longer reaches it get -1 (they cannot reach the tie window of the best).
 constexpr int kExactThreads = 128;
 template <typename T>
 __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
-    const double* __restrict__ W_s, const int* __restrict__ ord, int p0, double tie_tol,
-    OdCtl* ctl, double* __restrict__ scores) {
+    const double* __restrict__ W_s, const int* __restrict__ ord, int probe,
+    const int* __restrict__ list, double tie_tol, OdCtl* ctl, double* __restrict__ scores) {
   extern __shared__ double sh[];
   double* W = sh;               // 64 x kLdw
   double* lam = W + 64 * kLdw;  // 64
   double* rb = lam + 64;        // 4 x 64: rows of the group
   double* zp = rb + 4 * 64;     // 2 x 64
   double* zs = zp + 2 * 64;     // 4 x 64
-  __shared__ int list[kExactThreads];
+  __shared__ int surv[kExactThreads];
   __shared__ int nlist;
+  __shared__ int grp[4];  // the group's positions still to score (-1: none)
+  __shared__ int ngrp;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  const int end = ctl->n_c;
+  const int end = probe + ctl->n_list;  // entries: probe positions, then the list
   double best = 0.0;
   unsigned long long cnt = 0;
   bool staged = false;
   if (tid == 0) nlist = 0;
   __syncthreads();
   const int G = gridDim.x;
-  for (int base = 0; p0 + blockIdx.x + G * base < end; base += kExactThreads) {
-    const int pos = p0 + blockIdx.x + G * (base + tid);
-    if (pos < end) {
+  for (int base = 0; (int)blockIdx.x + G * base < end; base += kExactThreads) {
+    const int e = blockIdx.x + G * (base + tid);
+    if (e < end) {
+      const int pos = e < probe ? e : list[e - probe];
       const double U = scores[pos];
       if (U < lim) {
         if (U >= 0.0) scores[pos] = -1.0;
       } else {
-        list[atomicAdd(&nlist, 1)] = pos;
+        surv[atomicAdd(&nlist, 1)] = pos;
       }
     }
     __syncthreads();
@@ -904,15 +931,33 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
       staged = true;
     }
     for (int g = 0; g < n; g += 4) {
-      const int ng = n - g < 4 ? n - g : 4;
+      const int nq = n - g < 4 ? n - g : 4;
+      if (tid == 0) {
+        const double lnow =
+            fmax(lim, bitsd(*(volatile unsigned long long*)&ctl->smax) * (1.0 - 2.0 * tie_tol));
+        int k = 0;
+        for (int q = 0; q < nq; ++q) {
+          const int pos = surv[g + q];
+          if (scores[pos] >= lnow)
+            grp[k++] = pos;
+          else
+            scores[pos] = -1.0;
+        }
+        ngrp = k;
+      }
+      __syncthreads();
+      const int ng = ngrp;
       for (int idx = tid; idx < ng * 64; idx += kExactThreads) {
         const int q = idx >> 6, a = idx & 63;
-        rb[idx] = a < m ? (double)phi[(int64_t)a * N + ord[list[g + q]]] : 0.0;
+        rb[idx] = a < m ? (double)phi[(int64_t)a * N + ord[grp[q]]] : 0.0;
       }
       for (int q = 0; q < ng; ++q) z_block(W, kLdw, rb + 64 * q, m, zp, zs + 64 * q);
       if (wid < ng) {
         const double mu = secular_root_warp(zs + 64 * wid, lam, m, l1, l2);
-        if (lane == 0) scores[list[g + wid]] = mu;
+        if (lane == 0) {
+          scores[grp[wid]] = mu;
+          atomicMax(&ctl->smax, dbits(mu));  // raises the limit of later groups
+        }
         best = mu > best ? mu : best;
         ++cnt;
       }
@@ -1478,9 +1523,15 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   return o;
 }
 
+OdeimNorms odeim_norm_bufs(void* ws, int64_t N) {
+  const OdeimBufs o = carve(ws, N, 1);  // these buffers precede every m-dependent one
+  return OdeimNorms{o.nrm, o.bkt, o.bcnt, o.bmax};
+}
+
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
-                 void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg) {
+                 void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg,
+                 bool norms_ready) {
   if (m <= 0) return 0;
   if (np > N) np = (int)N;
   OdeimBufs o = carve(ws, N, m);
@@ -1490,11 +1541,13 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   M_(12);
   cudaMemsetAsync(o.ctl, 0, sizeof(OdCtl), s);
   cudaMemsetAsync(o.picked, 0, N, s);
-  cudaMemsetAsync(o.bcnt, 0, (kNB + 1) * sizeof(int), s);
-  cudaMemsetAsync(o.bmax, 0, kNB * sizeof(int), s);
   int64_t blocks = (N + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_rownorm<T><<<(int)blocks, 256, 0, HY_S(s)>>>(phi, N, m, o.nrm, o.bkt, o.bcnt, o.bmax);
+  if (!norms_ready) {  // else the basis product's epilogue formed them
+    cudaMemsetAsync(o.bcnt, 0, (kNB + 1) * sizeof(int), s);
+    cudaMemsetAsync(o.bmax, 0, kNB * sizeof(int), s);
+    k_rownorm<T><<<(int)blocks, 256, 0, HY_S(s)>>>(phi, N, m, o.nrm, o.bkt, o.bcnt, o.bmax);
+  }
   k_bucket_scan<<<1, 32, 0, HY_S(s)>>>(o.bcnt, o.bstart, o.bcur);
   k_bucket_scatter<<<(int)blocks, 256, 0, HY_S(s)>>>(N, o.bkt, o.bcur, o.ord);
   const int C = (int)(N < kCompact ? N : kCompact);
@@ -1524,7 +1577,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   if (np <= m) return 0;
   // ODEIM oversampling
   const int n = m % 2 ? m + 1 : m;  // Jacobi wants an even order
-  k_odeim_gram<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
+  k_odeim_gram<T><<<(m + 3) / 4, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
   const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 + 4 * 64 + 64);
   const size_t smem_ex = sizeof(double) * ((size_t)64 * kLdw + 64 + 4 * 64 + 2 * 64 + 4 * 64);
   M_(12);
@@ -1564,8 +1617,8 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     M_(-15);
     M_(15);
-    k_odeim_exact<T><<<152, kExactThreads, smem_ex, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord,
-                                                              0, tie_tol, o.ctl, o.scores);
+    k_odeim_exact<T><<<152, kExactThreads, smem_ex, HY_S(s)>>>(
+        phi, N, m, o.lam_s, o.W_s, o.ord, probe, o.list, tie_tol, o.ctl, o.scores);
     M_(-16);
     M_(17);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
@@ -1588,8 +1641,8 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
 }
 
 template int launch_odeim<float>(const float*, int64_t, int, int, double, int*, void*, void*,
-                                 cudaStream_t, void (*)(void*, int), void*);
+                                 cudaStream_t, void (*)(void*, int), void*, bool);
 template int launch_odeim<double>(const double*, int64_t, int, int, double, int*, void*, void*,
-                                  cudaStream_t, void (*)(void*, int), void*);
+                                  cudaStream_t, void (*)(void*, int), void*, bool);
 
 }  // namespace hy
