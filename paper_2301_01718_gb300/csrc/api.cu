@@ -113,6 +113,8 @@ struct hyrom_ctx {
   bool sample_ok = false;
   // the basis product formed ODEIM's row-norm data for the current basis
   bool norms_ready = false;
+  // the rebuild's DEIM and oversampling loops as CUDA graphs
+  hy::OdeimGraphs od_graphs;
   // pinned host mirror for read-backs
   void* host = nullptr;
   // optional per-stage CUDA-event timers (hyrom_profile): up to kEvPairs
@@ -130,6 +132,7 @@ struct hyrom_ctx {
 namespace hy {
 static unsigned long long g_launches = 0;
 void count_launch() { ++g_launches; }
+void add_launches(unsigned long long n) { g_launches += n; }
 unsigned long long launch_count() { return g_launches; }
 }  // namespace hy
 
@@ -623,7 +626,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     ctx->norms_ready = false;
     if (hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts,
                             ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx,
-                            nr) < 0)
+                            nr, &ctx->od_graphs) < 0)
       return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
     ctx->np_eff = np;
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));
@@ -822,6 +825,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
 void hyrom_destroy(hyrom_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  hy::odeim_graphs_free(&ctx->od_graphs);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host) cudaFreeHost(ctx->host);
   for (int i = 0; i < HYROM_NSTAGE; ++i) {

@@ -149,11 +149,24 @@ int launch_sample_gram_tc(const float* phi, int64_t N, int m, const int* cells, 
 
 // odeim.cu.  norms_ready: the row-norm bounds, bucket ids and bucket counts
 // and maxima (OdeimNorms) were already formed for phi (by the basis product).
+// graphs (nullable): the DEIM loop and the oversampling loop are captured as
+// CUDA graphs at the first call with a given (N, m, n_p) and replayed after;
+// the arguments baked into them (phi, pts, ws, tie_tol) must then be the
+// same on every call.  Inside a replayed loop no sub-stage marks are made.
+struct OdeimGraphs {
+  void* deim = nullptr;  // cudaGraphExec_t
+  void* over = nullptr;
+  int64_t N = -1;
+  int m = -1, np = -1;
+  unsigned long long deim_launches = 0, over_launches = 0;
+};
+void odeim_graphs_free(OdeimGraphs* g);
 OdeimNorms odeim_norm_bufs(void* ws, int64_t N);
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int) = nullptr,
-                 void* mark_arg = nullptr, bool norms_ready = false);
+                 void* mark_arg = nullptr, bool norms_ready = false,
+                 OdeimGraphs* graphs = nullptr);
 size_t odeim_ws_bytes(int64_t N, int m);
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
 void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s);

@@ -1528,13 +1528,63 @@ OdeimNorms odeim_norm_bufs(void* ws, int64_t N) {
   return OdeimNorms{o.nrm, o.bkt, o.bcnt, o.bmax};
 }
 
+void odeim_graphs_free(OdeimGraphs* g) {
+  if (g->deim) cudaGraphExecDestroy((cudaGraphExec_t)g->deim);
+  if (g->over) cudaGraphExecDestroy((cudaGraphExec_t)g->over);
+  g->deim = g->over = nullptr;
+  g->N = -1;
+  g->m = g->np = -1;
+}
+
+// Run `body` (stream work only, no synchronisation) on s: replay the graph in
+// *exec, or capture body into it and launch that; if the stream cannot be
+// captured, run body directly.  Launch counts: the launches made while
+// capturing stand for the first replay, later replays add *nlaunch.
+template <typename F>
+static void run_graphed(void** exec, unsigned long long* nlaunch, cudaStream_t s, F body) {
+  if (*exec) {
+    cudaGraphLaunch((cudaGraphExec_t)*exec, s);
+    add_launches(*nlaunch);
+    return;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+      cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    body();
+    return;
+  }
+  const unsigned long long before = launch_count();
+  body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  const unsigned long long n = launch_count() - before;
+  cudaGraphExec_t ge = nullptr;
+  if (e != cudaSuccess || !g || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    body();  // the captured work did not run
+    return;
+  }
+  cudaGraphDestroy(g);
+  *exec = (void*)ge;
+  *nlaunch = n;
+  cudaGraphLaunch(ge, s);
+}
+
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg,
-                 bool norms_ready) {
+                 bool norms_ready, OdeimGraphs* graphs) {
   if (m <= 0) return 0;
   if (np > N) np = (int)N;
   OdeimBufs o = carve(ws, N, m);
+  if (graphs && (graphs->N != N || graphs->m != m || graphs->np != np)) {
+    odeim_graphs_free(graphs);
+    graphs->N = N;
+    graphs->m = m;
+    graphs->np = np;
+  }
   auto M_ = [&](int id) {
     if (mark) mark(mark_arg, id);
   };
@@ -1559,6 +1609,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   // DEIM
   const size_t dsmem = sizeof(double) * 2 * 64 * 65;
   cudaFuncSetAttribute(k_deim_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+  auto deim_loop = [&]() {
   for (int l = 0; l < m; ++l) {
     k_deim_solve<T><<<1, 256, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
     k_deim_score<T><<<(probe + 255) / 256, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, 0,
@@ -1570,6 +1621,11 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
     if (l + 1 < m) k_deim_extend<T><<<1, 256, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
   }
+  };
+  if (graphs)
+    run_graphed(&graphs->deim, &graphs->deim_launches, s, deim_loop);
+  else
+    deim_loop();
   if (mark) {  // DEIM ends, oversampling begins
     mark(mark_arg, -12);
     mark(mark_arg, 9);
@@ -1599,15 +1655,20 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl, o.wt32);
   }
   M_(-13);
+  // sub-stage marks only where the loop is not replayed from a graph
+  auto ML_ = [&](int id) {
+    if (mark && !graphs) mark(mark_arg, id);
+  };
+  auto over_loop = [&]() {
   for (int l = m; l < np; ++l) {
-    M_(13);
+    ML_(13);
     // full FP32 bounds of the largest-norm rows, exact score of the best
     k_odeim_screen<T><<<(probe + 7) / 8, 256, 0, HY_S(s)>>>(
         phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores, o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     k_odeim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
-    M_(-14);
-    M_(14);
+    ML_(-14);
+    ML_(14);
     // the other rows whose norm can reach the best score: the z_1 bound for
     // all, the full bound for those it does not exclude
     k_odeim_z1<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
@@ -1615,17 +1676,17 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0,
                                                     -1, o.list, o.ctl, o.scores, o.rows, C);
     k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
-    M_(-15);
-    M_(15);
+    ML_(-15);
+    ML_(15);
     k_odeim_exact<T><<<152, kExactThreads, smem_ex, HY_S(s)>>>(
         phi, N, m, o.lam_s, o.W_s, o.ord, probe, o.list, tie_tol, o.ctl, o.scores);
-    M_(-16);
-    M_(17);
+    ML_(-16);
+    ML_(17);
     k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
     k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
-    M_(-18);
+    ML_(-18);
     if (l + 1 < np) {
-      M_(16);
+      ML_(16);
       k_r1_prepare<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
       k_r1_roots<<<m, 32, 0, HY_S(s)>>>(o.r1, o.Delta);
       k_r1_loewner<<<(m + 3) / 4, 128, 0, HY_S(s)>>>(o.r1, o.Delta);
@@ -1634,15 +1695,20 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
                                          o.ctl, o.wt32);
       std::swap(o.lam_s, o.lam_s2);
       std::swap(o.W_s, o.W_s2);
-      M_(-17);
+      ML_(-17);
     }
   }
+  };
+  if (graphs)
+    run_graphed(&graphs->over, &graphs->over_launches, s, over_loop);
+  else
+    over_loop();
   return 0;
 }
 
 template int launch_odeim<float>(const float*, int64_t, int, int, double, int*, void*, void*,
-                                 cudaStream_t, void (*)(void*, int), void*, bool);
+                                 cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*);
 template int launch_odeim<double>(const double*, int64_t, int, int, double, int*, void*, void*,
-                                  cudaStream_t, void (*)(void*, int), void*, bool);
+                                  cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*);
 
 }  // namespace hy
