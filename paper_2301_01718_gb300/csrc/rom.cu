@@ -65,7 +65,8 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
       beta[j] = (nrm == 0.0) ? 0.0 : -v0 / alpha;
       A[j * np + j] = alpha;
     }
-    for (int i = j + 1 + tid; i < np; i += nt) A[j * np + i] = (v0 == 0.0) ? 0.0 : A[j * np + i] / v0;
+    const double iv0 = (v0 == 0.0) ? 0.0 : rcp64(v0);
+    for (int i = j + 1 + tid; i < np; i += nt) A[j * np + i] *= iv0;
     __syncthreads();
     const double bj = beta[j];
     // apply (I - beta v v^T) to columns j+1..m-1, one warp per column
@@ -78,7 +79,7 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
       d = warp_sum(d) * bj;
       for (int i = j + lane; i < np; i += 32) {
         const double vi = i == j ? 1.0 : A[j * np + i];
-        A[col * np + i] = A[col * np + i] - d * vi;
+        A[col * np + i] = fma(-d, vi, A[col * np + i]);
       }
     }
     __syncthreads();
@@ -104,7 +105,7 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
       d = warp_sum(d) * bj;
       for (int i = j + lane; i < np; i += 32) {
         const double vi = i == j ? 1.0 : A[j * np + i];
-        Q[col * np + i] = Q[col * np + i] - d * vi;
+        Q[col * np + i] = fma(-d, vi, Q[col * np + i]);
       }
     }
     __syncthreads();
@@ -112,14 +113,25 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
   bool bad = false;
   for (int j = 0; j < m; ++j) bad |= (R[j * m + j] == 0.0);
   if (bad && tid == 0) atomicAdd(status, 1);
-  // pinv = R^{-1} Q^T : back substitution, one thread per column i of Q^T
+  // pinv = R^{-1} Q^T: back substitution in shared memory (X, m x n_p, in
+  // the reflectors' space, free once Q is formed), one thread per column i
+  // of Q^T, four chains, reciprocal diagonal; then one coalesced store
+  double* X = A;
   for (int i = tid; i < np; i += nt) {
     for (int r = m - 1; r >= 0; --r) {
-      double acc = Q[r * np + i];
-      for (int cc = r + 1; cc < m; ++cc) acc = fma(-R[r * m + cc], pinv[(int64_t)cc * np + i], acc);
-      pinv[(int64_t)r * np + i] = acc / R[r * m + r];
+      double p4[4] = {Q[r * np + i], 0.0, 0.0, 0.0};
+      int cc = r + 1;
+      for (; cc + 3 < m; cc += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p4[u] = fma(-R[r * m + cc + u], X[(cc + u) * np + i], p4[u]);
+      }
+      for (; cc < m; ++cc) p4[0] = fma(-R[r * m + cc], X[cc * np + i], p4[0]);
+      const double rr = R[r * m + r];
+      X[r * np + i] = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * (rr != 0.0 ? rcp64(rr) : 0.0);
     }
   }
+  __syncthreads();
+  for (int idx = tid; idx < m * np; idx += nt) pinv[idx] = X[idx];
 }
 
 template <typename T>
@@ -817,7 +829,9 @@ HY_DEV bool bj_rotate(double* X, double* Y, double* na, double* nc, int n, int l
     yv[u] = i < n ? Y[i] : 0.0;
   }
   const double a = *na, c = *nc;
-  double g = fma(xv[0], yv[0], xv[1] * yv[1]) + fma(xv[2], yv[2], xv[3] * yv[3]);
+  double g = xv[0] * yv[0];
+#pragma unroll
+  for (int u = 1; u < kPer; ++u) g = fma(xv[u], yv[u], g);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
   if (!(g * g > tol * tol * (a * c) && a > 0.0 && c > 0.0)) return false;
@@ -830,8 +844,9 @@ HY_DEV bool bj_rotate(double* X, double* Y, double* na, double* nc, int n, int l
   const float sc = fmaxf(fabsf(df), fabsf(g2));
   const float uu = df / sc, vv = g2 / sc;
   const float tf = copysignf(1.f, uu) * vv / (fabsf(uu) + sqrtf(fmaf(uu, uu, vv * vv)));
-  double cs, sn;
+  double cs, sn, tt;
   if (tf != 0.f && isfinite(tf)) {
+    tt = (double)tf;
     const float c32 = rsqrtf(fmaf(tf, tf, 1.f));
     const double c0 = (double)c32, s0 = (double)(c32 * tf);
     const double e = fma(c0, c0, s0 * s0) - 1.0;
@@ -843,6 +858,7 @@ HY_DEV bool bj_rotate(double* X, double* Y, double* na, double* nc, int n, int l
     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
     cs = 1.0 / sqrt(fma(t, t, 1.0));
     sn = cs * t;
+    tt = t;
   }
 #pragma unroll
   for (int u2 = 0; u2 < kPer; ++u2) {
@@ -852,10 +868,13 @@ HY_DEV bool bj_rotate(double* X, double* Y, double* na, double* nc, int n, int l
       Y[i] = fma(sn, xv[u2], cs * yv[u2]);
     }
   }
-  if (lane == 0) {  // squared norms after the rotation (any angle)
-    const double cc = cs * cs, ss = sn * sn, x2 = 2.0 * cs * sn * g;
-    *na = fma(cc, a, fma(ss, c, -x2));
-    *nc = fma(ss, a, fma(cc, c, x2));
+  // squared norms after the rotation, a - t g and c + t g: exact for the
+  // optimal angle, within the FP32 angle's error otherwise; they only steer
+  // the rest of the sweep (recomputed at each sweep, and the eigenvalues are
+  // formed from the final columns)
+  if (lane == 0) {
+    *na = fma(-tt, g, a);
+    *nc = fma(tt, g, c);
   }
   return true;
 }
