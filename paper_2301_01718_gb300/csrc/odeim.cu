@@ -1201,6 +1201,75 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   const double delj = dj - dorg, deln = last ? 0.0 : wk->dK[j + 1] - dorg;
   double t = (o == j) ? 0.5 * hi : 0.5 * lo;
   const double eps = 2.220446049250313e-16;
+  {  // the same model steps in FP32 (cheap) to a start for the FP64 ones,
+     // which keep their own bracket
+    const float fe = 1.1920929e-7f;
+    float fdel[2], fz2[2];
+    for (int u = 0; u < 2; ++u) {
+      fdel[u] = (float)del[u];
+      fz2[u] = (float)z2[u];
+    }
+    const float fdelj = (float)delj, fdeln = (float)deln;
+    float ft = (float)t, flo = (float)lo, fhi = (float)hi;
+    for (int it = 0; it < 16; ++it) {
+      float f = 0.f, fa = 0.f, dps = 0.f, dph = 0.f;
+      for (int u = 0; u < 2; ++u) {
+        const int i = lane + 32 * u;
+        if (i < nK) {
+          const float r = __frcp_rn(fdel[u] - ft);
+          const float q = fz2[u] * r;
+          f += q;
+          fa += fabsf(q);
+          if (i <= j)
+            dps = fmaf(q, r, dps);
+          else
+            dph = fmaf(q, r, dph);
+        }
+      }
+      f = 1.f + warp_sum(f);
+      fa = warp_sum(fa);
+      dps = warp_sum(dps);
+      dph = warp_sum(dph);
+      if (fabsf(f) <= 8.f * fe * (1.f + fa + fabsf(ft) * (dps + dph))) break;
+      if (f < 0.f)
+        flo = ft;
+      else
+        fhi = ft;
+      if (fhi - flo <= 2.f * fe * fmaxf(fabsf(fhi), fabsf(flo))) {
+        ft = 0.5f * (flo + fhi);
+        break;
+      }
+      const float Dj = fdelj - ft;
+      float eta = NAN;
+      if (last) {
+        const float sL = dps * Dj * Dj, cq = f - dps * Dj;
+        if (cq > 0.f) eta = Dj + sL / cq;
+      } else {
+        const float Dn = fdeln - ft;
+        const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+        const float A = f - dps * Dj - dph * Dn;
+        const float B = A * (Dj + Dn) + sL + sR;
+        const float Cq = f * Dj * Dn;
+        if (A == 0.f) {
+          if (B != 0.f) eta = Cq / B;
+        } else {
+          const float qq = 0.5f * (B + copysignf(sqrtf(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
+          const float e1 = qq / A, e2 = qq != 0.f ? Cq / qq : NAN;
+          if (e1 > Dj && e1 < Dn) eta = e1;
+          if (e2 > Dj && e2 < Dn) eta = e2;
+        }
+      }
+      float nt = ft + eta;
+      if (fabsf(nt - ft) <= 2.f * fe * fabsf(ft)) {
+        ft = nt;
+        break;
+      }
+      if (!(nt > flo && nt < fhi)) nt = 0.5f * (flo + fhi);
+      ft = nt;
+    }
+    const double tc = (double)ft;
+    if (tc > lo && tc < hi) t = tc;
+  }
   for (int it = 0; it < 100; ++it) {
     double f = 0.0, fa = 0.0, dps = 0.0, dph = 0.0;
     for (int u = 0; u < 2; ++u) {
