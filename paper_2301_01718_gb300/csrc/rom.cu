@@ -628,10 +628,12 @@ constexpr int kEigMaxN = 136;
 
 // Pivoted Cholesky in one CTA, the lower triangle of G in shared memory;
 // the pivot exchange swaps rows and columns in place (O(n) entries), so the
-// trailing update walks contiguous rows.  FP64 throughput bounds this
-// kernel: the update is s (s + 1) / 2 explicit FMAs at trailing size s.
-// B (column k = row k of R over the pivoted order), piv and r go to global
-// memory.
+// trailing update walks contiguous rows.  Row k of R is kept in the upper
+// triangle of the same array (row k, columns >= k: free once column k is
+// eliminated), so the loop touches no global memory.  FP64 throughput
+// bounds this kernel: the update is s (s + 1) / 2 explicit FMAs at trailing
+// size s.  B (column k = row k of R over the pivoted order), piv and r go to
+// global memory at the end.
 __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, int ldg, int n,
                                                 double* __restrict__ B, int* __restrict__ piv_out,
                                                 int* __restrict__ rank_out) {
@@ -644,7 +646,6 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx - i * n;
     A[idx] = G[(int64_t)i * ldg + j];
-    B[idx] = 0.0;
   }
   for (int i = tid; i < n; i += nt) piv[i] = i;
   __syncthreads();
@@ -708,30 +709,38 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
           A[i * n + p] = t;
         }
       }
-      for (int i = tid; i < k; i += nt) {
-        const double t = B[i * n + k];
-        B[i * n + k] = B[i * n + p];
-        B[i * n + p] = t;
+      for (int i = tid; i < k; i += nt) {  // rows of R already formed
+        const double t = A[i * n + k];
+        A[i * n + k] = A[i * n + p];
+        A[i * n + p] = t;
       }
     }
-    if (tid == 0) {
-      const double rkk = sqrt(A[k * n + k]);
-      rk_s[0] = rkk;
-      rk_s[1] = 1.0 / rkk;
+    if (tid == 0) {  // sqrt and 1 / sqrt from an FP32 seed and two Newton steps
+      const double a = A[k * n + k];
+      double y = (double)rsqrtf((float)a);
+      y = y * fma(-0.5 * a * y, y, 1.5);
+      y = y * fma(-0.5 * a * y, y, 1.5);
+      rk_s[0] = a * y;
+      rk_s[1] = y;
     }
     __syncthreads();
     for (int j = k + tid; j < n; j += nt) {
       const double v = j == k ? rk_s[0] : A[j * n + k] * rk_s[1];
       rk[j] = v;
-      B[k * n + j] = v;
     }
     __syncthreads();
+    for (int j = k + tid; j < n; j += nt) A[k * n + j] = rk[j];  // row k of R
     // trailing lower triangle: rows i > k, columns k < j <= i
     for (int i = k + 1 + wid; i < n; i += nt >> 5) {
       const double ri = rk[i];
       for (int j = k + 1 + lane; j <= i; j += 32) A[i * n + j] = fma(-ri, rk[j], A[i * n + j]);
     }
     __syncthreads();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx - i * n;
+    B[idx] = (i < r && j >= i) ? A[idx] : 0.0;
   }
   if (tid == 0) *rank_out = r;
   for (int i = tid; i < n; i += nt) piv_out[i] = piv[i];
