@@ -507,9 +507,10 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
           CK(cudaMemsetAsync(nout.bcnt, 0, (hy::kNormBucketCount + 1) * sizeof(int), ctx->st));
           CK(cudaMemsetAsync(nout.bmax, 0, hy::kNormBucketCount * sizeof(int), ctx->st));
         }
-        hy::launch_form_phi_tc(ring, ctx->N, ctx->win_dev, w, psi, (const float*)ctx->C, cf.m,
-                               ctx->m_eff_dev, phi_out, psi_next ? psi_next : (T*)ctx->fg,
-                               ctx->fail_dev + 4, nout, ctx->st);
+        hy::launch_form_phi_tc(ring, ctx->N, nslot, ctx->win_dev, w, psi, (const float*)ctx->C,
+                               cf.m, ctx->m_eff_dev, phi_out,
+                               psi_next ? psi_next : (T*)ctx->fg, ctx->fail_dev + 4, nout,
+                               ctx->st);
         ctx->norms_ready = nout.nrm != nullptr;
         tc_used = true;
       }

@@ -12,8 +12,10 @@
 //
 // One persistent CTA per SM takes 128-row tiles, with warp-specialised
 // roles handing chunks of 32 window slots to each other through mbarriers:
-//   * warp 0 (producer): bulk async copies (cp.async.bulk, one 512-byte slot
-//     of 128 rows per lane) into a 4-stage ring of raw FP32 chunks;
+//   * warp 0 (producer): a chunk (128 rows x 32 window slots) into a 4-stage
+//     ring of raw FP32 chunks by one 2D tensor copy (cp.async.bulk.tensor
+//     over the snapshot ring, rows x slots) when its slots are consecutive
+//     in the ring, else by bulk copies of one 512-byte slot per lane;
 //   * warps 8-11 (converters, one thread per row): Kahan window sum, centring
 //     by psi, TF32 hi/lo split, writes into a 2-stage ring of A tiles in the
 //     128-byte-swizzled K-major layout the tensor core reads; at a tile's
@@ -29,8 +31,13 @@
 // C is split and staged once per CTA.  Every mbarrier wait is bounded (about
 // a second); a timeout sets *err and a shared stop flag that ends every
 // role's loop, and the tensor memory is freed before the CTA returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -71,7 +78,8 @@ HY_DEV void split_tf32(float x, float& hi, float& lo) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_form_phi_tc(const float* __restrict__ ring, int64_t N, const int* __restrict__ win, int w,
+    k_form_phi_tc(const __grid_constant__ CUtensorMap tmap, int use_tma,
+                  const float* __restrict__ ring, int64_t N, const int* __restrict__ win, int w,
                   const float* __restrict__ psi, const float* __restrict__ C, int m,
                   const int* __restrict__ m_eff_dev, float* __restrict__ phi,
                   float* __restrict__ psi_next, int* __restrict__ err, OdeimNorms nout) {
@@ -162,11 +170,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int k0 = c * kChunk;
       const int nk = w - k0 < kChunk ? w - k0 : kChunk;
       float* dst = raw + s * (kRawBytes / 4);
-      if (lane == 0) mbar_expect_tx(&raw_full[s], (uint32_t)(nk * rows * 4));
-      __syncwarp();
-      if (lane < nk)
-        bulk_g2s(dst + lane * kRows, ring + (int64_t)ws[k0 + lane] * N + row0,
-                 (uint32_t)(rows * 4), &raw_full[s]);
+      const bool cons =
+          use_tma && __all_sync(0xffffffffu, lane >= nk || ws[k0 + lane] == ws[k0] + lane);
+      if (cons) {
+        // one box of 128 rows x 32 slots, laid out like the per-slot copies
+        // (slot-major); rows past N and slots past the ring read as zero
+        if (lane == 0) {
+          mbar_expect_tx(&raw_full[s], (uint32_t)kRawBytes);
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"((int)row0), "r"(ws[k0]),
+              "r"(saddr(&raw_full[s]))
+              : "memory");
+        }
+      } else {
+        if (lane == 0) mbar_expect_tx(&raw_full[s], (uint32_t)(nk * rows * 4));
+        __syncwarp();
+        if (lane < nk)
+          bulk_g2s(dst + lane * kRows, ring + (int64_t)ws[k0 + lane] * N + row0,
+                   (uint32_t)(rows * 4), &raw_full[s]);
+      }
     }
   } else if (warp == 1) {
     // ---- MMA issue (one thread) ----
@@ -353,14 +377,47 @@ bool form_phi_tc_ok(int64_t N, int w, int m) {
   return N > 0 && (N & 3) == 0 && w >= 1 && w <= kMaxW && m >= 1 && m <= kCols;
 }
 
-void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
-                        const float* C, int m, const int* m_eff_dev, float* phi,
-                        float* psi_next, int* err, OdeimNorms norms, cudaStream_t s) {
+// the driver's tensor-map encoder, through the runtime (no link to libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+void launch_form_phi_tc(const float* ring, int64_t N, int nslot, const int* win, int w,
+                        const float* psi, const float* C, int m, const int* m_eff_dev,
+                        float* phi, float* psi_next, int* err, OdeimNorms norms,
+                        cudaStream_t s) {
   cudaFuncSetAttribute(k_form_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   int64_t tiles = (N + kRows - 1) / kRows;
   const int grid = (int)(tiles < 152 ? tiles : 152);
-  k_form_phi_tc<<<grid, kThreads, kSmemBytes, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,
-                                                         phi, psi_next, err, norms);
+  // the ring as a 2D tensor: rows (contiguous, N) x slots (stride 4 N bytes),
+  // boxes of kRows x kChunk; the per-slot copies serve if it cannot be made
+  CUtensorMap tmap;
+  int use_tma = 0;
+  if (PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder()) {
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)nslot};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kRows, (cuuint32_t)kChunk};
+    const cuuint32_t estr[2] = {1, 1};
+    use_tma = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ring), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  if (!use_tma) memset(&tmap, 0, sizeof(tmap));
+  k_form_phi_tc<<<grid, kThreads, kSmemBytes, HY_S(s)>>>(tmap, use_tma, ring, N, win, w, psi, C,
+                                                         m, m_eff_dev, phi, psi_next, err, norms);
 }
 
 }  // namespace hy

@@ -101,9 +101,10 @@ struct OdeimNorms {
 // timed out.  With norms.nrm != NULL the epilogue also forms ODEIM's
 // row-norm data for the new Phi.
 bool form_phi_tc_ok(int64_t N, int w, int m);
-void launch_form_phi_tc(const float* ring, int64_t N, const int* win, int w, const float* psi,
-                        const float* C, int m, const int* m_eff_dev, float* phi,
-                        float* psi_next, int* err, OdeimNorms norms, cudaStream_t s);
+void launch_form_phi_tc(const float* ring, int64_t N, int nslot, const int* win, int w,
+                        const float* psi, const float* C, int m, const int* m_eff_dev,
+                        float* phi, float* psi_next, int* err, OdeimNorms norms,
+                        cudaStream_t s);
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
                 int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
