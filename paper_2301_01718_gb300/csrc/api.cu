@@ -115,6 +115,9 @@ struct hyrom_ctx {
   bool norms_ready = false;
   // the rebuild's DEIM and oversampling loops as CUDA graphs
   hy::OdeimGraphs od_graphs;
+  // the filter's passes as a CUDA graph, and their per-call arguments
+  hy::GraphSlot filt_graph;
+  void* fargs = nullptr;
   // pinned host mirror for read-backs
   void* host = nullptr;
   // optional per-stage CUDA-event timers (hyrom_profile): up to kEvPairs
@@ -417,7 +420,8 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     if (cf.n_filt > 0)
       hy::launch_filter_sparse<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp,
                                   k, (T*)ctx->fg, ctx->kbits, ctx->ftiles_a, ctx->ftiles_b,
-                                  ctx->fcounts, ctx->fpart, ctx->fctl, ctx->st);
+                                  ctx->fcounts, ctx->fpart, ctx->fctl, ctx->fargs,
+                                  &ctx->filt_graph, ctx->st);
     t_end(ctx, HYROM_T_FILTER);
   }
   CKL();
@@ -787,6 +791,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->X, ctx->f32 ? (size_t)N * sizeof(double) : (size_t)N * wp * sizeof(double));
   ok &= dal(ctx, &ctx->rawpart, 152 * 4 * sizeof(double));
   ok &= dal(ctx, &ctx->rotated, 64);
+  ok &= dalloc(ctx, &ctx->fargs, 64);
   if (ok) ok &= cudaMemsetAsync(ctx->rotated, 0, 64, ctx->st) == cudaSuccess;
   ok &= dal(ctx, &ctx->ident, (size_t)wp * wp * sizeof(double));
   ok &= dalloc(ctx, &ctx->od_ws, hy::odeim_ws_bytes(N, m));
@@ -827,6 +832,7 @@ void hyrom_destroy(hyrom_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   hy::odeim_graphs_free(&ctx->od_graphs);
+  hy::graph_slot_free(&ctx->filt_graph);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host) cudaFreeHost(ctx->host);
   for (int i = 0; i < HYROM_NSTAGE; ++i) {
@@ -1131,12 +1137,14 @@ hyrom_status hyrom_stage_filter(hyrom_ctx* ctx, void* q_io, const void* q_prev, 
       hy::launch_filter_sparse<float>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
                                       (float*)q_io, (const float*)q_prev, k, (float*)ctx->fg,
                                       ctx->kbits, ctx->ftiles_a, ctx->ftiles_b, ctx->fcounts,
-                                      ctx->fpart, ctx->fctl, ctx->st);
+                                      ctx->fpart, ctx->fctl, ctx->fargs, &ctx->filt_graph,
+                                      ctx->st);
     else
       hy::launch_filter_sparse<double>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f,
                                        (double*)q_io, (const double*)q_prev, k, (double*)ctx->fg,
                                        ctx->kbits, ctx->ftiles_a, ctx->ftiles_b, ctx->fcounts,
-                                       ctx->fpart, ctx->fctl, ctx->st);
+                                       ctx->fpart, ctx->fctl, ctx->fargs, &ctx->filt_graph,
+                                       ctx->st);
   }
   CKL();
   int* hi = (int*)ctx->host;

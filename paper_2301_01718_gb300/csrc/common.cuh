@@ -20,8 +20,6 @@ namespace hy {
 // Kernel-launch counter: every launch passes its stream through HY_S(), a
 // comma expression that counts the launch (for the benchmark's report).
 void count_launch();
-void add_launches(unsigned long long n);  // kernels of a replayed graph
-unsigned long long launch_count();
 #define HY_S(stream) (::hy::count_launch(), (stream))
 
 constexpr int kMaxVar = 4;

@@ -195,9 +195,25 @@ HY_DEV void nb_value(const DevCfg& c, const T* sm, int stride_v, int pos, int gi
   for (int a = 0; a < NV; ++a) out[a] = sm[a * stride_v + pos];
 }
 
+// The per-call arguments of the passes (the state filtered in place, the
+// previous state, the time), read from device memory so that one captured
+// graph of the whole filter serves every call.
+template <typename T>
+struct FiltArgs {
+  T* q;
+  const T* qp;
+  double t;
+};
+
+template <typename T>
+__global__ void k_set_filt_args(FiltArgs<T>* fa, T* q, const T* qp, double t) {
+  fa->q = q;
+  fa->qp = qp;
+  fa->t = t;
+}
+
 template <typename T, int NV, int NF, int TX, int TY>
-__global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const T* __restrict__ q,
-                                                     const T* __restrict__ qp, double t,
+__global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs<T>* __restrict__ fa,
                                                      T* __restrict__ gbuf, uint32_t* __restrict__ kbits,
                                                      const int* __restrict__ tiles,
                                                      const int* __restrict__ ntiles_dev,
@@ -213,6 +229,9 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const T* __res
   T* fx = qs + NV * SY * SX;
   T* gs = fx + NV * FY * FX;
   if (*done) return;
+  const T* __restrict__ q = fa->q;
+  const T* __restrict__ qp = fa->qp;
+  const double t = fa->t;
   const int tiles_x = (c.nx + TX - 1) / TX;
   const int ntiles = tiles ? *ntiles_dev : ntiles_all;
   const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
@@ -359,12 +378,13 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const T* __res
 
 // q = g on the kept cells of the listed tiles
 template <typename T>
-__global__ void k_filter_apply(DevCfg c, T* __restrict__ q, const T* __restrict__ gbuf,
+__global__ void k_filter_apply(DevCfg c, const FiltArgs<T>* __restrict__ fa, const T* __restrict__ gbuf,
                                const uint32_t* __restrict__ kbits, int TX, int TY,
                                const int* __restrict__ tiles, const int* __restrict__ ntiles_dev,
                                int ntiles_all) {
   const int tiles_x = (c.nx + TX - 1) / TX;
   const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  T* __restrict__ q = fa->q;
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const int tile = tiles ? tiles[it] : it;
     const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
@@ -458,12 +478,42 @@ template <typename T>
 void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
                           double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
                           int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
-                          cudaStream_t s) {
+                          void* fargs, GraphSlot* graph, cudaStream_t s) {
   const bool twoD = c.ny > 1;
   const int TX = twoD ? 32 : 256, TY = twoD ? 8 : 1;
   const int nt = ((c.nx + TX - 1) / TX) * ((c.ny + TY - 1) / TY);
   const int64_t nwords = (c.nc + 31) / 32;
-  const double t = (double)k * c.dt;
+  FiltArgs<T>* fa = reinterpret_cast<FiltArgs<T>*>(fargs);
+  // shared-memory limits of the pass kernels, set outside any capture
+  for (int o = 0; o < norders; ++o) {
+    const int n = orders[o];
+#define HY_FA(NV, NN, TXX, TYY)                                                              \
+  do {                                                                                       \
+    constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
+    constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
+    constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
+    cudaFuncSetAttribute(k_filter_pass<T, NV, NN, TXX, TYY>,                                 \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_);             \
+  } while (0)
+#define HY_FA_N(NV, TXX, TYY) \
+  do {                        \
+    if (n == 1)               \
+      HY_FA(NV, 1, TXX, TYY); \
+    else if (n == 2)          \
+      HY_FA(NV, 2, TXX, TYY); \
+    else                      \
+      HY_FA(NV, 3, TXX, TYY); \
+  } while (0)
+    if (c.nvar == 4) {
+      if (twoD) HY_FA_N(4, 32, 8); else HY_FA_N(4, 256, 1);
+    } else {
+      if (twoD) HY_FA_N(1, 32, 8); else HY_FA_N(1, 256, 1);
+    }
+#undef HY_FA_N
+#undef HY_FA
+  }
+  k_set_filt_args<T><<<1, 1, 0, HY_S(s)>>>(fa, q, qp, (double)k * c.dt);
+  auto body = [&]() {
   cudaMemsetAsync(ctl, 0, 3 * sizeof(int), s);
   for (int o = 0; o < norders; ++o) {
     const int n = orders[o];
@@ -480,10 +530,8 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
     constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
     constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
-    cudaFuncSetAttribute(k_filter_pass<T, NV, NN, TXX, TYY>,                                 \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_);             \
     k_filter_pass<T, NV, NN, TXX, TYY><<<grid, 256, sm_, HY_S(s)>>>(                         \
-        c, q, qp, t, gbuf, kbits, cur, cur_n, nt, part, ctl);                                \
+        c, fa, gbuf, kbits, cur, cur_n, nt, part, ctl);                                      \
   } while (0)
 #define HY_FP_N(NV, TXX, TYY) \
   do {                        \
@@ -502,7 +550,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
 #undef HY_FP_N
 #undef HY_FP
       k_gate_finalize<<<1, 256, 0, HY_S(s)>>>(part, grid, eps_f, ctl);
-      k_filter_apply<T><<<cur ? 152 * 8 : grid, 256, 0, HY_S(s)>>>(c, q, gbuf, kbits, TX, TY, cur,
+      k_filter_apply<T><<<cur ? 152 * 8 : grid, 256, 0, HY_S(s)>>>(c, fa, gbuf, kbits, TX, TY, cur,
                                                                    cur_n, nt);
       if (pass + 1 < jmax_f) {
         cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
@@ -516,6 +564,11 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
       }
     }
   }
+  };
+  if (graph)
+    run_graphed(graph, s, body);
+  else
+    body();
 }
 
 template void launch_filter<float>(const DevCfg&, const int*, int, int, double, float*,
@@ -523,10 +576,10 @@ template void launch_filter<float>(const DevCfg&, const int*, int, int, double, 
                                    int*, cudaStream_t);
 template void launch_filter_sparse<float>(const DevCfg&, const int*, int, int, double, float*,
                                           const float*, int64_t, float*, uint32_t*, int*, int*,
-                                          int*, double*, int*, cudaStream_t);
+                                          int*, double*, int*, void*, GraphSlot*, cudaStream_t);
 template void launch_filter_sparse<double>(const DevCfg&, const int*, int, int, double, double*,
                                            const double*, int64_t, double*, uint32_t*, int*, int*,
-                                           int*, double*, int*, cudaStream_t);
+                                           int*, double*, int*, void*, GraphSlot*, cudaStream_t);
 template void launch_filter<double>(const DevCfg&, const int*, int, int, double, double*,
                                     const double*, int64_t, double*, double*, double*, double*,
                                     double*, int*, cudaStream_t);

@@ -8,6 +8,58 @@ namespace hy {
 
 struct DevCfg;
 
+// Kernel-launch counter (api.cu): kernels of a replayed graph are added.
+unsigned long long launch_count();
+void add_launches(unsigned long long n);
+
+// A stream's work kept as a CUDA graph: captured at the first run, replayed
+// after.  Whatever the work bakes in (pointers, sizes) must be the same on
+// every run.  Launch counts: the launches made while capturing stand for the
+// first replay, later replays add `launches`.
+struct GraphSlot {
+  void* exec = nullptr;  // cudaGraphExec_t
+  unsigned long long launches = 0;
+};
+inline void graph_slot_free(GraphSlot* g) {
+  if (g->exec) cudaGraphExecDestroy((cudaGraphExec_t)g->exec);
+  g->exec = nullptr;
+  g->launches = 0;
+}
+// Run `body` (stream work only, no synchronisation) on s: replay the slot's
+// graph, or capture body into it and launch that; if the stream cannot be
+// captured (the legacy default stream), run body directly.
+template <typename F>
+void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
+  if (g->exec) {
+    cudaGraphLaunch((cudaGraphExec_t)g->exec, s);
+    add_launches(g->launches);
+    return;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+      cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    body();
+    return;
+  }
+  const unsigned long long before = launch_count();
+  body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  const unsigned long long n = launch_count() - before;
+  cudaGraphExec_t ge = nullptr;
+  if (e != cudaSuccess || !graph || cudaGraphInstantiate(&ge, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    body();  // the captured work did not run
+    return;
+  }
+  cudaGraphDestroy(graph);
+  g->exec = (void*)ge;
+  g->launches = n;
+  cudaGraphLaunch(ge, s);
+}
+
 // hdm.cu
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
@@ -39,11 +91,14 @@ void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, 
                    T* q, const T* qp, int64_t k, T* g, T* tmp, T* rho_old, T* rho_new,
                    double* part, int* ctl, cudaStream_t s);
 
+// fargs: device memory (64 bytes) for the per-call arguments; graph
+// (nullable): the passes kept as one CUDA graph (the other arguments must
+// then be the same on every call)
 template <typename T>
 void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
                           double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
                           int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
-                          cudaStream_t s);
+                          void* fargs, GraphSlot* graph, cudaStream_t s);
 
 // rom.cu
 template <typename T>
@@ -155,11 +210,9 @@ int launch_sample_gram_tc(const float* phi, int64_t N, int m, const int* cells, 
 // the arguments baked into them (phi, pts, ws, tie_tol) must then be the
 // same on every call.  Inside a replayed loop no sub-stage marks are made.
 struct OdeimGraphs {
-  void* deim = nullptr;  // cudaGraphExec_t
-  void* over = nullptr;
+  GraphSlot deim, over;
   int64_t N = -1;
   int m = -1, np = -1;
-  unsigned long long deim_launches = 0, over_launches = 0;
 };
 void odeim_graphs_free(OdeimGraphs* g);
 OdeimNorms odeim_norm_bufs(void* ws, int64_t N);

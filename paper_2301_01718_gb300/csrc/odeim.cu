@@ -1598,47 +1598,10 @@ OdeimNorms odeim_norm_bufs(void* ws, int64_t N) {
 }
 
 void odeim_graphs_free(OdeimGraphs* g) {
-  if (g->deim) cudaGraphExecDestroy((cudaGraphExec_t)g->deim);
-  if (g->over) cudaGraphExecDestroy((cudaGraphExec_t)g->over);
-  g->deim = g->over = nullptr;
+  graph_slot_free(&g->deim);
+  graph_slot_free(&g->over);
   g->N = -1;
   g->m = g->np = -1;
-}
-
-// Run `body` (stream work only, no synchronisation) on s: replay the graph in
-// *exec, or capture body into it and launch that; if the stream cannot be
-// captured, run body directly.  Launch counts: the launches made while
-// capturing stand for the first replay, later replays add *nlaunch.
-template <typename F>
-static void run_graphed(void** exec, unsigned long long* nlaunch, cudaStream_t s, F body) {
-  if (*exec) {
-    cudaGraphLaunch((cudaGraphExec_t)*exec, s);
-    add_launches(*nlaunch);
-    return;
-  }
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
-      cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaGetLastError();
-    body();
-    return;
-  }
-  const unsigned long long before = launch_count();
-  body();
-  cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(s, &g);
-  const unsigned long long n = launch_count() - before;
-  cudaGraphExec_t ge = nullptr;
-  if (e != cudaSuccess || !g || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
-    cudaGetLastError();
-    if (g) cudaGraphDestroy(g);
-    body();  // the captured work did not run
-    return;
-  }
-  cudaGraphDestroy(g);
-  *exec = (void*)ge;
-  *nlaunch = n;
-  cudaGraphLaunch(ge, s);
 }
 
 template <typename T>
@@ -1692,7 +1655,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   }
   };
   if (graphs)
-    run_graphed(&graphs->deim, &graphs->deim_launches, s, deim_loop);
+    run_graphed(&graphs->deim, s, deim_loop);
   else
     deim_loop();
   if (mark) {  // DEIM ends, oversampling begins
@@ -1769,7 +1732,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   }
   };
   if (graphs)
-    run_graphed(&graphs->over, &graphs->over_launches, s, over_loop);
+    run_graphed(&graphs->over, s, over_loop);
   else
     over_loop();
   return 0;
