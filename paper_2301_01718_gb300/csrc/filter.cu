@@ -40,87 +40,6 @@ struct Shapiro<3> {
   }
 };
 
-// One direction (AX = 0: x, AX = 1: y) of the order-2n filter for every dof.
-template <typename T, int N_, int AX>
-__global__ void k_shapiro(DevCfg c, const T* __restrict__ in, T* __restrict__ out,
-                          const int* __restrict__ done) {
-  if (done && *done) return;
-  const bool per = AX == 0 ? c.bc[0] == HYROM_BC_PERIODIC : c.bc[2] == HYROM_BC_PERIODIC;
-  const int L = AX == 0 ? c.nx : c.ny;
-  const T scale = (T)(N_ == 1 ? 0.25 : (N_ == 2 ? 0.0625 : 0.015625));
-  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < c.ndof;
-       d += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = d / c.nc, cell = d % c.nc;
-    const int i = (int)(cell % c.nx), j = (int)(cell / c.nx);
-    const int pos = AX == 0 ? i : j;
-    const T* base = in + v * c.nc;
-    T acc = (T)0;
-#pragma unroll
-    for (int t = 0; t < Shapiro<N_>::W; ++t) {
-      int p = pos + t - N_;
-      if (per)
-        p = imod(p, L);
-      else
-        p = p < 0 ? 0 : (p >= L ? L - 1 : p);
-      const T x = AX == 0 ? base[(int64_t)j * c.nx + p] : base[(int64_t)p * c.nx + i];
-      const double wt = Shapiro<N_>::w(t);
-      const T term = wt == 1.0 ? x : (wt == -1.0 ? -x : (T)wt * x);
-      acc = t == 0 ? term : acc + term;
-    }
-    out[d] = acc * scale;
-  }
-}
-
-template <typename T>
-void launch_shapiro(const DevCfg& c, int n, const T* in, T* tmp, T* out, const int* done,
-                    cudaStream_t s) {
-  int64_t blocks = (c.ndof + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  const bool twoD = c.ny > 1;
-  T* xdst = twoD ? tmp : out;
-#define HY_SH(NN)                                                                  \
-  do {                                                                             \
-    k_shapiro<T, NN, 0><<<(int)blocks, 256, 0, HY_S(s)>>>(c, in, xdst, done);            \
-    if (twoD) k_shapiro<T, NN, 1><<<(int)blocks, 256, 0, HY_S(s)>>>(c, tmp, out, done);  \
-  } while (0)
-  if (n == 1)
-    HY_SH(1);
-  else if (n == 2)
-    HY_SH(2);
-  else
-    HY_SH(3);
-#undef HY_SH
-}
-
-// Gate: keep the filtered value where rho_new < rho_old; per-block partial
-// (kept count, sum of decreases, sum of old values) for a fixed-order
-// reduction.
-template <typename T>
-__global__ void k_gate(int64_t nc, int nvar, T* __restrict__ q, const T* __restrict__ g,
-                       const T* __restrict__ rho_old, const T* __restrict__ rho_new,
-                       double* __restrict__ part, const int* __restrict__ done) {
-  if (*done) return;
-  double cnt = 0.0, dec = 0.0, tot = 0.0;
-  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < nc;
-       cell += (int64_t)gridDim.x * blockDim.x) {
-    const T ro = rho_old[cell], rn = rho_new[cell];
-    if (rn < ro) {
-      for (int v = 0; v < nvar; ++v) q[v * nc + cell] = g[v * nc + cell];
-      cnt += 1.0;
-      dec += (double)(ro - rn);
-      tot += (double)ro;
-    }
-  }
-  cnt = block_sum(cnt);
-  dec = block_sum(dec);
-  tot = block_sum(tot);
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x] = cnt;
-    part[3 * blockIdx.x + 1] = dec;
-    part[3 * blockIdx.x + 2] = tot;
-  }
-}
-
 // ctl[0] = done, ctl[1] = passes run, ctl[2] = cells kept (running total)
 __global__ void k_gate_finalize(const double* __restrict__ part, int nblk, double eps_f,
                                 int* ctl) {
@@ -143,33 +62,14 @@ __global__ void k_gate_finalize(const double* __restrict__ part, int nblk, doubl
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
-template <typename T>
-void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, double eps_f,
-                   T* q, const T* qp, int64_t k, T* g, T* tmp, T* rho_old, T* rho_new,
-                   double* part, int* ctl, cudaStream_t s) {
-  const int nblk = 152 * 4;
-  cudaMemsetAsync(ctl, 0, 3 * sizeof(int), s);
-  for (int o = 0; o < norders; ++o) {
-    k_set_int<<<1, 1, 0, HY_S(s)>>>(ctl, 0);
-    launch_cell_residual_skip<T>(c, q, qp, k, rho_old, ctl, s);
-    for (int pass = 0; pass < jmax_f; ++pass) {
-      launch_shapiro<T>(c, orders[o], q, tmp, g, ctl, s);
-      launch_cell_residual_skip<T>(c, g, qp, k, rho_new, ctl, s);
-      k_gate<T><<<nblk, 256, 0, HY_S(s)>>>(c.nc, c.nvar, q, g, rho_old, rho_new, part, ctl);
-      k_gate_finalize<<<1, 256, 0, HY_S(s)>>>(part, nblk, eps_f, ctl);
-      if (pass + 1 < jmax_f) launch_cell_residual_skip<T>(c, q, qp, k, rho_old, ctl, s);
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // fused, sparse filter pass
 //
 // One kernel per pass computes, for every cell of a tile, rho_old = rho(q),
 // the filtered state g = F_y(F_x(q)) and rho_new = rho(g) in shared memory
 // and takes the gate decision; kept cells get g in gbuf and a bit in kbits.
-// The values are those of the separate kernels above (same expressions, same
-// order), so FP64 results are identical.  After the first pass of an order,
+// The filter is the two one-dimensional sweeps (x, then y) with the weights
+// above, evaluated in that order.  After the first pass of an order,
 // q has changed only on the kept cells K, so g can change only within
 // distance n of K and rho_old / rho_new only within distance n + 1: every
 // other cell keeps its previous decision ("not kept").  The next pass
@@ -571,17 +471,11 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     body();
 }
 
-template void launch_filter<float>(const DevCfg&, const int*, int, int, double, float*,
-                                   const float*, int64_t, float*, float*, float*, float*, double*,
-                                   int*, cudaStream_t);
 template void launch_filter_sparse<float>(const DevCfg&, const int*, int, int, double, float*,
                                           const float*, int64_t, float*, uint32_t*, int*, int*,
                                           int*, double*, int*, void*, GraphSlot*, cudaStream_t);
 template void launch_filter_sparse<double>(const DevCfg&, const int*, int, int, double, double*,
                                            const double*, int64_t, double*, uint32_t*, int*, int*,
                                            int*, double*, int*, void*, GraphSlot*, cudaStream_t);
-template void launch_filter<double>(const DevCfg&, const int*, int, int, double, double*,
-                                    const double*, int64_t, double*, double*, double*, double*,
-                                    double*, int*, cudaStream_t);
 
 }  // namespace hy

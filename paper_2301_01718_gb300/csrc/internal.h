@@ -83,14 +83,6 @@ void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
                                    cudaStream_t s);
 
 // filter.cu
-template <typename T>
-void launch_shapiro(const DevCfg& c, int n, const T* in, T* tmp, T* out, const int* done,
-                    cudaStream_t s);
-template <typename T>
-void launch_filter(const DevCfg& c, const int* orders, int norders, int jmax_f, double eps_f,
-                   T* q, const T* qp, int64_t k, T* g, T* tmp, T* rho_old, T* rho_new,
-                   double* part, int* ctl, cudaStream_t s);
-
 // fargs: device memory (64 bytes) for the per-call arguments; graph
 // (nullable): the passes kept as one CUDA graph (the other arguments must
 // then be the same on every call)

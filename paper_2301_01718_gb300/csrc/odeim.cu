@@ -420,17 +420,6 @@ __global__ void __launch_bounds__(256) k_odeim_gram(const T* __restrict__ phi, i
   }
 }
 
-// M += phi_p phi_p^T for the point just chosen
-template <typename T>
-__global__ void k_odeim_rank1(const T* __restrict__ phi, int64_t N, int m, const OdCtl* ctl,
-                              double* __restrict__ M) {
-  const int p = ctl->argmin;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int a = idx / m, b = idx % m;
-    M[idx] = fma((double)phi[(int64_t)a * N + p], (double)phi[(int64_t)b * N + p], M[idx]);
-  }
-}
-
 // sort the Jacobi eigenpairs ascending: lam_s, W_s (m x m column-major);
 // reset the step's control block
 // The screens read the eigensystem in FP32, written once per step where it

@@ -746,64 +746,6 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
   for (int i = tid; i < n; i += nt) piv_out[i] = piv[i];
 }
 
-// One sweep (r' - 1 rounds, r' = r rounded up to even) of one-sided Jacobi
-// on the columns of B in one cooperative launch; CTA b rotates pair b of the
-// round in place (pairs of a round are disjoint).
-__global__ void k_osj_sweep(double* B, int n, const int* __restrict__ rank, double tol,
-                            int* rotated, GridBar* bar, int* err) {
-  __shared__ double cp[kEigMaxN], cq[kEigMaxN];
-  __shared__ double red[3][32];
-  const int r = *rank, rp = (r + 1) & ~1;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (int rd = 0; rd < rp - 1; ++rd) {
-    if ((int)blockIdx.x < rp / 2) {
-      int p, q;
-      rr_pair(rp, rd, blockIdx.x, p, q);
-      if (q < r) {
-        double a = 0.0, c = 0.0, g = 0.0;
-        for (int i = tid; i < n; i += blockDim.x) {
-          const double x = __ldcg(B + (int64_t)p * n + i), y = __ldcg(B + (int64_t)q * n + i);
-          cp[i] = x;
-          cq[i] = y;
-          a = fma(x, x, a);
-          c = fma(y, y, c);
-          g = fma(x, y, g);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          c += __shfl_xor_sync(0xffffffffu, c, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        if (lane == 0) {
-          red[0][wid] = a;
-          red[1][wid] = c;
-          red[2][wid] = g;
-        }
-        __syncthreads();
-        a = red[0][0];
-        c = red[1][0];
-        g = red[2][0];
-        for (int w2 = 1; w2 < nw; ++w2) {
-          a += red[0][w2];
-          c += red[1][w2];
-          g += red[2][w2];
-        }
-        if (fabs(g) > tol * sqrt(a * c) && a > 0.0 && c > 0.0) {
-          const double zeta = (c - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int i = tid; i < n; i += blockDim.x) {
-            B[(int64_t)p * n + i] = cs * cp[i] - sn * cq[i];
-            B[(int64_t)q * n + i] = sn * cp[i] + cs * cq[i];
-          }
-          if (tid == 0) *rotated = 1;
-        }
-      }
-    }
-    if (!grid_sync_bounded(bar, gridDim.x, err)) return;
-  }
-}
-
 // One-sided Jacobi on the columns of B (n <= 128), all sweeps in one launch
 // of one thread-block cluster of C = ceil(n / 8) CTAs, by blocks: the
 // columns form nb = 2 C blocks of four, block j held in CTA j % C (slot
