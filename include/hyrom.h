@@ -288,6 +288,18 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
 hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
                                int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
 
+/* ---- diagnostics -----------------------------------------------------------
+ * hyrom_selftest_math: the library's own FP64 reciprocal (which = 0: 1 / x
+ * from an FP32 seed and two Newton steps, used where an FP64 division would
+ * sit on a dependent chain) and reciprocal square root (which = 1: 1 /
+ * sqrt(x), x > 0, likewise) applied to n doubles x (device) into y (device),
+ * so that tests can hold them against CUDA's division and square root.
+ * Enqueued on `stream` (NULL = legacy default); does not synchronise.
+ * Errors: HYROM_EINVAL (null pointer, n < 0, which not 0 or 1),
+ * HYROM_ECUDA (launch). */
+hyrom_status hyrom_selftest_math(int32_t which, const double* x, double* y, int64_t n,
+                                 void* stream);
+
 /* ---- allocation-free variant ---------------------------------------------
  * hyrom_gappy_static: the gappy reduced coordinates of hyrom_stage_gappy,
  * y = (P^T Phi)^+ P^T (v - psi) (Algorithm 1, the gappy least-squares step),

@@ -120,6 +120,18 @@ HY_DEV double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// 1 / sqrt(a) for a > 0 in FP64 from an FP32 seed and two Newton steps
+// y <- y (3/2 - a y^2 / 2) (about an ulp), in place of an FP64 square root
+// and division; the FP64 square root and division outside the FP32 range.
+HY_DEV double rsqrt64(double a) {
+  const float af = (float)a;
+  if (!(af >= 1.17549435e-38f && af <= 1.7e38f)) return 1.0 / sqrt(a);
+  double y = (double)rsqrtf(af);
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  return y;
+}
+
 // Bucket of a row's squared-norm bound v among 256 (ratio 2^(1/4) per
 // bucket, bucket 255 for v = 0): the order ODEIM scans rows in.
 constexpr int kNormBuckets = 256;

@@ -207,9 +207,7 @@ __global__ void __launch_bounds__(256, 1) k_sample_chol(const double* __restrict
       piv[1] = 0.0;
       return;
     }
-    double y = (double)rsqrtf((float)x);
-    y = y * fma(-0.5 * x * y, y, 1.5);
-    y = y * fma(-0.5 * x * y, y, 1.5);
+    const double y = rsqrt64(x);
     piv[0] = x * y;
     piv[1] = y;
   };

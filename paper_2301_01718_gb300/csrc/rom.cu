@@ -717,9 +717,7 @@ __global__ void __launch_bounds__(1024) k_pchol(const double* __restrict__ G, in
     }
     if (tid == 0) {  // sqrt and 1 / sqrt from an FP32 seed and two Newton steps
       const double a = A[k * n + k];
-      double y = (double)rsqrtf((float)a);
-      y = y * fma(-0.5 * a * y, y, 1.5);
-      y = y * fma(-0.5 * a * y, y, 1.5);
+      const double y = rsqrt64(a);
       rk_s[0] = a * y;
       rk_s[1] = y;
     }

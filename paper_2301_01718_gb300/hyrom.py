@@ -136,6 +136,7 @@ def lib():
         "hyrom_stage_masks": (st, [vp, vp, vp, i32, vp, vp, C.POINTER(i32)]),
         "hyrom_stage_gappy_rows": (st, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
+        "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -319,3 +320,11 @@ def hyrom_gappy_static(phi, ndof, m, points, n_p, v, psi, precision, y_out, stre
                                  len(err))
     if s != HYROM_OK:
         raise HyromError(s, err.value.decode())
+
+
+def hyrom_selftest_math(which, x, y, stream=None):
+    """The library's FP64 reciprocal (which=0) or reciprocal square root
+    (which=1) of the device doubles x into y, on `stream`."""
+    s = lib().hyrom_selftest_math(int(which), _ptr(x), _ptr(y), int(x.numel()), _ptr(stream))
+    if s != HYROM_OK:
+        raise HyromError(s, "hyrom_selftest_math")
