@@ -14,7 +14,9 @@ Metric: hybrid steps per second (whole job: summed over replicas).  Also
 reported: sampled cell-updates/s, per-stage milliseconds from CUDA events
 on the library stream, the roofline of the dominant bandwidth kernel,
 FP32-vs-FP64 error on a reduced grid, the end-to-end rate through host
-buffers, and the CPU oracle on a bounded sample.
+buffers, the precision form (the sample-row normal matrix in each
+precision), the batching form (64 uneven instances stepped one at a time
+and by a pool of host threads), and the CPU oracle on a bounded sample.
 
 --impl reference runs the CPU oracle instead (the only reference this
 method has: the paper ships no code).
@@ -61,7 +63,13 @@ def parse():
     p.add_argument("--no-precision-form", action="store_true")
     p.add_argument("--precision-steps", type=int, default=4,
                    help="timed steps per variant of the precision form")
-    p.add_argument("--micro", choices=["sample_gram"], default=None,
+    p.add_argument("--no-batch-form", action="store_true")
+    p.add_argument("--batch-n", type=int, default=64, help="instances of the batching form")
+    p.add_argument("--batch-steps", type=int, default=3,
+                   help="timed hybrid steps per instance in each batching-form arm")
+    p.add_argument("--batch-threads", default="1,4,8,16",
+                   help="host-thread counts timed in the batching form (1 = one at a time)")
+    p.add_argument("--micro", choices=["sample_gram", "batch"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
     return p.parse_args()
@@ -316,6 +324,8 @@ def run_ours(a):
         out["err_vs_fp64"] = err_vs_fp64(a)
     if rank == 0 and not a.no_precision_form:
         out["precision_form"] = precision_form(a)
+    if rank == 0 and not a.no_batch_form:
+        out["batch_form"] = batch_form(a)
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(a)
     if world > 1:
@@ -465,6 +475,67 @@ def micro_sample_gram(a, m=64, calls=10):
             "rows": rows, "sample": "every other cell", "calls": calls, "variants": out}
 
 
+def batch_form(a):
+    """The batching form: a.batch_n independent Euler instances
+    (workloads.euler_batch: grids log-uniform 128^2..1024^2, Mach 0.3..2,
+    own basis k 8..48 and sample fraction 2..20 % each), every context on its
+    own stream, stepped by hyrom_batch_step with 1 host thread (the instances
+    one at a time) and with more threads (up to that many instances on the
+    GPU at once).  Each arm times a.batch_steps hybrid steps of every
+    instance, host clock around the synchronised call; rates are instance
+    hybrid steps/s and dof-steps/s (dofs advanced per second)."""
+    import torch
+    from paper_2301_01718_gb300 import build, hyrom
+    build.build()
+    insts = W.euler_batch(n_inst=a.batch_n, seed=5)
+    ctxs, streams = [], []
+    dofs = sum(c.ndof for _, c in insts)
+    try:
+        for q0, cfg in insts:
+            st = torch.cuda.Stream()
+            q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+            ctxs.append(hyrom.hyrom_init(cfg, q0d, stream=st.cuda_stream))
+            streams.append(st)
+            del q0d
+        dev_bytes = sum(hyrom.hyrom_device_bytes(c) for c in ctxs)
+        # each instance's own warm-up (w full steps and the first rebuild)
+        for c in ctxs:
+            while hyrom.hyrom_step(c)["was_full"]:
+                pass
+        arms = {}
+        for t in [int(x) for x in str(a.batch_threads).split(",") if x]:
+            b = hyrom.hyrom_batch_create(ctxs, threads=t)
+            try:
+                hyrom.hyrom_batch_step(b, len(ctxs), nsteps=1)     # warm-up
+                torch.cuda.synchronize()
+                l0 = hyrom.hyrom_kernel_launches()
+                t0 = time.perf_counter()
+                _, infos = hyrom.hyrom_batch_step(b, len(ctxs), nsteps=a.batch_steps)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                launches = hyrom.hyrom_kernel_launches() - l0
+                threads = hyrom.hyrom_batch_threads(b)
+            finally:
+                hyrom.hyrom_batch_destroy(b)
+            assert all(not i["was_full"] for i in infos)
+            steps = a.batch_steps * len(ctxs)
+            arms[str(threads)] = {"ms": el * 1e3, "instance_steps_per_s": steps / el,
+                                  "dof_steps_per_s": dofs * a.batch_steps / el,
+                                  "gpu_launches": int(launches)}
+    finally:
+        for c in ctxs:
+            hyrom.hyrom_destroy(c)
+    one = arms.get("1")
+    best = max(arms.values(), key=lambda r: r["instance_steps_per_s"])
+    return {"workload": f"{len(insts)} Euler vortex instances, grids 128^2..1024^2 "
+                        "log-uniform, Mach 0.3..2, k 8..48 (w = n_p = 2k), sample 2..20 %, FP32",
+            "instances": len(insts), "dofs": dofs, "device_bytes": dev_bytes,
+            "steps_per_instance": a.batch_steps, "unit": "instance hybrid steps/s",
+            "threads": arms,
+            "speedup_vs_one_at_a_time": (best["instance_steps_per_s"] /
+                                         one["instance_steps_per_s"]) if one else None}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -489,6 +560,8 @@ def main():
     a = parse()
     if a.micro == "sample_gram":
         out = micro_sample_gram(a)
+    elif a.micro == "batch":
+        out = {"micro": "batch", **batch_form(a)}
     else:
         out = run_reference(a) if a.impl == "reference" else run_ours(a)
     if out is not None:

@@ -288,6 +288,33 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
 hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
                                int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
 
+/* ---- batching form ---------------------------------------------------------
+ * Many independent instances of Algorithm 1 (each its own context, grid,
+ * basis size, window and sample fraction) stepped together by a pool of host
+ * threads.  hyrom_batch_create takes n distinct contexts (the caller keeps
+ * them: they must outlive the batch and not be used by another thread while
+ * a batch call runs) and starts `threads` host threads (0: min(n, 16)).
+ * hyrom_batch_step runs `nsteps` calls of hyrom_step on every instance: each
+ * thread takes one instance at a time, largest device footprint first, and
+ * runs its steps on the instance's own stream, so up to `threads` instances
+ * are on the GPU at once.  An instance's steps stay in order and launch the
+ * same kernels as when it is stepped alone, so its results are the same bits.
+ * Contexts on one shared stream (or the legacy default stream) keep their
+ * results and lose the overlap.  infos (n entries, nullable) receives each
+ * instance's last step; status (n entries, nullable) each instance's first
+ * non-OK status; an instance stops at a failure other than HYROM_ENOTCONV.
+ * Returns when every instance is done (synchronised): HYROM_OK or the first
+ * failing instance's status (by index).  Errors of hyrom_batch_create:
+ * HYROM_EINVAL (n <= 0, threads < 0, a null or repeated context),
+ * HYROM_ENOMEM, HYROM_ECUDA. */
+typedef struct hyrom_batch hyrom_batch;
+hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, int32_t threads,
+                                hyrom_batch** out);
+hyrom_status hyrom_batch_step(hyrom_batch* batch, int32_t nsteps, hyrom_step_info* infos,
+                              int32_t* status);
+int32_t hyrom_batch_threads(const hyrom_batch* batch);
+void hyrom_batch_destroy(hyrom_batch* batch);
+
 /* ---- diagnostics -----------------------------------------------------------
  * hyrom_selftest_math: the library's own FP64 reciprocal (which = 0: 1 / x
  * from an FP32 seed and two Newton steps, used where an FP64 division would

@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -133,10 +134,20 @@ struct hyrom_ctx {
 };
 
 namespace hy {
-static unsigned long long g_launches = 0;
-void count_launch() { ++g_launches; }
-void add_launches(unsigned long long n) { g_launches += n; }
-unsigned long long launch_count() { return g_launches; }
+// process total (any thread) and this thread's own count (graph capture
+// attributes the launches it made to the graph it captured)
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local unsigned long long t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void add_launches(unsigned long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+unsigned long long thread_launch_count() { return t_launches; }
 }  // namespace hy
 
 static __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {

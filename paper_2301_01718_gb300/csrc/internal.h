@@ -9,7 +9,9 @@ namespace hy {
 struct DevCfg;
 
 // Kernel-launch counter (api.cu): kernels of a replayed graph are added.
+// launch_count: all threads; thread_launch_count: the calling thread's.
 unsigned long long launch_count();
+unsigned long long thread_launch_count();
 void add_launches(unsigned long long n);
 
 // A stream's work kept as a CUDA graph: captured at the first run, replayed
@@ -42,11 +44,11 @@ void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
     body();
     return;
   }
-  const unsigned long long before = launch_count();
+  const unsigned long long before = thread_launch_count();
   body();
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(s, &graph);
-  const unsigned long long n = launch_count() - before;
+  const unsigned long long n = thread_launch_count() - before;
   cudaGraphExec_t ge = nullptr;
   if (e != cudaSuccess || !graph || cudaGraphInstantiate(&ge, graph, 0) != cudaSuccess) {
     cudaGetLastError();

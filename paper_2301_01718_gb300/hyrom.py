@@ -137,6 +137,10 @@ def lib():
         "hyrom_stage_gappy_rows": (st, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
         "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
+        "hyrom_batch_create": (st, [C.POINTER(vp), i32, i32, C.POINTER(vp)]),
+        "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
+        "hyrom_batch_threads": (i32, [vp]),
+        "hyrom_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -328,3 +332,36 @@ def hyrom_selftest_math(which, x, y, stream=None):
     s = lib().hyrom_selftest_math(int(which), _ptr(x), _ptr(y), int(x.numel()), _ptr(stream))
     if s != HYROM_OK:
         raise HyromError(s, "hyrom_selftest_math")
+
+
+def hyrom_batch_create(ctxs, threads=0):
+    """A batch over the contexts `ctxs` (kept by the caller) stepped by
+    `threads` host threads (0: min(len(ctxs), 16))."""
+    n = len(ctxs)
+    arr = (C.c_void_p * max(n, 1))(*ctxs)
+    out = C.c_void_p()
+    s = lib().hyrom_batch_create(arr, int(n), int(threads), C.byref(out))
+    if s != HYROM_OK:
+        raise HyromError(s, "hyrom_batch_create")
+    return out.value
+
+
+def hyrom_batch_step(batch, n, nsteps=1):
+    """nsteps hybrid steps of each of the n instances.  Returns (status per
+    instance, info dict of each instance's last step); raises HyromError
+    with the failing instances' messages when any status is not OK."""
+    infos = (HyromStepInfo * n)()
+    st = (C.c_int32 * n)()
+    s = lib().hyrom_batch_step(batch, int(nsteps), infos, st)
+    status = list(st)
+    if s != HYROM_OK:
+        raise HyromError(s, f"instances {[i for i, v in enumerate(status) if v]} failed")
+    return status, [i.as_dict() for i in infos]
+
+
+def hyrom_batch_threads(batch):
+    return lib().hyrom_batch_threads(batch)
+
+
+def hyrom_batch_destroy(batch):
+    lib().hyrom_batch_destroy(batch)

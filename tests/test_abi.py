@@ -8,6 +8,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,3 +79,38 @@ def test_make_config_fills_every_field():
     assert list(c.shock_post) == list(cfg.shock_post)
     assert c.n_filt == 3 and list(c.filt_orders) == [1, 2, 3]
     assert c.pod_abs == cfg.pod_abs and c.tie_tol == cfg.tie_tol
+
+
+def test_batch_argument_checks_need_no_gpu(lib):
+    """The batch entry points reject bad arguments before any CUDA call."""
+    from paper_2301_01718_gb300 import hyrom
+    L = hyrom.lib()
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.hyrom_batch_create(arr, 0, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
+    assert L.hyrom_batch_create(arr, 2, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
+    assert L.hyrom_batch_create(None, 1, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
+    assert out.value is None
+    assert L.hyrom_batch_step(None, 1, None, None) == hyrom.HYROM_EINVAL
+    assert L.hyrom_batch_threads(None) == 0
+    L.hyrom_batch_destroy(None)
+
+
+def test_batch_workload_recipe():
+    """The batching form's instances: grids log-uniform in [128, 1024], k in
+    [8, 48] with w = n_p = 2k, sample fractions in [2 %, 20 %], Mach in
+    [0.3, 2.0]; reproducible from the seed."""
+    import workloads as W
+    a = W.euler_batch()
+    b = W.euler_batch()
+    assert len(a) == 64
+    for (qa, ca), (qb, cb) in zip(a[:4], b[:4]):
+        assert ca == cb and np.array_equal(qa, qb)
+    n = np.array([c.nx for _, c in a])
+    k = np.array([c.m for _, c in a])
+    assert n.min() >= 128 and n.max() <= 1024 and len(set(n)) > 40
+    assert k.min() >= 8 and k.max() <= 48 and len(set(k)) > 20
+    assert all(c.w == 2 * c.m and c.n_p == 2 * c.m and c.nx == c.ny for _, c in a)
+    assert all(0.02 <= c.top_frac <= 0.20 for _, c in a)
+    # log-uniform sides: about half the instances below sqrt(128 * 1024)
+    assert 20 <= (n < 362).sum() <= 44

@@ -156,11 +156,11 @@ def burgers_sine(n=1024, seed=1, steps=200, **kw):
     return u0.reshape(1, n), cfg, steps
 
 
-def euler_vortex(n=512, seed=2, steps=500, **kw):
+def euler_vortex(n=512, seed=2, steps=500, minf=0.5, **kw):
     """2D Euler on periodic [0,10]^2: isentropic vortex (strength 5, centre
-    (5,5)) advected at Mach 0.5 along the diagonal, plus a Gaussian density
-    pulse of amplitude 0.2 and radius 0.5 at a seeded point of [2,8]^2 with
-    the pressure unchanged.  CFL 0.5, k = 20, w = 40, 5 % sample.
+    (5,5)) advected at Mach `minf` (0.5) along the diagonal, plus a Gaussian
+    density pulse of amplitude 0.2 and radius 0.5 at a seeded point of
+    [2,8]^2 with the pressure unchanged.  CFL 0.5, k = 20, w = 40, 5 % sample.
     Returns (q0 [4, n*n] cell index x-fastest, cfg, steps)."""
     gamma = 1.4
     rng = Rng(seed)
@@ -170,7 +170,6 @@ def euler_vortex(n=512, seed=2, steps=500, **kw):
     xc = (np.arange(n) + 0.5) * dx
     X, Y = np.meshgrid(xc, xc, indexing="xy")          # X varies along axis 1
     beta = 5.0
-    minf = 0.5
     cinf = math.sqrt(gamma)
     uinf = minf * cinf / math.sqrt(2.0)
     vinf = uinf
@@ -191,6 +190,28 @@ def euler_vortex(n=512, seed=2, steps=500, **kw):
                    pod_tol=1e-6, pod_abs=1e-6, precision=PREC_F32, seed=seed)
     cfg = replace(cfg, **kw)
     return q0, cfg, steps
+
+
+def euler_batch(n_inst=64, seed=5, nmin=128, nmax=1024, kmin=8, kmax=48, fmin=0.02,
+                fmax=0.20, mach=(0.3, 2.0)):
+    """The batching form: n_inst independent Euler instances, each the
+    vortex-plus-pulse problem (euler_vortex) on an n x n grid with n drawn
+    log-uniformly from [nmin, nmax] (so cell counts are log-uniform too),
+    free-stream Mach ~ U[mach], its own basis size k ~ U{kmin..kmax} with
+    w = n_p = 2k, and its own sample fraction ~ U[fmin, fmax] (uneven masks).
+    Returns a list of (q0, cfg)."""
+    rng = Rng(seed)
+    out = []
+    for i in range(n_inst):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        m_inf = rng.uniform(*mach)
+        k = kmin + int(rng.uniform(0.0, 1.0) * (kmax - kmin + 1))
+        k = min(k, kmax)
+        frac = rng.uniform(fmin, fmax)
+        q0, cfg, _ = euler_vortex(n=n, seed=seed * 1000 + i, minf=m_inf, w=2 * k, m=k,
+                                  n_p=2 * k, top_frac=frac)
+        out.append((q0, cfg))
+    return out
 
 
 def normal_shock_states(gamma, mach, rho1, p1):
