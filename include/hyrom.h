@@ -293,7 +293,8 @@ hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const i
  * basis size, window and sample fraction) stepped together by a pool of host
  * threads.  hyrom_batch_create takes n distinct contexts (the caller keeps
  * them: they must outlive the batch and not be used by another thread while
- * a batch call runs) and starts `threads` host threads (0: min(n, 16)).
+ * a batch call runs) and starts `threads` host threads (0: half the host's
+ * hardware threads, between 1 and 8; never more than n).
  * hyrom_batch_step runs `nsteps` calls of hyrom_step on every instance: each
  * thread takes one instance at a time, largest device footprint first, and
  * runs its steps on the instance's own stream, so up to `threads` instances

@@ -100,7 +100,11 @@ extern "C" hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, in
     delete b;
     return HYROM_ECUDA;
   }
-  const int nt = threads == 0 ? std::min(n, 16) : std::min(n, (int)threads);
+  // default: half the host's hardware threads, at most 8 (a thread spins on
+  // the CPU while its instance's stream drains; more threads than half the
+  // cores starved the launching ones)
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nt = std::min(n, threads == 0 ? std::max(1, std::min(8, hw / 2)) : (int)threads);
   try {
     for (int t = 0; t < nt; ++t) b->pool.emplace_back(worker, b);
   } catch (...) {

@@ -336,7 +336,7 @@ def hyrom_selftest_math(which, x, y, stream=None):
 
 def hyrom_batch_create(ctxs, threads=0):
     """A batch over the contexts `ctxs` (kept by the caller) stepped by
-    `threads` host threads (0: min(len(ctxs), 16))."""
+    `threads` host threads (0: half the host's hardware threads, 1..8)."""
     n = len(ctxs)
     arr = (C.c_void_p * max(n, 1))(*ctxs)
     out = C.c_void_p()
