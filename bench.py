@@ -506,11 +506,11 @@ def batch_form(a):
         for t in [int(x) for x in str(a.batch_threads).split(",") if x]:
             b = hyrom.hyrom_batch_create(ctxs, threads=t)
             try:
-                hyrom.hyrom_batch_step(b, len(ctxs), nsteps=1)     # warm-up
+                hyrom.hyrom_batch_step(b, len(ctxs), nsteps=1, ctxs=ctxs)     # warm-up
                 torch.cuda.synchronize()
                 l0 = hyrom.hyrom_kernel_launches()
                 t0 = time.perf_counter()
-                _, infos = hyrom.hyrom_batch_step(b, len(ctxs), nsteps=a.batch_steps)
+                _, infos = hyrom.hyrom_batch_step(b, len(ctxs), nsteps=a.batch_steps, ctxs=ctxs)
                 torch.cuda.synchronize()
                 el = time.perf_counter() - t0
                 launches = hyrom.hyrom_kernel_launches() - l0

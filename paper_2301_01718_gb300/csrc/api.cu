@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -148,6 +150,19 @@ void add_launches(unsigned long long n) {
 }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 unsigned long long thread_launch_count() { return t_launches; }
+
+void smem_at_least(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{dev, func}];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      cudaSuccess)
+    cur = bytes;
+}
 }  // namespace hy
 
 static __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {

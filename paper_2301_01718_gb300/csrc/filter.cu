@@ -392,8 +392,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
     constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
     constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
-    cudaFuncSetAttribute(k_filter_pass<T, NV, NN, TXX, TYY>,                                 \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_);             \
+    smem_at_least((const void*)k_filter_pass<T, NV, NN, TXX, TYY>, sm_);                    \
   } while (0)
 #define HY_FA_N(NV, TXX, TYY) \
   do {                        \

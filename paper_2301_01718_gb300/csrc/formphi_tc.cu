@@ -398,7 +398,7 @@ void launch_form_phi_tc(const float* ring, int64_t N, int nslot, const int* win,
                         const float* psi, const float* C, int m, const int* m_eff_dev,
                         float* phi, float* psi_next, int* err, OdeimNorms norms,
                         cudaStream_t s) {
-  cudaFuncSetAttribute(k_form_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  smem_at_least((const void*)k_form_phi_tc, kSmemBytes);
   int64_t tiles = (N + kRows - 1) / kRows;
   const int grid = (int)(tiles < 152 ? tiles : 152);
   // the ring as a 2D tensor: rows (contiguous, N) x slots (stride 4 N bytes),

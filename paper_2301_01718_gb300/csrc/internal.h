@@ -14,6 +14,13 @@ unsigned long long launch_count();
 unsigned long long thread_launch_count();
 void add_launches(unsigned long long n);
 
+// Raise the dynamic shared memory limit of kernel `func` on the current
+// device to at least `bytes`.  The limit is a per-function global shared by
+// all host threads; it is only ever raised (under a lock), so that a launch
+// never meets a limit another thread lowered for a smaller instance between
+// its own setting and its launch.
+void smem_at_least(const void* func, size_t bytes);
+
 // A stream's work kept as a CUDA graph: captured at the first run, replayed
 // after.  Whatever the work bakes in (pointers, sizes) must be the same on
 // every run.  Launch counts: the launches made while capturing stand for the

@@ -1629,7 +1629,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   M_(-13);
   // DEIM
   const size_t dsmem = sizeof(double) * 2 * 64 * 65;
-  cudaFuncSetAttribute(k_deim_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+  smem_at_least((const void*)k_deim_solve<T>, dsmem);
   auto deim_loop = [&]() {
   for (int l = 0; l < m; ++l) {
     k_deim_solve<T><<<1, 256, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);

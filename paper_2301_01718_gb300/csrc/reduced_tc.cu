@@ -306,8 +306,7 @@ void launch_mode(const float* phi, int64_t N, int m, const int* cells, int ns, i
   rpc = (rpc + kRS - 1) / kRS * kRS;
   nb = rpc > 0 ? (nrows + rpc - 1) / rpc : 1;
   if (nb < 1) nb = 1;
-  cudaFuncSetAttribute(k_sample_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSmemBytes);
+  smem_at_least((const void*)k_sample_gram_tc<MODE>, kSmemBytes);
   k_sample_gram_tc<MODE><<<(int)nb, kThreads, kSmemBytes, HY_S(s)>>>(phi, N, m, cells, ns, nvar,
                                                                      nc, rpc, part, err);
   *nb_out = (int)nb;

@@ -139,7 +139,7 @@ void launch_gappy_pinv(const T* phi, int64_t N, int m, const int* pts, int np, d
                        int* status, cudaStream_t s) {
   if (m <= 0) return;
   const size_t smem = sizeof(double) * ((size_t)2 * np * m + (size_t)m * m + m);
-  cudaFuncSetAttribute(k_gappy_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_at_least((const void*)k_gappy_pinv<T>, smem);
   k_gappy_pinv<T><<<1, 256, smem, HY_S(s)>>>(phi, N, m, pts, np, pinv, status);
 }
 
@@ -975,7 +975,7 @@ int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int
   int* piv = reinterpret_cast<int*>(buf + (size_t)n * n);
   int* rank = piv + kEigMaxN;
   const size_t smem = sizeof(double) * (size_t)n * n;
-  cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_at_least((const void*)k_pchol, smem);
   k_pchol<<<1, 1024, smem, HY_S(s)>>>(G, n, n, B, piv, rank);
   (void)host_flag;
   const double tol = 1e-14;
@@ -1265,8 +1265,7 @@ void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* p
   if (blocks > 152 * 8) blocks = 152 * 8;
 #define HY_FORM(MM)                                                                          \
   do {                                                                                       \
-    cudaFuncSetAttribute(k_form_phi<T, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                         (int)smem);                                                         \
+    smem_at_least((const void*)k_form_phi<T, MM>, smem);                                    \
     k_form_phi<T, MM><<<(int)blocks, 256, smem, HY_S(s)>>>(ring, N, win, w, psi, C, m, m_eff_dev,  \
                                                      phi, psi_next);                         \
   } while (0)
@@ -1281,13 +1280,11 @@ void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* p
     int64_t tiles = (N + 127) / 128;
     if (tiles > 152 * 2) tiles = 152 * 2;
     if (mt == 32) {
-      cudaFuncSetAttribute(k_form_phi_tiled<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm2);
+      smem_at_least((const void*)k_form_phi_tiled<32>, sm2);
       k_form_phi_tiled<32><<<(int)tiles, 256, sm2, HY_S(s)>>>(ringf, N, win, w, psif, Cf, m,
                                                               m_eff_dev, phif, pnf);
     } else {
-      cudaFuncSetAttribute(k_form_phi_tiled<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm2);
+      smem_at_least((const void*)k_form_phi_tiled<64>, sm2);
       k_form_phi_tiled<64><<<(int)tiles, 256, sm2, HY_S(s)>>>(ringf, N, win, w, psif, Cf, m,
                                                               m_eff_dev, phif, pnf);
     }

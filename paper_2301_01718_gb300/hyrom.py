@@ -346,16 +346,19 @@ def hyrom_batch_create(ctxs, threads=0):
     return out.value
 
 
-def hyrom_batch_step(batch, n, nsteps=1):
+def hyrom_batch_step(batch, n, nsteps=1, ctxs=None):
     """nsteps hybrid steps of each of the n instances.  Returns (status per
     instance, info dict of each instance's last step); raises HyromError
-    with the failing instances' messages when any status is not OK."""
+    naming the failing instances (with their last error messages when the
+    contexts `ctxs` are given) when any status is not OK."""
     infos = (HyromStepInfo * n)()
     st = (C.c_int32 * n)()
     s = lib().hyrom_batch_step(batch, int(nsteps), infos, st)
     status = list(st)
     if s != HYROM_OK:
-        raise HyromError(s, f"instances {[i for i, v in enumerate(status) if v]} failed")
+        bad = [i for i, v in enumerate(status) if v]
+        why = [f"{i}: {hyrom_last_error(ctxs[i])}" for i in bad] if ctxs else bad
+        raise HyromError(s, f"instances failed: {why}")
     return status, [i.as_dict() for i in infos]
 
 

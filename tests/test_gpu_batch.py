@@ -43,9 +43,18 @@ def _state(hy, ctx, cfg):
     return host(q).copy()
 
 
-def test_batch_matches_instances_stepped_alone():
+def _wide_instances():
+    """Eight instances with windows of 72 to 96 snapshots: their eigensolver
+    and pseudo-inverse kernels need different amounts of shared memory above
+    the 48 KB default, set per kernel for the whole process."""
+    return [b for b in W.euler_batch(n_inst=8, seed=9, nmin=40, nmax=80, kmin=36, kmax=48)]
+
+
+@pytest.mark.parametrize("kind", ["uneven", "wide"])
+def test_batch_matches_instances_stepped_alone(kind):
     hy = H()
-    insts = _instances()
+    insts = _instances() if kind == "uneven" else _wide_instances()
+    threads = 3 if kind == "uneven" else 8
     steps = max(c.w for _, c in insts) + 4          # warm-up and several rebuilds each
     # alone, one after another on the caller's thread
     ctxs, streams = _open(hy, insts)
@@ -58,14 +67,14 @@ def test_batch_matches_instances_stepped_alone():
     finally:
         for c in ctxs:
             hy.hyrom_destroy(c)
-    # together: 3 threads over 5 instances, in two calls (steps split unevenly)
+    # together: more instances than threads, in two calls (steps split unevenly)
     ctxs, streams = _open(hy, insts)
     try:
-        b = hy.hyrom_batch_create(ctxs, threads=3)
+        b = hy.hyrom_batch_create(ctxs, threads=threads)
         try:
-            assert hy.hyrom_batch_threads(b) == 3
-            st1, _ = hy.hyrom_batch_step(b, len(ctxs), nsteps=steps - 3)
-            st2, infos = hy.hyrom_batch_step(b, len(ctxs), nsteps=3)
+            assert hy.hyrom_batch_threads(b) == threads
+            st1, _ = hy.hyrom_batch_step(b, len(ctxs), nsteps=steps - 3, ctxs=ctxs)
+            st2, infos = hy.hyrom_batch_step(b, len(ctxs), nsteps=3, ctxs=ctxs)
             assert st1 == [0] * len(ctxs) and st2 == [0] * len(ctxs)
         finally:
             hy.hyrom_batch_destroy(b)
