@@ -112,6 +112,21 @@ __global__ void k_set_filt_args(FiltArgs<T>* fa, T* q, const T* qp, double t) {
   fa->t = t;
 }
 
+// shared memory of k_filter_pass: q on the tile and an NF+1 halo, F_x q,
+// g on the tile and a one-cell ring; for the Euler equations also the
+// resolved q and g on that ring, their primitives and the face fluxes
+template <typename T, int NV, int NF, int TX, int TY>
+constexpr size_t filter_pass_smem() {
+  constexpr bool TWO = TY > 1;
+  constexpr int H = NF + 1, SX = TX + 2 * H, SY = TWO ? TY + 2 * H : 1;
+  constexpr int GX = TX + 2, GY = TWO ? TY + 2 : 1;
+  size_t n = (size_t)NV * (SY * SX + SY * GX + GY * GX);
+  if (NV == 4)
+    n += (size_t)2 * NV * GY * GX + 2 * 4 * GY * GX + 2 * NV * TY * (TX + 1) +
+         (TWO ? 2 * NV * (TY + 1) * TX : 0);
+  return sizeof(T) * n;
+}
+
 template <typename T, int NV, int NF, int TX, int TY>
 __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs<T>* __restrict__ fa,
                                                      T* __restrict__ gbuf, uint32_t* __restrict__ kbits,
@@ -211,7 +226,120 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
       }
     }
     __syncthreads();
-    // residual measures and the gate on the tile
+    if constexpr (NV == 4) {
+      // Euler: the states the residuals read (q and g on the tile and its
+      // one-cell ring, ghost values resolved), their primitives once per
+      // cell, and each face flux once per face
+      T* qe = gs + NV * GY * GX;
+      T* ge = qe + NV * GY * GX;
+      T* wq = ge + NV * GY * GX;  // u, v, p, c of qe
+      T* wg = wq + 4 * GY * GX;
+      T* fxq = wg + 4 * GY * GX;  // x faces: row ly, face lx between ring columns lx, lx + 1
+      T* fxg = fxq + NV * TY * (TX + 1);
+      T* fyq = fxg + NV * TY * (TX + 1);  // y faces: row ly between ring rows ly, ly + 1
+      T* fyg = fyq + (TWO ? NV * (TY + 1) * TX : 0);
+      const T g = (T)c.gamma;
+      for (int idx = threadIdx.x; idx < GY * GX; idx += blockDim.x) {
+        const int gy = idx / GX, gx = idx % GX;
+        if (TWO && (gx == 0 || gx == GX - 1) && (gy == 0 || gy == GY - 1)) continue;  // unused
+        const int gi = x0 - 1 + gx, gj = TWO ? y0 - 1 + gy : 0;
+        T qv[NV], gv[NV];
+        // q: the staged (wrapped or clamped) value, or the shock state
+        nb_value<T, NV>(c, qs, SY * SX, (TWO ? gy + H - 1 : 0) * SX + gx + H - 1, gi, gj, t, qv);
+        // g: outside a non-periodic side, the boundary cell's g (or the
+        // shock state)
+        int gxe = gx, gye = gy;
+        if (!perx) gxe = gi < 0 ? gx + 1 : (gi >= c.nx ? gx - 1 : gx);
+        if (TWO && !pery) gye = gj < 0 ? gy + 1 : (gj >= c.ny ? gy - 1 : gy);
+        nb_value<T, NV>(c, gs, GY * GX, gye * GX + gxe, gi, gj, t, gv);
+        T wv[4], ww[4];
+        prims(qv, g, wv[0], wv[1], wv[2], wv[3]);
+        prims(gv, g, ww[0], ww[1], ww[2], ww[3]);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          qe[(a * GY + gy) * GX + gx] = qv[a];
+          ge[(a * GY + gy) * GX + gx] = gv[a];
+          wq[(a * GY + gy) * GX + gx] = wv[a];
+          wg[(a * GY + gy) * GX + gx] = ww[a];
+        }
+      }
+      __syncthreads();
+      constexpr int NFX = TY * (TX + 1), NFY = TWO ? (TY + 1) * TX : 0;
+      for (int f = threadIdx.x; f < 2 * (NFX + NFY); f += blockDim.x) {
+        const bool isg = f >= NFX + NFY;
+        const int e = isg ? f - (NFX + NFY) : f;
+        const T* S = isg ? ge : qe;
+        const T* Wp = isg ? wg : wq;
+        T qL[4], wL[4], qR[4], wR[4], F[4];
+        int oL, oR;
+        if (e < NFX) {
+          const int ly = e / (TX + 1), lx = e % (TX + 1), gy = TWO ? ly + 1 : 0;
+          oL = gy * GX + lx;
+          oR = oL + 1;
+        } else {
+          const int ly = (e - NFX) / TX, lx = (e - NFX) % TX;
+          oL = ly * GX + lx + 1;
+          oR = oL + GX;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          qL[a] = S[a * GY * GX + oL];
+          qR[a] = S[a * GY * GX + oR];
+          wL[a] = Wp[a * GY * GX + oL];
+          wR[a] = Wp[a * GY * GX + oR];
+        }
+        if (e < NFX) {
+          rusanov_p<T, 0>(qL, wL, qR, wR, F);
+          T* dst = isg ? fxg : fxq;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) dst[a * NFX + e] = F[a];
+        } else {
+          rusanov_p<T, 1>(qL, wL, qR, wR, F);
+          T* dst = isg ? fyg : fyq;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) dst[a * NFY + (e - NFX)] = F[a];
+        }
+      }
+      __syncthreads();
+      // residual measures and the gate on the tile (the operator's
+      // expressions of rhs_cell, from the shared face fluxes)
+      const T dxT = (T)c.dx, dyT = (T)c.dy;
+      for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+        const int ly = idx / TX, lx = idx % TX;
+        const int gi = x0 + lx, gj = y0 + ly;
+        if (gi >= c.nx || gj >= c.ny) continue;
+        const int64_t cell = (int64_t)gj * c.nx + gi;
+        const int oc = (TWO ? ly + 1 : 0) * GX + lx + 1;
+        const int fx0 = ly * (TX + 1) + lx, fy0 = ly * TX + lx;
+        T ro = (T)0, rn = (T)0;
+        T gC[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T r = -(fxq[a * NFX + fx0 + 1] - fxq[a * NFX + fx0]) / dxT;
+          T rg = -(fxg[a * NFX + fx0 + 1] - fxg[a * NFX + fx0]) / dxT;
+          if (TWO) {
+            r = r - (fyq[a * NFY + fy0 + TX] - fyq[a * NFY + fy0]) / dyT;
+            rg = rg - (fyg[a * NFY + fy0 + TX] - fyg[a * NFY + fy0]) / dyT;
+          }
+          const T qC = qe[a * GY * GX + oc];
+          gC[a] = ge[a * GY * GX + oc];
+          const T p = qp[a * c.nc + cell];
+          const T Ro = (qC - p) - dt * r;
+          const T Rn = (gC[a] - p) - dt * rg;
+          ro = a == 0 ? fabs(Ro) : ro + fabs(Ro);
+          rn = a == 0 ? fabs(Rn) : rn + fabs(Rn);
+        }
+        if (rn < ro) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) gbuf[a * c.nc + cell] = gC[a];
+          atomicOr(&kbits[cell >> 5], 1u << (cell & 31));
+          cnt += 1.0;
+          dec += (double)(ro - rn);
+          tot += (double)ro;
+        }
+      }
+    } else {
+    // Burgers: residual measures and the gate on the tile
     for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
       const int ly = idx / TX, lx = idx % TX;
       const int gi = x0 + lx, gj = y0 + ly;
@@ -264,6 +392,7 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
         dec += (double)(ro - rn);
         tot += (double)ro;
       }
+    }
     }
   }
   cnt = block_sum(cnt);
@@ -389,9 +518,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     const int n = orders[o];
 #define HY_FA(NV, NN, TXX, TYY)                                                              \
   do {                                                                                       \
-    constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
-    constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
-    constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
+    constexpr size_t sm_ = filter_pass_smem<T, NV, NN, TXX, TYY>();                          \
     smem_at_least((const void*)k_filter_pass<T, NV, NN, TXX, TYY>, sm_);                    \
   } while (0)
 #define HY_FA_N(NV, TXX, TYY) \
@@ -426,9 +553,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
       const int grid = cur ? 152 * 8 : (nt < 152 * 8 ? nt : 152 * 8);
 #define HY_FP(NV, NN, TXX, TYY)                                                              \
   do {                                                                                       \
-    constexpr int H_ = NN + 1, SY_ = TYY > 1 ? TYY + 2 * H_ : 1, SX_ = TXX + 2 * H_;         \
-    constexpr int GY_ = TYY > 1 ? TYY + 2 : 1;                                               \
-    constexpr size_t sm_ = sizeof(T) * NV * (SY_ * SX_ + SY_ * (TXX + 2) + GY_ * (TXX + 2)); \
+    constexpr size_t sm_ = filter_pass_smem<T, NV, NN, TXX, TYY>();                          \
     k_filter_pass<T, NV, NN, TXX, TYY><<<grid, 256, sm_, HY_S(s)>>>(                         \
         c, fa, gbuf, kbits, cur, cur_n, nt, part, ctl);                                      \
   } while (0)

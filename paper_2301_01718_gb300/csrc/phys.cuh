@@ -84,12 +84,13 @@ HY_DEV void prims(const T* q, T g, T& u, T& v, T& p, T& cs) {
   cs = sqrt(a2 > (T)0 ? a2 : (T)0);
 }
 
-// Rusanov flux across a face normal to x (AX = 0) or y (AX = 1).
+// Rusanov flux across a face normal to x (AX = 0) or y (AX = 1) from the
+// two states and their primitive values w = (u, v, p, c) (prims()); a
+// kernel that holds each cell's primitives evaluates each face once.
 template <typename T, int AX>
-HY_DEV void rusanov(const T* qL, const T* qR, T g, T* F) {
-  T uL, vL, pL, cL, uR, vR, pR, cR;
-  prims(qL, g, uL, vL, pL, cL);
-  prims(qR, g, uR, vR, pR, cR);
+HY_DEV void rusanov_p(const T* qL, const T* wL, const T* qR, const T* wR, T* F) {
+  const T uL = wL[0], vL = wL[1], pL = wL[2], cL = wL[3];
+  const T uR = wR[0], vR = wR[1], pR = wR[2], cR = wR[3];
   T fL[4], fR[4], a;
   if (AX == 0) {
     fL[0] = qL[1];
@@ -116,6 +117,14 @@ HY_DEV void rusanov(const T* qL, const T* qR, T g, T* F) {
   }
   const T ha = (T)0.5 * a;
   for (int v = 0; v < 4; ++v) F[v] = (T)0.5 * (fL[v] + fR[v]) - ha * (qR[v] - qL[v]);
+}
+
+template <typename T, int AX>
+HY_DEV void rusanov(const T* qL, const T* qR, T g, T* F) {
+  T wL[4], wR[4];
+  prims(qL, g, wL[0], wL[1], wL[2], wL[3]);
+  prims(qR, g, wR[0], wR[1], wR[2], wR[3]);
+  rusanov_p<T, AX>(qL, wL, qR, wR, F);
 }
 
 // f*(q) at one cell from its 5-point neighbourhood.

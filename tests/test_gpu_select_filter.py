@@ -79,9 +79,22 @@ def test_masks_bit_exact(periodic, scheme, halo, oned):
         assert np.array_equal(bits_of(st, nc), s_tilde.reshape(-1))
 
 
-@pytest.mark.parametrize("case", ["burgers", "vortex", "shock"])
+@pytest.mark.parametrize("case", ["burgers", "vortex", "shock", "sod_x", "shock_ragged"])
 def test_filter_matches_oracle(case):
-    if case == "burgers":
+    if case == "sod_x":     # Euler in one dimension: 256-cell tiles, a ragged last tile
+        q0, cfg = W.euler_riemann_x(n=300)
+        cfg = cfg.with_(w=4, m=2, n_p=4)
+        qp = q0.reshape(4, 1, 300)
+        k = 1
+        q1 = hdm.rk2_step(qp, cfg, k)
+    elif case == "shock_ragged":   # tiles ragged in both directions, shock and outflow sides
+        q0, cfg, _ = W.euler_oblique_shock(n=45, seed=4, k=4)
+        cfg = cfg.with_(precision=W.PREC_F64)
+        qp = q0.reshape(4, 45, 45)
+        k = 2
+        q1 = hdm.rk2_step(hdm.rk2_step(qp, cfg, 1), cfg, k)
+        qp = hdm.rk2_step(qp, cfg, 1)
+    elif case == "burgers":
         u0, cfg, _ = W.burgers_sine(n=400, seed=3)
         qp = u0.reshape(1, 1, -1)
         q1, _, _ = hdm.newton_be(qp, cfg, cfg.dt)
