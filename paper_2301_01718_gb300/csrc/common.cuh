@@ -132,6 +132,18 @@ HY_DEV double rsqrt64(double a) {
   return y;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic
+// stream serialization may be scheduled while its predecessor on the stream
+// still runs; pdl_enter, its first statement, waits until the predecessor has
+// completed and its writes are visible (griddepcontrol.wait; a no-op for an
+// ordinary launch), then lets the next kernel be scheduled in turn.  Every
+// kernel of such a chain therefore starts its work in stream order, only
+// without the launch gap.
+HY_DEV void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Bucket of a row's squared-norm bound v among 256 (ratio 2^(1/4) per
 // bucket, bucket 255 for v = 0): the order ODEIM scans rows in.
 constexpr int kNormBuckets = 256;

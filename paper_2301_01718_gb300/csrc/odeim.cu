@@ -164,6 +164,7 @@ __global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
                              const int* __restrict__ pts, const double* __restrict__ Lf,
                              const double* __restrict__ Uf, double* __restrict__ yv,
                              double* __restrict__ cvec, OdCtl* ctl) {
+  pdl_enter();
   // L and U transposed into shared memory (stride 65: conflict-free), so
   // that both solves run column by column: after x_i is known every lane
   // updates its two right-hand-side entries (j = lane, lane + 32).
@@ -248,6 +249,7 @@ template <typename T>
 __global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const OdCtl* ctl,
                               double* __restrict__ Lf, double* __restrict__ Uf,
                               const double* __restrict__ yv) {
+  pdl_enter();
   // column-oriented solve of U^T ell = a with U^T's columns = U's rows
   __shared__ double Us[64 * 64];
   const int p = ctl->argmin;
@@ -300,6 +302,7 @@ __global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
                              const unsigned char* __restrict__ picked, int p0, int p1,
                              OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R,
                              int C) {
+  pdl_enter();
   __shared__ double cs[64];
   for (int j = threadIdx.x; j < l; j += blockDim.x) cs[j] = cvec[j];
   __syncthreads();
@@ -350,6 +353,7 @@ __device__ void plan_rows(OdCtl* ctl, const unsigned int* __restrict__ bmax,
 // DEIM: |r_i| <= |phi_i| sqrt(1 + |c|^2), so rows need |phi_i|^2 >= lim^2 / cn2
 __global__ void k_deim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
                             const int* __restrict__ bstart, int probe_end, double tie_tol) {
+  pdl_enter();
   const double s = bitsd(ctl->smax);
   const double lim = s * (1.0 - 2.0 * tie_tol);
   plan_rows(ctl, bmax, bstart, probe_end, lim * lim / (ctl->cn2 * (1.0 + 1e-5)));
@@ -359,6 +363,7 @@ __global__ void k_deim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
 // lowest row among the scored rows within the tie window of the best
 __global__ void k_argmin_tie(const double* __restrict__ scores, const int* __restrict__ ord,
                              OdCtl* ctl, double tie_tol) {
+  pdl_enter();
   const double lim = bitsd(ctl->smax) * (1.0 - tie_tol);
   const int end = ctl->n_c;
   int best = 0x7fffffff;
@@ -378,6 +383,7 @@ __global__ void k_argmin_tie(const double* __restrict__ scores, const int* __res
 }
 
 __global__ void k_commit(OdCtl* ctl, int l, int* __restrict__ pts, unsigned char* picked) {
+  pdl_enter();
   const int p = ctl->argmin;
   pts[l] = p;
   picked[p] = 1;
@@ -641,6 +647,7 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
     double* __restrict__ scores, int* __restrict__ list, const float* __restrict__ R, int C) {
+  pdl_enter();
   __shared__ float w1[64];
   for (int a = threadIdx.x; a < 64; a += blockDim.x) w1[a] = a < m ? (float)W_s[a] : 0.f;
   __syncthreads();
@@ -707,6 +714,7 @@ __global__ void __launch_bounds__(256) k_odeim_screen(
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, int p1, const int* __restrict__ list,
     OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R, int C) {
+  pdl_enter();
   __shared__ __align__(16) float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
   __shared__ float dn[64], du[64];
   __shared__ float ph[8][64];
@@ -845,6 +853,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_odeim_probe_best(
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
     const double* __restrict__ W_s, const int* __restrict__ ord, OdCtl* ctl) {
+  pdl_enter();
   extern __shared__ double sh[];
   double* W = sh;               // 64 x kLdw
   double* lam = W + 64 * kLdw;  // 64
@@ -882,6 +891,7 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
     const double* __restrict__ W_s, const int* __restrict__ ord, int probe,
     const int* __restrict__ list, double tie_tol, OdCtl* ctl, double* __restrict__ scores) {
+  pdl_enter();
   extern __shared__ double sh[];
   double* W = sh;               // 64 x kLdw
   double* lam = W + 64 * kLdw;  // 64
@@ -963,6 +973,7 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
 // ODEIM: mu - l1 <= z_1^2 <= |phi_i|^2, so rows need |phi_i|^2 >= lim - l1
 __global__ void k_odeim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
                              const int* __restrict__ bstart, int probe_end, double tie_tol) {
+  pdl_enter();
   if (threadIdx.x == 0) ctl->stat[3] += 1;
   const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
   plan_rows(ctl, bmax, bstart, probe_end, (lim - ctl->lam1) / (1.0 + 1e-5));
@@ -999,6 +1010,7 @@ template <typename T>
 __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const OdCtl* ctl,
                              const double* __restrict__ d, const double* __restrict__ W,
                              double* __restrict__ Wrot, R1Work* wk) {
+  pdl_enter();
   __shared__ double Ws[64 * 64];
   __shared__ double ph[64], z[64], ds[64];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1148,6 +1160,7 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
 // |f| is within the rounding error of its evaluation, the step is below
 // 2 ulp, or the bracket has collapsed.
 __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
+  pdl_enter();
   const int j = blockIdx.x, lane = threadIdx.x;
   const int nK = wk->nK;
   if (j >= nK) return;
@@ -1331,6 +1344,7 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
 // signed like z_i.  One warp per component i (lane: q and q + 32), a product
 // tree over the lanes.
 __global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __restrict__ Delta) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nK = wk->nK;
@@ -1362,6 +1376,7 @@ __global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ w
                                                     const double* __restrict__ Wrot, int m,
                                                     double* __restrict__ Wnew,
                                                     double* __restrict__ lamnew) {
+  pdl_enter();
   __shared__ double v[64];
   __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
   __shared__ double part[4][64];
@@ -1416,6 +1431,7 @@ __global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restri
                            const double* __restrict__ Wnew, const double* __restrict__ lamnew,
                            int m, double* __restrict__ d_out, double* __restrict__ W_out,
                            OdCtl* ctl, float* __restrict__ wt32) {
+  pdl_enter();
   __shared__ double lv[64];
   __shared__ unsigned long long key[64];
   __shared__ int src[64];  // >= 0: new pair index; < 0: -(deflated idx)-1
@@ -1593,6 +1609,31 @@ void odeim_graphs_free(OdeimGraphs* g) {
   g->m = g->np = -1;
 }
 
+// Launch with programmatic stream serialization (the kernel starts with
+// pdl_enter(), which keeps stream order); where the attribute is refused,
+// an ordinary launch.  The arguments are converted to the kernel's
+// parameter types as in a triple-chevron launch.
+template <typename... KArgs, typename... Args>
+void pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+         Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  if (cudaLaunchKernelEx(&cfg, kern, args...) != cudaSuccess) {
+    cudaGetLastError();
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  }
+}
+
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg,
@@ -1627,20 +1668,22 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   }
   const int probe = (int)(N < kProbe ? N : kProbe);
   M_(-13);
-  // DEIM
+  // DEIM.  The kernels of both greedy loops start with pdl_enter() and are
+  // launched with programmatic stream serialization (pdl()): each is
+  // scheduled while its predecessor runs and waits for it on the device.
   const size_t dsmem = sizeof(double) * 2 * 64 * 65;
   smem_at_least((const void*)k_deim_solve<T>, dsmem);
   auto deim_loop = [&]() {
   for (int l = 0; l < m; ++l) {
-    k_deim_solve<T><<<1, 256, dsmem, HY_S(s)>>>(phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
-    k_deim_score<T><<<(probe + 255) / 256, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, 0,
-                                                        probe, o.ctl, o.scores, o.rows, C);
-    k_deim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
-    k_deim_score<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, l, o.cvec, o.ord, o.picked, probe, -1,
-                                            o.ctl, o.scores, o.rows, C);
-    k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
-    k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
-    if (l + 1 < m) k_deim_extend<T><<<1, 256, 0, HY_S(s)>>>(phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
+    pdl(k_deim_solve<T>, 1, 256, dsmem, s, phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
+    pdl(k_deim_score<T>, (probe + 255) / 256, 256, 0, s, phi, N, l, o.cvec, o.ord, o.picked, 0,
+        probe, o.ctl, o.scores, o.rows, C);
+    pdl(k_deim_plan, 1, 256, 0, s, o.ctl, o.bmax, o.bstart, probe, tie_tol);
+    pdl(k_deim_score<T>, 152 * 8, 256, 0, s, phi, N, l, o.cvec, o.ord, o.picked, probe, -1,
+        o.ctl, o.scores, o.rows, C);
+    pdl(k_argmin_tie, 152 * 4, 256, 0, s, o.scores, o.ord, o.ctl, tie_tol);
+    pdl(k_commit, 1, 1, 0, s, o.ctl, l, pts, o.picked);
+    if (l + 1 < m) pdl(k_deim_extend<T>, 1, 256, 0, s, phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
   }
   };
   if (graphs)
@@ -1684,36 +1727,36 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   for (int l = m; l < np; ++l) {
     ML_(13);
     // full FP32 bounds of the largest-norm rows, exact score of the best
-    k_odeim_screen<T><<<(probe + 7) / 8, 256, 0, HY_S(s)>>>(
-        phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0, probe, nullptr, o.ctl, o.scores, o.rows, C);
-    k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
-    k_odeim_plan<<<1, 256, 0, HY_S(s)>>>(o.ctl, o.bmax, o.bstart, probe, tie_tol);
+    pdl(k_odeim_screen<T>, (probe + 7) / 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked,
+        0, probe, (const int*)nullptr, o.ctl, o.scores, o.rows, C);
+    pdl(k_odeim_probe_best<T>, 1, 256, smem_pb, s, phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
+    pdl(k_odeim_plan, 1, 256, 0, s, o.ctl, o.bmax, o.bstart, probe, tie_tol);
     ML_(-14);
     ML_(14);
     // the other rows whose norm can reach the best score: the z_1 bound for
     // all, the full bound for those it does not exclude
-    k_odeim_z1<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
-                                                tie_tol, o.ctl, o.scores, o.list, o.rows, C);
-    k_odeim_screen<T><<<152 * 8, 256, 0, HY_S(s)>>>(phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0,
-                                                    -1, o.list, o.ctl, o.scores, o.rows, C);
-    k_odeim_probe_best<T><<<1, 256, smem_pb, HY_S(s)>>>(phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
+    pdl(k_odeim_z1<T>, 152 * 8, 256, 0, s, phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
+        tie_tol, o.ctl, o.scores, o.list, o.rows, C);
+    pdl(k_odeim_screen<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0, -1,
+        (const int*)o.list, o.ctl, o.scores, o.rows, C);
+    pdl(k_odeim_probe_best<T>, 1, 256, smem_pb, s, phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
     ML_(-15);
     ML_(15);
-    k_odeim_exact<T><<<152, kExactThreads, smem_ex, HY_S(s)>>>(
-        phi, N, m, o.lam_s, o.W_s, o.ord, probe, o.list, tie_tol, o.ctl, o.scores);
+    pdl(k_odeim_exact<T>, 152, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, o.ord, probe,
+        o.list, tie_tol, o.ctl, o.scores);
     ML_(-16);
     ML_(17);
-    k_argmin_tie<<<152 * 4, 256, 0, HY_S(s)>>>(o.scores, o.ord, o.ctl, tie_tol);
-    k_commit<<<1, 1, 0, HY_S(s)>>>(o.ctl, l, pts, o.picked);
+    pdl(k_argmin_tie, 152 * 4, 256, 0, s, o.scores, o.ord, o.ctl, tie_tol);
+    pdl(k_commit, 1, 1, 0, s, o.ctl, l, pts, o.picked);
     ML_(-18);
     if (l + 1 < np) {
       ML_(16);
-      k_r1_prepare<T><<<1, 256, 0, HY_S(s)>>>(phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
-      k_r1_roots<<<m, 32, 0, HY_S(s)>>>(o.r1, o.Delta);
-      k_r1_loewner<<<(m + 3) / 4, 128, 0, HY_S(s)>>>(o.r1, o.Delta);
-      k_r1_vectors<<<m, 256, 0, HY_S(s)>>>(o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
-      k_r1_merge<<<1, 256, 0, HY_S(s)>>>(o.r1, o.Wrot, o.Wnew, o.lamnew, m, o.lam_s2, o.W_s2,
-                                         o.ctl, o.wt32);
+      pdl(k_r1_prepare<T>, 1, 256, 0, s, phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
+      pdl(k_r1_roots, m, 32, 0, s, o.r1, o.Delta);
+      pdl(k_r1_loewner, (m + 3) / 4, 128, 0, s, o.r1, o.Delta);
+      pdl(k_r1_vectors, m, 256, 0, s, o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
+      pdl(k_r1_merge, 1, 256, 0, s, o.r1, o.Wrot, o.Wnew, o.lamnew, m, o.lam_s2, o.W_s2, o.ctl,
+          o.wt32);
       std::swap(o.lam_s, o.lam_s2);
       std::swap(o.W_s, o.W_s2);
       ML_(-17);
