@@ -69,7 +69,7 @@ def parse():
                    help="timed hybrid steps per instance in each batching-form arm")
     p.add_argument("--batch-threads", default="1,4,8,16",
                    help="host-thread counts timed in the batching form (1 = one at a time)")
-    p.add_argument("--micro", choices=["sample_gram", "batch"], default=None,
+    p.add_argument("--micro", choices=["sample_gram", "batch", "full_step"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
     return p.parse_args()
@@ -324,6 +324,8 @@ def run_ours(a):
         out["err_vs_fp64"] = err_vs_fp64(a)
     if rank == 0 and not a.no_precision_form:
         out["precision_form"] = precision_form(a)
+    if rank == 0:
+        out["full_step"] = full_step(a)
     if rank == 0 and not a.no_batch_form:
         out["batch_form"] = batch_form(a)
     if rank == 0 and not a.no_cpu_baseline:
@@ -536,6 +538,42 @@ def batch_form(a):
                                          one["instance_steps_per_s"]) if one else None}
 
 
+def full_step(a, calls=20, pairs=4):
+    """The full SSP-RK2 HDM step (hyrom_stage_full_step: the fused flux
+    kernel over every tile) on the benchmark grid: CUDA-event time of the
+    kernel per launch (stage timer around the launch), and its algorithmic
+    bytes (the state read once and written once: 2 x 4 x 4 B per cell) per
+    second against the measured HBM peak.  `pairs` input/output pairs are
+    used in turn, so that the bytes of consecutive launches (pairs x 134 MB
+    at 2048^2) exceed L2."""
+    import torch
+    from paper_2301_01718_gb300 import build, hyrom
+    build.build()
+    q0, cfg = workload(a)
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q0d)
+    try:
+        bufs = [(q0d.to(torch.float32).clone(), torch.empty(cfg.ndof, device="cuda"))
+                for _ in range(pairs)]
+        del q0d
+        for i in range(3):
+            hyrom.hyrom_stage_full_step(ctx, bufs[i % pairs][0], bufs[i % pairs][1], 1)
+        hyrom.hyrom_profile(ctx, True)
+        for i in range(calls):
+            hyrom.hyrom_stage_full_step(ctx, bufs[i % pairs][0], bufs[i % pairs][1], 1)
+        tot, cnt = hyrom.hyrom_stage_times(ctx)["full"]
+        hyrom.hyrom_profile(ctx, False)
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    ms = tot / max(cnt, 1)
+    byts = 2.0 * 4 * 4 * cfg.ncell
+    peaks = _peaks()
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"kernel": "k_rk2_euler", "grid": f"{cfg.nx}x{cfg.ny}", "ms_per_launch": ms,
+            "launches": cnt, "bytes_per_launch": byts, "achieved_gbs": gbs,
+            "peak_gbs": peaks["hbm"], "frac": gbs / peaks["hbm"], "peak_source": peaks["src"]}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -562,6 +600,8 @@ def main():
         out = micro_sample_gram(a)
     elif a.micro == "batch":
         out = {"micro": "batch", **batch_form(a)}
+    elif a.micro == "full_step":
+        out = {"micro": "full_step", **full_step(a)}
     else:
         out = run_reference(a) if a.impl == "reference" else run_ours(a)
     if out is not None:

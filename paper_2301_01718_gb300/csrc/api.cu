@@ -1019,12 +1019,14 @@ hyrom_status hyrom_stage_full_step(hyrom_ctx* ctx, const void* q_prev, void* q_o
   if (!q_prev || !q_out || q_prev == q_out) return HYROM_EINVAL;
   CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
   if (ctx->cfg.scheme == HYROM_SCHEME_RK2) {
+    t_begin(ctx, HYROM_T_FULL);
     if (ctx->f32)
       hy::launch_rk2<float>(ctx->dc, (const float*)q_prev, (float*)q_out, k, nullptr, nullptr,
                             nullptr, ctx->st);
     else
       hy::launch_rk2<double>(ctx->dc, (const double*)q_prev, (double*)q_out, k, nullptr, nullptr,
                              nullptr, ctx->st);
+    t_end(ctx, HYROM_T_FULL);
   } else {
     CK(cudaMemcpyAsync(q_out, q_prev, ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
     if (hyrom_status s = newton_full<double>(ctx, (const double*)q_prev, (double*)q_out)) return s;

@@ -118,6 +118,198 @@ __global__ void __launch_bounds__(256) k_rk2_tile(DevCfg c, const T* __restrict_
   }
 }
 
+// The same fused SSP-RK2 step for the Euler equations, with the work per
+// cell cut to what the stencil needs: the primitives (u, v, p, c) of every
+// staged cell are formed once, and every face flux once (a cell's residual
+// is the difference of its face fluxes).  Each face is evaluated by
+// rusanov_p on the same two states as rhs_cell evaluates it, so the step
+// gives the same bits as k_rk2_tile.
+template <typename T, int TX, int TY>
+constexpr size_t rk2_euler_smem() {
+  constexpr bool TWO = TY > 1;
+  constexpr int HX = TX + 4, HY = TWO ? TY + 4 : 1, H1X = TX + 2, H1Y = TWO ? TY + 2 : 1;
+  constexpr int NX1 = (TWO ? TY + 2 : 1) * (TX + 3), NY1 = TWO ? (TY + 3) * (TX + 2) : 0;
+  // q on the tile + 2 ring, q1 on the tile + 1 ring, primitives (of q, then
+  // of q1), x and y face fluxes (of stage 1, then of stage 2)
+  return sizeof(T) * 4 * ((size_t)2 * HY * HX + H1Y * H1X + NX1 + NY1);
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256) k_rk2_euler(DevCfg c, const T* __restrict__ q,
+                                                   T* __restrict__ out, int64_t k,
+                                                   const uint32_t* __restrict__ mask,
+                                                   const int* __restrict__ tiles,
+                                                   const int* __restrict__ ntiles_dev,
+                                                   int ntiles_all) {
+  constexpr bool TWO = TY > 1;
+  constexpr int HX = TX + 4, HY = TWO ? TY + 4 : 1, H1X = TX + 2, H1Y = TWO ? TY + 2 : 1;
+  constexpr int NX1 = (TWO ? TY + 2 : 1) * (TX + 3), NY1 = TWO ? (TY + 3) * (TX + 2) : 0;
+  constexpr int NX2 = TY * (TX + 1), NY2 = TWO ? (TY + 1) * TX : 0;
+  constexpr int PQ = HY * HX, P1 = H1Y * H1X;  // per-variable strides
+  extern __shared__ unsigned char rk_sm[];
+  T* qs = reinterpret_cast<T*>(rk_sm);  // [4][HY][HX]
+  T* q1s = qs + 4 * PQ;                  // [4][H1Y][H1X]
+  T* ws = q1s + 4 * P1;                  // [4][HY][HX] (stage 2: [4][H1Y][H1X])
+  T* fx = ws + 4 * PQ;                   // [4][NX1] (stage 2: [4][NX2])
+  T* fy = fx + 4 * NX1;                  // [4][NY1] (stage 2: [4][NY2])
+  const int tiles_x = (c.nx + TX - 1) / TX;
+  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  const double t0 = (double)(k - 1) * c.dt, t1 = (double)k * c.dt;
+  const T dt = (T)c.dt, dxT = (T)c.dx, dyT = (T)c.dy, g = (T)c.gamma;
+  const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int tile = tiles ? tiles[it] : it;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    __syncthreads();
+    // q on the tile and its two-cell ring (ghost values at t_{k-1}), and
+    // the primitives of each staged cell
+    for (int idx = threadIdx.x; idx < PQ; idx += blockDim.x) {
+      const int sy = idx / HX, sx = idx % HX;
+      T v[4], w[4];
+      fetch<T, 4>(c, q, x0 + sx - 2, TWO ? y0 + sy - 2 : 0, t0, v);
+      prims(v, g, w[0], w[1], w[2], w[3]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        qs[a * PQ + idx] = v[a];
+        ws[a * PQ + idx] = w[a];
+      }
+    }
+    __syncthreads();
+    // stage-1 face fluxes: x faces on the rows of the tile + 1 ring (face f
+    // between staged columns f and f + 1), y faces on its columns
+    for (int e = threadIdx.x; e < NX1 + NY1; e += blockDim.x) {
+      int oL, oR;
+      if (e < NX1) {
+        const int r = e / (TX + 3), f = e % (TX + 3);
+        oL = (TWO ? r + 1 : 0) * HX + f;
+        oR = oL + 1;
+      } else {
+        const int f = (e - NX1) / (TX + 2), cx = (e - NX1) % (TX + 2);
+        oL = f * HX + cx + 1;
+        oR = oL + HX;
+      }
+      T qL[4], wL[4], qR[4], wR[4], F[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        qL[a] = qs[a * PQ + oL];
+        wL[a] = ws[a * PQ + oL];
+        qR[a] = qs[a * PQ + oR];
+        wR[a] = ws[a * PQ + oR];
+      }
+      if (e < NX1) {
+        rusanov_p<T, 0>(qL, wL, qR, wR, F);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fx[a * NX1 + e] = F[a];
+      } else {
+        rusanov_p<T, 1>(qL, wL, qR, wR, F);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fy[a * NY1 + (e - NX1)] = F[a];
+      }
+    }
+    __syncthreads();
+    // stage 1 on the tile and its one-cell ring (positions inside the
+    // domain after periodic wrap)
+    for (int idx = threadIdx.x; idx < P1; idx += blockDim.x) {
+      const int ly = idx / H1X, lx = idx % H1X;
+      const int gi = x0 + lx - 1, gj = TWO ? y0 + ly - 1 : 0;
+      const bool inx = (gi >= 0 && gi < c.nx) || perx;
+      const bool iny = !TWO || (gj >= 0 && gj < c.ny) || pery;
+      if (!(inx && iny)) continue;
+      const int sc = (TWO ? ly + 1 : 0) * HX + lx + 1;
+      const int eL = ly * (TX + 3) + lx, eB = ly * (TX + 2) + lx;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T r = -(fx[a * NX1 + eL + 1] - fx[a * NX1 + eL]) / dxT;
+        if (TWO) r = r - (fy[a * NY1 + eB + TX + 2] - fy[a * NY1 + eB]) / dyT;
+        q1s[a * P1 + idx] = qs[a * PQ + sc] + dt * r;
+      }
+    }
+    __syncthreads();
+    // boundary values of the stage-1 state at t_k on non-periodic sides
+    for (int idx = threadIdx.x; idx < P1; idx += blockDim.x) {
+      const int ly = idx / H1X, lx = idx % H1X;
+      const int gi = x0 + lx - 1, gj = TWO ? y0 + ly - 1 : 0;
+      const bool outx = !((gi >= 0 && gi < c.nx) || perx);
+      const bool outy = TWO && !((gj >= 0 && gj < c.ny) || pery);
+      if (outx == outy) continue;  // inside, or an unused corner
+      const int side = outx ? (gi < 0 ? 0 : 1) : (gj < 0 ? 2 : 3);
+      if (c.bc[side] == HYROM_BC_SHOCK) {
+        T s4[4];
+        shock_state<T>(c, gi, gj, t1, s4);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) q1s[a * P1 + idx] = s4[a];
+      } else {
+        const int cx = outx ? (gi < 0 ? lx + 1 : lx - 1) : lx;
+        const int cy = outy ? (gj < 0 ? ly + 1 : ly - 1) : ly;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) q1s[a * P1 + idx] = q1s[a * P1 + cy * H1X + cx];
+      }
+    }
+    __syncthreads();
+    // primitives of the stage-1 state (the unused corners of the ring
+    // excepted)
+    for (int idx = threadIdx.x; idx < P1; idx += blockDim.x) {
+      const int ly = idx / H1X, lx = idx % H1X;
+      if (TWO && (lx == 0 || lx == H1X - 1) && (ly == 0 || ly == H1Y - 1)) continue;
+      T v[4], w[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v[a] = q1s[a * P1 + idx];
+      prims(v, g, w[0], w[1], w[2], w[3]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ws[a * P1 + idx] = w[a];
+    }
+    __syncthreads();
+    // stage-2 face fluxes on the tile
+    for (int e = threadIdx.x; e < NX2 + NY2; e += blockDim.x) {
+      int oL, oR;
+      if (e < NX2) {
+        const int r = e / (TX + 1), f = e % (TX + 1);
+        oL = (TWO ? r + 1 : 0) * H1X + f;
+        oR = oL + 1;
+      } else {
+        const int f = (e - NX2) / TX, cx = (e - NX2) % TX;
+        oL = f * H1X + cx + 1;
+        oR = oL + H1X;
+      }
+      T qL[4], wL[4], qR[4], wR[4], F[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        qL[a] = q1s[a * P1 + oL];
+        wL[a] = ws[a * P1 + oL];
+        qR[a] = q1s[a * P1 + oR];
+        wR[a] = ws[a * P1 + oR];
+      }
+      if (e < NX2) {
+        rusanov_p<T, 0>(qL, wL, qR, wR, F);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fx[a * NX2 + e] = F[a];
+      } else {
+        rusanov_p<T, 1>(qL, wL, qR, wR, F);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fy[a * NY2 + (e - NX2)] = F[a];
+      }
+    }
+    __syncthreads();
+    // stage 2 on the tile
+    for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+      const int ly = idx / TX, lx = idx % TX;
+      const int gi = x0 + lx, gj = y0 + ly;
+      if (gi >= c.nx || gj >= c.ny) continue;
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      if (mask && !bit_get(mask, cell)) continue;
+      const int s1 = (TWO ? ly + 1 : 0) * H1X + lx + 1;
+      const int s0 = (TWO ? ly + 2 : 0) * HX + lx + 2;
+      const int eL = ly * (TX + 1) + lx, eB = ly * TX + lx;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T r = -(fx[a * NX2 + eL + 1] - fx[a * NX2 + eL]) / dxT;
+        if (TWO) r = r - (fy[a * NY2 + eB + TX] - fy[a * NY2 + eB]) / dyT;
+        out[a * c.nc + cell] = (T)0.5 * qs[a * PQ + s0] + (T)0.5 * (q1s[a * P1 + s1] + dt * r);
+      }
+    }
+  }
+}
+
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
                 const int* tiles, const int* ntiles_dev, cudaStream_t s) {
@@ -128,10 +320,16 @@ void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* 
   int grid = tiles ? (nt < 152 * 8 ? nt : 152 * 8) : nt;
   if (grid < 1) grid = 1;
   if (c.nvar == 4) {
-    if (twoD)
-      k_rk2_tile<T, 4, 32, 8><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
-    else
-      k_rk2_tile<T, 4, 256, 1><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+    if (twoD) {
+      constexpr size_t sm = rk2_euler_smem<T, 32, 8>();
+      smem_at_least((const void*)k_rk2_euler<T, 32, 8>, sm);
+      k_rk2_euler<T, 32, 8><<<grid, 256, sm, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);
+    } else {
+      constexpr size_t sm = rk2_euler_smem<T, 256, 1>();
+      smem_at_least((const void*)k_rk2_euler<T, 256, 1>, sm);
+      k_rk2_euler<T, 256, 1><<<grid, 256, sm, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev,
+                                                          nt);
+    }
   } else {
     if (twoD)
       k_rk2_tile<T, 1, 32, 8><<<grid, 256, 0, HY_S(s)>>>(c, q, out, k, mask, tiles, ntiles_dev, nt);

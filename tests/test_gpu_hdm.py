@@ -16,8 +16,12 @@ pytestmark = pytest.mark.gpu
 def _cases():
     q, c, _ = W.euler_vortex(n=40, seed=3)
     yield "vortex40", q, c.with_(nx=40, ny=40)
+    q, c, _ = W.euler_vortex(n=45, seed=4)      # tiles ragged in x and y, periodic
+    yield "vortex45", q, c
     q, c, _ = W.euler_oblique_shock(n=72, seed=4, k=4)
     yield "shock72", q, c
+    q, c, _ = W.euler_oblique_shock(n=45, seed=6, k=4)   # ragged, shock and outflow sides
+    yield "shock45", q, c
     q, c = W.euler_riemann_x(n=200)
     yield "sod200", q, c
     u, c, _ = W.burgers_sine(n=300, seed=2)
