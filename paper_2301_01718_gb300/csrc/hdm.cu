@@ -160,13 +160,22 @@ __global__ void __launch_bounds__(256) k_rk2_euler(DevCfg c, const T* __restrict
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const int tile = tiles ? tiles[it] : it;
     const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    // every staged cell inside the domain: plain loads, no ghost values
+    const bool interior = x0 >= 2 && x0 + TX + 2 <= c.nx &&
+                          (!TWO || (y0 >= 2 && y0 + TY + 2 <= c.ny));
     __syncthreads();
     // q on the tile and its two-cell ring (ghost values at t_{k-1}), and
     // the primitives of each staged cell
     for (int idx = threadIdx.x; idx < PQ; idx += blockDim.x) {
       const int sy = idx / HX, sx = idx % HX;
       T v[4], w[4];
-      fetch<T, 4>(c, q, x0 + sx - 2, TWO ? y0 + sy - 2 : 0, t0, v);
+      if (interior) {
+        const int64_t cell = (int64_t)(TWO ? y0 + sy - 2 : 0) * c.nx + (x0 + sx - 2);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = q[a * c.nc + cell];
+      } else {
+        fetch<T, 4>(c, q, x0 + sx - 2, TWO ? y0 + sy - 2 : 0, t0, v);
+      }
       prims(v, g, w[0], w[1], w[2], w[3]);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -226,7 +235,8 @@ __global__ void __launch_bounds__(256) k_rk2_euler(DevCfg c, const T* __restrict
     }
     __syncthreads();
     // boundary values of the stage-1 state at t_k on non-periodic sides
-    for (int idx = threadIdx.x; idx < P1; idx += blockDim.x) {
+    // (none on an interior tile)
+    for (int idx = interior ? P1 : threadIdx.x; idx < P1; idx += blockDim.x) {
       const int ly = idx / H1X, lx = idx % H1X;
       const int gi = x0 + lx - 1, gj = TWO ? y0 + ly - 1 : 0;
       const bool outx = !((gi >= 0 && gi < c.nx) || perx);
@@ -320,6 +330,9 @@ void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* 
   int grid = tiles ? (nt < 152 * 8 ? nt : 152 * 8) : nt;
   if (grid < 1) grid = 1;
   if (c.nvar == 4) {
+    // persistent CTAs (six fit per SM), each looping over tiles: the run
+    // constants are converted once per CTA rather than once per tile
+    if (grid > 152 * 6) grid = 152 * 6;
     if (twoD) {
       constexpr size_t sm = rk2_euler_smem<T, 32, 8>();
       smem_at_least((const void*)k_rk2_euler<T, 32, 8>, sm);
