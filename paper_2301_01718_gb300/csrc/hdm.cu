@@ -330,9 +330,6 @@ void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* 
   int grid = tiles ? (nt < 152 * 8 ? nt : 152 * 8) : nt;
   if (grid < 1) grid = 1;
   if (c.nvar == 4) {
-    // persistent CTAs (six fit per SM), each looping over tiles: the run
-    // constants are converted once per CTA rather than once per tile
-    if (grid > 152 * 6) grid = 152 * 6;
     if (twoD) {
       constexpr size_t sm = rk2_euler_smem<T, 32, 8>();
       smem_at_least((const void*)k_rk2_euler<T, 32, 8>, sm);
