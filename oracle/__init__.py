@@ -10,7 +10,7 @@ module is workloads.py, which holds seeded inputs and no method arithmetic.
 Every function follows the paper's definitions in the paper's order, with
 numpy/LAPACK primitives (matmul, SVD, eigh, lstsq, solve) as steps and no
 blocking or fusion.  Where the paper is silent the reading taken is stated in
-the docstring and listed in the design doc.
+the docstring of the function that takes it.
 
 Modules
   hdm     - conservation laws, FV fluxes, residual R_k (Eq. hdm), BDF1 /

@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 State kept between steps: the last w+1 snapshots gamma_{k-w}..gamma_k, the
 basis Phi, points P, reference state psi and sampling sets in effect.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * explicit schemes (SSP-RK2): the partial HDM is S-hat^T gamma_k =
     S-hat^T RK2(gamma_{k-1}), exact with no subiterations (the remark on
     explicit time marching); its stencil reaches two cells.

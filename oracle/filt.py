@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * the explicit Shapiro filter of order 2n has the frequency response
     1 - sin^{2n}(theta/2):  u~ = u - (-1)^n (delta^2)^n u / 4^n with
     delta^2 u_i = u_{i-1} - 2 u_i + u_{i+1}.  Weights (times 4^n):

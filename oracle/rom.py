@@ -16,7 +16,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
                  form of the sample-row solve); round_tf32, round_bf16 and
                  split_tf32 are those roundings, bit for bit
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * numerical rank: mode j is kept when sigma_j > pod_tol * sigma_1 and
     sigma_j > pod_abs * ||X_raw||_F (the Frobenius norm of the uncentred
     window), so a window that differs from psi only by rounding noise has

@@ -4,7 +4,7 @@ S-hat) and Sec. 2.4 / Algorithm 1 (union, setdiff, Neighbors; Fig. 1).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * the selection unit is the cell: eps_cell = sum over the c variables of
     the pointwise squared error (the paper indexes dofs; a FV cell is solved
     with all its variables).
