@@ -69,7 +69,8 @@ def parse():
                    help="timed hybrid steps per instance in each batching-form arm")
     p.add_argument("--batch-threads", default="1,4,8,16",
                    help="host-thread counts timed in the batching form (1 = one at a time)")
-    p.add_argument("--micro", choices=["sample_gram", "batch", "full_step"], default=None,
+    p.add_argument("--micro", choices=["sample_gram", "batch", "full_step", "np_sweep",
+                                       "vortex512"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
     return p.parse_args()
@@ -312,6 +313,12 @@ def run_ours(a):
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
                 "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": traffic,
                 "bytes_per_launch": byts[dom], "peak_source": peaks["src"]}
+    # the step without ODEIM (a7): the step time less the DEIM and ODEIM stage
+    # times (the method's own step recomputes the points every step)
+    a7 = sum(per[n]["ms_per_step"] for n in ("odeim", "deim") if n in per)
+    no_a7 = {"ms_per_step": ms_max / a.steps - a7, "steps_per_s": 1e3 / (ms_max / a.steps - a7),
+             "odeim_ms_per_step": a7,
+             "note": "derived: step time minus the DEIM and ODEIM stage times"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -319,7 +326,8 @@ def run_ours(a):
            "sampled_cell_updates_per_s": world * ns_sum / (ms_max / 1e3),
            "n_s_avg": n_s_avg, "m_eff": m_eff, "stages": per,
            "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e,
-           "odeim_counters_last_step": odc, "eig_sweeps_last_step": eig_sw}
+           "odeim_counters_last_step": odc, "eig_sweeps_last_step": eig_sw,
+           "without_odeim": no_a7}
     if rank == 0 and not a.no_err:
         out["err_vs_fp64"] = err_vs_fp64(a)
     if rank == 0 and not a.no_precision_form:
@@ -574,6 +582,70 @@ def full_step(a, calls=20, pairs=4):
             "peak_gbs": peaks["hbm"], "frac": gbs / peaks["hbm"], "peak_source": peaks["src"]}
 
 
+def time_hybrid_steps(q0, cfg, steps=4, warmup=2):
+    """ms per hybrid step (CUDA events on the context stream) and per-stage
+    ms per step of one context, after the method's own warm-up."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    stream = torch.cuda.Stream()
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q0d, stream=stream.cuda_stream)
+    del q0d
+    try:
+        while hyrom.hyrom_step(ctx)["was_full"]:
+            pass
+        for _ in range(warmup):
+            hyrom.hyrom_step(ctx)
+        hyrom.hyrom_profile(ctx, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns = 0
+        for _ in range(steps):
+            ns += hyrom.hyrom_step(ctx)["n_s"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = hyrom.hyrom_stage_times(ctx)
+        hyrom.hyrom_profile(ctx, False)
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    ms = e0.elapsed_time(e1) / steps
+    return ms, {k: v[0] / steps for k, v in st.items() if v[1]}, ns / steps
+
+
+def np_sweep(a, values=(64, 96, 128, 160, 192), steps=4):
+    """n_p sensitivity: the benchmark workload with n_p ODEIM points (k = 64;
+    n_p <= 194 keeps the sampled pseudo-inverse in one CTA's shared memory)."""
+    from paper_2301_01718_gb300 import build
+    build.build()
+    out = {}
+    for n_p in values:
+        q0, cfg = workload(a)
+        cfg = cfg.with_(n_p=n_p)
+        ms, st, ns = time_hybrid_steps(q0, cfg, steps)
+        out[str(n_p)] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "n_s_avg": ns,
+                         "odeim_ms": st.get("odeim", 0.0), "deim_ms": st.get("deim", 0.0)}
+    return {"workload": config_dict(a, cfg)["workload"], "steps": steps, "n_p": out}
+
+
+def vortex512(a, steps=10):
+    """The isentropic-vortex configuration (512^2 periodic Euler, k = 20,
+    w = 40, 5 % sample, FP32): hybrid steps/s and the stage times.  Its
+    snapshot window (4 x 512^2 x 41 x 4 B = 172 MB) is about L2's size, so
+    the window passes run partly from L2: compare their GB/s with the 2048^2
+    run's."""
+    from paper_2301_01718_gb300 import build
+    build.build()
+    q0, cfg, _ = W.euler_vortex(n=512, seed=2)
+    ms, st, ns = time_hybrid_steps(q0, cfg, steps)
+    byts = stage_bytes(cfg, cfg.m, ns)
+    gbs = {n: byts[n] / (st[n] * 1e-3) / 1e9 for n in byts if n in st and st[n] > 0}
+    return {"workload": f"euler2d_vortex_{cfg.nx}x{cfg.ny}_k{cfg.m}_w{cfg.w}_top0.05",
+            "ms_per_step": ms, "steps_per_s": 1e3 / ms, "n_s_avg": ns,
+            "stages_ms": st, "stage_gbs": gbs,
+            "window_bytes": 4 * cfg.ndof * (cfg.w + 1)}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -602,6 +674,10 @@ def main():
         out = {"micro": "batch", **batch_form(a)}
     elif a.micro == "full_step":
         out = {"micro": "full_step", **full_step(a)}
+    elif a.micro == "np_sweep":
+        out = {"micro": "np_sweep", **np_sweep(a)}
+    elif a.micro == "vortex512":
+        out = {"micro": "vortex512", **vortex512(a)}
     else:
         out = run_reference(a) if a.impl == "reference" else run_ours(a)
     if out is not None:
