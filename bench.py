@@ -607,6 +607,7 @@ def time_hybrid_steps(q0, cfg, steps=4, warmup=2):
         torch.cuda.synchronize()
         st = hyrom.hyrom_stage_times(ctx)
         hyrom.hyrom_profile(ctx, False)
+        time_hybrid_steps.odeim_counters = hyrom.hyrom_odeim_counters(ctx)
     finally:
         hyrom.hyrom_destroy(ctx)
     ms = e0.elapsed_time(e1) / steps
@@ -624,7 +625,8 @@ def np_sweep(a, values=(64, 96, 128, 160, 192), steps=4):
         cfg = cfg.with_(n_p=n_p)
         ms, st, ns = time_hybrid_steps(q0, cfg, steps)
         out[str(n_p)] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "n_s_avg": ns,
-                         "odeim_ms": st.get("odeim", 0.0), "deim_ms": st.get("deim", 0.0)}
+                         "odeim_ms": st.get("odeim", 0.0), "deim_ms": st.get("deim", 0.0),
+                         "odeim_counters_last_step": time_hybrid_steps.odeim_counters}
     return {"workload": config_dict(a, cfg)["workload"], "steps": steps, "n_p": out}
 
 
@@ -643,6 +645,7 @@ def vortex512(a, steps=10):
     return {"workload": f"euler2d_vortex_{cfg.nx}x{cfg.ny}_k{cfg.m}_w{cfg.w}_top0.05",
             "ms_per_step": ms, "steps_per_s": 1e3 / ms, "n_s_avg": ns,
             "stages_ms": st, "stage_gbs": gbs,
+            "odeim_counters_last_step": time_hybrid_steps.odeim_counters,
             "window_bytes": 4 * cfg.ndof * (cfg.w + 1)}
 
 
