@@ -63,3 +63,28 @@ def test_single_rank_rate():
     import bench
     assert bench.max_over_ranks(42.0, 1, "cpu") == 42.0
     assert bench.whole_job_rate(10, 1, 500.0) == pytest.approx(20.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference on a tiny oracle sample prints one JSON line
+    with the contract's keys, the reference arm's e2e and cpu_baseline, and
+    the same metric and workload as the GPU arm."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--cpu-n", "8"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    for key in ("value", "n_gpus", "steps", "warmup", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["config"]["workload"].startswith("euler2d_oblique_shock_2048x2048")
