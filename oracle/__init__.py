@@ -21,4 +21,8 @@ Modules
             sampling-set algebra (union, setdiff, Neighbors)        [Sec. 2.3.3, 2.4]
   filt    - Shapiro filters and the residual-gated filter loop     [Sec. 2.3.4]
   arom    - Algorithm 1 driver and the metrics of Sec. 3.1
+  tangent - tangent-linear model of Algorithm 1 with the forward run's
+            decisions held (the differentiation form): JVPs of the HDM
+            step, gappy coordinates, POD and filter; dJ/dtheta of a
+            time-integrated output
 """

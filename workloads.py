@@ -214,6 +214,45 @@ def euler_batch(n_inst=64, seed=5, nmin=128, nmax=1024, kmin=8, kmax=48, fmin=0.
     return out
 
 
+# Parameters of the differentiation form's initial state, in order: vortex
+# strength beta, vortex centre x0, y0, vortex radius R, pulse amplitude,
+# pulse centre xp, yp, free-stream Mach number.  The default centre sits
+# off the grid's mirror lines: a vortex centred on a face line gives mirror
+# cells equal wave speeds, where the Rusanov flux is not differentiable.
+VORTEX_THETA_NAMES = ("beta", "x0", "y0", "radius", "pulse_amp", "pulse_x", "pulse_y", "mach")
+VORTEX_THETA0 = (5.0, 5.13, 4.87, 1.0, 0.2, 3.5, 6.0, 0.5)
+
+
+def euler_vortex_theta(n, theta, gamma=1.4, L=10.0):
+    """The isentropic vortex plus density pulse of euler_vortex as a function
+    of its parameters theta (VORTEX_THETA_NAMES) on the periodic [0, L]^2
+    with n x n cells: with r = |x - x_c| / R,
+      u = u_inf - beta/(2 pi) exp((1 - r^2)/2) (y - y0)/R,
+      v = v_inf + beta/(2 pi) exp((1 - r^2)/2) (x - x0)/R,
+      T = 1 - (gamma - 1) beta^2 / (8 gamma pi^2) exp(1 - r^2),
+      rho = T^(1/(gamma - 1)) + A exp(-|x - x_p|^2 / 0.25),  p = T^(gamma/(gamma-1)),
+    free stream along the diagonal at Mach M (|u_inf| = M sqrt(gamma)).
+    R = 1 and theta = (5, 5, 5, 1, 0.2, xp, yp, 0.5) give euler_vortex.
+    Every operation is analytic in theta, so a complex theta gives the
+    derivative by the complex step.  Returns q0 [4, n*n]."""
+    beta, x0, y0, R, amp, xp, yp, mach = theta
+    dx = L / n
+    xc = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(xc, xc, indexing="xy")
+    cinf = math.sqrt(gamma)
+    uinf = mach * cinf / math.sqrt(2.0)
+    xr, yr = (X - x0) / R, (Y - y0) / R
+    r2 = xr * xr + yr * yr
+    g = beta / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    u = uinf - g * yr
+    v = uinf + g * xr
+    T = 1.0 - (gamma - 1.0) * beta * beta / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    rho = rho + amp * np.exp(-((X - xp) ** 2 + (Y - yp) ** 2) / 0.25)
+    return _conserved(gamma, rho, u, v, p).reshape(4, n * n)
+
+
 def normal_shock_states(gamma, mach, rho1, p1):
     """Pre/post states of a normal shock of Mach `mach` moving into gas at
     rest (Rankine-Hugoniot jump relations).  Returns (rho2, u2, p2, speed)."""
