@@ -288,6 +288,22 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
 hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
                                int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
 
+/* ---- differentiation form ---------------------------------------------------
+ * hyrom_stage_rk2_vjp: the adjoint of one SSP-RK2 HDM step of the Euler
+ * equations (Sec. 2.2, the explicit scheme; Sec. 3.1, Rusanov flux): with
+ * q_k = RK2_k(q_prev) on the cells of s_hat and q_prev elsewhere (the partial
+ * HDM step of Algorithm 1; s_hat NULL = every cell, the full step),
+ *   lam_in = (d q_k / d q_prev)^T lam_out.
+ * Ghost cells: shock sides are fixed states (no share), outflow sides copy
+ * their boundary cell (its share goes to that cell), periodic sides wrap;
+ * at a tie of the two Rusanov wave speeds the left one is differentiated.
+ * q_prev, lam_out, lam_in: N doubles each (dev, SoA), lam_in distinct from
+ * both; work: 3 N doubles of device scratch (caller-owned); s_hat: cell
+ * bitmap (dev) or NULL.  FP64 Euler SSP-RK2 contexts only (else
+ * HYROM_EINVAL).  Synchronises. */
+hyrom_status hyrom_stage_rk2_vjp(hyrom_ctx* ctx, const void* q_prev, const void* lam_out,
+                                 void* lam_in, const uint32_t* s_hat, int64_t k, void* work);
+
 /* ---- batching form ---------------------------------------------------------
  * Many independent instances of Algorithm 1 (each its own context, grid,
  * basis size, window and sample fraction) stepped together by a pool of host

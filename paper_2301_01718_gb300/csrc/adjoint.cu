@@ -1,0 +1,235 @@
+// Adjoint (vector-Jacobian product) of the SSP-RK2 Euler HDM step, full or
+// restricted to the sampled cells: the first piece of the differentiation
+// form.  For the step
+//   q1 = q + dt L(q, t_{k-1}),   q_k = q/2 + (q1 + dt L(q1, t_k))/2
+// (Sec. 2.2, the explicit scheme of the run configurations), a cotangent
+// lambda of q_k pulls back to
+//   lambda_1 = lambda/2 + (dt/2) L'(q1)^T lambda,
+//   lambda_q = lambda/2 + lambda_1 + dt L'(q)^T lambda_1.
+// The partial step of Algorithm 1 replaces only the cells of S-hat, so
+// there lambda is first restricted to S-hat and the other cells pass their
+// lambda through unchanged.
+//
+// L'(q)^T mu is a gather per cell over its faces.  L_i = -(F_{i+1/2} -
+// F_{i-1/2})/dx - (G_{j+1/2} - G_{j-1/2})/dy, so a face carries the
+// cotangent Fbar_{i+1/2} = (mu_{i+1} - mu_i)/dx (mu = 0 at a ghost cell) and
+// passes dF/dq_side^T Fbar to each side's cell; an outflow ghost is a copy
+// of its boundary cell and passes its share to that cell too; a shock
+// ghost is a fixed state and passes nothing; periodic sides wrap.  The face
+// Jacobians come from the Rusanov flux's tangent (primitives, flux, wave
+// speed; at a tie of the two wave speeds the left one is differentiated)
+// applied to the unit vectors.  FP64 throughout.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "phys.cuh"
+
+namespace hy {
+
+namespace {
+
+// tangent of the primitives (u, v, p, c) along dq
+HY_DEV void prims_tan(const double* q, const double* dq, double g, double* w, double* dw) {
+  const double u = q[1] / q[0], v = q[2] / q[0];
+  const double du = (dq[1] - u * dq[0]) / q[0];
+  const double dv = (dq[2] - v * dq[0]) / q[0];
+  const double k2 = u * u + v * v;
+  const double p = (g - 1.0) * (q[3] - 0.5 * q[0] * k2);
+  const double dp = (g - 1.0) * (dq[3] - 0.5 * dq[0] * k2 - q[0] * (u * du + v * dv));
+  const double a2 = g * p / q[0];
+  const double da2 = g * (dp - p * dq[0] / q[0]) / q[0];
+  const double c = sqrt(a2 > 0.0 ? a2 : 0.0);
+  w[0] = u;
+  w[1] = v;
+  w[2] = p;
+  w[3] = c;
+  dw[0] = du;
+  dw[1] = dv;
+  dw[2] = dp;
+  dw[3] = (a2 > 0.0 && c > 0.0) ? 0.5 * da2 / c : 0.0;
+}
+
+HY_DEV double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// tangent of the Rusanov flux across an AX face along (dqL, dqR)
+template <int AX>
+HY_DEV void rusanov_tan(const double* qL, const double* dqL, const double* qR, const double* dqR,
+                        double g, double* dF) {
+  double wL[4], dwL[4], wR[4], dwR[4];
+  prims_tan(qL, dqL, g, wL, dwL);
+  prims_tan(qR, dqR, g, wR, dwR);
+  double dfL[4], dfR[4];
+  const double* W[2] = {wL, wR};
+  const double* DW[2] = {dwL, dwR};
+  const double* Q[2] = {qL, qR};
+  const double* DQ[2] = {dqL, dqR};
+  double* DF[2] = {dfL, dfR};
+  for (int s = 0; s < 2; ++s) {
+    const double *q = Q[s], *dq = DQ[s], *w = W[s], *dw = DW[s];
+    double* df = DF[s];
+    if (AX == 0) {
+      df[0] = dq[1];
+      df[1] = dq[1] * w[0] + q[1] * dw[0] + dw[2];
+      df[2] = dq[2] * w[0] + q[2] * dw[0];
+      df[3] = (dq[3] + dw[2]) * w[0] + (q[3] + w[2]) * dw[0];
+    } else {
+      df[0] = dq[2];
+      df[1] = dq[1] * w[1] + q[1] * dw[1];
+      df[2] = dq[2] * w[1] + q[2] * dw[1] + dw[2];
+      df[3] = (dq[3] + dw[2]) * w[1] + (q[3] + w[2]) * dw[1];
+    }
+  }
+  const double nL = AX == 0 ? wL[0] : wL[1], nR = AX == 0 ? wR[0] : wR[1];
+  const double dnL = AX == 0 ? dwL[0] : dwL[1], dnR = AX == 0 ? dwR[0] : dwR[1];
+  const double sL = fabs(nL) + wL[3], sR = fabs(nR) + wR[3];
+  const double a = sL > sR ? sL : sR;
+  const double da = sL >= sR ? sgn(nL) * dnL + dwL[3] : sgn(nR) * dnR + dwR[3];
+  for (int r = 0; r < 4; ++r)
+    dF[r] = 0.5 * (dfL[r] + dfR[r]) - 0.5 * (da * (qR[r] - qL[r]) + a * (dqR[r] - dqL[r]));
+}
+
+// acc += (dF/dq_side)^T fbar for the face (qL, qR); side 0 = left, 1 = right
+template <int AX>
+HY_DEV void face_pullback(const double* qL, const double* qR, double g, int side,
+                          const double* fbar, double* acc) {
+  const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c = 0; c < 4; ++c) {
+    double e[4] = {0.0, 0.0, 0.0, 0.0};
+    e[c] = 1.0;
+    double dF[4];
+    if (side == 0)
+      rusanov_tan<AX>(qL, e, qR, zero, g, dF);
+    else
+      rusanov_tan<AX>(qL, zero, qR, e, g, dF);
+    acc[c] += dF[0] * fbar[0] + dF[1] * fbar[1] + dF[2] * fbar[2] + dF[3] * fbar[3];
+  }
+}
+
+// mu at grid position (gi, gj): a domain cell (wrapped on periodic sides) or
+// 0 at a ghost
+HY_DEV void mu_at(const DevCfg& c, const double* mu, int gi, int gj, double* out) {
+  bool ghost = false;
+  if (gi < 0 || gi >= c.nx) {
+    if (c.bc[0] == HYROM_BC_PERIODIC)
+      gi = imod(gi, c.nx);
+    else
+      ghost = true;
+  }
+  if (c.ny > 1 && (gj < 0 || gj >= c.ny)) {
+    if (c.bc[2] == HYROM_BC_PERIODIC)
+      gj = imod(gj, c.ny);
+    else
+      ghost = true;
+  }
+  for (int v = 0; v < 4; ++v) out[v] = ghost ? 0.0 : mu[v * c.nc + (int64_t)gj * c.nx + gi];
+}
+
+// out = c1 b1 + c2 b2 + c3 b3 + coef L'(q, t)^T mu   (b2, b3 may be null)
+__global__ void k_rhs_vjp(DevCfg c, const double* __restrict__ q, const double* __restrict__ mu,
+                          double t, double coef, const double* __restrict__ b1, double c1,
+                          const double* __restrict__ b2, double c2,
+                          const double* __restrict__ b3, double c3, double* __restrict__ out) {
+  const bool twoD = c.ny > 1;
+  const double g = c.gamma;
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < c.nc;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    const int gi = (int)(cell % c.nx), gj = (int)(cell / c.nx);
+    double qC[4], m0[4], acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int v = 0; v < 4; ++v) {
+      qC[v] = q[v * c.nc + cell];
+      m0[v] = mu[v * c.nc + cell];
+    }
+    for (int ax = 0; ax < (twoD ? 2 : 1); ++ax) {
+      const double inv = ax == 0 ? 1.0 / c.dx : 1.0 / c.dy;
+      for (int s = 0; s < 2; ++s) {  // s = 0: the face below (left), 1: above (right)
+        const int ni = ax == 0 ? gi + (s ? 1 : -1) : gi;
+        const int nj = ax == 1 ? gj + (s ? 1 : -1) : gj;
+        double qN[4], mN[4], fbar[4];
+        fetch<double, 4>(c, q, ni, nj, t, qN);
+        mu_at(c, mu, ni, nj, mN);
+        // Fbar of the face: (mu_right - mu_left) / h
+        for (int v = 0; v < 4; ++v) fbar[v] = s ? (mN[v] - m0[v]) * inv : (m0[v] - mN[v]) * inv;
+        const double* qL = s ? qC : qN;
+        const double* qR = s ? qN : qC;
+        // this cell is the right state of the face below, the left of the one above
+        if (ax == 0)
+          face_pullback<0>(qL, qR, g, s ? 0 : 1, fbar, acc);
+        else
+          face_pullback<1>(qL, qR, g, s ? 0 : 1, fbar, acc);
+        // an outflow ghost is a copy of this cell: its side of the face too
+        const bool outside = ax == 0 ? (ni < 0 || ni >= c.nx) : (nj < 0 || nj >= c.ny);
+        const int side = ax == 0 ? (ni < 0 ? 0 : 1) : (nj < 0 ? 2 : 3);
+        if (outside && c.bc[side] == HYROM_BC_OUTFLOW) {
+          if (ax == 0)
+            face_pullback<0>(qL, qR, g, s ? 1 : 0, fbar, acc);
+          else
+            face_pullback<1>(qL, qR, g, s ? 1 : 0, fbar, acc);
+        }
+      }
+    }
+    for (int v = 0; v < 4; ++v) {
+      const int64_t i = v * c.nc + cell;
+      double o = c1 * b1[i];
+      if (b2) o += c2 * b2[i];
+      if (b3) o += c3 * b3[i];
+      out[i] = o + coef * acc[v];
+    }
+  }
+}
+
+// q1 = q + dt L(q, t) (stage 1 of the step, the expressions of rhs_cell)
+__global__ void k_stage1(DevCfg c, const double* __restrict__ q, double t,
+                         double* __restrict__ q1) {
+  const bool twoD = c.ny > 1;
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < c.nc;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    const int gi = (int)(cell % c.nx), gj = (int)(cell / c.nx);
+    double qC[4], qW[4], qE[4], qS[4], qN[4], r[4];
+    for (int v = 0; v < 4; ++v) qC[v] = q[v * c.nc + cell];
+    fetch<double, 4>(c, q, gi - 1, gj, t, qW);
+    fetch<double, 4>(c, q, gi + 1, gj, t, qE);
+    if (twoD) {
+      fetch<double, 4>(c, q, gi, gj - 1, t, qS);
+      fetch<double, 4>(c, q, gi, gj + 1, t, qN);
+    } else {
+      for (int v = 0; v < 4; ++v) qS[v] = qN[v] = qC[v];
+    }
+    rhs_cell<double, 4>(c, qC, qW, qE, qS, qN, r);
+    for (int v = 0; v < 4; ++v) q1[v * c.nc + cell] = qC[v] + c.dt * r[v];
+  }
+}
+
+// lam_m = lambda on the cells of the mask (all cells without one), else 0
+__global__ void k_restrict(DevCfg c, const double* __restrict__ lam, const uint32_t* mask,
+                           double* __restrict__ lam_m) {
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < c.nc;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    const bool in = !mask || bit_get(mask, cell);
+    for (int v = 0; v < 4; ++v) lam_m[v * c.nc + cell] = in ? lam[v * c.nc + cell] : 0.0;
+  }
+}
+
+}  // namespace
+
+void launch_rk2_vjp(const DevCfg& c, const double* q, const double* lam_out, double* lam_in,
+                    const uint32_t* mask, int64_t k, double* work, cudaStream_t s) {
+  const int64_t N = c.ndof;
+  double* q1 = work;
+  double* lam_m = work + N;
+  double* lam1 = work + 2 * N;
+  int64_t blocks = (c.nc + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  const double t0 = (double)(k - 1) * c.dt, t1 = (double)k * c.dt;
+  k_stage1<<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, t0, q1);
+  k_restrict<<<(int)blocks, 256, 0, HY_S(s)>>>(c, lam_out, mask, lam_m);
+  // lambda_1 = lam_m/2 + (dt/2) L'(q1)^T lam_m
+  k_rhs_vjp<<<(int)blocks, 256, 0, HY_S(s)>>>(c, q1, lam_m, t1, 0.5 * c.dt, lam_m, 0.5, nullptr,
+                                              0.0, nullptr, 0.0, lam1);
+  // lambda_q = lam_m/2 + lambda_1 + dt L'(q)^T lambda_1 + (lambda - lam_m)
+  k_rhs_vjp<<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, lam1, t0, c.dt, lam_m, -0.5, lam1, 1.0,
+                                              lam_out, 1.0, lam_in);
+}
+
+}  // namespace hy

@@ -1198,6 +1198,19 @@ hyrom_status hyrom_stage_cell_error(hyrom_ctx* ctx, const void* g, const void* p
   return sync(ctx);
 }
 
+hyrom_status hyrom_stage_rk2_vjp(hyrom_ctx* ctx, const void* q_prev, const void* lam_out,
+                                 void* lam_in, const uint32_t* s_hat, int64_t k, void* work) {
+  GUARD();
+  if (!q_prev || !lam_out || !lam_in || !work || lam_in == lam_out || lam_in == q_prev)
+    return HYROM_EINVAL;
+  if (ctx->f32 || ctx->cfg.scheme != HYROM_SCHEME_RK2 || ctx->cfg.pde != HYROM_PDE_EULER)
+    return fail(ctx, HYROM_EINVAL, "the step adjoint is defined for FP64 Euler SSP-RK2 contexts");
+  hy::launch_rk2_vjp(ctx->dc, (const double*)q_prev, (const double*)lam_out, (double*)lam_in,
+                     s_hat, k, (double*)work, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
 hyrom_status hyrom_stage_select(hyrom_ctx* ctx, const void* eps, uint32_t* g_bitmap,
                                 int32_t* n_g) {
   GUARD();

@@ -91,6 +91,13 @@ void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
                                    const double* tol_dev, int newton_max, double* ws, int* fail,
                                    cudaStream_t s);
 
+// adjoint.cu: lam_in = (d q_k / d q_prev)^T lam_out for the SSP-RK2 Euler
+// step k (FP64), restricted to the cells of mask (the partial step; the
+// other cells pass lam_out through) or the full step (mask null); work
+// holds 3 N doubles
+void launch_rk2_vjp(const DevCfg& c, const double* q, const double* lam_out, double* lam_in,
+                    const uint32_t* mask, int64_t k, double* work, cudaStream_t s);
+
 // filter.cu
 // fargs: device memory (64 bytes) for the per-call arguments; graph
 // (nullable): the passes kept as one CUDA graph (the other arguments must

@@ -137,6 +137,7 @@ def lib():
         "hyrom_stage_gappy_rows": (st, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
         "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
+        "hyrom_stage_rk2_vjp": (st, [vp, vp, vp, vp, vp, i64, vp]),
         "hyrom_batch_create": (st, [C.POINTER(vp), i32, i32, C.POINTER(vp)]),
         "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
         "hyrom_batch_threads": (i32, [vp]),
@@ -368,3 +369,10 @@ def hyrom_batch_threads(batch):
 
 def hyrom_batch_destroy(batch):
     lib().hyrom_batch_destroy(batch)
+
+
+def hyrom_stage_rk2_vjp(ctx, q_prev, lam_out, lam_in, s_hat, k, work):
+    """lam_in = (d q_k / d q_prev)^T lam_out for the SSP-RK2 step k (partial on
+    s_hat, or full when s_hat is None); work: 3 N doubles of device scratch."""
+    _check(ctx, lib().hyrom_stage_rk2_vjp(ctx, _ptr(q_prev), _ptr(lam_out), _ptr(lam_in),
+                                          _ptr(s_hat), int(k), _ptr(work)))

@@ -1,0 +1,88 @@
+"""The adjoint of the SSP-RK2 Euler step (hyrom_stage_rk2_vjp) against the
+oracle's tangent: the transposed Jacobian assembled column by column from
+the oracle's JVP (oracle/tangent.py) applied to a cotangent, element by
+element (FP64, within 1e-12 of its largest entry), for periodic, shock and
+outflow sides, one and two dimensions, the full step and the partial step
+on S-hat; and the dot-product identity <w, J v> = <J^T w, v> on a grid of
+several thread blocks."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hdm, tangent as T
+from tests.gpu_util import H, dev, dev_bits, host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    n = 12
+    _, cv, _ = W.euler_vortex(n=n, seed=2)
+    yield "vortex12", W.euler_vortex_theta(n, W.VORTEX_THETA0).reshape(4, n, n), \
+        cv.with_(precision=W.PREC_F64, w=4, m=2, n_p=4), 3
+    q0, cs, _ = W.euler_oblique_shock(n=n, seed=3, k=2)
+    cs = cs.with_(precision=W.PREC_F64)
+    yield "shock12", hdm.rk2_step(q0.reshape(4, n, n), cs, 1), cs, 2
+    q0, c1 = W.euler_riemann_x(n=30)
+    c1 = c1.with_(w=4, m=2, n_p=4)
+    yield "sod30", hdm.rk2_step(q0.reshape(4, 1, 30), c1, 1), c1, 2
+
+
+def _jt(q, cfg, k, w):
+    """J^T w of the oracle's step, J assembled from the tangent's columns."""
+    N = q.size
+    out = np.empty(N)
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        _, col = T.rk2_step_jvp(q, e.reshape(q.shape), cfg, k)
+        out[i] = np.dot(col.reshape(-1), w)
+    return out
+
+
+def _gpu_vjp(cfg, q, lam, k, mask=None):
+    hy = H()
+    ctx = hy.hyrom_init(cfg, dev(q.reshape(-1)))
+    try:
+        N = q.size
+        lam_in = torch.zeros(N, dtype=torch.float64, device="cuda")
+        work = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_rk2_vjp(ctx, dev(q.reshape(-1)), dev(lam), lam_in,
+                               None if mask is None else dev_bits(mask), k, work)
+        return host(lam_in)
+    finally:
+        hy.hyrom_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,q,cfg,k", list(_cases()), ids=[c[0] for c in _cases()])
+def test_step_adjoint_matches_the_oracle_transpose(name, q, cfg, k):
+    g = np.random.Generator(np.random.PCG64(7))
+    w = g.standard_normal(q.size)
+    want = _jt(q, cfg, k, w)
+    got = _gpu_vjp(cfg, q, w, k)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_partial_step_adjoint_passes_the_other_cells_through():
+    name, q, cfg, k = list(_cases())[1]
+    g = np.random.Generator(np.random.PCG64(8))
+    mask = g.random(cfg.ncell) < 0.3
+    w = g.standard_normal(q.size)
+    mrows = np.tile(mask, cfg.nvar)
+    want = _jt(q, cfg, k, np.where(mrows, w, 0.0)) + np.where(mrows, 0.0, w)
+    got = _gpu_vjp(cfg, q, w, k, mask)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_dot_product_identity_on_a_larger_grid():
+    n = 40
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=4, m=2, n_p=4)
+    q = W.euler_vortex_theta(n, W.VORTEX_THETA0).reshape(4, n, n)
+    g = np.random.Generator(np.random.PCG64(9))
+    v = g.standard_normal(q.shape)
+    w = g.standard_normal(q.size)
+    _, Jv = T.rk2_step_jvp(q, v, cfg, 2)
+    JTw = _gpu_vjp(cfg, q, w, 2)
+    lhs, rhs = float(np.dot(w, Jv.reshape(-1))), float(np.dot(JTw, v.reshape(-1)))
+    assert abs(lhs - rhs) <= 1e-12 * np.abs(w).sum() * np.abs(Jv).max()
