@@ -86,3 +86,29 @@ def test_dot_product_identity_on_a_larger_grid():
     JTw = _gpu_vjp(cfg, q, w, 2)
     lhs, rhs = float(np.dot(w, Jv.reshape(-1))), float(np.dot(JTw, v.reshape(-1)))
     assert abs(lhs - rhs) <= 1e-12 * np.abs(w).sum() * np.abs(Jv).max()
+
+
+def test_autograd_function_chains_steps():
+    """Two steps through HdmStep (a full step, then a partial step on S-hat)
+    and a weighted sum: q0.grad equals J1^T J2^T w from the oracle."""
+    from paper_2301_01718_gb300.autograd import HdmStep
+    hy = H()
+    name, q, cfg, k = list(_cases())[1]
+    g = np.random.Generator(np.random.PCG64(10))
+    mask = g.random(cfg.ncell) < 0.4
+    w = g.standard_normal(q.size)
+    ctx = hy.hyrom_init(cfg, dev(q.reshape(-1)))
+    try:
+        q0 = dev(q.reshape(-1)).requires_grad_(True)
+        q1 = HdmStep.apply(ctx, q0, k, None)
+        q2 = HdmStep.apply(ctx, q1, k + 1, dev_bits(mask))
+        (q2 * dev(w)).sum().backward()
+        got = host(q0.grad)
+        q1_host = host(q1.detach()).reshape(q.shape)
+    finally:
+        hy.hyrom_destroy(ctx)
+    assert np.array_equal(q1_host, hdm.rk2_step(q, cfg, k))
+    mrows = np.tile(mask, cfg.nvar)
+    lam1 = _jt(q1_host, cfg, k + 1, np.where(mrows, w, 0.0)) + np.where(mrows, 0.0, w)
+    want = _jt(q, cfg, k, lam1)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
