@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--batch-threads", default="1,4,8,16",
                    help="host-thread counts timed in the batching form (1 = one at a time)")
     p.add_argument("--micro", choices=["sample_gram", "batch", "full_step", "np_sweep",
-                                       "vortex512"], default=None,
+                                       "vortex512", "rk2_vjp"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
     return p.parse_args()
@@ -649,6 +649,40 @@ def vortex512(a, steps=10):
             "window_bytes": 4 * cfg.ndof * (cfg.w + 1)}
 
 
+def rk2_vjp(a, n=1024, calls=10):
+    """The adjoint of the SSP-RK2 Euler step (hyrom_stage_rk2_vjp, FP64) on
+    the n^2 vortex of the differentiation form: CUDA events on the legacy
+    stream around each call (its stage-1 recomputation, two L'^T passes and
+    the host synchronisation), ms per call and cells per second."""
+    import torch
+    from paper_2301_01718_gb300 import build, hyrom
+    build.build()
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=4, m=2, n_p=4)
+    q = torch.as_tensor(W.euler_vortex_theta(n, W.VORTEX_THETA0).reshape(-1),
+                        dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q)
+    try:
+        lam = torch.randn(cfg.ndof, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(lam)
+        work = torch.empty(3 * cfg.ndof, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            hyrom.hyrom_stage_rk2_vjp(ctx, q, lam, out, None, 2, work)
+        ms = []
+        for _ in range(calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hyrom.hyrom_stage_rk2_vjp(ctx, q, lam, out, None, 2, work)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    best = min(ms)
+    return {"grid": f"{n}x{n}", "dtype": "f64", "ms_per_call": best,
+            "ms_median": statistics.median(ms), "cells_per_s": cfg.ncell / (best * 1e-3)}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -681,6 +715,8 @@ def main():
         out = {"micro": "np_sweep", **np_sweep(a)}
     elif a.micro == "vortex512":
         out = {"micro": "vortex512", **vortex512(a)}
+    elif a.micro == "rk2_vjp":
+        out = {"micro": "rk2_vjp", **rk2_vjp(a)}
     else:
         out = run_reference(a) if a.impl == "reference" else run_ours(a)
     if out is not None:
