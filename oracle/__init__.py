@@ -25,4 +25,6 @@ Modules
             decisions held (the differentiation form): JVPs of the HDM
             step, gappy coordinates, POD and filter; dJ/dtheta of a
             time-integrated output
+  adjoint - its reverse mode: the transposes of those JVPs and one
+            reverse sweep over the recorded run for dJ/dq0
 """
