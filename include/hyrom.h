@@ -304,6 +304,25 @@ hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const i
 hyrom_status hyrom_stage_rk2_vjp(hyrom_ctx* ctx, const void* q_prev, const void* lam_out,
                                  void* lam_in, const uint32_t* s_hat, int64_t k, void* work);
 
+/* hyrom_stage_reduced_vjp: the adjoint of the reduced step of a hybrid step
+ * (Sec. 2.3.1, Eq. red_coord and the reconstruction of Algorithm 1): with
+ *   y = argmin |Phi[rows] y - (v - psi)[rows]|   and
+ *   v_final = v on the dofs of the cells in s_hat, psi + Phi y elsewhere,
+ * a cotangent lam of v_final pulls back to lam_v (of v), lam_psi (of psi) and
+ * lam_phi (of Phi), all overwritten.  Phi: N x m column-major doubles
+ * (1 <= m <= 64); rows: n_rows >= m distinct dof indices (int32, dev); y: the
+ * m coordinates of the forward step (dev doubles); v, psi, lam, lam_v,
+ * lam_psi: N doubles; lam_phi: N x m; work: hyrom_reduced_vjp_work_doubles(m,
+ * n_rows) doubles of device scratch.  FP64 contexts only.  Synchronises.
+ * Phi[rows] must have full column rank (its normal matrix is factored by
+ * Cholesky). */
+size_t hyrom_reduced_vjp_work_doubles(int32_t m, int32_t n_rows);
+hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
+                                     const int32_t* rows, int32_t n_rows, const void* v,
+                                     const void* psi, const double* y, const uint32_t* s_hat,
+                                     const void* lam, void* lam_v, void* lam_psi, void* lam_phi,
+                                     void* work);
+
 /* ---- batching form ---------------------------------------------------------
  * Many independent instances of Algorithm 1 (each its own context, grid,
  * basis size, window and sample fraction) stepped together by a pool of host

@@ -211,7 +211,157 @@ __global__ void k_restrict(DevCfg c, const double* __restrict__ lam, const uint3
   }
 }
 
+// ---------------------------------------------------------------------------
+// adjoint of the reduced step: v_final = v on the dofs of S-hat and
+// psi + Phi y on the others, y = argmin |Phi[rows] y - (v - psi)[rows]|
+// (Eq. red_coord).  Phi column-major N x m.
+// ---------------------------------------------------------------------------
+
+constexpr int kRedBlocks = 152 * 8;
+
+// split lam into the S-hat part (lam_v) and the reconstructed part lam_rec:
+// lam_psi = lam_rec, lam_phi = lam_rec y^T, and per-block partial sums of
+// Phi^T lam_rec (part[block * m + j])
+__global__ void __launch_bounds__(256) k_red_split(int64_t N, int64_t nc, int m,
+                                                   const double* __restrict__ lam,
+                                                   const uint32_t* __restrict__ s_hat,
+                                                   const double* __restrict__ phi,
+                                                   const double* __restrict__ y,
+                                                   double* __restrict__ lam_v,
+                                                   double* __restrict__ lam_psi,
+                                                   double* __restrict__ lam_phi,
+                                                   double* __restrict__ part) {
+  __shared__ double red[8][64];
+  double acc[64];
+  for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool in = bit_get(s_hat, i % nc);
+    const double l = lam[i];
+    const double lr = in ? 0.0 : l;
+    lam_v[i] = in ? l : 0.0;
+    lam_psi[i] = lr;
+    for (int j = 0; j < m; ++j) {
+      lam_phi[(int64_t)j * N + i] = lr * y[j];
+      acc[j] = fma(phi[(int64_t)j * N + i], lr, acc[j]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < m; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][j];
+    part[(int64_t)blockIdx.x * m + j] = s;
+  }
+}
+
+// one CTA: lam_y = sum of the partials, A = Phi[rows], r = b - A y,
+// z = (A^T A)^{-1} lam_y by Cholesky; writes z (m), Az and r (n_r)
+__global__ void __launch_bounds__(256) k_red_small(int64_t N, int m, const int* __restrict__ rows,
+                                                   int nr, const double* __restrict__ phi,
+                                                   const double* __restrict__ v,
+                                                   const double* __restrict__ psi,
+                                                   const double* __restrict__ y,
+                                                   const double* __restrict__ part, int nblk,
+                                                   double* __restrict__ z,
+                                                   double* __restrict__ Az,
+                                                   double* __restrict__ rvec) {
+  __shared__ double M[64][65];
+  __shared__ double ly[64];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * m + j];
+    ly[j] = s;
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    double s = 0.0;
+    for (int r = 0; r < nr; ++r)
+      s = fma(phi[(int64_t)i * N + rows[r]], phi[(int64_t)j * N + rows[r]], s);
+    M[i][j] = s;
+  }
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    double s = v[rows[r]] - psi[rows[r]];
+    for (int j = 0; j < m; ++j) s -= phi[(int64_t)j * N + rows[r]] * y[j];
+    rvec[r] = s;
+  }
+  __syncthreads();
+  // Cholesky M = L L^T in the lower triangle
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) M[k][k] = sqrt(M[k][k]);
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i][k] /= M[k][k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e % m;
+      if (j > k && i >= j) M[i][j] -= M[i][k] * M[j][k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {  // L w = lam_y, L^T z = w
+    for (int i = 0; i < m; ++i) {
+      double s = ly[i];
+      for (int j = 0; j < i; ++j) s -= M[i][j] * ly[j];
+      ly[i] = s / M[i][i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double s = ly[i];
+      for (int j = i + 1; j < m; ++j) s -= M[j][i] * ly[j];
+      ly[i] = s / M[i][i];
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) z[j] = ly[j];
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s = fma(phi[(int64_t)j * N + rows[r]], ly[j], s);
+    Az[r] = s;
+  }
+}
+
+// the regression rows: lam_phi[rows] += r z^T - (A z) y^T, lam_v[rows] += A z,
+// lam_psi[rows] -= A z (rows distinct)
+__global__ void k_red_rows(int64_t N, int m, const int* __restrict__ rows, int nr,
+                           const double* __restrict__ y, const double* __restrict__ z,
+                           const double* __restrict__ Az, const double* __restrict__ rvec,
+                           double* __restrict__ lam_v, double* __restrict__ lam_psi,
+                           double* __restrict__ lam_phi) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nr * m; e += gridDim.x * blockDim.x) {
+    const int r = e / m, j = e % m;
+    const int64_t row = rows[r];
+    lam_phi[(int64_t)j * N + row] += rvec[r] * z[j] - Az[r] * y[j];
+    if (j == 0) {
+      lam_v[row] += Az[r];
+      lam_psi[row] -= Az[r];
+    }
+  }
+}
+
 }  // namespace
+
+void launch_reduced_vjp(int64_t N, int64_t nc, int m, const double* phi, const int* rows, int nr,
+                        const double* v, const double* psi, const double* y,
+                        const uint32_t* s_hat, const double* lam, double* lam_v, double* lam_psi,
+                        double* lam_phi, double* work, cudaStream_t s) {
+  double* part = work;
+  double* z = part + (size_t)kRedBlocks * m;
+  double* Az = z + 64;
+  double* rvec = Az + nr;
+  k_red_split<<<kRedBlocks, 256, 0, HY_S(s)>>>(N, nc, m, lam, s_hat, phi, y, lam_v, lam_psi,
+                                               lam_phi, part);
+  k_red_small<<<1, 256, 0, HY_S(s)>>>(N, m, rows, nr, phi, v, psi, y, part, kRedBlocks, z, Az,
+                                      rvec);
+  const int blocks = (nr * m + 255) / 256;
+  k_red_rows<<<blocks < 1 ? 1 : blocks, 256, 0, HY_S(s)>>>(N, m, rows, nr, y, z, Az, rvec, lam_v,
+                                                           lam_psi, lam_phi);
+}
+
+size_t reduced_vjp_work_doubles(int m, int nr) { return (size_t)kRedBlocks * m + 64 + 2 * nr; }
 
 void launch_rk2_vjp(const DevCfg& c, const double* q, const double* lam_out, double* lam_in,
                     const uint32_t* mask, int64_t k, double* work, cudaStream_t s) {

@@ -1211,6 +1211,28 @@ hyrom_status hyrom_stage_rk2_vjp(hyrom_ctx* ctx, const void* q_prev, const void*
   return sync(ctx);
 }
 
+size_t hyrom_reduced_vjp_work_doubles(int32_t m, int32_t n_rows) {
+  if (m < 1 || m > 64 || n_rows < 0) return 0;
+  return hy::reduced_vjp_work_doubles(m, n_rows);
+}
+
+hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
+                                     const int32_t* rows, int32_t n_rows, const void* v,
+                                     const void* psi, const double* y, const uint32_t* s_hat,
+                                     const void* lam, void* lam_v, void* lam_psi, void* lam_phi,
+                                     void* work) {
+  GUARD();
+  if (!phi || !rows || !v || !psi || !y || !s_hat || !lam || !lam_v || !lam_psi || !lam_phi ||
+      !work || m < 1 || m > 64 || n_rows < m)
+    return HYROM_EINVAL;
+  if (ctx->f32) return fail(ctx, HYROM_EINVAL, "the reduced-step adjoint runs on FP64 contexts");
+  hy::launch_reduced_vjp(ctx->N, ctx->nc, m, (const double*)phi, rows, n_rows, (const double*)v,
+                         (const double*)psi, y, s_hat, (const double*)lam, (double*)lam_v,
+                         (double*)lam_psi, (double*)lam_phi, (double*)work, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
 hyrom_status hyrom_stage_select(hyrom_ctx* ctx, const void* eps, uint32_t* g_bitmap,
                                 int32_t* n_g) {
   GUARD();

@@ -98,6 +98,15 @@ void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
 void launch_rk2_vjp(const DevCfg& c, const double* q, const double* lam_out, double* lam_in,
                     const uint32_t* mask, int64_t k, double* work, cudaStream_t s);
 
+// adjoint.cu: the reduced step's adjoint (reconstruction on the dofs
+// outside S-hat and the gappy coordinates on `rows`), FP64, m <= 64,
+// Phi column-major N x m; work: reduced_vjp_work_doubles(m, nr) doubles
+void launch_reduced_vjp(int64_t N, int64_t nc, int m, const double* phi, const int* rows, int nr,
+                        const double* v, const double* psi, const double* y,
+                        const uint32_t* s_hat, const double* lam, double* lam_v, double* lam_psi,
+                        double* lam_phi, double* work, cudaStream_t s);
+size_t reduced_vjp_work_doubles(int m, int nr);
+
 // filter.cu
 // fargs: device memory (64 bytes) for the per-call arguments; graph
 // (nullable): the passes kept as one CUDA graph (the other arguments must

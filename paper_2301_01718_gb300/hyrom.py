@@ -138,6 +138,9 @@ def lib():
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
         "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
         "hyrom_stage_rk2_vjp": (st, [vp, vp, vp, vp, vp, i64, vp]),
+        "hyrom_reduced_vjp_work_doubles": (C.c_size_t, [i32, i32]),
+        "hyrom_stage_reduced_vjp": (st, [vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                         vp]),
         "hyrom_batch_create": (st, [C.POINTER(vp), i32, i32, C.POINTER(vp)]),
         "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
         "hyrom_batch_threads": (i32, [vp]),
@@ -376,3 +379,16 @@ def hyrom_stage_rk2_vjp(ctx, q_prev, lam_out, lam_in, s_hat, k, work):
     s_hat, or full when s_hat is None); work: 3 N doubles of device scratch."""
     _check(ctx, lib().hyrom_stage_rk2_vjp(ctx, _ptr(q_prev), _ptr(lam_out), _ptr(lam_in),
                                           _ptr(s_hat), int(k), _ptr(work)))
+
+
+def hyrom_reduced_vjp_work_doubles(m, n_rows):
+    return lib().hyrom_reduced_vjp_work_doubles(int(m), int(n_rows))
+
+
+def hyrom_stage_reduced_vjp(ctx, phi, m, rows, n_rows, v, psi, y, s_hat, lam, lam_v, lam_psi,
+                            lam_phi, work):
+    """The reduced step's adjoint: lam_v, lam_psi, lam_phi from lam (FP64)."""
+    _check(ctx, lib().hyrom_stage_reduced_vjp(ctx, _ptr(phi), int(m), _ptr(rows), int(n_rows),
+                                              _ptr(v), _ptr(psi), _ptr(y), _ptr(s_hat),
+                                              _ptr(lam), _ptr(lam_v), _ptr(lam_psi),
+                                              _ptr(lam_phi), _ptr(work)))

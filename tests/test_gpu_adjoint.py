@@ -112,3 +112,49 @@ def test_autograd_function_chains_steps():
     lam1 = _jt(q1_host, cfg, k + 1, np.where(mrows, w, 0.0)) + np.where(mrows, 0.0, w)
     want = _jt(q, cfg, k, lam1)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_reduced_step_adjoint_matches_the_oracle():
+    """hyrom_stage_reduced_vjp against the oracle's transposes of the
+    reconstruction on S-breve and the gappy coordinates (oracle/adjoint.py),
+    element by element: lam_v, lam_psi and lam_phi within 1e-12 of their
+    largest entries (20^2 Euler, m = 5, 12 regression rows inside S-hat)."""
+    from oracle import adjoint as A, rom
+    hy = H()
+    n, m = 20, 5
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=6, m=m, n_p=12)
+    N, nc = cfg.ndof, cfg.ncell
+    g = np.random.Generator(np.random.PCG64(11))
+    Phi, _ = np.linalg.qr(g.standard_normal((N, m)))
+    s_hat = g.random(nc) < 0.25
+    cells = np.flatnonzero(s_hat)
+    rows = np.sort(g.choice(np.concatenate([c * nc + cells for c in range(4)]), 12,
+                            replace=False)).astype(np.int32)
+    v, psi, lam = (g.standard_normal(N) for _ in range(3))
+    y = rom.gappy_coords(Phi, rows, v, psi)
+    # the oracle
+    sb = np.tile(~s_hat, 4)
+    lrec = np.where(sb, lam, 0.0)
+    gP, gv, gpsi = A.gappy_coords_vjp(Phi, rows, v, psi, Phi.T @ lrec)
+    want_v = np.where(sb, 0.0, lam) + gv
+    want_psi = lrec + gpsi
+    want_phi = np.outer(lrec, y) + gP
+    # the library
+    ctx = hy.hyrom_init(cfg, dev(np.zeros(N)))
+    try:
+        lv = torch.zeros(N, dtype=torch.float64, device="cuda")
+        lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+        lphi = torch.zeros(N * m, dtype=torch.float64, device="cuda")
+        work = torch.zeros(hy.hyrom_reduced_vjp_work_doubles(m, len(rows)), dtype=torch.float64,
+                           device="cuda")
+        phi_d = dev(Phi.T.reshape(-1))                     # column-major N x m
+        hy.hyrom_stage_reduced_vjp(ctx, phi_d, m, dev(rows, torch.int32), len(rows), dev(v),
+                                   dev(psi), dev(y), dev_bits(s_hat), dev(lam), lv, lp, lphi,
+                                   work)
+        got_v, got_psi = host(lv), host(lp)
+        got_phi = host(lphi).reshape(m, N).T
+    finally:
+        hy.hyrom_destroy(ctx)
+    for got, want in ((got_v, want_v), (got_psi, want_psi), (got_phi, want_phi)):
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
