@@ -310,7 +310,8 @@ hyrom_status hyrom_stage_rk2_vjp(hyrom_ctx* ctx, const void* q_prev, const void*
  *   v_final = v on the dofs of the cells in s_hat, psi + Phi y elsewhere,
  * a cotangent lam of v_final pulls back to lam_v (of v), lam_psi (of psi) and
  * lam_phi (of Phi), all overwritten.  Phi: N x m column-major doubles
- * (1 <= m <= 64); rows: n_rows >= m distinct dof indices (int32, dev); y: the
+ * (1 <= m <= 64); rows: m <= n_rows <= 4096 distinct dof indices (int32, dev;
+ * the ODEIM rows: one CTA forms their normal matrix); y: the
  * m coordinates of the forward step (dev doubles); v, psi, lam, lam_v,
  * lam_psi: N doubles; lam_phi: N x m; work: hyrom_reduced_vjp_work_doubles(m,
  * n_rows) doubles of device scratch.  FP64 contexts only.  Synchronises.

@@ -1223,7 +1223,7 @@ hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
                                      void* work) {
   GUARD();
   if (!phi || !rows || !v || !psi || !y || !s_hat || !lam || !lam_v || !lam_psi || !lam_phi ||
-      !work || m < 1 || m > 64 || n_rows < m)
+      !work || m < 1 || m > 64 || n_rows < m || n_rows > 4096)
     return HYROM_EINVAL;
   if (ctx->f32) return fail(ctx, HYROM_EINVAL, "the reduced-step adjoint runs on FP64 contexts");
   hy::launch_reduced_vjp(ctx->N, ctx->nc, m, (const double*)phi, rows, n_rows, (const double*)v,
