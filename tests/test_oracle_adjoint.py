@@ -72,14 +72,15 @@ def test_pod_transpose():
     assert _close(np.sum(lP * dP), np.sum(A.pod_vjp(X, lP, m, 1e-10, 0.0) * dX))
 
 
-def test_reverse_sweep_gradient_equals_the_tangent():
+@pytest.mark.parametrize("rows", [W.ROWS_ODEIM, W.ROWS_SAMPLE], ids=["odeim_rows", "sample_rows"])
+def test_reverse_sweep_gradient_equals_the_tangent(rows):
     """dJ/dtheta = (dq0/dtheta)^T lambda_0 from one reverse sweep over warm-up
     full steps, rebuilds and hybrid steps equals the tangent model's eight
     directional derivatives (the gradient is unique), and the recorded
-    forward run gives the same J."""
+    forward run gives the same J; for both forms of the reduced solve."""
     _, cfg, _ = W.euler_vortex(n=20, seed=2)
     cfg = cfg.with_(precision=W.PREC_F64, w=6, m=3, n_p=6, top_frac=0.15, pod_tol=1e-10,
-                    pod_abs=1e-13)
+                    pod_abs=1e-13, regress_rows=rows)
     th0 = np.array(W.VORTEX_THETA0)
     box, steps = (6, 14, 6, 14), cfg.w + 5
     q0 = W.euler_vortex_theta(20, th0)
