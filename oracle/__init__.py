@@ -27,4 +27,6 @@ Modules
             time-integrated output
   adjoint - its reverse mode: the transposes of those JVPs and one
             reverse sweep over the recorded run for dJ/dq0
+  hdm_muscl - the paper's own HDM: MUSCL + minmod + Roe, BDF2 solved by
+            Newton-GMRES                                      [Sec. 3.1]
 """

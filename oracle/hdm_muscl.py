@@ -1,0 +1,145 @@
+"""The paper's own HDM (Sec. 3.1): a second-order MUSCL finite-volume
+discretisation of the Euler equations with the Roe flux and the minmod
+limiter on a Cartesian mesh, integrated by the second-order BDF scheme
+(a0 = 1/3, a1 = -4/3, a2 = 1, beta = 2/3 in Eq. bdf), each implicit step
+R_k(q_k) = 0 (Eq. hdm) solved by Newton's method with GMRES.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Readings where the paper is silent:
+  * MUSCL reconstructs the conserved variables, component by component:
+    the slope of cell i is minmod(q_i - q_{i-1}, q_{i+1} - q_i) (zero when
+    the two differences differ in sign, else the one of smaller magnitude),
+    the face states are q_i + slope_i / 2 and q_{i+1} - slope_{i+1} / 2.
+  * the Roe flux has no entropy fix;
+  * in two dimensions each direction is reconstructed and fluxed
+    separately (dimension by dimension);
+  * ghost cells are two layers of hdm.pad_ghost (periodic, outflow or exact
+    shock state);
+  * the first step, which has no q_{k-2}, is BDF1 (backward Euler);
+  * the Newton solve is Jacobian-free (scipy's newton_krylov with GMRES)
+    and stops at max |R| <= tol * max(1, max |q_{k-1}|).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy import optimize
+
+import workloads as W
+from . import hdm
+
+
+def minmod(a, b):
+    return np.where(a * b > 0.0, np.where(np.abs(a) < np.abs(b), a, b), 0.0)
+
+
+def _flux(q, gamma, axis):
+    rho, mx, my, en = q
+    u, v = mx / rho, my / rho
+    p = (gamma - 1.0) * (en - 0.5 * rho * (u * u + v * v))
+    if axis == 0:
+        return np.stack([mx, mx * u + p, my * u, (en + p) * u])
+    return np.stack([my, mx * v, my * v + p, (en + p) * v])
+
+
+def roe_flux(qL, qR, gamma, axis):
+    """Roe's approximate Riemann solver across a face normal to x (axis 0) or
+    y (axis 1): F = (f(qL) + f(qR))/2 - sum_k |lambda_k| alpha_k r_k / 2 with
+    the Roe-averaged eigen-decomposition of the Euler flux Jacobian."""
+    rL, rR = qL[0], qR[0]
+    uL, uR = qL[1] / rL, qR[1] / rR
+    vL, vR = qL[2] / rL, qR[2] / rR
+    pL = (gamma - 1.0) * (qL[3] - 0.5 * rL * (uL * uL + vL * vL))
+    pR = (gamma - 1.0) * (qR[3] - 0.5 * rR * (uR * uR + vR * vR))
+    HL, HR = (qL[3] + pL) / rL, (qR[3] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    w = sL + sR
+    u = (sL * uL + sR * uR) / w
+    v = (sL * vL + sR * vR) / w
+    H = (sL * HL + sR * HR) / w
+    c = np.sqrt((gamma - 1.0) * (H - 0.5 * (u * u + v * v)))
+    rho = sL * sR
+    # normal / tangential velocity and their jumps
+    un, ut = (u, v) if axis == 0 else (v, u)
+    dr = rR - rL
+    dp = pR - pL
+    dun = (uR - uL) if axis == 0 else (vR - vL)
+    dut = (vR - vL) if axis == 0 else (uR - uL)
+    # wave strengths: acoustic (un - c, un + c), entropy, shear
+    a1 = (dp - rho * c * dun) / (2.0 * c * c)
+    a3 = (dp + rho * c * dun) / (2.0 * c * c)
+    a2 = dr - dp / (c * c)
+    a4 = rho * dut
+    l1, l2, l3 = np.abs(un - c), np.abs(un), np.abs(un + c)
+    one = np.ones_like(u)
+    if axis == 0:
+        r1 = np.stack([one, u - c, v, H - u * c])
+        r3 = np.stack([one, u + c, v, H + u * c])
+        r2 = np.stack([one, u, v, 0.5 * (u * u + v * v)])
+        r4 = np.stack([0.0 * one, 0.0 * one, one, v])
+    else:
+        r1 = np.stack([one, u, v - c, H - v * c])
+        r3 = np.stack([one, u, v + c, H + v * c])
+        r2 = np.stack([one, u, v, 0.5 * (u * u + v * v)])
+        r4 = np.stack([0.0 * one, one, 0.0 * one, u])
+    diss = l1 * a1 * r1 + l2 * a2 * r2 + l3 * a3 * r3 + l2 * a4 * r4
+    return 0.5 * (_flux(qL, gamma, axis) + _flux(qR, gamma, axis)) - 0.5 * diss
+
+
+def rhs(q, cfg, t):
+    """f*(q, t) of the MUSCL-Roe-minmod discretisation (Euler, 1D or 2D)."""
+    c, ny, nx = q.shape
+    qg = hdm.pad_ghost(q, cfg, t, 2)
+    rows = slice(2, ny + 2) if ny > 1 else slice(None)
+    qx = qg[:, rows, :]                                   # domain rows, 2 ghosts in x
+    d = qx[:, :, 1:] - qx[:, :, :-1]                      # nx + 3 differences
+    s = minmod(d[:, :, :-1], d[:, :, 1:])                 # slopes of padded cells 1..nx+2
+    # face f between padded cells f + 1 and f + 2 (f = 0..nx): cells f, f + 1 of s
+    qL = qx[:, :, 1:nx + 2] + 0.5 * s[:, :, 0:nx + 1]
+    qR = qx[:, :, 2:nx + 3] - 0.5 * s[:, :, 1:nx + 2]
+    F = roe_flux(qL, qR, cfg.gamma, 0)
+    out = -(F[:, :, 1:] - F[:, :, :-1]) / cfg.dx
+    if ny > 1:
+        qy = qg[:, :, 2:nx + 2]
+        d = qy[:, 1:, :] - qy[:, :-1, :]
+        s = minmod(d[:, :-1, :], d[:, 1:, :])
+        qL = qy[:, 1:ny + 2, :] + 0.5 * s[:, 0:ny + 1, :]
+        qR = qy[:, 2:ny + 3, :] - 0.5 * s[:, 1:ny + 2, :]
+        G = roe_flux(qL, qR, cfg.gamma, 1)
+        out = out - (G[:, 1:, :] - G[:, :-1, :]) / cfg.dy
+    return out
+
+
+BDF2 = (1.0 / 3.0, -4.0 / 3.0, 1.0, 2.0 / 3.0)     # a0, a1, a2, beta
+
+
+def residual(q, q_prev, q_prev2, cfg, t):
+    """R_k(q) = q - F_k(q) of Eq. hdm for BDF2 (BDF1 when q_prev2 is None)."""
+    if q_prev2 is None:
+        return (q - q_prev) - cfg.dt * rhs(q, cfg, t)
+    a0, a1, a2, beta = BDF2
+    return a2 * q + a1 * q_prev + a0 * q_prev2 - cfg.dt * beta * rhs(q, cfg, t)
+
+
+def step(q_prev, q_prev2, cfg, k, tol=1e-11):
+    """One implicit step k: the q with R_k(q) = 0, by Newton-GMRES from the
+    previous state."""
+    t = k * cfg.dt
+    shape = q_prev.shape
+    scale = max(1.0, float(np.abs(q_prev).max()))
+
+    def F(x):
+        return residual(x.reshape(shape), q_prev, q_prev2, cfg, t).reshape(-1)
+
+    x = optimize.newton_krylov(F, q_prev.reshape(-1).copy(), method="gmres",
+                               f_tol=tol * scale, maxiter=50)
+    return x.reshape(shape)
+
+
+def trajectory(q0, cfg, steps):
+    """q_1..q_steps: BDF1 for the first step, BDF2 after."""
+    qs = [np.asarray(q0, np.float64).reshape(cfg.nvar, cfg.ny, cfg.nx)]
+    for k in range(1, steps + 1):
+        q2 = qs[-2] if len(qs) >= 2 else None
+        qs.append(step(qs[-1], q2, cfg, k))
+    return qs[1:]
