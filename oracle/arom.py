@@ -10,8 +10,10 @@ Readings where the paper is silent:
   * explicit schemes (SSP-RK2): the partial HDM is S-hat^T gamma_k =
     S-hat^T RK2(gamma_{k-1}), exact with no subiterations (the remark on
     explicit time marching); its stencil reaches two cells.
-  * implicit schemes (BDF1): subiterations j = 1..J stop when
-    ||y^(j) - y^(j-1)||_2 < eps_y (checked from j = 2) or j = jmax.
+  * implicit schemes (BDF1, and the paper's MUSCL-Roe-BDF2 HDM of
+    oracle/hdm_muscl.py): subiterations j = 1..J stop when
+    ||y^(j) - y^(j-1)||_2 < eps_y (checked from j = 2) or j = jmax; with the
+    MUSCL HDM the filter's residual is that HDM's BDF2 residual.
   * psi, Phi, P "in effect": when a rebuild was skipped (mod(k+1, z) = 0)
     the most recent ones are used by the next RRE and POD.  The RRE needs a
     basis; before the first rebuild G is empty.
@@ -24,7 +26,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 import workloads as W
-from . import hdm, rom, select, filt
+from . import hdm, hdm_muscl, rom, select, filt
 
 
 @dataclass
@@ -100,8 +102,14 @@ class Arom:
         prev = self.snaps[k - 1]
         info = StepInfo(k=k, was_full=self._is_full(k))
         t = k * cfg.dt
+        muscl = cfg.scheme == W.SCHEME_BDF2_MUSCL
+        prev2 = self.snaps.get(k - 2) if muscl else None
+        resid = (lambda q: hdm_muscl.residual(q, prev, prev2, cfg, t)) if muscl else None
         if info.was_full:
-            gam = hdm.full_step(prev, cfg, k)                     # full HDM step
+            if muscl:                                             # the paper's HDM
+                gam = hdm_muscl.step(prev, prev2, cfg, k)
+            else:
+                gam = hdm.full_step(prev, cfg, k)                 # full HDM step
             info.n_s = cfg.ncell
         else:
             s_hat = self.s_hat
@@ -117,7 +125,10 @@ class Arom:
                 v = prev.copy()                                   # predictor
                 y = None
                 for j in range(1, cfg.jmax + 1):                  # subiterations
-                    v, _, _ = hdm.newton_be(prev, cfg, t, active=s_hat, q_init=v)
+                    if muscl:
+                        v = hdm_muscl.partial_step(prev, prev2, cfg, k, s_hat, v)
+                    else:
+                        v, _, _ = hdm.newton_be(prev, cfg, t, active=s_hat, q_init=v)
                     y_new = self._gappy(v)
                     conv = y is not None and np.linalg.norm(y_new - y) < cfg.eps_y
                     y = y_new
@@ -130,7 +141,7 @@ class Arom:
             rec = self._rec(y)                                    # reconstruction
             v = v.copy()
             v[:, s_breve] = rec[:, s_breve]
-            gam, info.filt_passes, _ = filt.spatial_filter(v, prev, cfg, t)  # SpatialFilter
+            gam, info.filt_passes, _ = filt.spatial_filter(v, prev, cfg, t, resid)  # SpatialFilter
             self.y = y
         self.snaps[k] = gam
         self.k = k

@@ -67,26 +67,28 @@ def shapiro(q, n, cfg):
     return out
 
 
-def cell_residual(q, q_prev, cfg, t):
-    """rho_i = sum_v |R_{v,i}(q)|, R the BDF1 residual at time t."""
-    R = np.abs(hdm.residual_be(q, q_prev, cfg, t))
+def cell_residual(q, q_prev, cfg, t, resid=None):
+    """rho_i = sum_v |R_{v,i}(q)|, R the BDF1 residual at time t (or
+    resid(q), the residual of the HDM in use)."""
+    R = np.abs(hdm.residual_be(q, q_prev, cfg, t) if resid is None else resid(q))
     acc = R[0].copy()
     for v in range(1, R.shape[0]):
         acc = acc + R[v]
     return acc
 
 
-def spatial_filter(q, q_prev, cfg, t):
+def spatial_filter(q, q_prev, cfg, t, resid=None):
     """SpatialFilter of Algorithm 1.  Returns (q_filtered,
-    passes_run, cells_kept_total)."""
+    passes_run, cells_kept_total).  resid: the residual of the HDM in use
+    (default the BDF1 form)."""
     q = q.copy()
     passes = 0
     kept_total = 0
     for n in cfg.filt_orders:
-        rho_old = cell_residual(q, q_prev, cfg, t)
+        rho_old = cell_residual(q, q_prev, cfg, t, resid)
         for _ in range(cfg.jmax_f):
             g = shapiro(q, n, cfg)
-            rho_new = cell_residual(g, q_prev, cfg, t)
+            rho_new = cell_residual(g, q_prev, cfg, t, resid)
             keep = rho_new < rho_old
             passes += 1
             nk = int(np.count_nonzero(keep))
@@ -98,5 +100,5 @@ def spatial_filter(q, q_prev, cfg, t):
             tot = float(np.sum(rho_old[keep]))
             if dec < cfg.eps_f * tot:
                 break
-            rho_old = cell_residual(q, q_prev, cfg, t)
+            rho_old = cell_residual(q, q_prev, cfg, t, resid)
     return q, passes, kept_total

@@ -136,6 +136,30 @@ def step(q_prev, q_prev2, cfg, k, tol=1e-11):
     return x.reshape(shape)
 
 
+def partial_step(q_prev, q_prev2, cfg, k, active, q_init, tol=1e-11):
+    """The partial HDM of Sec. 2.3 (Eq. partial_hdm2) for this HDM: the
+    cells of `active` (bool [ny, nx]) solve their rows of R_k(q) = 0, every
+    other cell keeps its value in q_init."""
+    t = k * cfg.dt
+    shape = q_prev.shape
+    act = np.broadcast_to(active[None], shape)
+    scale = max(1.0, float(np.abs(q_prev).max()))
+    base = q_init.copy()
+    if not act.any():
+        return base
+
+    def F(x):
+        q = base.copy()
+        q[act] = x
+        return residual(q, q_prev, q_prev2, cfg, t)[act]
+
+    x = optimize.newton_krylov(F, base[act].copy(), method="gmres", f_tol=tol * scale,
+                               maxiter=50)
+    out = base.copy()
+    out[act] = x
+    return out
+
+
 def trajectory(q0, cfg, steps):
     """q_1..q_steps: BDF1 for the first step, BDF2 after."""
     qs = [np.asarray(q0, np.float64).reshape(cfg.nvar, cfg.ny, cfg.nx)]

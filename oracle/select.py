@@ -120,7 +120,10 @@ def dilate(mask, radius, cfg):
 
 
 def stencil_radius(cfg):
-    return 2 if cfg.scheme == W.SCHEME_RK2 else 1
+    """Cells a partial solve on S-hat reads around it: one for the
+    first-order implicit residual, two for SSP-RK2's two stages and for the
+    MUSCL residual (its face states use the neighbours' slopes)."""
+    return 1 if cfg.scheme == W.SCHEME_BE else 2
 
 
 def build_masks(G_cells, P_rows, cfg):

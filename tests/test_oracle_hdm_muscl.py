@@ -114,3 +114,52 @@ def test_sod_shock_tube_against_the_exact_solution():
             assert e2 < 0.7 * prev
         prev = e2
     assert prev < 0.006
+
+
+def _sod_cfg(nx=100, **kw):
+    from oracle import arom  # noqa: F401
+    q0, cfg = W.euler_riemann_x(n=nx)
+    steps = int(round(0.2 / cfg.dt))
+    cfg = cfg.with_(scheme=W.SCHEME_BDF2_MUSCL, dt=0.2 / steps, w=10, m=5, n_p=10,
+                    top_frac=0.2, halo=2, pod_tol=1e-10, pod_abs=1e-13, **kw)
+    return q0.reshape(4, 1, nx), cfg, steps
+
+
+def test_partial_step_solves_the_active_rows_only():
+    q0, cfg, _ = _sod_cfg()
+    q1 = M.step(q0, None, cfg, 1)
+    g = np.random.Generator(np.random.PCG64(3))
+    active = (g.random((1, cfg.nx)) < 0.3)
+    init = q1 + 1e-3 * g.standard_normal(q1.shape)
+    out = M.partial_step(q1, q0, cfg, 2, active, init)
+    inactive = ~np.broadcast_to(active[None], q1.shape)
+    assert np.array_equal(out[inactive], init[inactive])
+    R = M.residual(out, q1, q0, cfg, 2 * cfg.dt)
+    assert np.abs(R[~inactive]).max() <= 1e-10
+
+
+def test_hybrid_method_with_the_papers_hdm():
+    """Algorithm 1 on Sod's tube with the MUSCL-Roe-BDF2 HDM: with every cell
+    sampled and no filter a hybrid step is the full HDM step (to the Newton
+    tolerance); with 20 % of the cells plus a 2-cell halo the hybrid
+    trajectory stays within 2 % (relative L1) of the HDM trajectory."""
+    from oracle import arom
+    q0, cfg, steps = _sod_cfg()
+    A = arom.Arom(q0, cfg.with_(top_frac=1.0, filt_orders=()))
+    seen = 0
+    for _ in range(cfg.w + 4):
+        prev2, prev = A.snaps.get(A.k - 1), A.gamma.copy()
+        info = A.step()
+        if not info.was_full and info.n_s == cfg.ncell:
+            assert np.abs(A.gamma - M.step(prev, prev2, cfg, info.k)).max() <= 1e-9
+            seen += 1
+    assert seen >= 3
+    ref = M.trajectory(q0, cfg, steps)
+    A = arom.Arom(q0, cfg)
+    worst = 0.0
+    for k in range(steps):
+        A.step()
+        worst = max(worst, arom.rel_l1(A.gamma, ref[k]))
+    sbar, _, _ = arom.sampling_averages(A.history, cfg.ncell, cfg.ndof)
+    assert worst < 2e-2 and sbar < 40.0, (worst, sbar)
+    assert any(h.J > 1 for h in A.history if not h.was_full)      # subiterations ran
