@@ -330,13 +330,16 @@ hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
  * threads.  hyrom_batch_create takes n distinct contexts (the caller keeps
  * them: they must outlive the batch and not be used by another thread while
  * a batch call runs) and starts `threads` host threads (0: half the host's
- * hardware threads, between 1 and 8; never more than n).
+ * hardware threads, between 1 and 8; never more than the number of distinct
+ * streams among the contexts).
  * hyrom_batch_step runs `nsteps` calls of hyrom_step on every instance: each
  * thread takes one instance at a time, largest device footprint first, and
  * runs its steps on the instance's own stream, so up to `threads` instances
  * are on the GPU at once.  An instance's steps stay in order and launch the
  * same kernels as when it is stepped alone, so its results are the same bits.
- * Contexts on one shared stream (or the legacy default stream) keep their
+ * Contexts that share a stream (the legacy default stream included) are
+ * stepped by one thread in turn, so that a stream being captured into one
+ * instance's CUDA graph sees no other instance's work: they keep their
  * results and lose the overlap.  infos (n entries, nullable) receives each
  * instance's last step; status (n entries, nullable) each instance's first
  * non-OK status; an instance stops at a failure other than HYROM_ENOTCONV.

@@ -725,6 +725,10 @@ hyrom_status init_state(hyrom_ctx* ctx, const double* q0, int on_host) {
 // public entry points
 // ---------------------------------------------------------------------------
 
+namespace hy {
+void* ctx_stream(const hyrom_ctx* ctx) { return ctx ? (void*)ctx->st : nullptr; }
+}  // namespace hy
+
 extern "C" {
 
 hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_host, void* stream,

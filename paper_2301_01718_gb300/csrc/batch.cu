@@ -8,7 +8,9 @@
 // device footprint, which grows with dofs x window), so the last ones to
 // finish are the short ones.  Per instance nothing changes: the same kernels
 // run in the same order on its stream, so its results are the same bits as
-// stepping it alone.
+// stepping it alone.  Instances that share a stream form one group, stepped
+// by one thread in turn: a stream being captured into an instance's CUDA
+// graph must see no other instance's work.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,10 +23,11 @@
 #include <vector>
 
 #include "../../include/hyrom.h"
+#include "internal.h"
 
 struct hyrom_batch {
   std::vector<hyrom_ctx*> ctx;
-  std::vector<int> order;  // instances, largest first
+  std::vector<std::vector<int>> groups;  // instances sharing a stream, largest groups first
   int device = 0;
   std::vector<std::thread> pool;
 
@@ -67,9 +70,9 @@ void worker(hyrom_batch* b) {
       if (b->quit) return;
       seen = b->gen;
     }
-    const int n = (int)b->ctx.size();
-    for (int j; (j = b->next.fetch_add(1, std::memory_order_relaxed)) < n;)
-      run_instance(b, b->order[j]);
+    const int ng = (int)b->groups.size();
+    for (int j; (j = b->next.fetch_add(1, std::memory_order_relaxed)) < ng;)
+      for (int i : b->groups[j]) run_instance(b, i);
     std::lock_guard<std::mutex> lk(b->mu);
     if (--b->busy == 0) b->cv_done.notify_all();
   }
@@ -81,20 +84,36 @@ extern "C" hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, in
                                            hyrom_batch** out) {
   if (!out || !ctxs || n <= 0 || threads < 0) return HYROM_EINVAL;
   for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return HYROM_EINVAL;
+  for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j)
-      if (!ctxs[i] || ctxs[i] == ctxs[j]) return HYROM_EINVAL;
+      if (ctxs[i] == ctxs[j]) return HYROM_EINVAL;
   hyrom_batch* b = new (std::nothrow) hyrom_batch;
   if (!b) return HYROM_ENOMEM;
   b->ctx.assign(ctxs, ctxs + n);
   b->status.assign(n, HYROM_OK);
-  b->order.resize(n);
-  std::vector<size_t> bytes(n);
+  // group by stream (first appearance order), then largest groups first
+  std::vector<void*> streams;
+  std::vector<size_t> gbytes;
   for (int i = 0; i < n; ++i) {
-    b->order[i] = i;
-    bytes[i] = hyrom_device_bytes(ctxs[i]);
+    void* st = hy::ctx_stream(ctxs[i]);
+    size_t g = 0;
+    while (g < streams.size() && streams[g] != st) ++g;
+    if (g == streams.size()) {
+      streams.push_back(st);
+      b->groups.emplace_back();
+      gbytes.push_back(0);
+    }
+    b->groups[g].push_back(i);
+    gbytes[g] += hyrom_device_bytes(ctxs[i]);
   }
-  std::stable_sort(b->order.begin(), b->order.end(),
-                   [&](int x, int y) { return bytes[x] > bytes[y]; });
+  std::vector<int> perm(b->groups.size());
+  for (size_t g = 0; g < perm.size(); ++g) perm[g] = (int)g;
+  std::stable_sort(perm.begin(), perm.end(),
+                   [&](int x, int y) { return gbytes[x] > gbytes[y]; });
+  std::vector<std::vector<int>> sorted;
+  for (int g : perm) sorted.push_back(b->groups[g]);
+  b->groups.swap(sorted);
   if (cudaGetDevice(&b->device) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -104,7 +123,8 @@ extern "C" hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, in
   // the CPU while its instance's stream drains; more threads than half the
   // cores starved the launching ones)
   const int hw = (int)std::thread::hardware_concurrency();
-  const int nt = std::min(n, threads == 0 ? std::max(1, std::min(8, hw / 2)) : (int)threads);
+  const int ng = (int)b->groups.size();
+  const int nt = std::min(ng, threads == 0 ? std::max(1, std::min(8, hw / 2)) : (int)threads);
   try {
     for (int t = 0; t < nt; ++t) b->pool.emplace_back(worker, b);
   } catch (...) {

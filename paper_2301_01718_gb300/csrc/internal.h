@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+typedef struct hyrom_ctx hyrom_ctx;
+
 namespace hy {
 
 struct DevCfg;
@@ -13,6 +15,9 @@ struct DevCfg;
 unsigned long long launch_count();
 unsigned long long thread_launch_count();
 void add_launches(unsigned long long n);
+
+// The stream a context was created with (api.cu).
+void* ctx_stream(const hyrom_ctx* ctx);
 
 // Raise the dynamic shared memory limit of kernel `func` on the current
 // device to at least `bytes`.  The limit is a per-function global shared by

@@ -90,6 +90,8 @@ def test_batch_argument_checks_need_no_gpu(lib):
     assert L.hyrom_batch_create(arr, 0, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
     assert L.hyrom_batch_create(arr, 2, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
     assert L.hyrom_batch_create(None, 1, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
+    first_null = (ctypes.c_void_p * 2)(None, 0x1000)      # rejected before any use
+    assert L.hyrom_batch_create(first_null, 2, 0, ctypes.byref(out)) == hyrom.HYROM_EINVAL
     assert out.value is None
     assert L.hyrom_batch_step(None, 1, None, None) == hyrom.HYROM_EINVAL
     assert L.hyrom_batch_threads(None) == 0
