@@ -183,6 +183,24 @@ def lambda_min_update_secular(M, rows):
     return hi
 
 
+def odeim_batched(Phi, n_p, tie_tol, b):
+    """A cheaper variant of ODEIM for study (not the paper's method): after
+    the DEIM points, each oversampling pass scores every row once against
+    the current sampled Gram matrix and takes the b best rows (in score
+    order, ties to the lowest index) instead of one.  b = 1 is odeim()."""
+    N, m = Phi.shape
+    p = deim(Phi, tie_tol)
+    if m == 0:
+        return p
+    n_p = min(n_p, N)
+    while len(p) < n_p:
+        A = Phi[p, :]
+        score = lambda_min_update_secular(A.T @ A, Phi)
+        for _ in range(min(b, n_p - len(p))):
+            p.append(argmax_tie(score, tie_tol, exclude=p))
+    return p
+
+
 def odeim(Phi, n_p, tie_tol, method="secular"):
     """ODEIM_{n_p}(Phi) (Eq. odeim): the DEIM points, then n_p - m greedy
     oversampling points, each maximising the smallest eigenvalue of the

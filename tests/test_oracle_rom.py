@@ -212,3 +212,20 @@ def test_normal_equations_follow_the_rounded_matrix():
         assert errs[red] <= kappa * eta / (1 - kappa * eta) + 1e-12, (red, errs[red])
     assert errs[W.RED_BF16] > 4 * errs[W.RED_TF32] > 0
     assert errs[W.RED_TF32_SPLIT] < 1e-6
+
+
+def test_batched_odeim_study_variant():
+    """rom.odeim_batched (a cheaper variant for study, not the paper's
+    method): with one point per pass it is ODEIM; with b per pass each pass
+    takes the b best-scored unpicked rows of that pass."""
+    g = np.random.Generator(np.random.PCG64(12))
+    Phi, _ = np.linalg.qr(g.standard_normal((300, 6)))
+    assert rom.odeim_batched(Phi, 20, 1e-12, 1) == rom.odeim(Phi, 20, 1e-12)
+    P = rom.odeim_batched(Phi, 20, 1e-12, 4)
+    assert len(P) == 20 and len(set(P)) == 20
+    first = rom.deim(Phi, 1e-12)
+    assert P[:6] == first
+    A = Phi[first, :]
+    score = rom.lambda_min_update_secular(A.T @ A, Phi)
+    score[first] = -np.inf
+    assert sorted(P[6:10]) == sorted(np.argsort(-score, kind="stable")[:4].tolist())
