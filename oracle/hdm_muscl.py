@@ -7,10 +7,13 @@ R_k(q_k) = 0 (Eq. hdm) solved by Newton's method with GMRES.
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Readings where the paper is silent:
-  * MUSCL reconstructs the conserved variables, component by component:
-    the slope of cell i is minmod(q_i - q_{i-1}, q_{i+1} - q_i) (zero when
-    the two differences differ in sign, else the one of smaller magnitude),
-    the face states are q_i + slope_i / 2 and q_{i+1} - slope_{i+1} / 2.
+  * MUSCL reconstructs the primitive variables (rho, u, v, p), component
+    by component: the slope of cell i is minmod(w_i - w_{i-1}, w_{i+1} - w_i)
+    (zero when the two differences differ in sign, else the one of smaller
+    magnitude), the face states are w_i + slope_i / 2 and
+    w_{i+1} - slope_{i+1} / 2, converted back to conserved variables for the
+    flux.  (Reconstructing the conserved variables instead put the paper's
+    Sod case further from the paper's printed figures.)
   * the Roe flux has no entropy fix;
   * in two dimensions each direction is reconstructed and fluxed
     separately (dimension by dimension);
@@ -86,26 +89,48 @@ def roe_flux(qL, qR, gamma, axis):
     return 0.5 * (_flux(qL, gamma, axis) + _flux(qR, gamma, axis)) - 0.5 * diss
 
 
+def to_primitive(q, gamma):
+    rho, mx, my, en = q
+    u, v = mx / rho, my / rho
+    return np.stack([rho, u, v, (gamma - 1.0) * (en - 0.5 * rho * (u * u + v * v))])
+
+
+def to_conserved(w, gamma):
+    rho, u, v, p = w
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def _faces(w, axis):
+    """MUSCL face states along `axis` (1 = y, 2 = x) of a primitive array
+    with two ghost layers on that axis: face f lies between padded cells
+    f + 1 and f + 2 (f = 0..n), the slopes are those of padded cells 1..n+2."""
+    n = w.shape[axis] - 4
+    d = np.diff(w, axis=axis)                             # n + 3 differences
+    lo = [slice(None)] * 3
+    hi = [slice(None)] * 3
+    lo[axis], hi[axis] = slice(0, n + 2), slice(1, n + 3)
+    s = minmod(d[tuple(lo)], d[tuple(hi)])                # slopes of padded cells 1..n+2
+    a = [slice(None)] * 3
+    b = [slice(None)] * 3
+    sa = [slice(None)] * 3
+    sb = [slice(None)] * 3
+    a[axis], b[axis] = slice(1, n + 2), slice(2, n + 3)
+    sa[axis], sb[axis] = slice(0, n + 1), slice(1, n + 2)
+    return w[tuple(a)] + 0.5 * s[tuple(sa)], w[tuple(b)] - 0.5 * s[tuple(sb)]
+
+
 def rhs(q, cfg, t):
     """f*(q, t) of the MUSCL-Roe-minmod discretisation (Euler, 1D or 2D)."""
     c, ny, nx = q.shape
+    g = cfg.gamma
     qg = hdm.pad_ghost(q, cfg, t, 2)
     rows = slice(2, ny + 2) if ny > 1 else slice(None)
-    qx = qg[:, rows, :]                                   # domain rows, 2 ghosts in x
-    d = qx[:, :, 1:] - qx[:, :, :-1]                      # nx + 3 differences
-    s = minmod(d[:, :, :-1], d[:, :, 1:])                 # slopes of padded cells 1..nx+2
-    # face f between padded cells f + 1 and f + 2 (f = 0..nx): cells f, f + 1 of s
-    qL = qx[:, :, 1:nx + 2] + 0.5 * s[:, :, 0:nx + 1]
-    qR = qx[:, :, 2:nx + 3] - 0.5 * s[:, :, 1:nx + 2]
-    F = roe_flux(qL, qR, cfg.gamma, 0)
+    wL, wR = _faces(to_primitive(qg[:, rows, :], g), 2)  # domain rows, 2 ghosts in x
+    F = roe_flux(to_conserved(wL, g), to_conserved(wR, g), g, 0)
     out = -(F[:, :, 1:] - F[:, :, :-1]) / cfg.dx
     if ny > 1:
-        qy = qg[:, :, 2:nx + 2]
-        d = qy[:, 1:, :] - qy[:, :-1, :]
-        s = minmod(d[:, :-1, :], d[:, 1:, :])
-        qL = qy[:, 1:ny + 2, :] + 0.5 * s[:, 0:ny + 1, :]
-        qR = qy[:, 2:ny + 3, :] - 0.5 * s[:, 1:ny + 2, :]
-        G = roe_flux(qL, qR, cfg.gamma, 1)
+        wL, wR = _faces(to_primitive(qg[:, :, 2:nx + 2], g), 1)
+        G = roe_flux(to_conserved(wL, g), to_conserved(wR, g), g, 1)
         out = out - (G[:, 1:, :] - G[:, :-1, :]) / cfg.dy
     return out
 
