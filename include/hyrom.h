@@ -51,7 +51,12 @@ typedef enum {
   HYROM_ENOTCONV = 4,  /* a Newton solve hit newton_max (result still set)  */
   HYROM_ESTATE = 5,    /* call out of order (e.g. no basis yet)             */
   HYROM_ECAP = 6,      /* output buffer too small                           */
-  HYROM_ETIMEOUT = 7   /* an iterative device solver hit its sweep limit    */
+  HYROM_ETIMEOUT = 7,  /* an iterative device solver hit its sweep limit    */
+  HYROM_ERANK = 8,     /* information, the call completed: the window has
+                          rank below m (POD kept m_eff < m modes, Sec.
+                          2.3.1) or P^T Phi is rank-deficient             */
+  HYROM_ENONPHYS = 9   /* the call completed but the Euler state has cells
+                          with rho <= 0 or p <= 0 (or not finite)          */
 } hyrom_status;
 
 enum { HYROM_PDE_BURGERS = 0, HYROM_PDE_EULER = 1 };
@@ -191,7 +196,16 @@ hyrom_status hyrom_stage_times(const hyrom_ctx* ctx, double* ms, int64_t* count)
  * Neighbors, psi_{k+1}; does nothing when the rebuild test is false.
  * hyrom_step = hyrom_advance then hyrom_update_basis (one loop iteration).
  * info may be NULL.  These calls synchronise the stream once per call (they
- * return counts in info). */
+ * return counts in info).
+ * Statuses that report on a completed step: hyrom_advance returns
+ * HYROM_ENONPHYS when the new Euler snapshot has cells with rho <= 0 or
+ * p <= 0 (checked on every step; the state is kept so that it can be
+ * inspected, but the run has left the ideal-gas model); hyrom_update_basis
+ * returns HYROM_ERANK when a rebuild kept m_eff < m modes (Sec. 2.3.1, the
+ * window's numerical rank) or found P^T Phi rank-deficient, which is
+ * information only: the basis in effect is valid and the run may go on.
+ * hyrom_step returns a failure of the rebuild first, then the advance's
+ * status, then HYROM_ERANK. */
 hyrom_status hyrom_advance(hyrom_ctx* ctx, hyrom_step_info* info);
 hyrom_status hyrom_update_basis(hyrom_ctx* ctx, hyrom_step_info* info);
 hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info);
@@ -234,7 +248,9 @@ hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* 
 
 /* Gappy reduced coordinates y = (P^T Phi)^+ P^T (v - psi) (Eq. red_coord)
  * by Householder QR in FP64.  phi: ndof x m (column-major), points: n_p dof
- * rows, y_out: m doubles (device). */
+ * rows, y_out: m doubles (device).  Synchronises.  When P^T Phi is
+ * rank-deficient (a pivot |R_jj| <= 64 n_p eps max|R_ii|, e.g. two equal rows
+ * with n_p = m) every y_j is NaN and the status is HYROM_ERANK. */
 hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const int32_t* points,
                                int32_t n_p, const void* v, const void* psi, double* y_out);
 
@@ -342,7 +358,8 @@ hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
  * instance's CUDA graph sees no other instance's work: they keep their
  * results and lose the overlap.  infos (n entries, nullable) receives each
  * instance's last step; status (n entries, nullable) each instance's first
- * non-OK status; an instance stops at a failure other than HYROM_ENOTCONV.
+ * non-OK status; an instance stops at a failure other than HYROM_ENOTCONV
+ * (HYROM_ERANK, information only, is not reported: see m_eff in infos).
  * Returns when every instance is done (synchronised): HYROM_OK or the first
  * failing instance's status (by index).  Errors of hyrom_batch_create:
  * HYROM_EINVAL (n <= 0, threads < 0, a null or repeated context),
@@ -369,8 +386,7 @@ hyrom_status hyrom_selftest_math(int32_t which, const double* x, double* y, int6
 
 /* ---- allocation-free variant ---------------------------------------------
  * hyrom_gappy_static: the gappy reduced coordinates of hyrom_stage_gappy,
- * y = (P^T Phi)^+ P^T (v - psi) (Algorithm 1, the gappy least-squares step),
- * for callers that cannot allocate device memory: host applications that
+ * y = (P^T Phi)^+ P^T (v - psi), for callers that cannot allocate device memory: host applications that
  * budget all device memory up front and pass only pointers into their own
  * pools, plugins that must not use the CUDA allocator of the program that
  * loads them, and time-critical loops where cudaMalloc / cudaFree would add
@@ -382,8 +398,9 @@ hyrom_status hyrom_selftest_math(int32_t which, const double* x, double* y, int6
  *   device arrays of `precision` (HYROM_PREC_F64 -> double, HYROM_PREC_F32
  *   -> float) except points (int32).  y_out: m doubles on the device.  Work is
  *   enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
- *   the call does not synchronise.  A rank-deficient P^T Phi gives
- *   non-finite y, as hyrom_stage_gappy does.
+ *   the call does not synchronise.  A rank-deficient P^T Phi (same
+ *   test as hyrom_stage_gappy) sets every y_j to NaN; the status, returned
+ *   before the work runs, stays HYROM_OK.
  *   err, err_len: optional caller buffer (may be NULL / 0) that receives a
  *   NUL-terminated reason on failure and an empty string on success.
  * Limits: 1 <= m <= 64 and m <= n_p <= min(128, ndof); other sizes return

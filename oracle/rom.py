@@ -159,28 +159,46 @@ def lambda_min_update_eig(M, rows):
     return out
 
 
-def lambda_min_update_secular(M, rows):
+def lambda_min_update_secular(M, rows, chunk=4096):
     """lambda_min(M + phi phi^T) for each phi in rows, as the smallest root
     of the secular equation 1 + sum_j z_j^2 / (lambda_j - mu) = 0 with
     M = W diag(lambda) W^T and z = W^T phi (Golub's rank-one modification
     of the symmetric eigenproblem).  The root lies in [lambda_1,
     min(lambda_2, lambda_1 + |z|^2)]; it is found by bisection to the last
-    bit.  When the secular function has no root there (z_1 = 0 or a double
-    eigenvalue) the bisection returns lambda_1, the correct answer."""
+    bit: a row stops when the midpoint of its bracket rounds to one of the
+    ends, and the upper end is returned.  The secular function is only
+    evaluated strictly inside (lambda_1, lambda_2), so no pole is touched.
+    When it has no root there the answer is lambda_1: z_1 = 0 (lambda_1
+    stays an eigenvalue and none falls below it) or a double eigenvalue
+    lambda_1 = lambda_2 (an empty bracket).  Rows are taken in chunks so the
+    work arrays stay small."""
     lam, Wm = np.linalg.eigh(M)
     Z = rows @ Wm
     z2 = Z * Z
-    lo = np.full(rows.shape[0], lam[0])
     if lam.size == 1:
         return lam[0] + z2[:, 0]
-    hi = np.minimum(lam[1], lam[0] + z2.sum(axis=1))
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        f = 1.0 + (z2 / (lam[None, :] - mid[:, None])).sum(axis=1)
-        below = f < 0.0
-        lo = np.where(below, mid, lo)
-        hi = np.where(below, hi, mid)
-    return hi
+    out = np.empty(rows.shape[0])
+    for a in range(0, rows.shape[0], chunk):
+        zc = z2[a:a + chunk]
+        lo = np.full(zc.shape[0], lam[0])
+        hi = np.minimum(lam[1], lam[0] + zc.sum(axis=1))
+        hi[zc[:, 0] == 0.0] = lam[0]
+        live = np.flatnonzero(lo < hi)
+        for _ in range(200):
+            if live.size == 0:
+                break
+            l, h = lo[live], hi[live]
+            mid = 0.5 * (l + h)
+            inside = (mid > l) & (mid < h)
+            live, l, h, mid = live[inside], l[inside], h[inside], mid[inside]
+            if live.size == 0:
+                break
+            f = 1.0 + (zc[live] / (lam[None, :] - mid[:, None])).sum(axis=1)
+            below = f < 0.0
+            lo[live] = np.where(below, mid, l)
+            hi[live] = np.where(below, h, mid)
+        out[a:a + chunk] = hi
+    return out
 
 
 def odeim_batched(Phi, n_p, tie_tol, b):

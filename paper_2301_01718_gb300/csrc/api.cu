@@ -386,6 +386,7 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   inf.k = k;
   inf.was_full = full;
   CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(ctx->fail_dev + 12, 0, sizeof(int), ctx->st));
   if (full) {
     t_begin(ctx, HYROM_T_FULL);
     if (cf.scheme == HYROM_SCHEME_RK2) {
@@ -450,6 +451,8 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
                                   &ctx->filt_graph, ctx->st);
     t_end(ctx, HYROM_T_FILTER);
   }
+  // physical-state check of the new snapshot (Euler): rho > 0 and p > 0
+  if (ctx->dc.nvar == 4) hy::launch_count_nonphys<T>(ctx->dc, q, ctx->fail_dev + 12, ctx->st);
   CKL();
   ctx->k = k;
   gram_update<T>(ctx, k);
@@ -457,12 +460,16 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (!full && cf.n_filt > 0)
     CK(cudaMemcpyAsync(hi + 1, ctx->fctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(hi + 2, ctx->fail_dev + 12, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (hyrom_status s = sync(ctx)) return s;
   inf.newton_fail = hi[0];
   inf.filt_passes = (!full && cf.n_filt > 0) ? hi[1] : 0;
   inf.n_p = ctx->np_eff;
   inf.m_eff = ctx->m_eff;
   if (info) *info = inf;
+  if (hi[2])
+    return fail(ctx, HYROM_ENONPHYS, "step %lld: %d cell(s) with rho <= 0 or p <= 0 or not finite",
+                (long long)k, hi[2]);
   if (inf.newton_fail) return fail(ctx, HYROM_ENOTCONV, "Newton hit newton_max in %d solve(s)", inf.newton_fail);
   return HYROM_OK;
 }
@@ -694,10 +701,19 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   for (int i = 0; i < w; ++i) ctx->psi_steps.push_back(k - w + 1 + i);
   ctx->has_basis = 1;
   CKL();
+  int* hq = (int*)ctx->host + 16;
+  hq[0] = 0;
+  if (me > 0) CK(cudaMemcpyAsync(hq, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if ((s = sync(ctx))) return s;
   inf.n_p = ctx->np_eff;
   inf.m_eff = ctx->m_eff;
   if (info) *info = inf;
+  // information: the step is complete, with fewer modes than asked for or
+  // a rank-deficient P^T Phi (its solve is truncated)
+  if (me < cf.m)
+    return fail(ctx, HYROM_ERANK, "step %lld: the window has rank %d < m = %d (POD kept %d modes)",
+                (long long)k, me, cf.m, me);
+  if (hq[0]) return fail(ctx, HYROM_ERANK, "step %lld: P^T Phi is rank-deficient", (long long)k);
   return HYROM_OK;
 }
 
@@ -957,10 +973,14 @@ hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info) {
   hyrom_step_info inf;
   memset(&inf, 0, sizeof inf);
   hyrom_status s = hyrom_advance(ctx, &inf);
-  if (s != HYROM_OK && s != HYROM_ENOTCONV) return s;
+  if (s != HYROM_OK && s != HYROM_ENOTCONV && s != HYROM_ENONPHYS) return s;
   hyrom_status s2 = hyrom_update_basis(ctx, &inf);
   if (info) *info = inf;
-  return s2 != HYROM_OK ? s2 : s;
+  // a failure of the rebuild first, then the advance's own condition, then
+  // the rebuild's rank information
+  if (s2 != HYROM_OK && s2 != HYROM_ERANK) return s2;
+  if (s != HYROM_OK) return s;
+  return s2;
 }
 
 hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t* n_out,
@@ -1087,15 +1107,19 @@ hyrom_status hyrom_stage_gappy(hyrom_ctx* ctx, const void* phi, int32_t m, const
   if (ctx->f32) {
     hy::launch_gappy_pinv<float>((const float*)phi, ctx->N, m, points, n_p, pinv, ctx->status, ctx->st);
     hy::launch_gappy_apply<float>(pinv, m, n_p, points, (const float*)v, (const float*)psi, y_out,
-                                  nullptr, nullptr, ctx->st);
+                                  nullptr, nullptr, ctx->st, ctx->status);
   } else {
     hy::launch_gappy_pinv<double>((const double*)phi, ctx->N, m, points, n_p, pinv, ctx->status, ctx->st);
     hy::launch_gappy_apply<double>(pinv, m, n_p, points, (const double*)v, (const double*)psi,
-                                   y_out, nullptr, nullptr, ctx->st);
+                                   y_out, nullptr, nullptr, ctx->st, ctx->status);
   }
   CKL();
   CK(cudaFreeAsync(pinv, ctx->st));
-  return sync(ctx);
+  int* hi = (int*)ctx->host;
+  CK(cudaMemcpyAsync(hi, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  if (hi[0]) return fail(ctx, HYROM_ERANK, "P^T Phi is rank-deficient (y set to NaN)");
+  return HYROM_OK;
 }
 
 hyrom_status hyrom_stage_gappy_rows(hyrom_ctx* ctx, const void* phi, int32_t m,

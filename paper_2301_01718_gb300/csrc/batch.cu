@@ -48,11 +48,14 @@ namespace {
 
 // One instance: nsteps steps in order; a failure other than a Newton solve
 // that hit its cap (whose state is still advanced) ends the instance's run.
+// The rank information HYROM_ERANK (a complete step with m_eff < m) is not a
+// failure and is not reported (m_eff is in the step info).
 void run_instance(hyrom_batch* b, int i) {
   hyrom_step_info info{};
   int32_t first = HYROM_OK;
   for (int s = 0; s < b->nsteps; ++s) {
-    const hyrom_status st = hyrom_step(b->ctx[i], &info);
+    hyrom_status st = hyrom_step(b->ctx[i], &info);
+    if (st == HYROM_ERANK) st = HYROM_OK;
     if (st != HYROM_OK && first == HYROM_OK) first = st;
     if (st != HYROM_OK && st != HYROM_ENOTCONV) break;
   }

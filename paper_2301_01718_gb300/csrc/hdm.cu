@@ -595,6 +595,33 @@ void launch_burgers_newton_partial(const DevCfg& c, const double* up, double* u,
                                                           tol_dev, newton_max, ws, fail);
 }
 
+// Cells of an Euler state that are not physical: rho <= 0, p <= 0 (ideal
+// gas, Sec. 3.1), or either not finite.  One count per call into *count
+// (which the caller clears).
+template <typename T>
+__global__ void k_count_nonphys(DevCfg c, const T* __restrict__ q, int* __restrict__ count) {
+  int bad = 0;
+  const T g1 = (T)(c.gamma - 1.0);
+  const T inf = (T)INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T r = q[i], mx = q[c.nc + i], my = q[2 * c.nc + i], en = q[3 * c.nc + i];
+    const T p = g1 * (en - (T)0.5 * (mx * mx + my * my) / r);
+    bad += !(r > (T)0 && r < inf && p > (T)0 && p < inf);
+  }
+  bad = __reduce_add_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, bad);
+}
+
+template <typename T>
+void launch_count_nonphys(const DevCfg& c, const T* q, int* count, cudaStream_t s) {
+  int64_t blocks = (c.nc + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_count_nonphys<T><<<(int)blocks, 256, 0, HY_S(s)>>>(c, q, count);
+}
+
+template void launch_count_nonphys<float>(const DevCfg&, const float*, int*, cudaStream_t);
+template void launch_count_nonphys<double>(const DevCfg&, const double*, int*, cudaStream_t);
 template void launch_rk2<float>(const DevCfg&, const float*, float*, int64_t, const uint32_t*,
                                  const int*, const int*, cudaStream_t);
 template void launch_rk2<double>(const DevCfg&, const double*, double*, int64_t, const uint32_t*,

@@ -78,6 +78,9 @@ void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
                 const int* tiles, const int* ntiles_dev, cudaStream_t s);
+// Euler cells with rho <= 0 or p <= 0 or not finite, added to *count.
+template <typename T>
+void launch_count_nonphys(const DevCfg& c, const T* q, int* count, cudaStream_t s);
 int rk2_tile_width(const DevCfg& c);
 int rk2_tile_height(const DevCfg& c);
 template <typename T>
@@ -130,7 +133,7 @@ size_t gappy_pinv_smem(int m, int np);
 template <typename T>
 void launch_gappy_apply(const double* pinv, int m, int np, const int* pts, const T* v,
                         const T* psi, double* y, const double* y_prev, double* dy,
-                        cudaStream_t s);
+                        cudaStream_t s, const int* rank_flag = nullptr);
 template <typename T>
 void launch_reconstruct(const T* phi, int64_t N, int64_t nc, int m, const double* y,
                         const T* psi, const uint32_t* s_hat, int only_set, T* q, cudaStream_t s);

@@ -110,8 +110,16 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
     }
     __syncthreads();
   }
-  bool bad = false;
-  for (int j = 0; j < m; ++j) bad |= (R[j * m + j] == 0.0);
+  // numerical rank: pivot j counts as zero when |R_jj| <= 64 n_p eps
+  // max_i |R_ii| (a QR without pivoting of a rank-deficient matrix, e.g. one
+  // with two equal rows and n_p = m, leaves a pivot of a few eps there); its
+  // reciprocal is taken as 0 below (a truncated solve) and *status is
+  // incremented
+  double rmax = 0.0;
+  for (int j = 0; j < m; ++j) rmax = fmax(rmax, fabs(R[j * m + j]));
+  const double rtol = 64.0 * (double)np * 2.220446049250313e-16 * rmax;
+  bool bad = rmax == 0.0;
+  for (int j = 0; j < m; ++j) bad |= !(fabs(R[j * m + j]) > rtol);
   if (bad && tid == 0) atomicAdd(status, 1);
   // pinv = R^{-1} Q^T: back substitution in shared memory (X, m x n_p, in
   // the reflectors' space, free once Q is formed), one thread per column i
@@ -127,7 +135,7 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
       }
       for (; cc < m; ++cc) p4[0] = fma(-R[r * m + cc], X[cc * np + i], p4[0]);
       const double rr = R[r * m + r];
-      X[r * np + i] = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * (rr != 0.0 ? rcp64(rr) : 0.0);
+      X[r * np + i] = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * (fabs(rr) > rtol ? rcp64(rr) : 0.0);
     }
   }
   __syncthreads();
@@ -148,11 +156,14 @@ size_t gappy_pinv_smem(int m, int np) {
 }
 
 // y = pinv (v[P] - psi[P]); also |y - y_prev|_2 into *dy when y_prev given.
+// With rank_flag given and non-zero (the QR found P^T Phi rank-deficient)
+// every y_j is set to NaN instead.
 template <typename T>
 __global__ void k_gappy_apply(const double* __restrict__ pinv, int m, int np,
                               const int* __restrict__ pts, const T* __restrict__ v,
                               const T* __restrict__ psi, double* __restrict__ y,
-                              const double* __restrict__ y_prev, double* dy) {
+                              const double* __restrict__ y_prev, double* dy,
+                              const int* __restrict__ rank_flag) {
   __shared__ double b[1024];
   __shared__ double ynew[256];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -173,15 +184,16 @@ __global__ void k_gappy_apply(const double* __restrict__ pinv, int m, int np,
     }
   }
   d2 = block_sum(d2);
-  for (int j = tid; j < m; j += blockDim.x) y[j] = ynew[j];
+  const bool deficient = rank_flag && *rank_flag != 0;
+  for (int j = tid; j < m; j += blockDim.x) y[j] = deficient ? __longlong_as_double(0x7ff8000000000000ll) : ynew[j];
   if (dy && tid == 0) *dy = sqrt(d2);
 }
 
 template <typename T>
 void launch_gappy_apply(const double* pinv, int m, int np, const int* pts, const T* v,
                         const T* psi, double* y, const double* y_prev, double* dy,
-                        cudaStream_t s) {
-  k_gappy_apply<T><<<1, 256, 0, HY_S(s)>>>(pinv, m, np, pts, v, psi, y, y_prev, dy);
+                        cudaStream_t s, const int* rank_flag) {
+  k_gappy_apply<T><<<1, 256, 0, HY_S(s)>>>(pinv, m, np, pts, v, psi, y, y_prev, dy, rank_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1494,7 +1506,8 @@ void launch_sign_fix(T* phi, int64_t N, int m, const int* m_eff, cudaStream_t s)
   template void launch_gappy_pinv<T>(const T*, int64_t, int, const int*, int, double*, int*,    \
                                      cudaStream_t);                                             \
   template void launch_gappy_apply<T>(const double*, int, int, const int*, const T*, const T*,  \
-                                      double*, const double*, double*, cudaStream_t);           \
+                                      double*, const double*, double*, cudaStream_t,            \
+                                      const int*);                                              \
   template void launch_reconstruct<T>(const T*, int64_t, int64_t, int, const double*, const T*, \
                                       const uint32_t*, int, T*, cudaStream_t);                  \
   template void launch_cell_error<T>(const T*, const T*, const T*, int64_t, int, int,           \

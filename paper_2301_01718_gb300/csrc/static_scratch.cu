@@ -26,7 +26,8 @@ constexpr int kStaticMaxM = 64;
 constexpr int kStaticMaxNp = 128;
 
 // m x n_p FP64 pseudo-inverse (64 x 128 doubles = 64 KB) and the counter the
-// QR kernel increments when a diagonal of R is zero.
+// QR kernel increments when a pivot of R is numerically zero (P^T Phi
+// rank-deficient); the second kernel then writes NaN into every y_j.
 __device__ __align__(256) double g_pinv_scratch[kStaticMaxM * kStaticMaxNp];
 __device__ __align__(256) int g_status_scratch[64];
 
@@ -109,12 +110,12 @@ extern "C" hyrom_status hyrom_gappy_static(const void* phi, int64_t ndof, int32_
   if (precision == HYROM_PREC_F32) {
     hy::launch_gappy_pinv<float>((const float*)phi, ndof, m, points, n_p, d->pinv, d->status, s);
     hy::launch_gappy_apply<float>(d->pinv, m, n_p, points, (const float*)v, (const float*)psi,
-                                  y_out, nullptr, nullptr, s);
+                                  y_out, nullptr, nullptr, s, d->status);
   } else {
     hy::launch_gappy_pinv<double>((const double*)phi, ndof, m, points, n_p, d->pinv, d->status,
                                   s);
     hy::launch_gappy_apply<double>(d->pinv, m, n_p, points, (const double*)v, (const double*)psi,
-                                   y_out, nullptr, nullptr, s);
+                                   y_out, nullptr, nullptr, s, d->status);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

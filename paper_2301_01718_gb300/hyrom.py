@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(_HERE, "libhyrom.so")
 
 HYROM_OK, HYROM_EINVAL, HYROM_ENOMEM, HYROM_ECUDA = 0, 1, 2, 3
 HYROM_ENOTCONV, HYROM_ESTATE, HYROM_ECAP, HYROM_ETIMEOUT = 4, 5, 6, 7
+HYROM_ERANK, HYROM_ENONPHYS = 8, 9
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ESTATE",
-                6: "ECAP", 7: "ETIMEOUT"}
+                6: "ECAP", 7: "ETIMEOUT", 8: "ERANK", 9: "ENONPHYS"}
 PREC_F64, PREC_F32 = 0, 1
 
 
@@ -225,19 +226,23 @@ def _info_call(fn, ctx, allow=()):
     s = fn(ctx, C.byref(info))
     if s not in allow:
         _check(ctx, s)
-    return info.as_dict()
+    d = info.as_dict()
+    d["status"] = s
+    return d
 
 
+# HYROM_ERANK reports a completed step (fewer modes than m, or a
+# rank-deficient sampled basis): returned in info["status"], not raised.
 def hyrom_advance(ctx):
     return _info_call(lib().hyrom_advance, ctx, allow=(HYROM_OK,))
 
 
 def hyrom_update_basis(ctx):
-    return _info_call(lib().hyrom_update_basis, ctx, allow=(HYROM_OK,))
+    return _info_call(lib().hyrom_update_basis, ctx, allow=(HYROM_OK, HYROM_ERANK))
 
 
 def hyrom_step(ctx):
-    return _info_call(lib().hyrom_step, ctx, allow=(HYROM_OK,))
+    return _info_call(lib().hyrom_step, ctx, allow=(HYROM_OK, HYROM_ERANK))
 
 
 def hyrom_sample(ctx, idx_dev=None, cap=0, bitmap_dev=None):

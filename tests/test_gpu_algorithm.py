@@ -7,6 +7,7 @@ import pytest
 import workloads as W
 from oracle import arom, hdm
 from tests.gpu_util import Ctx, dev, host, bits_of, rel_err, tdtype, torch
+from tests import oracle_spread
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +20,10 @@ def _cases():
                                pod_abs=1e-13, top_frac=0.05), 16
     q, c, _ = W.euler_oblique_shock(n=64, seed=3, k=3)
     yield "shock", q, c.with_(precision=W.PREC_F64, pod_tol=1e-10, pod_abs=1e-13), 16
+    # the benchmark's problem at 128^2 with k = 16, w = 32, n_p = 32: six
+    # rebuilds after the warm-up
+    q, c, _ = W.euler_oblique_shock(n=128, seed=3, k=16)
+    yield "shock128_k16", q, c.with_(precision=W.PREC_F64, pod_tol=1e-10, pod_abs=1e-13), 38
     # the sample-row form of the reduced solve (all dof rows of S-hat)
     u, c, _ = W.burgers_sine(n=256, seed=1)
     yield "burgers_sample_rows", u, c.with_(w=8, m=4, n_p=8, regress_rows=W.ROWS_SAMPLE), 30
@@ -51,18 +56,33 @@ def _lockstep(q0, cfg, steps):
 
 @pytest.mark.parametrize("name,q0,cfg,steps", list(_cases()), ids=[c[0] for c in _cases()])
 def test_fp64_lockstep_with_oracle(name, q0, cfg, steps):
+    """Every step: the same schedule and rank, identical sampled sets at every
+    rebuild, full steps bit for bit, and states within 1e-12 relative of the
+    oracle, or within 100x the drift between two oracle runs that differ
+    only in the rounding order of their POD once the method has amplified
+    that drift beyond 1e-14 (tests/oracle_spread.py; measured worst GPU
+    drift: 2.5e-10 after 11 hybrid steps of the 64^2 shock with k = 3,
+    where two oracle runs drift 2.6e-11 apart)."""
     recs = _lockstep(q0, cfg, steps)
-    worst = 0.0
-    for r in recs:
+    spread = oracle_spread.spread(q0, cfg, steps, [r["want"] for r in recs])
+    worst_full = worst_hyb = 0.0
+    per_step = []
+    for r, sp in zip(recs, spread):
         assert bool(r["info"]["was_full"]) == r["oinfo"].was_full
         assert bool(r["info"]["rebuilt"]) == r["oinfo"].rebuilt
         assert r["info"]["m_eff"] == r["oinfo"].m_eff
         e = rel_err(r["state"], r["want"])
-        worst = max(worst, e)
-        assert e < 1e-9, f"step {r['k']}: rel err {e}"
+        per_step.append((e, sp))
+        if r["oinfo"].was_full:
+            worst_full = max(worst_full, e)
+            assert e == 0.0, f"full step {r['k']}: rel err {e}"
+        else:
+            worst_hyb = max(worst_hyb, e)
+        assert e <= oracle_spread.bar(sp), f"step {r['k']}: rel err {e}, oracle spread {sp}"
         if "mask" in r:
             assert np.array_equal(r["mask"], r["want_mask"]), f"step {r['k']}: masks differ"
-    print(f"{name}: worst rel err {worst:.3e}")
+    print(f"{name}: worst rel err full steps {worst_full:.3e}, hybrid steps {worst_hyb:.3e}; "
+          f"per step (gpu, oracle spread) {['%.1e/%.1e' % p for p in per_step]}")
 
 
 def test_fp32_vortex_tracks_fp64_oracle():

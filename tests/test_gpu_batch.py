@@ -62,6 +62,7 @@ def test_batch_matches_instances_stepped_alone(kind):
     try:
         for ctx, (_, cfg) in zip(ctxs, insts):
             infos = [hy.hyrom_step(ctx) for _ in range(steps)]
+            infos[-1].pop("status")     # the batch reports statuses separately
             alone_info.append(infos[-1])
             alone.append(_state(hy, ctx, cfg))
     finally:
@@ -103,7 +104,8 @@ def test_batched_fp64_instance_tracks_oracle():
         finally:
             hy.hyrom_batch_destroy(b)
         e = rel_err(_state(hy, ctxs[0], cfg), A.gamma.reshape(-1))
-        assert e < 1e-9, e
+        print(f"batched FP64 instance after {steps} steps: rel err {e:.2e}")
+        assert e < 1e-12, e
     finally:
         for c in ctxs:
             hy.hyrom_destroy(c)

@@ -242,3 +242,84 @@ def test_odeim_points_identical(prec, N, m, n_p, conc):
         hy.hyrom_stage_odeim(ctx, dev(Phi.T.copy(), dt), m, n_p, pts)
         got = host(pts).tolist()
     assert got == want
+
+
+def _golden_odeim_cases():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "odeim_front_basis.json")
+    with open(path) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_odeim_cases(), ids=lambda c: c["prec"])
+def test_odeim_points_identical_at_benchmark_size(case):
+    """ODEIM at the 2048^2 benchmark's sizes (m = 64 modes, n_p = 128 points)
+    on 102 400 rows, so that the 2048-row probe, the norm-bucket pruning, the
+    rising exact-score limit and the four-rows-per-CTA exact scoring all run:
+    the points must equal the oracle's row for row.  The oracle needs ~5 s per
+    oversampling step here, so its points were written by
+    tests/golden/make_odeim_golden.py (oracle.rom.odeim only) for the same
+    bits of workloads.front_basis, which the SHA-256 checks first."""
+    import hashlib
+    prec = W.PREC_F64 if case["prec"] == "f64" else W.PREC_F32
+    Phi = W.front_basis(case["nrow"], case["m"], case["seed"])
+    if prec == W.PREC_F32:
+        Phi = Phi.astype(np.float32).astype(np.float64)
+    assert hashlib.sha256(np.ascontiguousarray(Phi).tobytes()).hexdigest() == case["sha256"]
+    N, m, n_p = case["nrow"], case["m"], case["n_p"]
+    cfg = W.ArConfig(pde=W.PDE_BURGERS, scheme=W.SCHEME_RK2, nx=N, ny=1, dx=1.0 / N, dy=1.0,
+                     dt=1e-3, w=2 * m, m=m, n_p=n_p, precision=prec, tie_tol=case["tie_tol"])
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        pts = torch.zeros(n_p, dtype=torch.int32, device="cuda")
+        hy.hyrom_stage_odeim(ctx, dev(Phi.T.copy(), dt), m, n_p, pts)
+        got = host(pts).tolist()
+        cnt = hy.hyrom_odeim_counters(ctx)
+    print(f"{case['prec']}: {cnt}")
+    assert got == case["points"]
+
+
+def test_pod_fp32_benchmark_shape():
+    """FP32 POD at the benchmark's window and basis sizes (w = 128, m = 64):
+    the eigensolve runs in a 16-CTA thread-block cluster and the tensor-core
+    basis product in four chunks of the window per row tile.  Rows: an Euler
+    160 x 160 grid (102 400 rows, 800 row tiles); the bars are those of
+    test_pod_fp32_wide_basis."""
+    w, m = 128, 64
+    cfg = W.ArConfig(pde=W.PDE_EULER, scheme=W.SCHEME_RK2, nx=160, ny=160, dx=0.1, dy=0.1,
+                     dt=0.01, w=w, m=m, n_p=2 * m, precision=W.PREC_F32, pod_tol=1e-6,
+                     pod_abs=1e-6)
+    N = cfg.ndof
+    g = np.random.Generator(np.random.PCG64(4096))
+    U, _ = np.linalg.qr(g.standard_normal((N, w)))
+    V, _ = np.linalg.qr(g.standard_normal((w, w)))
+    sig = 0.93 ** np.arange(w)
+    psi = (1.0 + g.standard_normal(N) * 0.1).astype(np.float32).astype(np.float64)
+    X = (psi[:, None] + (U * sig) @ V.T).astype(np.float32).astype(np.float64)
+    raw = float(np.sqrt((X * X).sum()))
+    Phi_o, s_o = rom.pod(X - psi[:, None], m, cfg.pod_tol, cfg.pod_abs * raw)
+    with Ctx(cfg) as (hy, ctx):
+        phi = torch.zeros(m * N, dtype=torch.float32, device="cuda")
+        sg = torch.zeros(w, dtype=torch.float64, device="cuda")
+        me = hy.hyrom_stage_pod(ctx, dev(X.T.copy(), torch.float32), w,
+                                dev(psi, torch.float32), phi, sg)
+        sweeps = hy.hyrom_eig_sweeps(ctx)
+        Pg = host(phi)[: me * N].reshape(me, N).T.astype(np.float64)
+        sg = host(sg)
+    assert me == Phi_o.shape[1] == m
+    e_sig = rel_err(sg[:m], s_o[:m])
+    nrm = np.linalg.norm(Pg, axis=0)
+    worst = max(1.0 - abs(float(Pg[:, j] @ Phi_o[:, j])) / nrm[j] for j in range(m))
+    print(f"sigma rel err {e_sig:.2e}, worst 1 - cos {worst:.2e}, sweeps {sweeps}")
+    assert e_sig < 1e-5
+    # column lengths: the FP32 bar (measured 1.5e-6, every column slightly
+    # short: the tensor cores' FP32 accumulation over the four chunks of the
+    # 128-snapshot window rounds towards zero)
+    assert np.abs(nrm - 1.0).max() < 1e-5
+    for j in range(m):
+        c = abs(float(Pg[:, j] @ Phi_o[:, j])) / nrm[j]
+        assert 1.0 - c < 1e-10 * (s_o[0] / s_o[j]) ** 2 + 1e-11, (j, 1.0 - c)
+    # orthonormality: an entry of Phi^T Phi - I carries both columns' FP32
+    # errors (measured 1.08e-5, the short column lengths above included)
+    assert np.abs(Pg.T @ Pg - np.eye(m)).max() < 2e-5

@@ -339,3 +339,30 @@ def random_spectrum_window(nrow, w, seed, decay=0.5, offset=1.0):
     V, _ = np.linalg.qr(g.standard_normal((w, w)))
     sig = decay ** np.arange(w)
     return offset + (U * sig) @ V.T, sig
+
+
+def splitmix64_array(seed: int, n: int) -> np.ndarray:
+    """The first n splitmix64 outputs of `seed`, vectorised (uint64 numpy
+    arithmetic wraps modulo 2^64 exactly as the scalar generator does)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & MASK64) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def front_basis(nrow, m, seed, period=700, width=90.0):
+    """A localised N x m basis like one POD builds around a moving front,
+    made only from splitmix64 draws and IEEE-exact operations (+, -, *, /), so
+    that it is the same bits on every machine: column j is uniform noise in
+    [-1/2, 1/2) times the rational bump 1 / (1 + (d / width)^2) + 1e-3 of the
+    distance d = (row mod period) - c_j to a seeded centre c_j.  Not
+    orthonormal (the point-selection stages do not need it).  Returns
+    float64 [nrow, m]."""
+    u = (splitmix64_array(seed, nrow * m) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    u = u.reshape(nrow, m) - 0.5
+    cj = (splitmix64_array(seed ^ 0x5DEECE66D, m) % np.uint64(period)).astype(np.float64)
+    d = (np.arange(nrow) % period).astype(np.float64)[:, None] - cj[None, :]
+    t = d / width
+    return u * (1.0 / (1.0 + t * t) + 1e-3)
