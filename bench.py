@@ -577,7 +577,7 @@ def full_step(a, calls=20, pairs=4):
     byts = 2.0 * 4 * 4 * cfg.ncell
     peaks = _peaks()
     gbs = byts / (ms * 1e-3) / 1e9
-    return {"kernel": "k_rk2_euler", "grid": f"{cfg.nx}x{cfg.ny}", "ms_per_launch": ms,
+    return {"kernel": "k_rk2_euler_sweep", "grid": f"{cfg.nx}x{cfg.ny}", "ms_per_launch": ms,
             "launches": cnt, "bytes_per_launch": byts, "achieved_gbs": gbs,
             "peak_gbs": peaks["hbm"], "frac": gbs / peaks["hbm"], "peak_source": peaks["src"]}
 

@@ -329,6 +329,13 @@ void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* 
   const int nt = ntx * nty;
   int grid = tiles ? (nt < 152 * 8 ? nt : 152 * 8) : nt;
   if (grid < 1) grid = 1;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 full step: the register-sweep kernel of hdm_f32.cu
+    if (!mask && !tiles && rk2_euler_sweep_ok(c)) {
+      launch_rk2_euler_sweep(c, (const float*)q, (float*)out, k, s);
+      return;
+    }
+  }
   if (c.nvar == 4) {
     if (twoD) {
       constexpr size_t sm = rk2_euler_smem<T, 32, 8>();

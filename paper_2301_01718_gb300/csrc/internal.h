@@ -78,6 +78,11 @@ void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
                 const int* tiles, const int* ntiles_dev, cudaStream_t s);
+// FP32 full SSP-RK2 step of the 2D Euler equations streamed by warp strips
+// (hdm_f32.cu); rk2_euler_sweep_ok tells whether it takes the grid.
+bool rk2_euler_sweep_ok(const DevCfg& c);
+void launch_rk2_euler_sweep(const DevCfg& c, const float* q, float* out, int64_t k,
+                            cudaStream_t s);
 // Euler cells with rho <= 0 or p <= 0 or not finite, added to *count.
 template <typename T>
 void launch_count_nonphys(const DevCfg& c, const T* q, int* count, cudaStream_t s);

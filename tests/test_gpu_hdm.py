@@ -22,6 +22,14 @@ def _cases():
     yield "shock72", q, c
     q, c, _ = W.euler_oblique_shock(n=45, seed=6, k=4)   # ragged, shock and outflow sides
     yield "shock45", q, c
+    # FP32 takes a register-sweep kernel (warp strips of 28 columns x 32
+    # rows): several strips wide and high, ragged in both directions, with
+    # strips that touch no side
+    q, c, _ = W.euler_oblique_shock(n=300, seed=7, k=4)
+    yield "shock300x203", q.reshape(4, 300, 300)[:, :203, :].reshape(4, -1).copy(), \
+        c.with_(ny=203)
+    q, c, _ = W.euler_vortex(n=131, seed=8)
+    yield "vortex131", q, c
     q, c = W.euler_riemann_x(n=200)
     yield "sod200", q, c
     u, c, _ = W.burgers_sine(n=300, seed=2)
