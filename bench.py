@@ -93,13 +93,12 @@ def config_dict(a, cfg):
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_rate(a, steps=2, warmup=0):
-    """Time `steps` hybrid steps of the oracle on a cpu_n^2 grid of the same
-    workload (after its untimed warm-up: the method's w full steps and first
-    rebuild, then `warmup` hybrid steps); scale steps/s by cells to the
-    benchmark grid (the oracle's cost per step is linear in the cells)."""
+def _oracle_step_time(a, n, steps, warmup):
+    """Seconds per hybrid step of the oracle on an n^2 grid of the workload
+    (after its untimed warm-up: the method's w full steps and first rebuild,
+    then `warmup` hybrid steps), and the sampled cells per step."""
     from oracle import arom
-    q0, cfg = workload(a, n=a.cpu_n, prec=W.PREC_F64)
+    q0, cfg = workload(a, n=n, prec=W.PREC_F64)
     A = arom.Arom(q0, cfg)
     while True:
         info = A.step()
@@ -111,13 +110,36 @@ def cpu_oracle_rate(a, steps=2, warmup=0):
     t0 = time.perf_counter()
     for _ in range(steps):
         ns += A.step().n_s
-    dt = time.perf_counter() - t0
-    scale = (a.cpu_n * a.cpu_n) / float(a.n * a.n)
-    return {"value": steps / dt * scale, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-            "sample": f"{steps} hybrid steps of the same workload on a {a.cpu_n}x{a.cpu_n} grid "
-                      f"(k={cfg.m}, w={cfg.w}) in {dt:.1f} s, steps/s scaled by cells "
-                      f"({a.cpu_n}^2/{a.n}^2)",
-            "sample_steps_per_s": steps / dt, "sample_cell_updates_per_s": ns / dt}
+    return (time.perf_counter() - t0) / steps, ns / steps, cfg
+
+
+def cpu_oracle_rate(a, steps=3, warmup=0, steps_large=None):
+    """The oracle's hybrid steps/s at the benchmark grid, from timed samples of
+    the same workload on two small grids (cpu_n^2 and (2 cpu_n)^2, `steps`
+    hybrid steps each; steps_large on the larger one if given).  The
+    oracle's time per step is not proportional to the
+    cells at these sizes (a fixed part: the m x m eigenproblems and Python
+    work of ODEIM's greedy steps), so it is fitted as t = t0 + t1 * cells
+    through the two samples and evaluated at the benchmark's cells; the rate
+    scaled by cells from the small grid alone is reported beside it."""
+    n1, n2 = a.cpu_n, 2 * a.cpu_n
+    t_1, ns1, cfg = _oracle_step_time(a, n1, steps, warmup)
+    s2 = steps if steps_large is None else steps_large
+    t_2, ns2, _ = _oracle_step_time(a, n2, s2, 0 if steps_large is not None else warmup)
+    c1, c2, cb = n1 * n1, n2 * n2, a.n * a.n
+    t1c = (t_2 - t_1) / (c2 - c1)
+    t0c = t_1 - t1c * c1
+    t_big = t0c + t1c * cb
+    return {"value": 1.0 / t_big, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"{steps} and {s2} hybrid steps of the same workload (k={cfg.m}, "
+                      f"w={cfg.w}) on {n1}x{n1} ({t_1:.2f} s/step) and {n2}x{n2} "
+                      f"({t_2:.2f} s/step); "
+                      f"time per step fitted as {t0c:.3g} s + {t1c:.3g} s/cell and "
+                      f"evaluated at {a.n}x{a.n}",
+            "s_per_step": {f"{n1}x{n1}": t_1, f"{n2}x{n2}": t_2},
+            "fit_s_per_step": {"fixed": t0c, "per_cell": t1c},
+            "scaled_by_cells_from_smallest": 1.0 / (t_1 * cb / c1),
+            "sample_cell_updates_per_s": ns1 / t_1}
 
 
 def _cores():
@@ -192,6 +214,52 @@ def stage_bytes(cfg, m_eff, n_s_avg, s=4):
         "gram": s * N * (w + 1),
         # error indicator: read g, psi, Phi; write eps; keys and radix passes
         "select": s * N * (m_eff + 2) + s * nc + 8 * nc * 9,
+    }
+
+
+def fp64_peak_tflops():
+    """This GPU's FP64 rate from the library's FMA loop (hyrom_probe_fp64),
+    timed with CUDA events: the denominator of the FP64 stages' roofline."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    blocks, iters, reps = 152 * 16, 2048, 5
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        hyrom.hyrom_probe_fp64(out, blocks, iters, st.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        hyrom.hyrom_probe_fp64(out, blocks, iters, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    flops = reps * blocks * 256 * 16 * iters
+    return flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def stage_costs(cfg, m_eff, n_s_avg, n_p, sweeps_pod, s=4):
+    """Work of the stages that stream no state-sized operand once, per step:
+      partial  - the partial RK2 step on S-hat: read gamma_{k-1} on S-hat and
+                 its 2-cell ring, write gamma_k on S-hat (c s (n_s + ring) 3)
+      filter   - the first pass of each of the three orders over the grid:
+                 read q and gamma_{k-1}, write g and the gate (~ s N 5)
+      deim     - the greedy DEIM loop as written, one residual pass over Phi's
+                 first l columns per point: s N (m^2/2 + 3m/2)  (naive)
+      odeim    - the oversampling loop as written, one scoring pass over Phi
+                 per point: s N m (n_p - m)  (naive)
+      eig      - the POD eigensolve, one-sided Jacobi on the w x w factor:
+                 ~12 w flops per column pair and sweep, 6 w^3 per sweep, plus
+                 w^3/3 for the pivoted Cholesky (FP64 flops)
+    The two ODEIM stages prune rows with certified bounds, so their naive
+    bytes over time exceed the HBM rate: the ratio is the pruning's gain."""
+    N, nc, w, m = cfg.ndof, cfg.ncell, cfg.w, m_eff
+    ring = 4 * (n_s_avg ** 0.5) * 2 if cfg.ny > 1 else 4
+    return {
+        "partial": ("bytes", s * cfg.nvar * (n_s_avg + ring) * 3),
+        "filter": ("bytes", 3 * s * N * 5),
+        "deim": ("bytes_naive", s * N * (m * m / 2 + 1.5 * m)),
+        "odeim": ("bytes_naive", s * N * m * max(n_p - m, 0)),
+        "eig": ("fp64_flops", sweeps_pod * 6.0 * w ** 3 + w ** 3 / 3.0),
     }
 
 
@@ -293,12 +361,26 @@ def run_ours(a):
     per = {}
     byts = stage_bytes(cfg, m_eff, n_s_avg)
     peaks = _peaks()
+    fp64 = fp64_peak_tflops() if rank == 0 else None
+    costs = stage_costs(cfg, m_eff, n_s_avg, infos[-1]["n_p"], eig_sw["pod"])
     for name, (tot, cnt) in stages.items():
         if cnt == 0:
             continue
-        d = {"ms_per_step": tot / a.steps, "launches": cnt, "ms_per_launch": tot / cnt}
+        d = {"ms_per_step": tot / a.steps, "launches": cnt, "ms_per_launch": tot / cnt,
+             "share_of_step": (tot / a.steps) / (ms_max / a.steps)}
         if name in byts:
             d["gbs"] = byts[name] / (tot / cnt * 1e-3) / 1e9
+            d["frac_of_hbm"] = d["gbs"] / peaks["hbm"]
+        elif name in costs:
+            kind, amount = costs[name]
+            rate = amount / (tot / a.steps * 1e-3)
+            if kind == "fp64_flops":
+                d["fp64_tflops"] = rate / 1e12
+                if fp64:
+                    d["frac_of_fp64"] = rate / 1e12 / fp64
+            else:
+                d["gbs" if kind == "bytes" else "naive_gbs"] = rate / 1e9
+                d["frac_of_hbm" if kind == "bytes" else "naive_over_hbm"] = rate / 1e9 / peaks["hbm"]
         per[name] = d
     # roofline of the dominant kernel with an algorithmic byte count
     cand = [(per[n]["ms_per_step"], n) for n in byts if n in per]
@@ -323,13 +405,16 @@ def run_ours(a):
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": config_dict(a, cfg),
-           "sampled_cell_updates_per_s": world * ns_sum / (ms_max / 1e3),
+           "sampled_cell_updates_per_s": (world * ns_sum / (stages["partial"][0] / 1e3)
+                                          if stages.get("partial", (0, 0))[0] > 0 else None),
+           "sampled_cells_per_s_of_step": world * ns_sum / (ms_max / 1e3),
+           "fp64_peak_tflops_measured": fp64,
            "n_s_avg": n_s_avg, "m_eff": m_eff, "stages": per,
            "roofline": roof, "gpu_launches": int(launches), "clocks": ck, "e2e": e2e,
            "odeim_counters_last_step": odc, "eig_sweeps_last_step": eig_sw,
            "without_odeim": no_a7}
     if rank == 0 and not a.no_err:
-        out["err_vs_fp64"] = err_vs_fp64(a)
+        out["err_vs_oracle"] = err_vs_oracle(a)
     if rank == 0 and not a.no_precision_form:
         out["precision_form"] = precision_form(a)
     if rank == 0:
@@ -360,38 +445,78 @@ def _peaks():
         return {"hbm": 6800.0, "src": "fallback 6.8 TB/s"}
 
 
-def err_vs_fp64(a, n=256, steps=12, **kw):
-    """FP32 GPU run against the FP64 GPU run (itself checked against the
-    oracle by the parity tests) of the same workload on an n^2 grid: relative
-    L1 and max errors of the state after `steps` hybrid steps.  kw: config
-    fields of the FP32 run (the FP64 run keeps the FP32 normal matrix, the
-    only one FP64 states have)."""
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(q0, cfg, steps_hyb):
+    """The oracle's states and sampled sets for the first `steps_hyb` hybrid
+    steps of Algorithm 1 (cached per configuration)."""
+    from oracle import arom
+    key = repr(cfg)
+    if key not in _ORACLE_RUNS:
+        A = arom.Arom(q0, cfg)
+        recs, hyb = [], 0
+        while hyb < steps_hyb:
+            info = A.step()
+            if not info.was_full:
+                hyb += 1
+            recs.append((info.was_full, info.rebuilt, A.gamma.reshape(-1).copy(),
+                         None if A.s_hat is None else A.s_hat.reshape(-1).copy()))
+        _ORACLE_RUNS[key] = recs
+    return _ORACLE_RUNS[key]
+
+
+def err_vs_oracle(a, n=128, k=16, steps=12, **kw):
+    """The FP32 GPU run against the FP64 oracle on an n^2 grid of the same
+    workload with k modes (w = n_p = 2k): per hybrid step the relative L1 and
+    max errors of the state and, at every rebuild, the Hamming distance
+    between the two sampled sets S-hat (cells in one and not the other).  The
+    two runs take their decisions (filter gates, selection, ODEIM points)
+    each in its own arithmetic, so the sets can part where an FP32 value sits
+    at a tie.  kw: further config fields of both runs."""
     import torch
     from paper_2301_01718_gb300 import hyrom
-    outs = {}
-    for prec in (W.PREC_F32, W.PREC_F64):
-        q0, cfg = workload(a, n=n, prec=prec)
-        if kw:
-            cfg = cfg.with_(**kw)
-        if prec == W.PREC_F64:
-            cfg = cfg.with_(pod_tol=1e-10, pod_abs=1e-13, reduced_prec=W.RED_F32)
-        q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
-        ctx = hyrom.hyrom_init(cfg, q0d)
-        try:
-            hyb = 0
-            while hyb < steps:
-                info = hyrom.hyrom_step(ctx)
-                hyb += 0 if info["was_full"] else 1
-            q = torch.zeros(cfg.ndof, dtype=torch.float32 if prec == W.PREC_F32 else torch.float64,
-                            device="cuda")
+    q0, cfg = workload(a, n=n, prec=W.PREC_F32)
+    cfg = cfg.with_(w=2 * k, m=k, n_p=2 * k, **kw)
+    ocfg = cfg.with_(precision=W.PREC_F64, reduced_prec=W.RED_F32)
+    want = _oracle_run(q0, ocfg, steps)
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q0d)
+    per = []
+    try:
+        q = torch.zeros(cfg.ndof, dtype=torch.float32, device="cuda")
+        bm = torch.zeros((cfg.ncell + 31) // 32, dtype=torch.int32, device="cuda")
+        for was_full, rebuilt, g_o, sh_o in want:
+            info = hyrom.hyrom_step(ctx)
+            if bool(info["was_full"]) != was_full:
+                raise RuntimeError("full/hybrid schedules differ")
+            if was_full:
+                continue
             hyrom.hyrom_get_state(ctx, q)
-            outs[prec] = q.double().cpu().numpy()
-        finally:
-            hyrom.hyrom_destroy(ctx)
-    d = outs[W.PREC_F32] - outs[W.PREC_F64]
-    return {"grid": f"{n}x{n}", "hybrid_steps": steps,
-            "rel_l1": float(np.abs(d).sum() / np.abs(outs[W.PREC_F64]).sum()),
-            "rel_max": float(np.abs(d).max() / np.abs(outs[W.PREC_F64]).max())}
+            g = q.double().cpu().numpy()
+            rec = {"k": int(info["k"]), "rel_l1": float(np.abs(g - g_o).sum() / np.abs(g_o).sum()),
+                   "rel_max": float(np.abs(g - g_o).max() / np.abs(g_o).max())}
+            if rebuilt:
+                hyrom.hyrom_sample(ctx, bitmap_dev=bm)
+                w = bm.cpu().numpy().view(np.uint32).astype(np.uint64)
+                bits = ((w[:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1))
+                sh = bits.reshape(-1)[: cfg.ncell].astype(bool)
+                rec["hamming"] = int(np.count_nonzero(sh != sh_o))
+                rec["n_s"] = int(sh_o.sum())
+            per.append(rec)
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    ham = [r["hamming"] for r in per if "hamming" in r]
+    return {"grid": f"{n}x{n}", "k": k, "w": 2 * k, "n_p": 2 * k, "hybrid_steps": len(per),
+            "max_rel_l1": max(r["rel_l1"] for r in per),
+            "max_rel_max": max(r["rel_max"] for r in per),
+            "max_hamming": max(ham) if ham else None,
+            "steps_with_identical_masks": sum(1 for h in ham if h == 0),
+            "per_step": per}
+
+
+def _err_summary(e):
+    return {k: v for k, v in e.items() if k != "per_step"}
 
 
 PRECISIONS = {"f32_cuda_cores": W.RED_F32, "tf32": W.RED_TF32, "bf16": W.RED_BF16,
@@ -404,7 +529,8 @@ def precision_form(a):
     TF32 and BF16 on the tensor cores (FP32 accumulation), and the TF32 hi/lo
     split; states, flux and right-hand side FP32, Cholesky and solve FP64.
     Per variant: the normal matrix's time per rebuild, steps/s of the whole
-    step on the benchmark workload, and the state error against FP64."""
+    step on the benchmark workload, and the state error against the FP64
+    oracle's sample-row run (err_vs_oracle)."""
     import torch
     from paper_2301_01718_gb300 import hyrom
     out = {}
@@ -438,8 +564,8 @@ def precision_form(a):
         out[name] = {"snormal_ms_per_rebuild": tot / max(cnt, 1), "rebuilds": cnt,
                      "gappy_ms_per_step": gt / a.precision_steps,
                      "steps_per_s": a.precision_steps / (ms / 1e3),
-                     "err_vs_fp64": None if a.no_err else err_vs_fp64(
-                         a, regress_rows=W.ROWS_SAMPLE, reduced_prec=red)}
+                     "err_vs_oracle": None if a.no_err else _err_summary(err_vs_oracle(
+                         a, regress_rows=W.ROWS_SAMPLE, reduced_prec=red))}
     return {"workload": "same grid and method, reduced coordinates fitted on every dof row "
                         "of S-hat (normal equations)", "steps": a.precision_steps,
             "variants": out}
@@ -686,13 +812,14 @@ def rk2_vjp(a, n=1024, calls=10):
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
-    workload), steps/s scaled by cells to the benchmark grid."""
+    workload; up to 3 more on the (2 cpu_n)^2 grid for the size fit of
+    cpu_oracle_rate), steps/s extrapolated to the benchmark grid."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     _, cfg = workload(a)
     steps = max(1, a.steps)
-    cb = cpu_oracle_rate(a, steps=steps, warmup=a.warmup)
+    cb = cpu_oracle_rate(a, steps=steps, warmup=a.warmup, steps_large=min(steps, 3))
     return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -383,6 +383,13 @@ void hyrom_batch_destroy(hyrom_batch* batch);
  * HYROM_ECUDA (launch). */
 hyrom_status hyrom_selftest_math(int32_t which, const double* x, double* y, int64_t n,
                                  void* stream);
+/* hyrom_probe_fp64: a dense FP64 FMA loop for measuring this GPU's FP64 rate
+ * (the roofline of the FP64-bound stages; the paper has no counterpart):
+ * `blocks` blocks of 256 threads, each thread 8 independent FMA chains of
+ * `iters` steps, i.e. blocks * 256 * 16 * iters flops; out receives one
+ * double per thread (device, blocks * 256 entries).  Enqueued on `stream`;
+ * the caller times it.  Errors: HYROM_EINVAL, HYROM_ECUDA. */
+hyrom_status hyrom_probe_fp64(double* out, int32_t blocks, int32_t iters, void* stream);
 
 /* ---- allocation-free variant ---------------------------------------------
  * hyrom_gappy_static: the gappy reduced coordinates of hyrom_stage_gappy,

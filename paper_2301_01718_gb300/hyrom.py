@@ -138,6 +138,7 @@ def lib():
         "hyrom_stage_gappy_rows": (st, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
         "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
+        "hyrom_probe_fp64": (st, [vp, i32, i32, vp]),
         "hyrom_stage_rk2_vjp": (st, [vp, vp, vp, vp, vp, i64, vp]),
         "hyrom_reduced_vjp_work_doubles": (C.c_size_t, [i32, i32]),
         "hyrom_stage_reduced_vjp": (st, [vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -341,6 +342,13 @@ def hyrom_selftest_math(which, x, y, stream=None):
     s = lib().hyrom_selftest_math(int(which), _ptr(x), _ptr(y), int(x.numel()), _ptr(stream))
     if s != HYROM_OK:
         raise HyromError(s, "hyrom_selftest_math")
+
+
+def hyrom_probe_fp64(out, blocks, iters, stream=None):
+    """Enqueue the FP64 FMA loop (blocks * 256 * 16 * iters flops)."""
+    s = lib().hyrom_probe_fp64(_ptr(out), int(blocks), int(iters), _ptr(stream))
+    if s != HYROM_OK:
+        raise HyromError(s, "hyrom_probe_fp64")
 
 
 def hyrom_batch_create(ctxs, threads=0):
