@@ -13,9 +13,8 @@ Readings where the paper is silent:
   * implicit schemes (BDF1, and the paper's MUSCL-Roe-BDF2 HDM of
     oracle/hdm_muscl.py): subiterations j = 1..J stop when
     ||y^(j) - y^(j-1)||_2 < eps_y (checked from j = 2) or j = jmax; with the
-    MUSCL HDM the filter's gate uses that HDM's f* in the first-order form
-    q - gamma_{k-1} - dt f*(q) (the BDF2 residual put the paper's Sod case
-    further from the paper's printed figures).
+    MUSCL HDM the filter's gate is that HDM's own residual R_k of Eq. hdm
+    (BDF2; BDF1 at the first step), the residual Sec. 2.3.4 names.
   * psi, Phi, P "in effect": when a rebuild was skipped (mod(k+1, z) = 0)
     the most recent ones are used by the next RRE and POD.  The RRE needs a
     basis; before the first rebuild G is empty.
@@ -106,9 +105,9 @@ class Arom:
         t = k * cfg.dt
         muscl = cfg.scheme == W.SCHEME_BDF2_MUSCL
         prev2 = self.snaps.get(k - 2) if muscl else None
-        # the filter's gate: the first-order form q - gamma_{k-1} - dt f*(q) of
-        # the HDM in use (as for the explicit scheme)
-        resid = (lambda q: (q - prev) - cfg.dt * hdm_muscl.rhs(q, cfg, t)) if muscl else None
+        # the filter's gate (Sec. 2.3.4): the residual R_k of Eq. hdm, i.e. for
+        # the paper's HDM the BDF2 residual (BDF1 at the first step)
+        resid = (lambda q: hdm_muscl.residual(q, prev, prev2, cfg, t)) if muscl else None
         if info.was_full:
             if muscl:                                             # the paper's HDM
                 gam = hdm_muscl.step(prev, prev2, cfg, k)

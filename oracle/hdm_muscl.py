@@ -12,8 +12,12 @@ Readings where the paper is silent:
     (zero when the two differences differ in sign, else the one of smaller
     magnitude), the face states are w_i + slope_i / 2 and
     w_{i+1} - slope_{i+1} / 2, converted back to conserved variables for the
-    flux.  (Reconstructing the conserved variables instead put the paper's
-    Sod case further from the paper's printed figures.)
+    flux.  The paper does not say which variables MUSCL reconstructs; the
+    primitive ones are taken because, with minmod slopes, every reconstructed
+    density and pressure then lies between the values of the two cells it
+    comes from, so a face state of positive neighbours is itself physical
+    (a conserved reconstruction can give a negative face pressure at a
+    strong shock).
   * the Roe flux has no entropy fix;
   * in two dimensions each direction is reconstructed and fluxed
     separately (dimension by dimension);

@@ -142,7 +142,9 @@ def test_hybrid_method_with_the_papers_hdm():
     """Algorithm 1 on Sod's tube with the MUSCL-Roe-BDF2 HDM: with every cell
     sampled and no filter a hybrid step is the full HDM step (to the Newton
     tolerance); with 20 % of the cells plus a 2-cell halo the hybrid
-    trajectory stays within 3 % (relative L1) of the HDM trajectory."""
+    trajectory stays within 2 % (relative L1) of the HDM trajectory (measured
+    0.62 %, s-bar 29.6 %, with the filter gated on the BDF2 residual R_k of
+    Eq. hdm)."""
     from oracle import arom
     q0, cfg, steps = _sod_cfg()
     A = arom.Arom(q0, cfg.with_(top_frac=1.0, filt_orders=()))
@@ -161,5 +163,5 @@ def test_hybrid_method_with_the_papers_hdm():
         A.step()
         worst = max(worst, arom.rel_l1(A.gamma, ref[k]))
     sbar, _, _ = arom.sampling_averages(A.history, cfg.ncell, cfg.ndof)
-    assert worst < 3e-2 and sbar < 45.0, (worst, sbar)
+    assert worst < 2e-2 and sbar < 40.0, (worst, sbar)
     assert any(h.J > 1 for h in A.history if not h.was_full)      # subiterations ran
