@@ -60,7 +60,12 @@ typedef enum {
 } hyrom_status;
 
 enum { HYROM_PDE_BURGERS = 0, HYROM_PDE_EULER = 1 };
-enum { HYROM_SCHEME_BE = 0, HYROM_SCHEME_RK2 = 1 };
+/* Time schemes: BDF1 (backward Euler, Burgers, Godunov flux), SSP-RK2
+ * (Rusanov flux), and the paper's own HDM (Sec. 3.1): MUSCL reconstruction of
+ * the primitive variables with the minmod limiter and the Roe flux, BDF2 of
+ * Eq. bdf (BDF1 for the first step), each step solved by Newton-GMRES with
+ * exact Jacobian-vector products (Euler, FP64). */
+enum { HYROM_SCHEME_BE = 0, HYROM_SCHEME_RK2 = 1, HYROM_SCHEME_BDF2_MUSCL = 2 };
 enum { HYROM_BC_PERIODIC = 0, HYROM_BC_OUTFLOW = 1, HYROM_BC_SHOCK = 2 };
 enum { HYROM_SEL_RRE = 0, HYROM_SEL_TOPFRAC = 1 };
 enum { HYROM_PREC_F64 = 0, HYROM_PREC_F32 = 1 };
@@ -303,6 +308,32 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
  * Bitmaps of ceil(Nc/32) words; *n_s gets |S-hat| (synchronises). */
 hyrom_status hyrom_stage_masks(hyrom_ctx* ctx, const uint32_t* g_bitmap, const int32_t* points,
                                int32_t n_p, uint32_t* s_hat, uint32_t* s_tilde, int32_t* n_s);
+
+/* ---- the paper's HDM (contexts with scheme HYROM_SCHEME_BDF2_MUSCL) --------
+ * Sec. 3.1: MUSCL reconstruction of (rho, u, v, p) with minmod slopes, Roe
+ * flux, BDF2 of Eq. bdf with a0 = 1/3, a1 = -4/3, a2 = 1, beta = 2/3 (BDF1
+ * when q_prev2 is NULL), two ghost layers.  All arrays are N doubles (SoA,
+ * device); other contexts get HYROM_EINVAL.
+ * hyrom_stage_muscl_residual: r_out = R_k(q) of Eq. hdm on every cell.
+ * hyrom_stage_muscl_jvp: jv_out = (d R_k / d q) v at q (exact directional
+ *   derivative; bdf2 selects beta = 2/3 and a2 = 1, else BDF1), every cell.
+ * hyrom_stage_muscl_step: R_k(q) = 0 by Newton-GMRES to max |R| <=
+ *   newton_tol max(1, max |q_prev|); s_hat NULL: the full step (q_io is
+ *   overwritten, the start is q_prev); else the partial HDM of Eq.
+ *   partial_hdm2 on the cells of the bitmap s_hat, q_io holding the start on
+ *   them and the frozen values elsewhere.  HYROM_ENOTCONV when a solve hit
+ *   newton_max (q_io still updated).
+ * hyrom_stage_muscl_filter: SpatialFilter (Sec. 2.3.4) of q_io in place,
+ *   gated on R_k of Eq. hdm; *passes (nullable) gets the passes run.
+ * All synchronise. */
+hyrom_status hyrom_stage_muscl_residual(hyrom_ctx* ctx, const double* q, const double* q_prev,
+                                        const double* q_prev2, int64_t k, double* r_out);
+hyrom_status hyrom_stage_muscl_jvp(hyrom_ctx* ctx, const double* q, const double* v, int64_t k,
+                                   int32_t bdf2, double* jv_out);
+hyrom_status hyrom_stage_muscl_step(hyrom_ctx* ctx, const double* q_prev2, const double* q_prev,
+                                    double* q_io, const uint32_t* s_hat, int64_t k);
+hyrom_status hyrom_stage_muscl_filter(hyrom_ctx* ctx, double* q_io, const double* q_prev,
+                                      const double* q_prev2, int64_t k, int32_t* passes);
 
 /* ---- differentiation form ---------------------------------------------------
  * hyrom_stage_rk2_vjp: the adjoint of one SSP-RK2 HDM step of the Euler

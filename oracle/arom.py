@@ -110,7 +110,7 @@ class Arom:
         resid = (lambda q: hdm_muscl.residual(q, prev, prev2, cfg, t)) if muscl else None
         if info.was_full:
             if muscl:                                             # the paper's HDM
-                gam = hdm_muscl.step(prev, prev2, cfg, k)
+                gam = hdm_muscl.step(prev, prev2, cfg, k, tol=cfg.newton_tol)
             else:
                 gam = hdm.full_step(prev, cfg, k)                 # full HDM step
             info.n_s = cfg.ncell
@@ -129,7 +129,8 @@ class Arom:
                 y = None
                 for j in range(1, cfg.jmax + 1):                  # subiterations
                     if muscl:
-                        v = hdm_muscl.partial_step(prev, prev2, cfg, k, s_hat, v)
+                        v = hdm_muscl.partial_step(prev, prev2, cfg, k, s_hat, v,
+                                                   tol=cfg.newton_tol)
                     else:
                         v, _, _ = hdm.newton_be(prev, cfg, t, active=s_hat, q_init=v)
                     y_new = self._gappy(v)

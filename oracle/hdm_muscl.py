@@ -25,7 +25,9 @@ Readings where the paper is silent:
     shock state);
   * the first step, which has no q_{k-2}, is BDF1 (backward Euler);
   * the Newton solve is Jacobian-free (scipy's newton_krylov with GMRES)
-    and stops at max |R| <= tol * max(1, max |q_{k-1}|).
+    and stops at max |R| <= tol * max(1, max |q_{k-1}|); Algorithm 1
+    (oracle/arom.py) passes the run parameter newton_tol, as for the BDF1
+    HDM.
 """
 from __future__ import annotations
 

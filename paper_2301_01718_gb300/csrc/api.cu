@@ -118,6 +118,12 @@ struct hyrom_ctx {
   bool norms_ready = false;
   // the rebuild's DEIM and oversampling loops as CUDA graphs
   hy::OdeimGraphs od_graphs;
+  // the paper's HDM (MUSCL-Roe-BDF2): Newton-GMRES solver and the S-hat cell
+  // list its partial solves run over
+  hy::MusclSolver* mus = nullptr;
+  int* mus_cells = nullptr;
+  int muscl_fail = 0;    // Newton solves of the current call that hit newton_max
+  int muscl_passes = 0;  // filter passes of the last hybrid step
   // the filter's passes as a CUDA graph, and their per-call arguments
   hy::GraphSlot filt_graph;
   void* fargs = nullptr;
@@ -227,7 +233,15 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
     return HYROM_EINVAL;
   };
   if (c->pde != HYROM_PDE_BURGERS && c->pde != HYROM_PDE_EULER) return bad("pde");
-  if (c->scheme != HYROM_SCHEME_BE && c->scheme != HYROM_SCHEME_RK2) return bad("scheme");
+  if (c->scheme != HYROM_SCHEME_BE && c->scheme != HYROM_SCHEME_RK2 &&
+      c->scheme != HYROM_SCHEME_BDF2_MUSCL)
+    return bad("scheme");
+  if (c->scheme == HYROM_SCHEME_BDF2_MUSCL) {
+    if (c->pde != HYROM_PDE_EULER) return bad("the MUSCL-Roe-BDF2 HDM is for the Euler equations");
+    if (c->precision != HYROM_PREC_F64) return bad("the MUSCL-Roe-BDF2 HDM runs in FP64");
+    if (c->nx < 4 || (c->ny > 1 && c->ny < 4)) return bad("MUSCL needs 4 cells per axis");
+    if (!(c->newton_tol > 0.0)) return bad("newton_tol > 0");
+  }
   if (c->precision != HYROM_PREC_F64 && c->precision != HYROM_PREC_F32) return bad("precision");
   if (c->nx < 4 || c->ny < 1) return bad("grid: nx >= 4, ny >= 1");
   if ((int64_t)c->nx * c->ny * (c->pde == HYROM_PDE_BURGERS ? 1 : 4) > (int64_t)1 << 30)
@@ -350,6 +364,23 @@ void gappy_y(hyrom_ctx* ctx, const T* v, const T* psi, double* y, const double* 
                               dy, ctx->st);
 }
 
+// The paper's HDM: R_k(q) = 0 by Newton-GMRES on the listed cells (all when
+// cells is null), q holding the start and the frozen values; the tolerance
+// is newton_tol * max(1, max |q_{k-1}|), as for the BDF1 HDM.
+hyrom_status muscl_solve(hyrom_ctx* ctx, double* q, const double* qp, const double* qp2,
+                         int64_t k, const int* cells, int64_t n) {
+  hy::launch_newton_tol(ctx->dc, qp, ctx->cfg.newton_tol, ctx->tol_dev, ctx->st);
+  double* hd = (double*)ctx->host + 24;
+  CK(cudaMemcpyAsync(hd, ctx->tol_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (hyrom_status s = sync(ctx)) return s;
+  int its = 0, arn = 0;
+  const int r = hy::muscl_newton(ctx->mus, ctx->dc, q, qp, qp2, k, cells, n, hd[0],
+                                 ctx->cfg.newton_max, 1e-6, ctx->st, &its, &arn);
+  if (r < 0) return fail(ctx, HYROM_ECUDA, "Newton-GMRES: %s", cudaGetErrorString(cudaGetLastError()));
+  if (r > 0) ctx->muscl_fail += 1;
+  return HYROM_OK;
+}
+
 // Algorithm 1, advance part: full-step test, full HDM step or hybrid step
 // ---------------------------------------------------------------------------
 
@@ -387,9 +418,17 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   inf.was_full = full;
   CK(cudaMemsetAsync(ctx->fail_dev, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(ctx->fail_dev + 12, 0, sizeof(int), ctx->st));
+  ctx->muscl_fail = 0;
+  const bool muscl = cf.scheme == HYROM_SCHEME_BDF2_MUSCL;
+  const T* qp2 = (muscl && k >= 2) ? ring_at<T>(ctx, k - 2) : nullptr;
   if (full) {
     t_begin(ctx, HYROM_T_FULL);
-    if (cf.scheme == HYROM_SCHEME_RK2) {
+    if (muscl) {
+      if constexpr (sizeof(T) == 8) {
+        CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+        if (hyrom_status s = muscl_solve(ctx, q, qp, qp2, k, nullptr, ctx->nc)) return s;
+      }
+    } else if (cf.scheme == HYROM_SCHEME_RK2) {
       hy::launch_rk2<T>(ctx->dc, qp, q, k, nullptr, nullptr, nullptr, ctx->st);
     } else {
       CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
@@ -414,11 +453,22 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
       inf.J = 1;
     } else {
       CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+      if (muscl)  // the cells of S-hat, ascending: the partial solve's unknowns
+        hy::launch_bits_to_list(ctx->shat, ctx->nc, ctx->list_cnt, ctx->mus_cells, ctx->nc,
+                                ctx->st);
       double* yv = ctx->y;
       double* yo = ctx->y2;
       double* hd = (double*)ctx->host;
       for (int j = 1; j <= cf.jmax; ++j) {
-        hyrom_status s = newton_partial<T>(ctx, qp, q, ctx->shat, ctx->n_s);
+        t_begin(ctx, HYROM_T_PARTIAL);
+        hyrom_status s = HYROM_OK;
+        if (muscl) {
+          if constexpr (sizeof(T) == 8)
+            s = muscl_solve(ctx, q, qp, qp2, k, ctx->mus_cells, ctx->n_s);
+        } else {
+          s = newton_partial<T>(ctx, qp, q, ctx->shat, ctx->n_s);
+        }
+        t_end(ctx, HYROM_T_PARTIAL);
         if (s) return s;
         inf.J = j;
         if (ctx->m_eff == 0) {
@@ -444,11 +494,22 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     t_end(ctx, HYROM_T_RECON);
     // SpatialFilter
     t_begin(ctx, HYROM_T_FILTER);
-    if (cf.n_filt > 0)
+    if (cf.n_filt > 0 && muscl) {
+      if constexpr (sizeof(T) == 8) {
+        const int np = hy::muscl_filter(ctx->dc, q, qp, qp2, k, cf.filt_orders, cf.n_filt,
+                                        cf.jmax_f, cf.eps_f, (double*)ctx->fg,
+                                        (double*)ctx->ftmp, (double*)ctx->rho_old,
+                                        (double*)ctx->rho_new, ctx->fpart, ctx->dy + 2,
+                                        (double*)ctx->host + 28, ctx->st);
+        if (np < 0) return fail(ctx, HYROM_ECUDA, "filter: %s", cudaGetErrorString(cudaGetLastError()));
+        ctx->muscl_passes = np;
+      }
+    } else if (cf.n_filt > 0) {
       hy::launch_filter_sparse<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp,
                                   k, (T*)ctx->fg, ctx->kbits, ctx->ftiles_a, ctx->ftiles_b,
                                   ctx->fcounts, ctx->fpart, ctx->fctl, ctx->fargs,
                                   &ctx->filt_graph, ctx->st);
+    }
     t_end(ctx, HYROM_T_FILTER);
   }
   // physical-state check of the new snapshot (Euler): rho > 0 and p > 0
@@ -458,12 +519,12 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   gram_update<T>(ctx, k);
   int* hi = (int*)ctx->host;
   CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  if (!full && cf.n_filt > 0)
+  if (!full && cf.n_filt > 0 && !muscl)
     CK(cudaMemcpyAsync(hi + 1, ctx->fctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(hi + 2, ctx->fail_dev + 12, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (hyrom_status s = sync(ctx)) return s;
-  inf.newton_fail = hi[0];
-  inf.filt_passes = (!full && cf.n_filt > 0) ? hi[1] : 0;
+  inf.newton_fail = muscl ? ctx->muscl_fail : hi[0];
+  inf.filt_passes = (!full && cf.n_filt > 0) ? (muscl ? ctx->muscl_passes : hi[1]) : 0;
   inf.n_p = ctx->np_eff;
   inf.m_eff = ctx->m_eff;
   if (info) *info = inf;
@@ -575,7 +636,9 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
 template <typename T>
 hyrom_status masks_and_tiles(hyrom_ctx* ctx, const uint32_t* gbm, const int* pts, int np,
                              uint32_t* shat, uint32_t* stilde, int64_t* n_s) {
-  const int rs = ctx->cfg.scheme == HYROM_SCHEME_RK2 ? 2 : 1;
+  // stencil reach: one cell for first-order BDF1, two for SSP-RK2 (two
+  // stages) and for MUSCL (two neighbours per face)
+  const int rs = ctx->cfg.scheme == HYROM_SCHEME_BE ? 1 : 2;
   t_begin(ctx, HYROM_T_MASKS);
   hy::launch_masks(ctx->dc, gbm, pts, np, ctx->cfg.halo, rs, ctx->base_bm, shat, stilde,
                    ctx->n_s_dev, ctx->st);
@@ -845,6 +908,12 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->tol_dev, 64);
   ok &= dal(ctx, &ctx->newton_ws, (size_t)6 * cfg->nx * sizeof(double));
   ok &= dal(ctx, &ctx->fail_dev, 64);
+  if (ok && cfg->scheme == HYROM_SCHEME_BDF2_MUSCL) {
+    ok &= dal(ctx, &ctx->mus_cells, (size_t)nc * sizeof(int));
+    ctx->mus = hy::muscl_create(nc, nc);
+    ok &= ctx->mus != nullptr;
+    ctx->bytes += hy::muscl_bytes(ctx->mus);
+  }
   if (!ok) {
     hyrom_destroy(ctx);
     fprintf(stderr, "hyrom_init: device allocation failed\n");
@@ -879,6 +948,7 @@ void hyrom_destroy(hyrom_ctx* ctx) {
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   hy::odeim_graphs_free(&ctx->od_graphs);
   hy::graph_slot_free(&ctx->filt_graph);
+  hy::muscl_destroy(ctx->mus);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host) cudaFreeHost(ctx->host);
   for (int i = 0; i < HYROM_NSTAGE; ++i) {
@@ -1060,6 +1130,75 @@ hyrom_status hyrom_stage_full_step(hyrom_ctx* ctx, const void* q_prev, void* q_o
   CK(cudaMemcpyAsync(hi, ctx->fail_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   if (hyrom_status s = sync(ctx)) return s;
   return hi[0] ? fail(ctx, HYROM_ENOTCONV, "Newton did not converge") : HYROM_OK;
+}
+
+// ---- the paper's HDM (MUSCL-Roe-BDF2) --------------------------------------
+#define MUSCL_ONLY()                                                          \
+  do {                                                                        \
+    if (ctx->cfg.scheme != HYROM_SCHEME_BDF2_MUSCL)                           \
+      return fail(ctx, HYROM_EINVAL, "needs a MUSCL-Roe-BDF2 context");       \
+  } while (0)
+
+hyrom_status hyrom_stage_muscl_residual(hyrom_ctx* ctx, const double* q, const double* q_prev,
+                                        const double* q_prev2, int64_t k, double* r_out) {
+  GUARD();
+  MUSCL_ONLY();
+  if (!q || !q_prev || !r_out) return HYROM_EINVAL;
+  hy::launch_muscl_residual(ctx->dc, q, q_prev, q_prev2, (double)k * ctx->cfg.dt, nullptr,
+                            ctx->nc, r_out, ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_muscl_jvp(hyrom_ctx* ctx, const double* q, const double* v, int64_t k,
+                                   int32_t bdf2, double* jv_out) {
+  GUARD();
+  MUSCL_ONLY();
+  if (!q || !v || !jv_out || v == jv_out) return HYROM_EINVAL;
+  const double dtb = bdf2 ? ctx->cfg.dt * (2.0 / 3.0) : ctx->cfg.dt;
+  hy::launch_muscl_jvp(ctx->dc, q, v, (double)k * ctx->cfg.dt, 1.0, dtb, nullptr, ctx->nc, jv_out,
+                       ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+hyrom_status hyrom_stage_muscl_step(hyrom_ctx* ctx, const double* q_prev2, const double* q_prev,
+                                    double* q_io, const uint32_t* s_hat, int64_t k) {
+  GUARD();
+  MUSCL_ONLY();
+  if (!q_prev || !q_io || q_prev == q_io || q_prev2 == q_io) return HYROM_EINVAL;
+  ctx->muscl_fail = 0;
+  if (!s_hat) {
+    CK(cudaMemcpyAsync(q_io, q_prev, ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    if (hyrom_status s = muscl_solve(ctx, q_io, q_prev, q_prev2, k, nullptr, ctx->nc)) return s;
+  } else {
+    long long* hl = (long long*)ctx->host;
+    CK(cudaMemsetAsync(ctx->list_cnt, 0, sizeof(long long), ctx->st));
+    hy::launch_bits_to_list(s_hat, ctx->nc, ctx->list_cnt, ctx->mus_cells, ctx->nc, ctx->st);
+    hy::launch_popcount(s_hat, ctx->nwords, ctx->n_s_dev, ctx->st);
+    CK(cudaMemcpyAsync(hl, ctx->n_s_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+    if (hyrom_status s = sync(ctx)) return s;
+    const int64_t n = hl[0];
+    if (n > 0)
+      if (hyrom_status s = muscl_solve(ctx, q_io, q_prev, q_prev2, k, ctx->mus_cells, n)) return s;
+  }
+  if (hyrom_status s = sync(ctx)) return s;
+  return ctx->muscl_fail ? fail(ctx, HYROM_ENOTCONV, "Newton-GMRES hit newton_max") : HYROM_OK;
+}
+
+hyrom_status hyrom_stage_muscl_filter(hyrom_ctx* ctx, double* q_io, const double* q_prev,
+                                      const double* q_prev2, int64_t k, int32_t* passes) {
+  GUARD();
+  MUSCL_ONLY();
+  if (!q_io || !q_prev || q_io == q_prev) return HYROM_EINVAL;
+  const hyrom_config& cf = ctx->cfg;
+  const int np = hy::muscl_filter(ctx->dc, q_io, q_prev, q_prev2, k, cf.filt_orders, cf.n_filt,
+                                  cf.jmax_f, cf.eps_f, (double*)ctx->fg, (double*)ctx->ftmp,
+                                  (double*)ctx->rho_old, (double*)ctx->rho_new, ctx->fpart,
+                                  ctx->dy + 2, (double*)ctx->host + 28, ctx->st);
+  if (np < 0) return fail(ctx, HYROM_ECUDA, "filter: %s", cudaGetErrorString(cudaGetLastError()));
+  if (passes) *passes = np;
+  return sync(ctx);
 }
 
 hyrom_status hyrom_stage_partial_step(hyrom_ctx* ctx, const void* q_prev, void* q_io,

@@ -78,6 +78,27 @@ void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
                 const int* tiles, const int* ntiles_dev, cudaStream_t s);
+// The paper's HDM (muscl.cu): MUSCL-minmod-Roe residual of BDF2 (BDF1 when
+// qp2 is null) on listed cells (null = all; compact SoA output), its exact
+// JVP, the filter's residual measure, and a Newton-GMRES solver with its
+// own workspace for up to max_cells unknown cells.  FP64.
+struct MusclSolver;
+MusclSolver* muscl_create(int64_t nc, int64_t max_cells);
+void muscl_destroy(MusclSolver* m);
+size_t muscl_bytes(const MusclSolver* m);
+void launch_muscl_residual(const DevCfg& c, const double* q, const double* qp, const double* qp2,
+                           double t, const int* cells, int64_t n, double* out, cudaStream_t s);
+void launch_muscl_jvp(const DevCfg& c, const double* q, const double* dv, double t, double a2,
+                      double dtb, const int* cells, int64_t n, double* out, cudaStream_t s);
+void launch_muscl_rho(const DevCfg& c, const double* q, const double* qp, const double* qp2,
+                      double t, double* rho, cudaStream_t s);
+int muscl_newton(MusclSolver* m, const DevCfg& c, double* q, const double* qp,
+                 const double* qp2, int64_t k, const int* cells, int64_t n, double tol_abs,
+                 int newton_max, double eta, cudaStream_t s, int* iters_out, int* arnoldi_out);
+int muscl_filter(const DevCfg& c, double* q, const double* qp, const double* qp2, int64_t k,
+                 const int* orders, int n_filt, int jmax_f, double eps_f, double* g,
+                 double* tmp, double* rho_old, double* rho_new, double* part, double* out3,
+                 double* host3, cudaStream_t s);
 // FP32 full SSP-RK2 step of the 2D Euler equations streamed by warp strips
 // (hdm_f32.cu); rk2_euler_sweep_ok tells whether it takes the grid.
 bool rk2_euler_sweep_ok(const DevCfg& c);
@@ -213,6 +234,8 @@ void launch_active_tiles(const DevCfg& c, const uint32_t* bm, int TX, int TY, in
                          int* ntiles, cudaStream_t s);
 void launch_bits_to_list(const uint32_t* bm, int64_t nc, long long* cnt_scratch, int* out,
                          int64_t cap, cudaStream_t s);
+// *out = number of set bits of bm (nwords words)
+void launch_popcount(const uint32_t* bm, int64_t nwords, long long* out, cudaStream_t s);
 
 // reduced.cu: sample-row reduced solve (normal equations on all dof rows
 // of the listed cells; red = HYROM_RED_* precision of the normal matrix;

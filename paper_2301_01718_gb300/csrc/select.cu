@@ -510,6 +510,11 @@ void launch_masks(const DevCfg& c, const uint32_t* g_bitmap, const int* pts, int
   k_popcount<<<152, 256, 0, HY_S(s)>>>(s_hat, nwords, n_s_dev);
 }
 
+void launch_popcount(const uint32_t* bm, int64_t nwords, long long* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(long long), s);
+  k_popcount<<<152, 256, 0, HY_S(s)>>>(bm, nwords, out);
+}
+
 void launch_active_tiles(const DevCfg& c, const uint32_t* bm, int TX, int TY, int* tiles,
                          int* ntiles, cudaStream_t s) {
   cudaMemsetAsync(ntiles, 0, sizeof(int), s);

@@ -139,6 +139,10 @@ def lib():
         "hyrom_gappy_static": (st, [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, C.c_char_p, i32]),
         "hyrom_selftest_math": (st, [i32, vp, vp, i64, vp]),
         "hyrom_probe_fp64": (st, [vp, i32, i32, vp]),
+        "hyrom_stage_muscl_residual": (st, [vp, vp, vp, vp, i64, vp]),
+        "hyrom_stage_muscl_jvp": (st, [vp, vp, vp, i64, i32, vp]),
+        "hyrom_stage_muscl_step": (st, [vp, vp, vp, vp, vp, i64]),
+        "hyrom_stage_muscl_filter": (st, [vp, vp, vp, vp, i64, C.POINTER(i32)]),
         "hyrom_stage_rk2_vjp": (st, [vp, vp, vp, vp, vp, i64, vp]),
         "hyrom_reduced_vjp_work_doubles": (C.c_size_t, [i32, i32]),
         "hyrom_stage_reduced_vjp": (st, [vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -323,6 +327,28 @@ def hyrom_stage_masks(ctx, g_bitmap, points, n_p, s_hat, s_tilde):
     _check(ctx, lib().hyrom_stage_masks(ctx, _ptr(g_bitmap), _ptr(points), int(n_p), _ptr(s_hat),
                                         _ptr(s_tilde), C.byref(n)))
     return n.value
+
+
+def hyrom_stage_muscl_residual(ctx, q, q_prev, q_prev2, k, r_out):
+    _check(ctx, lib().hyrom_stage_muscl_residual(ctx, _ptr(q), _ptr(q_prev), _ptr(q_prev2),
+                                                 int(k), _ptr(r_out)))
+
+
+def hyrom_stage_muscl_jvp(ctx, q, v, k, bdf2, jv_out):
+    _check(ctx, lib().hyrom_stage_muscl_jvp(ctx, _ptr(q), _ptr(v), int(k), int(bool(bdf2)),
+                                            _ptr(jv_out)))
+
+
+def hyrom_stage_muscl_step(ctx, q_prev2, q_prev, q_io, s_hat, k):
+    _check(ctx, lib().hyrom_stage_muscl_step(ctx, _ptr(q_prev2), _ptr(q_prev), _ptr(q_io),
+                                             _ptr(s_hat), int(k)))
+
+
+def hyrom_stage_muscl_filter(ctx, q_io, q_prev, q_prev2, k):
+    p = C.c_int32()
+    _check(ctx, lib().hyrom_stage_muscl_filter(ctx, _ptr(q_io), _ptr(q_prev), _ptr(q_prev2),
+                                               int(k), C.byref(p)))
+    return p.value
 
 
 def hyrom_gappy_static(phi, ndof, m, points, n_p, v, psi, precision, y_out, stream=None):

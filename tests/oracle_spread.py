@@ -45,6 +45,19 @@ def spread(q0, cfg, steps, ref_states):
     return out
 
 
+def newton_spread(q0, cfg, steps, ref_states, tighter=100.0):
+    """Per-step relative max difference between the run of ref_states and the
+    same run with every Newton solve taken `tighter` times further: how far
+    apart two runs can lie that both stop their solves within the
+    tolerance, after the method has carried the difference along."""
+    B = arom.Arom(q0, cfg.with_(newton_tol=cfg.newton_tol / tighter))
+    out = []
+    for k in range(steps):
+        B.step()
+        out.append(rel_max(B.gamma.reshape(-1), ref_states[k]))
+    return out
+
+
 def bar(spread_k, floor=1e-12, factor=100.0):
     """The lockstep bound at one step: 1e-12 relative (the per-stage FP64
     tolerance) while the rounding-order spread is small, and 100x the spread

@@ -1,0 +1,214 @@
+"""GPU parity of the paper's HDM (Sec. 3.1: MUSCL reconstruction with the
+minmod limiter, the Roe flux, BDF2 of Eq. bdf; Eq. hdm solved by
+Newton-GMRES) against oracle/hdm_muscl.py, stage by stage and through
+Algorithm 1:
+
+  * the residual R_k of Eq. hdm, BDF1 and BDF2: the same bits (both sides
+    evaluate the same expressions in the same order);
+  * the exact Jacobian-vector product against central differences of the
+    oracle's residual;
+  * full and partial (Eq. partial_hdm2) Newton solves: within 1e-12 of the
+    oracle's solve at the same tolerance (both converge to the root of the
+    same residual; the tolerance bounds their distance);
+  * the filter gated on R_k (Sec. 2.3.4): within 1e-12 and the same passes;
+  * Algorithm 1 in lockstep: the same schedule, identical sampled sets at
+    every rebuild, states within 1e-12 or 100x the oracle's own drift under
+    a change of rounding order or of the Newton tolerance (both runs stop
+    their solves anywhere within it; tests/oracle_spread.py)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import arom, filt, hdm_muscl as M
+from tests import oracle_spread
+from tests.gpu_util import Ctx, dev, host, dev_bits, bits_of, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _muscl(cfg):
+    return cfg.with_(scheme=W.SCHEME_BDF2_MUSCL, precision=W.PREC_F64, newton_tol=1e-13,
+                     pod_tol=1e-10, pod_abs=1e-13)
+
+
+def _cases():
+    q, c, _ = W.euler_oblique_shock(n=24, seed=3, k=3)
+    yield "shock24", q.reshape(4, 24, 24)[:, :21, :].copy(), _muscl(c.with_(ny=21))
+    q, c, _ = W.euler_vortex(n=20, seed=4)
+    yield "vortex20", q, _muscl(c.with_(nx=20, ny=20))
+    q, c = W.euler_riemann_x(n=60)
+    yield "sod60", q, _muscl(c)
+
+
+CASES = list(_cases())
+IDS = [c[0] for c in CASES]
+
+
+def _states(q0, cfg, seed):
+    """q_{k-2}, q_{k-1} and a nearby q: smooth perturbations of the state."""
+    shape = (4, cfg.ny, cfg.nx)
+    g = np.random.Generator(np.random.PCG64(seed))
+    base = np.asarray(q0, np.float64).reshape(shape)
+    x = np.linspace(0.0, 2.0 * np.pi, cfg.nx)[None, None, :]
+    y = np.linspace(0.0, 2.0 * np.pi, cfg.ny)[None, :, None]
+    amp = 0.01 * np.abs(base).max(axis=(1, 2), keepdims=True) + 1e-3
+
+    def bump():
+        a, b, c = g.uniform(0.5, 2.0, 3)
+        return amp * np.sin(a * x + c) * np.cos(b * y + c)
+    qp2 = base
+    qp = base + bump()
+    q = qp + bump()
+    return qp2, qp, q
+
+
+@pytest.mark.parametrize("name,q0,cfg", CASES, ids=IDS)
+@pytest.mark.parametrize("bdf2", [False, True])
+def test_residual_same_bits(name, q0, cfg, bdf2):
+    qp2, qp, q = _states(q0, cfg, 1)
+    k = 5
+    want = M.residual(q, qp, qp2 if bdf2 else None, cfg, k * cfg.dt).reshape(-1)
+    with Ctx(cfg, q0) as (hy, ctx):
+        out = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_muscl_residual(ctx, dev(q.reshape(-1)), dev(qp.reshape(-1)),
+                                      dev(qp2.reshape(-1)) if bdf2 else None, k, out)
+        got = host(out)
+    assert np.array_equal(got, want), f"max diff {np.abs(got - want).max()}"
+
+
+@pytest.mark.parametrize("name,q0,cfg", CASES, ids=IDS)
+@pytest.mark.parametrize("bdf2", [False, True])
+def test_jvp_against_central_differences(name, q0, cfg, bdf2):
+    """(R(q + h v) - R(q - h v)) / 2h against the exact JVP.  The residual
+    has kinks (|u_n|, |u_n +- c| of the Roe flux at zero, minmod switching
+    between its arguments), and central differences are no reference on a
+    cell whose stencil crosses one within h: those cells are found as the
+    ones where h = 1e-6 and h = 1e-7 (relative to max |v|) disagree by more
+    than 1e-7, and must be few (measured 1 to 5 % of the cells).  On every
+    other cell the JVP is within 1e-6 of the largest entry."""
+    qp2, qp, q = _states(q0, cfg, 2)
+    g = np.random.Generator(np.random.PCG64(3))
+    v = g.standard_normal(q.shape) * np.abs(q).max(axis=(1, 2), keepdims=True)
+    k = 4
+    p2 = qp2 if bdf2 else None
+
+    def fd(hh):
+        h = hh / np.abs(v).max()
+        return (M.residual(q + h * v, qp, p2, cfg, k * cfg.dt) -
+                M.residual(q - h * v, qp, p2, cfg, k * cfg.dt)) / (2.0 * h)
+    f1, f2 = fd(1e-6), fd(1e-7)
+    scale = np.abs(f1).max()
+    smooth = np.abs(f1 - f2).max(axis=0) <= 1e-7 * scale
+    with Ctx(cfg, q0) as (hy, ctx):
+        out = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_muscl_jvp(ctx, dev(q.reshape(-1)), dev(v.reshape(-1)), k, bdf2, out)
+        got = host(out).reshape(q.shape)
+    err = float(np.abs(got - f1)[:, smooth].max() / scale)
+    print(f"{name} bdf2={bdf2}: {smooth.mean():.3f} of the cells smooth at h, err {err:.2e}")
+    assert smooth.mean() >= 0.9
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("name,q0,cfg", CASES, ids=IDS)
+def test_full_newton_step(name, q0, cfg):
+    """BDF1 first step, then a BDF2 step, each against the oracle's solve."""
+    shape = (4, cfg.ny, cfg.nx)
+    q0s = np.asarray(q0, np.float64).reshape(shape)
+    w1 = M.step(q0s, None, cfg, 1, tol=cfg.newton_tol)
+    w2 = M.step(w1, q0s, cfg, 2, tol=cfg.newton_tol)
+    with Ctx(cfg, q0) as (hy, ctx):
+        a, b = dev(q0s.reshape(-1)), torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_muscl_step(ctx, None, a, b, None, 1)
+        g1 = host(b).copy()
+        c = torch.zeros_like(b)
+        hy.hyrom_stage_muscl_step(ctx, a, dev(w1.reshape(-1)), c, None, 2)
+        g2 = host(c)
+        r = torch.zeros_like(b)
+        hy.hyrom_stage_muscl_residual(ctx, c, dev(w1.reshape(-1)), a, 2, r)
+        rmax = float(np.abs(host(r)).max())
+    e1, e2 = rel_err(g1, w1.reshape(-1)), rel_err(g2, w2.reshape(-1))
+    print(f"{name}: BDF1 {e1:.2e}, BDF2 {e2:.2e}, GPU max|R| {rmax:.2e}")
+    assert e1 < 1e-12 and e2 < 1e-12
+    assert rmax <= cfg.newton_tol * max(1.0, np.abs(w1).max())
+
+
+@pytest.mark.parametrize("name,q0,cfg", CASES, ids=IDS)
+def test_partial_newton_step(name, q0, cfg):
+    """The rows of a random 30 % of the cells solved with the others frozen:
+    frozen cells keep their bits, solved ones match the oracle."""
+    shape = (4, cfg.ny, cfg.nx)
+    qp2, qp, start = _states(q0, cfg, 5)
+    g = np.random.Generator(np.random.PCG64(6))
+    active = g.random((cfg.ny, cfg.nx)) < 0.3
+    want = M.partial_step(qp, qp2, cfg, 3, active, start, tol=cfg.newton_tol)
+    with Ctx(cfg, q0) as (hy, ctx):
+        io = dev(start.reshape(-1))
+        hy.hyrom_stage_muscl_step(ctx, dev(qp2.reshape(-1)), dev(qp.reshape(-1)), io,
+                                  dev_bits(active.reshape(-1)), 3)
+        got = host(io).reshape(shape)
+    act = np.broadcast_to(active[None], shape)
+    assert np.array_equal(got[~act], start[~act])
+    assert rel_err(got[act], want[act]) < 1e-12, rel_err(got[act], want[act])
+
+
+@pytest.mark.parametrize("name,q0,cfg", CASES, ids=IDS)
+def test_filter_gated_on_bdf2_residual(name, q0, cfg):
+    shape = (4, cfg.ny, cfg.nx)
+    qp2, qp, q = _states(q0, cfg, 7)
+    g = np.random.Generator(np.random.PCG64(8))
+    noisy = q + 0.02 * np.abs(q).max(axis=(1, 2), keepdims=True) * g.standard_normal(q.shape)
+    k = 6
+    t = k * cfg.dt
+    want, passes, _ = filt.spatial_filter(noisy, qp, cfg, t,
+                                          lambda x: M.residual(x, qp, qp2, cfg, t))
+    with Ctx(cfg, q0) as (hy, ctx):
+        io = dev(noisy.reshape(-1))
+        got_passes = hy.hyrom_stage_muscl_filter(ctx, io, dev(qp.reshape(-1)),
+                                                 dev(qp2.reshape(-1)), k)
+        got = host(io)
+    assert got_passes == passes
+    assert rel_err(got, want.reshape(-1)) < 1e-12
+
+
+def _alg_cases():
+    q, c, _ = W.euler_oblique_shock(n=32, seed=3, k=3)
+    yield "shock32", q, _muscl(c.with_(w=6, m=3, n_p=6, top_frac=0.15)), 12
+    q, c = W.euler_riemann_x(n=100)
+    yield "sod100", q, _muscl(c.with_(w=10, m=5, n_p=10, top_frac=0.2, halo=2)), 18
+
+
+@pytest.mark.parametrize("name,q0,cfg,steps", list(_alg_cases()),
+                         ids=[c[0] for c in _alg_cases()])
+def test_algorithm1_lockstep_with_the_papers_hdm(name, q0, cfg, steps):
+    A = arom.Arom(q0, cfg)
+    recs = []
+    with Ctx(cfg, q0) as (hy, ctx):
+        nw = (cfg.ncell + 31) // 32
+        bm = torch.zeros(nw, dtype=torch.int32, device="cuda")
+        q = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        for _ in range(steps):
+            info = hy.hyrom_step(ctx)
+            oi = A.step()
+            hy.hyrom_get_state(ctx, q)
+            rec = dict(k=oi.k, info=info, oinfo=oi, state=host(q).copy(),
+                       want=A.gamma.reshape(-1).copy())
+            if oi.rebuilt:
+                hy.hyrom_sample(ctx, bitmap_dev=bm)
+                rec["mask"] = bits_of(bm, cfg.ncell)
+                rec["want_mask"] = A.s_hat.reshape(-1).copy()
+            recs.append(rec)
+    ref = [r["want"] for r in recs]
+    spread = np.maximum(oracle_spread.spread(q0, cfg, steps, ref),
+                        oracle_spread.newton_spread(q0, cfg, steps, ref))
+    worst = 0.0
+    for r, sp in zip(recs, spread):
+        assert bool(r["info"]["was_full"]) == r["oinfo"].was_full
+        assert r["info"]["m_eff"] == r["oinfo"].m_eff
+        e = rel_err(r["state"], r["want"])
+        worst = max(worst, e)
+        assert e <= oracle_spread.bar(sp), f"step {r['k']}: rel err {e}, spread {sp}"
+        if not r["oinfo"].was_full:
+            assert r["info"]["J"] == r["oinfo"].J, f"step {r['k']}: subiterations differ"
+        if "mask" in r:
+            assert np.array_equal(r["mask"], r["want_mask"]), f"step {r['k']}: masks differ"
+    print(f"{name}: worst rel err {worst:.2e}; J {[r['oinfo'].J for r in recs]}")

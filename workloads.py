@@ -29,7 +29,7 @@ import numpy as np
 # --- enumerations shared with the C ABI (include/hyrom.h) -------------------
 PDE_BURGERS, PDE_EULER = 0, 1
 SCHEME_BE, SCHEME_RK2 = 0, 1            # backward Euler (BDF1), SSP-RK2
-SCHEME_BDF2_MUSCL = 2                   # the paper's HDM (MUSCL-Roe, BDF2); CPU oracle only
+SCHEME_BDF2_MUSCL = 2                   # the paper's HDM (MUSCL-Roe, BDF2)
 BC_PERIODIC, BC_OUTFLOW, BC_SHOCK = 0, 1, 2
 SEL_RRE, SEL_TOPFRAC = 0, 1             # RRE threshold delta, top fraction
 PREC_F64, PREC_F32 = 0, 1
