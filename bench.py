@@ -69,7 +69,10 @@ def parse():
                    help="timed hybrid steps per instance in each batching-form arm")
     p.add_argument("--batch-threads", default="1,4,8,16",
                    help="host-thread counts timed in the batching form (1 = one at a time)")
-    p.add_argument("--micro", choices=["sample_gram", "batch", "full_step", "np_sweep",
+    p.add_argument("--implicit-n", type=int, default=512,
+                   help="grid of the implicit (paper's HDM) workload")
+    p.add_argument("--no-implicit", action="store_true")
+    p.add_argument("--micro", choices=["sample_gram", "batch", "full_step", "np_sweep", "implicit",
                                        "vortex512", "rk2_vjp"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
@@ -421,6 +424,8 @@ def run_ours(a):
         out["full_step"] = full_step(a)
     if rank == 0 and not a.no_batch_form:
         out["batch_form"] = batch_form(a)
+    if rank == 0 and not a.no_implicit:
+        out["implicit_form"] = implicit_form(a)
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(a)
     if world > 1:
@@ -809,6 +814,65 @@ def rk2_vjp(a, n=1024, calls=10):
             "ms_median": statistics.median(ms), "cells_per_s": cfg.ncell / (best * 1e-3)}
 
 
+def implicit_form(a, n=None, steps=14):
+    """The paper's own HDM (Sec. 3.1: MUSCL-minmod-Roe, BDF2 by Newton-GMRES,
+    FP64) on the oblique-shock workload with the parameters of the paper's
+    implosion run (w = 6, m = 4, z = 7, RRE threshold delta = 0.9, filters of
+    orders 2, 4, 6): host-clocked time of each step of Algorithm 1 after the
+    warm-up, split into full-HDM steps (every z-th) and hybrid steps (partial
+    Newton solves with subiterations, reconstruction, filter, and the basis
+    update), and the paper's speedup S = time per snapshot of the full HDM /
+    time per snapshot of the AROM (Sec. 2.4.2) over the measured cycle."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    n = n or a.implicit_n
+    q0, cfg, _ = W.euler_oblique_shock(n=n, seed=a.seed, k=4)
+    cfg = cfg.with_(scheme=W.SCHEME_BDF2_MUSCL, precision=W.PREC_F64, w=6, m=4, n_p=8, z=7,
+                    sel_mode=W.SEL_RRE, delta=0.9, newton_tol=1e-10, pod_tol=1e-10,
+                    pod_abs=1e-13)
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    ctx = hyrom.hyrom_init(cfg, q0d, stream=stream.cuda_stream)
+    del q0d
+    full, hyb, ns, J, passes = [], [], [], [], []
+    try:
+        k = 0
+        while k < cfg.w + 1:                      # the method's warm-up
+            k = hyrom.hyrom_step(ctx)["k"]
+        hyrom.hyrom_profile(ctx, True)
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = hyrom.hyrom_step(ctx)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) * 1e3
+            (full if info["was_full"] else hyb).append(dt)
+            if not info["was_full"]:
+                ns.append(info["n_s"])
+                J.append(info["J"])
+                passes.append(info["filt_passes"])
+        st = hyrom.hyrom_stage_times(ctx)
+        hyrom.hyrom_profile(ctx, False)
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    tf = statistics.median(full) if full else None
+    th = statistics.mean(hyb) if hyb else None
+    z = cfg.z
+    out = {"workload": f"euler2d_oblique_shock_{n}x{n}_muscl_roe_bdf2_w{cfg.w}_m{cfg.m}_z{z}"
+                       f"_rre{cfg.delta:g}",
+           "full_ms": tf, "hybrid_ms": th, "full_steps": len(full), "hybrid_steps": len(hyb),
+           "n_s_frac_mean": float(np.mean(ns)) / cfg.ncell if ns else None,
+           "J_mean": float(np.mean(J)) if J else None,
+           "filter_passes_mean": float(np.mean(passes)) if passes else None,
+           "stage_ms_per_hybrid_step": {k2: v[0] / max(len(hyb), 1) for k2, v in st.items()
+                                        if v[1] and k2 != "full"},
+           "newton_tol": cfg.newton_tol}
+    if tf and th:
+        out["speedup_S"] = z * tf / ((z - 1) * th + tf)
+        out["hybrid_over_full"] = th / tf
+    return out
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -838,6 +902,8 @@ def main():
         out = {"micro": "batch", **batch_form(a)}
     elif a.micro == "full_step":
         out = {"micro": "full_step", **full_step(a)}
+    elif a.micro == "implicit":
+        out = {"micro": "implicit", **implicit_form(a)}
     elif a.micro == "np_sweep":
         out = {"micro": "np_sweep", **np_sweep(a)}
     elif a.micro == "vortex512":

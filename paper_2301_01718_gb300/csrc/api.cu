@@ -496,7 +496,7 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     t_begin(ctx, HYROM_T_FILTER);
     if (cf.n_filt > 0 && muscl) {
       if constexpr (sizeof(T) == 8) {
-        const int np = hy::muscl_filter(ctx->dc, q, qp, qp2, k, cf.filt_orders, cf.n_filt,
+        const int np = hy::muscl_filter(ctx->mus, ctx->dc, q, qp, qp2, k, cf.filt_orders, cf.n_filt,
                                         cf.jmax_f, cf.eps_f, (double*)ctx->fg,
                                         (double*)ctx->ftmp, (double*)ctx->rho_old,
                                         (double*)ctx->rho_new, ctx->fpart, ctx->dy + 2,
@@ -553,6 +553,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
   const hyrom_config& cf = ctx->cfg;
   if (!ctx->f32) {
     // FP64: one-sided Jacobi SVD of the centred window
+    t_begin(ctx, HYROM_T_EIG);
     hy::launch_center_window<T>(ring, ctx->N, ctx->win_dev, w, wp, psi, ctx->X, ctx->rawpart,
                                 ctx->xraw2, ctx->st);
     hy::launch_identity(ctx->V, wp, ctx->st);
@@ -560,17 +561,21 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
     for (int sweep = 0; sweep < 60; ++sweep) {
       CK(cudaMemsetAsync(ctx->rotated, 0, sizeof(int), ctx->st));
       for (int r = 0; r < wp - 1; ++r)
-        hy::launch_hestenes_round(ctx->X, ctx->N, wp, ctx->V, r, 1e-15, ctx->rotated, ctx->st);
+        hy::launch_hestenes_round(ctx->X, ctx->N, wp, ctx->V, r, 1e-15, ctx->rotated, ctx->jbuf,
+                                  ctx->st);
       CK(cudaMemcpyAsync(hi, ctx->rotated, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       if (hyrom_status s = sync(ctx)) return s;
       if (!hi[0]) break;
     }
+    t_end(ctx, HYROM_T_EIG);
+    t_begin(ctx, HYROM_T_FORMPHI);
     hy::launch_colnorm2(ctx->X, ctx->N, wp, ctx->lam, ctx->st);
     hy::launch_pod_coeffs<double>(ctx->lam, nullptr, wp, wp, cf.m, cf.pod_tol, cf.pod_abs,
                                   ctx->xraw2, ctx->sig, ctx->m_eff_dev, ctx->Cd, ctx->st);
     hy::launch_phi_from_columns<T>(ctx->X, ctx->N, wp, ctx->Cd, ctx->m_eff_dev, cf.m, phi_out,
                                    ctx->st);
     if (psi_next) hy::launch_window_mean<T>(ring, ctx->N, ctx->win_dev, w, psi_next, ctx->st);
+    t_end(ctx, HYROM_T_FORMPHI);
   } else {
     // FP32: raw ring Gram, centred by the identity, FP64 Jacobi
     t_begin(ctx, HYROM_T_EIG);
@@ -890,7 +895,12 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->lam, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->sig, (size_t)wp * sizeof(double));
   ok &= dal(ctx, &ctx->xraw2, 64);
-  ok &= dal(ctx, &ctx->jbuf, ((size_t)2 * wp * wp + 512) * sizeof(double));
+  {
+    // the eigensolver's work array (FP32 POD), or the FP64 Jacobi rounds'
+    // partial sums and rotations
+    const size_t a = (size_t)2 * wp * wp + 512, b = hy::hestenes_scratch_doubles(wp);
+    ok &= dal(ctx, &ctx->jbuf, (a > b ? a : b) * sizeof(double));
+  }
   ok &= dal(ctx, &ctx->m_eff_dev, 64);
   ok &= dalloc(ctx, &ctx->C, (size_t)wp * m * es);
   ok &= dal(ctx, &ctx->Cd, (size_t)wp * m * sizeof(double));
@@ -1192,7 +1202,7 @@ hyrom_status hyrom_stage_muscl_filter(hyrom_ctx* ctx, double* q_io, const double
   MUSCL_ONLY();
   if (!q_io || !q_prev || q_io == q_prev) return HYROM_EINVAL;
   const hyrom_config& cf = ctx->cfg;
-  const int np = hy::muscl_filter(ctx->dc, q_io, q_prev, q_prev2, k, cf.filt_orders, cf.n_filt,
+  const int np = hy::muscl_filter(ctx->mus, ctx->dc, q_io, q_prev, q_prev2, k, cf.filt_orders, cf.n_filt,
                                   cf.jmax_f, cf.eps_f, (double*)ctx->fg, (double*)ctx->ftmp,
                                   (double*)ctx->rho_old, (double*)ctx->rho_new, ctx->fpart,
                                   ctx->dy + 2, (double*)ctx->host + 28, ctx->st);

@@ -95,7 +95,7 @@ void launch_muscl_rho(const DevCfg& c, const double* q, const double* qp, const 
 int muscl_newton(MusclSolver* m, const DevCfg& c, double* q, const double* qp,
                  const double* qp2, int64_t k, const int* cells, int64_t n, double tol_abs,
                  int newton_max, double eta, cudaStream_t s, int* iters_out, int* arnoldi_out);
-int muscl_filter(const DevCfg& c, double* q, const double* qp, const double* qp2, int64_t k,
+int muscl_filter(MusclSolver* m, const DevCfg& c, double* q, const double* qp, const double* qp2, int64_t k,
                  const int* orders, int n_filt, int jmax_f, double eps_f, double* g,
                  double* tmp, double* rho_old, double* rho_new, double* part, double* out3,
                  double* host3, cudaStream_t s);
@@ -187,8 +187,9 @@ void launch_form_phi(const T* ring, int64_t N, const int* win, int w, const T* p
 template <typename T>
 void launch_center_window(const T* ring, int64_t N, const int* win, int w, int wp, const T* psi,
                           double* X, double* raw_part, double* raw_out, cudaStream_t s);
+size_t hestenes_scratch_doubles(int wp);
 void launch_hestenes_round(double* X, int64_t N, int wp, double* V, int r, double tol,
-                           int* rotated, cudaStream_t s);
+                           int* rotated, double* scratch, cudaStream_t s);
 void launch_identity(double* V, int n, cudaStream_t s);
 int run_jacobi_multi(const double* A, int n, double* V, double* lam, double* buf, int* flag,
                      int* host_flag, double* scale_dev, double* host_scale, int max_sweeps,

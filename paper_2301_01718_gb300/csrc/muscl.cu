@@ -592,6 +592,137 @@ __global__ void k_gate_sum(const double* __restrict__ part, int nb, double* __re
   }
 }
 
+// ---- sparse filter passes ---------------------------------------------------
+// dst = src dilated by r cells along one axis (square dilation = x then y)
+template <int AX>
+__global__ void k_dilate_axis(DevCfg c, const uint32_t* __restrict__ src, int r,
+                              uint32_t* __restrict__ dst) {
+  const bool per = AX == 0 ? c.bc[0] == HYROM_BC_PERIODIC : c.bc[2] == HYROM_BC_PERIODIC;
+  const int len = AX == 0 ? c.nx : c.ny;
+  const int64_t nwords = (c.nc + 31) / 32;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll;
+       base < nwords * 32; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = base + (threadIdx.x & 31);
+    bool on = false;
+    if (cell < c.nc) {
+      const int i = (int)(cell % c.nx), j = (int)(cell / c.nx);
+      const int a = AX == 0 ? i : j;
+      for (int d = -r; d <= r && !on; ++d) {
+        int b = a + d;
+        if (per) b = imod(b, len);
+        else if (b < 0 || b >= len) continue;
+        on = bit_get(src, AX == 0 ? (int64_t)j * c.nx + b : (int64_t)b * c.nx + i);
+      }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, on);
+    if ((threadIdx.x & 31) == 0 && base < c.nc) dst[base >> 5] = word;
+  }
+}
+
+// g on the listed cells: the separable filter x then y, each sum left to
+// right and scaled, as the dense kernels (and the oracle) form it
+__global__ void k_filter_cells(DevCfg c, int n, const double* __restrict__ q,
+                               const int* __restrict__ cells, const long long* __restrict__ count,
+                               double* __restrict__ g) {
+  const double W1[3] = {1.0, 2.0, 1.0};
+  const double W2[5] = {-1.0, 4.0, 10.0, 4.0, -1.0};
+  const double W3[7] = {1.0, -6.0, 15.0, 44.0, 15.0, -6.0, 1.0};
+  const double* wt = n == 1 ? W1 : (n == 2 ? W2 : W3);
+  const double scale = n == 1 ? 0.25 : (n == 2 ? 0.0625 : 0.015625);
+  const bool px = c.bc[0] == HYROM_BC_PERIODIC, py = c.bc[2] == HYROM_BC_PERIODIC;
+  const bool two = c.ny > 1;
+  const int64_t cnt = *count;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 4 * cnt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = e / cnt, cell = cells[e % cnt];
+    const int i = (int)(cell % c.nx), j = (int)(cell / c.nx);
+    double acc_y = 0.0;
+    const int ty = two ? 2 * n : 0;
+    for (int tt = 0; tt <= ty; ++tt) {
+      int jj = two ? j + tt - n : j;
+      jj = py ? imod(jj, c.ny) : (jj < 0 ? 0 : (jj >= c.ny ? c.ny - 1 : jj));
+      double acc = 0.0;
+      for (int ss = 0; ss <= 2 * n; ++ss) {
+        int ii = i + ss - n;
+        ii = px ? imod(ii, c.nx) : (ii < 0 ? 0 : (ii >= c.nx ? c.nx - 1 : ii));
+        const double x = q[v * c.nc + (int64_t)jj * c.nx + ii];
+        const double term = wt[ss] == 1.0 ? x : (wt[ss] == -1.0 ? -x : wt[ss] * x);
+        acc = ss == 0 ? term : acc + term;
+      }
+      const double fx = acc * scale;
+      if (!two) {
+        acc_y = fx;
+        break;
+      }
+      const double term = wt[tt] == 1.0 ? fx : (wt[tt] == -1.0 ? -fx : wt[tt] * fx);
+      acc_y = tt == 0 ? term : acc_y + term;
+    }
+    g[v * c.nc + cell] = two ? acc_y * scale : acc_y;
+  }
+}
+
+// rho on the listed cells
+__global__ void k_muscl_rho_cells(DevCfg c, const double* __restrict__ q,
+                                  const double* __restrict__ qp, const double* __restrict__ qp2,
+                                  double t, const int* __restrict__ cells,
+                                  const long long* __restrict__ count, double* __restrict__ rho) {
+  const Src<double> src{q};
+  const int64_t cnt = *count;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < cnt;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = cells[idx];
+    const int i = (int)(cell % c.nx), j = (int)(cell / c.nx);
+    double f[4];
+    muscl_rhs_cell<double>(c, src, i, j, t, f);
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double qc = q[v * c.nc + cell], p1 = qp[v * c.nc + cell];
+      double R;
+      if (qp2) {
+        const double p2 = qp2[v * c.nc + cell];
+        R = ((1.0 * qc + (-4.0 / 3.0) * p1) + (1.0 / 3.0) * p2) - (c.dt * (2.0 / 3.0)) * f[v];
+      } else {
+        R = (qc - p1) - c.dt * f[v];
+      }
+      acc = v == 0 ? fabs(R) : acc + fabs(R);
+    }
+    rho[cell] = acc;
+  }
+}
+
+// gate on the listed cells (all cells when cells is null): keep where
+// rho_new < rho_old, set the cell's bit in kbits, per-block partial sums
+__global__ void k_gate_cells(DevCfg c, const int* __restrict__ cells,
+                             const long long* __restrict__ count,
+                             const double* __restrict__ rho_old,
+                             const double* __restrict__ rho_new, const double* __restrict__ g,
+                             double* __restrict__ q, uint32_t* __restrict__ kbits,
+                             double* __restrict__ part) {
+  double cnt = 0.0, dec = 0.0, tot = 0.0;
+  const int64_t n = cells ? *count : c.nc;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = cells ? cells[idx] : idx;
+    const double ro = rho_old[cell], rn = rho_new[cell];
+    if (rn < ro) {
+      cnt += 1.0;
+      dec += ro - rn;
+      tot += ro;
+      for (int v = 0; v < 4; ++v) q[v * c.nc + cell] = g[v * c.nc + cell];
+      atomicOr(kbits + (cell >> 5), 1u << (cell & 31));
+    }
+  }
+  cnt = block_sum(cnt);
+  dec = block_sum(dec);
+  tot = block_sum(tot);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = cnt;
+    part[3 * blockIdx.x + 1] = dec;
+    part[3 * blockIdx.x + 2] = tot;
+  }
+}
+
 int grid_for(int64_t n, int per = 256) {
   int64_t b = (n + per - 1) / per;
   if (b > 152 * 8) b = 152 * 8;
@@ -616,6 +747,10 @@ struct MusclSolver {
   double* y = nullptr;
   GmresState* st = nullptr;
   double* host = nullptr;  // pinned: [0] max |R|, [1] scale
+  // sparse filter passes: kept cells, the two dilations and their lists
+  uint32_t *kbits = nullptr, *bm_a = nullptr, *bm_b = nullptr, *bm_t = nullptr;
+  int *list_r = nullptr, *list_g = nullptr;
+  long long *cnt = nullptr, *scan = nullptr;
   size_t bytes = 0;
 };
 
@@ -643,6 +778,15 @@ MusclSolver* muscl_create(int64_t nc, int64_t max_cells) {
   al((void**)&m->nrm, sizeof(double) * 4);
   al((void**)&m->y, sizeof(double) * kRestart);
   al((void**)&m->st, sizeof(GmresState));
+  const int64_t nw = (nc + 31) / 32;
+  al((void**)&m->kbits, sizeof(uint32_t) * nw);
+  al((void**)&m->bm_a, sizeof(uint32_t) * nw);
+  al((void**)&m->bm_b, sizeof(uint32_t) * nw);
+  al((void**)&m->bm_t, sizeof(uint32_t) * nw);
+  al((void**)&m->list_r, sizeof(int) * nc);
+  al((void**)&m->list_g, sizeof(int) * nc);
+  al((void**)&m->cnt, sizeof(long long) * 4);
+  al((void**)&m->scan, sizeof(long long) * 1024);
   if (ok && cudaMallocHost((void**)&m->host, 64) != cudaSuccess) {
     cudaGetLastError();
     ok = false;
@@ -665,6 +809,14 @@ void muscl_destroy(MusclSolver* m) {
   cudaFree(m->nrm);
   cudaFree(m->y);
   cudaFree(m->st);
+  cudaFree(m->kbits);
+  cudaFree(m->bm_a);
+  cudaFree(m->bm_b);
+  cudaFree(m->bm_t);
+  cudaFree(m->list_r);
+  cudaFree(m->list_g);
+  cudaFree(m->cnt);
+  cudaFree(m->scan);
   if (m->host) cudaFreeHost(m->host);
   delete m;
 }
@@ -736,6 +888,14 @@ int muscl_newton(MusclSolver* m, const DevCfg& c, double* q, const double* qp,
       k_norm_reduce<<<1, 256, 0, HY_S(s)>>>(m->part, done, m->nrm);
       k_scale<<<gL, 256, 0, HY_S(s)>>>(m->w, L, m->nrm, 0, done, m->V + (int64_t)(j + 1) * L);
       k_gmres_givens<<<1, 1, 0, HY_S(s)>>>(m->st, j, m->nrm);
+      // every fourth step: stop enqueueing once the cycle has converged
+      if ((j & 3) == 3 && j + 1 < kRestart) {
+        if (cudaMemcpyAsync(m->host + 2, &m->st->done, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          return -1;
+        if (*reinterpret_cast<int*>(m->host + 2)) break;
+      }
     }
     k_gmres_solve<<<1, 1, 0, HY_S(s)>>>(m->st, m->y);
     k_update_state<<<gL, 256, 0, HY_S(s)>>>(c, m->V, n, m->y, m->st, cells, q);
@@ -750,29 +910,58 @@ int muscl_newton(MusclSolver* m, const DevCfg& c, double* q, const double* qp,
 // R_k of Eq. hdm (BDF2; BDF1 when qp2 is null): for each order, the
 // residual measure of q, then passes of filter / measure / gate until no
 // cell is kept, the kept cells' decrease falls below eps_f times their
-// previous total, or jmax_f passes ran.  Every pass covers the whole grid;
-// the decisions are read back once per pass.  g, tmp: 4 nc doubles;
+// previous total, or jmax_f passes ran.  The first pass of an order covers
+// the grid.  A later pass can change g only within a square of n cells of
+// the cells K the previous pass kept, and the residual measure only within
+// two more (the MUSCL stencil): it visits the square of radius n + 2 around
+// K for the measures and the gate and that of radius n + 4 for g; every
+// other cell keeps its "not kept" decision, as the dense pass would give.
+// The decisions are read back once per pass.  g, tmp: 4 nc doubles;
 // rho_old, rho_new: nc; part: 3 * 1216 doubles; out3: 3 device doubles.
 // Returns the passes run, or -1 on a CUDA error.
-int muscl_filter(const DevCfg& c, double* q, const double* qp, const double* qp2, int64_t k,
-                 const int* orders, int n_filt, int jmax_f, double eps_f, double* g,
+int muscl_filter(MusclSolver* m, const DevCfg& c, double* q, const double* qp, const double* qp2,
+                 int64_t k, const int* orders, int n_filt, int jmax_f, double eps_f, double* g,
                  double* tmp, double* rho_old, double* rho_new, double* part, double* out3,
                  double* host3, cudaStream_t s) {
   const double t = (double)k * c.dt;
   const int gq = grid_for(4 * c.nc), gc = grid_for(c.nc);
+  const int64_t nw = (c.nc + 31) / 32;
+  const int gw = grid_for(nw * 32);
   int passes = 0;
+  auto dilate = [&](int r, uint32_t* out) {
+    k_dilate_axis<0><<<gw, 256, 0, HY_S(s)>>>(c, m->kbits, r, c.ny > 1 ? m->bm_t : out);
+    if (c.ny > 1) k_dilate_axis<1><<<gw, 256, 0, HY_S(s)>>>(c, m->bm_t, r, out);
+  };
+  auto listify = [&](const uint32_t* bm, int* list, long long* cnt) {
+    launch_popcount(bm, nw, cnt, s);
+    launch_bits_to_list(bm, c.nc, m->scan, list, c.nc, s);
+  };
   for (int o = 0; o < n_filt; ++o) {
     const int n = orders[o];
-    k_muscl_rho<<<grid_for(c.nc, 128), 128, 0, HY_S(s)>>>(c, q, qp, qp2, t, rho_old);
     for (int p = 0; p < jmax_f; ++p) {
-      if (c.ny > 1) {
-        k_shapiro<0><<<gq, 256, 0, HY_S(s)>>>(c, n, q, tmp);
-        k_shapiro<1><<<gq, 256, 0, HY_S(s)>>>(c, n, tmp, g);
+      if (cudaMemsetAsync(m->kbits, 0, sizeof(uint32_t) * nw, s) != cudaSuccess) return -1;
+      if (p == 0) {
+        k_muscl_rho<<<grid_for(c.nc, 128), 128, 0, HY_S(s)>>>(c, q, qp, qp2, t, rho_old);
+        if (c.ny > 1) {
+          k_shapiro<0><<<gq, 256, 0, HY_S(s)>>>(c, n, q, tmp);
+          k_shapiro<1><<<gq, 256, 0, HY_S(s)>>>(c, n, tmp, g);
+        } else {
+          k_shapiro<0><<<gq, 256, 0, HY_S(s)>>>(c, n, q, g);
+        }
+        k_muscl_rho<<<grid_for(c.nc, 128), 128, 0, HY_S(s)>>>(c, g, qp, qp2, t, rho_new);
+        k_gate_cells<<<gc, 256, 0, HY_S(s)>>>(c, nullptr, nullptr, rho_old, rho_new, g, q,
+                                              m->kbits, part);
       } else {
-        k_shapiro<0><<<gq, 256, 0, HY_S(s)>>>(c, n, q, g);
+        // the cells kept by the previous pass are in bm_a (saved below)
+        const int gr = grid_for(c.nc, 128);
+        k_muscl_rho_cells<<<gr, 128, 0, HY_S(s)>>>(c, q, qp, qp2, t, m->list_r, m->cnt,
+                                                    rho_old);
+        k_filter_cells<<<gq, 256, 0, HY_S(s)>>>(c, n, q, m->list_g, m->cnt + 1, g);
+        k_muscl_rho_cells<<<gr, 128, 0, HY_S(s)>>>(c, g, qp, qp2, t, m->list_r, m->cnt,
+                                                    rho_new);
+        k_gate_cells<<<gc, 256, 0, HY_S(s)>>>(c, m->list_r, m->cnt, rho_old, rho_new, g, q,
+                                              m->kbits, part);
       }
-      k_muscl_rho<<<grid_for(c.nc, 128), 128, 0, HY_S(s)>>>(c, g, qp, qp2, t, rho_new);
-      k_gate<<<gc, 256, 0, HY_S(s)>>>(c, rho_old, rho_new, g, q, part);
       k_gate_sum<<<1, 256, 0, HY_S(s)>>>(part, gc, out3);
       if (cudaMemcpyAsync(host3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
               cudaSuccess ||
@@ -781,7 +970,12 @@ int muscl_filter(const DevCfg& c, double* q, const double* qp, const double* qp2
       ++passes;
       if (host3[0] == 0.0) break;
       if (host3[1] < eps_f * host3[2]) break;
-      k_muscl_rho<<<grid_for(c.nc, 128), 128, 0, HY_S(s)>>>(c, q, qp, qp2, t, rho_old);
+      if (p + 1 < jmax_f) {  // the next pass's cells, from the cells just kept
+        dilate(n + 2, m->bm_a);
+        listify(m->bm_a, m->list_r, m->cnt);
+        dilate(n + 4, m->bm_b);
+        listify(m->bm_b, m->list_g, m->cnt + 1);
+      }
     }
   }
   return passes;

@@ -1346,16 +1346,26 @@ __global__ void k_sum_parts(const double* __restrict__ part, int n, double* out)
   if (threadIdx.x == 0) *out = a;
 }
 
-// One round: CTA b orthogonalises the column pair (p, q) of X and applies
-// the same rotation to V (wp x wp column-major).
-__global__ void k_hestenes_round(double* __restrict__ X, int64_t N, int wp,
-                                 double* __restrict__ V, int r, double tol, int* rotated) {
+// One round of the one-sided Jacobi SVD of the window: the wp/2 disjoint
+// column pairs (p, q) of round r are orthogonalised at once, spread over
+// every SM in three launches:
+//   k_hj_dots   - partial sums of |x_p|^2, |x_q|^2 and x_p . x_q, kHjBlocks
+//                 row slices per pair;
+//   k_hj_angles - one warp per pair sums its partials in a fixed order and
+//                 forms the rotation (or none: g = 0 or |g| <= tol |x_p||x_q|),
+//                 applies it to V;
+//   k_hj_apply  - rotates the columns of X, row by row.
+constexpr int kHjBlocks = 128;
+
+__global__ void k_hj_dots(const double* __restrict__ X, int64_t N, int wp, int r,
+                          double* __restrict__ part) {
   int p, q;
-  rr_pair(wp, r, blockIdx.x, p, q);
-  double* xp = X + (int64_t)p * N;
-  double* xq = X + (int64_t)q * N;
+  rr_pair(wp, r, blockIdx.y, p, q);
+  const double* xp = X + (int64_t)p * N;
+  const double* xq = X + (int64_t)q * N;
   double a = 0.0, b = 0.0, g = 0.0;
-  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const double u = xp[i], v = xq[i];
     a = fma(u, u, a);
     b = fma(v, v, b);
@@ -1364,26 +1374,83 @@ __global__ void k_hestenes_round(double* __restrict__ X, int64_t N, int wp,
   a = block_sum(a);
   b = block_sum(b);
   g = block_sum(g);
-  if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) return;
-  const double zeta = (b - a) / (2.0 * g);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
-    const double u = xp[i], v = xq[i];
-    xp[i] = c * u - s * v;
-    xq[i] = s * u + c * v;
+  if (threadIdx.x == 0) {
+    double* o = part + ((int64_t)blockIdx.y * kHjBlocks + blockIdx.x) * 3;
+    o[0] = a;
+    o[1] = b;
+    o[2] = g;
   }
-  for (int i = threadIdx.x; i < wp; i += blockDim.x) {
-    const double u = V[(int64_t)p * wp + i], v = V[(int64_t)q * wp + i];
-    V[(int64_t)p * wp + i] = c * u - s * v;
-    V[(int64_t)q * wp + i] = s * u + c * v;
-  }
-  if (threadIdx.x == 0) *rotated = 1;
 }
 
+__global__ void k_hj_angles(const double* __restrict__ part, int wp, int r, double tol,
+                            double* __restrict__ cs, double* __restrict__ V, int* rotated) {
+  const int lane = threadIdx.x & 31;
+  for (int pair = threadIdx.x >> 5; pair < wp / 2; pair += blockDim.x >> 5) {
+  int p, q;
+  rr_pair(wp, r, pair, p, q);
+  double a = 0.0, b = 0.0, g = 0.0;
+  for (int k = lane; k < kHjBlocks; k += 32) {
+    const double* o = part + ((int64_t)pair * kHjBlocks + k) * 3;
+    a += o[0];
+    b += o[1];
+    g += o[2];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  g = warp_sum(g);
+  double c = 1.0, sn = 0.0;
+  const bool rot = !(g == 0.0 || fabs(g) <= tol * sqrt(a * b));
+  if (rot) {
+    const double zeta = (b - a) / (2.0 * g);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    sn = c * t;
+    for (int i = lane; i < wp; i += 32) {
+      const double u = V[(int64_t)p * wp + i], v = V[(int64_t)q * wp + i];
+      V[(int64_t)p * wp + i] = c * u - sn * v;
+      V[(int64_t)q * wp + i] = sn * u + c * v;
+    }
+    if (lane == 0) *rotated = 1;
+  }
+  if (lane == 0) {
+    cs[2 * pair] = c;
+    cs[2 * pair + 1] = rot ? sn : 0.0;
+  }
+  }
+}
+
+__global__ void k_hj_apply(double* __restrict__ X, int64_t N, int wp, int r,
+                           const double* __restrict__ cs) {
+  const int np = wp / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int pair = 0; pair < np; ++pair) {
+      const double sn = cs[2 * pair + 1];
+      if (sn == 0.0) continue;
+      const double c = cs[2 * pair];
+      int p, q;
+      rr_pair(wp, r, pair, p, q);
+      double* xp = X + (int64_t)p * N;
+      double* xq = X + (int64_t)q * N;
+      const double u = xp[i], v = xq[i];
+      xp[i] = c * u - sn * v;
+      xq[i] = sn * u + c * v;
+    }
+  }
+}
+
+size_t hestenes_scratch_doubles(int wp) { return (size_t)(wp / 2) * (kHjBlocks * 3 + 2); }
+
 void launch_hestenes_round(double* X, int64_t N, int wp, double* V, int r, double tol,
-                           int* rotated, cudaStream_t s) {
-  k_hestenes_round<<<wp / 2, 256, 0, HY_S(s)>>>(X, N, wp, V, r, tol, rotated);
+                           int* rotated, double* scratch, cudaStream_t s) {
+  const int np = wp / 2;
+  double* part = scratch;
+  double* cs = scratch + (size_t)np * kHjBlocks * 3;
+  k_hj_dots<<<dim3(kHjBlocks, np), 256, 0, HY_S(s)>>>(X, N, wp, r, part);
+  k_hj_angles<<<1, 32 * (np < 32 ? np : 32), 0, HY_S(s)>>>(part, wp, r, tol, cs, V, rotated);
+  int64_t blocks = (N + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_hj_apply<<<(int)blocks, 256, 0, HY_S(s)>>>(X, N, wp, r, cs);
 }
 
 __global__ void k_colnorm2(const double* __restrict__ X, int64_t N, double* __restrict__ out) {
