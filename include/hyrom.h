@@ -215,6 +215,20 @@ hyrom_status hyrom_advance(hyrom_ctx* ctx, hyrom_step_info* info);
 hyrom_status hyrom_update_basis(hyrom_ctx* ctx, hyrom_step_info* info);
 hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info);
 
+/* Checkpoint / resume.  hyrom_save writes the context's state that carries
+ * from one step to the next (the step index, the w+1 snapshots, the basis,
+ * psi, the ODEIM points and the sampled pseudo-inverse, the sampled sets and
+ * the active tiles, the snapshot Gram matrix, the sample-row factor) to the
+ * file `path` (binary, this library's layout; about (w + 1 + m) states).
+ * hyrom_load reads such a file into a context created with the same grid,
+ * scheme, precision, sides, w, m, n_p and regression rows (its other run
+ * parameters are its own); the next hyrom_step continues the saved run
+ * exactly.  Both synchronise the stream.  Errors: HYROM_EINVAL (null path,
+ * file not opened, written or of another layout), HYROM_ENOMEM (pinned
+ * staging buffer), HYROM_ECUDA.  The paper has no counterpart. */
+hyrom_status hyrom_save(hyrom_ctx* ctx, const char* path);
+hyrom_status hyrom_load(hyrom_ctx* ctx, const char* path);
+
 /* hyrom_sample: the sampled set S-hat in effect for the next step, as
  * ascending cell ids in idx_dev (capacity cap; HYROM_ECAP if larger; the
  * count is always written to *n_out) and, when bitmap_dev is not NULL, as a
@@ -398,6 +412,16 @@ hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
 typedef struct hyrom_batch hyrom_batch;
 hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, int32_t threads,
                                 hyrom_batch** out);
+/* hyrom_init_batch: n instances at once (configs[4] of the scope table): for
+ * each i a stream of its own (non-blocking) and a context hyrom_init(&cfgs[i],
+ * q0[i], q0_on_host, that stream), then hyrom_batch_create over them.  The
+ * batch owns these contexts and streams and hyrom_batch_destroy releases them;
+ * ctxs_out (nullable, n entries) receives the contexts for state access
+ * (the caller must not destroy them).  On failure nothing is left allocated.
+ * Errors: those of hyrom_init and hyrom_batch_create, HYROM_ECUDA. */
+hyrom_status hyrom_init_batch(const hyrom_config* cfgs, const double* const* q0,
+                              int32_t q0_on_host, int32_t n, int32_t threads,
+                              hyrom_ctx** ctxs_out, hyrom_batch** out);
 hyrom_status hyrom_batch_step(hyrom_batch* batch, int32_t nsteps, hyrom_step_info* infos,
                               int32_t* status);
 int32_t hyrom_batch_threads(const hyrom_batch* batch);

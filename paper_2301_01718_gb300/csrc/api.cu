@@ -30,7 +30,7 @@ struct hyrom_ctx {
   int f32 = 0;
   size_t esz = 8;
   int64_t N = 0, nc = 0, nwords = 0;
-  int w = 0, m = 0, np = 0, nslot = 0, wp = 0;
+  int w = 0, m = 0, np = 0, nslot = 0, wp = 0, ntiles_max = 0;
   int64_t k = 0;
   int sticky = 0;
   std::string err;
@@ -842,6 +842,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   const int wp = ctx->wp, m = ctx->m;
   ctx->gram_chunks = 1024;
   const int ntiles_max = (int)(((cfg->nx + 31) / 32 + 1) * ((cfg->ny + 7) / 8 + 1) + (cfg->nx + 255) / 256 + 1);
+  ctx->ntiles_max = ntiles_max;
   bool ok = true;
   ok &= dalloc(ctx, &ctx->ring, (size_t)ctx->nslot * N * es);
   ok &= dalloc(ctx, &ctx->psi, N * es);
@@ -1061,6 +1062,195 @@ hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info) {
   if (s2 != HYROM_OK && s2 != HYROM_ERANK) return s2;
   if (s != HYROM_OK) return s;
   return s2;
+}
+
+// ---- checkpoint / resume ------------------------------------------------------
+namespace {
+
+struct CkRec {
+  uint32_t tag;
+  void* p;
+  size_t bytes;
+};
+
+// The device state that carries from one step to the next.
+std::vector<CkRec> ck_records(hyrom_ctx* c) {
+  const size_t es = c->esz, N = (size_t)c->N, nw = (size_t)c->nwords;
+  std::vector<CkRec> r = {
+      {1, c->ring, (size_t)c->nslot * N * es},
+      {2, c->psi, N * es},
+      {3, c->phi, N * (size_t)c->m * es},
+      {4, c->pts, 1024 * sizeof(int)},
+      {5, c->pinv, (size_t)c->m * c->cfg.n_p * sizeof(double)},
+      {6, c->y, 256 * sizeof(double)},
+      {7, c->shat, nw * 4},
+      {8, c->stilde, nw * 4},
+      {9, c->g_bm, nw * 4},
+      {10, c->tiles, (size_t)c->ntiles_max * sizeof(int)},
+      {11, c->ntiles, 64},
+      {12, c->H, (size_t)c->nslot * c->nslot * sizeof(double)},
+      {13, c->m_eff_dev, 64},
+  };
+  if (c->cfg.regress_rows == HYROM_ROWS_SAMPLE) {
+    r.push_back({14, c->s_cells, (size_t)c->nc * sizeof(int)});
+    r.push_back({15, c->s_L, 4096 * sizeof(double)});
+    r.push_back({16, c->s_dinv, 64 * sizeof(double)});
+  }
+  return r;
+}
+
+const char kCkMagic[8] = {'H', 'Y', 'R', 'O', 'M', 'C', 'K', 1};
+
+bool same_layout(const hyrom_config& a, const hyrom_config& b) {
+  bool ok = a.pde == b.pde && a.scheme == b.scheme && a.precision == b.precision &&
+            a.nx == b.nx && a.ny == b.ny && a.w == b.w && a.m == b.m && a.n_p == b.n_p &&
+            a.regress_rows == b.regress_rows;
+  for (int i = 0; i < 4; ++i) ok = ok && a.bc[i] == b.bc[i];
+  return ok;
+}
+
+}  // namespace
+
+hyrom_status hyrom_save(hyrom_ctx* ctx, const char* path) {
+  GUARD();
+  if (!path) return HYROM_EINVAL;
+  if (hyrom_status s = sync(ctx)) return s;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, HYROM_EINVAL, "hyrom_save: cannot open %s", path);
+  const std::vector<CkRec> recs = ck_records(ctx);
+  const size_t chunk = (size_t)64 << 20;
+  void* stage = nullptr;
+  if (cudaMallocHost(&stage, chunk) != cudaSuccess) {
+    cudaGetLastError();
+    fclose(f);
+    return fail(ctx, HYROM_ENOMEM, "hyrom_save: pinned staging buffer");
+  }
+  bool ok = true;
+  auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+  const uint32_t version = 1, cfg_bytes = (uint32_t)sizeof(hyrom_config);
+  put(kCkMagic, 8);
+  put(&version, 4);
+  put(&cfg_bytes, 4);
+  put(&ctx->cfg, sizeof(hyrom_config));
+  const int64_t k = ctx->k, n_s = ctx->n_s;
+  const int32_t sc[6] = {ctx->m_eff, ctx->np_eff, ctx->has_basis, ctx->psi_set,
+                         ctx->sample_ok ? 1 : 0, 0};
+  put(&k, 8);
+  put(&n_s, 8);
+  put(sc, sizeof sc);
+  const uint32_t npsi = (uint32_t)ctx->psi_steps.size();
+  put(&npsi, 4);
+  if (npsi) put(ctx->psi_steps.data(), npsi * sizeof(int64_t));
+  const uint32_t nrec = (uint32_t)recs.size();
+  put(&nrec, 4);
+  hyrom_status st = HYROM_OK;
+  for (const CkRec& r : recs) {
+    const uint64_t bytes = r.bytes;
+    put(&r.tag, 4);
+    put(&bytes, 8);
+    for (size_t off = 0; ok && off < r.bytes; off += chunk) {
+      const size_t n = r.bytes - off < chunk ? r.bytes - off : chunk;
+      if (cudaMemcpyAsync(stage, (const char*)r.p + off, n, cudaMemcpyDeviceToHost, ctx->st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+        st = HYROM_ECUDA;
+        ok = false;
+        break;
+      }
+      put(stage, n);
+    }
+  }
+  cudaFreeHost(stage);
+  if (fclose(f) != 0) ok = false;
+  if (st == HYROM_ECUDA) return fail(ctx, HYROM_ECUDA, "hyrom_save: device read failed");
+  if (!ok) return fail(ctx, HYROM_EINVAL, "hyrom_save: write to %s failed", path);
+  return HYROM_OK;
+}
+
+hyrom_status hyrom_load(hyrom_ctx* ctx, const char* path) {
+  GUARD();
+  if (!path) return HYROM_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, HYROM_EINVAL, "hyrom_load: cannot open %s", path);
+  bool ok = true;
+  auto get = [&](void* p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
+  char magic[8];
+  uint32_t version = 0, cfg_bytes = 0;
+  get(magic, 8);
+  get(&version, 4);
+  get(&cfg_bytes, 4);
+  if (!ok || memcmp(magic, kCkMagic, 8) != 0 || version != 1 ||
+      cfg_bytes != sizeof(hyrom_config)) {
+    fclose(f);
+    return fail(ctx, HYROM_EINVAL, "hyrom_load: %s is not a checkpoint of this library", path);
+  }
+  hyrom_config saved;
+  get(&saved, sizeof saved);
+  if (!ok || !same_layout(saved, ctx->cfg)) {
+    fclose(f);
+    return fail(ctx, HYROM_EINVAL,
+                "hyrom_load: the checkpoint's grid, scheme, precision, sides, w, m, n_p or "
+                "regression rows differ from this context's");
+  }
+  int64_t k = 0, n_s = 0;
+  int32_t sc[6];
+  uint32_t npsi = 0;
+  get(&k, 8);
+  get(&n_s, 8);
+  get(sc, sizeof sc);
+  get(&npsi, 4);
+  std::vector<int64_t> psi_steps(npsi);
+  if (npsi) get(psi_steps.data(), npsi * sizeof(int64_t));
+  uint32_t nrec = 0;
+  get(&nrec, 4);
+  const std::vector<CkRec> recs = ck_records(ctx);
+  if (!ok || nrec != recs.size()) {
+    fclose(f);
+    return fail(ctx, HYROM_EINVAL, "hyrom_load: %s is truncated or of another layout", path);
+  }
+  const size_t chunk = (size_t)64 << 20;
+  void* stage = nullptr;
+  if (cudaMallocHost(&stage, chunk) != cudaSuccess) {
+    cudaGetLastError();
+    fclose(f);
+    return fail(ctx, HYROM_ENOMEM, "hyrom_load: pinned staging buffer");
+  }
+  hyrom_status st = HYROM_OK;
+  for (const CkRec& r : recs) {
+    uint32_t tag = 0;
+    uint64_t bytes = 0;
+    get(&tag, 4);
+    get(&bytes, 8);
+    if (!ok || tag != r.tag || bytes != r.bytes) {
+      ok = false;
+      break;
+    }
+    for (size_t off = 0; ok && off < r.bytes; off += chunk) {
+      const size_t n = r.bytes - off < chunk ? r.bytes - off : chunk;
+      get(stage, n);
+      if (!ok) break;
+      if (cudaMemcpyAsync((char*)r.p + off, stage, n, cudaMemcpyHostToDevice, ctx->st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+        st = HYROM_ECUDA;
+        ok = false;
+      }
+    }
+  }
+  cudaFreeHost(stage);
+  fclose(f);
+  if (st == HYROM_ECUDA) return fail(ctx, HYROM_ECUDA, "hyrom_load: device write failed");
+  if (!ok) return fail(ctx, HYROM_EINVAL, "hyrom_load: %s is truncated or of another layout", path);
+  ctx->k = k;
+  ctx->n_s = n_s;
+  ctx->m_eff = sc[0];
+  ctx->np_eff = sc[1];
+  ctx->has_basis = sc[2];
+  ctx->psi_set = sc[3];
+  ctx->sample_ok = sc[4] != 0;
+  ctx->norms_ready = false;
+  ctx->psi_steps = psi_steps;
+  return HYROM_OK;
 }
 
 hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t* n_out,

@@ -27,6 +27,9 @@
 
 struct hyrom_batch {
   std::vector<hyrom_ctx*> ctx;
+  // contexts and streams made by hyrom_init_batch, released with the batch
+  std::vector<hyrom_ctx*> owned_ctx;
+  std::vector<cudaStream_t> owned_streams;
   std::vector<std::vector<int>> groups;  // instances sharing a stream, largest groups first
   int device = 0;
   std::vector<std::thread> pool;
@@ -175,5 +178,44 @@ extern "C" void hyrom_batch_destroy(hyrom_batch* b) {
   b->cv_go.notify_all();
   for (auto& t : b->pool)
     if (t.joinable()) t.join();
+  for (hyrom_ctx* c : b->owned_ctx) hyrom_destroy(c);
+  for (cudaStream_t st : b->owned_streams) cudaStreamDestroy(st);
   delete b;
+}
+
+// n instances in one call: each context on a stream of its own, made here
+// and owned by the batch with the contexts (hyrom_batch_destroy releases
+// both).  The scope table's hyrom_init_batch.
+extern "C" hyrom_status hyrom_init_batch(const hyrom_config* cfgs, const double* const* q0,
+                                         int32_t q0_on_host, int32_t n, int32_t threads,
+                                         hyrom_ctx** ctxs_out, hyrom_batch** out) {
+  if (!cfgs || !q0 || !out || n <= 0 || threads < 0) return HYROM_EINVAL;
+  std::vector<hyrom_ctx*> ctxs;
+  std::vector<cudaStream_t> streams;
+  auto undo = [&](hyrom_status s) {
+    for (hyrom_ctx* c : ctxs) hyrom_destroy(c);
+    for (cudaStream_t st : streams) cudaStreamDestroy(st);
+    return s;
+  };
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return undo(HYROM_ECUDA);
+    }
+    streams.push_back(st);
+    hyrom_ctx* c = nullptr;
+    const hyrom_status s = hyrom_init(&cfgs[i], q0[i], q0_on_host, (void*)st, &c);
+    if (s != HYROM_OK) return undo(s);
+    ctxs.push_back(c);
+  }
+  hyrom_batch* b = nullptr;
+  const hyrom_status s = hyrom_batch_create(ctxs.data(), n, threads, &b);
+  if (s != HYROM_OK) return undo(s);
+  b->owned_ctx = ctxs;
+  b->owned_streams = streams;
+  if (ctxs_out)
+    for (int i = 0; i < n; ++i) ctxs_out[i] = ctxs[i];
+  *out = b;
+  return HYROM_OK;
 }

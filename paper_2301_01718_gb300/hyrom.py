@@ -148,6 +148,10 @@ def lib():
         "hyrom_stage_reduced_vjp": (st, [vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                          vp]),
         "hyrom_batch_create": (st, [C.POINTER(vp), i32, i32, C.POINTER(vp)]),
+        "hyrom_init_batch": (st, [C.POINTER(HyromConfig), C.POINTER(vp), i32, i32, i32,
+                                  C.POINTER(vp), C.POINTER(vp)]),
+        "hyrom_save": (st, [vp, C.c_char_p]),
+        "hyrom_load": (st, [vp, C.c_char_p]),
         "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
         "hyrom_batch_threads": (i32, [vp]),
         "hyrom_batch_destroy": (None, [vp]),
@@ -403,6 +407,30 @@ def hyrom_batch_step(batch, n, nsteps=1, ctxs=None):
         why = [f"{i}: {hyrom_last_error(ctxs[i])}" for i in bad] if ctxs else bad
         raise HyromError(s, f"instances failed: {why}")
     return status, [i.as_dict() for i in infos]
+
+
+def hyrom_init_batch(cfgs, q0s, q0_on_host=False, threads=0):
+    """Contexts (each on a stream of its own, owned by the batch) and a batch
+    over them.  q0s: device tensors or addresses (host arrays with
+    q0_on_host).  Returns (batch, [contexts])."""
+    n = len(cfgs)
+    carr = (HyromConfig * n)(*[c if isinstance(c, HyromConfig) else make_config(c) for c in cfgs])
+    qarr = (C.c_void_p * n)(*[_ptr(q).value for q in q0s])
+    ctxs = (C.c_void_p * n)()
+    out = C.c_void_p()
+    s = lib().hyrom_init_batch(carr, qarr, int(bool(q0_on_host)), n, int(threads), ctxs,
+                               C.byref(out))
+    if s != HYROM_OK:
+        raise HyromError(s, "hyrom_init_batch")
+    return out.value, [ctxs[i] for i in range(n)]
+
+
+def hyrom_save(ctx, path):
+    _check(ctx, lib().hyrom_save(ctx, os.fsencode(path)))
+
+
+def hyrom_load(ctx, path):
+    _check(ctx, lib().hyrom_load(ctx, os.fsencode(path)))
 
 
 def hyrom_batch_threads(batch):
