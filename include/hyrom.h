@@ -385,6 +385,47 @@ hyrom_status hyrom_stage_reduced_vjp(hyrom_ctx* ctx, const void* phi, int32_t m,
                                      const void* lam, void* lam_v, void* lam_psi, void* lam_phi,
                                      void* work);
 
+/* hyrom_stage_pod_vjp: the adjoint of POD_m (Eq. pod) of one window as
+ * hyrom_adjoint applies it (thin-SVD derivative, distinct singular values):
+ * for the window X (N x w column-major, w = cfg.w, time order) centred at
+ * psi and the cotangent lphi (N x m) of the m kept, signed modes (the POD
+ * must keep exactly m), lam_window (N x w, overwritten) gets the cotangent
+ * of the window columns and lpsi_out (N, overwritten) that of psi (minus the
+ * sum of lam_window's columns).  FP64 contexts.  Synchronises.
+ * hyrom_stage_filter_vjp: the adjoint of SpatialFilter (Sec. 2.3.4) at q
+ * with the residual relative to q_prev at t_k, the forward passes' keep
+ * masks and stops held: the filter runs on a copy of q recording each pass,
+ * then lam_io <- the passes' transposes in reverse order applied to lam_io.
+ * FP64 Euler SSP-RK2 contexts.  Synchronises. */
+hyrom_status hyrom_stage_pod_vjp(hyrom_ctx* ctx, const double* window, int32_t w,
+                                 const double* psi, const double* lphi, int32_t m,
+                                 double* lam_window, double* lpsi_out);
+hyrom_status hyrom_stage_filter_vjp(hyrom_ctx* ctx, const double* q, const double* q_prev,
+                                    int64_t k, double* lam_io);
+
+/* hyrom_adjoint: the gradient of the time-integrated box pressure
+ *   J = sum_{k=1..steps} dt sum_{box} p(gamma_k) dx dy
+ * with respect to the initial state gamma_0, through Algorithm 1 with the
+ * forward run's decisions held (the sampled sets, G, the ODEIM points, every
+ * filter pass's keep mask and stop, the POD rank and each mode's sign; the
+ * bases and reference states are differentiated as functions of the
+ * snapshots, by the thin-SVD derivative, distinct singular values).  The
+ * context must be at k = 0 (fresh from hyrom_init); the call runs `steps`
+ * steps of Algorithm 1 recording what the reverse sweep needs (every state,
+ * and per hybrid step the predictor, coordinates, sets and keep masks; about
+ * 2 N doubles per step), then one reverse sweep: per step the output term,
+ * the transposed filter passes, the reduced step's adjoint, the step adjoint,
+ * and per rebuild the POD adjoint (each basis recomputed from its window in
+ * reverse) and the window means'.  box: {i0, i1, j0, j1} host int32 (cells
+ * [i0, i1) x [j0, j1)); J_out: host double (nullable); dJdq0: N device
+ * doubles.  FP64 Euler SSP-RK2 contexts on ODEIM rows.  The context is left
+ * at k = steps.  Synchronises.  dJ/dtheta for parameters of the initial
+ * state is (dq0/dtheta)^T dJdq0.  Errors: HYROM_EINVAL, HYROM_ESTATE (not at
+ * k = 0, or a window of rank below m), HYROM_ENOMEM, HYROM_ECUDA, and those of
+ * hyrom_step. */
+hyrom_status hyrom_adjoint(hyrom_ctx* ctx, int32_t steps, const int32_t* box, double* J_out,
+                           double* dJdq0);
+
 /* ---- batching form ---------------------------------------------------------
  * Many independent instances of Algorithm 1 (each its own context, grid,
  * basis size, window and sample fraction) stepped together by a pool of host

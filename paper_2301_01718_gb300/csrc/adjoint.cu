@@ -382,4 +382,253 @@ void launch_rk2_vjp(const DevCfg& c, const double* q, const double* lam_out, dou
                                               lam_out, 1.0, lam_in);
 }
 
+// ---------------------------------------------------------------------------
+// reverse sweep pieces (hyrom_adjoint)
+// ---------------------------------------------------------------------------
+
+// lam += w (dp/dq)^T on the cells of the box [i0, i1) x [j0, j1), p the ideal
+// gas pressure (gamma - 1)(E - |m|^2 / (2 rho)): the output term of a step
+__global__ void k_pressure_vjp(DevCfg c, const double* __restrict__ q, int i0, int i1, int j0,
+                               int j1, double w, double* __restrict__ lam) {
+  const int bw = i1 - i0;
+  const int64_t nb = (int64_t)bw * (j1 - j0);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = (int64_t)(j0 + e / bw) * c.nx + (i0 + e % bw);
+    const double rho = q[cell], mx = q[c.nc + cell], my = q[2 * c.nc + cell];
+    const double kin = (mx * mx + my * my) / rho;
+    const double g1 = (c.gamma - 1.0) * w;
+    lam[cell] += g1 * (0.5 * kin / rho);
+    lam[c.nc + cell] += g1 * (-mx / rho);
+    lam[2 * c.nc + cell] += g1 * (-my / rho);
+    lam[3 * c.nc + cell] += g1;
+  }
+}
+
+// sum over the box of w p(q), one partial per block, added into *acc by the
+// last step of the reduction
+__global__ void k_box_pressure(DevCfg c, const double* __restrict__ q, int i0, int i1, int j0,
+                               int j1, double w, double* __restrict__ acc) {
+  const int bw = i1 - i0;
+  const int64_t nb = (int64_t)bw * (j1 - j0);
+  double sum = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = (int64_t)(j0 + e / bw) * c.nx + (i0 + e % bw);
+    const double rho = q[cell], mx = q[c.nc + cell], my = q[2 * c.nc + cell],
+                 en = q[3 * c.nc + cell];
+    sum += (c.gamma - 1.0) * (en - 0.5 * (mx * mx + my * my) / rho);
+  }
+  sum = block_sum(sum);
+  if (threadIdx.x == 0) acc[blockIdx.x] = w * sum;
+}
+
+__global__ void k_sum_into(const double* __restrict__ part, int n, double* __restrict__ total) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *total += s;
+}
+
+// kept = lam on the cells of `keep` (zero elsewhere); lam zeroed there
+__global__ void k_keep_split(DevCfg c, const uint32_t* __restrict__ keep, double* __restrict__ lam,
+                             double* __restrict__ kept) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.ndof;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = e % c.nc;
+    const bool k = bit_get(keep, cell);
+    kept[e] = k ? lam[e] : 0.0;
+    if (k) lam[e] = 0.0;
+  }
+}
+
+// Transpose of the order-2n Shapiro filter along x (AX = 0) or y (AX = 1):
+// out_a = 4^-n sum over the (b, t) whose tap b + t - n lands on a (after the
+// wrap of a periodic side or the clamp of another) of w_t in_b
+template <int AX>
+__global__ void k_shapiro_T(DevCfg c, int n, const double* __restrict__ in,
+                            double* __restrict__ out, int accumulate) {
+  const double W1[3] = {1.0, 2.0, 1.0};
+  const double W2[5] = {-1.0, 4.0, 10.0, 4.0, -1.0};
+  const double W3[7] = {1.0, -6.0, 15.0, 44.0, 15.0, -6.0, 1.0};
+  const double* wt = n == 1 ? W1 : (n == 2 ? W2 : W3);
+  const double scale = n == 1 ? 0.25 : (n == 2 ? 0.0625 : 0.015625);
+  const bool per = AX == 0 ? c.bc[0] == HYROM_BC_PERIODIC : c.bc[2] == HYROM_BC_PERIODIC;
+  const int len = AX == 0 ? c.nx : c.ny;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.ndof;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = e / c.nc, cell = e % c.nc;
+    const int i = (int)(cell % c.nx), j = (int)(cell / c.nx);
+    const int a = AX == 0 ? i : j;
+    double acc = 0.0;
+    if (per) {
+      // tap t of source b lands on a exactly when b = a - t + n (mod len)
+      for (int t = 0; t <= 2 * n; ++t) {
+        const int bb = imod(a - t + n, len);
+        const int64_t src = AX == 0 ? (int64_t)j * c.nx + bb : (int64_t)bb * c.nx + i;
+        acc += wt[t] * in[v * c.nc + src];
+      }
+    } else {
+      // sources b within n of a, and on an end cell also the sources whose
+      // taps run past it and are clamped onto it
+      const int lo = a - n - (a == 0 ? n : 0), hi = a + n + (a == len - 1 ? n : 0);
+      for (int b = lo < 0 ? 0 : lo; b <= hi && b < len; ++b) {
+        for (int t = 0; t <= 2 * n; ++t) {
+          int tap = b + t - n;
+          tap = tap < 0 ? 0 : (tap >= len ? len - 1 : tap);
+          if (tap != a) continue;
+          const int64_t src = AX == 0 ? (int64_t)j * c.nx + b : (int64_t)b * c.nx + i;
+          acc += wt[t] * in[v * c.nc + src];
+        }
+      }
+    }
+    const double r = acc * scale;
+    out[e] = accumulate ? out[e] + r : r;
+  }
+}
+
+// X[:, c] = state_{win_c} - psi (column-major N x wp; columns w..wp-1 zero)
+__global__ void k_center_states(const double* __restrict__ states, int64_t N,
+                                const int* __restrict__ win, int w, int wp,
+                                const double* __restrict__ psi, double* __restrict__ X) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * wp;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(e / N);
+    const int64_t r = e % N;
+    X[e] = col < w ? states[(int64_t)win[col] * N + r] - psi[r] : 0.0;
+  }
+}
+
+// part[(a * nb + b)] = partial sums of A[:, a] . B[:, b] over row slices
+// (grid.x slices, grid.y = na * nb pairs)
+__global__ void k_tsdots(const double* __restrict__ A, int na, const double* __restrict__ B,
+                         int nb, int64_t N, double* __restrict__ part) {
+  const int pair = blockIdx.y, a = pair / nb, b = pair % nb;
+  double acc = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(A[(int64_t)a * N + r], B[(int64_t)b * N + r], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(int64_t)pair * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_tsdots_reduce(const double* __restrict__ part, int npairs, int nslice,
+                                double* __restrict__ out) {
+  for (int p = threadIdx.x >> 5; p < npairs; p += blockDim.x >> 5) {
+    double acc = 0.0;
+    for (int k = threadIdx.x & 31; k < nslice; k += 32) acc += part[(int64_t)p * nslice + k];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) out[p] = acc;
+  }
+}
+
+// The thin-SVD adjoint applied to the window: for each window column c,
+//   lx = sum_j L[:, j] B1[j, c] + sum_i X[:, i] B2[i, c],
+// lam_{win_c} += lx + lpsi_new / w, and lpsi_cur -= sum_c lx.
+// L: N x m, X: N x wp, B1: m x w, B2: wp x w (row-major small matrices).
+__global__ void k_pod_vjp_apply(int64_t N, int m, int wp, int w, const double* __restrict__ L,
+                                const double* __restrict__ X, const double* __restrict__ B1,
+                                const double* __restrict__ B2, const int* __restrict__ win,
+                                const double* __restrict__ lpsi_new, double* __restrict__ lam,
+                                double* __restrict__ lpsi_cur) {
+  extern __shared__ double sb[];
+  double* b1 = sb;
+  double* b2 = sb + m * w;
+  for (int i = threadIdx.x; i < m * w; i += blockDim.x) b1[i] = B1[i];
+  for (int i = threadIdx.x; i < wp * w; i += blockDim.x) b2[i] = B2[i];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double pn = lpsi_new ? lpsi_new[r] / (double)w : 0.0;
+    double tot = 0.0;
+    for (int col = 0; col < w; ++col) {
+      double lx = 0.0;
+      for (int j = 0; j < m; ++j) lx = fma(L[(int64_t)j * N + r], b1[j * w + col], lx);
+      for (int i = 0; i < wp; ++i) lx = fma(X[(int64_t)i * N + r], b2[i * w + col], lx);
+      lam[(int64_t)win[col] * N + r] += lx + pn;
+      tot += lx;
+    }
+    lpsi_cur[r] -= tot;
+  }
+}
+
+// lam_{j} += lpsi / w for the w window snapshots j = win[c]
+__global__ void k_mean_vjp(int64_t N, const int* __restrict__ win, int w,
+                           const double* __restrict__ lpsi, double* __restrict__ lam) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = lpsi[r] / (double)w;
+    for (int c = 0; c < w; ++c) lam[(int64_t)win[c] * N + r] += v;
+  }
+}
+
+namespace {
+int agrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+}  // namespace
+
+void launch_pressure_vjp(const DevCfg& c, const double* q, const int* box, double w, double* lam,
+                         cudaStream_t s) {
+  const int64_t nb = (int64_t)(box[1] - box[0]) * (box[3] - box[2]);
+  k_pressure_vjp<<<agrid(nb), 256, 0, HY_S(s)>>>(c, q, box[0], box[1], box[2], box[3], w, lam);
+}
+
+void launch_box_pressure(const DevCfg& c, const double* q, const int* box, double w,
+                         double* part, double* total, cudaStream_t s) {
+  const int64_t nb = (int64_t)(box[1] - box[0]) * (box[3] - box[2]);
+  const int g = agrid(nb);
+  k_box_pressure<<<g, 256, 0, HY_S(s)>>>(c, q, box[0], box[1], box[2], box[3], w, part);
+  k_sum_into<<<1, 256, 0, HY_S(s)>>>(part, g, total);
+}
+
+// lam <- lam off the kept cells + F^T (lam on them), the passes in reverse
+void launch_filter_vjp(const DevCfg& c, const uint32_t* keeps, const int* orders, int npass,
+                       double* lam, double* tmp1, double* tmp2, cudaStream_t s) {
+  const int64_t nw = (c.nc + 31) / 32;
+  const int g = agrid(c.ndof);
+  for (int p = npass - 1; p >= 0; --p) {
+    const int n = orders[p];
+    k_keep_split<<<g, 256, 0, HY_S(s)>>>(c, keeps + (int64_t)p * nw, lam, tmp1);
+    if (c.ny > 1) {
+      k_shapiro_T<1><<<g, 256, 0, HY_S(s)>>>(c, n, tmp1, tmp2, 0);
+      k_shapiro_T<0><<<g, 256, 0, HY_S(s)>>>(c, n, tmp2, lam, 1);
+    } else {
+      k_shapiro_T<0><<<g, 256, 0, HY_S(s)>>>(c, n, tmp1, lam, 1);
+    }
+  }
+}
+
+void launch_center_states(const double* states, int64_t N, const int* win, int w, int wp,
+                          const double* psi, double* X, cudaStream_t s) {
+  k_center_states<<<agrid(N * wp), 256, 0, HY_S(s)>>>(states, N, win, w, wp, psi, X);
+}
+
+// out (na x nb, row-major a, b) = A^T B for column-major N x na and N x nb
+void launch_tsdots(const double* A, int na, const double* B, int nb, int64_t N, double* part,
+                   double* out, cudaStream_t s) {
+  const int ns = 64;
+  k_tsdots<<<dim3(ns, na * nb), 256, 0, HY_S(s)>>>(A, na, B, nb, N, part);
+  k_tsdots_reduce<<<1, 1024, 0, HY_S(s)>>>(part, na * nb, ns, out);
+}
+
+size_t tsdots_part_doubles(int na, int nb) { return (size_t)64 * na * nb; }
+
+void launch_pod_vjp_apply(int64_t N, int m, int wp, int w, const double* L, const double* X,
+                          const double* B1, const double* B2, const int* win,
+                          const double* lpsi_new, double* lam, double* lpsi_cur,
+                          cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)m * w + (size_t)wp * w);
+  smem_at_least((const void*)k_pod_vjp_apply, smem);
+  k_pod_vjp_apply<<<agrid(N), 256, smem, HY_S(s)>>>(N, m, wp, w, L, X, B1, B2, win, lpsi_new, lam,
+                                                    lpsi_cur);
+}
+
+void launch_mean_vjp(int64_t N, const int* win, int w, const double* lpsi, double* lam,
+                     cudaStream_t s) {
+  k_mean_vjp<<<agrid(N), 256, 0, HY_S(s)>>>(N, win, w, lpsi, lam);
+}
+
 }  // namespace hy

@@ -8,7 +8,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <cstdarg>
@@ -23,8 +25,38 @@
 
 using hy::DevCfg;
 
+// The forward record of a run that hyrom_adjoint sweeps backwards: every
+// state, and for each hybrid step the predictor (the partial step before the
+// reconstruction), the reduced coordinates, the sampled set and ODEIM points
+// in effect, and each filter pass's keep bitmap and order; for each rebuild
+// the window and the reference-state versions it read and made.  Bases are
+// not kept: the reverse sweep recomputes each from its window.
+struct AdjStep {
+  bool full = false, rebuild = false, psi_init = false;
+  int phi_ver = -1, psi_ver = -1, m_eff = 0, n_p = 0;
+  int psi_cur = -1, new_phi = -1, new_psi = -1, init_psi = -1;
+};
+struct AdjTape {
+  int steps = 0, passmax = 0, box[4] = {0, 0, 0, 0};
+  double wgt = 0.0;
+  double* states = nullptr;   // (steps + 1) x N
+  double* vpred = nullptr;    // (steps + 1) x N
+  double* ys = nullptr;       // (steps + 1) x 64
+  uint32_t* shats = nullptr;  // (steps + 1) x nwords
+  int* rows = nullptr;        // (steps + 1) x n_p
+  uint32_t* keeps = nullptr;  // (steps + 1) x passmax x nwords
+  int* orders = nullptr;      // (steps + 1) x passmax
+  int* npass = nullptr;       // steps + 1
+  double* Jpart = nullptr;    // 1216 partial sums
+  double* J = nullptr;        // the output
+  std::vector<double*> psis;  // reference-state versions (N each)
+  std::vector<AdjStep> rec;   // index = step
+  int cur_phi = -1, cur_psi = -1, nphi = 0;
+};
+
 struct hyrom_ctx {
   hyrom_config cfg;
+  AdjTape* tape = nullptr;  // set while hyrom_adjoint records its forward run
   DevCfg dc;
   cudaStream_t st = nullptr;
   int f32 = 0;
@@ -451,6 +483,20 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
         gappy_y<T>(ctx, q, psi, ctx->y, nullptr, nullptr);
       t_end(ctx, HYROM_T_GAPPY);
       inf.J = 1;
+      if (AdjTape* tp = ctx->tape) {  // the adjoint's record of this hybrid step
+        const size_t N = (size_t)ctx->N, nw = (size_t)ctx->nwords;
+        CK(cudaMemcpyAsync(tp->vpred + k * N, q, N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(tp->ys + k * 64, ctx->y, 64 * 8, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(tp->shats + k * nw, ctx->shat, nw * 4, cudaMemcpyDeviceToDevice,
+                           ctx->st));
+        CK(cudaMemcpyAsync(tp->rows + k * (size_t)cf.n_p, ctx->pts, (size_t)ctx->np_eff * 4,
+                           cudaMemcpyDeviceToDevice, ctx->st));
+        AdjStep& r = tp->rec[k];
+        r.phi_ver = tp->cur_phi;
+        r.psi_ver = tp->cur_psi;
+        r.m_eff = ctx->m_eff;
+        r.n_p = ctx->np_eff;
+      }
     } else {
       CK(cudaMemcpyAsync(q, qp, ctx->N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
       if (muscl)  // the cells of S-hat, ascending: the partial solve's unknowns
@@ -505,15 +551,28 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
         ctx->muscl_passes = np;
       }
     } else if (cf.n_filt > 0) {
+      AdjTape* tp = ctx->tape;
+      const size_t nw = (size_t)ctx->nwords;
       hy::launch_filter_sparse<T>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, q, qp,
                                   k, (T*)ctx->fg, ctx->kbits, ctx->ftiles_a, ctx->ftiles_b,
                                   ctx->fcounts, ctx->fpart, ctx->fctl, ctx->fargs,
-                                  &ctx->filt_graph, ctx->st);
+                                  &ctx->filt_graph, ctx->st,
+                                  tp ? tp->keeps + (size_t)k * tp->passmax * nw : nullptr,
+                                  tp ? tp->orders + (size_t)k * tp->passmax : nullptr,
+                                  tp ? tp->npass + k : nullptr);
     }
     t_end(ctx, HYROM_T_FILTER);
   }
   // physical-state check of the new snapshot (Euler): rho > 0 and p > 0
   if (ctx->dc.nvar == 4) hy::launch_count_nonphys<T>(ctx->dc, q, ctx->fail_dev + 12, ctx->st);
+  if (AdjTape* tp = ctx->tape) {  // the state and the output term of this step
+    if constexpr (sizeof(T) == 8) {
+      CK(cudaMemcpyAsync(tp->states + k * (size_t)ctx->N, q, (size_t)ctx->N * 8,
+                         cudaMemcpyDeviceToDevice, ctx->st));
+      hy::launch_box_pressure(ctx->dc, q, tp->box, tp->wgt, tp->Jpart, tp->J, ctx->st);
+    }
+    tp->rec[k].full = full;
+  }
   CKL();
   ctx->k = k;
   gram_update<T>(ctx, k);
@@ -677,6 +736,15 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     CK(cudaMemcpyAsync(ctx->win_dev, win.data(), w * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
     hy::launch_window_mean<T>((const T*)ctx->ring, ctx->N, ctx->win_dev, w, (T*)ctx->psi, ctx->st);
     ctx->psi_set = 1;
+    if (AdjTape* tp = ctx->tape) {  // version: psi_{w-1}
+      double* v = nullptr;
+      CK(cudaMalloc((void**)&v, (size_t)ctx->N * 8));
+      CK(cudaMemcpyAsync(v, ctx->psi, (size_t)ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+      tp->psis.push_back(v);
+      tp->cur_psi = (int)tp->psis.size() - 1;
+      tp->rec[k].psi_init = true;
+      tp->rec[k].init_psi = tp->cur_psi;
+    }
   }
   const bool due = k >= w - 1 && (cf.z <= 0 || (k + 1) % cf.z != 0);
   if (!due) {
@@ -765,6 +833,18 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
                             hy::rk2_tile_height(ctx->dc), ctx->tiles, ctx->ntiles, ctx->st);
   // psi update: psi_{k+1} = mean of the window
   std::swap(ctx->psi, ctx->psi_next);
+  if (AdjTape* tp = ctx->tape) {  // this rebuild: its window and versions
+    AdjStep& r = tp->rec[k];
+    r.rebuild = true;
+    r.psi_cur = tp->cur_psi;
+    double* v = nullptr;
+    CK(cudaMalloc((void**)&v, (size_t)ctx->N * 8));
+    CK(cudaMemcpyAsync(v, ctx->psi, (size_t)ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    tp->psis.push_back(v);
+    r.new_psi = tp->cur_psi = (int)tp->psis.size() - 1;
+    r.new_phi = tp->cur_phi = tp->nphi++;
+    r.m_eff = me;
+  }
   ctx->psi_steps.clear();
   for (int i = 0; i < w; ++i) ctx->psi_steps.push_back(k - w + 1 + i);
   ctx->has_basis = 1;
@@ -1062,6 +1142,390 @@ hyrom_status hyrom_step(hyrom_ctx* ctx, hyrom_step_info* info) {
   if (s2 != HYROM_OK && s2 != HYROM_ERANK) return s2;
   if (s != HYROM_OK) return s;
   return s2;
+}
+
+// ---- the reverse sweep (hyrom_adjoint) -------------------------------------------
+namespace {
+
+__global__ void k_add_into(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+void add_into(const double* x, double* y, int64_t n, cudaStream_t s) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  k_add_into<<<(int)(b < 1 ? 1 : b), 256, 0, HY_S(s)>>>(x, y, n);
+}
+
+void free_tape(AdjTape* tp) {
+  if (!tp) return;
+  cudaFree(tp->states);
+  cudaFree(tp->vpred);
+  cudaFree(tp->ys);
+  cudaFree(tp->shats);
+  cudaFree(tp->rows);
+  cudaFree(tp->keeps);
+  cudaFree(tp->orders);
+  cudaFree(tp->npass);
+  cudaFree(tp->Jpart);
+  cudaFree(tp->J);
+  for (double* v : tp->psis) cudaFree(v);
+  delete tp;
+}
+
+// The POD of version v recomputed from its window (the same kernels on the
+// same inputs as the forward rebuild, so the same bits): phi_out gets Phi,
+// ctx->X the rotated window columns (U Sigma, unsorted), ctx->V their right
+// vectors, ctx->lam the squared column norms.
+hyrom_status recompute_pod(hyrom_ctx* ctx, AdjTape* tp, int k_rebuild, int psi_cur, double* phi_out,
+                           int* me) {
+  const int w = ctx->cfg.w;
+  const size_t N = (size_t)ctx->N;
+  std::vector<int> win(w);
+  for (int c = 0; c < w; ++c) {
+    win[c] = c;
+    CK(cudaMemcpyAsync((double*)ctx->ring + (size_t)c * N, tp->states + (size_t)(k_rebuild - w + 1 + c) * N,
+                       N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  }
+  return pod_t<double>(ctx, (const double*)ctx->ring, ctx->nslot, win, tp->psis[psi_cur], nullptr,
+                       phi_out, nullptr, me);
+}
+
+// The thin-SVD adjoint of a rebuild (Sec. 2.3.1, Eq. pod; distinct singular
+// values): with the POD's window columns X = U Sigma V^T (ctx->X, ->V, ->lam
+// after recompute_pod) and the cotangent L of Phi's m kept columns (Phi_j =
+// g_j U_j, g_j the sign that makes Phi's largest entry positive),
+//   lam_X = sum_j [(l_j - U U^T l_j) / s_j] V_j^T
+//         + sum_j sum_{i != j} c_ij (s_j U_i V_j^T + s_i U_j V_i^T),
+//   c_ij = (U_i . l_j) / (s_j^2 - s_i^2),
+// written as lam_X = L B1 + X B2 with small B1 (m x w), B2 (wp x w) formed on
+// the host; then lam_{window} += lam_X + lpsi_new / w, lpsi_cur -= sum_c lam_X.
+hyrom_status pod_vjp(hyrom_ctx* ctx, AdjTape* tp, int k_rebuild, const double* phi, int m,
+                     const double* lphi, const double* lpsi_new, double* lpsi_cur, double* lam,
+                     double* part) {
+  // the POD's own column count: the window padded to an even width
+  const int w = ctx->cfg.w, wp = w % 2 ? w + 1 : w;
+  const int64_t N = ctx->N;
+  std::vector<double> lam2(wp), V((size_t)wp * wp), D1((size_t)wp * std::max(m, 1)),
+      D2((size_t)wp * std::max(m, 1));
+  CK(cudaMemcpyAsync(lam2.data(), ctx->lam, wp * 8, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(V.data(), ctx->V, (size_t)wp * wp * 8, cudaMemcpyDeviceToHost, ctx->st));
+  double* dev_small = part + hy::tsdots_part_doubles(wp, m);
+  if (m > 0) {
+    hy::launch_tsdots(ctx->X, wp, lphi, m, N, part, dev_small, ctx->st);
+    CK(cudaMemcpyAsync(D1.data(), dev_small, (size_t)wp * m * 8, cudaMemcpyDeviceToHost, ctx->st));
+    hy::launch_tsdots(ctx->X, wp, phi, m, N, part, dev_small, ctx->st);
+    CK(cudaMemcpyAsync(D2.data(), dev_small, (size_t)wp * m * 8, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (hyrom_status s = sync(ctx)) return s;
+  // singular values in descending order (ties: lower column first), nonzero ones
+  std::vector<int> perm;
+  for (int c = 0; c < wp; ++c)
+    if (lam2[c] > 0.0) perm.push_back(c);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return lam2[a] > lam2[b]; });
+  const int r = (int)perm.size();
+  if (m > r) return fail(ctx, HYROM_ESTATE, "adjoint: the window has rank %d < %d", r, m);
+  std::vector<double> sg(r), gsign(r, 1.0);
+  for (int i = 0; i < r; ++i) sg[i] = std::sqrt(lam2[perm[i]]);
+  for (int j = 0; j < m; ++j) gsign[j] = D2[(size_t)perm[j] * m + j] >= 0.0 ? 1.0 : -1.0;
+  auto Vv = [&](int i, int c) { return gsign[i] * V[(size_t)perm[i] * wp + c]; };  // V_i[c]
+  // A[i][j] = U_i . l_j
+  std::vector<double> A((size_t)r * m);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = gsign[i] * D1[(size_t)perm[i] * m + j] / sg[i];
+  std::vector<double> B1((size_t)std::max(m, 1) * w, 0.0), M((size_t)r * w, 0.0),
+      B2((size_t)wp * w, 0.0);
+  for (int j = 0; j < m; ++j)
+    for (int c = 0; c < w; ++c) B1[(size_t)j * w + c] = Vv(j, c) / sg[j];
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < m; ++j) {
+      double coef = -A[(size_t)i * m + j] / sg[j];
+      if (i != j) coef += A[(size_t)i * m + j] / (sg[j] * sg[j] - sg[i] * sg[i]) * sg[j];
+      for (int c = 0; c < w; ++c) M[(size_t)i * w + c] += coef * Vv(j, c);
+    }
+  for (int j = 0; j < m; ++j)  // term 3 on U_j: sum_{i != j} c_ij s_i V_i
+    for (int i = 0; i < r; ++i) {
+      if (i == j) continue;
+      const double cij = A[(size_t)i * m + j] / (sg[j] * sg[j] - sg[i] * sg[i]);
+      for (int c = 0; c < w; ++c) M[(size_t)j * w + c] += cij * sg[i] * Vv(i, c);
+    }
+  for (int i = 0; i < r; ++i)  // U_i = g_i X[:, perm_i] / s_i
+    for (int c = 0; c < w; ++c) B2[(size_t)perm[i] * w + c] = gsign[i] * M[(size_t)i * w + c] / sg[i];
+  double* dB1 = dev_small;
+  double* dB2 = dev_small + (size_t)std::max(m, 1) * w;
+  int* dwin = (int*)(dB2 + (size_t)wp * w);
+  std::vector<int> win(w);
+  for (int c = 0; c < w; ++c) win[c] = k_rebuild - w + 1 + c;
+  CK(cudaMemcpyAsync(dB1, B1.data(), B1.size() * 8, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(dB2, B2.data(), B2.size() * 8, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(dwin, win.data(), w * 4, cudaMemcpyHostToDevice, ctx->st));
+  hy::launch_pod_vjp_apply(N, m, wp, w, lphi, ctx->X, dB1, dB2, dwin, lpsi_new, lam, lpsi_cur,
+                           ctx->st);
+  CKL();
+  return sync(ctx);
+}
+
+}  // namespace
+
+hyrom_status hyrom_stage_pod_vjp(hyrom_ctx* ctx, const double* window, int32_t w,
+                                 const double* psi, const double* lphi, int32_t m,
+                                 double* lam_window, double* lpsi_out) {
+  GUARD();
+  if (!window || !psi || !lphi || !lam_window || !lpsi_out || w != ctx->cfg.w || m < 1)
+    return HYROM_EINVAL;
+  if (ctx->f32) return fail(ctx, HYROM_EINVAL, "hyrom_stage_pod_vjp: FP64 contexts");
+  const size_t N = (size_t)ctx->N;
+  std::vector<int> win(w);
+  for (int c = 0; c < w; ++c) {
+    win[c] = c;
+    CK(cudaMemcpyAsync((double*)ctx->ring + c * N, window + c * N, N * 8, cudaMemcpyDeviceToDevice,
+                       ctx->st));
+  }
+  double* phi = nullptr;
+  double* part = nullptr;
+  const size_t pwork = hy::tsdots_part_doubles(ctx->wp, m) + (size_t)m * w + (size_t)ctx->wp * w +
+                       w + 64;
+  if (cudaMalloc((void**)&phi, N * m * 8) != cudaSuccess ||
+      cudaMalloc((void**)&part, pwork * 8) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(phi);
+    return fail(ctx, HYROM_ENOMEM, "hyrom_stage_pod_vjp: scratch");
+  }
+  int me = 0;
+  hyrom_status s = pod_t<double>(ctx, (const double*)ctx->ring, ctx->nslot, win, psi, nullptr, phi,
+                                 nullptr, &me);
+  if (s == HYROM_OK && me != m)
+    s = fail(ctx, HYROM_EINVAL, "hyrom_stage_pod_vjp: the POD keeps %d modes, not %d", me, m);
+  if (s == HYROM_OK && (cudaMemsetAsync(lam_window, 0, N * w * 8, ctx->st) != cudaSuccess ||
+                        cudaMemsetAsync(lpsi_out, 0, N * 8, ctx->st) != cudaSuccess))
+    s = fail(ctx, HYROM_ECUDA, "hyrom_stage_pod_vjp: clear");
+  if (s == HYROM_OK) {
+    AdjTape tp;  // window c = step c: the window lands on lam_window's columns
+    s = pod_vjp(ctx, &tp, w - 1, phi, m, lphi, nullptr, lpsi_out, lam_window, part);
+  }
+  cudaFree(phi);
+  cudaFree(part);
+  return s;
+}
+
+hyrom_status hyrom_stage_filter_vjp(hyrom_ctx* ctx, const double* q, const double* q_prev,
+                                    int64_t k, double* lam_io) {
+  GUARD();
+  if (!q || !q_prev || !lam_io) return HYROM_EINVAL;
+  if (ctx->f32 || ctx->cfg.scheme != HYROM_SCHEME_RK2 || ctx->cfg.pde != HYROM_PDE_EULER)
+    return fail(ctx, HYROM_EINVAL, "hyrom_stage_filter_vjp: FP64 Euler SSP-RK2 contexts");
+  const hyrom_config& cf = ctx->cfg;
+  const size_t N = (size_t)ctx->N, nw = (size_t)ctx->nwords;
+  const int passmax = std::max(1, cf.n_filt * cf.jmax_f);
+  double *qf = nullptr, *t1 = nullptr, *t2 = nullptr;
+  uint32_t* keeps = nullptr;
+  int *orders = nullptr, *count = nullptr;
+  bool ok = cudaMalloc((void**)&qf, N * 8) == cudaSuccess &&
+            cudaMalloc((void**)&t1, N * 8) == cudaSuccess &&
+            cudaMalloc((void**)&t2, N * 8) == cudaSuccess &&
+            cudaMalloc((void**)&keeps, (size_t)passmax * nw * 4) == cudaSuccess &&
+            cudaMalloc((void**)&orders, (size_t)passmax * 4) == cudaSuccess &&
+            cudaMalloc((void**)&count, 4) == cudaSuccess;
+  hyrom_status s = HYROM_OK;
+  if (!ok) {
+    cudaGetLastError();
+    s = fail(ctx, HYROM_ENOMEM, "hyrom_stage_filter_vjp: scratch");
+  }
+  std::vector<int> ord(passmax);
+  int npass = 0;
+  if (s == HYROM_OK) {
+    CK(cudaMemcpyAsync(qf, q, N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    hy::launch_filter_sparse<double>(ctx->dc, cf.filt_orders, cf.n_filt, cf.jmax_f, cf.eps_f, qf,
+                                     q_prev, k, (double*)ctx->fg, ctx->kbits, ctx->ftiles_a,
+                                     ctx->ftiles_b, ctx->fcounts, ctx->fpart, ctx->fctl,
+                                     ctx->fargs, nullptr, ctx->st, keeps, orders, count);
+    CK(cudaMemcpyAsync(&npass, count, 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ord.data(), orders, passmax * 4, cudaMemcpyDeviceToHost, ctx->st));
+    s = sync(ctx);
+  }
+  if (s == HYROM_OK) {
+    hy::launch_filter_vjp(ctx->dc, keeps, ord.data(), npass, lam_io, t1, t2, ctx->st);
+    s = sync(ctx);
+  }
+  cudaFree(qf);
+  cudaFree(t1);
+  cudaFree(t2);
+  cudaFree(keeps);
+  cudaFree(orders);
+  cudaFree(count);
+  return s;
+}
+
+hyrom_status hyrom_adjoint(hyrom_ctx* ctx, int32_t steps, const int32_t* box, double* J_out,
+                           double* dJdq0) {
+  GUARD();
+  const hyrom_config& cf = ctx->cfg;
+  if (steps < 1 || !box || !dJdq0) return HYROM_EINVAL;
+  if (ctx->f32 || cf.pde != HYROM_PDE_EULER || cf.scheme != HYROM_SCHEME_RK2 ||
+      cf.regress_rows != HYROM_ROWS_ODEIM)
+    return fail(ctx, HYROM_EINVAL, "hyrom_adjoint: FP64 Euler SSP-RK2 contexts on ODEIM rows");
+  if (ctx->k != 0) return fail(ctx, HYROM_ESTATE, "hyrom_adjoint: the context must be at k = 0");
+  if (!(box[0] >= 0 && box[0] < box[1] && box[1] <= cf.nx && box[2] >= 0 && box[2] < box[3] &&
+        box[3] <= cf.ny))
+    return fail(ctx, HYROM_EINVAL, "hyrom_adjoint: box outside the grid");
+  const size_t N = (size_t)ctx->N, nw = (size_t)ctx->nwords;
+  AdjTape* tp = new AdjTape;
+  tp->steps = steps;
+  for (int i = 0; i < 4; ++i) tp->box[i] = box[i];
+  tp->wgt = cf.dt * cf.dx * cf.dy;
+  tp->passmax = std::max(1, cf.n_filt * cf.jmax_f);
+  tp->rec.assign(steps + 1, AdjStep());
+  const size_t S = (size_t)steps + 1;
+  bool ok = true;
+  auto al = [&](void** p, size_t b) {
+    if (ok && cudaMalloc(p, b) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  };
+  al((void**)&tp->states, S * N * 8);
+  al((void**)&tp->vpred, S * N * 8);
+  al((void**)&tp->ys, S * 64 * 8);
+  al((void**)&tp->shats, S * nw * 4);
+  al((void**)&tp->rows, S * (size_t)cf.n_p * 4);
+  al((void**)&tp->keeps, S * tp->passmax * nw * 4);
+  al((void**)&tp->orders, S * tp->passmax * 4);
+  al((void**)&tp->npass, S * 4);
+  al((void**)&tp->Jpart, 152 * 8 * 8);
+  al((void**)&tp->J, 8);
+  if (!ok) {
+    free_tape(tp);
+    return fail(ctx, HYROM_ENOMEM, "hyrom_adjoint: tape allocation");
+  }
+  hyrom_status st = HYROM_OK;
+  auto done = [&](hyrom_status s) {
+    ctx->tape = nullptr;
+    free_tape(tp);
+    return s;
+  };
+  if (cudaMemsetAsync(tp->J, 0, 8, ctx->st) != cudaSuccess ||
+      cudaMemsetAsync(tp->npass, 0, S * 4, ctx->st) != cudaSuccess ||
+      cudaMemcpyAsync(tp->states, ring_at<double>(ctx, 0), N * 8, cudaMemcpyDeviceToDevice,
+                      ctx->st) != cudaSuccess)
+    return done(fail(ctx, HYROM_ECUDA, "hyrom_adjoint: tape set-up"));
+  // ---- forward run, recorded
+  ctx->tape = tp;
+  for (int k = 1; k <= steps; ++k) {
+    hyrom_step_info inf;
+    st = hyrom_step(ctx, &inf);
+    if (st != HYROM_OK && st != HYROM_ERANK) return done(st);
+  }
+  ctx->tape = nullptr;
+  std::vector<int> npass(S);
+  std::vector<int> orders(S * tp->passmax);
+  double Jh = 0.0;
+  if (cudaMemcpyAsync(npass.data(), tp->npass, S * 4, cudaMemcpyDeviceToHost, ctx->st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(orders.data(), tp->orders, S * tp->passmax * 4, cudaMemcpyDeviceToHost,
+                      ctx->st) != cudaSuccess ||
+      cudaMemcpyAsync(&Jh, tp->J, 8, cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess)
+    return done(fail(ctx, HYROM_ECUDA, "hyrom_adjoint: tape read-back"));
+  if ((st = sync(ctx))) return done(st);
+  if (J_out) *J_out = Jh;
+  // ---- reverse sweep
+  const int m = cf.m;
+  double *lam = nullptr, *lphi = nullptr, *phi = nullptr, *lk = nullptr, *lv = nullptr,
+         *lpsi_t = nullptr, *lphi_t = nullptr, *lin = nullptr, *t1 = nullptr, *t2 = nullptr,
+         *work = nullptr, *part = nullptr;
+  std::vector<double*> lpsi(tp->psis.size(), nullptr);
+  const size_t rwork = hy::reduced_vjp_work_doubles(m, cf.n_p);
+  const size_t pwork = hy::tsdots_part_doubles(ctx->wp, m) + (size_t)m * cf.w +
+                       (size_t)ctx->wp * cf.w + cf.w + 64;
+  al((void**)&lam, S * N * 8);
+  al((void**)&lphi, N * m * 8);
+  al((void**)&phi, N * m * 8);
+  al((void**)&lk, N * 8);
+  al((void**)&lv, N * 8);
+  al((void**)&lpsi_t, N * 8);
+  al((void**)&lphi_t, N * m * 8);
+  al((void**)&lin, N * 8);
+  al((void**)&t1, N * 8);
+  al((void**)&t2, N * 8);
+  al((void**)&work, std::max(rwork, 3 * N) * 8);
+  al((void**)&part, pwork * 8);
+  for (auto& p : lpsi) al((void**)&p, N * 8);
+  auto release = [&](hyrom_status s) {
+    for (double* p : {lam, lphi, phi, lk, lv, lpsi_t, lphi_t, lin, t1, t2, work, part}) cudaFree(p);
+    for (double* p : lpsi) cudaFree(p);
+    return done(s);
+  };
+  if (!ok) return release(fail(ctx, HYROM_ENOMEM, "hyrom_adjoint: sweep allocation"));
+  if (cudaMemsetAsync(lam, 0, S * N * 8, ctx->st) != cudaSuccess ||
+      cudaMemsetAsync(lphi, 0, N * m * 8, ctx->st) != cudaSuccess)
+    return release(fail(ctx, HYROM_ECUDA, "hyrom_adjoint: sweep set-up"));
+  for (double* p : lpsi)
+    if (cudaMemsetAsync(p, 0, N * 8, ctx->st) != cudaSuccess)
+      return release(fail(ctx, HYROM_ECUDA, "hyrom_adjoint: sweep set-up"));
+  // rebuild step of each basis version, and the version whose POD is in phi
+  std::vector<int> made_at(tp->nphi, -1), made_psi(tp->nphi, -1);
+  for (int k = 0; k <= steps; ++k)
+    if (tp->rec[k].rebuild) {
+      made_at[tp->rec[k].new_phi] = k;
+      made_psi[tp->rec[k].new_phi] = tp->rec[k].psi_cur;
+    }
+  int cached = -1, cached_me = 0;
+  auto ensure_pod = [&](int v) -> hyrom_status {
+    if (cached == v) return HYROM_OK;
+    int me = 0;
+    if (hyrom_status s = recompute_pod(ctx, tp, made_at[v], made_psi[v], phi, &me)) return s;
+    cached = v;
+    cached_me = me;
+    return HYROM_OK;
+  };
+  for (int k = steps; k >= 1; --k) {
+    const AdjStep& r = tp->rec[k];
+    if (r.rebuild) {  // the rebuild after step k: its POD and its psi
+      if ((st = ensure_pod(r.new_phi))) return release(st);
+      if (cached_me != r.m_eff) return release(fail(ctx, HYROM_ECUDA, "adjoint: POD rank differs"));
+      if ((st = pod_vjp(ctx, tp, k, phi, r.m_eff, lphi, lpsi[r.new_psi], lpsi[r.psi_cur], lam, part)))
+        return release(st);
+      if (cudaMemsetAsync(lphi, 0, N * m * 8, ctx->st) != cudaSuccess)
+        return release(fail(ctx, HYROM_ECUDA, "adjoint"));
+    }
+    if (r.psi_init) {  // psi_{w-1} = mean(gamma_0 .. gamma_{w-1})
+      std::vector<int> win(cf.w);
+      for (int c = 0; c < cf.w; ++c) win[c] = c;
+      int* dwin = (int*)part;
+      CK(cudaMemcpyAsync(dwin, win.data(), cf.w * 4, cudaMemcpyHostToDevice, ctx->st));
+      hy::launch_mean_vjp(ctx->N, dwin, cf.w, lpsi[r.init_psi], lam, ctx->st);
+      if ((st = sync(ctx))) return release(st);
+    }
+    // lk = lambda_k + the output term of step k
+    CK(cudaMemcpyAsync(lk, lam + (size_t)k * N, N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    hy::launch_pressure_vjp(ctx->dc, tp->states + (size_t)k * N, tp->box, tp->wgt, lk, ctx->st);
+    const double* prev = tp->states + (size_t)(k - 1) * N;
+    double* lprev = lam + (size_t)(k - 1) * N;
+    if (r.full) {
+      hy::launch_rk2_vjp(ctx->dc, prev, lk, lin, nullptr, k, work, ctx->st);
+      add_into(lin, lprev, (int64_t)N, ctx->st);
+    } else {
+      const uint32_t* shat = tp->shats + (size_t)k * nw;
+      hy::launch_filter_vjp(ctx->dc, tp->keeps + (size_t)k * tp->passmax * nw,
+                            orders.data() + (size_t)k * tp->passmax, npass[k], lk, t1, t2,
+                            ctx->st);
+      if ((st = ensure_pod(r.phi_ver))) return release(st);
+      hy::launch_reduced_vjp(ctx->N, ctx->nc, r.m_eff, phi, tp->rows + (size_t)k * cf.n_p, r.n_p,
+                             tp->vpred + (size_t)k * N, tp->psis[r.psi_ver],
+                             tp->ys + (size_t)k * 64, shat, lk, lv, lpsi_t, lphi_t, work,
+                             ctx->st);
+      add_into(lpsi_t, lpsi[r.psi_ver], (int64_t)N, ctx->st);
+      add_into(lphi_t, lphi, (int64_t)N * r.m_eff, ctx->st);
+      hy::launch_rk2_vjp(ctx->dc, prev, lv, lin, shat, k, work, ctx->st);
+      add_into(lin, lprev, (int64_t)N, ctx->st);
+    }
+    CKL();
+    if ((st = sync(ctx))) return release(st);
+  }
+  CK(cudaMemcpyAsync(dJdq0, lam, N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  st = sync(ctx);
+  return release(st);
 }
 
 // ---- checkpoint / resume ------------------------------------------------------

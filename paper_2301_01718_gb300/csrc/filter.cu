@@ -62,6 +62,7 @@ __global__ void k_gate_finalize(const double* __restrict__ part, int nblk, doubl
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
+
 // ---------------------------------------------------------------------------
 // fused, sparse filter pass
 //
@@ -103,13 +104,46 @@ struct FiltArgs {
   T* q;
   const T* qp;
   double t;
+  // optional record of the passes run (the adjoint's forward tape): pass p's
+  // keep bitmap at keeps + p * nwords, its Shapiro n at orders[p], the
+  // number recorded in *count (null keeps: nothing is recorded)
+  uint32_t* keeps;
+  int* orders;
+  int* count;
 };
 
 template <typename T>
-__global__ void k_set_filt_args(FiltArgs<T>* fa, T* q, const T* qp, double t) {
+__global__ void k_set_filt_args(FiltArgs<T>* fa, T* q, const T* qp, double t, uint32_t* keeps,
+                                int* orders, int* count) {
   fa->q = q;
   fa->qp = qp;
   fa->t = t;
+  fa->keeps = keeps;
+  fa->orders = orders;
+  fa->count = count;
+  if (count) *count = 0;
+}
+
+// Record this pass's keep bitmap and order when it ran (ctl[1], the passes
+// run, moved past the count recorded so far) and a record is asked for.
+template <typename T>
+__global__ void k_tape_pass(const FiltArgs<T>* __restrict__ fa, const uint32_t* __restrict__ kbits,
+                            int64_t nwords, int n, const int* __restrict__ ctl) {
+  if (!fa->keeps) return;
+  const int ran = ctl[1];
+  const int have = *fa->count;
+  if (ran <= have) return;
+  uint32_t* dst = fa->keeps + (int64_t)have * nwords;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = kbits[i];
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) fa->orders[have] = n;
+}
+
+template <typename T>
+__global__ void k_tape_commit(const FiltArgs<T>* __restrict__ fa, const int* __restrict__ ctl) {
+  if (fa->keeps && ctl[1] > *fa->count) *fa->count = ctl[1];
 }
 
 // shared memory of k_filter_pass: q on the tile and an NF+1 halo, F_x q,
@@ -507,7 +541,8 @@ template <typename T>
 void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
                           double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
                           int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
-                          void* fargs, GraphSlot* graph, cudaStream_t s) {
+                          void* fargs, GraphSlot* graph, cudaStream_t s, uint32_t* tape_keeps,
+                          int* tape_orders, int* tape_count) {
   const bool twoD = c.ny > 1;
   const int TX = twoD ? 32 : 256, TY = twoD ? 8 : 1;
   const int nt = ((c.nx + TX - 1) / TX) * ((c.ny + TY - 1) / TY);
@@ -538,7 +573,8 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
 #undef HY_FA_N
 #undef HY_FA
   }
-  k_set_filt_args<T><<<1, 1, 0, HY_S(s)>>>(fa, q, qp, (double)k * c.dt);
+  k_set_filt_args<T><<<1, 1, 0, HY_S(s)>>>(fa, q, qp, (double)k * c.dt, tape_keeps, tape_orders,
+                                          tape_count);
   auto body = [&]() {
   cudaMemsetAsync(ctl, 0, 3 * sizeof(int), s);
   for (int o = 0; o < norders; ++o) {
@@ -576,6 +612,10 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
       k_gate_finalize<<<1, 256, 0, HY_S(s)>>>(part, grid, eps_f, ctl);
       k_filter_apply<T><<<cur ? 152 * 8 : grid, 256, 0, HY_S(s)>>>(c, fa, gbuf, kbits, TX, TY, cur,
                                                                    cur_n, nt);
+      if (tape_keeps) {  // recording (direct launches only: not in the captured graph)
+        k_tape_pass<T><<<1, 256, 0, HY_S(s)>>>(fa, kbits, nwords, n, ctl);
+        k_tape_commit<T><<<1, 1, 0, HY_S(s)>>>(fa, ctl);
+      }
       if (pass + 1 < jmax_f) {
         cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
         k_filter_next_tiles<<<(nt + 7) / 8, 256, 0, HY_S(s)>>>(c, kbits, TX, TY, n + 1, nxt,
@@ -589,7 +629,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     }
   }
   };
-  if (graph)
+  if (graph && !tape_keeps)
     run_graphed(graph, s, body);
   else
     body();
@@ -597,9 +637,11 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
 
 template void launch_filter_sparse<float>(const DevCfg&, const int*, int, int, double, float*,
                                           const float*, int64_t, float*, uint32_t*, int*, int*,
-                                          int*, double*, int*, void*, GraphSlot*, cudaStream_t);
+                                          int*, double*, int*, void*, GraphSlot*, cudaStream_t,
+                                          uint32_t*, int*, int*);
 template void launch_filter_sparse<double>(const DevCfg&, const int*, int, int, double, double*,
                                            const double*, int64_t, double*, uint32_t*, int*, int*,
-                                           int*, double*, int*, void*, GraphSlot*, cudaStream_t);
+                                           int*, double*, int*, void*, GraphSlot*, cudaStream_t,
+                                           uint32_t*, int*, int*);
 
 }  // namespace hy

@@ -78,6 +78,24 @@ void run_graphed(GraphSlot* g, cudaStream_t s, F body) {
 template <typename T>
 void launch_rk2(const DevCfg& c, const T* q, T* out, int64_t k, const uint32_t* mask,
                 const int* tiles, const int* ntiles_dev, cudaStream_t s);
+// Reverse-sweep pieces (adjoint.cu), FP64.  box: {i0, i1, j0, j1}.
+void launch_pressure_vjp(const DevCfg& c, const double* q, const int* box, double w, double* lam,
+                         cudaStream_t s);
+void launch_box_pressure(const DevCfg& c, const double* q, const int* box, double w,
+                         double* part, double* total, cudaStream_t s);
+void launch_filter_vjp(const DevCfg& c, const uint32_t* keeps, const int* orders, int npass,
+                       double* lam, double* tmp1, double* tmp2, cudaStream_t s);
+void launch_center_states(const double* states, int64_t N, const int* win, int w, int wp,
+                          const double* psi, double* X, cudaStream_t s);
+void launch_tsdots(const double* A, int na, const double* B, int nb, int64_t N, double* part,
+                   double* out, cudaStream_t s);
+size_t tsdots_part_doubles(int na, int nb);
+void launch_pod_vjp_apply(int64_t N, int m, int wp, int w, const double* L, const double* X,
+                          const double* B1, const double* B2, const int* win,
+                          const double* lpsi_new, double* lam, double* lpsi_cur, cudaStream_t s);
+void launch_mean_vjp(int64_t N, const int* win, int w, const double* lpsi, double* lam,
+                     cudaStream_t s);
+
 // The paper's HDM (muscl.cu): MUSCL-minmod-Roe residual of BDF2 (BDF1 when
 // qp2 is null) on listed cells (null = all; compact SoA output), its exact
 // JVP, the filter's residual measure, and a Newton-GMRES solver with its
@@ -144,12 +162,16 @@ size_t reduced_vjp_work_doubles(int m, int nr);
 // filter.cu
 // fargs: device memory (64 bytes) for the per-call arguments; graph
 // (nullable): the passes kept as one CUDA graph (the other arguments must
-// then be the same on every call)
+// then be the same on every call).  tape_keeps (nullable): record each pass
+// run (keep bitmap of ceil(Nc/32) words, Shapiro n in tape_orders, count in
+// *tape_count); recording calls launch directly, outside the graph.
 template <typename T>
 void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int jmax_f,
                           double eps_f, T* q, const T* qp, int64_t k, T* gbuf, uint32_t* kbits,
                           int* tiles_a, int* tiles_b, int* counts, double* part, int* ctl,
-                          void* fargs, GraphSlot* graph, cudaStream_t s);
+                          void* fargs, GraphSlot* graph, cudaStream_t s,
+                          uint32_t* tape_keeps = nullptr, int* tape_orders = nullptr,
+                          int* tape_count = nullptr);
 
 // rom.cu
 template <typename T>

@@ -151,6 +151,9 @@ def lib():
         "hyrom_init_batch": (st, [C.POINTER(HyromConfig), C.POINTER(vp), i32, i32, i32,
                                   C.POINTER(vp), C.POINTER(vp)]),
         "hyrom_save": (st, [vp, C.c_char_p]),
+        "hyrom_adjoint": (st, [vp, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]),
+        "hyrom_stage_pod_vjp": (st, [vp, vp, i32, vp, vp, i32, vp, vp]),
+        "hyrom_stage_filter_vjp": (st, [vp, vp, vp, i64, vp]),
         "hyrom_load": (st, [vp, C.c_char_p]),
         "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
         "hyrom_batch_threads": (i32, [vp]),
@@ -423,6 +426,24 @@ def hyrom_init_batch(cfgs, q0s, q0_on_host=False, threads=0):
     if s != HYROM_OK:
         raise HyromError(s, "hyrom_init_batch")
     return out.value, [ctxs[i] for i in range(n)]
+
+
+def hyrom_adjoint(ctx, steps, box, dJdq0):
+    """J and dJ/dq0 (into the device array dJdq0) of the time-integrated box
+    pressure over `steps` steps from the context's k = 0; returns J."""
+    b = (C.c_int32 * 4)(*[int(v) for v in box])
+    J = C.c_double()
+    _check(ctx, lib().hyrom_adjoint(ctx, int(steps), b, C.byref(J), _ptr(dJdq0)))
+    return J.value
+
+
+def hyrom_stage_pod_vjp(ctx, window, w, psi, lphi, m, lam_window, lpsi_out):
+    _check(ctx, lib().hyrom_stage_pod_vjp(ctx, _ptr(window), int(w), _ptr(psi), _ptr(lphi),
+                                          int(m), _ptr(lam_window), _ptr(lpsi_out)))
+
+
+def hyrom_stage_filter_vjp(ctx, q, q_prev, k, lam_io):
+    _check(ctx, lib().hyrom_stage_filter_vjp(ctx, _ptr(q), _ptr(q_prev), int(k), _ptr(lam_io)))
 
 
 def hyrom_save(ctx, path):

@@ -10,7 +10,7 @@ import pytest
 
 import workloads as W
 from oracle import hdm, tangent as T
-from tests.gpu_util import H, dev, dev_bits, host, torch
+from tests.gpu_util import Ctx, H, dev, dev_bits, host, rel_err, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -158,3 +158,134 @@ def test_reduced_step_adjoint_matches_the_oracle():
         hy.hyrom_destroy(ctx)
     for got, want in ((got_v, want_v), (got_psi, want_psi), (got_phi, want_phi)):
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def _theta_dirs(n, th0):
+    """dq0/dtheta_i of the vortex initial state by the complex step (the
+    workload's analytic map, no method arithmetic)."""
+    out = []
+    for i in range(len(th0)):
+        th = np.asarray(th0, complex)
+        th[i] += 1e-30j
+        out.append(W.euler_vortex_theta(n, th).imag.reshape(-1) / 1e-30)
+    return out
+
+
+def test_adjoint_sweep_matches_the_oracle_reverse_sweep():
+    """hyrom_adjoint against oracle.adjoint.gradient on the 20^2 vortex
+    (warm-up full steps, rebuilds and hybrid steps): the same J to 1e-12 and
+    dJ/dq0 within 1e-12 of its largest entry; and the eight dJ/dtheta =
+    (dq0/dtheta)^T dJ/dq0 within 1e-12 of the oracle's."""
+    from oracle import adjoint as A
+    n = 20
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=6, m=3, n_p=6, top_frac=0.15, pod_tol=1e-10,
+                    pod_abs=1e-13)
+    th0 = np.array(W.VORTEX_THETA0)
+    box, steps = (6, 14, 6, 14), cfg.w + 5
+    q0 = W.euler_vortex_theta(n, th0)
+    J_o, lam_o = A.gradient(q0, cfg, steps, box)
+    with Ctx(cfg, q0) as (hy, ctx):
+        g = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        J = hy.hyrom_adjoint(ctx, steps, box, g)
+        lam = host(g)
+    lam_o = lam_o.reshape(-1)
+    print(f"J {J:.15e} vs {J_o:.15e}; dJ/dq0 rel err {rel_err(lam, lam_o):.2e}")
+    assert abs(J - J_o) <= 1e-12 * abs(J_o)
+    assert rel_err(lam, lam_o) < 1e-12
+    dirs = _theta_dirs(n, th0)
+    gg = np.array([lam @ d for d in dirs])
+    go = np.array([lam_o @ d for d in dirs])
+    scale = np.maximum(np.abs(go), 1e-3 * abs(J_o))
+    assert np.all(np.abs(gg - go) <= 1e-12 * scale), (gg, go)
+
+
+def test_adjoint_gradient_against_central_differences():
+    """dJ/dtheta from hyrom_adjoint against central differences of the GPU's
+    own J (h = 1e-6 relative, FP64) over the whole method: for each parameter
+    whose +-h runs keep the same sampled sets as the base run, within 1e-6 of
+    max(|dJ/dtheta|, 1e-3 |J|)."""
+    n = 20
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=6, m=3, n_p=6, top_frac=0.15, pod_tol=1e-10,
+                    pod_abs=1e-13)
+    th0 = np.array(W.VORTEX_THETA0)
+    box, steps = (6, 14, 6, 14), cfg.w + 5
+
+    def run(theta):
+        q0 = W.euler_vortex_theta(n, theta)
+        with Ctx(cfg, q0) as (hy, ctx):
+            g = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+            J = hy.hyrom_adjoint(ctx, steps, box, g)
+            nw = (cfg.ncell + 31) // 32
+            bm = torch.zeros(nw, dtype=torch.int32, device="cuda")
+            hy.hyrom_sample(ctx, bitmap_dev=bm)
+            return J, host(g), host(bm).copy()
+    J0, lam0, m0 = run(th0)
+    dirs = _theta_dirs(n, th0)
+    checked = 0
+    for i in range(8):
+        h = 1e-6 * max(1.0, abs(th0[i]))
+        tp, tm = th0.copy(), th0.copy()
+        tp[i] += h
+        tm[i] -= h
+        Jp, _, mp = run(tp)
+        Jm, _, mm = run(tm)
+        if not (np.array_equal(mp, m0) and np.array_equal(mm, m0)):
+            continue
+        fd = (Jp - Jm) / (2 * h)
+        ad = float(lam0 @ dirs[i])
+        scale = max(abs(ad), 1e-3 * abs(J0))
+        print(f"theta_{i}: adjoint {ad:.9e}, central difference {fd:.9e}")
+        assert abs(ad - fd) <= 1e-6 * scale, (i, ad, fd)
+        checked += 1
+    assert checked >= 6
+
+
+def test_pod_vjp_stage_matches_the_oracle():
+    """hyrom_stage_pod_vjp (the thin-SVD adjoint the sweep applies at each
+    rebuild) against oracle.adjoint.pod_vjp on a window of known, distinct
+    spectrum: window and reference-state cotangents within 1e-12."""
+    from oracle import adjoint as A
+    n, w, m = 20, 6, 3
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(nx=n, ny=n, precision=W.PREC_F64, w=w, m=m, n_p=2 * m, pod_tol=1e-10,
+                    pod_abs=1e-13)
+    N = cfg.ndof
+    X, _ = W.random_spectrum_window(N, w, 11, decay=0.6, offset=1.0)
+    g = np.random.Generator(np.random.PCG64(12))
+    psi = 1.0 + 0.1 * g.standard_normal(N)
+    lphi = g.standard_normal((N, m))
+    raw = float(np.sqrt((X * X).sum()))
+    want = A.pod_vjp(X - psi[:, None], lphi, m, cfg.pod_tol, cfg.pod_abs * raw)
+    with Ctx(cfg) as (hy, ctx):
+        lw = torch.zeros(N * w, dtype=torch.float64, device="cuda")
+        lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+        hy.hyrom_stage_pod_vjp(ctx, dev(X.T.copy()), w, dev(psi), dev(lphi.T.copy()), m, lw, lp)
+        got = host(lw).reshape(w, N).T
+        gotp = host(lp)
+    print(f"pod vjp rel err {rel_err(got, want):.2e}")
+    assert rel_err(got, want) < 1e-12
+    assert rel_err(gotp, -want.sum(axis=1)) < 1e-12
+
+
+def test_filter_vjp_stage_matches_the_oracle():
+    """hyrom_stage_filter_vjp against oracle.adjoint.spatial_filter_vjp with
+    the oracle's logged keep masks: the same passes, cotangent within 1e-12."""
+    from oracle import adjoint as A
+    n = 24
+    q0, cfg, _ = W.euler_vortex(n=n, seed=3)
+    cfg = cfg.with_(nx=n, ny=n, precision=W.PREC_F64)
+    qp = q0.reshape(4, n, n)
+    g = np.random.Generator(np.random.PCG64(13))
+    k = 3
+    q = hdm.rk2_step(qp, cfg, k) + 0.01 * g.standard_normal(qp.shape)
+    lam = g.standard_normal(qp.shape)
+    _, keeps, orders = A._filter_logged(q, qp, cfg, k * cfg.dt)
+    want = A.spatial_filter_vjp(lam, orders, keeps, cfg)
+    with Ctx(cfg, q0) as (hy, ctx):
+        io = dev(lam.reshape(-1))
+        hy.hyrom_stage_filter_vjp(ctx, dev(q.reshape(-1)), dev(qp.reshape(-1)), k, io)
+        got = host(io)
+    print(f"filter vjp: {len(orders)} passes, rel err {rel_err(got, want.reshape(-1)):.2e}")
+    assert rel_err(got, want.reshape(-1)) < 1e-12
