@@ -72,7 +72,12 @@ def parse():
     p.add_argument("--implicit-n", type=int, default=512,
                    help="grid of the implicit (paper's HDM) workload")
     p.add_argument("--no-implicit", action="store_true")
+    p.add_argument("--adjoint-n", type=int, default=256, help="grid of the differentiation form")
+    p.add_argument("--adjoint-steps", type=int, default=100)
+    p.add_argument("--adjoint-k", type=int, default=16)
+    p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--micro", choices=["sample_gram", "batch", "full_step", "np_sweep", "implicit",
+                                       "adjoint",
                                        "vortex512", "rk2_vjp"], default=None,
                    help="instead of the step: time one stage on a synthetic input "
                         "(sample_gram: the sample-row normal matrix in each precision)")
@@ -426,6 +431,8 @@ def run_ours(a):
         out["batch_form"] = batch_form(a)
     if rank == 0 and not a.no_implicit:
         out["implicit_form"] = implicit_form(a)
+    if rank == 0 and not a.no_adjoint:
+        out["adjoint_form"] = adjoint_form(a)
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(a)
     if world > 1:
@@ -873,6 +880,59 @@ def implicit_form(a, n=None, steps=14):
     return out
 
 
+def adjoint_form(a, n=None, steps=None, k=None):
+    """The differentiation form: J = time integral over `steps` steps of the
+    pressure over a fixed 64 x 64 box of the vortex-plus-pulse problem with
+    the eight-parameter initial state (euler_vortex_theta), FP64; dJ/dq0 by
+    hyrom_adjoint (the forward run taped, then one reverse sweep) and
+    dJ/dtheta = (dq0/dtheta)^T dJ/dq0 (dq0/dtheta by the complex step of the
+    analytic initial state).  Host-clocked: the plain forward run of the same
+    steps, and the whole gradient call."""
+    import torch
+    from paper_2301_01718_gb300 import hyrom
+    n = n or a.adjoint_n
+    steps = steps or a.adjoint_steps
+    k = k or a.adjoint_k
+    th0 = np.array(W.VORTEX_THETA0)
+    q0 = W.euler_vortex_theta(n, th0)
+    _, cfg, _ = W.euler_vortex(n=n, seed=2)
+    cfg = cfg.with_(precision=W.PREC_F64, w=2 * k, m=k, n_p=2 * k, pod_tol=1e-10, pod_abs=1e-13)
+    b0 = (n - 64) // 2
+    box = (b0, b0 + 64, b0, b0 + 64)
+    q0d = torch.as_tensor(q0.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = hyrom.hyrom_init(cfg, q0d)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            hyrom.hyrom_step(ctx)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    ctx = hyrom.hyrom_init(cfg, q0d)
+    try:
+        g = torch.zeros(cfg.ndof, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = hyrom.hyrom_adjoint(ctx, steps, box, g)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+        lam = g.cpu().numpy()
+    finally:
+        hyrom.hyrom_destroy(ctx)
+    dtheta = []
+    for i in range(8):
+        th = th0.astype(complex)
+        th[i] += 1e-30j
+        dtheta.append(float(lam @ (W.euler_vortex_theta(n, th).imag.reshape(-1) / 1e-30)))
+    return {"workload": f"euler2d_vortex_theta_{n}x{n}_k{k}_w{2 * k}_steps{steps}_box64",
+            "J": J, "dJ_dtheta": dict(zip(W.VORTEX_THETA_NAMES, dtheta)),
+            "forward_s": t_fwd, "gradient_s": t_grad,
+            "gradient_over_forward": t_grad / t_fwd,
+            "tape_bytes": 8 * cfg.ndof * 3 * (steps + 1)}
+
+
 def run_reference(a):
     """The CPU oracle as the reference arm: --warmup untimed and --steps timed
     hybrid steps, each a bounded sample (the cpu_n^2 grid of the same
@@ -904,6 +964,8 @@ def main():
         out = {"micro": "full_step", **full_step(a)}
     elif a.micro == "implicit":
         out = {"micro": "implicit", **implicit_form(a)}
+    elif a.micro == "adjoint":
+        out = {"micro": "adjoint", **adjoint_form(a)}
     elif a.micro == "np_sweep":
         out = {"micro": "np_sweep", **np_sweep(a)}
     elif a.micro == "vortex512":
