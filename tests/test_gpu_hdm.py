@@ -22,9 +22,10 @@ def _cases():
     yield "shock72", q, c
     q, c, _ = W.euler_oblique_shock(n=45, seed=6, k=4)   # ragged, shock and outflow sides
     yield "shock45", q, c
-    # FP32 takes a register-sweep kernel (warp strips of 28 columns x 32
-    # rows): several strips wide and high, ragged in both directions, with
-    # strips that touch no side
+    # FP32 takes a register-sweep kernel (warp strips of 64 columns, 60 of
+    # them written, and rows split so that the strips fill one wave): several
+    # strips wide and high, ragged in both directions, with strips that
+    # touch no side
     q, c, _ = W.euler_oblique_shock(n=300, seed=7, k=4)
     yield "shock300x203", q.reshape(4, 300, 300)[:, :203, :].reshape(4, -1).copy(), \
         c.with_(ny=203)
