@@ -159,8 +159,12 @@ def test_filter_gated_on_bdf2_residual(name, q0, cfg):
     noisy = q + 0.02 * np.abs(q).max(axis=(1, 2), keepdims=True) * g.standard_normal(q.shape)
     k = 6
     t = k * cfg.dt
-    want, passes, _ = filt.spatial_filter(noisy, qp, cfg, t,
-                                          lambda x: M.residual(x, qp, qp2, cfg, t))
+    # the noise makes the pressure negative in a few pre-shock cells of the
+    # oblique shock: their Roe averages have no sound speed, the residual
+    # there is NaN on both sides, and a NaN rho is never kept by the gate
+    with np.errstate(invalid="ignore"):
+        want, passes, _ = filt.spatial_filter(noisy, qp, cfg, t,
+                                              lambda x: M.residual(x, qp, qp2, cfg, t))
     with Ctx(cfg, q0) as (hy, ctx):
         io = dev(noisy.reshape(-1))
         got_passes = hy.hyrom_stage_muscl_filter(ctx, io, dev(qp.reshape(-1)),
