@@ -166,11 +166,11 @@ enum {
   HYROM_T_DEIM = 11,    /* DEIM points, the first m of ODEIM               */
   /* parts of HYROM_T_DEIM / HYROM_T_ODEIM: */
   HYROM_T_OD_INIT = 12,   /* row-norm buckets + first eigensystem          */
-  HYROM_T_OD_PROBE = 13,  /* exact scores of the largest-norm rows         */
-  HYROM_T_OD_SCREEN = 14, /* FP32 bound screen and its probe               */
-  HYROM_T_OD_EXACT = 15,  /* exact scores of the surviving rows            */
+  HYROM_T_OD_PROBE = 13,  /* bounds of the largest-norm rows, one exact   */
+  HYROM_T_OD_SCREEN = 14, /* bounds from z_1, z_2 of the rows still open   */
+  HYROM_T_OD_EXACT = 15,  /* exact scores, tie-aware pick, update setup    */
   HYROM_T_OD_UPDATE = 16, /* rank-one eigensystem update                   */
-  HYROM_T_OD_PICK = 17,   /* tie-aware arg-max and commit                  */
+  HYROM_T_OD_LIST = 17,   /* full FP32 bounds of the rows passed on        */
   HYROM_T_SNORMAL = 18,   /* sample-row normal matrix and its factor       */
   HYROM_NSTAGE = 19
 };

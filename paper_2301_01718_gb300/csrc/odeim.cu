@@ -32,6 +32,10 @@ constexpr int kNB = 256;       // norm buckets
 constexpr int kProbe = 2048;   // rows scored before the bound is applied
 constexpr int kLdw = 65;       // odd leading dimension of W in shared memory
 constexpr int kCompact = 524288;  // leading ordered rows kept row-major (FP32, 64 wide)
+// the step's eigensystem in FP32 for the screens: W^T (64 x 64), then the
+// poles relative to lam_1 (dn, du, dd) and to lam_2 (en, eu, ed), then
+// lam_2 - lam_1 (rounded to nearest, upward, downward)
+constexpr int kW32 = 64 * 64 + 7 * 64;
 
 struct OdCtl {
   unsigned long long smax;  // bits of the best score so far (>= 0)
@@ -41,7 +45,10 @@ struct OdCtl {
   double lam1, lam2, lmax;  // eigenvalues of M (ODEIM)
   int n_list;                // rows passed on by the z_1 filter (ODEIM)
   int eig_sweeps;            // Jacobi sweeps of the first eigensystem (ODEIM)
-  unsigned long long ubest;  // packed (upper bound bits, position) (ODEIM)
+  unsigned long long slo;    // bits of the best certified lower bound (ODEIM)
+  int ncand;                 // candidates listed in the step
+  int n_x;                   // rows listed for exact scores (ODEIM)
+  unsigned ticket;           // CTAs finished in the current pass
   // counters over one ODEIM call: DEIM rows scored, ODEIM rows given the
   // full FP32 bound, ODEIM exact scores, greedy steps
   unsigned long long stat[4];
@@ -60,6 +67,11 @@ void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s) {
   const OdCtl* c = (const OdCtl*)ws;
   cudaMemcpyAsync(out, &c->eig_sweeps, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
+
+// sqrt(x) for x >= 0 from the approximate reciprocal square root: the FP32
+// model steps of the root solvers and screens only steer their iterates
+// (every bound is certified apart, every root finished in FP64)
+HY_DEV float fsqrt_fast(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
 // ---- row norms and buckets --------------------------------------------------
 
@@ -135,12 +147,6 @@ __global__ void k_bucket_scatter(int64_t N, const unsigned char* __restrict__ bk
 
 // ---- DEIM -------------------------------------------------------------------
 
-// DEIM interpolation coefficients c = A_l^{-1} Phi[P, l] with A_l = P^T Phi[:, :l]
-// (rows in pick order).  A_l = L U is kept as a bordered factorisation: the
-// DEIM picks are the partial-pivoting order of A_l, so no pivoting is needed
-// (|L| <= 1 up to the tie tolerance).  Each step costs two triangular solves
-// (one warp, O(l^2)); k_deim_extend then borders L and U with the new point.
-// Lf, Uf: 64 x 64 row-major; y = L^{-1} Phi[P, l] is kept for the border.
 // Rows ord[0 .. C) of Phi copied once per call into a row-major FP32 array
 // R (64 values per row, zero beyond m), so that the per-step scoring passes
 // read each candidate row as 256 contiguous bytes instead of m scattered
@@ -159,234 +165,330 @@ __global__ void k_gather_rows(const T* __restrict__ phi, int64_t N, int m,
   }
 }
 
+// Value a of row i of Phi: from the row copy where the row's ordered
+// position is inside it (it holds the FP32 values exactly), else from Phi.
 template <typename T>
-__global__ void k_deim_solve(const T* __restrict__ phi, int64_t N, int l,
-                             const int* __restrict__ pts, const double* __restrict__ Lf,
-                             const double* __restrict__ Uf, double* __restrict__ yv,
-                             double* __restrict__ cvec, OdCtl* ctl) {
-  pdl_enter();
-  // L and U transposed into shared memory (stride 65: conflict-free), so
-  // that both solves run column by column: after x_i is known every lane
-  // updates its two right-hand-side entries (j = lane, lane + 32).
-  extern __shared__ double dsm[];
-  double* Lt = dsm;            // Lt[i * 65 + j] = L[j][i]
-  double* Ut = dsm + 64 * 65;  // Ut[i * 65 + j] = U[j][i]
-  // all threads stage (8 loads in flight each); warp 0 solves
-  for (int base = threadIdx.x; base < l * l; base += blockDim.x * 8) {
-    double lv[8], uv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int rr = idx / (l > 0 ? l : 1), cc = idx - rr * l;
-      lv[u] = idx < l * l ? Lf[rr * 64 + cc] : 0.0;
-      uv[u] = idx < l * l ? Uf[rr * 64 + cc] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < l * l) {
-        const int rr = idx / l, cc = idx - rr * l;
-        Lt[cc * 65 + rr] = lv[u];
-        Ut[cc * 65 + rr] = uv[u];
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  double b0 = 0.0, b1 = 0.0;  // right-hand side, entries lane and lane + 32
-  if (lane < l) b0 = (double)phi[(int64_t)l * N + pts[lane]];
-  if (lane + 32 < l) b1 = (double)phi[(int64_t)l * N + pts[lane + 32]];
-  __syncwarp();
-  // forward: L y = b (unit diagonal)
-  for (int i = 0; i < l; ++i) {
-    const double yi = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31);
-    const double* col = Lt + i * 65;
-    if (lane > i && lane < l) b0 = fma(-col[lane], yi, b0);
-    if (lane + 32 > i && lane + 32 < l) b1 = fma(-col[lane + 32], yi, b1);
-  }
-  const double y0 = b0, y1 = b1;
-  // backward: U c = y, with the reciprocals of U's diagonal formed up front
-  // (a division on every step of the dependent chain costs ~650 cycles)
-  const double iu0 = lane < l ? 1.0 / Ut[lane * 65 + lane] : 0.0;
-  const double iu1 = lane + 32 < l ? 1.0 / Ut[(lane + 32) * 65 + lane + 32] : 0.0;
-  for (int i = l - 1; i >= 0; --i) {
-    const double ci = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31) *
-                      __shfl_sync(0xffffffffu, i < 32 ? iu0 : iu1, i & 31);
-    if (lane == (i & 31)) {
-      if (i < 32)
-        b0 = ci;
-      else
-        b1 = ci;
-    }
-    const double* col = Ut + i * 65;
-    if (lane < i) b0 = fma(-col[lane], ci, b0);
-    if (lane + 32 < i) b1 = fma(-col[lane + 32], ci, b1);
-  }
-  double cn = 0.0;
-  if (lane < l) {
-    cvec[lane] = b0;
-    yv[lane] = y0;
-    cn = b0 * b0;
-  }
-  if (lane + 32 < l) {
-    cvec[lane + 32] = b1;
-    yv[lane + 32] = y1;
-    cn = fma(b1, b1, cn);
-  }
-  cn = warp_sum(cn);
-  if (lane == 0) {
-    ctl->cn2 = 1.0 + cn;
-    ctl->smax = 0ull;
-    ctl->argmin = 0x7fffffff;
-    ctl->n_c = 0;
-  }
+HY_DEV double phi_at(const T* __restrict__ phi, int64_t N, int a, int i, int pos,
+                     const float* __restrict__ R, int C) {
+  if (sizeof(T) == 4 && pos >= 0 && pos < C) return (double)R[(int64_t)pos * 64 + a];
+  return (double)phi[(int64_t)a * N + i];
 }
 
-// Border the factors with point p_l (ctl->argmin, already committed):
-// U[:l, l] = y, U[l, :l] L-row ell with U^T ell = Phi[p_l, :l], U[l][l] = beta.
-template <typename T>
-__global__ void k_deim_extend(const T* __restrict__ phi, int64_t N, int l, const OdCtl* ctl,
-                              double* __restrict__ Lf, double* __restrict__ Uf,
-                              const double* __restrict__ yv) {
-  pdl_enter();
-  // column-oriented solve of U^T ell = a with U^T's columns = U's rows
-  __shared__ double Us[64 * 64];
-  const int p = ctl->argmin;
-  stage_copy(Us, Uf, l * 64);  // rows 0..l-1 (stride 64)
+// The last non-empty bucket whose largest squared-norm bound reaches tau
+// bounds the ordered rows still to score: every row after it has a smaller
+// bound.  Returns max(that end, probe_end); all threads of the CTA get it.
+HY_DEV int plan_end(const unsigned int* __restrict__ bmax, const int* __restrict__ bstart,
+                    int probe_end, double tau) {
+  __shared__ int red[32];
+  int blast = -1;
+  for (int b = threadIdx.x; b < kNB; b += blockDim.x)
+    if (bstart[b + 1] > bstart[b] && (double)__uint_as_float(bmax[b]) >= tau) blast = b;
+  for (int o = 16; o > 0; o >>= 1) blast = max(blast, __shfl_xor_sync(0xffffffffu, blast, o));
   __syncthreads();
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  double a0 = 0.0, a1 = 0.0;
-  if (lane < l) a0 = (double)phi[(int64_t)lane * N + p];
-  if (lane + 32 < l) a1 = (double)phi[(int64_t)(lane + 32) * N + p];
-  const double pl = (double)phi[(int64_t)l * N + p];
-  __syncwarp();
-  const double iu0 = lane < l ? 1.0 / Us[lane * 64 + lane] : 0.0;
-  const double iu1 = lane + 32 < l ? 1.0 / Us[(lane + 32) * 64 + lane + 32] : 0.0;
-  for (int j = 0; j < l; ++j) {  // ell_j = (a_j - sum_{i<j} U_ij ell_i) / U_jj
-    const double ej = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31) *
-                      __shfl_sync(0xffffffffu, j < 32 ? iu0 : iu1, j & 31);
-    if (lane == (j & 31)) {
-      if (j < 32)
-        a0 = ej;
-      else
-        a1 = ej;
-    }
-    const double* row = Us + j * 64;
-    if (lane > j && lane < l) a0 = fma(-row[lane], ej, a0);
-    if (lane + 32 > j && lane + 32 < l) a1 = fma(-row[lane + 32], ej, a1);
-  }
-  double dot = 0.0;
-  if (lane < l) {
-    Lf[l * 64 + lane] = a0;
-    Uf[lane * 64 + l] = yv[lane];
-    dot = a0 * yv[lane];
-  }
-  if (lane + 32 < l) {
-    Lf[l * 64 + lane + 32] = a1;
-    Uf[(lane + 32) * 64 + l] = yv[lane + 32];
-    dot = fma(a1, yv[lane + 32], dot);
-  }
-  dot = warp_sum(dot);
-  if (lane == 0) {
-    Lf[l * 64 + l] = 1.0;
-    Uf[l * 64 + l] = pl - dot;
-  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = blast;
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) blast = max(blast, red[w]);
+  const int n = blast >= 0 ? bstart[blast + 1] : 0;
+  __syncthreads();
+  return n > probe_end ? n : probe_end;
 }
 
-// exact |r_i| for the ordered rows [p0, p1) (p1 < 0: up to ctl->n_c)
+// Block-wide maximum of unsigned 64-bit keys (integer compares: the FP64
+// compare runs on the narrow FP64 pipe).  All threads get the result.
+HY_DEV unsigned long long block_max_u64(unsigned long long v) {
+  __shared__ unsigned long long sh[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = sh[w] > v ? sh[w] : v;
+  __syncthreads();
+  return v;
+}
+
+HY_DEV unsigned long long block_min_u64(unsigned long long v) {
+  __shared__ unsigned long long sh[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u < v ? u : v;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = sh[w] < v ? sh[w] : v;
+  __syncthreads();
+  return v;
+}
+
+// One pass of a greedy step's scoring, block-synchronous (every thread of
+// the CTA calls it with its score sc, or -1 for none): the best score of the
+// pass raises the step's best ctl->smax, and scores that reach the tie
+// window of the best known to this CTA (its own passes and the global best
+// returned by the atomic) are appended to the candidate list.  The final
+// winner's tie window lies inside every such window, so the list holds every
+// row that can still win (and some that cannot, which the final pick drops).
+// run: this CTA's running best (dbits of a non-negative double).
+HY_DEV void note_scores(double sc, int pos, double tie_tol, unsigned long long& run, OdCtl* ctl,
+                        int* __restrict__ cand) {
+  __shared__ unsigned long long runs;
+  const unsigned long long k = sc > 0.0 ? dbits(sc) : 0ull;
+  const unsigned long long bm = block_max_u64(k);
+  if (threadIdx.x == 0) {
+    unsigned long long r = run > bm ? run : bm;
+    if (bm > run) {
+      const unsigned long long old = atomicMax(&ctl->smax, bm);
+      r = old > r ? old : r;
+    }
+    runs = r;
+  }
+  __syncthreads();
+  run = runs;
+  const bool keep = sc >= 0.0 && sc >= bitsd(run) * (1.0 - tie_tol);
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (bal) {
+    const int lane = threadIdx.x & 31;
+    int first = 0;
+    if (lane == __ffs(bal) - 1) first = atomicAdd(&ctl->ncand, __popc(bal));
+    first = __shfl_sync(0xffffffffu, first, __ffs(bal) - 1);
+    if (keep) cand[first + __popc(bal & ((1u << lane) - 1u))] = pos;
+  }
+  __syncthreads();
+}
+
+// True in the CTA that finishes a grid last (all threads); its reads of what
+// the other CTAs wrote see their writes.
+HY_DEV bool last_block(unsigned* ticket) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// The step's winner: the lowest row index among the candidates whose score
+// reaches the tie window of the step's best, picked and recorded as point
+// l.  Returns (row << 32 | ordered position) to all threads, ~0 if no
+// candidate qualifies (then nothing is recorded).
+HY_DEV unsigned long long pick_winner(const double* __restrict__ scores,
+                                      const int* __restrict__ ord, const int* __restrict__ cand,
+                                      OdCtl* ctl, double tie_tol, int l, int* __restrict__ pts,
+                                      unsigned char* __restrict__ picked) {
+  const double lim = bitsd(*(volatile unsigned long long*)&ctl->smax) * (1.0 - tie_tol);
+  const int nc = *(volatile int*)&ctl->ncand;
+  unsigned long long best = ~0ull;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int pos = cand[k];
+    const double sc = scores[pos];
+    if (sc >= 0.0 && sc >= lim) {
+      const unsigned long long key = ((unsigned long long)(unsigned)ord[pos] << 32) | (unsigned)pos;
+      best = key < best ? key : best;
+    }
+  }
+  best = block_min_u64(best);
+  if (threadIdx.x == 0 && best != ~0ull) {
+    const int p = (int)(best >> 32);
+    pts[l] = p;
+    picked[p] = 1;
+    ctl->argmin = p;
+  }
+  return best;
+}
+
+// DEIM residual |r_i| of column l for ordered position pos (-1: picked),
+// by the four lanes of a quad (lane c = threadIdx.x % 4 sums the terms
+// j = c mod 4; an FP64 instruction holds its SM sub-partition for 64 cycles
+// whatever the number of active lanes, so the row's terms are spread over
+// lanes, and rows over more warps).  All four lanes return the score.
 template <typename T>
-__global__ void k_deim_score(const T* __restrict__ phi, int64_t N, int l,
-                             const double* __restrict__ cvec, const int* __restrict__ ord,
-                             const unsigned char* __restrict__ picked, int p0, int p1,
-                             OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R,
-                             int C) {
+HY_DEV double deim_score(const T* __restrict__ phi, int64_t N, int l, const double* cs,
+                         const int* __restrict__ ord, const unsigned char* __restrict__ picked,
+                         int pos, const float* __restrict__ R, int C) {
+  const int c = threadIdx.x & 3;
+  const int i = ord[pos];
+  const bool row = sizeof(T) == 4 && pos < C;  // the copy holds the FP32 values exactly
+  const float* rr = R + (int64_t)(row ? pos : 0) * 64;
+  auto x = [&](int j) { return row ? (double)rr[j] : (double)phi[(int64_t)j * N + i]; };
+  double sc = 0.0;
+  for (int j = c; j < l; j += 4) sc = fma(x(j), cs[j], sc);
+  sc = sc + __shfl_xor_sync(0xffffffffu, sc, 1);  // (s0 + s1), (s2 + s3)
+  sc = sc + __shfl_xor_sync(0xffffffffu, sc, 2);
+  return picked[i] ? -1.0 : fabs(x(l) - sc);
+}
+
+// DEIM step l, pass 1: exact |r_i| of the probe rows (the largest-norm
+// ordered rows [0, probe), a quad of lanes per row, 16 rows per CTA of 64
+// threads so that they spread over the SMs); the CTA that finishes last sets the rows still
+// to score: |r_i| <= |phi_i| sqrt(1 + |c|^2), so only rows with
+// |phi_i|^2 >= lim^2 / (1 + |c|^2) can reach the tie window of the best.
+template <typename T>
+__global__ void __launch_bounds__(256) k_deim_probe(
+    const T* __restrict__ phi, int64_t N, int l, const double* __restrict__ cvec,
+    const int* __restrict__ ord, const unsigned char* __restrict__ picked, int probe,
+    const unsigned int* __restrict__ bmax, const int* __restrict__ bstart, double tie_tol,
+    OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, const float* __restrict__ R,
+    int C) {
   pdl_enter();
   __shared__ double cs[64];
   for (int j = threadIdx.x; j < l; j += blockDim.x) cs[j] = cvec[j];
   __syncthreads();
-  const int end = p1 >= 0 ? p1 : ctl->n_c;
-  double best = 0.0;
-  for (int pos = p0 + blockIdx.x * blockDim.x + threadIdx.x; pos < end;
-       pos += gridDim.x * blockDim.x) {
-    const int i = ord[pos];
+  unsigned long long run = 0ull;
+  const int rows = blockDim.x >> 2;  // one quad per row
+  for (int base = blockIdx.x * rows; base < probe; base += gridDim.x * rows) {
+    const int pos = base + (threadIdx.x >> 2);
+    // every lane takes part in the quad's shuffles (rows past the end
+    // score row `base` again and drop it)
+    const bool valid = pos < probe;
+    const double s0 = deim_score<T>(phi, N, l, cs, ord, picked, valid ? pos : base, R, C);
     double sc = -1.0;
-    if (!picked[i]) {
-      double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains
-      if (sizeof(T) == 4 && pos < C) {  // the copy holds the FP32 values exactly
-        const float* rr = R + (int64_t)pos * 64;
-        for (int j = 0; j < l; ++j) s4[j & 3] = fma((double)rr[j], cs[j], s4[j & 3]);
-        sc = fabs((double)rr[l] - ((s4[0] + s4[1]) + (s4[2] + s4[3])));
-      } else {
-        for (int j = 0; j < l; ++j)
-          s4[j & 3] = fma((double)phi[(int64_t)j * N + i], cs[j], s4[j & 3]);
-        sc = fabs((double)phi[(int64_t)l * N + i] - ((s4[0] + s4[1]) + (s4[2] + s4[3])));
-      }
-      best = sc > best ? sc : best;
+    if (valid && (threadIdx.x & 3) == 0) {
+      sc = s0;
+      scores[pos] = sc;
     }
-    scores[pos] = sc;
+    note_scores(sc, pos, tie_tol, run, ctl, cand);
   }
-  best = block_max(best);
-  if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(best));
-}
-
-// one thread per bucket: the last non-empty bucket whose largest squared
-// norm reaches tau bounds the rows still to score
-__device__ void plan_rows(OdCtl* ctl, const unsigned int* __restrict__ bmax,
-                          const int* __restrict__ bstart, int probe_end, double tau) {
-  int blast = -1;
-  for (int b = threadIdx.x; b < kNB; b += blockDim.x)
-    if (bstart[b + 1] > bstart[b] && (double)__uint_as_float(bmax[b]) >= tau) blast = b;
-  __shared__ int red[32];
-  for (int o = 16; o > 0; o >>= 1) blast = max(blast, __shfl_xor_sync(0xffffffffu, blast, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = blast;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) blast = max(blast, red[w]);
-    blast = max(blast, red[0]);
-    const int n = blast >= 0 ? bstart[blast + 1] : 0;
-    ctl->n_c = n > probe_end ? n : probe_end;
-  }
-}
-
-// DEIM: |r_i| <= |phi_i| sqrt(1 + |c|^2), so rows need |phi_i|^2 >= lim^2 / cn2
-__global__ void k_deim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
-                            const int* __restrict__ bstart, int probe_end, double tie_tol) {
-  pdl_enter();
-  const double s = bitsd(ctl->smax);
+  if (!last_block(&ctl->ticket)) return;
+  const double s = bitsd(*(volatile unsigned long long*)&ctl->smax);
   const double lim = s * (1.0 - 2.0 * tie_tol);
-  plan_rows(ctl, bmax, bstart, probe_end, lim * lim / (ctl->cn2 * (1.0 + 1e-5)));
-  if (threadIdx.x == 0) ctl->stat[0] += (unsigned long long)(ctl->n_c - probe_end);
+  const double cn2 = l == 0 ? 1.0 : ctl->cn2;
+  const int n = plan_end(bmax, bstart, probe, lim * lim / (cn2 * (1.0 + 1e-5)));
+  if (threadIdx.x == 0) {
+    ctl->n_c = n;
+    ctl->ticket = 0u;
+    ctl->stat[0] += (unsigned long long)(n - probe);
+  }
 }
 
-// lowest row among the scored rows within the tie window of the best
-__global__ void k_argmin_tie(const double* __restrict__ scores, const int* __restrict__ ord,
-                             OdCtl* ctl, double tie_tol) {
-  pdl_enter();
-  const double lim = bitsd(ctl->smax) * (1.0 - tie_tol);
-  const int end = ctl->n_c;
-  int best = 0x7fffffff;
-  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < end;
-       pos += gridDim.x * blockDim.x) {
-    const double sc = scores[pos];
-    if (sc >= 0.0 && sc >= lim) {
-      const int i = ord[pos];
-      best = i < best ? i : best;
+// DEIM step l, pass 2: the rows [probe, n_c); the CTA that finishes last
+// picks point l and, for l + 1 < m, borders the factors with it and forms
+// the coefficients of step l + 1.
+//
+// With A_l = P^T Phi[:, :l] = L U (rows in pick order; the DEIM picks are
+// the partial-pivoting order of A_l, so no pivoting is needed) the CTA keeps
+// the inverses Li = L^{-1} and Ui = U^{-1} (64 x 64 row-major):
+//   step coefficients   y = Li b, c = Ui y      (b = Phi[P, l])
+//   new point p         ell = Ui^T a (a = Phi[p, :l]), beta = Phi[p, l] - ell . y,
+//                       Li row l = [-ell^T Li, 1], Ui column l = [-c / beta; 1 / beta]
+// (Ui y = c).  Each product is a 64 x 64 matrix-vector product spread over
+// the CTA's eight warps, in place of the dependent chains of forward and
+// back substitution (an FP64 instruction holds its SM sub-partition for 64
+// cycles, so those chains cost more than all the scoring).
+HY_DEV void matvec_part(const double* __restrict__ A, bool trans, const double* x, int k0, int k1,
+                        int n, double (*part)[64]) {
+  // part[h][r] = sum over k in the h-th quarter of [k0, k1) of A(r, k) x_k
+  // (A(r, k) = A[r * 64 + k], or A[k * 64 + r] when trans), r < n
+  const int r = threadIdx.x & 63, h = threadIdx.x >> 6;
+  const int len = (k1 - k0 + 3) / 4, a0 = k0 + h * len, a1 = a0 + len < k1 ? a0 + len : k1;
+  double p0 = 0.0, p1 = 0.0;
+  if (r < n) {
+    int k = a0;
+    for (; k + 1 < a1; k += 2) {
+      p0 = fma(trans ? A[k * 64 + r] : A[r * 64 + k], x[k], p0);
+      p1 = fma(trans ? A[(k + 1) * 64 + r] : A[r * 64 + k + 1], x[k + 1], p1);
     }
+    if (k < a1) p0 = fma(trans ? A[k * 64 + r] : A[r * 64 + k], x[k], p0);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const int u = __shfl_xor_sync(0xffffffffu, best, o);
-    best = u < best ? u : best;
-  }
-  if ((threadIdx.x & 31) == 0 && best != 0x7fffffff) atomicMin(&ctl->argmin, best);
+  part[h][r] = p0 + p1;
 }
 
-__global__ void k_commit(OdCtl* ctl, int l, int* __restrict__ pts, unsigned char* picked) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_deim_rest(
+    const T* __restrict__ phi, int64_t N, int l, int m, const double* __restrict__ cvec_in,
+    const int* __restrict__ ord, unsigned char* __restrict__ picked, int probe, double tie_tol,
+    OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, const float* __restrict__ R,
+    int C, int* __restrict__ pts, double* __restrict__ Li, double* __restrict__ Ui,
+    double* __restrict__ yv, double* __restrict__ cvec) {
   pdl_enter();
-  const int p = ctl->argmin;
-  pts[l] = p;
-  picked[p] = 1;
+  __shared__ double cs[64];
+  for (int j = threadIdx.x; j < l; j += blockDim.x) cs[j] = cvec_in[j];
+  __syncthreads();
+  const int end = ctl->n_c;
+  unsigned long long run = ctl->smax;
+  const int rows = blockDim.x >> 2;  // one quad per row
+  for (int base = probe + blockIdx.x * rows; base < end; base += gridDim.x * rows) {
+    const int pos = base + (threadIdx.x >> 2);
+    // every lane takes part in the quad's shuffles (rows past the end
+    // score row `base` again and drop it)
+    const bool valid = pos < end;
+    const double s0 = deim_score<T>(phi, N, l, cs, ord, picked, valid ? pos : base, R, C);
+    double sc = -1.0;
+    if (valid && (threadIdx.x & 3) == 0) {
+      sc = s0;
+      scores[pos] = sc;
+    }
+    note_scores(sc, pos, tie_tol, run, ctl, cand);
+  }
+  if (!last_block(&ctl->ticket)) return;
+  // ---- the pick, then the factors of step l + 1 (this CTA alone) ----
+  const int tid = threadIdx.x;
+  const unsigned long long key = pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked);
+  const int p = (int)(key >> 32), wpos = (int)(key & 0xffffffffull);
+  __shared__ double a[64], ell[64], y[64], b[64], c[64];
+  __shared__ double part[4][64];
+  __shared__ double beta_s;
+  if (l + 1 < m && key != ~0ull) {
+    // a = Phi[p, :l], its entry l, y and c of step l
+    if (tid <= l) a[tid] = phi_at<T>(phi, N, tid, p, wpos, R, C);
+    if (tid < l) {
+      y[tid] = yv[tid];
+      c[tid] = cvec_in[tid];
+    }
+    __syncthreads();
+    // ell = Ui^T a: ell_k = sum_{r <= k} Ui[r][k] a_r
+    matvec_part(Ui, true, a, 0, l, l, part);
+    __syncthreads();
+    if (tid < l) ell[tid] = (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+    __syncthreads();
+    double dot = tid < l ? ell[tid] * y[tid] : 0.0;
+    dot = block_sum(dot);
+    if (tid == 0) beta_s = a[l] - dot;
+    // Li row l = -ell^T Li (Li lower triangular)
+    matvec_part(Li, true, ell, 0, l, l, part);
+    __syncthreads();
+    const double beta = beta_s;
+    const double ib = 1.0 / beta;
+    if (tid < l) {
+      Li[l * 64 + tid] = -((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]));
+      Ui[tid * 64 + l] = -c[tid] * ib;
+    }
+    if (tid == 0) {
+      Li[l * 64 + l] = 1.0;
+      Ui[l * 64 + l] = ib;
+    }
+    // step l + 1: b = Phi[P, l + 1] over the l + 1 points
+    const int k = l + 1;
+    if (tid < k) b[tid] = (double)phi[(int64_t)k * N + pts[tid]];
+    __syncthreads();
+    // y = Li b (rows r < k; Li lower triangular, zero beyond the diagonal)
+    matvec_part(Li, false, b, 0, k, k, part);
+    __syncthreads();
+    if (tid < k) y[tid] = (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+    __syncthreads();
+    // c = Ui y
+    matvec_part(Ui, false, y, 0, k, k, part);
+    __syncthreads();
+    double cn = 0.0;
+    if (tid < k) {
+      const double ci = (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+      cvec[tid] = ci;
+      yv[tid] = y[tid];
+      cn = ci * ci;
+    }
+    cn = block_sum(cn);
+    if (tid == 0) ctl->cn2 = 1.0 + cn;
+  }
+  if (tid == 0) {
+    ctl->smax = 0ull;
+    ctl->ncand = 0;
+    ctl->ticket = 0u;
+    ctl->n_c = 0;
+  }
 }
 
 // ---- ODEIM oversampling -----------------------------------------------------
@@ -429,9 +531,11 @@ __global__ void __launch_bounds__(256) k_odeim_gram(const T* __restrict__ phi, i
 // sort the Jacobi eigenpairs ascending: lam_s, W_s (m x m column-major);
 // reset the step's control block
 // The screens read the eigensystem in FP32, written once per step where it
-// changes: wt32[a * 64 + j] = W_ja (zero for j >= m), then dn[64] and du[64]
-// at wt32 + 4096: d_j = lam_j - lam_1 (sorted) rounded to nearest and upward
-// for 1 <= j < m, +inf otherwise (slot 0 carries z_1 itself).  One CTA.
+// changes: wt32[a * 64 + j] = W_ja (zero for j >= m), then dn[64], du[64]
+// and dd[64] at wt32 + 4096: d_j = lam_j - lam_1 (sorted) rounded to
+// nearest, upward and downward for 1 <= j < m, +inf otherwise (slot 0
+// carries z_1 itself); en, eu, ed: e_j = lam_j - lam_2 likewise for j < m
+// (+inf beyond; e_1 < 0, e_2 = 0); d2[3]: lam_2 - lam_1.  One CTA.
 HY_DEV void w32_tail(const double* __restrict__ lam_sorted, int m, float* __restrict__ wt32) {
   for (int idx = threadIdx.x; idx < m * (64 - m); idx += blockDim.x) {
     const int a = idx / (64 - m), j = m + idx % (64 - m);
@@ -439,15 +543,37 @@ HY_DEV void w32_tail(const double* __restrict__ lam_sorted, int m, float* __rest
   }
   float* dn = wt32 + 64 * 64;
   float* du = dn + 64;
+  float* dd = du + 64;
+  float* en = dd + 64;
+  float* eu = en + 64;
+  float* ed = eu + 64;
+  float* d2 = ed + 64;
   const double l1 = lam_sorted[0];
+  const double l2 = m > 1 ? lam_sorted[1] : 0.0;
   for (int j = threadIdx.x; j < 64; j += blockDim.x) {
     if (j >= 1 && j < m) {
       dn[j] = (float)(lam_sorted[j] - l1);
       du[j] = __double2float_ru(__dsub_ru(lam_sorted[j], l1));
+      dd[j] = __double2float_rd(__dsub_rd(lam_sorted[j], l1));
     } else {
       dn[j] = INFINITY;
       du[j] = INFINITY;
+      dd[j] = INFINITY;
     }
+    if (m > 1 && j < m) {
+      en[j] = (float)(lam_sorted[j] - l2);
+      eu[j] = __double2float_ru(__dsub_ru(lam_sorted[j], l2));
+      ed[j] = __double2float_rd(__dsub_rd(lam_sorted[j], l2));
+    } else {
+      en[j] = INFINITY;
+      eu[j] = INFINITY;
+      ed[j] = INFINITY;
+    }
+  }
+  if (threadIdx.x == 0) {
+    d2[0] = m > 1 ? (float)(l2 - l1) : INFINITY;
+    d2[1] = m > 1 ? __double2float_ru(__dsub_ru(l2, l1)) : INFINITY;
+    d2[2] = m > 1 ? __double2float_rd(__dsub_rd(l2, l1)) : INFINITY;
   }
 }
 
@@ -470,8 +596,11 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
     ctl->lam2 = m > 1 ? lam[perm[1]] : INFINITY;
     ctl->lmax = lam[perm[m - 1]];
     ctl->smax = 0ull;
+    ctl->slo = 0ull;
     ctl->n_list = 0;
-    ctl->ubest = 0ull;
+    ctl->n_x = 0;
+    ctl->ncand = 0;
+    ctl->ticket = 0u;
     ctl->argmin = 0x7fffffff;
     ctl->n_c = 0;
   }
@@ -485,112 +614,166 @@ __global__ void k_odeim_sort(const double* __restrict__ lam, const double* __res
   w32_tail(lam_s, m, wt32);
 }
 
-// Smallest root of 1 + sum_j z_j^2 / (lam_j - mu) (lam ascending): with
-// mu = l1 + tau and d_j = lam_j - l1 it is the root in (0, min(d_2, |z|^2)] of
-//   h(tau) = tau (1 + g(tau)) - z_1^2,   g(tau) = sum_{j>=2} z_j^2 / (d_j - tau),
-// which is increasing and has no pole at tau = 0 (the secular equation
-// multiplied by tau).  Each step solves the two-pole model of the secular
-// equation: the pole at 0 exactly, and g replaced by a + b / (d_2 - tau)
-// with a and b matching g and g' at the current iterate (the "middle way"
-// of Li's secular-equation solver, as in LAPACK's dlaed4); the model's
-// smaller root is
-//   tau' = 2 z_1^2 d_2 / (B + sqrt(B^2 - 4 C z_1^2 d_2)),
-//   C = 1 + a,  B = C d_2 + z_1^2 + b.
-// These steps run in FP32 (an FP64 divide or square root costs ~650
-// cycles on this GPU, an FP32 reciprocal ~85), from tau = 0 until the step is
-// at FP32 rounding; FP64 Newton steps on h then finish inside a shrinking
-// bracket (bisection otherwise).  Stop when |h| is within the rounding error
-// of its evaluation, the step is below 2 ulp, or the bracket has collapsed.  One warp; z in shared
-// memory (lane j takes z_j and z_{j+32}).
+// Smallest root mu of the secular equation
+//   f(mu) = 1 + sum_j z_j^2 / (lam_j - mu)   (lam ascending, m <= 64),
+// i.e. lambda_min(diag(lam) + z z^T), one warp (lane: terms j = lane and
+// lane + 32; z and lam in shared memory).  The root lies in (lam_1, lam_2).
+// It is found in coordinates shifted to the nearer of the two poles (the
+// sign of f at their midpoint tells which), mu = lam_o + t, so that both
+// t and every lam_j - mu keep full relative accuracy; the steps solve the
+// two-pole model of f ("middle way" of Li's secular-equation solver, as in
+// LAPACK's dlaed4): with psi the term of pole 1 and phi the others,
+//   f ~ c + s / (del_1 - t') + S / (del_2 - t'),
+//   s = psi' (del_1 - t)^2, S = phi' (del_2 - t)^2,
+//   c = f - psi' (del_1 - t) - phi' (del_2 - t),
+// a quadratic whose root in the interval is taken; steps stay inside a
+// shrinking bracket (bisection otherwise).  FP32 steps first (an FP64
+// instruction holds its SM sub-partition for 64 cycles), then FP64 steps
+// until |f| is within the rounding error of its evaluation, the step is
+// below 2 ulp, or the bracket has collapsed.  The greedy's best rows lift
+// lambda_min to just below lam_2, where a root in unshifted coordinates
+// took about seven FP64 steps (the poles' differences lost their digits);
+// shifted, it takes two.  Special cases: m = 1 (mu = lam_1 + z_1^2), and
+// z_1 = 0 or lam_1 = lam_2 (mu = lam_1: no eigenvalue falls below it).
 __device__ double secular_root_warp(const double* __restrict__ z, const double* __restrict__ lam,
                                     int m, double l1, double l2) {
   const int lane = threadIdx.x & 31;
-  const int j0 = lane, j1 = lane + 32;
-  const double z0 = j0 < m ? z[j0] : 0.0, z1 = j1 < m ? z[j1] : 0.0;
-  const double q0 = z0 * z0, q1 = z1 * z1;
-  const double zz = warp_sum(q0 + q1);
-  const double zf = __shfl_sync(0xffffffffu, q0, 0);  // z_1^2
+  double dv[2], z2[2];
+  for (int u = 0; u < 2; ++u) {
+    const int i = lane + 32 * u;
+    dv[u] = i < m ? lam[i] : 0.0;
+    const double zi = i < m ? z[i] : 0.0;
+    z2[u] = zi * zi;
+  }
+  const double zf = __shfl_sync(0xffffffffu, z2[0], 0);  // z_1^2
   if (m == 1) return l1 + zf;
-  // shifted poles of the other terms (lane 0's first slot is the pole itself)
-  const double d0 = lam[j0 < m ? j0 : 0] - l1, d1 = j1 < m ? lam[j1] - l1 : 0.0;
-  const double w0 = (j0 >= 1 && j0 < m) ? q0 : 0.0, w1 = j1 < m ? q1 : 0.0;
-  const double d2 = l2 - l1;
-  double hi = fmin(d2, zz), lo = 0.0;
-  if (!(hi > 0.0) || zf == 0.0) return l1;  // z_1 = 0 or a double eigenvalue
+  if (zf == 0.0 || !(l2 > l1)) return l1;
+  const double mid = 0.5 * (l1 + l2);
+  double f = 0.0;
+  for (int u = 0; u < 2; ++u)
+    if (lane + 32 * u < m) f = f + z2[u] / (dv[u] - mid);
+  f = 1.0 + warp_sum(f);
+  const bool left = f >= 0.0;  // the root lies in (lam_1, mid]
+  const double dorg = left ? l1 : l2;
+  double lo = left ? 0.0 : mid - l2, hi = left ? mid - l1 : 0.0;
+  double del[2];
+  for (int u = 0; u < 2; ++u) del[u] = dv[u] - dorg;
+  const double delj = l1 - dorg, deln = l2 - dorg;
+  double t = left ? 0.5 * hi : 0.5 * lo;
   const double eps = 2.220446049250313e-16;
-  // FP32 two-pole model steps (cheap) to a starting point for FP64 Newton
-  double tau;
-  {
-    const float fd0 = (float)d0, fd1 = (float)d1, fw0 = (float)w0, fw1 = (float)w1;
-    const float fzf = (float)zf, fd2 = (float)d2;
-    float t = 0.f, flo = 0.f, fhi = (float)hi;
-    for (int it = 0; it < 12; ++it) {
-      float g = 0.f, dg = 0.f;
-      if (fw0 > 0.f) {
-        const float r = __frcp_rn(fd0 - t);
-        g = fw0 * r;
-        dg = g * r;
+  {  // FP32 model steps to a start for the FP64 ones, which keep their own bracket
+    const float fe = 1.1920929e-7f;
+    float fdel[2], fz2[2];
+    for (int u = 0; u < 2; ++u) {
+      fdel[u] = (float)del[u];
+      fz2[u] = (float)z2[u];
+    }
+    const float fdelj = (float)delj, fdeln = (float)deln;
+    float ft = (float)t, flo = (float)lo, fhi = (float)hi;
+    for (int it = 0; it < 16; ++it) {
+      float ff = 0.f, fa = 0.f, dps = 0.f, dph = 0.f;
+      for (int u = 0; u < 2; ++u) {
+        const int i = lane + 32 * u;
+        if (i < m) {
+          const float r = __frcp_rn(fdel[u] - ft);
+          const float q = fz2[u] * r;
+          ff += q;
+          fa += fabsf(q);
+          if (i == 0)
+            dps = fmaf(q, r, dps);
+          else
+            dph = fmaf(q, r, dph);
+        }
       }
-      if (fw1 > 0.f) {
-        const float r = __frcp_rn(fd1 - t);
-        const float q = fw1 * r;
-        g += q;
-        dg = fmaf(q, r, dg);
+      ff = 1.f + warp_sum(ff);
+      fa = warp_sum(fa);
+      dps = warp_sum(dps);
+      dph = warp_sum(dph);
+      if (fabsf(ff) <= 8.f * fe * (1.f + fa + fabsf(ft) * (dps + dph))) break;
+      if (ff < 0.f)
+        flo = ft;
+      else
+        fhi = ft;
+      if (fhi - flo <= 2.f * fe * fmaxf(fabsf(fhi), fabsf(flo))) {
+        ft = 0.5f * (flo + fhi);
+        break;
       }
-      g = warp_sum(g);
-      dg = warp_sum(dg);
-      if (it > 0) {
-        const float h = fmaf(t, 1.f + g, -fzf);
-        if (h < 0.f)
-          flo = t;
+      const float Dj = fdelj - ft, Dn = fdeln - ft;
+      const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+      const float A = ff - dps * Dj - dph * Dn;
+      const float B = A * (Dj + Dn) + sL + sR;
+      const float Cq = ff * Dj * Dn;
+      float eta = NAN;
+      if (A == 0.f) {
+        if (B != 0.f) eta = __fdividef(Cq, B);
+      } else {
+        const float qq = 0.5f * (B + copysignf(fsqrt_fast(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
+        const float e1 = __fdividef(qq, A), e2 = qq != 0.f ? __fdividef(Cq, qq) : NAN;
+        if (e1 > Dj && e1 < Dn) eta = e1;
+        if (e2 > Dj && e2 < Dn) eta = e2;
+      }
+      float nt = ft + eta;
+      if (fabsf(nt - ft) <= 2.f * fe * fabsf(ft)) {
+        ft = nt;
+        break;
+      }
+      if (!(nt > flo && nt < fhi)) nt = 0.5f * (flo + fhi);
+      ft = nt;
+    }
+    const double tc = (double)ft;
+    if (tc > lo && tc < hi) t = tc;
+  }
+  for (int it = 0; it < 100; ++it) {
+    double ff = 0.0, fa = 0.0, dps = 0.0, dph = 0.0;
+    for (int u = 0; u < 2; ++u) {
+      const int i = lane + 32 * u;
+      if (i < m) {
+        const double r = 1.0 / (del[u] - t);
+        const double q = z2[u] * r;
+        ff = ff + q;
+        fa = fa + fabs(q);
+        if (i == 0)
+          dps = dps + q * r;
         else
-          fhi = t;
+          dph = dph + q * r;
       }
-      const float gap = fd2 - t;
-      const float C = 1.f + (g - dg * gap);
-      const float B = C * fd2 + fzf + dg * gap * gap;
-      const float nt = 2.f * fzf * fd2 / (B + sqrtf(fmaxf(B * B - 4.f * C * fzf * fd2, 0.f)));
-      const bool done = it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t;
-      t = (nt > flo && nt < fhi) ? nt : 0.5f * (flo + fhi);
-      if (done) break;
     }
-    tau = (double)t;
-    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
-  }
-  // FP64 Newton steps on h inside the bracket
-  for (int itr = 0; itr < 60; ++itr) {
-    double g = 0.0, dg = 0.0;
-    if (w0 > 0.0) {
-      const double r = rcp64(d0 - tau);
-      g = w0 * r;
-      dg = g * r;
-    }
-    if (w1 > 0.0) {
-      const double r = rcp64(d1 - tau);
-      const double q = w1 * r;
-      g = g + q;
-      dg = fma(q, r, dg);
-    }
-    g = warp_sum(g);
-    dg = warp_sum(dg);
-    const double h = tau * (1.0 + g) - zf;
-    if (fabs(h) <= 16.0 * eps * (tau * (1.0 + g) + zf)) break;
-    if (h < 0.0)
-      lo = tau;
+    ff = 1.0 + warp_sum(ff);
+    fa = warp_sum(fa);
+    dps = warp_sum(dps);
+    dph = warp_sum(dph);
+    if (fabs(ff) <= 8.0 * eps * (1.0 + fa + fabs(t) * (dps + dph))) break;
+    if (ff < 0.0)
+      lo = t;
     else
-      hi = tau;
-    if (hi - lo <= 2.0 * eps * hi) {
-      tau = hi;
+      hi = t;
+    if (hi - lo <= 2.0 * eps * fmax(fabs(hi), fabs(lo))) {
+      t = 0.5 * (lo + hi);
       break;
     }
-    const double nt = tau - h / fma(tau, dg, 1.0 + g);
-    if (fabs(nt - tau) <= 2.0 * eps * tau) {
-      tau = nt;
+    const double Dj = delj - t, Dn = deln - t;
+    const double sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+    const double A = ff - dps * Dj - dph * Dn;
+    const double B = A * (Dj + Dn) + sL + sR;
+    const double Cq = ff * Dj * Dn;
+    double eta = NAN;  // A eta^2 - B eta + Cq = 0: the root in (Dj, Dn)
+    if (A == 0.0) {
+      if (B != 0.0) eta = Cq / B;
+    } else {
+      const double q = 0.5 * (B + copysign(sqrt(fmax(B * B - 4.0 * A * Cq, 0.0)), B));
+      const double e1 = q / A, e2 = q != 0.0 ? Cq / q : NAN;
+      if (e1 > Dj && e1 < Dn) eta = e1;
+      if (e2 > Dj && e2 < Dn) eta = e2;
+    }
+    double nt = t + eta;
+    if (fabs(nt - t) <= 2.0 * eps * fabs(t)) {  // before the bracket test: a
+      t = nt;                                    // converged step may sit on it
       break;
     }
-    tau = (nt > lo && nt < hi) ? nt : 0.5 * (lo + hi);
+    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+    t = nt;
   }
-  return l1 + tau;
+  return dorg + t;
 }
 
 // z = W^T rb for the m x m eigenvector block W (column j at W + j ldw) by the
@@ -635,193 +818,266 @@ HY_DEV void z_block(const double* W, int ldw, const double* rb, int m, double* z
 // the rounding of the stored norm), so with b1 = |z~_1| + dl and
 // a_j = max(|z~_j| - dl, 0) the function
 //   h_L(t) = t (1 + sum_{j>=2} a_j^2 / (d_j - t)) - b1^2  <=  h(t),
-// and h_L(t) >= 0 proves tau <= t.  Every bound below is evaluated with
-// directed rounding, so it stays an upper bound of the exact score.
+// and h_L(t) >= 0 proves tau <= t: an upper bound U of the exact score.
+// Symmetrically, with B1 = max(|z~_1| - dl, 0), A_j = |z~_j| + dl and the
+// poles rounded down,
+//   h_U(t) = t (1 + sum_{j>=2} A_j^2 / (d_j - t)) - B1^2  >=  h(t),
+// and h_U(t) <= 0 proves tau >= t: a lower bound L.  Every bound is
+// evaluated with directed rounding.  The largest L found raises the step's
+// pruning limit before any exact score is known.
+//
+// A step's rows are taken in three passes: the probe rows (the largest
+// norms) get both bounds, and the exact score of the row with the best U;
+// the rows whose norm can still reach the limit get the bound from z_1
+// alone, and those it does not exclude both full bounds; the rows whose U
+// reaches the limit get the exact score.  The last pass also picks the point
+// and prepares the eigensystem update.
 
-// Stage 1, one thread per ordered row in [p0, ctl->n_c): the bound
-// U1 = min(l1 + b1^2, l2) from z_1 alone (one m-term dot product).  Rows
-// with U1 >= lim = smax (1 - 2 tie) are appended to `list` for stage 2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_z1(
-    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ W_s,
-    const float* __restrict__ nrm, const int* __restrict__ ord,
-    const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
-    double* __restrict__ scores, int* __restrict__ list, const float* __restrict__ R, int C) {
-  pdl_enter();
-  __shared__ float w1[64];
-  for (int a = threadIdx.x; a < 64; a += blockDim.x) w1[a] = a < m ? (float)W_s[a] : 0.f;
-  __syncthreads();
-  const double l1 = ctl->lam1, l2 = ctl->lam2;
-  const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  const int end = ctl->n_c;
-  const int lane = threadIdx.x & 31;
-  for (int base = p0 + blockIdx.x * blockDim.x; base < end; base += gridDim.x * blockDim.x) {
-    const int pos = base + threadIdx.x;
-    bool pass = false;
-    if (pos < end) {
-      const int i = ord[pos];
-      double U = -1.0;
-      if (!picked[i]) {
-        float z1 = 0.f;
-        if (pos < C) {  // contiguous copy (zero beyond m: same sum)
-          const float4* rp = reinterpret_cast<const float4*>(R + (int64_t)pos * 64);
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float4 v = rp[q];
-            z1 = fmaf(w1[4 * q], v.x, z1);
-            z1 = fmaf(w1[4 * q + 1], v.y, z1);
-            z1 = fmaf(w1[4 * q + 2], v.z, z1);
-            z1 = fmaf(w1[4 * q + 3], v.w, z1);
-          }
-        } else {
-          for (int a = 0; a < 64; ++a)
-            z1 = fmaf(w1[a], a < m ? (float)phi[(int64_t)a * N + i] : 0.f, z1);
-        }
-        const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
-        const float b1 = __fadd_ru(fabsf(z1), dl);
-        U = fmin(__dadd_ru(l1, (double)__fmul_ru(b1, b1)), l2);
-        pass = U >= lim;
-      }
-      scores[pos] = U;
-    }
-    // warp-aggregated append
-    const unsigned bal = __ballot_sync(0xffffffffu, pass);
-    if (bal) {
-      int first = 0;
-      if (lane == 0) first = atomicAdd(&ctl->n_list, __popc(bal));
-      first = __shfl_sync(0xffffffffu, first, 0);
-      if (pass) list[first + __popc(bal & ((1u << lane) - 1u))] = pos;
-    }
-  }
-}
-
-// Stage 2, one warp per row (rows [p0, p1) of the order, or with list !=
-// NULL the ctl->n_list positions in list): the bound from all m components,
-// lane j holding z_j and z_{j+32}.  The root of h_L is approached with the
-// two-pole model steps of secular_min_warp in FP32 (first step from t = 0)
-// until |h_L| is at its rounding level; h_L(t') >= 0 is then checked, in
-// directed rounding, at t' slightly above the iterate.  Rows whose check
-// fails keep U = min(U1, l2).  The row with the largest bound is packed into
-// ctl->ubest for the exact probe.
 HY_DEV float warp_sum_rd(float v) {
   for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
   return __shfl_sync(0xffffffffu, v, 0);
 }
+HY_DEV float warp_sum_ru(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return __shfl_sync(0xffffffffu, v, 0);
+}
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_screen(
-    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
-    const float* __restrict__ nrm, const int* __restrict__ ord,
-    const unsigned char* __restrict__ picked, int p0, int p1, const int* __restrict__ list,
-    OdCtl* ctl, double* __restrict__ scores, const float* __restrict__ R, int C) {
-  pdl_enter();
-  __shared__ __align__(16) float Wt[64][64];  // Wt[a][j] = W_ja in FP32, zero padded
-  __shared__ float dn[64], du[64];
-  __shared__ float ph[8][64];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double l1 = ctl->lam1, l2 = ctl->lam2;
-  {  // the step's FP32 eigensystem: rows a < m of Wt, then the shifts
-    const float4* src = reinterpret_cast<const float4*>(wt32);
-    float4* dst = reinterpret_cast<float4*>(&Wt[0][0]);
-    for (int i = threadIdx.x; i < m * 16; i += blockDim.x) dst[i] = src[i];
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-      dn[j] = wt32[4096 + j];
-      du[j] = wt32[4096 + 64 + j];
-    }
+// The step's eigensystem in FP32, staged by every CTA of the screening
+// passes: Wt[a][j] = W_ja (zero padded), the shifted poles d_j rounded to
+// nearest, upward and downward (+inf for j = 0 and j >= m).
+struct ScreenSm {
+  float Wt[64][64];
+  float dn[64], du[64], dd[64];
+  float en[64], eu[64], ed[64], d2[4];
+  float ph[8][64];
+};
+
+HY_DEV void stage_screen(const float* __restrict__ wt32, int m, ScreenSm& S) {
+  const float4* src = reinterpret_cast<const float4*>(wt32);
+  float4* dst = reinterpret_cast<float4*>(&S.Wt[0][0]);
+  for (int i = threadIdx.x; i < m * 16; i += blockDim.x) dst[i] = src[i];
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    S.dn[j] = wt32[4096 + j];
+    S.du[j] = wt32[4096 + 64 + j];
+    S.dd[j] = wt32[4096 + 128 + j];
+    S.en[j] = wt32[4096 + 192 + j];
+    S.eu[j] = wt32[4096 + 256 + j];
+    S.ed[j] = wt32[4096 + 320 + j];
   }
-  __syncthreads();
-  const float d2n = m > 1 ? dn[1] : INFINITY, d2u = m > 1 ? du[1] : INFINITY;
-  const float dn0 = dn[lane], dn1 = dn[lane + 32], du0 = du[lane], du1 = du[lane + 32];
-  const int count = list ? ctl->n_list : (p1 >= 0 ? p1 : ctl->n_c) - p0;
-  float* pr = ph[wid];
-  unsigned long long bestU = 0ull, cnt = 0;
-  for (int t0 = blockIdx.x * nw + wid; t0 < count; t0 += gridDim.x * nw) {
-    const int pos = list ? list[t0] : p0 + t0;
-    const int i = ord[pos];
-    if (picked[i]) {
-      if (lane == 0) scores[pos] = -1.0;
-      continue;
-    }
-    if (pos < C) {
-      pr[lane] = R[(int64_t)pos * 64 + lane];
-      pr[lane + 32] = R[(int64_t)pos * 64 + lane + 32];
-    } else {
-      pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
-      pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
-    }
-    __syncwarp();
-    float z0 = 0.f, z1 = 0.f;
+  if (threadIdx.x < 3) S.d2[threadIdx.x] = wt32[4096 + 384 + threadIdx.x];
+}
+
+// Both certified bounds of one row's exact score, U >= mu >= L (one warp;
+// the row's FP32 values in pr[0..64), zero beyond m; nrm_i its squared-norm
+// bound).  The root is approached in the coordinates of the nearer pole
+// (the sign of the secular function at the midpoint of (l1, l2) tells
+// which): tau = mu - l1 as above, or sigma = l2 - mu, where
+//   f(sigma) = 1 + sum_j z_j^2 / (e_j + sigma),  e_j = lam_j - l2,
+// is decreasing on (0, l2 - l1) (the j = 1 term is the negative one), so a
+// certified lower bound f_lo(s) >= 0 proves sigma >= s (mu <= l2 - s) and a
+// certified upper bound f_hi(s) <= 0 proves sigma <= s.  The greedy's best
+// rows lift lambda_min to just below l2, where only these coordinates
+// resolve sigma: in tau the bounds would stop at l2 itself.
+HY_DEV void screen_row(const ScreenSm& S, int m, double l1, double l2, const float* pr,
+                       float nrm_i, double& U, double& L) {
+  const int lane = threadIdx.x & 31;
+  float z0 = 0.f, z1 = 0.f;
 #pragma unroll 8
-    for (int a = 0; a < m; ++a) {
-      const float x = pr[a];
-      z0 = fmaf(Wt[a][lane], x, z0);
-      z1 = fmaf(Wt[a][lane + 32], x, z1);
+  for (int a = 0; a < m; ++a) {
+    const float x = pr[a];
+    z0 = fmaf(S.Wt[a][lane], x, z0);
+    z1 = fmaf(S.Wt[a][lane + 32], x, z1);
+  }
+  const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm_i));
+  const float zf = __shfl_sync(0xffffffffu, z0, 0);
+  const float b1 = __fadd_ru(fabsf(zf), dl);
+  const float b1s = __fmul_ru(b1, b1);
+  const float B1 = fmaxf(__fsub_rd(fabsf(zf), dl), 0.f);
+  const float B1s = __fmul_rd(B1, B1);
+  // bounds of z_j^2 (j >= 2) from below (a) and above (c); lane 0's first
+  // slot is z_1 itself
+  float a0 = lane == 0 ? 0.f : fmaxf(__fsub_rd(fabsf(z0), dl), 0.f);
+  float a1 = fmaxf(__fsub_rd(fabsf(z1), dl), 0.f);
+  a0 = __fmul_rd(a0, a0);
+  a1 = __fmul_rd(a1, a1);
+  float c0 = lane == 0 ? 0.f : __fadd_ru(fabsf(z0), dl);
+  float c1 = __fadd_ru(fabsf(z1), dl);
+  c0 = __fmul_ru(c0, c0);
+  c1 = __fmul_ru(c1, c1);
+  U = fmin(__dadd_ru(l1, (double)b1s), l2);
+  L = l1;
+  if (m == 1) {
+    L = __dadd_rd(l1, (double)B1s);
+    return;
+  }
+  const float d2n = S.dn[1], d2u = S.du[1], d2d = S.dd[1];
+  if (!(d2n > 0.f)) return;  // a double eigenvalue: mu = l1
+  const float E0 = S.en[lane], E1 = S.en[lane + 32];
+  const float qn0 = z0 * z0, qn1 = z1 * z1;
+  const float hm = 0.5f * d2n;
+  const float fmid = 1.f + warp_sum(__fdividef(qn0, E0 + hm) + __fdividef(qn1, E1 + hm));
+  if (fmid >= 0.f) {
+    // the root in (l1, mid]: tau coordinates
+    const float dn0 = S.dn[lane], dn1 = S.dn[lane + 32], du0 = S.du[lane], du1 = S.du[lane + 32];
+    const float dd0 = S.dd[lane], dd1 = S.dd[lane + 32];
+    float t = 0.f, lo = 0.f, hi = fminf(d2n, b1s);
+    float g = warp_sum(__fdividef(a0, dn0) + __fdividef(a1, dn1));
+    float dg = warp_sum(__fdividef(a0, dn0 * dn0) + __fdividef(a1, dn1 * dn1));
+    for (int it = 0; it < 16; ++it) {
+      if (it > 0) {
+        const float r0 = __frcp_rn(dn0 - t), r1 = __frcp_rn(dn1 - t);
+        const float q0 = a0 * r0, q1 = a1 * r1;
+        g = warp_sum(q0 + q1);
+        dg = warp_sum(fmaf(q0, r0, q1 * r1));
+        const float h = fmaf(t, 1.f + g, -b1s);
+        if (fabsf(h) <= 32.f * 1.1920929e-7f * (t * (1.f + g) + b1s)) break;
+        if (h < 0.f)
+          lo = t;
+        else
+          hi = t;
+      }
+      const float gap = d2n - t;
+      const float C = 1.f + (g - dg * gap);
+      const float B = C * d2n + b1s + dg * gap * gap;
+      const float nt = __fdividef(2.f * b1s * d2n, B + fsqrt_fast(fmaxf(B * B - 4.f * C * b1s * d2n, 0.f)));
+      if (it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t) {
+        t = nt;
+        break;
+      }
+      t = (nt > lo && nt < hi) ? nt : 0.5f * (lo + hi);
     }
-    __syncwarp();
-    const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
-    const float zf = __shfl_sync(0xffffffffu, z0, 0);
-    const float b1 = __fadd_ru(fabsf(zf), dl);
-    const float b1s = __fmul_ru(b1, b1);
-    // lower bounds of z_j^2 (j >= 2); lane 0's first slot is z_1 itself
-    float a0 = lane == 0 ? 0.f : fmaxf(__fsub_rd(fabsf(z0), dl), 0.f);
-    float a1 = fmaxf(__fsub_rd(fabsf(z1), dl), 0.f);
-    a0 = __fmul_rd(a0, a0);
-    a1 = __fmul_rd(a1, a1);
-    double U = fmin(__dadd_ru(l1, (double)b1s), l2);
-    if (m == 1 || !(d2n > 0.f)) {
-      // U already exact up to rounding (m = 1) or the interlacing bound l2
+    // certify h_L(t') >= 0: t' 3e-5 above the iterate, else 5e-4
+    for (int tr = 0; tr < 2; ++tr) {
+      const float tu = __fmul_ru(t, tr == 0 ? 1.f + 1.0f / 32768.f : 1.f + 1.0f / 2048.f);
+      if (!(tu < d2u)) break;
+      const float Sl = warp_sum_rd(__fadd_rd(__fmul_rd(a0, __frcp_rd(__fsub_ru(du0, tu))),
+                                             __fmul_rd(a1, __frcp_rd(__fsub_ru(du1, tu)))));
+      const float hl = __fsub_rd(__fmul_rd(tu, __fadd_rd(1.f, Sl)), b1s);
+      if (hl >= 0.f) {
+        U = fmin(U, __dadd_ru(l1, (double)tu));
+        break;
+      }
+    }
+    // certify h_U(t') <= 0 below the iterate (the root of h_U lies below it)
+    if (!(B1s > 0.f)) return;
+    for (int tr = 0; tr < 3; ++tr) {
+      const float td = __fmul_rd(t, tr == 0 ? 1.f - 1.0f / 32768.f
+                                            : (tr == 1 ? 1.f - 1.0f / 2048.f : 1.f - 1.0f / 128.f));
+      if (!(td > 0.f && td < d2d)) continue;
+      const float Su = warp_sum_ru(__fadd_ru(__fmul_ru(c0, __frcp_ru(__fsub_rd(dd0, td))),
+                                             __fmul_ru(c1, __frcp_ru(__fsub_rd(dd1, td)))));
+      const float hu = __fsub_ru(__fmul_ru(td, __fadd_ru(1.f, Su)), B1s);
+      if (hu <= 0.f) {
+        L = __dadd_rd(l1, (double)td);
+        return;
+      }
+    }
+    return;
+  }
+  // the root in (mid, l2): sigma = -t, two-pole model steps in t around the
+  // poles e_1 = -d2 and e_2 = 0 (the root solver's FP32 steps)
+  const float fe = 1.1920929e-7f;
+  const float fdelj = -d2n;
+  float ft = -0.5f * hm, flo = -hm, fhi = 0.f;
+  for (int it = 0; it < 16; ++it) {
+    const float r0 = __frcp_rn(E0 - ft), r1 = __frcp_rn(E1 - ft);
+    const float q0 = qn0 * r0, q1 = qn1 * r1;
+    // the j = 1 term (lane 0's first) is the only negative one and the only
+    // one left of the root: its value and slope come by a shuffle, and
+    // sum |q| = (f - 1) - 2 q_1
+    const float ql = __shfl_sync(0xffffffffu, q0, 0), rl = __shfl_sync(0xffffffffu, r0, 0);
+    const float ff = 1.f + warp_sum(q0 + q1);
+    const float dps = ql * rl;
+    const float dph = warp_sum((lane == 0 ? 0.f : q0 * r0) + q1 * r1);
+    const float fa = (ff - 1.f) - 2.f * ql;
+    if (fabsf(ff) <= 8.f * fe * (1.f + fa + fabsf(ft) * (dps + dph))) break;
+    if (ff < 0.f)
+      flo = ft;
+    else
+      fhi = ft;
+    if (fhi - flo <= 2.f * fe * fmaxf(fabsf(fhi), fabsf(flo))) {
+      ft = 0.5f * (flo + fhi);
+      break;
+    }
+    const float Dj = fdelj - ft, Dn = -ft;
+    const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+    const float A = ff - dps * Dj - dph * Dn;
+    const float B = A * (Dj + Dn) + sL + sR;
+    const float Cq = ff * Dj * Dn;
+    float eta = NAN;
+    if (A == 0.f) {
+      if (B != 0.f) eta = __fdividef(Cq, B);
     } else {
-      float t = 0.f, lo = 0.f, hi = fminf(d2n, b1s);
-      float g = warp_sum(a0 / dn0 + a1 / dn1);
-      float dg = warp_sum(a0 / (dn0 * dn0) + a1 / (dn1 * dn1));
-      for (int it = 0; it < 16; ++it) {
-        if (it > 0) {
-          const float r0 = __frcp_rn(dn0 - t), r1 = __frcp_rn(dn1 - t);
-          const float q0 = a0 * r0, q1 = a1 * r1;
-          g = warp_sum(q0 + q1);
-          dg = warp_sum(fmaf(q0, r0, q1 * r1));
-          const float h = fmaf(t, 1.f + g, -b1s);
-          if (fabsf(h) <= 32.f * 1.1920929e-7f * (t * (1.f + g) + b1s)) break;
-          if (h < 0.f)
-            lo = t;
-          else
-            hi = t;
-        }
-        const float gap = d2n - t;
-        const float C = 1.f + (g - dg * gap);
-        const float B = C * d2n + b1s + dg * gap * gap;
-        const float nt = 2.f * b1s * d2n / (B + sqrtf(fmaxf(B * B - 4.f * C * b1s * d2n, 0.f)));
-        if (it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t) {
-          t = nt;
-          break;
-        }
-        t = (nt > lo && nt < hi) ? nt : 0.5f * (lo + hi);
-      }
-      // certify h_L(t') >= 0: t' 3e-5 above the iterate, else 5e-4
-      for (int tr = 0; tr < 2; ++tr) {
-        const float tu = __fmul_ru(t, tr == 0 ? 1.f + 1.0f / 32768.f : 1.f + 1.0f / 2048.f);
-        if (!(tu < d2u)) break;
-        const float S = warp_sum_rd(__fadd_rd(__fmul_rd(a0, __frcp_rd(__fsub_ru(du0, tu))),
-                                              __fmul_rd(a1, __frcp_rd(__fsub_ru(du1, tu)))));
-        const float hl = __fsub_rd(__fmul_rd(tu, __fadd_rd(1.f, S)), b1s);
-        if (hl >= 0.f) {
-          U = fmin(U, __dadd_ru(l1, (double)tu));
-          break;
-        }
-      }
+      const float qq = 0.5f * (B + copysignf(fsqrt_fast(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
+      const float e1 = __fdividef(qq, A), e2 = qq != 0.f ? __fdividef(Cq, qq) : NAN;
+      if (e1 > Dj && e1 < Dn) eta = e1;
+      if (e2 > Dj && e2 < Dn) eta = e2;
     }
-    if (lane == 0) {
-      scores[pos] = U;
-      ++cnt;
-      const unsigned long long kU =
-          ((unsigned long long)(__double_as_longlong(U) >> 20) << 32) | (unsigned)pos;
-      bestU = kU > bestU ? kU : bestU;
+    float nt = ft + eta;
+    if (fabsf(nt - ft) <= 2.f * fe * fabsf(ft)) {
+      ft = nt;
+      break;
+    }
+    if (!(nt > flo && nt < fhi)) nt = 0.5f * (flo + fhi);
+    ft = nt;
+  }
+  const float sg = -ft;
+  if (!(sg > 0.f)) return;
+  const float eu0 = S.eu[lane], eu1 = S.eu[lane + 32], ed0 = S.ed[lane], ed1 = S.ed[lane + 32];
+  // sigma scales with z_2^2 (and with z_1^2 through the negative term),
+  // whose FP32 errors are about 2 dl / |z_2| and 2 dl / |z_1| relative: the
+  // first margin tried is three times that, the second four times more
+  const float z2a = fabsf(__shfl_sync(0xffffffffu, z0, 1));
+  const float kap = fminf(__fdividef(6.f * dl, fmaxf(z2a, 1e-30f)) +
+                              __fdividef(6.f * dl, fmaxf(fabsf(zf), 1e-30f)) + 1.0f / 32768.f,
+                          0.5f);
+  // U: f_lo(s) >= 0 at s below the iterate (z_1^2 from above in the
+  // negative term, the others from below); a / b from below as
+  // a * rcp_rd(b) rounded down, from above as a * rcp_ru(b) rounded up
+  for (int tr = 0; tr < 2; ++tr) {
+    const float sl = __fmul_rd(sg, 1.f - (tr == 0 ? kap : fminf(4.f * kap, 0.75f)));
+    if (!(sl > 0.f)) continue;
+    const float t0 = lane == 0 ? -__fmul_ru(b1s, __frcp_ru(__fsub_rd(d2d, sl)))
+                               : __fmul_rd(a0, __frcp_rd(__fadd_ru(eu0, sl)));
+    const float t1 = __fmul_rd(a1, __frcp_rd(__fadd_ru(eu1, sl)));
+    const float flo_ = __fadd_rd(1.f, warp_sum_rd(__fadd_rd(t0, t1)));
+    if (flo_ >= 0.f) {
+      U = fmin(U, __dsub_ru(l2, (double)sl));
+      break;
     }
   }
-  if (lane == 0) {
-    if (bestU) atomicMax(&ctl->ubest, bestU);
-    if (cnt) atomicAdd(&ctl->stat[1], cnt);
+  // L: f_hi(s) <= 0 at s above the iterate, relatively, then by a fraction
+  // of l2 - l1 (sigma is not resolved when z_2 is below the FP32 error of
+  // the screen; l2 - s is then still a bound as good as tau's)
+  for (int tr = 0; tr < 3; ++tr) {
+    const float su = tr == 0 ? __fmul_ru(sg, 1.f + kap)
+                             : (tr == 1 ? __fmul_ru(sg, 1.f + 4.f * kap)
+                                        : __fadd_ru(sg, __fmul_ru(d2u, 1.0f / 32768.f)));
+    if (!(su < d2d)) continue;
+    const float t0 = lane == 0 ? -__fmul_rd(B1s, __frcp_rd(__fsub_ru(d2u, su)))
+                               : __fmul_ru(c0, __frcp_ru(__fadd_rd(ed0, su)));
+    const float t1 = __fmul_ru(c1, __frcp_ru(__fadd_rd(ed1, su)));
+    const float fhi_ = __fadd_ru(1.f, warp_sum_ru(__fadd_ru(t0, t1)));
+    if (fhi_ <= 0.f) {
+      L = fmax(L, __dsub_rd(l2, (double)su));
+      break;
+    }
   }
+}
+
+// One warp loads ordered row pos of Phi as FP32 into pr[0..64).
+template <typename T>
+HY_DEV void load_row32(const T* __restrict__ phi, int64_t N, int m, int i, int pos,
+                       const float* __restrict__ R, int C, float* pr) {
+  const int lane = threadIdx.x & 31;
+  if (pos < C) {
+    pr[lane] = R[(int64_t)pos * 64 + lane];
+    pr[lane + 32] = R[(int64_t)pos * 64 + lane + 32];
+  } else {
+    pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
+    pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
+  }
+  __syncwarp();
 }
 
 // stage a CTA's copy of W (m x m, column j = eigenvector j) with an odd
@@ -847,136 +1103,202 @@ HY_DEV void stage_w(const double* __restrict__ W_s, const double* __restrict__ l
   for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = lam_s[i];
 }
 
-// exact score of the row with the largest screen bound -> raise smax to it
-// (z by the whole CTA, the root by warp 0)
-template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_probe_best(
-    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
-    const double* __restrict__ W_s, const int* __restrict__ ord, OdCtl* ctl) {
-  pdl_enter();
-  extern __shared__ double sh[];
-  double* W = sh;               // 64 x kLdw
-  double* lam = W + 64 * kLdw;  // 64
-  double* rb = lam + 64;        // 64
-  double* zp = rb + 64;         // 4 x 64
-  double* zs = zp + 4 * 64;     // 64
-  const unsigned long long key = ctl->ubest;
-  if (!key) return;
-  const int row = ord[(int)(key & 0xffffffffull)];
-  stage_w(W_s, lam_s, m, W, lam);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) rb[i] = (double)phi[(int64_t)i * N + row];
-  z_block(W, kLdw, rb, m, zp, zs);
-  if (threadIdx.x < 32) {
-    const double mu = secular_root_warp(zs, lam, m, ctl->lam1, ctl->lam2);
-    if (threadIdx.x == 0) atomicMax(&ctl->smax, dbits(mu));
-  }
+HY_DEV double limit_of(const OdCtl* ctl, double tie_tol) {
+  const unsigned long long a = *(const volatile unsigned long long*)&ctl->smax;
+  const unsigned long long b = *(const volatile unsigned long long*)&ctl->slo;
+  return bitsd(a > b ? a : b) * (1.0 - 2.0 * tie_tol);
 }
 
-// exact scores of the rows whose bound reaches smax (1 - 2 tie); the others
-// get -1.  Only the probe positions [0, probe) and the ctl->n_list positions
-// in `list` (the rows the z_1 bound passed to the full screen) can reach it:
-// every other row keeps its z_1 bound, which is below the limit of that
-// time and so below every later one.  One CTA of 128 threads per SM walks
-// tiles of 128 of these, interleaved over the CTAs (entry c + G (128 k + t)
-// for CTA c of G) because the rows that reach the limit are the largest-norm
-// ones at the front of the order: the tile's rows that reach it are listed in shared
-// memory, W is staged at the CTA's first such row, and the rows are scored
-// four at a time — z by the whole CTA for each, then warp w solves the
-// secular equation of the w-th row.  Before each group the limit is raised
-// to the best exact score any CTA has found so far; rows whose bound no
-// longer reaches it get -1 (they cannot reach the tie window of the best).
-constexpr int kExactThreads = 128;
+// Pass 1: both bounds of the probe rows [0, probe), one warp per row; the
+// best L raises the limit.  The CTA that finishes last sets the rows the
+// next pass takes: mu - l1 <= z_1^2 <= |phi_i|^2, so only rows with
+// |phi_i|^2 >= lim - l1 can reach the limit.
 template <typename T>
-__global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
-    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
-    const double* __restrict__ W_s, const int* __restrict__ ord, int probe,
-    const int* __restrict__ list, double tie_tol, OdCtl* ctl, double* __restrict__ scores) {
+__global__ void __launch_bounds__(256) k_odeim_probe(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
+    const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
+    const float* __restrict__ R, int C) {
   pdl_enter();
-  extern __shared__ double sh[];
-  double* W = sh;               // 64 x kLdw
-  double* lam = W + 64 * kLdw;  // 64
-  double* rb = lam + 64;        // 4 x 64: rows of the group
-  double* zp = rb + 4 * 64;     // 2 x 64
-  double* zs = zp + 2 * 64;     // 4 x 64
-  __shared__ int surv[kExactThreads];
-  __shared__ int nlist;
-  __shared__ int grp[4];  // the group's positions still to score (-1: none)
-  __shared__ int ngrp;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ __align__(16) ScreenSm S;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double l1 = ctl->lam1, l2 = ctl->lam2;
-  const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  const int end = probe + ctl->n_list;  // entries: probe positions, then the list
-  double best = 0.0;
-  unsigned long long cnt = 0;
-  bool staged = false;
-  if (tid == 0) nlist = 0;
+  stage_screen(wt32, m, S);
   __syncthreads();
-  const int G = gridDim.x;
-  for (int base = 0; (int)blockIdx.x + G * base < end; base += kExactThreads) {
-    const int e = blockIdx.x + G * (base + tid);
-    if (e < end) {
-      const int pos = e < probe ? e : list[e - probe];
-      const double U = scores[pos];
-      if (U < lim) {
-        if (U >= 0.0) scores[pos] = -1.0;
-      } else {
-        surv[atomicAdd(&nlist, 1)] = pos;
-      }
+  float* pr = S.ph[wid];
+  unsigned long long bestL = 0ull, cnt = 0;
+  for (int t0 = blockIdx.x * nw + wid; t0 < probe; t0 += gridDim.x * nw) {
+    const int pos = t0;
+    const int i = ord[pos];
+    if (picked[i]) {
+      if (lane == 0) scores[pos] = -1.0;
+      continue;
     }
-    __syncthreads();
-    const int n = nlist;
-    if (n > 0 && !staged) {
-      stage_w(W_s, lam_s, m, W, lam);
-      staged = true;
+    load_row32<T>(phi, N, m, i, pos, R, C, pr);
+    double U, L;
+    screen_row(S, m, l1, l2, pr, nrm[i], U, L);
+    __syncwarp();
+    if (lane == 0) {
+      scores[pos] = U;
+      ++cnt;
+      bestL = dbits(L) > bestL ? dbits(L) : bestL;
     }
-    for (int g = 0; g < n; g += 4) {
-      const int nq = n - g < 4 ? n - g : 4;
-      if (tid == 0) {
-        const double lnow =
-            fmax(lim, bitsd(*(volatile unsigned long long*)&ctl->smax) * (1.0 - 2.0 * tie_tol));
-        int k = 0;
-        for (int q = 0; q < nq; ++q) {
-          const int pos = surv[g + q];
-          if (scores[pos] >= lnow)
-            grp[k++] = pos;
-          else
-            scores[pos] = -1.0;
-        }
-        ngrp = k;
-      }
-      __syncthreads();
-      const int ng = ngrp;
-      for (int idx = tid; idx < ng * 64; idx += kExactThreads) {
-        const int q = idx >> 6, a = idx & 63;
-        rb[idx] = a < m ? (double)phi[(int64_t)a * N + ord[grp[q]]] : 0.0;
-      }
-      for (int q = 0; q < ng; ++q) z_block(W, kLdw, rb + 64 * q, m, zp, zs + 64 * q);
-      if (wid < ng) {
-        const double mu = secular_root_warp(zs + 64 * wid, lam, m, l1, l2);
-        if (lane == 0) {
-          scores[grp[wid]] = mu;
-          atomicMax(&ctl->smax, dbits(mu));  // raises the limit of later groups
-        }
-        best = mu > best ? mu : best;
-        ++cnt;
-      }
-      __syncthreads();
-    }
-    if (tid == 0) nlist = 0;
-    __syncthreads();
   }
-  best = block_max(best);
-  if (tid == 0) atomicMax(&ctl->smax, dbits(best));
-  if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
+  bestL = block_max_u64(bestL);
+  if (threadIdx.x == 0 && bestL) atomicMax(&ctl->slo, bestL);
+  if (lane == 0 && cnt) atomicAdd(&ctl->stat[1], cnt);
+  if (!last_block(&ctl->ticket)) return;
+  const double lim = limit_of(ctl, tie_tol);
+  const int n = plan_end(bmax, bstart, probe, (lim - l1) / (1.0 + 1e-5));
+  if (threadIdx.x == 0) {
+    ctl->n_c = n;
+    ctl->ticket = 0u;
+    ctl->stat[3] += 1;
+  }
 }
 
-// ODEIM: mu - l1 <= z_1^2 <= |phi_i|^2, so rows need |phi_i|^2 >= lim - l1
-__global__ void k_odeim_plan(OdCtl* ctl, const unsigned int* __restrict__ bmax,
-                             const int* __restrict__ bstart, int probe_end, double tie_tol) {
+// Pass 2a, one thread per ordered row in [probe, n_c): bounds from z_1 and
+// z_2 alone (two m-term dot products): U1 = min(l1 + b1^2, l2), and, below
+// l2, l2 - s for the s at which the two-term secular function
+//   f2(s) = 1 + z_2^2 / s - z_1^2 / (d2 - s)
+// is certified non-negative (the true f has further positive terms, so
+// f(s) >= f2(s) >= 0 and sigma >= s; s from f2's root less a margin for the
+// FP32 errors of z).  Rows whose bound reaches the limit are appended to
+// `list` for pass 2b.
+template <typename T>
+__global__ void __launch_bounds__(256) k_odeim_z1(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
+    double* __restrict__ scores, int* __restrict__ list, const float* __restrict__ R, int C) {
   pdl_enter();
-  if (threadIdx.x == 0) ctl->stat[3] += 1;
-  const double lim = bitsd(ctl->smax) * (1.0 - 2.0 * tie_tol);
-  plan_rows(ctl, bmax, bstart, probe_end, (lim - ctl->lam1) / (1.0 + 1e-5));
+  __shared__ float w1[64], w2[64];
+  for (int a = threadIdx.x; a < 64; a += blockDim.x) {
+    w1[a] = a < m ? wt32[a * 64] : 0.f;
+    w2[a] = a < m && m > 1 ? wt32[a * 64 + 1] : 0.f;
+  }
+  __syncthreads();
+  const double l1 = ctl->lam1, l2 = ctl->lam2;
+  const double lim = limit_of(ctl, tie_tol);
+  const int end = ctl->n_c;
+  const int lane = threadIdx.x & 31;
+  const float d2n = wt32[4096 + 384], d2d = wt32[4096 + 384 + 2];
+  for (int base = p0 + blockIdx.x * blockDim.x; base < end; base += gridDim.x * blockDim.x) {
+    const int pos = base + threadIdx.x;
+    bool pass = false;
+    if (pos < end) {
+      const int i = ord[pos];
+      double U = -1.0;
+      if (!picked[i]) {
+        float z1 = 0.f, z2 = 0.f;
+        if (pos < C) {  // contiguous copy (zero beyond m: same sum)
+          const float4* rp = reinterpret_cast<const float4*>(R + (int64_t)pos * 64);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float4 v = rp[q];
+            z1 = fmaf(w1[4 * q], v.x, z1);
+            z1 = fmaf(w1[4 * q + 1], v.y, z1);
+            z1 = fmaf(w1[4 * q + 2], v.z, z1);
+            z1 = fmaf(w1[4 * q + 3], v.w, z1);
+            z2 = fmaf(w2[4 * q], v.x, z2);
+            z2 = fmaf(w2[4 * q + 1], v.y, z2);
+            z2 = fmaf(w2[4 * q + 2], v.z, z2);
+            z2 = fmaf(w2[4 * q + 3], v.w, z2);
+          }
+        } else {
+          for (int a = 0; a < 64; ++a) {
+            const float x = a < m ? (float)phi[(int64_t)a * N + i] : 0.f;
+            z1 = fmaf(w1[a], x, z1);
+            z2 = fmaf(w2[a], x, z2);
+          }
+        }
+        const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm[i]));
+        const float b1 = __fadd_ru(fabsf(z1), dl);
+        const float bh = __fmul_ru(b1, b1);
+        U = fmin(__dadd_ru(l1, (double)bh), l2);
+        const float al = fmaxf(__fsub_rd(fabsf(z2), dl), 0.f);
+        if (m > 1 && d2n > 0.f && al > 0.f) {
+          const float a = z2 * z2, b = z1 * z1, p = d2n - a - b;
+          const float rt = fsqrt_fast(fmaf(p, p, 4.f * a * d2n));
+          const float s0 = p >= 0.f ? 0.5f * (p + rt) : __fdividef(2.f * a * d2n, rt - p);
+          const float kap = fminf(__fdividef(6.f * dl, fmaxf(fabsf(z2), 1e-30f)) +
+                                      __fdividef(6.f * dl, fmaxf(fabsf(z1), 1e-30f)) +
+                                      1.0f / 32768.f,
+                                  0.75f);
+          const float sl = __fmul_rd(s0, 1.f - kap);
+          if (sl > 0.f && sl < d2d) {
+            const float ta = __fmul_rd(__fmul_rd(al, al), __frcp_rd(sl));
+            const float tb = __fmul_ru(bh, __frcp_ru(__fsub_rd(d2d, sl)));
+            if (__fsub_rd(__fadd_rd(1.f, ta), tb) >= 0.f) U = fmin(U, __dsub_ru(l2, (double)sl));
+          }
+        }
+        pass = U >= lim;
+      }
+      scores[pos] = U;
+    }
+    // warp-aggregated append
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (bal) {
+      int first = 0;
+      if (lane == 0) first = atomicAdd(&ctl->n_list, __popc(bal));
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (pass) list[first + __popc(bal & ((1u << lane) - 1u))] = pos;
+    }
+  }
+}
+
+// Pass 2b, one warp per row listed by pass 2a: both full bounds (U replaces
+// the row's score); every L raises the limit.  The rows whose U reaches the
+// limit of the time, and the probe rows whose U does, are listed in xlist
+// for the exact pass.
+template <typename T>
+__global__ void __launch_bounds__(256) k_odeim_screen(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
+    int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
+    const float* __restrict__ R, int C) {
+  pdl_enter();
+  __shared__ __align__(16) ScreenSm S;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int count = ctl->n_list;
+  {  // the probe rows
+    const double lim = limit_of(ctl, tie_tol);
+    for (int base = blockIdx.x * blockDim.x; base < probe; base += gridDim.x * blockDim.x) {
+      const int pos = base + threadIdx.x;
+      const bool x = pos < probe && scores[pos] >= lim;
+      const unsigned bal = __ballot_sync(0xffffffffu, x);
+      if (bal) {
+        int first = 0;
+        if (lane == __ffs(bal) - 1) first = atomicAdd(&ctl->n_x, __popc(bal));
+        first = __shfl_sync(0xffffffffu, first, __ffs(bal) - 1);
+        if (x) xlist[first + __popc(bal & ((1u << lane) - 1u))] = pos;
+      }
+    }
+  }
+  if ((int)blockIdx.x * nw >= count) return;  // no listed row for this CTA
+  const double l1 = ctl->lam1, l2 = ctl->lam2;
+  stage_screen(wt32, m, S);
+  __syncthreads();
+  float* pr = S.ph[wid];
+  unsigned long long bestL = 0ull, cnt = 0;
+  for (int t0 = blockIdx.x * nw + wid; t0 < count; t0 += gridDim.x * nw) {
+    const int pos = list[t0];
+    const int i = ord[pos];
+    load_row32<T>(phi, N, m, i, pos, R, C, pr);
+    double U, L;
+    screen_row(S, m, l1, l2, pr, nrm[i], U, L);
+    __syncwarp();
+    if (lane == 0) {
+      scores[pos] = U;
+      ++cnt;
+      bestL = dbits(L) > bestL ? dbits(L) : bestL;
+      if (U >= limit_of(ctl, tie_tol)) xlist[atomicAdd(&ctl->n_x, 1)] = pos;
+    }
+  }
+  bestL = block_max_u64(bestL);  // one atomic per CTA on the shared limit
+  if (threadIdx.x == 0 && bestL) atomicMax(&ctl->slo, bestL);
+  if (lane == 0 && cnt) atomicAdd(&ctl->stat[1], cnt);
 }
 
 // ---- rank-one update of the eigensystem of M (one per oversampling step) ----
@@ -1006,39 +1328,17 @@ struct R1Work {
   double zh[64];   // Loewner z of the non-deflated components
 };
 
-template <typename T>
-__global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const OdCtl* ctl,
-                             const double* __restrict__ d, const double* __restrict__ W,
-                             double* __restrict__ Wrot, R1Work* wk) {
-  pdl_enter();
-  __shared__ double Ws[64 * 64];
-  __shared__ double ph[64], z[64], ds[64];
+// The eigensystem update's preparation for the point p just picked (one
+// CTA, blockDim a multiple of 64): z = W^T phi_p, then deflation of the
+// negligible z components and of nearly equal poles (a Givens rotation
+// folds one z component into its neighbour), as in the divide-and-conquer
+// eigensolver (Bunch, Nielsen & Sorensen 1978).  W (stride kLdw) and the
+// eigenvalues ds are the CTA's shared copies (both may be rotated); the
+// kept components go to wk, the possibly rotated W to Wrot (stride m).
+HY_DEV void r1_prepare_block(double* W, double* ds, const double* ph, int m, double* zp,
+                             double* z, R1Work* wk, double* __restrict__ Wrot) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int p = ctl->argmin;
-  for (int a = tid; a < m; a += blockDim.x) {
-    ph[a] = (double)phi[(int64_t)a * N + p];
-    ds[a] = d[a];
-  }
-  stage_copy(Ws, W, m * m);
-  __shared__ double zp[4][64];
-  {  // z = W^T phi: thread t forms component t % 64 over a quarter of the terms
-    __syncthreads();
-    const int j = tid & 63, h = tid >> 6;
-    const int len = (m + 3) / 4, a0 = h * len, a1 = a0 + len < m ? a0 + len : m;
-    double p0 = 0.0, p1 = 0.0;
-    if (j < m && h < 4) {
-      int a = a0;
-      for (; a + 1 < a1; a += 2) {
-        p0 = fma(Ws[j * m + a], ph[a], p0);
-        p1 = fma(Ws[j * m + a + 1], ph[a + 1], p1);
-      }
-      if (a < a1) p0 = fma(Ws[j * m + a], ph[a], p0);
-    }
-    if (h < 4) zp[h][j] = p0 + p1;
-    __syncthreads();
-    if (tid < m) z[tid] = (zp[0][tid] + zp[1][tid]) + (zp[2][tid] + zp[3][tid]);
-    __syncthreads();
-  }
+  z_block(W, kLdw, ph, m, zp, z);
   __shared__ int nonsmall[64], nns, anyclose;
   __shared__ double tol_s, nz_s;
   {
@@ -1115,9 +1415,9 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
         const double dp = c * c * ds[prev] + sn * sn * ds[i];
         const double di = sn * sn * ds[prev] + c * c * ds[i];
         for (int a2 = 0; a2 < m; ++a2) {
-          const double wp = Ws[prev * m + a2], wi = Ws[i * m + a2];
-          Ws[prev * m + a2] = c * wp - sn * wi;
-          Ws[i * m + a2] = sn * wp + c * wi;
+          const double wp = W[prev * kLdw + a2], wi = W[i * kLdw + a2];
+          W[prev * kLdw + a2] = c * wp - sn * wi;
+          W[i * kLdw + a2] = sn * wp + c * wi;
         }
         z[prev] = 0.0;
         z[i] = t;
@@ -1141,7 +1441,108 @@ __global__ void k_r1_prepare(const T* __restrict__ phi, int64_t N, int m, const 
     wk->nD = nD;
   }
   __syncthreads();
-  for (int i = tid; i < m * m; i += blockDim.x) Wrot[i] = Ws[i];
+  for (int i = tid; i < m * m; i += blockDim.x) {
+    const int j = i / m, a = i - j * m;
+    Wrot[i] = W[j * kLdw + a];
+  }
+}
+
+// Pass 3: exact scores of the rows listed in xlist (U reached the limit of
+// its time), spread over the CTAs round-robin (row k of the list to CTA
+// k mod G) so that the FP64 work spreads over the SMs, four at a time per
+// CTA: z by the whole CTA for each, then warp w solves the secular equation
+// of the w-th row.  Before each group the limit is raised to the best
+// exact score any CTA has found so far (and the best L); rows whose bound
+// no longer reaches it get -1 (they cannot reach the tie window of the
+// best).  Every exact score is listed as a candidate.  The CTA that finishes
+// last picks point l (the lowest row in the tie window of the best exact
+// score) and, for l + 1 < n_p, prepares the eigensystem update with it; it
+// then resets the step's control block.
+constexpr int kExactThreads = 128;
+template <typename T>
+__global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
+    const double* __restrict__ W_s, const int* __restrict__ ord, const int* __restrict__ xlist,
+    double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, int l,
+    int np, int* __restrict__ pts, unsigned char* __restrict__ picked,
+    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot) {
+  pdl_enter();
+  extern __shared__ double sh[];
+  double* W = sh;               // 64 x kLdw
+  double* lam = W + 64 * kLdw;  // 64
+  double* rb = lam + 64;        // 4 x 64: rows of the group
+  double* zp = rb + 4 * 64;     // 2 x 64
+  double* zs = zp + 2 * 64;     // 4 x 64
+  __shared__ int grp[4];  // the group's positions still to score
+  __shared__ int ngrp;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const double l1 = ctl->lam1, l2 = ctl->lam2;
+  const int nx = ctl->n_x;
+  const int G = gridDim.x;
+  double best = 0.0;
+  unsigned long long cnt = 0;
+  bool staged = false;
+  for (int k0 = blockIdx.x; k0 < nx; k0 += 4 * G) {
+    if (tid == 0) {
+      const double lnow = limit_of(ctl, tie_tol);
+      int k = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int e = k0 + q * G;
+        if (e >= nx) break;
+        const int pos = xlist[e];
+        if (scores[pos] >= lnow)
+          grp[k++] = pos;
+        else
+          scores[pos] = -1.0;
+      }
+      ngrp = k;
+    }
+    __syncthreads();
+    const int ng = ngrp;
+    if (ng > 0 && !staged) {
+      stage_w(W_s, lam_s, m, W, lam);
+      staged = true;
+    }
+    for (int idx = tid; idx < ng * 64; idx += kExactThreads) {
+      const int q = idx >> 6, a = idx & 63;
+      rb[idx] = a < m ? phi_at<T>(phi, N, a, ord[grp[q]], grp[q], R, C) : 0.0;
+    }
+    for (int q = 0; q < ng; ++q) z_block(W, kLdw, rb + 64 * q, m, zp, zs + 64 * q);
+    if (wid < ng) {
+      const double mu = secular_root_warp(zs + 64 * wid, lam, m, l1, l2);
+      if (lane == 0) {
+        scores[grp[wid]] = mu;
+        atomicMax(&ctl->smax, dbits(mu));  // raises the limit of later groups
+        cand[atomicAdd(&ctl->ncand, 1)] = grp[wid];
+      }
+      best = mu > best ? mu : best;
+      ++cnt;
+    }
+    __syncthreads();
+  }
+  best = block_max(best);
+  if (tid == 0) atomicMax(&ctl->smax, dbits(best));
+  if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
+  if (!last_block(&ctl->ticket)) return;
+  // ---- the pick, then the update's preparation (this CTA alone) ----
+  const unsigned long long key = pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked);
+  if (l + 1 < np && key != ~0ull) {
+    const int p = (int)(key >> 32), wpos = (int)(key & 0xffffffffull);
+    if (!staged) stage_w(W_s, lam_s, m, W, lam);
+    for (int a = tid; a < 64; a += blockDim.x)
+      rb[a] = a < m ? phi_at<T>(phi, N, a, p, wpos, R, C) : 0.0;
+    r1_prepare_block(W, lam, rb, m, zp, zs, wk, Wrot);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    ctl->smax = 0ull;
+    ctl->slo = 0ull;
+    ctl->n_list = 0;
+    ctl->n_x = 0;
+    ctl->ncand = 0;
+    ctl->ticket = 0u;
+    ctl->n_c = 0;
+  }
 }
 
 // One warp per root (CTA j); Delta[i * 64 + j] = d_i - lambda_j.
@@ -1245,7 +1646,7 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
       float eta = NAN;
       if (last) {
         const float sL = dps * Dj * Dj, cq = f - dps * Dj;
-        if (cq > 0.f) eta = Dj + sL / cq;
+        if (cq > 0.f) eta = Dj + __fdividef(sL, cq);
       } else {
         const float Dn = fdeln - ft;
         const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
@@ -1253,10 +1654,10 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
         const float B = A * (Dj + Dn) + sL + sR;
         const float Cq = f * Dj * Dn;
         if (A == 0.f) {
-          if (B != 0.f) eta = Cq / B;
+          if (B != 0.f) eta = __fdividef(Cq, B);
         } else {
-          const float qq = 0.5f * (B + copysignf(sqrtf(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
-          const float e1 = qq / A, e2 = qq != 0.f ? Cq / qq : NAN;
+          const float qq = 0.5f * (B + copysignf(fsqrt_fast(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
+          const float e1 = __fdividef(qq, A), e2 = qq != 0.f ? __fdividef(Cq, qq) : NAN;
           if (e1 > Dj && e1 < Dn) eta = e1;
           if (e2 > Dj && e2 < Dn) eta = e2;
         }
@@ -1367,131 +1768,106 @@ __global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __
   }
 }
 
-// Eigenvector j of diag(dK) + z z^T, v_i = zh_i / (d_i - lambda_j), mapped
-// back through W.  CTA j writes column j of Wnew (m values) and lamnew[j];
-// the product with W is split over the CTA's eight warps (thread t: row
-// a = t % 64 over a quarter of the components).
+// Eigenpair j of M + phi phi^T, written straight to its place in ascending
+// order (CTA j of m).  For j < nK, the new pair: the root
+// lambda_j = dK[org_j] + tau_j and the vector v_i = zh_i / (d_i - lambda_j)
+// mapped back through W (the product split over the CTA's eight warps,
+// thread t: row a = t % 64 over a quarter of the components); for j >= nK
+// the deflated pair (dD, Wrot column D) unchanged.  Its rank among all m
+// eigenvalues (ties by index) is the column it takes in W_out and wt32.
+// CTA 0 also writes the sorted eigenvalues' control entries and the FP32
+// tails of wt32.
 __global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ wk,
                                                     const double* __restrict__ Delta,
                                                     const double* __restrict__ Wrot, int m,
-                                                    double* __restrict__ Wnew,
-                                                    double* __restrict__ lamnew) {
+                                                    double* __restrict__ d_out,
+                                                    double* __restrict__ W_out, OdCtl* ctl,
+                                                    float* __restrict__ wt32) {
   pdl_enter();
   __shared__ double v[64];
   __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
   __shared__ double part[4][64];
   __shared__ int Ks[64];
-  const int j = blockIdx.x, tid = threadIdx.x;
-  const int nK = wk->nK;
-  if (j >= nK) return;
-  for (int i = tid; i < nK; i += blockDim.x) Ks[i] = wk->K[i];
-  __syncthreads();
-  for (int base = tid; base < nK * 64; base += blockDim.x * 8) {
-    double wv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int i = idx >> 6, a = idx & 63;
-      wv[u] = idx < nK * 64 && a < m ? Wrot[Ks[i] * m + a] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < nK * 64) Wk[(idx >> 6) * 65 + (idx & 63)] = wv[u];
-    }
-  }
-  double vi = 0.0;
-  if (tid < 64) {
-    if (tid < nK) vi = wk->zh[tid] * rcp64(Delta[tid * 64 + j]);
-    v[tid] = vi;
-  }
-  __syncthreads();
-  double nrm = tid < 64 ? vi * vi : 0.0;
-  nrm = block_sum(nrm);
-  const double inv = 1.0 / sqrt(nrm);
-  {
-    const int a = tid & 63, h = tid >> 6;
-    const int i0 = h * 16, i1 = i0 + 16 < nK ? i0 + 16 : nK;
-    double acc0 = 0.0, acc1 = 0.0;
-    int i = i0;
-    for (; i + 1 < i1; i += 2) {
-      acc0 = fma(Wk[i * 65 + a], v[i], acc0);
-      acc1 = fma(Wk[(i + 1) * 65 + a], v[i + 1], acc1);
-    }
-    if (i < i1) acc0 = fma(Wk[i * 65 + a], v[i], acc0);
-    part[h][a] = acc0 + acc1;
-  }
-  __syncthreads();
-  if (tid < m) Wnew[j * m + tid] = ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
-  if (tid == 0) lamnew[j] = wk->dK[wk->org[j]] + wk->tau[j];
-}
-
-// Merge deflated and new eigenpairs, ascending; reset the step's control.
-__global__ void k_r1_merge(const R1Work* __restrict__ wk, const double* __restrict__ Wrot,
-                           const double* __restrict__ Wnew, const double* __restrict__ lamnew,
-                           int m, double* __restrict__ d_out, double* __restrict__ W_out,
-                           OdCtl* ctl, float* __restrict__ wt32) {
-  pdl_enter();
   __shared__ double lv[64];
   __shared__ unsigned long long key[64];
-  __shared__ int src[64];  // >= 0: new pair index; < 0: -(deflated idx)-1
-  __shared__ int perm[64];
-  const int tid = threadIdx.x;
-  const int nK = wk->nK, nD = wk->nD;
-  for (int j = tid; j < m; j += blockDim.x) {
-    if (j < nK) {
-      lv[j] = lamnew[j];
-      src[j] = j;
-    } else {
-      lv[j] = wk->dD[j - nK];
-      src[j] = -wk->D[j - nK] - 1;
-    }
-    key[j] = dkey(lv[j]);
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const int nK = wk->nK;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const double x = i < nK ? wk->dK[wk->org[i]] + wk->tau[i] : wk->dD[i - nK];
+    lv[i] = x;
+    key[i] = dkey(x);
   }
   __syncthreads();
-  for (int j = tid; j < m; j += blockDim.x) {  // rank = position in ascending order
-    int r = 0;
-    for (int i = 0; i < m; ++i) r += (key[i] < key[j]) || (key[i] == key[j] && i < j);
-    perm[r] = j;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    ctl->lam1 = lv[perm[0]];
-    ctl->lam2 = m > 1 ? lv[perm[1]] : INFINITY;
-    ctl->lmax = lv[perm[m - 1]];
-    ctl->smax = 0ull;
-    ctl->n_list = 0;
-    ctl->ubest = 0ull;
-    ctl->argmin = 0x7fffffff;
-    ctl->n_c = 0;
-  }
-  (void)nD;
-  for (int i = tid; i < m; i += blockDim.x) d_out[i] = lv[perm[i]];
-  // eight loads in flight per thread before any store
-  for (int base = tid; base < m * m; base += blockDim.x * 8) {
-    double v[8];
+  int r = 0;
+  for (int i = 0; i < m; ++i) r += (key[i] < key[j]) || (key[i] == key[j] && i < j);
+  if (j < nK) {
+    for (int i = tid; i < nK; i += blockDim.x) Ks[i] = wk->K[i];
+    __syncthreads();
+    for (int base = tid; base < nK * 64; base += blockDim.x * 8) {
+      double wv[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      v[u] = 0.0;
-      if (idx < m * m) {
-        const int j = idx / m, a = idx - j * m;
-        const int sidx = src[perm[j]];
-        v[u] = sidx >= 0 ? Wnew[sidx * m + a] : Wrot[(-sidx - 1) * m + a];
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int i = idx >> 6, a = idx & 63;
+        wv[u] = idx < nK * 64 && a < m ? Wrot[Ks[i] * m + a] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < nK * 64) Wk[(idx >> 6) * 65 + (idx & 63)] = wv[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < m * m) {
-        W_out[idx] = v[u];
-        const int j = idx / m, a = idx - j * m;
-        wt32[a * 64 + j] = (float)v[u];
+    double vi = 0.0;
+    if (tid < 64) {
+      if (tid < nK) vi = wk->zh[tid] * rcp64(Delta[tid * 64 + j]);
+      v[tid] = vi;
+    }
+    __syncthreads();
+    double nrm = tid < 64 ? vi * vi : 0.0;
+    nrm = block_sum(nrm);
+    const double inv = 1.0 / sqrt(nrm);
+    {
+      const int a = tid & 63, h = tid >> 6;
+      const int i0 = h * 16, i1 = i0 + 16 < nK ? i0 + 16 : nK;
+      double acc0 = 0.0, acc1 = 0.0;
+      int i = i0;
+      for (; i + 1 < i1; i += 2) {
+        acc0 = fma(Wk[i * 65 + a], v[i], acc0);
+        acc1 = fma(Wk[(i + 1) * 65 + a], v[i + 1], acc1);
       }
+      if (i < i1) acc0 = fma(Wk[i * 65 + a], v[i], acc0);
+      part[h][a] = acc0 + acc1;
+    }
+    __syncthreads();
+    if (tid < m) {
+      const double x = ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
+      W_out[r * m + tid] = x;
+      wt32[tid * 64 + r] = (float)x;
+    }
+  } else {
+    const int src = wk->D[j - nK];
+    for (int a = tid; a < m; a += blockDim.x) {
+      const double x = Wrot[src * m + a];
+      W_out[r * m + a] = x;
+      wt32[a * 64 + r] = (float)x;
     }
   }
-  __syncthreads();  // d_out complete
-  w32_tail(d_out, m, wt32);
+  if (tid == 0) d_out[r] = lv[j];
+  if (j == 0) {
+    __shared__ double ls[64];
+    for (int i = tid; i < m; i += blockDim.x) {
+      int ri = 0;
+      for (int q = 0; q < m; ++q) ri += (key[q] < key[i]) || (key[q] == key[i] && q < i);
+      ls[ri] = lv[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      ctl->lam1 = ls[0];
+      ctl->lam2 = m > 1 ? ls[1] : INFINITY;
+      ctl->lmax = ls[m - 1];
+    }
+    w32_tail(ls, m, wt32);
+  }
 }
 
 __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
@@ -1505,6 +1881,8 @@ __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* _
 
 struct OdeimBufs {
   int* list;
+  int* cand;
+  int* xlist;
   float* rows;
   float* nrm;
   unsigned char* bkt;
@@ -1532,16 +1910,16 @@ struct OdeimBufs {
   double* jbuf;
   double* jscale;
   int* jflag;
-  double* Lf;
-  double* Uf;
+  double* Li;  // DEIM: inverses of the bordered factors (64 x 64 row-major)
+  double* Ui;
   double* yv;
   OdCtl* ctl;
-  float* wt32;  // the step's eigensystem in FP32 for the screens (4096 + 128)
+  float* wt32;  // the step's eigensystem in FP32 for the screens (kW32 floats)
 };
 
 size_t odeim_ws_bytes(int64_t N, int m) {
   size_t b = 0;
-  b += N * sizeof(float) + N + N + 2 * N * sizeof(int) + N * sizeof(double) + 256;
+  b += N * sizeof(float) + N + N + 4 * N * sizeof(int) + N * sizeof(double) + 768;
   b += (size_t)(N < kCompact ? N : kCompact) * 64 * sizeof(float) + 256;
   b += (3 * (kNB + 1) + kNB) * sizeof(int);
   b += sizeof(double) * (64 + 6 * (size_t)(m + 1) * (m + 1) + 4 * m + 64);
@@ -1549,7 +1927,7 @@ size_t odeim_ws_bytes(int64_t N, int m) {
   b += sizeof(double) * (5 * 64 * 64 + 3 * 64) + sizeof(R1Work) + 16 * 256;
   b += sizeof(double) * (2 * (m + 1) * (m + 1) + 512) + 3 * 256;
   b += sizeof(double) * (2 * 64 * 64 + 64) + 3 * 256;
-  b += sizeof(float) * (64 * 64 + 128) + 256;
+  b += sizeof(float) * kW32 + 256;
   return b + 4096;
 }
 
@@ -1566,6 +1944,8 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.nrm = (float*)take(N * sizeof(float));
   o.ord = (int*)take(N * sizeof(int));
   o.list = (int*)take(N * sizeof(int));
+  o.cand = (int*)take(N * sizeof(int));
+  o.xlist = (int*)take(N * sizeof(int));
   o.rows = (float*)take((size_t)(N < kCompact ? N : kCompact) * 64 * sizeof(float));
   o.bkt = (unsigned char*)take(N);
   o.picked = (unsigned char*)take(N);
@@ -1590,10 +1970,10 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.jbuf = (double*)take(((size_t)2 * (m + 1) * (m + 1) + 512) * sizeof(double));
   o.jscale = (double*)take(64);
   o.jflag = (int*)take(64);
-  o.Lf = (double*)take((size_t)64 * 64 * sizeof(double));
-  o.Uf = (double*)take((size_t)64 * 64 * sizeof(double));
+  o.Li = (double*)take((size_t)64 * 64 * sizeof(double));
+  o.Ui = (double*)take((size_t)64 * 64 * sizeof(double));
   o.yv = (double*)take(64 * sizeof(double));
-  o.wt32 = (float*)take((64 * 64 + 128) * sizeof(float));
+  o.wt32 = (float*)take(kW32 * sizeof(float));
   return o;
 }
 
@@ -1671,20 +2051,17 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   // DEIM.  The kernels of both greedy loops start with pdl_enter() and are
   // launched with programmatic stream serialization (pdl()): each is
   // scheduled while its predecessor runs and waits for it on the device.
-  const size_t dsmem = sizeof(double) * 2 * 64 * 65;
-  smem_at_least((const void*)k_deim_solve<T>, dsmem);
+  // A step is two passes; the second pass's last CTA picks the point and
+  // forms the next step's coefficients.
   auto deim_loop = [&]() {
-  for (int l = 0; l < m; ++l) {
-    pdl(k_deim_solve<T>, 1, 256, dsmem, s, phi, N, l, pts, o.Lf, o.Uf, o.yv, o.cvec, o.ctl);
-    pdl(k_deim_score<T>, (probe + 255) / 256, 256, 0, s, phi, N, l, o.cvec, o.ord, o.picked, 0,
-        probe, o.ctl, o.scores, o.rows, C);
-    pdl(k_deim_plan, 1, 256, 0, s, o.ctl, o.bmax, o.bstart, probe, tie_tol);
-    pdl(k_deim_score<T>, 152 * 8, 256, 0, s, phi, N, l, o.cvec, o.ord, o.picked, probe, -1,
-        o.ctl, o.scores, o.rows, C);
-    pdl(k_argmin_tie, 152 * 4, 256, 0, s, o.scores, o.ord, o.ctl, tie_tol);
-    pdl(k_commit, 1, 1, 0, s, o.ctl, l, pts, o.picked);
-    if (l + 1 < m) pdl(k_deim_extend<T>, 1, 256, 0, s, phi, N, l, o.ctl, o.Lf, o.Uf, o.yv);
-  }
+    cudaMemsetAsync(o.Li, 0, (size_t)64 * 64 * sizeof(double), s);
+    cudaMemsetAsync(o.Ui, 0, (size_t)64 * 64 * sizeof(double), s);
+    for (int l = 0; l < m; ++l) {
+      pdl(k_deim_probe<T>, (probe + 15) / 16, 64, 0, s, phi, N, l, o.cvec, o.ord, o.picked,
+          probe, o.bmax, o.bstart, tie_tol, o.ctl, o.scores, o.cand, o.rows, C);
+      pdl(k_deim_rest<T>, 152 * 8, 256, 0, s, phi, N, l, m, o.cvec, o.ord, o.picked, probe,
+          tie_tol, o.ctl, o.scores, o.cand, o.rows, C, pts, o.Li, o.Ui, o.yv, o.cvec);
+    }
   };
   if (graphs)
     run_graphed(&graphs->deim, s, deim_loop);
@@ -1698,7 +2075,6 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   // ODEIM oversampling
   const int n = m % 2 ? m + 1 : m;  // Jacobi wants an even order
   k_odeim_gram<T><<<(m + 3) / 4, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
-  const size_t smem_pb = sizeof(double) * ((size_t)64 * kLdw + 64 + 64 + 4 * 64 + 64);
   const size_t smem_ex = sizeof(double) * ((size_t)64 * kLdw + 64 + 4 * 64 + 2 * 64 + 4 * 64);
   M_(12);
   // eigensystem of M: pivoted Cholesky + one-sided Jacobi; two-sided
@@ -1719,49 +2095,44 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     k_odeim_sort<<<1, 256, 0, HY_S(s)>>>(o.lam, o.V, n, m, o.lam_s, o.W_s, o.ctl, o.wt32);
   }
   M_(-13);
-  // sub-stage marks only where the loop is not replayed from a graph
+  // sub-stage marks only where the loop is not replayed from a graph (no
+  // slot, or the legacy default stream, which cannot be captured)
   auto ML_ = [&](int id) {
-    if (mark && !graphs) mark(mark_arg, id);
+    if (mark && (!graphs || s == 0)) mark(mark_arg, id);
   };
+  smem_at_least((const void*)k_odeim_exact<T>, smem_ex);
+  // A step is four scoring passes (the last picks the point and prepares
+  // the update) and the three of the eigensystem update.
   auto over_loop = [&]() {
-  for (int l = m; l < np; ++l) {
-    ML_(13);
-    // full FP32 bounds of the largest-norm rows, exact score of the best
-    pdl(k_odeim_screen<T>, (probe + 7) / 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked,
-        0, probe, (const int*)nullptr, o.ctl, o.scores, o.rows, C);
-    pdl(k_odeim_probe_best<T>, 1, 256, smem_pb, s, phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
-    pdl(k_odeim_plan, 1, 256, 0, s, o.ctl, o.bmax, o.bstart, probe, tie_tol);
-    ML_(-14);
-    ML_(14);
-    // the other rows whose norm can reach the best score: the z_1 bound for
-    // all, the full bound for those it does not exclude
-    pdl(k_odeim_z1<T>, 152 * 8, 256, 0, s, phi, N, m, o.W_s, o.nrm, o.ord, o.picked, probe,
-        tie_tol, o.ctl, o.scores, o.list, o.rows, C);
-    pdl(k_odeim_screen<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked, 0, -1,
-        (const int*)o.list, o.ctl, o.scores, o.rows, C);
-    pdl(k_odeim_probe_best<T>, 1, 256, smem_pb, s, phi, N, m, o.lam_s, o.W_s, o.ord, o.ctl);
-    ML_(-15);
-    ML_(15);
-    pdl(k_odeim_exact<T>, 152, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, o.ord, probe,
-        o.list, tie_tol, o.ctl, o.scores);
-    ML_(-16);
-    ML_(17);
-    pdl(k_argmin_tie, 152 * 4, 256, 0, s, o.scores, o.ord, o.ctl, tie_tol);
-    pdl(k_commit, 1, 1, 0, s, o.ctl, l, pts, o.picked);
-    ML_(-18);
-    if (l + 1 < np) {
-      ML_(16);
-      pdl(k_r1_prepare<T>, 1, 256, 0, s, phi, N, m, o.ctl, o.lam_s, o.W_s, o.Wrot, o.r1);
-      pdl(k_r1_roots, m, 32, 0, s, o.r1, o.Delta);
-      pdl(k_r1_loewner, (m + 3) / 4, 128, 0, s, o.r1, o.Delta);
-      pdl(k_r1_vectors, m, 256, 0, s, o.r1, o.Delta, o.Wrot, m, o.Wnew, o.lamnew);
-      pdl(k_r1_merge, 1, 256, 0, s, o.r1, o.Wrot, o.Wnew, o.lamnew, m, o.lam_s2, o.W_s2, o.ctl,
-          o.wt32);
-      std::swap(o.lam_s, o.lam_s2);
-      std::swap(o.W_s, o.W_s2);
-      ML_(-17);
+    for (int l = m; l < np; ++l) {
+      ML_(13);
+      pdl(k_odeim_probe<T>, (probe + 7) / 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord,
+          o.picked, probe, o.bmax, o.bstart, tie_tol, o.ctl, o.scores, o.rows, C);
+      ML_(-14);
+      ML_(14);
+      pdl(k_odeim_z1<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked, probe,
+          tie_tol, o.ctl, o.scores, o.list, o.rows, C);
+      ML_(-15);
+      ML_(17);
+      pdl(k_odeim_screen<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.list, probe,
+          tie_tol, o.ctl, o.scores, o.xlist, o.rows, C);
+      ML_(-18);
+      ML_(15);
+      pdl(k_odeim_exact<T>, 152, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, o.ord,
+          o.xlist, tie_tol, o.ctl, o.scores, o.cand, l, np, pts, o.picked, o.rows, C, o.r1,
+          o.Wrot);
+      ML_(-16);
+      if (l + 1 < np) {
+        ML_(16);
+        pdl(k_r1_roots, m, 32, 0, s, o.r1, o.Delta);
+        pdl(k_r1_loewner, (m + 3) / 4, 128, 0, s, o.r1, o.Delta);
+        pdl(k_r1_vectors, m, 256, 0, s, o.r1, o.Delta, o.Wrot, m, o.lam_s2, o.W_s2, o.ctl,
+            o.wt32);
+        std::swap(o.lam_s, o.lam_s2);
+        std::swap(o.W_s, o.W_s2);
+        ML_(-17);
+      }
     }
-  }
   };
   if (graphs)
     run_graphed(&graphs->over, s, over_loop);

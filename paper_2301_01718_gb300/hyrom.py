@@ -205,7 +205,7 @@ def hyrom_kernel_launches():
 
 STAGES = ["full", "partial", "gappy", "recon", "filter", "select", "gram", "eig", "formphi",
           "odeim", "masks", "deim", "od_init", "od_probe", "od_screen", "od_exact",
-          "od_update", "od_pick", "snormal"]
+          "od_update", "od_list", "snormal"]
 
 
 def hyrom_profile(ctx, on=True):
