@@ -833,252 +833,6 @@ HY_DEV void z_block(const double* W, int ldw, const double* rb, int m, double* z
 // reaches the limit get the exact score.  The last pass also picks the point
 // and prepares the eigensystem update.
 
-HY_DEV float warp_sum_rd(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return __shfl_sync(0xffffffffu, v, 0);
-}
-HY_DEV float warp_sum_ru(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return __shfl_sync(0xffffffffu, v, 0);
-}
-
-// The step's eigensystem in FP32, staged by every CTA of the screening
-// passes: Wt[a][j] = W_ja (zero padded), the shifted poles d_j rounded to
-// nearest, upward and downward (+inf for j = 0 and j >= m).
-struct ScreenSm {
-  float Wt[64][64];
-  float dn[64], du[64], dd[64];
-  float en[64], eu[64], ed[64], d2[4];
-  float ph[8][64];
-};
-
-HY_DEV void stage_screen(const float* __restrict__ wt32, int m, ScreenSm& S) {
-  const float4* src = reinterpret_cast<const float4*>(wt32);
-  float4* dst = reinterpret_cast<float4*>(&S.Wt[0][0]);
-  for (int i = threadIdx.x; i < m * 16; i += blockDim.x) dst[i] = src[i];
-  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-    S.dn[j] = wt32[4096 + j];
-    S.du[j] = wt32[4096 + 64 + j];
-    S.dd[j] = wt32[4096 + 128 + j];
-    S.en[j] = wt32[4096 + 192 + j];
-    S.eu[j] = wt32[4096 + 256 + j];
-    S.ed[j] = wt32[4096 + 320 + j];
-  }
-  if (threadIdx.x < 3) S.d2[threadIdx.x] = wt32[4096 + 384 + threadIdx.x];
-}
-
-// Both certified bounds of one row's exact score, U >= mu >= L (one warp;
-// the row's FP32 values in pr[0..64), zero beyond m; nrm_i its squared-norm
-// bound).  The root is approached in the coordinates of the nearer pole
-// (the sign of the secular function at the midpoint of (l1, l2) tells
-// which): tau = mu - l1 as above, or sigma = l2 - mu, where
-//   f(sigma) = 1 + sum_j z_j^2 / (e_j + sigma),  e_j = lam_j - l2,
-// is decreasing on (0, l2 - l1) (the j = 1 term is the negative one), so a
-// certified lower bound f_lo(s) >= 0 proves sigma >= s (mu <= l2 - s) and a
-// certified upper bound f_hi(s) <= 0 proves sigma <= s.  The greedy's best
-// rows lift lambda_min to just below l2, where only these coordinates
-// resolve sigma: in tau the bounds would stop at l2 itself.
-HY_DEV void screen_row(const ScreenSm& S, int m, double l1, double l2, const float* pr,
-                       float nrm_i, double& U, double& L) {
-  const int lane = threadIdx.x & 31;
-  float z0 = 0.f, z1 = 0.f;
-#pragma unroll 8
-  for (int a = 0; a < m; ++a) {
-    const float x = pr[a];
-    z0 = fmaf(S.Wt[a][lane], x, z0);
-    z1 = fmaf(S.Wt[a][lane + 32], x, z1);
-  }
-  const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm_i));
-  const float zf = __shfl_sync(0xffffffffu, z0, 0);
-  const float b1 = __fadd_ru(fabsf(zf), dl);
-  const float b1s = __fmul_ru(b1, b1);
-  const float B1 = fmaxf(__fsub_rd(fabsf(zf), dl), 0.f);
-  const float B1s = __fmul_rd(B1, B1);
-  // bounds of z_j^2 (j >= 2) from below (a) and above (c); lane 0's first
-  // slot is z_1 itself
-  float a0 = lane == 0 ? 0.f : fmaxf(__fsub_rd(fabsf(z0), dl), 0.f);
-  float a1 = fmaxf(__fsub_rd(fabsf(z1), dl), 0.f);
-  a0 = __fmul_rd(a0, a0);
-  a1 = __fmul_rd(a1, a1);
-  float c0 = lane == 0 ? 0.f : __fadd_ru(fabsf(z0), dl);
-  float c1 = __fadd_ru(fabsf(z1), dl);
-  c0 = __fmul_ru(c0, c0);
-  c1 = __fmul_ru(c1, c1);
-  U = fmin(__dadd_ru(l1, (double)b1s), l2);
-  L = l1;
-  if (m == 1) {
-    L = __dadd_rd(l1, (double)B1s);
-    return;
-  }
-  const float d2n = S.dn[1], d2u = S.du[1], d2d = S.dd[1];
-  if (!(d2n > 0.f)) return;  // a double eigenvalue: mu = l1
-  const float E0 = S.en[lane], E1 = S.en[lane + 32];
-  const float qn0 = z0 * z0, qn1 = z1 * z1;
-  const float hm = 0.5f * d2n;
-  const float fmid = 1.f + warp_sum(__fdividef(qn0, E0 + hm) + __fdividef(qn1, E1 + hm));
-  if (fmid >= 0.f) {
-    // the root in (l1, mid]: tau coordinates
-    const float dn0 = S.dn[lane], dn1 = S.dn[lane + 32], du0 = S.du[lane], du1 = S.du[lane + 32];
-    const float dd0 = S.dd[lane], dd1 = S.dd[lane + 32];
-    float t = 0.f, lo = 0.f, hi = fminf(d2n, b1s);
-    float g = warp_sum(__fdividef(a0, dn0) + __fdividef(a1, dn1));
-    float dg = warp_sum(__fdividef(a0, dn0 * dn0) + __fdividef(a1, dn1 * dn1));
-    for (int it = 0; it < 16; ++it) {
-      if (it > 0) {
-        const float r0 = __frcp_rn(dn0 - t), r1 = __frcp_rn(dn1 - t);
-        const float q0 = a0 * r0, q1 = a1 * r1;
-        g = warp_sum(q0 + q1);
-        dg = warp_sum(fmaf(q0, r0, q1 * r1));
-        const float h = fmaf(t, 1.f + g, -b1s);
-        if (fabsf(h) <= 32.f * 1.1920929e-7f * (t * (1.f + g) + b1s)) break;
-        if (h < 0.f)
-          lo = t;
-        else
-          hi = t;
-      }
-      const float gap = d2n - t;
-      const float C = 1.f + (g - dg * gap);
-      const float B = C * d2n + b1s + dg * gap * gap;
-      const float nt = __fdividef(2.f * b1s * d2n, B + fsqrt_fast(fmaxf(B * B - 4.f * C * b1s * d2n, 0.f)));
-      if (it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t) {
-        t = nt;
-        break;
-      }
-      t = (nt > lo && nt < hi) ? nt : 0.5f * (lo + hi);
-    }
-    // certify h_L(t') >= 0: t' 3e-5 above the iterate, else 5e-4
-    for (int tr = 0; tr < 2; ++tr) {
-      const float tu = __fmul_ru(t, tr == 0 ? 1.f + 1.0f / 32768.f : 1.f + 1.0f / 2048.f);
-      if (!(tu < d2u)) break;
-      const float Sl = warp_sum_rd(__fadd_rd(__fmul_rd(a0, __frcp_rd(__fsub_ru(du0, tu))),
-                                             __fmul_rd(a1, __frcp_rd(__fsub_ru(du1, tu)))));
-      const float hl = __fsub_rd(__fmul_rd(tu, __fadd_rd(1.f, Sl)), b1s);
-      if (hl >= 0.f) {
-        U = fmin(U, __dadd_ru(l1, (double)tu));
-        break;
-      }
-    }
-    // certify h_U(t') <= 0 below the iterate (the root of h_U lies below it)
-    if (!(B1s > 0.f)) return;
-    for (int tr = 0; tr < 3; ++tr) {
-      const float td = __fmul_rd(t, tr == 0 ? 1.f - 1.0f / 32768.f
-                                            : (tr == 1 ? 1.f - 1.0f / 2048.f : 1.f - 1.0f / 128.f));
-      if (!(td > 0.f && td < d2d)) continue;
-      const float Su = warp_sum_ru(__fadd_ru(__fmul_ru(c0, __frcp_ru(__fsub_rd(dd0, td))),
-                                             __fmul_ru(c1, __frcp_ru(__fsub_rd(dd1, td)))));
-      const float hu = __fsub_ru(__fmul_ru(td, __fadd_ru(1.f, Su)), B1s);
-      if (hu <= 0.f) {
-        L = __dadd_rd(l1, (double)td);
-        return;
-      }
-    }
-    return;
-  }
-  // the root in (mid, l2): sigma = -t, two-pole model steps in t around the
-  // poles e_1 = -d2 and e_2 = 0 (the root solver's FP32 steps)
-  const float fe = 1.1920929e-7f;
-  const float fdelj = -d2n;
-  float ft = -0.5f * hm, flo = -hm, fhi = 0.f;
-  for (int it = 0; it < 16; ++it) {
-    const float r0 = __frcp_rn(E0 - ft), r1 = __frcp_rn(E1 - ft);
-    const float q0 = qn0 * r0, q1 = qn1 * r1;
-    // the j = 1 term (lane 0's first) is the only negative one and the only
-    // one left of the root: its value and slope come by a shuffle, and
-    // sum |q| = (f - 1) - 2 q_1
-    const float ql = __shfl_sync(0xffffffffu, q0, 0), rl = __shfl_sync(0xffffffffu, r0, 0);
-    const float ff = 1.f + warp_sum(q0 + q1);
-    const float dps = ql * rl;
-    const float dph = warp_sum((lane == 0 ? 0.f : q0 * r0) + q1 * r1);
-    const float fa = (ff - 1.f) - 2.f * ql;
-    if (fabsf(ff) <= 8.f * fe * (1.f + fa + fabsf(ft) * (dps + dph))) break;
-    if (ff < 0.f)
-      flo = ft;
-    else
-      fhi = ft;
-    if (fhi - flo <= 2.f * fe * fmaxf(fabsf(fhi), fabsf(flo))) {
-      ft = 0.5f * (flo + fhi);
-      break;
-    }
-    const float Dj = fdelj - ft, Dn = -ft;
-    const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
-    const float A = ff - dps * Dj - dph * Dn;
-    const float B = A * (Dj + Dn) + sL + sR;
-    const float Cq = ff * Dj * Dn;
-    float eta = NAN;
-    if (A == 0.f) {
-      if (B != 0.f) eta = __fdividef(Cq, B);
-    } else {
-      const float qq = 0.5f * (B + copysignf(fsqrt_fast(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
-      const float e1 = __fdividef(qq, A), e2 = qq != 0.f ? __fdividef(Cq, qq) : NAN;
-      if (e1 > Dj && e1 < Dn) eta = e1;
-      if (e2 > Dj && e2 < Dn) eta = e2;
-    }
-    float nt = ft + eta;
-    if (fabsf(nt - ft) <= 2.f * fe * fabsf(ft)) {
-      ft = nt;
-      break;
-    }
-    if (!(nt > flo && nt < fhi)) nt = 0.5f * (flo + fhi);
-    ft = nt;
-  }
-  const float sg = -ft;
-  if (!(sg > 0.f)) return;
-  const float eu0 = S.eu[lane], eu1 = S.eu[lane + 32], ed0 = S.ed[lane], ed1 = S.ed[lane + 32];
-  // sigma scales with z_2^2 (and with z_1^2 through the negative term),
-  // whose FP32 errors are about 2 dl / |z_2| and 2 dl / |z_1| relative: the
-  // first margin tried is three times that, the second four times more
-  const float z2a = fabsf(__shfl_sync(0xffffffffu, z0, 1));
-  const float kap = fminf(__fdividef(6.f * dl, fmaxf(z2a, 1e-30f)) +
-                              __fdividef(6.f * dl, fmaxf(fabsf(zf), 1e-30f)) + 1.0f / 32768.f,
-                          0.5f);
-  // U: f_lo(s) >= 0 at s below the iterate (z_1^2 from above in the
-  // negative term, the others from below); a / b from below as
-  // a * rcp_rd(b) rounded down, from above as a * rcp_ru(b) rounded up
-  for (int tr = 0; tr < 2; ++tr) {
-    const float sl = __fmul_rd(sg, 1.f - (tr == 0 ? kap : fminf(4.f * kap, 0.75f)));
-    if (!(sl > 0.f)) continue;
-    const float t0 = lane == 0 ? -__fmul_ru(b1s, __frcp_ru(__fsub_rd(d2d, sl)))
-                               : __fmul_rd(a0, __frcp_rd(__fadd_ru(eu0, sl)));
-    const float t1 = __fmul_rd(a1, __frcp_rd(__fadd_ru(eu1, sl)));
-    const float flo_ = __fadd_rd(1.f, warp_sum_rd(__fadd_rd(t0, t1)));
-    if (flo_ >= 0.f) {
-      U = fmin(U, __dsub_ru(l2, (double)sl));
-      break;
-    }
-  }
-  // L: f_hi(s) <= 0 at s above the iterate, relatively, then by a fraction
-  // of l2 - l1 (sigma is not resolved when z_2 is below the FP32 error of
-  // the screen; l2 - s is then still a bound as good as tau's)
-  for (int tr = 0; tr < 3; ++tr) {
-    const float su = tr == 0 ? __fmul_ru(sg, 1.f + kap)
-                             : (tr == 1 ? __fmul_ru(sg, 1.f + 4.f * kap)
-                                        : __fadd_ru(sg, __fmul_ru(d2u, 1.0f / 32768.f)));
-    if (!(su < d2d)) continue;
-    const float t0 = lane == 0 ? -__fmul_rd(B1s, __frcp_rd(__fsub_ru(d2u, su)))
-                               : __fmul_ru(c0, __frcp_ru(__fadd_rd(ed0, su)));
-    const float t1 = __fmul_ru(c1, __frcp_ru(__fadd_rd(ed1, su)));
-    const float fhi_ = __fadd_ru(1.f, warp_sum_ru(__fadd_ru(t0, t1)));
-    if (fhi_ <= 0.f) {
-      L = fmax(L, __dsub_rd(l2, (double)su));
-      break;
-    }
-  }
-}
-
-// One warp loads ordered row pos of Phi as FP32 into pr[0..64).
-template <typename T>
-HY_DEV void load_row32(const T* __restrict__ phi, int64_t N, int m, int i, int pos,
-                       const float* __restrict__ R, int C, float* pr) {
-  const int lane = threadIdx.x & 31;
-  if (pos < C) {
-    pr[lane] = R[(int64_t)pos * 64 + lane];
-    pr[lane + 32] = R[(int64_t)pos * 64 + lane + 32];
-  } else {
-    pr[lane] = lane < m ? (float)phi[(int64_t)lane * N + i] : 0.f;
-    pr[lane + 32] = lane + 32 < m ? (float)phi[(int64_t)(lane + 32) * N + i] : 0.f;
-  }
-  __syncwarp();
-}
 
 // stage a CTA's copy of W (m x m, column j = eigenvector j) with an odd
 // leading dimension, and the eigenvalues
@@ -1107,55 +861,6 @@ HY_DEV double limit_of(const OdCtl* ctl, double tie_tol) {
   const unsigned long long a = *(const volatile unsigned long long*)&ctl->smax;
   const unsigned long long b = *(const volatile unsigned long long*)&ctl->slo;
   return bitsd(a > b ? a : b) * (1.0 - 2.0 * tie_tol);
-}
-
-// Pass 1: both bounds of the probe rows [0, probe), one warp per row; the
-// best L raises the limit.  The CTA that finishes last sets the rows the
-// next pass takes: mu - l1 <= z_1^2 <= |phi_i|^2, so only rows with
-// |phi_i|^2 >= lim - l1 can reach the limit.
-template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_probe(
-    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
-    const float* __restrict__ nrm, const int* __restrict__ ord,
-    const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
-    const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
-    const float* __restrict__ R, int C) {
-  pdl_enter();
-  __shared__ __align__(16) ScreenSm S;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double l1 = ctl->lam1, l2 = ctl->lam2;
-  stage_screen(wt32, m, S);
-  __syncthreads();
-  float* pr = S.ph[wid];
-  unsigned long long bestL = 0ull, cnt = 0;
-  for (int t0 = blockIdx.x * nw + wid; t0 < probe; t0 += gridDim.x * nw) {
-    const int pos = t0;
-    const int i = ord[pos];
-    if (picked[i]) {
-      if (lane == 0) scores[pos] = -1.0;
-      continue;
-    }
-    load_row32<T>(phi, N, m, i, pos, R, C, pr);
-    double U, L;
-    screen_row(S, m, l1, l2, pr, nrm[i], U, L);
-    __syncwarp();
-    if (lane == 0) {
-      scores[pos] = U;
-      ++cnt;
-      bestL = dbits(L) > bestL ? dbits(L) : bestL;
-    }
-  }
-  bestL = block_max_u64(bestL);
-  if (threadIdx.x == 0 && bestL) atomicMax(&ctl->slo, bestL);
-  if (lane == 0 && cnt) atomicAdd(&ctl->stat[1], cnt);
-  if (!last_block(&ctl->ticket)) return;
-  const double lim = limit_of(ctl, tie_tol);
-  const int n = plan_end(bmax, bstart, probe, (lim - l1) / (1.0 + 1e-5));
-  if (threadIdx.x == 0) {
-    ctl->n_c = n;
-    ctl->ticket = 0u;
-    ctl->stat[3] += 1;
-  }
 }
 
 // Pass 2a, one thread per ordered row in [probe, n_c): bounds from z_1 and
@@ -1248,24 +953,387 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
   }
 }
 
-// Pass 2b, one warp per row listed by pass 2a: both full bounds (U replaces
-// the row's score); every L raises the limit.  The rows whose U reaches the
-// limit of the time, and the probe rows whose U does, are listed in xlist
-// for the exact pass.
+// ---- certified bounds, eight lanes per row ----------------------------------
+//
+// The probe pass and the full-bound pass take their rows in tiles of kTile
+// rows per CTA of kTile * kGrp threads: the tile's rows are gathered
+// (row-major FP32, 256 contiguous bytes each) into shared memory, z = W^T phi
+// of every row is formed as a small matrix product (thread: one row, eight
+// components), and then the kGrp lanes of a row certify its bounds, lane g
+// taking the components j = g mod kGrp and the sums closing with three
+// shuffles.  A warp per row spent most of its time in five-level shuffle
+// sums; a thread per row in long dependent chains.
+
+constexpr int kTile = 32;        // rows per CTA
+constexpr int kGrp = 8;          // lanes per row
+constexpr int kTileThreads = kTile * kGrp;
+constexpr int kTileLd = 65;      // odd row stride of the tile in shared memory
+
+struct TileSm {
+  float Wt[64][64];
+  float dn[64], du[64], dd[64];
+  float en[64], eu[64], ed[64], d2[4];
+  float zt[kTile * kTileLd];     // the rows, then their z
+  int pos[kTile], row[kTile];
+  float nrm[kTile];
+};
+
+HY_DEV void stage_tile_tables(const float* __restrict__ wt32, int m, TileSm& S) {
+  const float4* src = reinterpret_cast<const float4*>(wt32);
+  float4* dst = reinterpret_cast<float4*>(&S.Wt[0][0]);
+  for (int i = threadIdx.x; i < m * 16; i += blockDim.x) dst[i] = src[i];
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    S.dn[j] = wt32[4096 + j];
+    S.du[j] = wt32[4096 + 64 + j];
+    S.dd[j] = wt32[4096 + 128 + j];
+    S.en[j] = wt32[4096 + 192 + j];
+    S.eu[j] = wt32[4096 + 256 + j];
+    S.ed[j] = wt32[4096 + 320 + j];
+  }
+  if (threadIdx.x < 3) S.d2[threadIdx.x] = wt32[4096 + 384 + threadIdx.x];
+}
+
+// The tile's rows (S.pos[r] >= 0; -1: no row) into S.zt, then their z in
+// place (zero beyond m).  blockDim.x == kTileThreads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_screen(
+HY_DEV void tile_z(const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ R,
+                   int C, TileSm& S) {
+  const int t = threadIdx.x;
+  for (int idx = t; idx < kTile * 16; idx += kTileThreads) {  // float4 k of row r
+    const int r = idx >> 4, k = idx & 15;
+    const int pos = S.pos[r];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pos >= 0) {
+      if (pos < C) {
+        v = reinterpret_cast<const float4*>(R + (int64_t)pos * 64)[k];
+      } else {
+        const int i = S.row[r];
+        const int a = 4 * k;
+        v.x = a < m ? (float)phi[(int64_t)a * N + i] : 0.f;
+        v.y = a + 1 < m ? (float)phi[(int64_t)(a + 1) * N + i] : 0.f;
+        v.z = a + 2 < m ? (float)phi[(int64_t)(a + 2) * N + i] : 0.f;
+        v.w = a + 3 < m ? (float)phi[(int64_t)(a + 3) * N + i] : 0.f;
+      }
+    }
+    float* d = S.zt + r * kTileLd + 4 * k;
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  }
+  __syncthreads();
+  const int r = t / kGrp, c0 = (t % kGrp) * 8;
+  float acc[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) acc[v] = 0.f;
+  for (int a = 0; a < m; ++a) {
+    const float x = S.zt[r * kTileLd + a];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] = fmaf(S.Wt[a][c0 + v], x, acc[v]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 8; ++v) S.zt[r * kTileLd + c0 + v] = c0 + v < m ? acc[v] : 0.f;
+  __syncthreads();
+}
+
+// Sums over a row's kGrp lanes (mask: the group's lanes); the group's first
+// lane's result is given to all, so that every lane takes the same branches.
+HY_DEV float grp_sum(float v, unsigned mask, int base) {
+#pragma unroll
+  for (int o = kGrp / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return __shfl_sync(mask, v, base);
+}
+HY_DEV float grp_sum_rd(float v, unsigned mask, int base) {
+#pragma unroll
+  for (int o = kGrp / 2; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(mask, v, o));
+  return __shfl_sync(mask, v, base);
+}
+HY_DEV float grp_sum_ru(float v, unsigned mask, int base) {
+#pragma unroll
+  for (int o = kGrp / 2; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(mask, v, o));
+  return __shfl_sync(mask, v, base);
+}
+
+// Both certified bounds, U >= mu >= L, of one row from its FP32 z (zr, m
+// values) and squared-norm bound, by one thread.  The root is approached in
+// the coordinates of the nearer pole (the sign of the secular function at
+// the midpoint of (l1, l2) tells which): tau = mu - l1 as above, or
+// sigma = l2 - mu, where
+//   f(sigma) = 1 + sum_j z_j^2 / (e_j + sigma),  e_j = lam_j - l2,
+// is decreasing on (0, l2 - l1) (the j = 1 term is the negative one), so a
+// certified lower bound f_lo(s) >= 0 proves sigma >= s (mu <= l2 - s) and a
+// certified upper bound f_hi(s) <= 0 proves sigma <= s.  The greedy's best
+// rows lift lambda_min to just below l2, where only these coordinates
+// resolve sigma: in tau the bounds would stop at l2 itself.  sigma scales
+// with z_2^2 (and z_1^2), whose FP32 errors are about 2 dl / |z_2| and
+// 2 dl / |z_1| relative: the first margin tried is three times that.
+HY_DEV void bounds_row(const TileSm& S, int m, double l1, double l2, const float* zr,
+                       float nrm_i, unsigned mask, int base, int g, double& U, double& L) {
+  const float dl = __fmul_ru(8e-6f, __fsqrt_ru(nrm_i));
+  const float zf = zr[0];
+  const float b1 = __fadd_ru(fabsf(zf), dl);
+  const float b1s = __fmul_ru(b1, b1);
+  const float B1 = fmaxf(__fsub_rd(fabsf(zf), dl), 0.f);
+  const float B1s = __fmul_rd(B1, B1);
+  U = fmin(__dadd_ru(l1, (double)b1s), l2);
+  L = l1;
+  if (m == 1) {
+    L = __dadd_rd(l1, (double)B1s);
+    return;
+  }
+  const float d2n = S.dn[1], d2u = S.du[1], d2d = S.dd[1];
+  if (!(d2n > 0.f)) return;  // a double eigenvalue: mu = l1
+  auto alo = [&](int j) {    // z_j^2 from below
+    const float x = fmaxf(__fsub_rd(fabsf(zr[j]), dl), 0.f);
+    return __fmul_rd(x, x);
+  };
+  auto chi = [&](int j) {    // z_j^2 from above
+    const float x = __fadd_ru(fabsf(zr[j]), dl);
+    return __fmul_ru(x, x);
+  };
+  const float hm = 0.5f * d2n;
+  float fm = 0.f;
+  for (int j = g; j < m; j += kGrp) fm += __fdividef(zr[j] * zr[j], S.en[j] + hm);
+  const float fmid = 1.f + grp_sum(fm, mask, base);
+  const int j1 = g == 0 ? kGrp : g;  // this lane's first component j >= 1
+  if (fmid >= 0.f) {
+    // the root in (l1, mid]: tau coordinates
+    float t = 0.f, lo = 0.f, hi = fminf(d2n, b1s);
+    float g0 = 0.f, dg0 = 0.f;
+    for (int j = j1; j < m; j += kGrp) {
+      const float a = alo(j), r = __fdividef(1.f, S.dn[j]);
+      g0 = fmaf(a, r, g0);
+      dg0 = fmaf(a * r, r, dg0);
+    }
+    float gs = grp_sum(g0, mask, base), dgs = grp_sum(dg0, mask, base);
+    for (int it = 0; it < 16; ++it) {
+      if (it > 0) {
+        float q0 = 0.f, d0 = 0.f;
+        for (int j = j1; j < m; j += kGrp) {
+          const float r = __frcp_rn(S.dn[j] - t);
+          const float q = alo(j) * r;
+          q0 += q;
+          d0 = fmaf(q, r, d0);
+        }
+        gs = grp_sum(q0, mask, base);
+        dgs = grp_sum(d0, mask, base);
+        const float h = fmaf(t, 1.f + gs, -b1s);
+        if (fabsf(h) <= 32.f * 1.1920929e-7f * (t * (1.f + gs) + b1s)) break;
+        if (h < 0.f)
+          lo = t;
+        else
+          hi = t;
+      }
+      const float gap = d2n - t;
+      const float C = 1.f + (gs - dgs * gap);
+      const float B = C * d2n + b1s + dgs * gap * gap;
+      const float nt =
+          __fdividef(2.f * b1s * d2n, B + fsqrt_fast(fmaxf(B * B - 4.f * C * b1s * d2n, 0.f)));
+      if (it > 0 && fabsf(nt - t) <= 4.f * 1.1920929e-7f * t) {
+        t = nt;
+        break;
+      }
+      t = (nt > lo && nt < hi) ? nt : 0.5f * (lo + hi);
+    }
+    for (int tr = 0; tr < 2; ++tr) {  // h_L(t') >= 0 above the iterate
+      const float tu = __fmul_ru(t, tr == 0 ? 1.f + 1.0f / 32768.f : 1.f + 1.0f / 2048.f);
+      if (!(tu < d2u)) break;
+      float sl = 0.f;
+      for (int j = j1; j < m; j += kGrp)
+        sl = __fadd_rd(sl, __fmul_rd(alo(j), __frcp_rd(__fsub_ru(S.du[j], tu))));
+      const float hl = __fsub_rd(__fmul_rd(tu, __fadd_rd(1.f, grp_sum_rd(sl, mask, base))), b1s);
+      if (hl >= 0.f) {
+        U = fmin(U, __dadd_ru(l1, (double)tu));
+        break;
+      }
+    }
+    if (!(B1s > 0.f)) return;
+    for (int tr = 0; tr < 3; ++tr) {  // h_U(t') <= 0 below the iterate
+      const float td = __fmul_rd(t, tr == 0 ? 1.f - 1.0f / 32768.f
+                                            : (tr == 1 ? 1.f - 1.0f / 2048.f : 1.f - 1.0f / 128.f));
+      if (!(td > 0.f && td < d2d)) continue;
+      float su = 0.f;
+      for (int j = j1; j < m; j += kGrp)
+        su = __fadd_ru(su, __fmul_ru(chi(j), __frcp_ru(__fsub_rd(S.dd[j], td))));
+      const float hu = __fsub_ru(__fmul_ru(td, __fadd_ru(1.f, grp_sum_ru(su, mask, base))), B1s);
+      if (hu <= 0.f) {
+        L = __dadd_rd(l1, (double)td);
+        return;
+      }
+    }
+    return;
+  }
+  // the root in (mid, l2): sigma = -t, model steps around the poles
+  // e_1 = -d2 and e_2 = 0
+  const float fe = 1.1920929e-7f;
+  const float fdelj = -d2n;
+  float ft = -0.5f * hm, flo = -hm, fhi = 0.f;
+  for (int it = 0; it < 16; ++it) {
+    const float r0 = __frcp_rn(S.en[0] - ft);
+    const float ql = zf * zf * r0;
+    float q0 = 0.f, d0 = 0.f;
+    for (int j = j1; j < m; j += kGrp) {
+      const float r = __frcp_rn(S.en[j] - ft);
+      const float q = zr[j] * zr[j] * r;
+      q0 += q;
+      d0 = fmaf(q, r, d0);
+    }
+    const float ff = 1.f + ql + grp_sum(q0, mask, base);
+    const float dph = grp_sum(d0, mask, base);
+    const float dps = ql * r0;
+    const float fa = (ff - 1.f) - 2.f * ql;
+    if (fabsf(ff) <= 8.f * fe * (1.f + fa + fabsf(ft) * (dps + dph))) break;
+    if (ff < 0.f)
+      flo = ft;
+    else
+      fhi = ft;
+    if (fhi - flo <= 2.f * fe * fmaxf(fabsf(fhi), fabsf(flo))) {
+      ft = 0.5f * (flo + fhi);
+      break;
+    }
+    const float Dj = fdelj - ft, Dn = -ft;
+    const float sL = dps * Dj * Dj, sR = dph * Dn * Dn;
+    const float A = ff - dps * Dj - dph * Dn;
+    const float B = A * (Dj + Dn) + sL + sR;
+    const float Cq = ff * Dj * Dn;
+    float eta = NAN;
+    if (A == 0.f) {
+      if (B != 0.f) eta = __fdividef(Cq, B);
+    } else {
+      const float qq = 0.5f * (B + copysignf(fsqrt_fast(fmaxf(B * B - 4.f * A * Cq, 0.f)), B));
+      const float e1 = __fdividef(qq, A), e2 = qq != 0.f ? __fdividef(Cq, qq) : NAN;
+      if (e1 > Dj && e1 < Dn) eta = e1;
+      if (e2 > Dj && e2 < Dn) eta = e2;
+    }
+    float nt = ft + eta;
+    if (fabsf(nt - ft) <= 2.f * fe * fabsf(ft)) {
+      ft = nt;
+      break;
+    }
+    if (!(nt > flo && nt < fhi)) nt = 0.5f * (flo + fhi);
+    ft = nt;
+  }
+  const float sg = -ft;
+  if (!(sg > 0.f)) return;
+  const float kap = fminf(__fdividef(6.f * dl, fmaxf(fabsf(zr[1]), 1e-30f)) +
+                              __fdividef(6.f * dl, fmaxf(fabsf(zf), 1e-30f)) + 1.0f / 32768.f,
+                          0.5f);
+  for (int tr = 0; tr < 2; ++tr) {  // U: f_lo(s) >= 0 below the iterate
+    const float sl = __fmul_rd(sg, 1.f - (tr == 0 ? kap : fminf(4.f * kap, 0.75f)));
+    if (!(sl > 0.f)) continue;
+    float part = 0.f;
+    for (int j = j1; j < m; j += kGrp)
+      part = __fadd_rd(part, __fmul_rd(alo(j), __frcp_rd(__fadd_ru(S.eu[j], sl))));
+    const float neg = __fmul_ru(b1s, __frcp_ru(__fsub_rd(d2d, sl)));
+    const float fl = __fadd_rd(__fsub_rd(1.f, neg), grp_sum_rd(part, mask, base));
+    if (fl >= 0.f) {
+      U = fmin(U, __dsub_ru(l2, (double)sl));
+      break;
+    }
+  }
+  for (int tr = 0; tr < 3; ++tr) {  // L: f_hi(s) <= 0 above the iterate
+    const float su = tr == 0 ? __fmul_ru(sg, 1.f + kap)
+                             : (tr == 1 ? __fmul_ru(sg, 1.f + 4.f * kap)
+                                        : __fadd_ru(sg, __fmul_ru(d2u, 1.0f / 32768.f)));
+    if (!(su < d2d)) continue;
+    float part = 0.f;
+    for (int j = j1; j < m; j += kGrp)
+      part = __fadd_ru(part, __fmul_ru(chi(j), __frcp_ru(__fadd_rd(S.ed[j], su))));
+    const float pos_ = __fmul_rd(B1s, __frcp_rd(__fsub_ru(d2u, su)));
+    const float fh = __fadd_ru(__fsub_ru(1.f, pos_), grp_sum_ru(part, mask, base));
+    if (fh <= 0.f) {
+      L = fmax(L, __dsub_rd(l2, (double)su));
+      break;
+    }
+  }
+}
+
+// Pass 1: both bounds of the probe rows [0, probe), a tile of kTile rows per
+// CTA; the best L raises the limit.  The CTA that finishes last sets the
+// rows the next pass takes: mu - l1 <= z_1^2 <= |phi_i|^2, so only rows
+// with |phi_i|^2 >= lim - l1 can reach the limit.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
+    const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
+    const float* __restrict__ R, int C) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char tsm[];
+  TileSm& S = *reinterpret_cast<TileSm*>(tsm);
+  const int t = threadIdx.x, r = t / kGrp, g = t % kGrp;
+  const int gbase = (t & 31) & ~(kGrp - 1);
+  const unsigned gmask = ((1u << kGrp) - 1u) << gbase;
+  const double l1 = ctl->lam1, l2 = ctl->lam2;
+  stage_tile_tables(wt32, m, S);
+  unsigned long long bestL = 0ull, cnt = 0;
+  for (int b0 = blockIdx.x * kTile; b0 < probe; b0 += gridDim.x * kTile) {
+    const int pos = b0 + r;
+    if (g == 0) {
+      int i = -1;
+      if (pos < probe) {
+        i = ord[pos];
+        if (picked[i]) {
+          scores[pos] = -1.0;
+          i = -1;
+        }
+      }
+      S.pos[r] = i >= 0 ? pos : -1;
+      S.row[r] = i;
+      S.nrm[r] = i >= 0 ? nrm[i] : 0.f;
+    }
+    __syncthreads();
+    tile_z<T>(phi, N, m, R, C, S);
+    if (S.pos[r] >= 0) {
+      double U, L;
+      bounds_row(S, m, l1, l2, S.zt + r * kTileLd, S.nrm[r], gmask, gbase, g, U, L);
+      if (g == 0) {
+        scores[pos] = U;
+        ++cnt;
+        bestL = dbits(L) > bestL ? dbits(L) : bestL;
+      }
+    }
+    __syncthreads();
+  }
+  bestL = block_max_u64(bestL);
+  cnt = block_sum(cnt);
+  if (t == 0) {
+    if (bestL) atomicMax(&ctl->slo, bestL);
+    if (cnt) atomicAdd(&ctl->stat[1], cnt);
+  }
+  if (!last_block(&ctl->ticket)) return;
+  const double lim = limit_of(ctl, tie_tol);
+  const int n = plan_end(bmax, bstart, probe, (lim - l1) / (1.0 + 1e-5));
+  if (t == 0) {
+    ctl->n_c = n;
+    ctl->ticket = 0u;
+    ctl->stat[3] += 1;
+  }
+}
+
+// Pass 2b: both full bounds of the rows pass 2a listed, a tile of kTile
+// rows per CTA (U replaces the row's score); the best L raises the limit.
+// The rows whose U reaches the limit of the time, and the probe rows whose
+// U does, are listed in xlist for the exact pass.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
     int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
     const float* __restrict__ R, int C) {
   pdl_enter();
-  __shared__ __align__(16) ScreenSm S;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char tsm[];
+  TileSm& S = *reinterpret_cast<TileSm*>(tsm);
+  const int t = threadIdx.x, lane = t & 31, r = t / kGrp, g = t % kGrp;
+  const int gbase = lane & ~(kGrp - 1);
+  const unsigned gmask = ((1u << kGrp) - 1u) << gbase;
   const int count = ctl->n_list;
   {  // the probe rows
     const double lim = limit_of(ctl, tie_tol);
-    for (int base = blockIdx.x * blockDim.x; base < probe; base += gridDim.x * blockDim.x) {
-      const int pos = base + threadIdx.x;
+    for (int base = blockIdx.x * kTileThreads; base < probe; base += gridDim.x * kTileThreads) {
+      const int pos = base + t;
       const bool x = pos < probe && scores[pos] >= lim;
       const unsigned bal = __ballot_sync(0xffffffffu, x);
       if (bal) {
@@ -1276,29 +1344,40 @@ __global__ void __launch_bounds__(256) k_odeim_screen(
       }
     }
   }
-  if ((int)blockIdx.x * nw >= count) return;  // no listed row for this CTA
+  if ((int)blockIdx.x * kTile >= count) return;  // no listed row for this CTA
   const double l1 = ctl->lam1, l2 = ctl->lam2;
-  stage_screen(wt32, m, S);
-  __syncthreads();
-  float* pr = S.ph[wid];
+  stage_tile_tables(wt32, m, S);
   unsigned long long bestL = 0ull, cnt = 0;
-  for (int t0 = blockIdx.x * nw + wid; t0 < count; t0 += gridDim.x * nw) {
-    const int pos = list[t0];
-    const int i = ord[pos];
-    load_row32<T>(phi, N, m, i, pos, R, C, pr);
-    double U, L;
-    screen_row(S, m, l1, l2, pr, nrm[i], U, L);
-    __syncwarp();
-    if (lane == 0) {
-      scores[pos] = U;
-      ++cnt;
-      bestL = dbits(L) > bestL ? dbits(L) : bestL;
-      if (U >= limit_of(ctl, tie_tol)) xlist[atomicAdd(&ctl->n_x, 1)] = pos;
+  for (int b0 = blockIdx.x * kTile; b0 < count; b0 += gridDim.x * kTile) {
+    if (g == 0) {
+      const int e = b0 + r;
+      const int pos = e < count ? list[e] : -1;
+      const int i = pos >= 0 ? ord[pos] : -1;
+      S.pos[r] = pos;
+      S.row[r] = i;
+      S.nrm[r] = i >= 0 ? nrm[i] : 0.f;
     }
+    __syncthreads();
+    tile_z<T>(phi, N, m, R, C, S);
+    const int pos = S.pos[r];
+    if (pos >= 0) {
+      double U, L;
+      bounds_row(S, m, l1, l2, S.zt + r * kTileLd, S.nrm[r], gmask, gbase, g, U, L);
+      if (g == 0) {
+        scores[pos] = U;
+        ++cnt;
+        bestL = dbits(L) > bestL ? dbits(L) : bestL;
+        if (U >= limit_of(ctl, tie_tol)) xlist[atomicAdd(&ctl->n_x, 1)] = pos;
+      }
+    }
+    __syncthreads();
   }
-  bestL = block_max_u64(bestL);  // one atomic per CTA on the shared limit
-  if (threadIdx.x == 0 && bestL) atomicMax(&ctl->slo, bestL);
-  if (lane == 0 && cnt) atomicAdd(&ctl->stat[1], cnt);
+  bestL = block_max_u64(bestL);
+  cnt = block_sum(cnt);
+  if (t == 0) {
+    if (bestL) atomicMax(&ctl->slo, bestL);
+    if (cnt) atomicAdd(&ctl->stat[1], cnt);
+  }
 }
 
 // ---- rank-one update of the eigensystem of M (one per oversampling step) ----
@@ -2106,16 +2185,17 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   auto over_loop = [&]() {
     for (int l = m; l < np; ++l) {
       ML_(13);
-      pdl(k_odeim_probe<T>, (probe + 7) / 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord,
-          o.picked, probe, o.bmax, o.bstart, tie_tol, o.ctl, o.scores, o.rows, C);
+      pdl(k_odeim_probe<T>, (probe + kTile - 1) / kTile, kTileThreads, sizeof(TileSm), s, phi,
+          N, m, o.wt32, o.nrm, o.ord, o.picked, probe, o.bmax, o.bstart, tie_tol, o.ctl,
+          o.scores, o.rows, C);
       ML_(-14);
       ML_(14);
       pdl(k_odeim_z1<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked, probe,
           tie_tol, o.ctl, o.scores, o.list, o.rows, C);
       ML_(-15);
       ML_(17);
-      pdl(k_odeim_screen<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.list, probe,
-          tie_tol, o.ctl, o.scores, o.xlist, o.rows, C);
+      pdl(k_odeim_screen<T>, 152 * 4, kTileThreads, sizeof(TileSm), s, phi, N, m, o.wt32,
+          o.nrm, o.ord, o.list, probe, tie_tol, o.ctl, o.scores, o.xlist, o.rows, C);
       ML_(-18);
       ML_(15);
       pdl(k_odeim_exact<T>, 152, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, o.ord,
