@@ -961,7 +961,8 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->fpart, 3 * 152 * 8 * sizeof(double));
   ok &= dal(ctx, &ctx->kbits, nw * 4);
   ok &= dal(ctx, &ctx->ftiles_a, (size_t)ntiles_max * sizeof(int));
-  ok &= dal(ctx, &ctx->ftiles_b, (size_t)ntiles_max * sizeof(int));
+  // the second tile list, then the filter's per-tile claim stamps
+  ok &= dal(ctx, &ctx->ftiles_b, (size_t)2 * ntiles_max * sizeof(int));
   ok &= dal(ctx, &ctx->fcounts, 64);
   ok &= dal(ctx, &ctx->fctl, 64);
   ok &= dalloc(ctx, &ctx->eps, nc * es);
@@ -1020,7 +1021,9 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   hyrom_status s = HYROM_OK;
   if (cudaMemcpy(ctx->ident, id.data(), id.size() * sizeof(double), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaMemset(ctx->H, 0, (size_t)ctx->nslot * ctx->nslot * sizeof(double)) != cudaSuccess) {
+      cudaMemset(ctx->H, 0, (size_t)ctx->nslot * ctx->nslot * sizeof(double)) != cudaSuccess ||
+      cudaMemset(ctx->ftiles_b, 0, (size_t)2 * ntiles_max * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->fctl, 0, 64) != cudaSuccess) {
     s = HYROM_ECUDA;
   }
   if (s == HYROM_OK) s = ctx->f32 ? init_state<float>(ctx, q0, q0_on_host)

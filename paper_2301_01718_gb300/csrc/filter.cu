@@ -40,10 +40,11 @@ struct Shapiro<3> {
   }
 };
 
-// ctl[0] = done, ctl[1] = passes run, ctl[2] = cells kept (running total)
-__global__ void k_gate_finalize(const double* __restrict__ part, int nblk, double eps_f,
-                                int* ctl) {
-  if (ctl[0]) return;
+// ctl[0] = done, ctl[1] = passes run, ctl[2] = cells kept (running total),
+// ctl[3] = CTAs of the current pass finished, ctl[4] = pass stamp.  The
+// pass's totals over its CTAs' partials (fixed order) and the stop test:
+// no cell kept, or the kept cells' decrease below eps_f of their total.
+__device__ void gate_close(const double* __restrict__ part, int nblk, double eps_f, int* ctl) {
   double cnt = 0.0, dec = 0.0, tot = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
     cnt += part[3 * i];
@@ -57,6 +58,8 @@ __global__ void k_gate_finalize(const double* __restrict__ part, int nblk, doubl
     ctl[1] += 1;
     ctl[2] += (int)cnt;
     if (cnt == 0.0 || dec < eps_f * tot) ctl[0] = 1;
+    ctl[3] = 0;
+    ctl[4] += 1;
   }
 }
 
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
                                                      const int* __restrict__ tiles,
                                                      const int* __restrict__ ntiles_dev,
                                                      int ntiles_all, double* __restrict__ part,
-                                                     const int* __restrict__ done) {
+                                                     int* __restrict__ ctl, double eps_f) {
   constexpr bool TWO = TY > 1;
   constexpr int H = NF + 1;
   constexpr int SX = TX + 2 * H, SY = TWO ? TY + 2 * H : 1;
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
   T* qs = reinterpret_cast<T*>(fsm);
   T* fx = qs + NV * SY * SX;
   T* gs = fx + NV * FY * FX;
-  if (*done) return;
+  if (*(volatile int*)ctl) return;
   const T* __restrict__ q = fa->q;
   const T* __restrict__ qp = fa->qp;
   const double t = fa->t;
@@ -437,31 +440,21 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
     part[3 * blockIdx.x + 1] = dec;
     part[3 * blockIdx.x + 2] = tot;
   }
-}
-
-// q = g on the kept cells of the listed tiles
-template <typename T>
-__global__ void k_filter_apply(DevCfg c, const FiltArgs<T>* __restrict__ fa, const T* __restrict__ gbuf,
-                               const uint32_t* __restrict__ kbits, int TX, int TY,
-                               const int* __restrict__ tiles, const int* __restrict__ ntiles_dev,
-                               int ntiles_all) {
-  const int tiles_x = (c.nx + TX - 1) / TX;
-  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
-  T* __restrict__ q = fa->q;
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int tile = tiles ? tiles[it] : it;
-    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-    for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-      const int gi = x0 + idx % TX, gj = y0 + idx / TX;
-      if (gi >= c.nx || gj >= c.ny) continue;
-      const int64_t cell = (int64_t)gj * c.nx + gi;
-      if (!bit_get(kbits, cell)) continue;
-      for (int v = 0; v < c.nvar; ++v) q[v * c.nc + cell] = gbuf[v * c.nc + cell];
-    }
+  // the CTA that finishes last closes the pass: the kept count, the stop
+  // test, and the stamp of the next tile search (ctl[3]: CTAs finished,
+  // ctl[4]: pass stamp)
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl[3], 1) == (int)gridDim.x - 1;
   }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  gate_close(part, gridDim.x, eps_f, ctl);
 }
 
-// tiles that contain a cell within box distance R of a kept cell
 // any bit set in [b, b + len) of the bitmap (len <= 64: at most 3 words)
 HY_DEV bool bits_any(const uint32_t* __restrict__ bm, int64_t b, int len) {
   const int64_t w0 = b >> 5;
@@ -481,59 +474,116 @@ HY_DEV bool bits_any(const uint32_t* __restrict__ bm, int64_t b, int len) {
   return acc != 0u;
 }
 
-// Tiles within R cells (x and y) of a kept cell, one warp per tile.
+// Whether tile t has a kept cell within R cells (x and y), by one warp.
 // Interior tiles: lane r reads neighbourhood row r (TY + 2R rows) as at most
 // three masked words of the bitmap, and a ballot combines the rows.  Tiles
 // whose neighbourhood crosses the domain edge (and 1D tiles, wider than 64
 // cells) take the per-cell path with the periodic wrap or the clip, their
 // cells spread over the lanes 32 at a time.
-__global__ void k_filter_next_tiles(DevCfg c, const uint32_t* __restrict__ kbits, int TX, int TY,
-                                    int R, int* __restrict__ tiles, int* __restrict__ ntiles,
-                                    const int* __restrict__ done) {
-  if (*done) return;
+HY_DEV bool tile_near_kept(const DevCfg& c, const uint32_t* __restrict__ kbits, int TX, int TY,
+                           int R, int t) {
   const int lane = threadIdx.x & 31;
-  const int tx = (c.nx + TX - 1) / TX, ty = (c.ny + TY - 1) / TY;
+  const int tx = (c.nx + TX - 1) / TX;
   const bool twoD = c.ny > 1;
   const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
   const int Ry = twoD ? R : 0;
   const int nrows = TY + 2 * Ry, ncols = TX + 2 * R;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tx * ty; t += warps) {
-    const int x0 = (t % tx) * TX, y0 = (t / tx) * TY;
-    const bool inx = x0 - R >= 0 && x0 + TX + R <= c.nx;
-    const bool iny = !twoD || (y0 - Ry >= 0 && y0 + TY + Ry <= c.ny);
-    bool any = false;
-    if (inx && iny && ncols <= 64 && nrows <= 32) {
+  const int x0 = (t % tx) * TX, y0 = (t / tx) * TY;
+  const bool inx = x0 - R >= 0 && x0 + TX + R <= c.nx;
+  const bool iny = !twoD || (y0 - Ry >= 0 && y0 + TY + Ry <= c.ny);
+  bool any = false;
+  if (inx && iny && ncols <= 64 && nrows <= 32) {
+    bool mine = false;
+    if (lane < nrows)
+      mine = bits_any(kbits, (int64_t)(twoD ? y0 - Ry + lane : 0) * c.nx + (x0 - R), ncols);
+    any = __any_sync(0xffffffffu, mine);
+  } else {
+    const int cells = nrows * ncols;
+    for (int e0 = 0; e0 < cells && !any; e0 += 32) {
       bool mine = false;
-      if (lane < nrows)
-        mine = bits_any(kbits, (int64_t)(twoD ? y0 - Ry + lane : 0) * c.nx + (x0 - R), ncols);
-      any = __any_sync(0xffffffffu, mine);
-    } else {
-      const int cells = nrows * ncols;
-      for (int e0 = 0; e0 < cells && !any; e0 += 32) {
-        bool mine = false;
-        const int e = e0 + lane;
-        if (e < cells) {
-          const int j = y0 - Ry + e / ncols, i = x0 - R + e % ncols;
-          int jj = 0, ii = i;
-          bool ok = true;
-          if (twoD) {
-            jj = j;
-            if (pery)
-              jj = imod(j, c.ny);
-            else if (j < 0 || j >= c.ny)
-              ok = false;
-          }
-          if (perx)
-            ii = imod(i, c.nx);
-          else if (i < 0 || i >= c.nx)
+      const int e = e0 + lane;
+      if (e < cells) {
+        const int j = y0 - Ry + e / ncols, i = x0 - R + e % ncols;
+        int jj = 0, ii = i;
+        bool ok = true;
+        if (twoD) {
+          jj = j;
+          if (pery)
+            jj = imod(j, c.ny);
+          else if (j < 0 || j >= c.ny)
             ok = false;
-          mine = ok && bit_get(kbits, (int64_t)jj * c.nx + ii);
         }
-        any = __any_sync(0xffffffffu, mine);
+        if (perx)
+          ii = imod(i, c.nx);
+        else if (i < 0 || i >= c.nx)
+          ok = false;
+        mine = ok && bit_get(kbits, (int64_t)jj * c.nx + ii);
       }
+      any = __any_sync(0xffffffffu, mine);
     }
-    if (any && lane == 0) tiles[atomicAdd(ntiles, 1)] = t;
+  }
+  return any;
+}
+
+// After a pass: q = g on its kept cells (the pass's tiles), and, when another
+// pass follows and the gate has not stopped, the tiles for it: those within
+// R = n + 1 cells of a kept cell.  After the first pass of an order every
+// tile is a candidate; after a sparse pass only the pass's tiles and their
+// eight neighbours can be (R is below the tile size and kept cells lie in
+// the pass's tiles), each claimed once through a per-tile stamp (the pass
+// stamp ctl[4]).
+template <typename T>
+__global__ void k_filter_apply_next(DevCfg c, const FiltArgs<T>* __restrict__ fa,
+                                    const T* __restrict__ gbuf, const uint32_t* __restrict__ kbits,
+                                    int TX, int TY, const int* __restrict__ tiles,
+                                    const int* __restrict__ ntiles_dev, int ntiles_all, int R,
+                                    int* __restrict__ nxt, int* __restrict__ nxt_n,
+                                    int* __restrict__ tstamp, const int* __restrict__ ctl,
+                                    int next) {
+  const int tiles_x = (c.nx + TX - 1) / TX, tiles_y = (c.ny + TY - 1) / TY;
+  const int ntiles = tiles ? *ntiles_dev : ntiles_all;
+  T* __restrict__ q = fa->q;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int tile = tiles ? tiles[it] : it;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
+      const int gi = x0 + idx % TX, gj = y0 + idx / TX;
+      if (gi >= c.nx || gj >= c.ny) continue;
+      const int64_t cell = (int64_t)gj * c.nx + gi;
+      if (!bit_get(kbits, cell)) continue;
+      for (int v = 0; v < c.nvar; ++v) q[v * c.nc + cell] = gbuf[v * c.nc + cell];
+    }
+  }
+  if (!next || ctl[0]) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (!tiles) {
+    for (int t = w0; t < ntiles_all; t += warps)
+      if (tile_near_kept(c, kbits, TX, TY, R, t) && lane == 0) nxt[atomicAdd(nxt_n, 1)] = t;
+    return;
+  }
+  const int stamp = ctl[4];
+  const bool twoD = c.ny > 1;
+  const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
+  const int nb = twoD ? 9 : 3;
+  for (int k = w0; k < ntiles * nb; k += warps) {
+    const int tile = tiles[k / nb], d = k % nb;
+    const int dx = twoD ? d % 3 - 1 : d - 1, dy = twoD ? d / 3 - 1 : 0;
+    int txi = tile % tiles_x + dx, tyi = tile / tiles_x + dy;
+    if (txi < 0 || txi >= tiles_x) {
+      if (!perx) continue;
+      txi = imod(txi, tiles_x);
+    }
+    if (tyi < 0 || tyi >= tiles_y) {
+      if (!pery) continue;
+      tyi = imod(tyi, tiles_y);
+    }
+    const int t = tyi * tiles_x + txi;
+    int first = 0;
+    if (lane == 0) first = atomicExch(&tstamp[t], stamp) != stamp;
+    if (!__shfl_sync(0xffffffffu, first, 0)) continue;  // claimed by another warp
+    if (tile_near_kept(c, kbits, TX, TY, R, t) && lane == 0) nxt[atomicAdd(nxt_n, 1)] = t;
   }
 }
 
@@ -548,6 +598,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
   const int nt = ((c.nx + TX - 1) / TX) * ((c.ny + TY - 1) / TY);
   const int64_t nwords = (c.nc + 31) / 32;
   FiltArgs<T>* fa = reinterpret_cast<FiltArgs<T>*>(fargs);
+  int* tstamp = tiles_b + nt;  // per-tile claim stamps (the buffer holds 2 nt)
   // shared-memory limits of the pass kernels, set outside any capture
   for (int o = 0; o < norders; ++o) {
     const int n = orders[o];
@@ -591,7 +642,7 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
   do {                                                                                       \
     constexpr size_t sm_ = filter_pass_smem<T, NV, NN, TXX, TYY>();                          \
     k_filter_pass<T, NV, NN, TXX, TYY><<<grid, 256, sm_, HY_S(s)>>>(                         \
-        c, fa, gbuf, kbits, cur, cur_n, nt, part, ctl);                                      \
+        c, fa, gbuf, kbits, cur, cur_n, nt, part, ctl, eps_f);                               \
   } while (0)
 #define HY_FP_N(NV, TXX, TYY) \
   do {                        \
@@ -609,17 +660,16 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
       }
 #undef HY_FP_N
 #undef HY_FP
-      k_gate_finalize<<<1, 256, 0, HY_S(s)>>>(part, grid, eps_f, ctl);
-      k_filter_apply<T><<<cur ? 152 * 8 : grid, 256, 0, HY_S(s)>>>(c, fa, gbuf, kbits, TX, TY, cur,
-                                                                   cur_n, nt);
+      const bool more = pass + 1 < jmax_f;
+      if (more) cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
       if (tape_keeps) {  // recording (direct launches only: not in the captured graph)
         k_tape_pass<T><<<1, 256, 0, HY_S(s)>>>(fa, kbits, nwords, n, ctl);
         k_tape_commit<T><<<1, 1, 0, HY_S(s)>>>(fa, ctl);
       }
-      if (pass + 1 < jmax_f) {
-        cudaMemsetAsync(nxt_n, 0, sizeof(int), s);
-        k_filter_next_tiles<<<(nt + 7) / 8, 256, 0, HY_S(s)>>>(c, kbits, TX, TY, n + 1, nxt,
-                                                               nxt_n, ctl);
+      k_filter_apply_next<T><<<152 * 8, 256, 0, HY_S(s)>>>(c, fa, gbuf, kbits, TX, TY, cur, cur_n,
+                                                           nt, n + 1, nxt, nxt_n, tstamp, ctl,
+                                                           more ? 1 : 0);
+      if (more) {
         cur = nxt;
         nxt = (nxt == tiles_a) ? tiles_b : tiles_a;
         int* tn = cur_n;
