@@ -23,11 +23,19 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-CONTRACTED = {"hdm_f32.cu"}   # files compiled with FMA contraction
+CONTRACTED = {"hdm_f32.cu", "filter_f32.cu"}   # files compiled with FMA contraction
+FAST_DIV = {"filter_f32.cu"}   # files with approximate FP32 division and square root
 
 
 def _fmad(src):
     return "-fmad=true" if os.path.basename(src) in CONTRACTED else "-fmad=false"
+
+
+def _arith(src):
+    f = [_fmad(src)]
+    if os.path.basename(src) in FAST_DIV:
+        f += ["-prec-div=false", "-prec-sqrt=false"]
+    return f
 
 
 def _nvcc():
@@ -59,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, _fmad(src), "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *_arith(src), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
