@@ -59,6 +59,12 @@ struct hyrom_ctx {
   AdjTape* tape = nullptr;  // set while hyrom_adjoint records its forward run
   DevCfg dc;
   cudaStream_t st = nullptr;
+  // the selection of G_{k+1} runs on st2 beside the basis rebuild's
+  // eigensolve (it reads the old basis; the new one is written after the
+  // join); sel_pending: a selection forked and not yet joined
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool sel_pending = false;
   int f32 = 0;
   size_t esz = 8;
   int64_t N = 0, nc = 0, nwords = 0;
@@ -319,16 +325,25 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
 }
 
 // ---- stage timers: events on the context stream around each stage ----------
-void t_begin(hyrom_ctx* c, int id) {
+void t_begin(hyrom_ctx* c, int id, cudaStream_t s) {
   if (!c->profile || c->ev_used[id] >= hyrom_ctx::kEvPairs) return;
-  cudaEventRecord(c->ev_a[id][c->ev_used[id]], c->st);
+  cudaEventRecord(c->ev_a[id][c->ev_used[id]], s);
   c->ev_open[id] = 1;
 }
-void t_end(hyrom_ctx* c, int id) {
+void t_end(hyrom_ctx* c, int id, cudaStream_t s) {
   if (!c->profile || !c->ev_open[id]) return;
-  cudaEventRecord(c->ev_b[id][c->ev_used[id]], c->st);
+  cudaEventRecord(c->ev_b[id][c->ev_used[id]], s);
   c->ev_used[id] += 1;
   c->ev_open[id] = 0;
+}
+void t_begin(hyrom_ctx* c, int id) { t_begin(c, id, c->st); }
+void t_end(hyrom_ctx* c, int id) { t_end(c, id, c->st); }
+
+// the rebuild's stream waits for a forked selection
+void join_select(hyrom_ctx* c) {
+  if (!c->sel_pending) return;
+  cudaStreamWaitEvent(c->st, c->ev_join, 0);
+  c->sel_pending = false;
 }
 // after a stream synchronisation: fold finished intervals into the totals
 void t_collect(hyrom_ctx* c) {
@@ -386,14 +401,19 @@ void gram_update(hyrom_ctx* c, int64_t step) {
 // Cholesky factor of the sample-row normal matrix.
 template <typename T>
 void gappy_y(hyrom_ctx* ctx, const T* v, const T* psi, double* y, const double* y_prev,
-             double* dy) {
+             double* dy, cudaStream_t s) {
   if (ctx->sample_ok)
     hy::launch_sample_solve<T>((const T*)ctx->phi, ctx->N, ctx->m_eff, ctx->s_cells,
                                (int)ctx->n_s, ctx->dc.nvar, ctx->nc, v, psi, ctx->s_part,
-                               ctx->s_b, ctx->s_L, ctx->s_dinv, y, y_prev, dy, ctx->st);
+                               ctx->s_b, ctx->s_L, ctx->s_dinv, y, y_prev, dy, s);
   else
     hy::launch_gappy_apply<T>(ctx->pinv, ctx->m_eff, ctx->np_eff, ctx->pts, v, psi, y, y_prev,
-                              dy, ctx->st);
+                              dy, s);
+}
+template <typename T>
+void gappy_y(hyrom_ctx* ctx, const T* v, const T* psi, double* y, const double* y_prev,
+             double* dy) {
+  gappy_y<T>(ctx, v, psi, y, y_prev, dy, ctx->st);
 }
 
 // The paper's HDM: R_k(q) = 0 by Newton-GMRES on the listed cells (all when
@@ -612,6 +632,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
   const hyrom_config& cf = ctx->cfg;
   if (!ctx->f32) {
     // FP64: one-sided Jacobi SVD of the centred window
+    join_select(ctx);
     t_begin(ctx, HYROM_T_EIG);
     hy::launch_center_window<T>(ring, ctx->N, ctx->win_dev, w, wp, psi, ctx->X, ctx->rawpart,
                                 ctx->xraw2, ctx->st);
@@ -656,6 +677,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
     hy::launch_pod_coeffs<T>(ctx->lam, ctx->V, wp, w, cf.m, cf.pod_tol, cf.pod_abs, ctx->xraw2,
                              ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
     t_end(ctx, HYROM_T_EIG);
+    join_select(ctx);  // the selection has read the old basis
     t_begin(ctx, HYROM_T_FORMPHI);
     if constexpr (sizeof(T) == 4) {
       if (kUseTensorBasisProduct && hy::form_phi_tc_ok(ctx->N, w, cf.m)) {
@@ -759,20 +781,25 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   // selection: G_{k+1} from the reconstruction error of the final gamma_k
   const uint32_t* gbm = nullptr;
   int64_t n_g = 0;
+  // (on st2, beside the eigensolve: it reads the old basis, which the
+  // rebuild overwrites only after joining it)
+  long long* hl = (long long*)((char*)ctx->host + 128);
   if (k >= w && ctx->has_basis) {
-    t_begin(ctx, HYROM_T_SELECT);
+    cudaStream_t ss = ctx->st2;
+    CK(cudaEventRecord(ctx->ev_fork, ctx->st));
+    CK(cudaStreamWaitEvent(ss, ctx->ev_fork, 0));
+    t_begin(ctx, HYROM_T_SELECT, ss);
     if (ctx->m_eff > 0)
-      gappy_y<T>(ctx, gk, (const T*)ctx->psi, ctx->y2, nullptr, nullptr);
+      gappy_y<T>(ctx, gk, (const T*)ctx->psi, ctx->y2, nullptr, nullptr, ss);
     hy::launch_cell_error<T>(gk, (const T*)ctx->psi, (const T*)ctx->phi, ctx->nc, ctx->dc.nvar,
-                             ctx->m_eff, ctx->y2, (T*)ctx->eps, ctx->st);
+                             ctx->m_eff, ctx->y2, (T*)ctx->eps, ss);
     hy::launch_select(ctx->eps, ctx->f32, ctx->nc, cf.sel_mode, cf.delta, cf.top_frac, ctx->keys,
-                      ctx->sel_scratch, ctx->g_bm, ctx->n_g_dev, ctx->st);
-    t_end(ctx, HYROM_T_SELECT);
+                      ctx->sel_scratch, ctx->g_bm, ctx->n_g_dev, ss);
+    t_end(ctx, HYROM_T_SELECT, ss);
     CKL();
-    long long* hl = (long long*)ctx->host;
-    CK(cudaMemcpyAsync(hl, ctx->n_g_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
-    if (hyrom_status s = sync(ctx)) return s;
-    n_g = hl[0];
+    CK(cudaMemcpyAsync(hl, ctx->n_g_dev, sizeof(long long), cudaMemcpyDeviceToHost, ss));
+    CK(cudaEventRecord(ctx->ev_join, ss));
+    ctx->sel_pending = true;
     gbm = ctx->g_bm;
   }
   inf.n_g = (int32_t)n_g;
@@ -788,7 +815,12 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   int me = 0;
   hyrom_status s = pod_t<T>(ctx, (const T*)ctx->ring, ctx->nslot, win, (const T*)ctx->psi,
                             ps_ok ? &ps : nullptr, (T*)ctx->phi, (T*)ctx->psi_next, &me);
+  join_select(ctx);
   if (s) return s;
+  if (gbm) {  // pod_t synchronised ctx->st after joining the selection
+    n_g = hl[0];
+    inf.n_g = (int32_t)n_g;
+  }
   ctx->m_eff = me;
   // ODEIM points
   ctx->np_eff = 0;
@@ -1011,7 +1043,10 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
     fprintf(stderr, "hyrom_init: device allocation failed\n");
     return HYROM_ENOMEM;
   }
-  if (cudaMallocHost(&ctx->host, 4096) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->host, 4096) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     hyrom_destroy(ctx);
     return HYROM_ENOMEM;
@@ -1040,6 +1075,12 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
 void hyrom_destroy(hyrom_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  if (ctx->st2) {
+    cudaStreamSynchronize(ctx->st2);
+    cudaStreamDestroy(ctx->st2);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   hy::odeim_graphs_free(&ctx->od_graphs);
   hy::graph_slot_free(&ctx->filt_graph);
   hy::muscl_destroy(ctx->mus);
