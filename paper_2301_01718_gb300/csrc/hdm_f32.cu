@@ -417,7 +417,29 @@ __global__ void __launch_bounds__(kWarps * 32, HY_SWEEP_MINB)
   const int lane = threadIdx.x & 31;
   const int strip = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (strip >= nstrips) return;  // whole warp leaves together
-  const int sxi = strip % strips_x, syi = strip / strips_x;
+  // The strips along the domain's sides take the slower general path; they
+  // are handed out first (bottom and top rows, then the left and right
+  // columns), so that the launch does not end on them.
+  const int strips_y = nstrips / strips_x;
+  int sxi, syi;
+  if (strips_x >= 3 && strips_y >= 3) {
+    const int nb = 2 * strips_x + 2 * (strips_y - 2);
+    if (strip < 2 * strips_x) {
+      sxi = strip % strips_x;
+      syi = strip < strips_x ? 0 : strips_y - 1;
+    } else if (strip < nb) {
+      const int e = strip - 2 * strips_x;
+      sxi = e < strips_y - 2 ? 0 : strips_x - 1;
+      syi = 1 + (e < strips_y - 2 ? e : e - (strips_y - 2));
+    } else {
+      const int e = strip - nb;
+      sxi = 1 + e % (strips_x - 2);
+      syi = 1 + e / (strips_x - 2);
+    }
+  } else {
+    sxi = strip % strips_x;
+    syi = strip / strips_x;
+  }
   const int x0 = sxi * kStripW, y0 = syi * H;
   if (x0 - 2 >= 0 && x0 + 62 <= c.nx && y0 - 2 >= 0 && y0 + H + 2 <= c.ny)
     sweep_strip<VEC, true>(c, q, out, lane, x0, y0, H);
