@@ -142,10 +142,196 @@ __global__ void k_gappy_pinv(const T* __restrict__ phi, int64_t N, int m,
   for (int idx = tid; idx < m * np; idx += nt) pinv[idx] = X[idx];
 }
 
+// The same pseudo-inverse by a thread-block cluster of C = min(16, m) CTAs
+// of 128 threads, CTA c owning the columns [c cpc, (c + 1) cpc) of A (and of
+// Q), so that the FP64 work of each step spreads over C SMs:
+//   * QR: at step j the owner of column j forms the reflector; after a
+//     cluster barrier every CTA copies it (and beta_j) from the owner's
+//     shared memory and applies it to its own columns beyond j;
+//   * every CTA then gathers the whole factored A (reflectors and R) and
+//     forms its own columns of Q = H_0 ... H_{m-1} [I; 0];
+//   * row r of R^{-1} for each of its own rows r, by forward substitution
+//     in R^T (one warp per row; pivots at or below the rank tolerance
+//     contribute zero, as in the one-CTA kernel's truncated solve);
+//   * after a second barrier, the whole Q gathered, and its rows of
+//     pinv = R^{-1} Q^T.
+// Shared memory: the whole A or Q (n_p m), own A and Q columns (2 n_p cpc),
+// the reflector (n_p), R^{-1} rows (cpc m) doubles.
+constexpr int kPinvThreads = 128;
+constexpr int kPinvMaxC = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kPinvThreads, 1)
+    k_gappy_pinv_cl(const T* __restrict__ phi, int64_t N, int m, const int* __restrict__ pts,
+                    int np, double* __restrict__ pinv, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const int cpc = (m + C - 1) / C;
+  const int c0 = me * cpc, nc = c0 < m ? (c0 + cpc <= m ? cpc : m - c0) : 0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kPinvThreads >> 5;
+  extern __shared__ double psm[];
+  double* Full = psm;                      // n_p x m, column-major
+  double* Aloc = Full + (size_t)np * m;    // n_p x cpc: own columns of A
+  double* Qloc = Aloc + (size_t)np * cpc;  // n_p x cpc: own columns of Q
+  double* vloc = Qloc + (size_t)np * cpc;  // n_p: the step's reflector
+  double* Y = vloc + np;                   // cpc x m: own rows of R^{-1}
+  __shared__ double beta_own[64];
+  __shared__ double vbeta;
+  for (int idx = tid; idx < np * nc; idx += kPinvThreads) {
+    const int i = idx % np, jj = idx / np;
+    Aloc[idx] = (double)phi[(int64_t)(c0 + jj) * N + pts[i]];
+  }
+  cl.sync();
+  // Householder QR: reflector j stored in column j (rows > j), v_j = 1 implied
+  for (int j = 0; j < m; ++j) {
+    const int o = j / cpc, jo = j - o * cpc;
+    if (me == o) {
+      double* a = Aloc + (size_t)jo * np;
+      double s = 0.0;
+      for (int i = j + tid; i < np; i += kPinvThreads) s = fma(a[i], a[i], s);
+      s = block_sum(s);
+      const double ajj = a[j];
+      const double nrm = sqrt(s);
+      const double alpha = ajj >= 0.0 ? -nrm : nrm;  // R_jj
+      const double v0 = ajj - alpha;
+      __syncthreads();
+      if (tid == 0) {
+        beta_own[jo] = (nrm == 0.0) ? 0.0 : -v0 / alpha;
+        a[j] = alpha;
+      }
+      const double iv0 = (v0 == 0.0) ? 0.0 : 1.0 / v0;
+      for (int i = j + 1 + tid; i < np; i += kPinvThreads) a[i] *= iv0;
+    }
+    cl.sync();
+    // the reflector from its owner, then applied to the own columns beyond j
+    if (nc > 0 && c0 + nc - 1 > j) {
+      const double* ao = cl.map_shared_rank(Aloc, (unsigned)o) + (size_t)jo * np;
+      for (int i = j + 1 + tid; i < np; i += kPinvThreads) vloc[i] = ao[i];
+      if (tid == 0) vbeta = cl.map_shared_rank(beta_own, (unsigned)o)[jo];
+      __syncthreads();
+      const double bj = vbeta;
+      for (int jj = wid; jj < nc; jj += nw) {
+        if (c0 + jj <= j) continue;
+        double* col = Aloc + (size_t)jj * np;
+        double d = 0.0;
+        for (int i = j + lane; i < np; i += 32) d = fma(i == j ? 1.0 : vloc[i], col[i], d);
+        d = warp_sum(d) * bj;
+        for (int i = j + lane; i < np; i += 32) col[i] = fma(-d, i == j ? 1.0 : vloc[i], col[i]);
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();
+  // the whole factored A, and the betas
+  __shared__ double betas[64];
+  for (int idx = tid; idx < np * m; idx += kPinvThreads) {
+    const int i = idx % np, j = idx / np, o = j / cpc, jo = j - o * cpc;
+    Full[idx] = cl.map_shared_rank(Aloc, (unsigned)o)[(size_t)jo * np + i];
+  }
+  for (int j = tid; j < m; j += kPinvThreads) {
+    const int o = j / cpc;
+    betas[j] = cl.map_shared_rank(beta_own, (unsigned)o)[j - o * cpc];
+  }
+  __syncthreads();
+  // numerical rank (the same rule and tolerance as the one-CTA kernel)
+  double rmax = 0.0;
+  for (int j = 0; j < m; ++j) rmax = fmax(rmax, fabs(Full[(size_t)j * np + j]));
+  const double rtol = 64.0 * (double)np * 2.220446049250313e-16 * rmax;
+  bool bad = rmax == 0.0;
+  for (int j = 0; j < m; ++j) bad |= !(fabs(Full[(size_t)j * np + j]) > rtol);
+  if (bad && me == 0 && tid == 0) atomicAdd(status, 1);
+  __shared__ double rdiag[64];  // 1 / R_kk, 0 for a pivot at or below the tolerance
+  for (int k = tid; k < m; k += kPinvThreads) {
+    const double d = Full[(size_t)k * np + k];
+    rdiag[k] = fabs(d) > rtol ? 1.0 / d : 0.0;
+  }
+  // own columns of Q = H_0 ... H_{m-1} [I; 0]
+  for (int idx = tid; idx < np * nc; idx += kPinvThreads) {
+    const int i = idx % np, jj = idx / np;
+    Qloc[idx] = i == c0 + jj ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    const double bj = betas[j];
+    const double* v = Full + (size_t)j * np;
+    for (int jj = wid; jj < nc; jj += nw) {
+      if (c0 + jj < j) continue;
+      double* col = Qloc + (size_t)jj * np;
+      double d = 0.0;
+      for (int i = j + lane; i < np; i += 32) d = fma(i == j ? 1.0 : v[i], col[i], d);
+      d = warp_sum(d) * bj;
+      for (int i = j + lane; i < np; i += 32) col[i] = fma(-d, i == j ? 1.0 : v[i], col[i]);
+    }
+    __syncthreads();
+  }
+  // own rows r of R^{-1}: y^T R = e_r^T, i.e. y_k = -(sum_{r<=l<k} R_lk y_l) / R_kk
+  // (R_lk = Full[k np + l] for l <= k)
+  for (int rr = wid; rr < nc; rr += nw) {
+    const int r = c0 + rr;
+    double* y = Y + (size_t)rr * m;
+    for (int k = lane; k < m; k += 32) y[k] = 0.0;
+    __syncwarp();
+    if (lane == 0) y[r] = rdiag[r];
+    __syncwarp();
+    for (int k = r + 1; k < m; ++k) {
+      double acc = 0.0;
+      for (int l = r + lane; l < k; l += 32) acc = fma(Full[(size_t)k * np + l], y[l], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) y[k] = -acc * rdiag[k];
+      __syncwarp();
+    }
+  }
+  cl.sync();
+  // the whole Q (its own columns from every CTA), then own rows of pinv
+  for (int idx = tid; idx < np * m; idx += kPinvThreads) {
+    const int i = idx % np, j = idx / np, o = j / cpc, jo = j - o * cpc;
+    Full[idx] = cl.map_shared_rank(Qloc, (unsigned)o)[(size_t)jo * np + i];
+  }
+  cl.sync();  // no CTA leaves while another still reads its Q columns
+  for (int idx = tid; idx < nc * np; idx += kPinvThreads) {
+    const int rr = idx / np, i = idx % np, r = c0 + rr;
+    const double* y = Y + (size_t)rr * m;
+    double p4[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = r;
+    for (; k + 3 < m; k += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p4[u] = fma(y[k + u], Full[(size_t)(k + u) * np + i], p4[u]);
+    }
+    for (; k < m; ++k) p4[0] = fma(y[k], Full[(size_t)k * np + i], p4[0]);
+    pinv[(size_t)r * np + i] = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+  }
+}
+
 template <typename T>
 void launch_gappy_pinv(const T* phi, int64_t N, int m, const int* pts, int np, double* pinv,
                        int* status, cudaStream_t s) {
   if (m <= 0) return;
+  // the cluster version where its shared memory fits, else one CTA
+  const int cpc = (m + kPinvMaxC - 1) / kPinvMaxC, C = (m + cpc - 1) / cpc;
+  const size_t smem_cl =
+      sizeof(double) * ((size_t)np * m + (size_t)2 * np * cpc + np + (size_t)cpc * m);
+  if (C > 1 && m <= 64 && smem_cl <= 200 * 1024) {
+    cudaFuncSetAttribute(k_gappy_pinv_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    smem_at_least((const void*)k_gappy_pinv_cl<T>, smem_cl);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(C);
+    lc.blockDim = dim3(kPinvThreads);
+    lc.dynamicSmemBytes = smem_cl;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    ::hy::count_launch();
+    if (cudaLaunchKernelEx(&lc, k_gappy_pinv_cl<T>, phi, N, m, pts, np, pinv, status) ==
+        cudaSuccess)
+      return;
+    cudaGetLastError();
+  }
   const size_t smem = sizeof(double) * ((size_t)2 * np * m + (size_t)m * m + m);
   smem_at_least((const void*)k_gappy_pinv<T>, smem);
   k_gappy_pinv<T><<<1, 256, smem, HY_S(s)>>>(phi, N, m, pts, np, pinv, status);
