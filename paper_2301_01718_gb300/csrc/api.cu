@@ -672,7 +672,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
                                       wp, ctx->xraw2, ctx->st);
     }
     if (hy::run_psd_eig(ctx->Gc, wp, ctx->V, ctx->lam, ctx->jbuf, ctx->rotated,
-                        (int*)ctx->host + 8, 60, ctx->st) < 0)
+                        (int*)ctx->host + 8, 60, ctx->st, nullptr, true) < 0)
       return fail(ctx, HYROM_ECUDA, "Jacobi eigensolver: %s", cudaGetErrorString(cudaGetLastError()));
     hy::launch_pod_coeffs<T>(ctx->lam, ctx->V, wp, w, cf.m, cf.pod_tol, cf.pod_abs, ctx->xraw2,
                              ctx->sig, ctx->m_eff_dev, (T*)ctx->C, ctx->st);
@@ -1012,7 +1012,9 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   {
     // the eigensolver's work array (FP32 POD), or the FP64 Jacobi rounds'
     // partial sums and rotations
-    const size_t a = (size_t)2 * wp * wp + 512, b = hy::hestenes_scratch_doubles(wp);
+    size_t a = (size_t)2 * wp * wp + 512;
+    const size_t b = hy::hestenes_scratch_doubles(wp), c2 = hy::psd_eig_scratch_doubles(wp);
+    if (c2 > a) a = c2;
     ok &= dal(ctx, &ctx->jbuf, (a > b ? a : b) * sizeof(double));
   }
   ok &= dal(ctx, &ctx->m_eff_dev, 64);

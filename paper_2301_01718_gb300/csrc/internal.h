@@ -234,8 +234,13 @@ void launch_form_phi_tc(const float* ring, int64_t N, int nslot, const int* win,
                         const float* psi, const float* C, int m, const int* m_eff_dev,
                         float* phi, float* psi_next, int* err, OdeimNorms norms,
                         cudaStream_t s);
+// scratch (doubles) run_psd_eig needs at order n
+size_t psd_eig_scratch_doubles(int n);
+// fp32_pre: FP32 preconditioning sweeps first (the FP32 POD's window
+// Gram, where eigenvalues accurate to eps times the largest suffice)
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
-                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr);
+                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank = nullptr,
+                bool fp32_pre = false);
 void launch_colnorm2(const double* X, int64_t N, int ncol, double* out, cudaStream_t s);
 template <typename T>
 void launch_phi_from_columns(const double* X, int64_t N, int wp, const double* C,

@@ -2004,7 +2004,7 @@ size_t odeim_ws_bytes(int64_t N, int m) {
   b += sizeof(double) * (64 + 6 * (size_t)(m + 1) * (m + 1) + 4 * m + 64);
   b += 16 * 256;
   b += sizeof(double) * (5 * 64 * 64 + 3 * 64) + sizeof(R1Work) + 16 * 256;
-  b += sizeof(double) * (2 * (m + 1) * (m + 1) + 512) + 3 * 256;
+  b += sizeof(double) * (psd_eig_scratch_doubles(m + 1) + 2 * (m + 1) * (m + 1) + 512) + 3 * 256;
   b += sizeof(double) * (2 * 64 * 64 + 64) + 3 * 256;
   b += sizeof(float) * kW32 + 256;
   return b + 4096;
@@ -2046,7 +2046,8 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.lam_s2 = (double*)take(64 * sizeof(double));
   o.W_s2 = (double*)take((size_t)64 * 64 * sizeof(double));
   o.r1 = (R1Work*)take(sizeof(R1Work));
-  o.jbuf = (double*)take(((size_t)2 * (m + 1) * (m + 1) + 512) * sizeof(double));
+  o.jbuf = (double*)take((psd_eig_scratch_doubles(m + 1) + (size_t)2 * (m + 1) * (m + 1) + 512) *
+                         sizeof(double));
   o.jscale = (double*)take(64);
   o.jflag = (int*)take(64);
   o.Li = (double*)take((size_t)64 * 64 * sizeof(double));

@@ -1143,6 +1143,223 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_osj_block(double* __restrict_
   if (sweeps_out && me == 0 && tid == 0) *sweeps_out = sw < max_sweeps ? sw + 1 : max_sweeps;
 }
 
+// ---- FP32 preconditioning sweeps of the block one-sided Jacobi -------------
+//
+// Most of the Jacobi sweeps only bring the columns near orthogonality, which
+// FP32 does as well as FP64 at a fraction of the cost: a warp-wide FP64
+// instruction holds an SM sub-partition for 64 cycles, an FP32 one about
+// one.  So B (the columns of R^T) is first rotated in FP32, with the
+// rotations accumulated in J (n x n, FP32, from the identity), until no
+// pair rotates at the FP32 tolerance; J is then made orthogonal to FP64
+// precision by two Newton-Schulz steps J <- J (3 I - J^T J) / 2 (from
+// |J^T J - I| ~ 1e-6: 1e-12, then rounding), B <- B J in FP64, and the FP64
+// sweeps finish from there (typically two, and the one that finds no
+// rotation).  B J has the same Gram B B^T up to the rounding of the product
+// (eps |B| absolute), so the eigenvectors and eigenvalues are those of the
+// same matrix.
+HY_DEV bool bj_rotate32(float* X, float* Y, float* JX, float* JY, float* na, float* nc, int n,
+                        int lane, float tol) {
+  constexpr int kPer = kBjMaxN / 32;
+  float xv[kPer], yv[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = lane + 32 * u;
+    xv[u] = i < n ? X[i] : 0.f;
+    yv[u] = i < n ? Y[i] : 0.f;
+  }
+  const float a = *na, c = *nc;
+  float g = xv[0] * yv[0];
+#pragma unroll
+  for (int u = 1; u < kPer; ++u) g = fmaf(xv[u], yv[u], g);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if (!(g * g > tol * tol * (a * c) && a > 0.f && c > 0.f)) return false;
+  const float df = c - a, g2 = 2.f * g;
+  const float sc = fmaxf(fabsf(df), fabsf(g2));
+  const float uu = df / sc, vv = g2 / sc;
+  const float t = copysignf(1.f, uu) * vv / (fabsf(uu) + sqrtf(fmaf(uu, uu, vv * vv)));
+  const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = lane + 32 * u;
+    if (i < n) {
+      X[i] = fmaf(cs, xv[u], -sn * yv[u]);
+      Y[i] = fmaf(sn, xv[u], cs * yv[u]);
+      const float jx = JX[i], jy = JY[i];
+      JX[i] = fmaf(cs, jx, -sn * jy);
+      JY[i] = fmaf(sn, jx, cs * jy);
+    }
+  }
+  if (lane == 0) {
+    *na = fmaf(-t, g, a);
+    *nc = fmaf(t, g, c);
+  }
+  return true;
+}
+
+// The FP32 sweeps in one thread-block cluster, with the same layout and
+// tournament as k_osj_block: B32 and J32 (n x n, column j at + j n, FP32)
+// in, rotated in place.
+__global__ void __launch_bounds__(kBjThreads, 1) k_osj_block32(float* __restrict__ B32,
+                                                            float* __restrict__ J32, int n,
+                                                            const int* __restrict__ rank,
+                                                            float tol, int max_sweeps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ float hcol[2][2 * kBjCols][kBjMaxN];  // home blocks: X columns, then J columns
+  __shared__ float hnrm[2][kBjCols];
+  __shared__ float wcol[2][2 * kBjCols][kBjMaxN];  // the round's pair of blocks
+  __shared__ float wnrm[2][kBjCols];
+  __shared__ int rot_flag[2];
+  __shared__ int rot_local;
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const int nb = 2 * C;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  const int r = *rank;
+  const int row = tid;
+#pragma unroll
+  for (int k = 0; k < 2 * kBjCols; ++k) {
+    const int sl = k / kBjCols, c = k % kBjCols;
+    const int j = kBjCols * (me + C * sl) + c;
+    hcol[sl][c][row] = (j < r && row < n) ? B32[(int64_t)j * n + row] : 0.f;
+    hcol[sl][kBjCols + c][row] = (j < n && row < n) ? J32[(int64_t)j * n + row] : 0.f;
+  }
+  if (tid < 2) rot_flag[tid] = 0;
+  cl.sync();
+  int* flag0 = cl.map_shared_rank(&rot_flag[0], 0);
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    for (int k = wid; k < 2 * kBjCols; k += nw) {
+      const int sl = k / kBjCols, c = k % kBjCols;
+      float a = 0.f;
+      for (int i = lane; i < n; i += 32) a = fmaf(hcol[sl][c][i], hcol[sl][c][i], a);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) hnrm[sl][c] = a;
+    }
+    if (tid == 0) rot_local = 0;
+    cl.sync();
+    for (int rd = 0; rd < nb - 1; ++rd) {
+      int pb, qb;
+      rr_pair(nb, rd, me, pb, qb);
+      float(*hp)[kBjMaxN] = cl.map_shared_rank(hcol[pb / C], (unsigned)(pb % C));
+      float(*hq)[kBjMaxN] = cl.map_shared_rank(hcol[qb / C], (unsigned)(qb % C));
+      float* np_ = cl.map_shared_rank(hnrm[pb / C], (unsigned)(pb % C));
+      float* nq_ = cl.map_shared_rank(hnrm[qb / C], (unsigned)(qb % C));
+      {
+        float v[4 * kBjCols];
+#pragma unroll
+        for (int c = 0; c < 2 * kBjCols; ++c) {
+          v[c] = hp[c][row];
+          v[2 * kBjCols + c] = hq[c][row];
+        }
+#pragma unroll
+        for (int c = 0; c < 2 * kBjCols; ++c) {
+          wcol[0][c][row] = v[c];
+          wcol[1][c][row] = v[2 * kBjCols + c];
+        }
+      }
+      if (tid < 2 * kBjCols) {
+        const int s2 = tid / kBjCols, c = tid % kBjCols;
+        wnrm[s2][c] = s2 == 0 ? np_[c] : nq_[c];
+      }
+      __syncthreads();
+      bool rot = false;
+      if (rd == 0) {
+        const int wx[3][2] = {{0, 2}, {0, 1}, {0, 1}}, wy[3][2] = {{1, 3}, {2, 3}, {3, 2}};
+        const int s2 = wid >> 1, h = wid & 1;
+        for (int t = 0; t < 3; ++t) {
+          const int x = wx[t][h], y = wy[t][h];
+          rot |= bj_rotate32(wcol[s2][x], wcol[s2][y], wcol[s2][kBjCols + x],
+                             wcol[s2][kBjCols + y], &wnrm[s2][x], &wnrm[s2][y], n, lane, tol);
+          __syncthreads();
+        }
+      }
+      for (int t = 0; t < kBjCols; ++t) {
+        const int y = (wid + t) % kBjCols;
+        rot |= bj_rotate32(wcol[0][wid], wcol[1][y], wcol[0][kBjCols + wid], wcol[1][kBjCols + y],
+                           &wnrm[0][wid], &wnrm[1][y], n, lane, tol);
+        __syncthreads();
+      }
+      if (rot && lane == 0) rot_local = 1;
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < 2 * kBjCols; ++c) {
+        hp[c][row] = wcol[0][c][row];
+        hq[c][row] = wcol[1][c][row];
+      }
+      if (tid < 2 * kBjCols) {
+        const int s2 = tid / kBjCols, c = tid % kBjCols;
+        (s2 == 0 ? np_ : nq_)[c] = wnrm[s2][c];
+      }
+      cl.sync();
+    }
+    if (tid == 0 && rot_local) atomicOr(flag0 + (sw & 1), 1);
+    cl.sync();
+    const int rotated = *((volatile int*)(flag0 + (sw & 1)));
+    cl.sync();
+    if (me == 0 && tid == 0) rot_flag[(sw + 1) & 1] = 0;
+    cl.sync();
+    if (!rotated) break;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * kBjCols; ++k) {
+    const int sl = k / kBjCols, c = k % kBjCols;
+    const int j = kBjCols * (me + C * sl) + c;
+    if (j < n && row < n) {
+      B32[(int64_t)j * n + row] = hcol[sl][c][row];
+      J32[(int64_t)j * n + row] = hcol[sl][kBjCols + c][row];
+    }
+  }
+}
+
+// B32 = (float) B on the first r columns (zero beyond), J32 = I (n x n)
+__global__ void k_osj32_init(const double* __restrict__ B, float* __restrict__ B32,
+                             float* __restrict__ J32, int n, const int* __restrict__ rank) {
+  const int r = *rank;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += gridDim.x * blockDim.x) {
+    B32[idx] = idx / n < r ? (float)B[idx] : 0.f;
+    J32[idx] = (idx % n) == (idx / n) ? 1.f : 0.f;
+  }
+}
+
+// B = (columns < r of) B kept, beyond r zeroed, for the product B J
+__global__ void k_zero_beyond_rank(double* __restrict__ B, int n, const int* __restrict__ rank) {
+  const int r = *rank;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += gridDim.x * blockDim.x)
+    if (idx / n >= r) B[idx] = 0.0;
+}
+
+// C = op(A) B for n x n column-major FP64 matrices (op: A or A^T; A may be
+// FP32), each thread one entry, the sum in four chains; plus alpha I when
+// asked (C = alpha I + beta op(A) B).
+template <typename TA, bool TRANS>
+__global__ void k_gemm_nn64(const TA* __restrict__ A, const double* __restrict__ B,
+                            double* __restrict__ Cm, int n, double alpha, double beta) {
+  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  if (i >= n || j >= n) return;
+  double p[4] = {0.0, 0.0, 0.0, 0.0};
+  int k = 0;
+  for (; k + 3 < n; k += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double a = TRANS ? (double)A[(int64_t)i * n + k + u] : (double)A[(int64_t)(k + u) * n + i];
+      p[u] = fma(a, B[(int64_t)j * n + k + u], p[u]);
+    }
+  }
+  for (; k < n; ++k) {
+    const double a = TRANS ? (double)A[(int64_t)i * n + k] : (double)A[(int64_t)k * n + i];
+    p[0] = fma(a, B[(int64_t)j * n + k], p[0]);
+  }
+  Cm[(int64_t)j * n + i] = (i == j ? alpha : 0.0) + beta * ((p[0] + p[1]) + (p[2] + p[3]));
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int n) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+    b[idx] = (double)a[idx];
+}
+
 // lam[j] = |b_j|^2 and V[:, j] = Pi b_j / |b_j| for j < r; zero beyond.
 __global__ void k_osj_finish(const double* __restrict__ B, int n, const int* __restrict__ rank,
                              const int* __restrict__ piv, double* __restrict__ lam,
@@ -1166,8 +1383,10 @@ __global__ void k_osj_finish(const double* __restrict__ B, int n, const int* __r
 // and 2 * kEigMaxN ints.  flag (device, 5 ints, nullable): flag[4] = the
 // sweeps the one-sided Jacobi ran.  With host_rank (pinned) the numerical
 // rank is read back (one synchronisation).  Returns 0, or -1 on a CUDA error.
+size_t psd_eig_scratch_doubles(int n) { return (size_t)5 * n * n + kEigMaxN + 64; }
+
 int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int* flag,
-                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank) {
+                int* host_flag, int max_sweeps, cudaStream_t s, int* host_rank, bool fp32_pre) {
   if (n > kEigMaxN) return -1;
   double* B = buf;
   int* piv = reinterpret_cast<int*>(buf + (size_t)n * n);
@@ -1179,6 +1398,46 @@ int run_psd_eig(const double* G, int n, double* V, double* lam, double* buf, int
   const double tol = 1e-14;
   if (n > kBjMaxN) return -1;
   const int C = (n + 2 * kBjCols - 1) / (2 * kBjCols);  // two blocks of four per CTA
+  if (fp32_pre && n >= 32) {
+    // FP32 sweeps with the rotations accumulated, J made orthogonal in FP64
+    // (two Newton-Schulz steps), B <- B J; the FP64 sweeps finish below
+    float* B32 = reinterpret_cast<float*>(buf + (size_t)n * n + kEigMaxN);
+    float* J32 = B32 + (size_t)n * n;
+    double* J = reinterpret_cast<double*>(J32 + (size_t)n * n);
+    double* T1 = J + (size_t)n * n;
+    double* T2 = T1 + (size_t)n * n;
+    const int g = (n * n + 255) / 256;
+    k_osj32_init<<<g, 256, 0, HY_S(s)>>>(B, B32, J32, n, rank);
+    cudaFuncSetAttribute(k_osj_block32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(C);
+    lc.blockDim = dim3(kBjThreads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    ::hy::count_launch();
+    if (cudaLaunchKernelEx(&lc, k_osj_block32, B32, J32, n, (const int*)rank, 1e-5f, 12) !=
+        cudaSuccess)
+      return -1;
+    k_f32_to_f64<<<g, 256, 0, HY_S(s)>>>(J32, J, n * n);
+    const dim3 gb((n + 15) / 16, (n + 15) / 16), tb(16, 16);
+    for (int it = 0; it < 2; ++it) {
+      k_gemm_nn64<double, true><<<gb, tb, 0, HY_S(s)>>>(J, J, T1, n, 1.5, -0.5);
+      k_gemm_nn64<double, false><<<gb, tb, 0, HY_S(s)>>>(J, T1, T2, n, 0.0, 1.0);
+      double* t = J;
+      J = T2;
+      T2 = t;
+    }
+    k_zero_beyond_rank<<<g, 256, 0, HY_S(s)>>>(B, n, rank);
+    k_gemm_nn64<double, false><<<gb, tb, 0, HY_S(s)>>>(B, J, T1, n, 0.0, 1.0);
+    cudaMemcpyAsync(B, T1, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s);
+  }
   cudaFuncSetAttribute(k_osj_block, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(C);
