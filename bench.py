@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--batch-n", type=int, default=64, help="instances of the batching form")
     p.add_argument("--batch-steps", type=int, default=3,
                    help="timed hybrid steps per instance in each batching-form arm")
+    p.add_argument("--batch-fused-threads", default="8,16",
+                   help="host threads of the fused batching arms (empty: none)")
     p.add_argument("--batch-threads", default="1,4,8,16",
                    help="host-thread counts timed in the batching form (1 = one at a time)")
     p.add_argument("--implicit-n", type=int, default=512,
@@ -629,9 +631,11 @@ def batch_form(a):
     own basis k 8..48 and sample fraction 2..20 % each), every context on its
     own stream, stepped by hyrom_batch_step with 1 host thread (the instances
     one at a time) and with more threads (up to that many instances on the
-    GPU at once).  Each arm times a.batch_steps hybrid steps of every
-    instance, host clock around the synchronised call; rates are instance
-    hybrid steps/s and dof-steps/s (dofs advanced per second)."""
+    GPU at once), then in the fused form (HYROM_BATCH_FUSED: every
+    instance's oversampling loop in one launch per pass, after the
+    autotuner's nine untimed steps).  Each arm times a.batch_steps hybrid
+    steps of every instance, host clock around the synchronised call; rates
+    are instance hybrid steps/s and dof-steps/s (dofs advanced per second)."""
     import torch
     from paper_2301_01718_gb300 import build, hyrom
     build.build()
@@ -650,11 +654,19 @@ def batch_form(a):
         for c in ctxs:
             while hyrom.hyrom_step(c)["was_full"]:
                 pass
-        arms = {}
-        for t in [int(x) for x in str(a.batch_threads).split(",") if x]:
+        arms, fused = {}, {}
+        runs = [(int(x), False) for x in str(a.batch_threads).split(",") if x]
+        runs += [(int(x), True) for x in str(a.batch_fused_threads).split(",") if x]
+        for t, is_fused in runs:
             b = hyrom.hyrom_batch_create(ctxs, threads=t)
             try:
-                hyrom.hyrom_batch_step(b, len(ctxs), nsteps=1, ctxs=ctxs)     # warm-up
+                if is_fused:
+                    # the autotuner times its four candidates twice each
+                    hyrom.hyrom_batch_set_mode(b, hyrom.HYROM_BATCH_FUSED)
+                    hyrom.hyrom_batch_step(b, len(ctxs), nsteps=9, ctxs=ctxs)
+                else:
+                    hyrom.hyrom_batch_set_mode(b, hyrom.HYROM_BATCH_STREAMS)
+                    hyrom.hyrom_batch_step(b, len(ctxs), nsteps=1, ctxs=ctxs)     # warm-up
                 torch.cuda.synchronize()
                 l0 = hyrom.hyrom_kernel_launches()
                 t0 = time.perf_counter()
@@ -663,23 +675,35 @@ def batch_form(a):
                 el = time.perf_counter() - t0
                 launches = hyrom.hyrom_kernel_launches() - l0
                 threads = hyrom.hyrom_batch_threads(b)
+                tuning = hyrom.hyrom_batch_tuning(b)
             finally:
                 hyrom.hyrom_batch_destroy(b)
             assert all(not i["was_full"] for i in infos)
             steps = a.batch_steps * len(ctxs)
-            arms[str(threads)] = {"ms": el * 1e3, "instance_steps_per_s": steps / el,
-                                  "dof_steps_per_s": dofs * a.batch_steps / el,
-                                  "gpu_launches": int(launches)}
+            arm = {"ms": el * 1e3, "instance_steps_per_s": steps / el,
+                   "dof_steps_per_s": dofs * a.batch_steps / el,
+                   "gpu_launches": int(launches)}
+            if is_fused:
+                arm["rows_per_cta"] = tuning[0]
+                arm["tuning_ms_per_greedy_step"] = dict(zip(["1024", "2048", "4096", "8192"],
+                                                            tuning[1]))
+                fused[str(threads)] = arm
+            else:
+                arms[str(threads)] = arm
     finally:
         for c in ctxs:
             hyrom.hyrom_destroy(c)
     one = arms.get("1")
-    best = max(arms.values(), key=lambda r: r["instance_steps_per_s"])
+    best = max(list(arms.values()) + list(fused.values()),
+               key=lambda r: r["instance_steps_per_s"])
     return {"workload": f"{len(insts)} Euler vortex instances, grids 128^2..1024^2 "
                         "log-uniform, Mach 0.3..2, k 8..48 (w = n_p = 2k), sample 2..20 %, FP32",
             "instances": len(insts), "dofs": dofs, "device_bytes": dev_bytes,
             "steps_per_instance": a.batch_steps, "unit": "instance hybrid steps/s",
             "threads": arms,
+            "fused": {"form": "each step in two phases around one launch per pass of every "
+                              "instance's oversampling loop (CUDA graph, autotuned rows per CTA)",
+                      "threads": fused},
             "speedup_vs_one_at_a_time": (best["instance_steps_per_s"] /
                                          one["instance_steps_per_s"]) if one else None}
 

@@ -434,11 +434,13 @@ hyrom_status hyrom_adjoint(hyrom_ctx* ctx, int32_t steps, const int32_t* box, do
  * a batch call runs) and starts `threads` host threads (0: half the host's
  * hardware threads, between 1 and 8; never more than the number of distinct
  * streams among the contexts).
- * hyrom_batch_step runs `nsteps` calls of hyrom_step on every instance: each
+ * hyrom_batch_step runs `nsteps` calls of hyrom_step on every instance, in
+ * the form hyrom_batch_set_mode selects (below).  In the streams form each
  * thread takes one instance at a time, largest device footprint first, and
  * runs its steps on the instance's own stream, so up to `threads` instances
- * are on the GPU at once.  An instance's steps stay in order and launch the
- * same kernels as when it is stepped alone, so its results are the same bits.
+ * are on the GPU at once.  In either form an instance's steps stay in order
+ * and compute what they compute when it is stepped alone, so its results are
+ * the same bits.
  * Contexts that share a stream (the legacy default stream included) are
  * stepped by one thread in turn, so that a stream being captured into one
  * instance's CUDA graph sees no other instance's work: they keep their
@@ -466,6 +468,30 @@ hyrom_status hyrom_init_batch(const hyrom_config* cfgs, const double* const* q0,
 hyrom_status hyrom_batch_step(hyrom_batch* batch, int32_t nsteps, hyrom_step_info* infos,
                               int32_t* status);
 int32_t hyrom_batch_threads(const hyrom_batch* batch);
+/* hyrom_batch_set_mode: how hyrom_batch_step runs a step (Algorithm 1's
+ * hybrid step, applied to every instance).
+ *   HYROM_BATCH_STREAMS: as described above, each instance's steps run
+ *   whole on its own stream, up to `threads` instances at a time.
+ *   HYROM_BATCH_FUSED (the default): the instances advance one step at a
+ *   time together.
+ *   The threads run every instance's step up to its ODEIM oversampling loop
+ *   (Sec. 2.3.1, Eq. odeim: the greedy steps after the first m points); the
+ *   loops of all instances then run as one launch per pass over all
+ *   instances (a CTA finds its instance in a work list in device memory),
+ *   replayed from a CUDA graph on a stream of the batch, with the scoring
+ *   passes' rows per CTA picked by timing four candidates over the first
+ *   eight steps; then the threads finish every instance's step.  Each instance
+ *   gets the same points, hence the same results, as stepped alone.
+ * Errors: HYROM_EINVAL (null batch, unknown mode).
+ * hyrom_batch_tuning: the fused form's autotuner: *rows_per_cta (nullable)
+ * receives the rows per CTA in use (0 while still timing), ms_per_step (n
+ * entries, nullable) the measured ms per greedy step of each candidate (-1:
+ * not timed).  Returns the number of candidates, 0 before the first fused
+ * step, -1 for a null batch. */
+enum { HYROM_BATCH_STREAMS = 0, HYROM_BATCH_FUSED = 1 };
+hyrom_status hyrom_batch_set_mode(hyrom_batch* batch, int32_t mode);
+int32_t hyrom_batch_tuning(const hyrom_batch* batch, int32_t* rows_per_cta, float* ms_per_step,
+                           int32_t n);
 void hyrom_batch_destroy(hyrom_batch* batch);
 
 /* ---- diagnostics -----------------------------------------------------------

@@ -156,6 +156,17 @@ struct hyrom_ctx {
   bool norms_ready = false;
   // the rebuild's DEIM and oversampling loops as CUDA graphs
   hy::OdeimGraphs od_graphs;
+  // batching: a rebuild leaves its oversampling loop (described in `over`)
+  // to a multi-instance launch and stops before the loop's consumers; the
+  // rest of the rebuild runs in finish_rebuild
+  bool defer_over = false;
+  hy::OdeimOver over{};
+  struct {
+    bool on = false;
+    hyrom_step_info inf{};
+    const uint32_t* gbm = nullptr;
+    int me = 0, np = 0;
+  } pend;
   // the paper's HDM (MUSCL-Roe-BDF2): Newton-GMRES solver and the S-hat cell
   // list its partial solves run over
   hy::MusclSolver* mus = nullptr;
@@ -738,6 +749,10 @@ hyrom_status masks_and_tiles(hyrom_ctx* ctx, const uint32_t* gbm, const int* pts
 }
 
 template <typename T>
+hyrom_status rebuild_tail_t(hyrom_ctx* ctx, hyrom_step_info inf, const uint32_t* gbm, int me,
+                            int np, hyrom_step_info* info);
+
+template <typename T>
 hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   const hyrom_config& cf = ctx->cfg;
   const int64_t k = ctx->k;
@@ -824,16 +839,43 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
   ctx->m_eff = me;
   // ODEIM points
   ctx->np_eff = 0;
+  int np = 0;
   if (me > 0) {
-    int np = cf.n_p;
+    np = cf.n_p;
     if (np > ctx->N) np = (int)ctx->N;
     t_begin(ctx, HYROM_T_DEIM);
     const bool nr = ctx->norms_ready;
     ctx->norms_ready = false;
+    hy::OdeimOver* ov = ctx->defer_over ? &ctx->over : nullptr;
+    if (ov && ov->m_cap < cf.m) ov->m_cap = cf.m < 64 ? cf.m : 64;
     if (hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts,
                             ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx,
-                            nr, &ctx->od_graphs) < 0)
+                            nr, &ctx->od_graphs, ov) < 0)
       return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
+    if (ov && ov->active) {  // finish_rebuild completes the step
+      ctx->pend.on = true;
+      ctx->pend.inf = inf;
+      ctx->pend.gbm = gbm;
+      ctx->pend.me = me;
+      ctx->pend.np = np;
+      if (info) *info = inf;
+      return HYROM_OK;
+    }
+  }
+  return rebuild_tail_t<T>(ctx, inf, gbm, me, np, info);
+}
+
+// The rebuild after its ODEIM points: the sampled pseudo-inverse, the
+// sampling sets, the sample-row normal matrix, the tiles and the psi
+// update (Algorithm 1, after the greedy selection of the points).
+template <typename T>
+hyrom_status rebuild_tail_t(hyrom_ctx* ctx, hyrom_step_info inf, const uint32_t* gbm, int me,
+                            int np, hyrom_step_info* info) {
+  const hyrom_config& cf = ctx->cfg;
+  const int64_t k = ctx->k;
+  const int w = cf.w;
+  hyrom_status s;
+  if (me > 0) {
     ctx->np_eff = np;
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->st));
     hy::launch_gappy_pinv<T>((const T*)ctx->phi, ctx->N, me, ctx->pts, np, ctx->pinv,
@@ -923,6 +965,24 @@ hyrom_status init_state(hyrom_ctx* ctx, const double* q0, int on_host) {
 
 namespace hy {
 void* ctx_stream(const hyrom_ctx* ctx) { return ctx ? (void*)ctx->st : nullptr; }
+void ctx_set_defer(hyrom_ctx* ctx, bool on) {
+  if (ctx) ctx->defer_over = on;
+}
+const OdeimOver* ctx_pending_over(const hyrom_ctx* ctx) {
+  return ctx && ctx->pend.on ? &ctx->over : nullptr;
+}
+bool ctx_is_f32(const hyrom_ctx* ctx) { return ctx && ctx->f32; }
+void ctx_drop_pending(hyrom_ctx* ctx) {
+  if (ctx) ctx->pend.on = false;
+}
+hyrom_status ctx_finish_rebuild(hyrom_ctx* ctx, hyrom_step_info* info) {
+  if (!ctx || !ctx->pend.on) return HYROM_OK;
+  ctx->pend.on = false;
+  if (ctx->sticky) return HYROM_ECUDA;
+  const auto& p = ctx->pend;
+  return ctx->f32 ? rebuild_tail_t<float>(ctx, p.inf, p.gbm, p.me, p.np, info)
+                  : rebuild_tail_t<double>(ctx, p.inf, p.gbm, p.me, p.np, info);
+}
 }  // namespace hy
 
 extern "C" {

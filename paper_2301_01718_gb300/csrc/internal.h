@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-typedef struct hyrom_ctx hyrom_ctx;
+#include "../../include/hyrom.h"
 
 namespace hy {
 
@@ -18,6 +18,16 @@ void add_launches(unsigned long long n);
 
 // The stream a context was created with (api.cu).
 void* ctx_stream(const hyrom_ctx* ctx);
+// batching (api.cu): with defer on, a rebuild that has an oversampling loop
+// describes it (ctx_pending_over) and returns before the loop's consumers;
+// after the loop has run, ctx_finish_rebuild completes the rebuild (its
+// status and step info are those hyrom_update_basis would have returned).
+struct OdeimOver;
+void ctx_set_defer(hyrom_ctx* ctx, bool on);
+const OdeimOver* ctx_pending_over(const hyrom_ctx* ctx);
+bool ctx_is_f32(const hyrom_ctx* ctx);
+hyrom_status ctx_finish_rebuild(hyrom_ctx* ctx, hyrom_step_info* info);
+void ctx_drop_pending(hyrom_ctx* ctx);  // the loop did not run: forget the rebuild's rest
 
 // Raise the dynamic shared memory limit of kernel `func` on the current
 // device to at least `bytes`.  The limit is a per-function global shared by
@@ -297,11 +307,57 @@ struct OdeimGraphs {
 };
 void odeim_graphs_free(OdeimGraphs* g);
 OdeimNorms odeim_norm_bufs(void* ws, int64_t N);
+// One instance's oversampling loop, described for a launch that runs the
+// loops of several instances together (launch_odeim_multi) instead of being
+// run by launch_odeim.  Pointers are device pointers into the instance's
+// ODEIM workspace; the struct is copied to the device as it is.
+struct OdeimOver {
+  int active;  // 1: the loop has steps (np > m) and was left to the caller
+  int m_cap;   // upper bound of m over the instance's calls (sizes the update's grids)
+  const void* phi;  // T*, N x m column-major
+  int64_t N;
+  int m, np, probe, C;
+  double tie_tol;
+  float* wt32;
+  const float* nrm;
+  const int* ord;
+  unsigned char* picked;
+  const unsigned* bmax;
+  const int* bstart;
+  void* ctl;  // the control block
+  double* scores;
+  int* list;
+  int* xlist;
+  const float* R;
+  double* lam[2];  // eigenvalues of M, read at even / odd steps (the other is written)
+  double* W[2];    // eigenvectors likewise
+  int* cand;
+  int* pts;
+  void* r1;  // the rank-one update's work block
+  double* Wrot;
+  double* Delta;
+};
+// over (nullable): if given, launch_odeim runs DEIM and the first
+// eigensystem, then describes the oversampling loop in *over instead of
+// running it (over->active = 0 when there is none).
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int) = nullptr,
                  void* mark_arg = nullptr, bool norms_ready = false,
-                 OdeimGraphs* graphs = nullptr);
+                 OdeimGraphs* graphs = nullptr, OdeimOver* over = nullptr);
+// Several instances' oversampling loops (all of element type T) run
+// together: one launch per pass over all instances, a CTA's instance found
+// from a work list, replayed from a CUDA graph; the rows-per-CTA of the
+// scoring passes picked by timing candidates on the first calls.  Results
+// are those of each loop run alone.  Returns 0, or -1 on a CUDA error.
+struct OdeimMulti;
+OdeimMulti* odeim_multi_create();
+void odeim_multi_free(OdeimMulti* mu);
+template <typename T>
+int launch_odeim_multi(OdeimMulti* mu, const OdeimOver* const* inst, int n, cudaStream_t s);
+// the autotuner's state: the rows per CTA in use (0 while still timing) and
+// the measured ms per greedy step of each candidate (nc entries, -1 untimed)
+int odeim_multi_tuning(const OdeimMulti* mu, int* rows_per_cta, float* ms, int nc);
 size_t odeim_ws_bytes(int64_t N, int m);
 void odeim_stats(const void* ws, unsigned long long* out4, cudaStream_t s);
 void odeim_eig_sweeps(const void* ws, int* out, cudaStream_t s);

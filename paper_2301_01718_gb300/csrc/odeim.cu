@@ -21,7 +21,9 @@
 // computes, so the chosen points do not depend on the pruning.
 #include <math.h>
 
+#include <new>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -258,14 +260,14 @@ HY_DEV void note_scores(double sc, int pos, double tie_tol, unsigned long long& 
   __syncthreads();
 }
 
-// True in the CTA that finishes a grid last (all threads); its reads of what
-// the other CTAs wrote see their writes.
-HY_DEV bool last_block(unsigned* ticket) {
+// True in the CTA that finishes a grid of nb CTAs last (all threads); its
+// reads of what the other CTAs wrote see their writes.
+HY_DEV bool last_block(unsigned* ticket, unsigned nb) {
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(ticket, 1u) == nb - 1;
   }
   __syncthreads();
   if (last) __threadfence();
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(256) k_deim_probe(
     }
     note_scores(sc, pos, tie_tol, run, ctl, cand);
   }
-  if (!last_block(&ctl->ticket)) return;
+  if (!last_block(&ctl->ticket, gridDim.x)) return;
   const double s = bitsd(*(volatile unsigned long long*)&ctl->smax);
   const double lim = s * (1.0 - 2.0 * tie_tol);
   const double cn2 = l == 0 ? 1.0 : ctl->cn2;
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256) k_deim_rest(
     }
     note_scores(sc, pos, tie_tol, run, ctl, cand);
   }
-  if (!last_block(&ctl->ticket)) return;
+  if (!last_block(&ctl->ticket, gridDim.x)) return;
   // ---- the pick, then the factors of step l + 1 (this CTA alone) ----
   const int tid = threadIdx.x;
   const unsigned long long key = pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked);
@@ -872,7 +874,7 @@ HY_DEV double limit_of(const OdCtl* ctl, double tie_tol) {
 // FP32 errors of z).  Rows whose bound reaches the limit are appended to
 // `list` for pass 2b.
 template <typename T>
-__global__ void __launch_bounds__(256) k_odeim_z1(
+HY_DEV void odeim_z1_body(int bid, int nb,
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
@@ -889,7 +891,7 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
   const int end = ctl->n_c;
   const int lane = threadIdx.x & 31;
   const float d2n = wt32[4096 + 384], d2d = wt32[4096 + 384 + 2];
-  for (int base = p0 + blockIdx.x * blockDim.x; base < end; base += gridDim.x * blockDim.x) {
+  for (int base = p0 + bid * blockDim.x; base < end; base += nb * blockDim.x) {
     const int pos = base + threadIdx.x;
     bool pass = false;
     if (pos < end) {
@@ -951,6 +953,16 @@ __global__ void __launch_bounds__(256) k_odeim_z1(
       if (pass) list[first + __popc(bal & ((1u << lane) - 1u))] = pos;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_odeim_z1(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int p0, double tie_tol, OdCtl* ctl,
+    double* __restrict__ scores, int* __restrict__ list, const float* __restrict__ R, int C) {
+  odeim_z1_body<T>(blockIdx.x, gridDim.x, phi, N, m, wt32, nrm, ord, picked, p0, tie_tol, ctl,
+                   scores, list, R, C);
 }
 
 // ---- certified bounds, eight lanes per row ----------------------------------
@@ -1254,7 +1266,7 @@ HY_DEV void bounds_row(const TileSm& S, int m, double l1, double l2, const float
 // rows the next pass takes: mu - l1 <= z_1^2 <= |phi_i|^2, so only rows
 // with |phi_i|^2 >= lim - l1 can reach the limit.
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
+HY_DEV void odeim_probe_body(int bid, int nb,
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
@@ -1269,7 +1281,7 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   stage_tile_tables(wt32, m, S);
   unsigned long long bestL = 0ull, cnt = 0;
-  for (int b0 = blockIdx.x * kTile; b0 < probe; b0 += gridDim.x * kTile) {
+  for (int b0 = bid * kTile; b0 < probe; b0 += nb * kTile) {
     const int pos = b0 + r;
     if (g == 0) {
       int i = -1;
@@ -1303,7 +1315,7 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
     if (bestL) atomicMax(&ctl->slo, bestL);
     if (cnt) atomicAdd(&ctl->stat[1], cnt);
   }
-  if (!last_block(&ctl->ticket)) return;
+  if (!last_block(&ctl->ticket, nb)) return;
   const double lim = limit_of(ctl, tie_tol);
   const int n = plan_end(bmax, bstart, probe, (lim - l1) / (1.0 + 1e-5));
   if (t == 0) {
@@ -1313,12 +1325,23 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord,
+    const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
+    const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
+    const float* __restrict__ R, int C) {
+  odeim_probe_body<T>(blockIdx.x, gridDim.x, phi, N, m, wt32, nrm, ord, picked, probe, bmax,
+                      bstart, tie_tol, ctl, scores, R, C);
+}
+
 // Pass 2b: both full bounds of the rows pass 2a listed, a tile of kTile
 // rows per CTA (U replaces the row's score); the best L raises the limit.
 // The rows whose U reaches the limit of the time, and the probe rows whose
 // U does, are listed in xlist for the exact pass.
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
+HY_DEV void odeim_screen_body(int bid, int nb,
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
     int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
@@ -1332,7 +1355,7 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
   const int count = ctl->n_list;
   {  // the probe rows
     const double lim = limit_of(ctl, tie_tol);
-    for (int base = blockIdx.x * kTileThreads; base < probe; base += gridDim.x * kTileThreads) {
+    for (int base = bid * kTileThreads; base < probe; base += nb * kTileThreads) {
       const int pos = base + t;
       const bool x = pos < probe && scores[pos] >= lim;
       const unsigned bal = __ballot_sync(0xffffffffu, x);
@@ -1344,11 +1367,11 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
       }
     }
   }
-  if ((int)blockIdx.x * kTile >= count) return;  // no listed row for this CTA
+  if ((int)bid * kTile >= count) return;  // no listed row for this CTA
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   stage_tile_tables(wt32, m, S);
   unsigned long long bestL = 0ull, cnt = 0;
-  for (int b0 = blockIdx.x * kTile; b0 < count; b0 += gridDim.x * kTile) {
+  for (int b0 = bid * kTile; b0 < count; b0 += nb * kTile) {
     if (g == 0) {
       const int e = b0 + r;
       const int pos = e < count ? list[e] : -1;
@@ -1378,6 +1401,16 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
     if (bestL) atomicMax(&ctl->slo, bestL);
     if (cnt) atomicAdd(&ctl->stat[1], cnt);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
+    const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
+    const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
+    int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
+    const float* __restrict__ R, int C) {
+  odeim_screen_body<T>(blockIdx.x, gridDim.x, phi, N, m, wt32, nrm, ord, list, probe, tie_tol,
+                       ctl, scores, xlist, R, C);
 }
 
 // ---- rank-one update of the eigensystem of M (one per oversampling step) ----
@@ -1539,7 +1572,7 @@ HY_DEV void r1_prepare_block(double* W, double* ds, const double* ph, int m, dou
 // then resets the step's control block.
 constexpr int kExactThreads = 128;
 template <typename T>
-__global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
+HY_DEV void odeim_exact_body(int bid, int nb,
     const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
     const double* __restrict__ W_s, const int* __restrict__ ord, const int* __restrict__ xlist,
     double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, int l,
@@ -1557,11 +1590,11 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const double l1 = ctl->lam1, l2 = ctl->lam2;
   const int nx = ctl->n_x;
-  const int G = gridDim.x;
+  const int G = nb;
   double best = 0.0;
   unsigned long long cnt = 0;
   bool staged = false;
-  for (int k0 = blockIdx.x; k0 < nx; k0 += 4 * G) {
+  for (int k0 = bid; k0 < nx; k0 += 4 * G) {
     if (tid == 0) {
       const double lnow = limit_of(ctl, tie_tol);
       int k = 0;
@@ -1602,7 +1635,7 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
   best = block_max(best);
   if (tid == 0) atomicMax(&ctl->smax, dbits(best));
   if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
-  if (!last_block(&ctl->ticket)) return;
+  if (!last_block(&ctl->ticket, nb)) return;
   // ---- the pick, then the update's preparation (this CTA alone) ----
   const unsigned long long key = pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked);
   if (l + 1 < np && key != ~0ull) {
@@ -1624,6 +1657,17 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
+    const double* __restrict__ W_s, const int* __restrict__ ord, const int* __restrict__ xlist,
+    double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, int l,
+    int np, int* __restrict__ pts, unsigned char* __restrict__ picked,
+    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot) {
+  odeim_exact_body<T>(blockIdx.x, gridDim.x, phi, N, m, lam_s, W_s, ord, xlist, tie_tol, ctl,
+                      scores, cand, l, np, pts, picked, R, C, wk, Wrot);
+}
+
 // One warp per root (CTA j); Delta[i * 64 + j] = d_i - lambda_j.
 // Root j lies in (d_j, d_{j+1}) (the last one in (d_n, d_n + |z|^2)); it is
 // computed as tau in coordinates shifted to the nearer pole o, so that
@@ -1639,9 +1683,9 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
 // inside a shrinking bracket (bisection otherwise); the iteration stops once
 // |f| is within the rounding error of its evaluation, the step is below
 // 2 ulp, or the bracket has collapsed.
-__global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
+HY_DEV void r1_roots_body(int bid, R1Work* wk, double* __restrict__ Delta) {
   pdl_enter();
-  const int j = blockIdx.x, lane = threadIdx.x;
+  const int j = bid, lane = threadIdx.x;
   const int nK = wk->nK;
   if (j >= nK) return;
   double dv[2], z2[2];
@@ -1819,14 +1863,18 @@ __global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
   }
 }
 
+__global__ void k_r1_roots(R1Work* wk, double* __restrict__ Delta) {
+  r1_roots_body(blockIdx.x, wk, Delta);
+}
+
 // Loewner's z (Gu & Eisenstat): with Delta_iq = d_i - lambda_q,
 //   zh_i^2 = (lambda_i - d_i) prod_{q != i} (lambda_q - d_i) / (d_q - d_i),
 // signed like z_i.  One warp per component i (lane: q and q + 32), a product
 // tree over the lanes.
-__global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __restrict__ Delta) {
+HY_DEV void r1_loewner_body(int bid, R1Work* wk, const double* __restrict__ Delta) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int i = bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nK = wk->nK;
   if (i >= nK) return;
   const double di = wk->dK[i];
@@ -1847,6 +1895,10 @@ __global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __
   }
 }
 
+__global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __restrict__ Delta) {
+  r1_loewner_body(blockIdx.x, wk, Delta);
+}
+
 // Eigenpair j of M + phi phi^T, written straight to its place in ascending
 // order (CTA j of m).  For j < nK, the new pair: the root
 // lambda_j = dK[org_j] + tau_j and the vector v_i = zh_i / (d_i - lambda_j)
@@ -1856,12 +1908,11 @@ __global__ void __launch_bounds__(128) k_r1_loewner(R1Work* wk, const double* __
 // eigenvalues (ties by index) is the column it takes in W_out and wt32.
 // CTA 0 also writes the sorted eigenvalues' control entries and the FP32
 // tails of wt32.
-__global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ wk,
-                                                    const double* __restrict__ Delta,
-                                                    const double* __restrict__ Wrot, int m,
-                                                    double* __restrict__ d_out,
-                                                    double* __restrict__ W_out, OdCtl* ctl,
-                                                    float* __restrict__ wt32) {
+HY_DEV void r1_vectors_body(int bid, const R1Work* __restrict__ wk,
+                                const double* __restrict__ Delta,
+                                const double* __restrict__ Wrot, int m,
+                                double* __restrict__ d_out, double* __restrict__ W_out,
+                                OdCtl* ctl, float* __restrict__ wt32) {
   pdl_enter();
   __shared__ double v[64];
   __shared__ double Wk[64 * 65];  // rows K[i] of Wrot, stride 65
@@ -1869,7 +1920,7 @@ __global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ w
   __shared__ int Ks[64];
   __shared__ double lv[64];
   __shared__ unsigned long long key[64];
-  const int j = blockIdx.x, tid = threadIdx.x;
+  const int j = bid, tid = threadIdx.x;
   const int nK = wk->nK;
   for (int i = tid; i < m; i += blockDim.x) {
     const double x = i < nK ? wk->dK[wk->org[i]] + wk->tau[i] : wk->dD[i - nK];
@@ -1947,6 +1998,15 @@ __global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ w
     }
     w32_tail(ls, m, wt32);
   }
+}
+
+__global__ void __launch_bounds__(256) k_r1_vectors(const R1Work* __restrict__ wk,
+                                                    const double* __restrict__ Delta,
+                                                    const double* __restrict__ Wrot, int m,
+                                                    double* __restrict__ d_out,
+                                                    double* __restrict__ W_out, OdCtl* ctl,
+                                                    float* __restrict__ wt32) {
+  r1_vectors_body(blockIdx.x, wk, Delta, Wrot, m, d_out, W_out, ctl, wt32);
 }
 
 __global__ void k_pad_sym2(const double* __restrict__ M, int m, int n, double* __restrict__ P) {
@@ -2097,7 +2157,8 @@ void pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t 
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg,
-                 bool norms_ready, OdeimGraphs* graphs) {
+                 bool norms_ready, OdeimGraphs* graphs, OdeimOver* over) {
+  if (over) over->active = 0;
   if (m <= 0) return 0;
   if (np > N) np = (int)N;
   OdeimBufs o = carve(ws, N, m);
@@ -2180,6 +2241,39 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   auto ML_ = [&](int id) {
     if (mark && (!graphs || s == 0)) mark(mark_arg, id);
   };
+  if (over) {  // the loop is left to a multi-instance launch
+    OdeimOver& v = *over;
+    v.phi = phi;
+    v.N = N;
+    v.m = m;
+    v.np = np;
+    v.probe = probe;
+    v.C = C;
+    v.tie_tol = tie_tol;
+    v.wt32 = o.wt32;
+    v.nrm = o.nrm;
+    v.ord = o.ord;
+    v.picked = o.picked;
+    v.bmax = o.bmax;
+    v.bstart = o.bstart;
+    v.ctl = o.ctl;
+    v.scores = o.scores;
+    v.list = o.list;
+    v.xlist = o.xlist;
+    v.R = o.rows;
+    v.lam[0] = o.lam_s;
+    v.lam[1] = o.lam_s2;
+    v.W[0] = o.W_s;
+    v.W[1] = o.W_s2;
+    v.cand = o.cand;
+    v.pts = pts;
+    v.r1 = o.r1;
+    v.Wrot = o.Wrot;
+    v.Delta = o.Delta;
+    if (v.m_cap < m) v.m_cap = m;
+    v.active = 1;
+    return 0;
+  }
   smem_at_least((const void*)k_odeim_exact<T>, smem_ex);
   // A step is four scoring passes (the last picks the point and prepares
   // the update) and the three of the eigensystem update.
@@ -2223,8 +2317,305 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
 }
 
 template int launch_odeim<float>(const float*, int64_t, int, int, double, int*, void*, void*,
-                                 cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*);
+                                 cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*,
+                                 OdeimOver*);
 template int launch_odeim<double>(const double*, int64_t, int, int, double, int*, void*, void*,
-                                  cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*);
+                                  cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*,
+                                  OdeimOver*);
+
+
+// ---- several instances' oversampling loops, one launch per pass ------------
+//
+// The loops of n instances advance together: greedy step t of every
+// instance (its point l = m + t) runs in one launch of each of the seven
+// passes, instead of seven launches per instance and step.  An instance whose
+// loop has ended (l >= np) leaves its CTAs idle.  The grid of a pass is the
+// concatenation of the instances' own grids: work list `start` (n + 1 entries
+// per pass) gives instance i the CTAs [start[i], start[i + 1]), and each
+// CTA runs the single-instance pass body with its index and count within its
+// instance, so the result is that of the instance's loop run alone (the
+// picked point depends only on the exact scores, not on the CTA that scored
+// a row).  The scoring passes' CTA counts follow the instance's row count
+// (rows per CTA: the autotuned knob); the update's follow its m.
+
+constexpr int kMultiPasses = 7;
+constexpr int kTuneCands = 4;
+constexpr int kRowsPerCta[kTuneCands] = {1024, 2048, 4096, 8192};
+constexpr int kTuneReps = 2;
+
+// the instance of CTA b: start[i] <= b < start[i + 1] (start ascending)
+HY_DEV int multi_inst(const int* __restrict__ start, int n, int b) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_multi_probe(const OdeimOver* __restrict__ d,
+                                                              const int* __restrict__ start,
+                                                              int n, int t) {
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  if (!o.active || o.m + t >= o.np) return;
+  odeim_probe_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N, o.m,
+                      o.wt32, o.nrm, o.ord, o.picked, o.probe, o.bmax, o.bstart, o.tie_tol,
+                      (OdCtl*)o.ctl, o.scores, o.R, o.C);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_multi_z1(const OdeimOver* __restrict__ d,
+                                                  const int* __restrict__ start, int n, int t) {
+  start += n + 1;
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  if (!o.active || o.m + t >= o.np) return;
+  odeim_z1_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N, o.m,
+                   o.wt32, o.nrm, o.ord, o.picked, o.probe, o.tie_tol, (OdCtl*)o.ctl, o.scores,
+                   o.list, o.R, o.C);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_multi_screen(const OdeimOver* __restrict__ d,
+                                                               const int* __restrict__ start,
+                                                               int n, int t) {
+  start += 2 * (n + 1);
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  if (!o.active || o.m + t >= o.np) return;
+  odeim_screen_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N,
+                       o.m, o.wt32, o.nrm, o.ord, o.list, o.probe, o.tie_tol, (OdCtl*)o.ctl,
+                       o.scores, o.xlist, o.R, o.C);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kExactThreads) k_multi_exact(const OdeimOver* __restrict__ d,
+                                                               const int* __restrict__ start,
+                                                               int n, int t) {
+  start += 3 * (n + 1);
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  const int l = o.m + t;
+  if (!o.active || l >= o.np) return;
+  odeim_exact_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N, o.m,
+                      o.lam[t & 1], o.W[t & 1], o.ord, o.xlist, o.tie_tol, (OdCtl*)o.ctl,
+                      o.scores, o.cand, l, o.np, o.pts, o.picked, o.R, o.C, (R1Work*)o.r1,
+                      o.Wrot);
+}
+
+__global__ void k_multi_roots(const OdeimOver* __restrict__ d, const int* __restrict__ start,
+                              int n, int t) {
+  start += 4 * (n + 1);
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  if (!o.active || o.m + t + 1 >= o.np) return;
+  r1_roots_body(blockIdx.x - start[i], (R1Work*)o.r1, o.Delta);
+}
+
+__global__ void __launch_bounds__(128) k_multi_loewner(const OdeimOver* __restrict__ d,
+                                                       const int* __restrict__ start, int n,
+                                                       int t) {
+  start += 5 * (n + 1);
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  if (!o.active || o.m + t + 1 >= o.np) return;
+  r1_loewner_body(blockIdx.x - start[i], (R1Work*)o.r1, o.Delta);
+}
+
+__global__ void __launch_bounds__(256) k_multi_vectors(const OdeimOver* __restrict__ d,
+                                                       const int* __restrict__ start, int n,
+                                                       int t) {
+  start += 6 * (n + 1);
+  const int i = multi_inst(start, n, blockIdx.x);
+  const OdeimOver& o = d[i];
+  const int j = blockIdx.x - start[i];
+  if (!o.active || o.m + t + 1 >= o.np || j >= o.m) return;
+  r1_vectors_body(j, (const R1Work*)o.r1, o.Delta, o.Wrot, o.m, o.lam[(t + 1) & 1],
+                  o.W[(t + 1) & 1], (OdCtl*)o.ctl, o.wt32);
+}
+
+struct OdeimMulti {
+  int cap = 0;                     // instances the buffers hold
+  OdeimOver* ddesc = nullptr;      // device: descriptors
+  int* dstart = nullptr;           // device: kMultiPasses work lists of n + 1 entries
+  OdeimOver* hdesc = nullptr;      // pinned staging of both
+  int* hstart = nullptr;
+  std::vector<long long> key;      // layout the graphs were captured for
+  std::vector<std::pair<int, GraphSlot>> graphs;  // by step count
+  // the autotuner: candidate c is timed kTuneReps times (ms per greedy step,
+  // the least kept), then the fastest is used from then on
+  int choice = -1;
+  int calls = 0;
+  float best[kTuneCands] = {-1.f, -1.f, -1.f, -1.f};
+  int timed_cand = -1, timed_steps = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+OdeimMulti* odeim_multi_create() {
+  OdeimMulti* mu = new (std::nothrow) OdeimMulti;
+  if (!mu) return nullptr;
+  if (cudaEventCreate(&mu->e0) != cudaSuccess || cudaEventCreate(&mu->e1) != cudaSuccess) {
+    cudaGetLastError();
+    odeim_multi_free(mu);
+    return nullptr;
+  }
+  return mu;
+}
+
+void odeim_multi_free(OdeimMulti* mu) {
+  if (!mu) return;
+  for (auto& g : mu->graphs) graph_slot_free(&g.second);
+  cudaFree(mu->ddesc);
+  cudaFree(mu->dstart);
+  cudaFreeHost(mu->hdesc);
+  cudaFreeHost(mu->hstart);
+  if (mu->e0) cudaEventDestroy(mu->e0);
+  if (mu->e1) cudaEventDestroy(mu->e1);
+  delete mu;
+}
+
+int odeim_multi_tuning(const OdeimMulti* mu, int* rows_per_cta, float* ms, int nc) {
+  if (!mu) return -1;
+  if (rows_per_cta) *rows_per_cta = mu->choice >= 0 ? kRowsPerCta[mu->choice] : 0;
+  for (int c = 0; c < nc && c < kTuneCands; ++c) ms[c] = mu->best[c];
+  return kTuneCands;
+}
+
+namespace {
+template <typename... KArgs, typename... Args>
+void pdl_multi(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+               Args&&... args) {
+  if (grid > 0) pdl(kern, grid, block, smem, s, std::forward<Args>(args)...);
+}
+
+int clampi(long long v, int lo, int hi) { return (int)(v < lo ? lo : v > hi ? hi : v); }
+}  // namespace
+
+template <typename T>
+int launch_odeim_multi(OdeimMulti* mu, const OdeimOver* const* inst, int n, cudaStream_t s) {
+  if (!mu || n <= 0) return 0;
+  // the timing of the previous call, if it was a tuning call
+  if (mu->timed_cand >= 0) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, mu->e0, mu->e1) == cudaSuccess && mu->timed_steps > 0) {
+      const float per = ms / mu->timed_steps;
+      float& b = mu->best[mu->timed_cand];
+      b = b < 0.f || per < b ? per : b;
+    }
+    cudaGetLastError();
+    mu->timed_cand = -1;
+  }
+  int cand = mu->choice;
+  if (cand < 0) {
+    if (mu->calls >= kTuneCands * kTuneReps) {
+      int c0 = 0;
+      for (int c = 1; c < kTuneCands; ++c)
+        if (mu->best[c] >= 0.f && (mu->best[c0] < 0.f || mu->best[c] < mu->best[c0])) c0 = c;
+      mu->choice = cand = c0;
+    } else {
+      cand = mu->calls / kTuneReps;
+    }
+  }
+  ++mu->calls;
+  if (n > mu->cap) {
+    cudaFree(mu->ddesc);
+    cudaFree(mu->dstart);
+    cudaFreeHost(mu->hdesc);
+    cudaFreeHost(mu->hstart);
+    mu->ddesc = nullptr;
+    mu->dstart = nullptr;
+    mu->hdesc = nullptr;
+    mu->hstart = nullptr;
+    mu->cap = 0;
+    const size_t sb = (size_t)kMultiPasses * (n + 1) * sizeof(int);
+    if (cudaMalloc((void**)&mu->ddesc, n * sizeof(OdeimOver)) != cudaSuccess ||
+        cudaMalloc((void**)&mu->dstart, sb) != cudaSuccess ||
+        cudaMallocHost((void**)&mu->hdesc, n * sizeof(OdeimOver)) != cudaSuccess ||
+        cudaMallocHost((void**)&mu->hstart, sb) != cudaSuccess)
+      return -1;
+    mu->cap = n;
+  }
+  // work lists and the graph key
+  const int rows = kRowsPerCta[cand];
+  std::vector<long long> key;
+  key.push_back(cand);
+  key.push_back(n);
+  int steps = 0;
+  int* st = mu->hstart;
+  for (int p = 0; p < kMultiPasses; ++p) st[p * (n + 1)] = 0;
+  for (int i = 0; i < n; ++i) {
+    const OdeimOver& v = *inst[i];
+    mu->hdesc[i] = v;
+    if (v.active && v.np - v.m > steps) steps = v.np - v.m;
+    const int mc = v.m_cap > 0 ? v.m_cap : 1;
+    const int cnt[kMultiPasses] = {
+        (v.probe + kTile - 1) / kTile,
+        clampi((v.N + rows - 1) / rows, 1, 152 * 16),
+        clampi((v.N + 2ll * rows - 1) / (2ll * rows), 1, 152 * 8),
+        clampi((v.N + 8ll * rows - 1) / (8ll * rows), 1, 152 * 2),
+        mc,
+        (mc + 3) / 4,
+        mc};
+    for (int p = 0; p < kMultiPasses; ++p) st[p * (n + 1) + i + 1] = st[p * (n + 1) + i] + cnt[p];
+    key.push_back(v.N);
+    key.push_back(v.probe);
+    key.push_back(mc);
+  }
+  if (steps == 0) return 0;
+  if (key != mu->key) {
+    for (auto& g : mu->graphs) graph_slot_free(&g.second);
+    mu->graphs.clear();
+    mu->key = key;
+  }
+  if (cudaMemcpyAsync(mu->ddesc, mu->hdesc, n * sizeof(OdeimOver), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(mu->dstart, mu->hstart, (size_t)kMultiPasses * (n + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return -1;
+  int grid[kMultiPasses];
+  for (int p = 0; p < kMultiPasses; ++p) grid[p] = st[p * (n + 1) + n];
+  const size_t smem_ex = sizeof(double) * ((size_t)64 * kLdw + 64 + 4 * 64 + 2 * 64 + 4 * 64);
+  smem_at_least((const void*)k_multi_exact<T>, smem_ex);
+  const OdeimOver* dd = mu->ddesc;
+  const int* ds = mu->dstart;
+  auto loop = [&]() {
+    for (int t = 0; t < steps; ++t) {
+      pdl_multi(k_multi_probe<T>, grid[0], kTileThreads, sizeof(TileSm), s, dd, ds, n, t);
+      pdl_multi(k_multi_z1<T>, grid[1], 256, 0, s, dd, ds, n, t);
+      pdl_multi(k_multi_screen<T>, grid[2], kTileThreads, sizeof(TileSm), s, dd, ds, n, t);
+      pdl_multi(k_multi_exact<T>, grid[3], kExactThreads, smem_ex, s, dd, ds, n, t);
+      if (t + 1 < steps) {
+        pdl_multi(k_multi_roots, grid[4], 32, 0, s, dd, ds, n, t);
+        pdl_multi(k_multi_loewner, grid[5], 128, 0, s, dd, ds, n, t);
+        pdl_multi(k_multi_vectors, grid[6], 256, 0, s, dd, ds, n, t);
+      }
+    }
+  };
+  GraphSlot* g = nullptr;
+  for (auto& e : mu->graphs)
+    if (e.first == steps) g = &e.second;
+  if (!g) {
+    mu->graphs.emplace_back(steps, GraphSlot{});
+    g = &mu->graphs.back().second;
+  }
+  const bool timing = mu->choice < 0;
+  if (timing) cudaEventRecord(mu->e0, s);
+  run_graphed(g, s, loop);
+  if (timing) {
+    cudaEventRecord(mu->e1, s);
+    mu->timed_cand = cand;
+    mu->timed_steps = steps;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template int launch_odeim_multi<float>(OdeimMulti*, const OdeimOver* const*, int, cudaStream_t);
+template int launch_odeim_multi<double>(OdeimMulti*, const OdeimOver* const*, int,
+                                        cudaStream_t);
 
 }  // namespace hy

@@ -157,6 +157,8 @@ def lib():
         "hyrom_load": (st, [vp, C.c_char_p]),
         "hyrom_batch_step": (st, [vp, i32, C.POINTER(HyromStepInfo), C.POINTER(i32)]),
         "hyrom_batch_threads": (i32, [vp]),
+        "hyrom_batch_set_mode": (st, [vp, i32]),
+        "hyrom_batch_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(C.c_float), i32]),
         "hyrom_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
@@ -456,6 +458,27 @@ def hyrom_load(ctx, path):
 
 def hyrom_batch_threads(batch):
     return lib().hyrom_batch_threads(batch)
+
+
+HYROM_BATCH_STREAMS, HYROM_BATCH_FUSED = 0, 1
+
+
+def hyrom_batch_set_mode(batch, mode):
+    """HYROM_BATCH_STREAMS (each instance's steps whole on its own stream) or
+    HYROM_BATCH_FUSED (all instances' oversampling loops as one launch per
+    pass under a CUDA graph)."""
+    s = lib().hyrom_batch_set_mode(batch, int(mode))
+    if s != HYROM_OK:
+        raise HyromError(s, "hyrom_batch_set_mode")
+
+
+def hyrom_batch_tuning(batch):
+    """The fused form's autotuner: (rows per CTA in use, 0 while timing;
+    measured ms per greedy step of each candidate, -1 if untimed)."""
+    r = C.c_int32()
+    ms = (C.c_float * 8)()
+    n = lib().hyrom_batch_tuning(batch, C.byref(r), ms, 8)
+    return r.value, [ms[i] for i in range(max(n, 0))]
 
 
 def hyrom_batch_destroy(batch):

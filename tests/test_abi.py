@@ -95,6 +95,8 @@ def test_batch_argument_checks_need_no_gpu(lib):
     assert out.value is None
     assert L.hyrom_batch_step(None, 1, None, None) == hyrom.HYROM_EINVAL
     assert L.hyrom_batch_threads(None) == 0
+    assert L.hyrom_batch_set_mode(None, hyrom.HYROM_BATCH_FUSED) == hyrom.HYROM_EINVAL
+    assert L.hyrom_batch_tuning(None, None, None, 0) == -1
     L.hyrom_batch_destroy(None)
 
 

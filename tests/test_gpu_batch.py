@@ -1,7 +1,8 @@
 """The batching form: instances stepped together by the library's thread
-pool (each on its own stream) give, instance by instance and step by step,
-the same bits as the same instances stepped alone; an FP64 instance of the
-batch also tracks the oracle."""
+pool (each on its own stream), or in the fused form (every instance's
+oversampling loop in one multi-instance launch per pass), give, instance by
+instance and step by step, the same bits as the same instances stepped
+alone; an FP64 instance of the batch also tracks the oracle."""
 import numpy as np
 import pytest
 
@@ -50,8 +51,9 @@ def _wide_instances():
     return [b for b in W.euler_batch(n_inst=8, seed=9, nmin=40, nmax=80, kmin=36, kmax=48)]
 
 
+@pytest.mark.parametrize("mode", ["streams", "fused"])
 @pytest.mark.parametrize("kind", ["uneven", "wide"])
-def test_batch_matches_instances_stepped_alone(kind):
+def test_batch_matches_instances_stepped_alone(kind, mode):
     hy = H()
     insts = _instances() if kind == "uneven" else _wide_instances()
     threads = 3 if kind == "uneven" else 8
@@ -74,9 +76,20 @@ def test_batch_matches_instances_stepped_alone(kind):
         b = hy.hyrom_batch_create(ctxs, threads=threads)
         try:
             assert hy.hyrom_batch_threads(b) == threads
+            hy.hyrom_batch_set_mode(b, hy.HYROM_BATCH_FUSED if mode == "fused"
+                                    else hy.HYROM_BATCH_STREAMS)
             st1, _ = hy.hyrom_batch_step(b, len(ctxs), nsteps=steps - 3, ctxs=ctxs)
             st2, infos = hy.hyrom_batch_step(b, len(ctxs), nsteps=3, ctxs=ctxs)
             assert st1 == [0] * len(ctxs) and st2 == [0] * len(ctxs)
+            rows, ms = hy.hyrom_batch_tuning(b)
+            if mode == "fused":
+                # the autotuner timed its first candidates (each twice) on
+                # these calls; the results above are the same whichever ran
+                # each step
+                assert rows in (0, 1024, 2048, 4096, 8192) and len(ms) == 4, (rows, ms)
+                assert sum(x > 0 for x in ms) >= 2, ms
+            else:
+                assert rows == 0
         finally:
             hy.hyrom_batch_destroy(b)
         for i, (ctx, (_, cfg)) in enumerate(zip(ctxs, insts)):
@@ -121,6 +134,12 @@ def test_batch_rejects_bad_arguments():
                 hy.hyrom_batch_create(bad)
         with pytest.raises(hy.HyromError):
             hy.hyrom_batch_create(ctxs, threads=-1)
+        b = hy.hyrom_batch_create(ctxs)
+        try:
+            with pytest.raises(hy.HyromError):
+                hy.hyrom_batch_set_mode(b, 2)
+        finally:
+            hy.hyrom_batch_destroy(b)
     finally:
         for c in ctxs:
             hy.hyrom_destroy(c)
