@@ -195,7 +195,10 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
   const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
   const T scale = (T)(NF == 1 ? 0.25 : (NF == 2 ? 0.0625 : 0.015625));
   const T dt = (T)c.dt;
-  double cnt = 0.0, dec = 0.0, tot = 0.0;
+  // the gate's totals: a thread's sums in the state's precision (one kept
+  // cell per thread and tile), combined over the CTA in FP64
+  int cnt_i = 0;
+  T dec_t = (T)0, tot_t = (T)0;
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const int tile = tiles ? tiles[it] : it;
     const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
@@ -376,9 +379,9 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
 #pragma unroll
           for (int a = 0; a < 4; ++a) gbuf[a * c.nc + cell] = gC[a];
           atomicOr(&kbits[cell >> 5], 1u << (cell & 31));
-          cnt += 1.0;
-          dec += (double)(ro - rn);
-          tot += (double)ro;
+          ++cnt_i;
+          dec_t += ro - rn;
+          tot_t += ro;
         }
       }
     } else {
@@ -431,16 +434,19 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
       if (rn < ro) {
         for (int a = 0; a < NV; ++a) gbuf[a * c.nc + cell] = gC[a];
         atomicOr(&kbits[cell >> 5], 1u << (cell & 31));
-        cnt += 1.0;
-        dec += (double)(ro - rn);
-        tot += (double)ro;
+        ++cnt_i;
+        dec_t += ro - rn;
+        tot_t += ro;
       }
     }
     }
   }
-  cnt = block_sum(cnt);
-  dec = block_sum(dec);
-  tot = block_sum(tot);
+  double cnt = 0.0, dec = 0.0, tot = 0.0;
+  if ((int)blockIdx.x < ntiles) {  // (a CTA without a tile adds nothing)
+    cnt = block_sum((double)cnt_i);
+    dec = block_sum((double)dec_t);
+    tot = block_sum((double)tot_t);
+  }
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x] = cnt;
     part[3 * blockIdx.x + 1] = dec;
@@ -643,7 +649,9 @@ void launch_filter_sparse(const DevCfg& c, const int* orders, int norders, int j
     int* nxt_n = counts + 1;
     for (int pass = 0; pass < jmax_f; ++pass) {
       cudaMemsetAsync(kbits, 0, nwords * sizeof(uint32_t), s);
-      const int grid = cur ? 152 * 8 : (nt < 152 * 8 ? nt : 152 * 8);
+      // one wave: three CTAs per SM (the kernel's register and shared
+      // memory bounds), tiles taken grid-stride
+      const int grid = cur ? 152 * 3 : (nt < 152 * 3 ? nt : 152 * 3);
 #define HY_FP(NV, NN, TXX, TYY)                                                              \
   do {                                                                                       \
     constexpr size_t sm_ = filter_pass_smem<T, NV, NN, TXX, TYY>();                          \
