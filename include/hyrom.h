@@ -239,7 +239,11 @@ hyrom_status hyrom_sample(hyrom_ctx* ctx, int32_t* idx_dev, int64_t cap, int64_t
 
 /* State access: gamma_k as nvar*Nc reals of the context precision. */
 hyrom_status hyrom_get_state(hyrom_ctx* ctx, void* q, int q_on_host);
-/* Overwrite gamma_k (and its snapshot-Gram entries).  Same layout. */
+/* Overwrite gamma_k (and its snapshot-Gram entries).  Same layout.  For
+ * FP32 contexts the snapshot-Gram row of the new gamma_k is formed by the
+ * next Gram update (the next step's, in the same pass over the window as
+ * that step's own row) or before the Gram matrix is next read, with the same
+ * values as when formed at once. */
 hyrom_status hyrom_set_state(hyrom_ctx* ctx, const void* q, int q_on_host);
 /* Basis in effect: Phi (ndof x m_eff reals, column-major, device) and
  * *m_eff; psi (ndof reals, device); points (n_p int32 dof rows in the order

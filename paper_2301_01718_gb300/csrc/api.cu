@@ -119,6 +119,9 @@ struct hyrom_ctx {
   double* H = nullptr;
   double* Hpart = nullptr;
   int gram_chunks = 0;
+  // a step whose state hyrom_set_state replaced and whose Gram row is still
+  // to form (-1: none); the next Gram update forms it in the same pass
+  int64_t gram_dirty = -1;
   double* hp = nullptr;
   double* pp = nullptr;
   double* Gc = nullptr;
@@ -401,9 +404,21 @@ template <typename T>
 void gram_update(hyrom_ctx* c, int64_t step) {
   if (!c->f32) return;
   t_begin(c, HYROM_T_GRAM);
-  hy::launch_gram_row<T>((const T*)c->ring, c->N, c->nslot, slot_of(c, step), c->Hpart,
-                         c->gram_chunks, c->H, c->st);
+  const int64_t d = c->gram_dirty;
+  c->gram_dirty = -1;
+  if (d >= 0 && d != step && slot_of(c, d) != slot_of(c, step))
+    hy::launch_gram_rows2<T>((const T*)c->ring, c->N, c->nslot, slot_of(c, d), slot_of(c, step),
+                             c->Hpart, c->gram_chunks, c->H, c->st);
+  else
+    hy::launch_gram_row<T>((const T*)c->ring, c->N, c->nslot, slot_of(c, step), c->Hpart,
+                           c->gram_chunks, c->H, c->st);
   t_end(c, HYROM_T_GRAM);
+}
+
+// Form a Gram row left pending by hyrom_set_state (before H is read).
+void gram_flush(hyrom_ctx* c) {
+  if (c->gram_dirty < 0) return;
+  gram_update<float>(c, c->gram_dirty);
 }
 
 // ---------------------------------------------------------------------------
@@ -636,6 +651,7 @@ template <typename T>
 hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<int>& win,
                    const T* psi, const std::vector<int>* psi_slots, T* phi_out, T* psi_next,
                    int* m_eff_host) {
+  if (ctx->f32 && (const void*)ring == ctx->ring) gram_flush(ctx);
   const int w = (int)win.size();
   const int wp = w % 2 ? w + 1 : w;
   bool tc_used = false;
@@ -1061,7 +1077,7 @@ hyrom_status hyrom_init(const hyrom_config* cfg, const double* q0, int q0_on_hos
   ok &= dal(ctx, &ctx->keys, nc * sizeof(unsigned long long));
   ok &= dalloc(ctx, &ctx->sel_scratch, hy::select_scratch_bytes());
   ok &= dal(ctx, &ctx->H, (size_t)ctx->nslot * ctx->nslot * sizeof(double));
-  ok &= dal(ctx, &ctx->Hpart, (size_t)(ctx->nslot + 1) * ctx->gram_chunks * sizeof(double));
+  ok &= dal(ctx, &ctx->Hpart, (size_t)(2 * ctx->nslot + 1) * ctx->gram_chunks * sizeof(double));
   ok &= dal(ctx, &ctx->hp, (size_t)(ctx->nslot + 1) * sizeof(double));
   ok &= dal(ctx, &ctx->pp, 64);
   ok &= dal(ctx, &ctx->Gc, (size_t)wp * wp * sizeof(double));
@@ -1684,6 +1700,7 @@ bool same_layout(const hyrom_config& a, const hyrom_config& b) {
 hyrom_status hyrom_save(hyrom_ctx* ctx, const char* path) {
   GUARD();
   if (!path) return HYROM_EINVAL;
+  if (ctx->f32) gram_flush(ctx);
   if (hyrom_status s = sync(ctx)) return s;
   FILE* f = fopen(path, "wb");
   if (!f) return fail(ctx, HYROM_EINVAL, "hyrom_save: cannot open %s", path);
@@ -1740,6 +1757,7 @@ hyrom_status hyrom_save(hyrom_ctx* ctx, const char* path) {
 hyrom_status hyrom_load(hyrom_ctx* ctx, const char* path) {
   GUARD();
   if (!path) return HYROM_EINVAL;
+  ctx->gram_dirty = -1;  // the file holds a complete H
   FILE* f = fopen(path, "rb");
   if (!f) return fail(ctx, HYROM_EINVAL, "hyrom_load: cannot open %s", path);
   bool ok = true;
@@ -1853,8 +1871,13 @@ hyrom_status hyrom_set_state(hyrom_ctx* ctx, const void* q, int q_on_host) {
   void* dst = (char*)ctx->ring + (size_t)slot_of(ctx, ctx->k) * ctx->N * ctx->esz;
   CK(cudaMemcpyAsync(dst, q, ctx->N * ctx->esz,
                      q_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->st));
-  if (ctx->f32)
-    gram_update<float>(ctx, ctx->k);
+  if (ctx->f32) {
+    // the new state's Gram row is formed by the next Gram update (the next
+    // step's, in the same pass over the window as its own row), or before H
+    // is next read
+    if (ctx->gram_dirty >= 0 && ctx->gram_dirty != ctx->k) gram_flush(ctx);
+    ctx->gram_dirty = ctx->k;
+  }
   CKL();
   return sync(ctx);
 }
@@ -2194,6 +2217,7 @@ hyrom_status hyrom_stage_pod(hyrom_ctx* ctx, const void* window, int32_t w, cons
   int me = 0;
   hyrom_status s;
   if (ctx->f32) {
+    ctx->gram_dirty = -1;  // every live row is formed again below
     // raw Gram of the caller's window (all pairs), psi given explicitly
     for (int i = 0; i < w; ++i)
       hy::launch_gram_row<float>((const float*)window, ctx->N, w, i, ctx->Hpart, ctx->gram_chunks,

@@ -201,6 +201,11 @@ void launch_cell_error(const T* g, const T* psi, const T* phi, int64_t nc, int n
 template <typename T>
 void launch_gram_row(const T* ring, int64_t N, int nslot, int s, double* part, int max_chunks,
                      double* H, cudaStream_t st);
+// rows s1 and s2 of H in one pass over the ring (the same bits as two
+// launch_gram_row calls); part holds 2 * nslot * max_chunks doubles
+template <typename T>
+void launch_gram_rows2(const T* ring, int64_t N, int nslot, int s1, int s2, double* part,
+                       int max_chunks, double* H, cudaStream_t st);
 void launch_gram_center(const double* H, int nslot, const int* win, int w, const int* ps,
                         int npsi, double* G, int ldg, double* xraw2, cudaStream_t s);
 void launch_gram_center_explicit(const double* H, int nslot, const int* win, int w,

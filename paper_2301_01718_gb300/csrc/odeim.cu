@@ -2218,11 +2218,12 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
   k_odeim_gram<T><<<(m + 3) / 4, 256, 0, HY_S(s)>>>(phi, N, m, pts, m, o.M);
   const size_t smem_ex = sizeof(double) * ((size_t)64 * kLdw + 64 + 4 * 64 + 2 * 64 + 4 * 64);
   M_(12);
-  // eigensystem of M: pivoted Cholesky + one-sided Jacobi; two-sided
-  // Jacobi if M is numerically rank deficient (its null space is needed)
+  // eigensystem of M: pivoted Cholesky + one-sided Jacobi (FP32 sweeps
+  // first, then FP64 sweeps to full accuracy); two-sided Jacobi if M is
+  // numerically rank deficient (its null space is needed)
   int rank_m = 0;
   if (run_psd_eig(o.M, m, o.V, o.lam, o.jbuf, o.jflag, (int*)host_pinned, 60, s,
-                  (int*)host_pinned + 2) < 0)
+                  (int*)host_pinned + 2, true) < 0)
     return -1;
   rank_m = ((int*)host_pinned)[2];
   cudaMemcpyAsync(&o.ctl->eig_sweeps, o.jflag + 4, sizeof(int), cudaMemcpyDeviceToDevice, s);

@@ -488,6 +488,50 @@ __global__ void k_gram_row(const T* __restrict__ ring, int64_t N, int s, int64_t
   if (threadIdx.x == 0) part[(int64_t)j * gridDim.y + blockIdx.y] = acc;
 }
 
+// Two rows at once, s1 and s2, in one pass over the ring: each block reads
+// its chunk of slot j once for both dot products.  Each dot product is
+// accumulated exactly as k_gram_row accumulates it (same rows per thread,
+// same order), so the rows are the same bits as two k_gram_row passes.
+// part: row s1's partials at [j * nchunk + y], row s2's at
+// [(nslot + j) * nchunk + y].
+template <typename T>
+__global__ void k_gram_row2(const T* __restrict__ ring, int64_t N, int s1, int s2, int64_t chunk,
+                            double* __restrict__ part) {
+  const int j = blockIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * chunk;
+  int64_t r1 = r0 + chunk;
+  if (r1 > N) r1 = N;
+  const T* a1 = ring + (int64_t)s1 * N;
+  const T* a2 = ring + (int64_t)s2 * N;
+  const T* b = ring + (int64_t)j * N;
+  double acc1 = 0.0, acc2 = 0.0;
+  if (sizeof(T) == 4) {
+    float hi1 = 0.f, lo1 = 0.f, hi2 = 0.f, lo2 = 0.f;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const float y = (float)b[r];
+      const float x1 = (float)a1[r], x2 = (float)a2[r];
+      const float p1 = x1 * y, p2 = x2 * y;
+      const float e1 = fmaf(x1, y, -p1), e2 = fmaf(x2, y, -p2);
+      ff_add(hi1, lo1, p1, e1);
+      ff_add(hi2, lo2, p2, e2);
+    }
+    acc1 = (double)hi1 + (double)lo1;
+    acc2 = (double)hi2 + (double)lo2;
+  } else {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const double y = (double)b[r];
+      acc1 = fma((double)a1[r], y, acc1);
+      acc2 = fma((double)a2[r], y, acc2);
+    }
+  }
+  acc1 = block_sum(acc1);
+  acc2 = block_sum(acc2);
+  if (threadIdx.x == 0) {
+    part[(int64_t)j * gridDim.y + blockIdx.y] = acc1;
+    part[((int64_t)gridDim.x + j) * gridDim.y + blockIdx.y] = acc2;
+  }
+}
+
 __global__ void k_gram_finalize(const double* __restrict__ part, int nslot, int nchunk, int s,
                                 double* __restrict__ H) {
   const int j = blockIdx.x;
@@ -509,6 +553,19 @@ void launch_gram_row(const T* ring, int64_t N, int nslot, int s, double* part, i
   dim3 grid(nslot, nchunk);
   k_gram_row<T><<<grid, 256, 0, HY_S(st)>>>(ring, N, s, chunk, part);
   k_gram_finalize<<<nslot, 256, 0, HY_S(st)>>>(part, nslot, nchunk, s, H);
+}
+
+template <typename T>
+void launch_gram_rows2(const T* ring, int64_t N, int nslot, int s1, int s2, double* part,
+                       int max_chunks, double* H, cudaStream_t st) {
+  int64_t chunk = (N + max_chunks - 1) / max_chunks;
+  if (chunk < 1024) chunk = 1024;
+  const int nchunk = (int)((N + chunk - 1) / chunk);
+  dim3 grid(nslot, nchunk);
+  k_gram_row2<T><<<grid, 256, 0, HY_S(st)>>>(ring, N, s1, s2, chunk, part);
+  k_gram_finalize<<<nslot, 256, 0, HY_S(st)>>>(part, nslot, nchunk, s1, H);
+  k_gram_finalize<<<nslot, 256, 0, HY_S(st)>>>(part + (size_t)nslot * nchunk, nslot, nchunk, s2,
+                                               H);
 }
 
 // Centred Gram of the window from the ring Gram H (nslot x nslot):
@@ -2026,6 +2083,8 @@ void launch_sign_fix(T* phi, int64_t N, int m, const int* m_eff, cudaStream_t s)
                                      const double*, T*, cudaStream_t);                          \
   template void launch_gram_row<T>(const T*, int64_t, int, int, double*, int, double*,          \
                                    cudaStream_t);                                               \
+  template void launch_gram_rows2<T>(const T*, int64_t, int, int, int, double*, int, double*,   \
+                                     cudaStream_t);                                             \
   template void launch_pod_coeffs<T>(const double*, const double*, int, int, int, double,       \
                                      double, const double*, double*, int*, T*, cudaStream_t);   \
   template void launch_form_phi<T>(const T*, int64_t, const int*, int, const T*, const T*, int, \

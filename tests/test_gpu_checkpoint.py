@@ -119,3 +119,63 @@ def test_init_batch_matches_instances_stepped_alone():
             assert np.array_equal(host(x), want)
     finally:
         hy.hyrom_batch_destroy(batch)
+
+
+def _run_with_set_state(hy, q0, cfg, steps, at, scale, flush_path=None):
+    """Steps of an FP32 run in which, after every step, the state is read and
+    written back through hyrom_get_state / hyrom_set_state (host buffers),
+    scaled by `scale` after step `at`; with flush_path, hyrom_save right
+    after each write forms the new state's Gram row at once."""
+    nw = (cfg.ncell + 31) // 32
+    bm = torch.zeros(nw, dtype=torch.int32, device="cuda")
+    q = torch.zeros(cfg.ndof, dtype=tdtype(cfg), device="cuda")
+    hq = torch.zeros(cfg.ndof, dtype=tdtype(cfg), pin_memory=True)
+    ctx = hy.hyrom_init(cfg, dev(np.asarray(q0).reshape(-1)))
+    out = []
+    try:
+        for i in range(steps):
+            info = hy.hyrom_step(ctx)
+            hy.hyrom_get_state(ctx, hq.data_ptr(), on_host=True)
+            if i == at:
+                hq.mul_(scale)
+            hy.hyrom_set_state(ctx, hq.data_ptr(), on_host=True)
+            if flush_path is not None:
+                hy.hyrom_save(ctx, flush_path)
+            if i < cfg.w:  # no sampled set before the first rebuild
+                continue
+            hy.hyrom_get_state(ctx, q)
+            hy.hyrom_sample(ctx, bitmap_dev=bm)
+            out.append((info["k"], host(q).copy(), bits_of(bm, cfg.ncell)))
+    finally:
+        hy.hyrom_destroy(ctx)
+    return out
+
+
+def test_set_state_gram_row_is_formed_with_the_same_bits(tmp_path):
+    """hyrom_set_state leaves the new state's snapshot-Gram row to the next
+    step's Gram pass (both rows in one pass over the window).  Writing back
+    the state a step produced changes nothing: the run keeps the bits of a
+    run without the round trips.  Writing a changed state gives the same bits
+    whether its row is formed in the next step's pass or at once (here by the
+    flush that hyrom_save makes)."""
+    hy = H()
+    q0, cfg, _ = W.euler_oblique_shock(n=48, seed=3, k=3)
+    steps = cfg.w + 8
+    ctx = hy.hyrom_init(cfg, dev(np.asarray(q0).reshape(-1)))
+    try:
+        for _ in range(cfg.w):
+            hy.hyrom_step(ctx)
+        plain = _record(hy, ctx, cfg, steps - cfg.w)
+    finally:
+        hy.hyrom_destroy(ctx)
+    same = _run_with_set_state(hy, q0, cfg, steps, at=-1, scale=1.0)
+    for a, b in zip(plain, same):
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]), a[0]
+    at = cfg.w + 2
+    late = _run_with_set_state(hy, q0, cfg, steps, at=at, scale=1.001)
+    now = _run_with_set_state(hy, q0, cfg, steps, at=at, scale=1.001,
+                              flush_path=str(tmp_path / "flush.ck"))
+    j = at + 1 - cfg.w  # the first recorded step after the change
+    assert not np.array_equal(late[j][1], plain[j][1])  # the change took effect
+    for a, b in zip(late, now):
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]), a[0]
