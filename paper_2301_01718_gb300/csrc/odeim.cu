@@ -899,11 +899,9 @@ HY_DEV void odeim_z1_body(int bid, int nb,
       double U = -1.0;
       if (!picked[i]) {
         float z1 = 0.f, z2 = 0.f;
-        if (pos < C) {  // contiguous copy (zero beyond m: same sum)
+        if (pos < C) {  // contiguous copy (zero beyond m: the m columns suffice)
           const float4* rp = reinterpret_cast<const float4*>(R + (int64_t)pos * 64);
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float4 v = rp[q];
+          auto term = [&](const float4 v, int q) {
             z1 = fmaf(w1[4 * q], v.x, z1);
             z1 = fmaf(w1[4 * q + 1], v.y, z1);
             z1 = fmaf(w1[4 * q + 2], v.z, z1);
@@ -912,10 +910,18 @@ HY_DEV void odeim_z1_body(int bid, int nb,
             z2 = fmaf(w2[4 * q + 1], v.y, z2);
             z2 = fmaf(w2[4 * q + 2], v.z, z2);
             z2 = fmaf(w2[4 * q + 3], v.w, z2);
+          };
+          const int nq = (m + 3) >> 2;
+          if (nq == 16) {  // all 16 loads in flight at once
+#pragma unroll
+            for (int q = 0; q < 16; ++q) term(rp[q], q);
+          } else {
+#pragma unroll 4
+            for (int q = 0; q < nq; ++q) term(rp[q], q);
           }
         } else {
-          for (int a = 0; a < 64; ++a) {
-            const float x = a < m ? (float)phi[(int64_t)a * N + i] : 0.f;
+          for (int a = 0; a < m; ++a) {
+            const float x = (float)phi[(int64_t)a * N + i];
             z1 = fmaf(w1[a], x, z1);
             z2 = fmaf(w2[a], x, z2);
           }
@@ -1015,7 +1021,7 @@ HY_DEV void tile_z(const T* __restrict__ phi, int64_t N, int m, const float* __r
     const int r = idx >> 4, k = idx & 15;
     const int pos = S.pos[r];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (pos >= 0) {
+    if (pos >= 0 && 4 * k < m) {  // (the product below reads the first m only)
       if (pos < C) {
         v = reinterpret_cast<const float4*>(R + (int64_t)pos * 64)[k];
       } else {
