@@ -194,9 +194,12 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
   const int ntiles = tiles ? *ntiles_dev : ntiles_all;
   const bool perx = c.bc[0] == HYROM_BC_PERIODIC, pery = c.bc[2] == HYROM_BC_PERIODIC;
   const T scale = (T)(NF == 1 ? 0.25 : (NF == 2 ? 0.0625 : 0.015625));
+  // the constants in the state's precision, converted once (a conversion
+  // from FP64 runs on the narrow FP64 pipe)
   const T dt = (T)c.dt;
+  const T gam = (T)c.gamma, dxT = (T)c.dx, dyT = (T)c.dy;
   // the gate's totals: a thread's sums in the state's precision (one kept
-  // cell per thread and tile), combined over the CTA in FP64
+  // cell per thread and tile), the CTA's too, combined over CTAs in FP64
   int cnt_i = 0;
   T dec_t = (T)0, tot_t = (T)0;
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
       T* fxg = fxq + NV * TY * (TX + 1);
       T* fyq = fxg + NV * TY * (TX + 1);  // y faces: row ly between ring rows ly, ly + 1
       T* fyg = fyq + (TWO ? NV * (TY + 1) * TX : 0);
-      const T g = (T)c.gamma;
+      const T g = gam;
       for (int idx = threadIdx.x; idx < GY * GX; idx += blockDim.x) {
         const int gy = idx / GX, gx = idx % GX;
         if (TWO && (gx == 0 || gx == GX - 1) && (gy == 0 || gy == GY - 1)) continue;  // unused
@@ -349,7 +352,6 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
       __syncthreads();
       // residual measures and the gate on the tile (the operator's
       // expressions of rhs_cell, from the shared face fluxes)
-      const T dxT = (T)c.dx, dyT = (T)c.dy;
       for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
         const int ly = idx / TX, lx = idx % TX;
         const int gi = x0 + lx, gj = y0 + ly;
@@ -441,11 +443,12 @@ __global__ void __launch_bounds__(256, 3) k_filter_pass(DevCfg c, const FiltArgs
     }
     }
   }
+  // over the CTA in the state's precision (the count exactly), then FP64
   double cnt = 0.0, dec = 0.0, tot = 0.0;
   if ((int)blockIdx.x < ntiles) {  // (a CTA without a tile adds nothing)
-    cnt = block_sum((double)cnt_i);
-    dec = block_sum((double)dec_t);
-    tot = block_sum((double)tot_t);
+    cnt = (double)block_sum(cnt_i);
+    dec = (double)block_sum(dec_t);
+    tot = (double)block_sum(tot_t);
   }
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x] = cnt;
