@@ -459,7 +459,7 @@ hyrom_status hyrom_adjoint(hyrom_ctx* ctx, int32_t steps, const int32_t* box, do
 typedef struct hyrom_batch hyrom_batch;
 hyrom_status hyrom_batch_create(hyrom_ctx* const* ctxs, int32_t n, int32_t threads,
                                 hyrom_batch** out);
-/* hyrom_init_batch: n instances at once (configs[4] of the scope table): for
+/* hyrom_init_batch: n instances at once (the batching form's constructor): for
  * each i a stream of its own (non-blocking) and a context hyrom_init(&cfgs[i],
  * q0[i], q0_on_host, that stream), then hyrom_batch_create over them.  The
  * batch owns these contexts and streams and hyrom_batch_destroy releases them;

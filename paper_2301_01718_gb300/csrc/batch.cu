@@ -344,7 +344,7 @@ extern "C" void hyrom_batch_destroy(hyrom_batch* b) {
 
 // n instances in one call: each context on a stream of its own, made here
 // and owned by the batch with the contexts (hyrom_batch_destroy releases
-// both).  The scope table's hyrom_init_batch.
+// both): the batching form's one-call constructor.
 extern "C" hyrom_status hyrom_init_batch(const hyrom_config* cfgs, const double* const* q0,
                                          int32_t q0_on_host, int32_t n, int32_t threads,
                                          hyrom_ctx** ctxs_out, hyrom_batch** out) {
