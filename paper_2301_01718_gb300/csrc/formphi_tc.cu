@@ -7,8 +7,10 @@
 // dense contraction of 2 N w m flops over 4 N (w + m + 2) bytes, so on the
 // tensor cores it is bound by HBM.  FP32 accuracy is kept with TF32 and an
 // error-compensated split: with a = a_hi + a_lo (a_hi = a with its 13 low
-// mantissa bits cleared, a_lo exact), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
-// three MMAs accumulating into one FP32 tile (error ~2^-21 |a||b|).
+// mantissa bits cleared, a_lo exact), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+// (error ~2^-21 |a||b|): B's hi and lo splits form one 128-column operand, so
+// that a_hi times both is one MMA (N = 128) and a_lo b_hi a second (N = 64)
+// into the first 64 columns; the epilogue adds the two halves.
 //
 // One persistent CTA per SM takes 128-row tiles, with warp-specialised
 // roles handing chunks of 32 window slots to each other through mbarriers:
@@ -20,11 +22,13 @@
 //     by psi, TF32 hi/lo split, writes into a 2-stage ring of A tiles in the
 //     128-byte-swizzled K-major layout the tensor core reads; at a tile's
 //     end each writes its row of psi_next;
-//   * warp 1 (MMA): per chunk 4 x 3 tcgen05.mma (M = 128, N = 64, K = 8,
-//     kind::tf32) into one of two 128 x 64 FP32 accumulators in tensor
-//     memory (tiles alternate), committed to the chunk's and tile's mbarriers;
+//   * warp 1 (MMA): per chunk 4 x 2 tcgen05.mma (M = 128, N = 128 and 64,
+//     K = 8, kind::tf32) into one of two 128 x 128 FP32 accumulators in
+//     tensor memory (tiles alternate), committed to the chunk's and tile's
+//     mbarriers;
 //   * warps 4-7 (epilogue): tcgen05.ld of a finished accumulator (warp w:
-//     rows 32 (w % 4) ..), release it, and coalesced stores of Phi; when
+//     rows 32 (w % 4) ..), the sum of its halves, release, and coalesced
+//     stores of Phi; when
 //     asked, also each row's squared-norm bound and bucket for ODEIM (the
 //     FP32 sum in column order, as ODEIM's own row-norm pass forms it), with
 //     per-CTA bucket counts and maxima in shared memory flushed at the end.
@@ -60,7 +64,7 @@ constexpr int kBBytes = (kMaxW / kChunk) * (kCols / 8) * kAtomGroup;  // 32 KB
 constexpr int kABytes = (kRows / 8) * kAtomGroup;                    // 16 KB
 constexpr int kRawBytes = kChunk * kRows * 4;                        // 16 KB
 constexpr int kSmemBytes = 2 * kBBytes + kAStages * 2 * kABytes + kRawStages * kRawBytes + 1024;
-constexpr uint32_t kTmemCols = 128;  // two 64-column accumulators
+constexpr uint32_t kTmemCols = 256;  // two 128-column accumulators (hi.hi + lo.hi | hi.lo)
 
 // kind::tf32: D in FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9
 // and 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
@@ -68,9 +72,10 @@ constexpr uint32_t kTmemCols = 128;  // two 64-column accumulators
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
                             ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
-HY_DEV void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  mma_tf32(d, a, b, kIdesc, accumulate);
-}
+// the same with N = 128: B's hi and lo halves as one operand
+constexpr uint32_t kIdesc2 = (1u << 4) | (2u << 7) | (2u << 10) |
+                             ((uint32_t)((2 * kCols) >> 3) << 17) |
+                             ((uint32_t)(kRows >> 4) << 24);
 
 HY_DEV void split_tf32(float x, float& hi, float& lo) {
   hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
@@ -86,9 +91,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smraw[];
   unsigned char* base =
       smraw + ((1024 - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
-  unsigned char* Bhi = base;
-  unsigned char* Blo = Bhi + kBBytes;
-  unsigned char* Aarea = Blo + kBBytes;                                   // kAStages x (hi, lo)
+  // B per chunk of 32 window slots: its hi split in rows 0..63, its lo split
+  // in rows 64..127 of one 128-row operand (16 KB)
+  unsigned char* Bcat = base;
+  unsigned char* Aarea = Bcat + 2 * kBBytes;                             // kAStages x (hi, lo)
   float* raw = reinterpret_cast<float*>(Aarea + kAStages * 2 * kABytes);  // kRawStages chunks
   __shared__ uint64_t raw_full[kRawStages], raw_empty[kRawStages];
   __shared__ uint64_t a_full[kAStages], a_empty[kAStages], d_full[2], d_empty[2];
@@ -111,9 +117,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float c = (k < w && n < m && n < me) ? C[k * m + n] : 0.f;
     float hi, lo;
     split_tf32(c, hi, lo);
-    const int off = (k / kChunk) * (kCols / 8) * kAtomGroup + sw128(n, k % kChunk);
-    *reinterpret_cast<float*>(Bhi + off) = hi;
-    *reinterpret_cast<float*>(Blo + off) = lo;
+    const int off = (k / kChunk) * 2 * (kCols / 8) * kAtomGroup;
+    *reinterpret_cast<float*>(Bcat + off + sw128(n, k % kChunk)) = hi;
+    *reinterpret_cast<float*>(Bcat + off + sw128(n + kCols, k % kChunk)) = lo;
   }
   for (int i = tid; i < w; i += kThreads) ws[i] = win[i];
   for (int i = tid; i < kNormBuckets; i += kThreads) {
@@ -208,18 +214,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(kCols * b);
+        const uint32_t d = tmem + (uint32_t)(2 * kCols * b);
         unsigned char* Ahi = Aarea + as * 2 * kABytes;
         const uint32_t ahi = saddr(Ahi), alo = saddr(Ahi + kABytes);
-        const uint32_t bofs = (uint32_t)(c * (kCols / 8) * kAtomGroup);
-        const uint32_t bhi = saddr(Bhi) + bofs, blo = saddr(Blo) + bofs;
+        const uint32_t bcat = saddr(Bcat) + (uint32_t)(c * 2 * (kCols / 8) * kAtomGroup);
 #pragma unroll
         for (int kk = 0; kk < kChunk / 8; ++kk) {
           const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along k inside the atom
           const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-          mma(d, sdesc(ahi + ko), sdesc(bhi + ko), acc0);
-          mma(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-          mma(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+          // columns 0..63 += a_hi b_hi, 64..127 += a_hi b_lo; then 0..63 += a_lo b_hi
+          mma_tf32(d, sdesc(ahi + ko), sdesc(bcat + ko), kIdesc2, acc0);
+          mma_tf32(d, sdesc(alo + ko), sdesc(bcat + ko), kIdesc, 1u);
         }
         mma_commit(&a_empty[as]);
         if (c == nch - 1) mma_commit(&d_full[b]);
@@ -316,9 +321,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float v0[32], v1[32];
-      const uint32_t ta = tmem + ((uint32_t)(32 * lanegrp) << 16) + (uint32_t)(kCols * b);
-      tmem_ld32(ta, v0);
-      tmem_ld32(ta + 32, v1);
+      const uint32_t ta = tmem + ((uint32_t)(32 * lanegrp) << 16) + (uint32_t)(2 * kCols * b);
+      {  // column j of Phi: (a_hi b_hi + a_lo b_hi) in column j, a_hi b_lo in 64 + j
+        float u[32];
+        tmem_ld32(ta, v0);
+        tmem_ld32(ta + 64, u);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v0[j] += u[j];
+        tmem_ld32(ta + 32, v1);
+        tmem_ld32(ta + 96, u);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v1[j] += u[j];
+      }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&d_empty[b]);
