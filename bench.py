@@ -446,7 +446,7 @@ def run_ours(a):
 # summarised in profiles/form_phi_tc_euler_1024.md (k_form_phi_tc, w = 128,
 # m = 64, 1024 x 1024 cells), scaled by dofs; set to None when the kernel
 # changes until it is captured again.
-FORMPHI_TRAFFIC_PER_DOF = (2164439000 + 1077174000) / 4194304  # 772.9 B per dof
+FORMPHI_TRAFFIC_PER_DOF = (2164398000 + 1078423000) / 4194304  # 773.2 B per dof
 
 
 def _peaks():
