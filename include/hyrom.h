@@ -96,14 +96,17 @@ enum { HYROM_RED_F32 = 0, HYROM_RED_TF32 = 1, HYROM_RED_BF16 = 2, HYROM_RED_TF32
  * within relative tie_tol go to the lowest index.  The reduced coordinates
  * are fitted on the rows regress_rows selects (HYROM_ROWS_*), the sample-row
  * normal matrix in precision reduced_prec (HYROM_RED_*; the tensor-core
- * precisions need FP32 states).  reserved_ must be 0. */
+ * precisions need FP32 states).  odeim_batch (0 or 1: the paper's ODEIM, one
+ * greedy point per scoring pass, Eq. odeim; 2..16: a cheaper variant that is
+ * not the paper's, taking the odeim_batch best rows of each pass, ties to the
+ * lowest index, before updating the sampled Gram matrix with all of them). */
 typedef struct {
   int32_t pde, scheme, precision, nx, ny;
   int32_t bc[4];
   double dx, dy, dt, gamma;
   double shock_n[2], shock_d0, shock_speed, shock_pre[4], shock_post[4];
   int32_t w, m, z, n_p, sel_mode, halo, jmax, jmax_f, newton_max, n_filt;
-  int32_t filt_orders[3], regress_rows, reduced_prec, reserved_;
+  int32_t filt_orders[3], regress_rows, reduced_prec, odeim_batch;
   double delta, top_frac, eps_y, eps_f, pod_tol, pod_abs, tie_tol, newton_tol;
   uint64_t seed;
 } hyrom_config;
@@ -316,7 +319,9 @@ hyrom_status hyrom_stage_pod(hyrom_ctx* ctx, const void* window, int32_t w, cons
                              void* phi_out, double* sigma_out, int32_t* m_eff);
 
 /* ODEIM_{n_p} (Eq. odeim) of phi (ndof x m): points_out gets n_p dof rows
- * in the order chosen (the m DEIM points first). */
+ * in the order chosen (the m DEIM points first).  With the context's
+ * odeim_batch b > 1, the oversampling points are taken b per scoring pass
+ * (the cheaper variant described at hyrom_config). */
 hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32_t n_p,
                                int32_t* points_out);
 

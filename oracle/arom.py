@@ -167,7 +167,11 @@ class Arom:
             Xc = np.stack([self._flat(g) - self._flat(self.psi) for g in win], axis=1)
             raw = float(np.sqrt(sum(float(np.sum(g * g)) for g in win)))
             self.Phi, _ = rom.pod(Xc, cfg.m, cfg.pod_tol, cfg.pod_abs * raw)  # POD
-            self.P = rom.odeim(self.Phi, cfg.n_p, cfg.tie_tol)    # ODEIM
+            b = getattr(cfg, "odeim_batch", 1)
+            if b > 1:   # the cheaper variant (not the paper's): b points per pass
+                self.P = rom.odeim_batched(self.Phi, cfg.n_p, cfg.tie_tol, b)
+            else:
+                self.P = rom.odeim(self.Phi, cfg.n_p, cfg.tie_tol)    # ODEIM
             self.s_hat, self.s_tilde = select.build_masks(self.G, self.P, cfg)  # sampling sets
             self.psi = rom.window_mean(win)                       # psi update
         info.n_p = len(self.P)

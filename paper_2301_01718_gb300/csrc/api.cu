@@ -329,7 +329,7 @@ hyrom_status validate(const hyrom_config* c, char* why, size_t nwhy) {
     return bad("reduced_prec");
   if (c->reduced_prec != HYROM_RED_F32 && c->precision != HYROM_PREC_F32)
     return bad("tensor-core normal matrices need FP32 states");
-  if (c->reserved_ != 0) return bad("reserved_ must be 0");
+  if (c->odeim_batch < 0 || c->odeim_batch > 16) return bad("odeim_batch must be in [0, 16]");
   if (c->jmax < 1 || c->jmax_f < 1 || c->newton_max < 1) return bad("iteration limits >= 1");
   if (c->n_filt < 0 || c->n_filt > 3) return bad("n_filt");
   for (int i = 0; i < c->n_filt; ++i)
@@ -866,7 +866,7 @@ hyrom_status update_basis_t(hyrom_ctx* ctx, hyrom_step_info* info) {
     if (ov && ov->m_cap < cf.m) ov->m_cap = cf.m < 64 ? cf.m : 64;
     if (hy::launch_odeim<T>((const T*)ctx->phi, ctx->N, me, np, cf.tie_tol, ctx->pts,
                             ctx->od_ws, (char*)ctx->host + 256, ctx->st, &odeim_mark, ctx,
-                            nr, &ctx->od_graphs, ov) < 0)
+                            nr, &ctx->od_graphs, ov, cf.odeim_batch) < 0)
       return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
     if (ov && ov->active) {  // finish_rebuild completes the step
       ctx->pend.on = true;
@@ -2247,12 +2247,15 @@ hyrom_status hyrom_stage_odeim(hyrom_ctx* ctx, const void* phi, int32_t m, int32
   GUARD();
   if (!phi || !points_out || m < 1 || m > ctx->cfg.m || n_p < m || n_p > 1024) return HYROM_EINVAL;
   int rc;
+  const int bs = ctx->cfg.odeim_batch;
   if (ctx->f32)
     rc = hy::launch_odeim<float>((const float*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol, points_out,
-                                 ctx->od_ws, (char*)ctx->host + 256, ctx->st);
+                                 ctx->od_ws, (char*)ctx->host + 256, ctx->st, nullptr, nullptr,
+                                 false, nullptr, nullptr, bs);
   else
     rc = hy::launch_odeim<double>((const double*)phi, ctx->N, m, n_p, ctx->cfg.tie_tol,
-                                  points_out, ctx->od_ws, (char*)ctx->host + 256, ctx->st);
+                                  points_out, ctx->od_ws, (char*)ctx->host + 256, ctx->st, nullptr,
+                                  nullptr, false, nullptr, nullptr, bs);
   if (rc < 0) return fail(ctx, HYROM_ECUDA, "ODEIM: %s", cudaGetErrorString(cudaGetLastError()));
   CKL();
   return sync(ctx);

@@ -308,7 +308,7 @@ int launch_sample_gram_tc(const float* phi, int64_t N, int m, const int* cells, 
 struct OdeimGraphs {
   GraphSlot deim, over;
   int64_t N = -1;
-  int m = -1, np = -1;
+  int m = -1, np = -1, bs = -1;
 };
 void odeim_graphs_free(OdeimGraphs* g);
 OdeimNorms odeim_norm_bufs(void* ws, int64_t N);
@@ -344,12 +344,14 @@ struct OdeimOver {
 };
 // over (nullable): if given, launch_odeim runs DEIM and the first
 // eigensystem, then describes the oversampling loop in *over instead of
-// running it (over->active = 0 when there is none).
+// running it (over->active = 0 when there is none).  bsel > 1: the
+// oversampling takes the bsel best rows per scoring pass (a cheaper variant,
+// not the paper's greedy); its loop is then always run here.
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int) = nullptr,
                  void* mark_arg = nullptr, bool norms_ready = false,
-                 OdeimGraphs* graphs = nullptr, OdeimOver* over = nullptr);
+                 OdeimGraphs* graphs = nullptr, OdeimOver* over = nullptr, int bsel = 1);
 // Several instances' oversampling loops (all of element type T) run
 // together: one launch per pass over all instances, a CTA's instance found
 // from a work list, replayed from a CUDA graph; the rows-per-CTA of the

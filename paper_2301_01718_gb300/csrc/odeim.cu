@@ -303,6 +303,61 @@ HY_DEV unsigned long long pick_winner(const double* __restrict__ scores,
   return best;
 }
 
+// Several points of one pass (the cheaper variant): nbp rounds of the
+// single pick over the same exact scores, each excluding the rows picked
+// before it (the best of the rest, its tie window, the lowest row in the
+// window).  Points l, l + 1, ... are recorded, their ordered positions in
+// pick_pos[0..) and their count in pick_pos[16].  Returns the first pick's
+// key (row << 32 | position), ~0 if none.
+HY_DEV unsigned long long pick_several(const double* __restrict__ scores,
+                                       const int* __restrict__ ord, const int* __restrict__ cand,
+                                       OdCtl* ctl, double tie_tol, int l, int nbp,
+                                       int* __restrict__ pts, unsigned char* __restrict__ picked,
+                                       int* __restrict__ pick_pos) {
+  const int nc = *(volatile int*)&ctl->ncand;
+  unsigned long long first = ~0ull;
+  int got = 0;
+  for (int r = 0; r < nbp; ++r) {
+    // keys 1 + bits of a score >= 0 (ordered like the score), 0 for none
+    unsigned long long mx = 0ull;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const int pos = cand[k];
+      const double sc = scores[pos];
+      if (sc >= 0.0 && !picked[ord[pos]]) {
+        const unsigned long long b = sc > 0.0 ? dbits(sc) + 1ull : 1ull;
+        mx = b > mx ? b : mx;
+      }
+    }
+    mx = block_max_u64(mx);
+    if (mx == 0ull) break;
+    const double lim = (mx > 1ull ? bitsd(mx - 1ull) : 0.0) * (1.0 - tie_tol);
+    unsigned long long best = ~0ull;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const int pos = cand[k];
+      const double sc = scores[pos];
+      if (sc >= 0.0 && sc >= lim && !picked[ord[pos]]) {
+        const unsigned long long key = ((unsigned long long)(unsigned)ord[pos] << 32) | (unsigned)pos;
+        best = key < best ? key : best;
+      }
+    }
+    best = block_min_u64(best);
+    if (best == ~0ull) break;
+    if (threadIdx.x == 0) {
+      const int p = (int)(best >> 32);
+      pts[l + r] = p;
+      picked[p] = 1;
+      pick_pos[r] = (int)(best & 0xffffffffull);
+      if (r == 0) ctl->argmin = p;
+    }
+    if (r == 0) first = best;
+    ++got;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pick_pos[16] = got;
+  __syncthreads();
+  return first;
+}
+
 // DEIM residual |r_i| of column l for ordered position pos (-1: picked),
 // by the four lanes of a quad (lane c = threadIdx.x % 4 sums the terms
 // j = c mod 4; an FP64 instruction holds its SM sub-partition for 64 cycles
@@ -1277,7 +1332,7 @@ HY_DEV void odeim_probe_body(int bid, int nb,
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
     const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
-    const float* __restrict__ R, int C) {
+    const float* __restrict__ R, int C, int bsel, double* __restrict__ Lbuf) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char tsm[];
   TileSm& S = *reinterpret_cast<TileSm*>(tsm);
@@ -1295,6 +1350,7 @@ HY_DEV void odeim_probe_body(int bid, int nb,
         i = ord[pos];
         if (picked[i]) {
           scores[pos] = -1.0;
+          if (bsel > 1) Lbuf[pos] = -1.0;
           i = -1;
         }
       }
@@ -1311,6 +1367,7 @@ HY_DEV void odeim_probe_body(int bid, int nb,
         scores[pos] = U;
         ++cnt;
         bestL = dbits(L) > bestL ? dbits(L) : bestL;
+        if (bsel > 1) Lbuf[pos] = L;
       }
     }
     __syncthreads();
@@ -1318,10 +1375,43 @@ HY_DEV void odeim_probe_body(int bid, int nb,
   bestL = block_max_u64(bestL);
   cnt = block_sum(cnt);
   if (t == 0) {
-    if (bestL) atomicMax(&ctl->slo, bestL);
+    if (bestL && bsel <= 1) atomicMax(&ctl->slo, bestL);
     if (cnt) atomicAdd(&ctl->stat[1], cnt);
   }
   if (!last_block(&ctl->ticket, nb)) return;
+  if (bsel > 1) {
+    // several points per pass: the limit is the bsel-th largest lower bound
+    // L of the probe rows (bsel rows score at least that much, so every row
+    // among the pass's bsel best reaches it), counted with multiplicity
+    unsigned long long above = ~0ull, kth = 0ull;
+    long long seen = 0;
+    for (int round = 0; round < bsel; ++round) {
+      unsigned long long mx = 0ull;
+      // keys: the bits of L > 0 (ordered like L), 0 for L <= 0; -1 marks a
+      // picked row
+      for (int q = t; q < probe; q += blockDim.x) {
+        const double v = Lbuf[q];
+        const unsigned long long k = v > 0.0 ? dbits(v) : 0ull;
+        if (v != -1.0 && k < above) mx = k > mx ? k : mx;
+      }
+      mx = block_max_u64(mx);
+      unsigned long long c = 0;
+      for (int q = t; q < probe; q += blockDim.x) {
+        const double v = Lbuf[q];
+        c += (v != -1.0 && (v > 0.0 ? dbits(v) : 0ull) == mx && mx < above) ? 1ull : 0ull;
+      }
+      c = block_sum(c);
+      if (c == 0) break;  // fewer than bsel probe rows: no limit from them
+      seen += (long long)c;
+      if (seen >= bsel) {
+        kth = mx;
+        break;
+      }
+      above = mx;
+    }
+    if (t == 0) ctl->slo = kth;
+    __syncthreads();
+  }
   const double lim = limit_of(ctl, tie_tol);
   const int n = plan_end(bmax, bstart, probe, (lim - l1) / (1.0 + 1e-5));
   if (t == 0) {
@@ -1337,9 +1427,9 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_probe(
     const float* __restrict__ nrm, const int* __restrict__ ord,
     const unsigned char* __restrict__ picked, int probe, const unsigned int* __restrict__ bmax,
     const int* __restrict__ bstart, double tie_tol, OdCtl* ctl, double* __restrict__ scores,
-    const float* __restrict__ R, int C) {
+    const float* __restrict__ R, int C, int bsel, double* __restrict__ Lbuf) {
   odeim_probe_body<T>(blockIdx.x, gridDim.x, phi, N, m, wt32, nrm, ord, picked, probe, bmax,
-                      bstart, tie_tol, ctl, scores, R, C);
+                      bstart, tie_tol, ctl, scores, R, C, bsel, Lbuf);
 }
 
 // Pass 2b: both full bounds of the rows pass 2a listed, a tile of kTile
@@ -1351,7 +1441,7 @@ HY_DEV void odeim_screen_body(int bid, int nb,
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
     int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
-    const float* __restrict__ R, int C) {
+    const float* __restrict__ R, int C, int bsel) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char tsm[];
   TileSm& S = *reinterpret_cast<TileSm*>(tsm);
@@ -1404,7 +1494,7 @@ HY_DEV void odeim_screen_body(int bid, int nb,
   bestL = block_max_u64(bestL);
   cnt = block_sum(cnt);
   if (t == 0) {
-    if (bestL) atomicMax(&ctl->slo, bestL);
+    if (bestL && bsel <= 1) atomicMax(&ctl->slo, bestL);  // (several points: the limit stays)
     if (cnt) atomicAdd(&ctl->stat[1], cnt);
   }
 }
@@ -1414,9 +1504,9 @@ __global__ void __launch_bounds__(kTileThreads) k_odeim_screen(
     const T* __restrict__ phi, int64_t N, int m, const float* __restrict__ wt32,
     const float* __restrict__ nrm, const int* __restrict__ ord, const int* __restrict__ list,
     int probe, double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ xlist,
-    const float* __restrict__ R, int C) {
+    const float* __restrict__ R, int C, int bsel) {
   odeim_screen_body<T>(blockIdx.x, gridDim.x, phi, N, m, wt32, nrm, ord, list, probe, tie_tol,
-                       ctl, scores, xlist, R, C);
+                       ctl, scores, xlist, R, C, bsel);
 }
 
 // ---- rank-one update of the eigensystem of M (one per oversampling step) ----
@@ -1583,7 +1673,8 @@ HY_DEV void odeim_exact_body(int bid, int nb,
     const double* __restrict__ W_s, const int* __restrict__ ord, const int* __restrict__ xlist,
     double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, int l,
     int np, int* __restrict__ pts, unsigned char* __restrict__ picked,
-    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot) {
+    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot, int bsel,
+    int* __restrict__ pick_pos) {
   pdl_enter();
   extern __shared__ double sh[];
   double* W = sh;               // 64 x kLdw
@@ -1630,7 +1721,7 @@ HY_DEV void odeim_exact_body(int bid, int nb,
       const double mu = secular_root_warp(zs + 64 * wid, lam, m, l1, l2);
       if (lane == 0) {
         scores[grp[wid]] = mu;
-        atomicMax(&ctl->smax, dbits(mu));  // raises the limit of later groups
+        if (bsel <= 1) atomicMax(&ctl->smax, dbits(mu));  // raises the limit of later groups
         cand[atomicAdd(&ctl->ncand, 1)] = grp[wid];
       }
       best = mu > best ? mu : best;
@@ -1639,11 +1730,14 @@ HY_DEV void odeim_exact_body(int bid, int nb,
     __syncthreads();
   }
   best = block_max(best);
-  if (tid == 0) atomicMax(&ctl->smax, dbits(best));
+  if (tid == 0 && bsel <= 1) atomicMax(&ctl->smax, dbits(best));
   if (lane == 0 && cnt) atomicAdd(&ctl->stat[2], cnt);
   if (!last_block(&ctl->ticket, nb)) return;
-  // ---- the pick, then the update's preparation (this CTA alone) ----
-  const unsigned long long key = pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked);
+  // ---- the pick(s), then the update's preparation (this CTA alone) ----
+  const unsigned long long key =
+      bsel <= 1 ? pick_winner(scores, ord, cand, ctl, tie_tol, l, pts, picked)
+                : pick_several(scores, ord, cand, ctl, tie_tol, l, np - l < bsel ? np - l : bsel,
+                               pts, picked, pick_pos);
   if (l + 1 < np && key != ~0ull) {
     const int p = (int)(key >> 32), wpos = (int)(key & 0xffffffffull);
     if (!staged) stage_w(W_s, lam_s, m, W, lam);
@@ -1669,9 +1763,51 @@ __global__ void __launch_bounds__(kExactThreads) k_odeim_exact(
     const double* __restrict__ W_s, const int* __restrict__ ord, const int* __restrict__ xlist,
     double tie_tol, OdCtl* ctl, double* __restrict__ scores, int* __restrict__ cand, int l,
     int np, int* __restrict__ pts, unsigned char* __restrict__ picked,
-    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot) {
+    const float* __restrict__ R, int C, R1Work* wk, double* __restrict__ Wrot, int bsel,
+    int* __restrict__ pick_pos) {
   odeim_exact_body<T>(blockIdx.x, gridDim.x, phi, N, m, lam_s, W_s, ord, xlist, tie_tol, ctl,
-                      scores, cand, l, np, pts, picked, R, C, wk, Wrot);
+                      scores, cand, l, np, pts, picked, R, C, wk, Wrot, bsel, pick_pos);
+}
+
+// The update's preparation for the r-th point (r >= 1) of a pass that took
+// several, once the eigensystem holds the earlier ones (one CTA).  Where the
+// pass found fewer points, the update is the identity: every component
+// deflated, the eigenpairs unchanged.
+template <typename T>
+__global__ void __launch_bounds__(kExactThreads) k_r1_prepare(
+    const T* __restrict__ phi, int64_t N, int m, const double* __restrict__ lam_s,
+    const double* __restrict__ W_s, const int* __restrict__ pts, int idx,
+    const int* __restrict__ pick_pos, int r, const float* __restrict__ R, int C, R1Work* wk,
+    double* __restrict__ Wrot) {
+  pdl_enter();
+  extern __shared__ double sh[];
+  double* W = sh;               // 64 x kLdw
+  double* lam = W + 64 * kLdw;  // 64
+  double* rb = lam + 64;        // 64
+  double* zp = rb + 4 * 64;     // 2 x 64
+  double* zs = zp + 2 * 64;     // 64
+  const int tid = threadIdx.x;
+  stage_w(W_s, lam_s, m, W, lam);
+  const int p = pts[idx], wpos = pick_pos[r];
+  if (r >= pick_pos[16] || p < 0 || p >= N || wpos < 0 || wpos >= N) {
+    __syncthreads();
+    if (tid == 0) {
+      wk->nK = 0;
+      wk->nD = m;
+    }
+    for (int j = tid; j < m; j += blockDim.x) {
+      wk->D[j] = j;
+      wk->dD[j] = lam[j];
+    }
+    for (int i = tid; i < m * m; i += blockDim.x) {
+      const int j = i / m, a = i - j * m;
+      Wrot[i] = W[j * kLdw + a];
+    }
+    return;
+  }
+  for (int a = tid; a < 64; a += blockDim.x) rb[a] = a < m ? phi_at<T>(phi, N, a, p, wpos, R, C) : 0.0;
+  __syncthreads();
+  r1_prepare_block(W, lam, rb, m, zp, zs, wk, Wrot);
 }
 
 // One warp per root (CTA j); Delta[i * 64 + j] = d_i - lambda_j.
@@ -2055,6 +2191,8 @@ struct OdeimBufs {
   double* jbuf;
   double* jscale;
   int* jflag;
+  double* Lbuf;   // several points per pass: the probe rows' lower bounds
+  int* pick_pos;  // the pass's picked positions, [16] = how many
   double* Li;  // DEIM: inverses of the bordered factors (64 x 64 row-major)
   double* Ui;
   double* yv;
@@ -2073,6 +2211,7 @@ size_t odeim_ws_bytes(int64_t N, int m) {
   b += sizeof(double) * (psd_eig_scratch_doubles(m + 1) + 2 * (m + 1) * (m + 1) + 512) + 3 * 256;
   b += sizeof(double) * (2 * 64 * 64 + 64) + 3 * 256;
   b += sizeof(float) * kW32 + 256;
+  b += sizeof(double) * kProbe + 256 + 32 * sizeof(int) + 256;
   return b + 4096;
 }
 
@@ -2120,6 +2259,8 @@ static OdeimBufs carve(void* ws, int64_t N, int m) {
   o.Ui = (double*)take((size_t)64 * 64 * sizeof(double));
   o.yv = (double*)take(64 * sizeof(double));
   o.wt32 = (float*)take(kW32 * sizeof(float));
+  o.Lbuf = (double*)take(kProbe * sizeof(double));
+  o.pick_pos = (int*)take(32 * sizeof(int));
   return o;
 }
 
@@ -2132,7 +2273,7 @@ void odeim_graphs_free(OdeimGraphs* g) {
   graph_slot_free(&g->deim);
   graph_slot_free(&g->over);
   g->N = -1;
-  g->m = g->np = -1;
+  g->m = g->np = g->bs = -1;
 }
 
 // Launch with programmatic stream serialization (the kernel starts with
@@ -2163,16 +2304,19 @@ void pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t 
 template <typename T>
 int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pts, void* ws,
                  void* host_pinned, cudaStream_t s, void (*mark)(void*, int), void* mark_arg,
-                 bool norms_ready, OdeimGraphs* graphs, OdeimOver* over) {
+                 bool norms_ready, OdeimGraphs* graphs, OdeimOver* over, int bsel) {
   if (over) over->active = 0;
   if (m <= 0) return 0;
   if (np > N) np = (int)N;
+  const int bs = bsel > 1 ? bsel : 1;
+  if (bs > 1) over = nullptr;  // (the multi-instance loops take one point per pass)
   OdeimBufs o = carve(ws, N, m);
-  if (graphs && (graphs->N != N || graphs->m != m || graphs->np != np)) {
+  if (graphs && (graphs->N != N || graphs->m != m || graphs->np != np || graphs->bs != bs)) {
     odeim_graphs_free(graphs);
     graphs->N = N;
     graphs->m = m;
     graphs->np = np;
+    graphs->bs = bs;
   }
   auto M_ = [&](int id) {
     if (mark) mark(mark_arg, id);
@@ -2282,14 +2426,18 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
     return 0;
   }
   smem_at_least((const void*)k_odeim_exact<T>, smem_ex);
-  // A step is four scoring passes (the last picks the point and prepares
-  // the update) and the three of the eigensystem update.
+  smem_at_least((const void*)k_r1_prepare<T>, smem_ex);
+  // A pass is four scoring launches (the last picks the pass's points and
+  // prepares the update for the first) and the three launches of each
+  // eigensystem update (one point per pass in the paper's ODEIM; with
+  // several, the updates of the later points each start with a preparation).
   auto over_loop = [&]() {
-    for (int l = m; l < np; ++l) {
+    for (int l = m; l < np;) {
+      const int nbp = np - l < bs ? np - l : bs;
       ML_(13);
       pdl(k_odeim_probe<T>, (probe + kTile - 1) / kTile, kTileThreads, sizeof(TileSm), s, phi,
           N, m, o.wt32, o.nrm, o.ord, o.picked, probe, o.bmax, o.bstart, tie_tol, o.ctl,
-          o.scores, o.rows, C);
+          o.scores, o.rows, C, bs, o.Lbuf);
       ML_(-14);
       ML_(14);
       pdl(k_odeim_z1<T>, 152 * 8, 256, 0, s, phi, N, m, o.wt32, o.nrm, o.ord, o.picked, probe,
@@ -2297,15 +2445,18 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
       ML_(-15);
       ML_(17);
       pdl(k_odeim_screen<T>, 152 * 4, kTileThreads, sizeof(TileSm), s, phi, N, m, o.wt32,
-          o.nrm, o.ord, o.list, probe, tie_tol, o.ctl, o.scores, o.xlist, o.rows, C);
+          o.nrm, o.ord, o.list, probe, tie_tol, o.ctl, o.scores, o.xlist, o.rows, C, bs);
       ML_(-18);
       ML_(15);
       pdl(k_odeim_exact<T>, 152, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, o.ord,
           o.xlist, tie_tol, o.ctl, o.scores, o.cand, l, np, pts, o.picked, o.rows, C, o.r1,
-          o.Wrot);
+          o.Wrot, bs, o.pick_pos);
       ML_(-16);
-      if (l + 1 < np) {
+      for (int i = 0; i < nbp && l + i + 1 < np; ++i) {
         ML_(16);
+        if (i > 0)
+          pdl(k_r1_prepare<T>, 1, kExactThreads, smem_ex, s, phi, N, m, o.lam_s, o.W_s, pts,
+              l + i, o.pick_pos, i, o.rows, C, o.r1, o.Wrot);
         pdl(k_r1_roots, m, 32, 0, s, o.r1, o.Delta);
         pdl(k_r1_loewner, (m + 3) / 4, 128, 0, s, o.r1, o.Delta);
         pdl(k_r1_vectors, m, 256, 0, s, o.r1, o.Delta, o.Wrot, m, o.lam_s2, o.W_s2, o.ctl,
@@ -2314,6 +2465,7 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
         std::swap(o.W_s, o.W_s2);
         ML_(-17);
       }
+      l += nbp;
     }
   };
   if (graphs)
@@ -2325,10 +2477,10 @@ int launch_odeim(const T* phi, int64_t N, int m, int np, double tie_tol, int* pt
 
 template int launch_odeim<float>(const float*, int64_t, int, int, double, int*, void*, void*,
                                  cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*,
-                                 OdeimOver*);
+                                 OdeimOver*, int);
 template int launch_odeim<double>(const double*, int64_t, int, int, double, int*, void*, void*,
                                   cudaStream_t, void (*)(void*, int), void*, bool, OdeimGraphs*,
-                                  OdeimOver*);
+                                  OdeimOver*, int);
 
 
 // ---- several instances' oversampling loops, one launch per pass ------------
@@ -2372,7 +2524,7 @@ __global__ void __launch_bounds__(kTileThreads) k_multi_probe(const OdeimOver* _
   if (!o.active || o.m + t >= o.np) return;
   odeim_probe_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N, o.m,
                       o.wt32, o.nrm, o.ord, o.picked, o.probe, o.bmax, o.bstart, o.tie_tol,
-                      (OdCtl*)o.ctl, o.scores, o.R, o.C);
+                      (OdCtl*)o.ctl, o.scores, o.R, o.C, 1, (double*)nullptr);
 }
 
 template <typename T>
@@ -2397,7 +2549,7 @@ __global__ void __launch_bounds__(kTileThreads) k_multi_screen(const OdeimOver* 
   if (!o.active || o.m + t >= o.np) return;
   odeim_screen_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N,
                        o.m, o.wt32, o.nrm, o.ord, o.list, o.probe, o.tie_tol, (OdCtl*)o.ctl,
-                       o.scores, o.xlist, o.R, o.C);
+                       o.scores, o.xlist, o.R, o.C, 1);
 }
 
 template <typename T>
@@ -2412,7 +2564,7 @@ __global__ void __launch_bounds__(kExactThreads) k_multi_exact(const OdeimOver* 
   odeim_exact_body<T>(blockIdx.x - start[i], start[i + 1] - start[i], (const T*)o.phi, o.N, o.m,
                       o.lam[t & 1], o.W[t & 1], o.ord, o.xlist, o.tie_tol, (OdCtl*)o.ctl,
                       o.scores, o.cand, l, o.np, o.pts, o.picked, o.R, o.C, (R1Work*)o.r1,
-                      o.Wrot);
+                      o.Wrot, 1, (int*)nullptr);
 }
 
 __global__ void k_multi_roots(const OdeimOver* __restrict__ d, const int* __restrict__ start,

@@ -33,7 +33,7 @@ class HyromConfig(C.Structure):
         ("sel_mode", C.c_int32), ("halo", C.c_int32), ("jmax", C.c_int32),
         ("jmax_f", C.c_int32), ("newton_max", C.c_int32), ("n_filt", C.c_int32),
         ("filt_orders", C.c_int32 * 3), ("regress_rows", C.c_int32),
-        ("reduced_prec", C.c_int32), ("reserved_", C.c_int32),
+        ("reduced_prec", C.c_int32), ("odeim_batch", C.c_int32),
         ("delta", C.c_double), ("top_frac", C.c_double), ("eps_y", C.c_double),
         ("eps_f", C.c_double), ("pod_tol", C.c_double), ("pod_abs", C.c_double),
         ("tie_tol", C.c_double), ("newton_tol", C.c_double),

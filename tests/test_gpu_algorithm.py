@@ -24,6 +24,11 @@ def _cases():
     # rebuilds after the warm-up
     q, c, _ = W.euler_oblique_shock(n=128, seed=3, k=16)
     yield "shock128_k16", q, c.with_(precision=W.PREC_F64, pod_tol=1e-10, pod_abs=1e-13), 38
+    # the cheaper oversampling variant (three points per scoring pass; the
+    # oracle takes the same variant)
+    q, c, _ = W.euler_oblique_shock(n=64, seed=3, k=4)
+    yield "shock_odeim_batch3", q, c.with_(precision=W.PREC_F64, pod_tol=1e-10, pod_abs=1e-13,
+                                           odeim_batch=3), 16
     # the sample-row form of the reduced solve (all dof rows of S-hat)
     u, c, _ = W.burgers_sine(n=256, seed=1)
     yield "burgers_sample_rows", u, c.with_(w=8, m=4, n_p=8, regress_rows=W.ROWS_SAMPLE), 30

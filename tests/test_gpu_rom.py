@@ -244,6 +244,27 @@ def test_odeim_points_identical(prec, N, m, n_p, conc):
     assert got == want
 
 
+@pytest.mark.parametrize("b", [2, 4])
+@pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_F32])
+@pytest.mark.parametrize("N,m,n_p,conc", [(600, 4, 9, False), (40000, 8, 17, True),
+                                          (40000, 16, 32, False)])
+def test_odeim_batched_points_identical(prec, N, m, n_p, conc, b):
+    """The cheaper oversampling variant (odeim_batch = b: the b best rows of
+    each scoring pass, not the paper's greedy) gives the oracle's
+    rom.odeim_batched points row for row, including a last pass with fewer
+    than b points."""
+    cfg = W.ArConfig(pde=W.PDE_BURGERS, scheme=W.SCHEME_RK2, nx=N, ny=1, dx=1.0 / N, dy=1.0,
+                     dt=1e-3, w=m + 2, m=m, n_p=n_p, precision=prec, odeim_batch=b)
+    Phi = _basis(N, m, 20 + m, prec, concentrated=conc)
+    want = rom.odeim_batched(Phi, n_p, cfg.tie_tol, b)
+    dt = torch.float32 if prec == W.PREC_F32 else torch.float64
+    with Ctx(cfg) as (hy, ctx):
+        pts = torch.zeros(n_p, dtype=torch.int32, device="cuda")
+        hy.hyrom_stage_odeim(ctx, dev(Phi.T.copy(), dt), m, n_p, pts)
+        got = host(pts).tolist()
+    assert got == want
+
+
 def _golden_odeim_cases():
     import json
     import os

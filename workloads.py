@@ -99,6 +99,9 @@ class ArConfig:
     newton_max: int = 50
     regress_rows: int = ROWS_ODEIM
     reduced_prec: int = RED_F32
+    # ODEIM oversampling points taken per scoring pass (1: the paper's greedy,
+    # one point per pass; b > 1: the b best rows of each pass, a cheaper variant)
+    odeim_batch: int = 1
     precision: int = PREC_F64
     seed: int = 0
 
