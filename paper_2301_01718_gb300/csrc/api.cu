@@ -647,6 +647,17 @@ hyrom_status advance_t(hyrom_ctx* ctx, hyrom_step_info* info) {
 
 constexpr bool kUseTensorBasisProduct = true;
 
+// n ints from host memory to dev on the context stream, staged through the
+// context's pinned scratch at byte offset off (bytes [1024, 4096) are kept for
+// this): a copy from pageable memory would first wait for the stream to drain.
+cudaError_t h2d_ints(hyrom_ctx* ctx, int* dev, const int* src, size_t n, size_t off) {
+  if (off < 1024 || off + n * sizeof(int) > 4096)
+    return cudaMemcpyAsync(dev, src, n * sizeof(int), cudaMemcpyHostToDevice, ctx->st);
+  int* stage = (int*)((char*)ctx->host + off);
+  memcpy(stage, src, n * sizeof(int));
+  return cudaMemcpyAsync(dev, stage, n * sizeof(int), cudaMemcpyHostToDevice, ctx->st);
+}
+
 template <typename T>
 hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<int>& win,
                    const T* psi, const std::vector<int>* psi_slots, T* phi_out, T* psi_next,
@@ -655,7 +666,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
   const int w = (int)win.size();
   const int wp = w % 2 ? w + 1 : w;
   bool tc_used = false;
-  CK(cudaMemcpyAsync(ctx->win_dev, win.data(), w * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(h2d_ints(ctx, ctx->win_dev, win.data(), (size_t)w, 1024));
   const hyrom_config& cf = ctx->cfg;
   if (!ctx->f32) {
     // FP64: one-sided Jacobi SVD of the centred window
@@ -688,8 +699,7 @@ hyrom_status pod_t(hyrom_ctx* ctx, const T* ring, int nslot, const std::vector<i
     t_begin(ctx, HYROM_T_EIG);
     bool ident_ok = psi_slots != nullptr;
     if (ident_ok) {
-      CK(cudaMemcpyAsync(ctx->ps_dev, psi_slots->data(), psi_slots->size() * sizeof(int),
-                         cudaMemcpyHostToDevice, ctx->st));
+      CK(h2d_ints(ctx, ctx->ps_dev, psi_slots->data(), psi_slots->size(), 2048));
       hy::launch_gram_center(ctx->H, nslot, ctx->win_dev, w, ctx->ps_dev, (int)psi_slots->size(),
                              ctx->Gc, wp, ctx->xraw2, ctx->st);
     } else {
